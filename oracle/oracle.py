@@ -1,0 +1,280 @@
+"""ctypes wrapper of the FP64 CPU oracle (``pz_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``.  The product path never imports it.
+
+The wrapper only marshals numpy arrays; every arithmetic step of the oracle is
+in the C file, except two plain numpy steps that are themselves definitions:
+applying the instrument's banded weights (a weighted sum over taps) and the
+species-to-element sum of per-line gradients.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pz_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int32)
+_lp = C.POINTER(C.c_int64)
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("n_depth", C.c_int32), ("n_species", C.c_int32),
+        ("m", _dp), ("T", _dp), ("rho", _dp), ("n_e", _dp), ("n_pert", _dp), ("pop", _dp),
+        ("mass_amu", _dp), ("xi_cms", C.c_double), ("kappa_c", _dp),
+        ("lambda0_nm", C.c_double), ("R_grid", C.c_double), ("n_lambda", C.c_int64),
+        ("n_lines", C.c_int64), ("lambda_nm", _dp),
+        ("log_gf", _fp), ("E_low_eV", _fp), ("log_gamma_rad", _fp), ("log_gamma4", _fp),
+        ("log_gamma6", _fp), ("species", _ip), ("half_window", C.c_int32),
+        ("dlog_gf", _dp), ("dlog_gamma6", _dp), ("dabund", _dp), ("elem_of_species", _ip),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, OpenMP over columns)."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = _LIB + ".tmp.%d" % os.getpid()
+        cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-ffp-contract=off",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = build()
+        L = C.CDLL(path)
+        L.pzo_voigt_vec.argtypes = [C.c_int64, _dp, _dp, _dp, _dp, _dp]
+        L.pzo_expn_vec.argtypes = [C.c_int, C.c_int64, _dp, _dp]
+        L.pzo_expn.argtypes = [C.c_int, C.c_double]
+        L.pzo_expn.restype = C.c_double
+        L.pzo_kappa_line.argtypes = [C.POINTER(_Problem), C.c_int64, _lp, _dp]
+        L.pzo_flux.argtypes = [C.POINTER(_Problem), C.c_int64, _lp, _dp, _dp, _dp]
+        L.pzo_instrument_taps.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, C.c_double,
+                                          C.c_int64, _dp, _lp, _ip, _dp, C.c_int32]
+        L.pzo_instrument_taps.restype = C.c_int
+        L.pzo_rt_adjoint.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
+        L.pzo_line_grad.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
+        L.pzo_chi2.argtypes = [C.c_int64, _dp, _dp, _dp, _dp]
+        L.pzo_chi2.restype = C.c_double
+        L.pzo_flux_tau.argtypes = [C.c_int, _dp, _dp]
+        L.pzo_flux_tau.restype = C.c_double
+        L.pzo_flux_dtau.argtypes = [C.c_int, _dp, _dp, _dp]
+        L.pzo_planck_nm.argtypes = [C.c_double, C.c_double]
+        L.pzo_planck_nm.restype = C.c_double
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a, t):
+    return a.ctypes.data_as(t)
+
+
+class _Keep:
+    """Holds the numpy arrays a _Problem points into."""
+
+    def __init__(self, prob, corrections=None):
+        at, ll = prob.atmos, prob.lines
+        self.arrs = {
+            "m": _d(at.m), "T": _d(at.T), "rho": _d(at.rho), "n_e": _d(at.n_e),
+            "n_pert": _d(at.n_pert), "pop": _d(at.pop), "mass": _d(at.mass_amu),
+            "kc": _d(prob.kappa_c), "lam": _d(ll.lambda_nm),
+            "gf": np.ascontiguousarray(ll.log_gf, np.float32),
+            "E": np.ascontiguousarray(ll.E_low_eV, np.float32),
+            "grad": np.ascontiguousarray(ll.log_gamma_rad, np.float32),
+            "g4": np.ascontiguousarray(ll.log_gamma4, np.float32),
+            "g6": np.ascontiguousarray(ll.log_gamma6, np.float32),
+            "sp": np.ascontiguousarray(ll.species, np.int32),
+        }
+        P = _Problem()
+        P.n_depth = at.n_depth
+        P.n_species = at.n_species
+        A = self.arrs
+        P.m, P.T, P.rho = _ptr(A["m"], _dp), _ptr(A["T"], _dp), _ptr(A["rho"], _dp)
+        P.n_e, P.n_pert, P.pop = _ptr(A["n_e"], _dp), _ptr(A["n_pert"], _dp), _ptr(A["pop"], _dp)
+        P.mass_amu = _ptr(A["mass"], _dp)
+        P.xi_cms = at.xi_cms
+        P.kappa_c = _ptr(A["kc"], _dp)
+        P.lambda0_nm = prob.grid.lambda0_nm
+        P.R_grid = prob.grid.R_grid
+        P.n_lambda = prob.grid.n_lambda
+        P.n_lines = ll.n_lines
+        P.lambda_nm = _ptr(A["lam"], _dp)
+        P.log_gf, P.E_low_eV = _ptr(A["gf"], _fp), _ptr(A["E"], _fp)
+        P.log_gamma_rad, P.log_gamma4, P.log_gamma6 = _ptr(A["grad"], _fp), _ptr(A["g4"], _fp), _ptr(A["g6"], _fp)
+        P.species = _ptr(A["sp"], _ip)
+        P.half_window = ll.half_window
+        if corrections:
+            if corrections.get("dlog_gf") is not None:
+                A["dgf"] = _d(corrections["dlog_gf"])
+                P.dlog_gf = _ptr(A["dgf"], _dp)
+            if corrections.get("dlog_gamma6") is not None:
+                A["dg6"] = _d(corrections["dlog_gamma6"])
+                P.dlog_gamma6 = _ptr(A["dg6"], _dp)
+            if corrections.get("dabund") is not None:
+                A["dab"] = _d(corrections["dabund"])
+                A["eos"] = np.ascontiguousarray(prob.elem_of_species, np.int32)
+                P.dabund = _ptr(A["dab"], _dp)
+                P.elem_of_species = _ptr(A["eos"], _ip)
+        self.P = P
+
+
+# ---------------------------------------------------------------------------
+# elementary functions
+# ---------------------------------------------------------------------------
+
+def voigt(a, v):
+    """H(a,v), L(a,v) = Im w, dH/da, elementwise."""
+    a, v = np.broadcast_arrays(np.asarray(a, np.float64), np.asarray(v, np.float64))
+    a, v = _d(a.ravel()), _d(v.ravel())
+    H, L, dH = np.empty_like(a), np.empty_like(a), np.empty_like(a)
+    lib().pzo_voigt_vec(a.size, _ptr(a, _dp), _ptr(v, _dp), _ptr(H, _dp), _ptr(L, _dp), _ptr(dH, _dp))
+    return H, L, dH
+
+
+def expn(n, x):
+    x = _d(np.atleast_1d(x))
+    out = np.empty_like(x)
+    lib().pzo_expn_vec(int(n), x.size, _ptr(x, _dp), _ptr(out, _dp))
+    return out
+
+
+def flux_tau(tau, S):
+    tau, S = _d(tau), _d(S)
+    return lib().pzo_flux_tau(tau.size, _ptr(tau, _dp), _ptr(S, _dp))
+
+
+def flux_dtau(tau, S):
+    tau, S = _d(tau), _d(S)
+    out = np.empty_like(tau)
+    lib().pzo_flux_dtau(tau.size, _ptr(tau, _dp), _ptr(S, _dp), _ptr(out, _dp))
+    return out
+
+
+def planck_nm(lambda_nm, T):
+    return lib().pzo_planck_nm(float(lambda_nm), float(T))
+
+
+# ---------------------------------------------------------------------------
+# synthesis stages
+# ---------------------------------------------------------------------------
+
+def kappa_line(prob, cols=None, corrections=None):
+    """kappa_line[d, c] for grid columns ``cols`` (default: all)."""
+    if cols is None:
+        cols = np.arange(prob.grid.n_lambda)
+    cols = np.ascontiguousarray(cols, np.int64)
+    k = _Keep(prob, corrections)
+    out = np.empty((prob.atmos.n_depth, cols.size))
+    lib().pzo_kappa_line(C.byref(k.P), cols.size, _ptr(cols, _lp), _ptr(out, _dp))
+    return out
+
+
+def flux(prob, cols, kline):
+    cols = np.ascontiguousarray(cols, np.int64)
+    kline = _d(kline)
+    k = _Keep(prob)
+    F, Fc = np.empty(cols.size), np.empty(cols.size)
+    lib().pzo_flux(C.byref(k.P), cols.size, _ptr(cols, _lp), _ptr(kline, _dp), _ptr(F, _dp), _ptr(Fc, _dp))
+    return F, Fc
+
+
+def instrument_taps(prob, inst, max_taps=4096):
+    pix = _d(inst.pix_lambda_nm)
+    n = pix.size
+    tap0 = np.empty(n, np.int64)
+    ntap = np.empty(n, np.int32)
+    w = np.zeros((n, max_taps))
+    k = _Keep(prob)
+    rc = lib().pzo_instrument_taps(C.byref(k.P), inst.v_r_kms, inst.v_b_kms, inst.R_lsf, n,
+                                   _ptr(pix, _dp), _ptr(tap0, _lp), _ptr(ntap, _ip), _ptr(w, _dp), max_taps)
+    if rc != 0:
+        raise ValueError("oracle instrument_taps failed: %d" % rc)
+    width = int(ntap.max())
+    return tap0, ntap, np.ascontiguousarray(w[:, :width])
+
+
+def apply_taps(tap0, ntap, w, F):
+    """(K F)_p = sum_k w_pk F[tap0_p + k]."""
+    out = np.zeros(tap0.size)
+    for k in range(w.shape[1]):
+        m = k < ntap
+        out[m] += w[m, k] * F[tap0[m] + k]
+    return out
+
+
+def apply_taps_T(tap0, ntap, w, g, n_lambda):
+    """(K^T g)_i."""
+    out = np.zeros(n_lambda)
+    for k in range(w.shape[1]):
+        m = k < ntap
+        np.add.at(out, tap0[m] + k, w[m, k] * g[m])
+    return out
+
+
+def forward(prob, corrections=None):
+    """Full forward on every column: kappa_line, F, F_c, f (instrument applied if present)."""
+    cols = np.arange(prob.grid.n_lambda)
+    kl = kappa_line(prob, cols, corrections)
+    F, Fc = flux(prob, cols, kl)
+    out = {"kline": kl, "F": F, "Fc": Fc}
+    if prob.instrument is not None:
+        taps = instrument_taps(prob, prob.instrument)
+        g, gc = apply_taps(*taps, F), apply_taps(*taps, Fc)
+        out.update(g=g, gc=gc, f=g / gc, taps=taps)
+    else:
+        out["f"] = F / Fc
+    return out
+
+
+def chi2(y, w, f):
+    y, w, f = _d(y), _d(np.broadcast_to(w, np.shape(y))), _d(f)
+    dL = np.empty_like(f)
+    L = lib().pzo_chi2(f.size, _ptr(y, _dp), _ptr(w, _dp), _ptr(f, _dp), _ptr(dL, _dp))
+    return L, dL
+
+
+def gradient(prob, y, w, corrections=None, fwd=None):
+    """Loss and hand-written adjoint: returns (L, g_gf, g_g6, g_abund, fwd)."""
+    if fwd is None:
+        fwd = forward(prob, corrections)
+    L, dLdf = chi2(y, w, fwd["f"])
+    if prob.instrument is not None:
+        tap0, ntap, wt = fwd["taps"]
+        dLdF = apply_taps_T(tap0, ntap, wt, dLdf / fwd["gc"], prob.grid.n_lambda)
+    else:
+        dLdF = dLdf / fwd["Fc"]
+    k = _Keep(prob, corrections)
+    kl = _d(fwd["kline"])
+    G = np.empty_like(kl)
+    lib().pzo_rt_adjoint(C.byref(k.P), _ptr(kl, _dp), _ptr(_d(dLdF), _dp), _ptr(G, _dp))
+    ggf = np.empty(prob.lines.n_lines)
+    gg6 = np.empty(prob.lines.n_lines)
+    lib().pzo_line_grad(C.byref(k.P), _ptr(G, _dp), _ptr(ggf, _dp), _ptr(gg6, _dp))
+    gab = None
+    if prob.elem_of_species is not None:
+        gab = np.zeros(prob.n_elem)
+        np.add.at(gab, prob.elem_of_species[prob.lines.species], ggf)
+    return L, ggf, gg6, gab, fwd

@@ -1,0 +1,511 @@
+/*
+ * pz_oracle.c -- plain FP64 CPU oracle for the synthesis hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and
+ * bench.py's CPU-baseline leg may load this library.  It shares no code,
+ * header, table or constant with the CUDA library; the two meet only in the
+ * seeded input arrays.
+ *
+ * Every routine is the plain definition written out in double precision, in
+ * the order the paper states it (arXiv:2607.24141, "The Payne Zero Project I"):
+ *
+ *   grid            Sec. 2.1, Eq. 1        lambda_i = lambda_0 (1 + 1/R)^i
+ *   line opacity    Sec. 2.1, Eqs. 4-5     LTE strength x Voigt profile,
+ *                                           phi = H(a,v) / (sqrt(pi) dnu_D)
+ *   extinction      Sec. 2.1, Eq. 3        chi = kappa_c + sum_l kappa_l (sigma_c = 0)
+ *   optical depth   Sec. 2.1 (dtau = chi dm), trapezoid on column mass
+ *   source          Sec. 2.1, Eq. 6        eps = 1  =>  S = B_lambda(T)
+ *   flux            Sec. 2.1, Eqs. 7-8     F = 2 pi Int S E_2 dtau, closed form
+ *                                           on piecewise-linear S
+ *   instrument      Sec. 7 (f_p equation) and Eq. 9: shift + broaden + LSF +
+ *                                           sampling, applied to F and F_c
+ *                                           before the ratio
+ *   adjoint         Sec. 6: reverse pass from the pixel loss to per-line
+ *                   Delta log gf, Delta log gamma_6 and abundances (Eq. 10)
+ *
+ * Readings where the paper is silent (units, window rule, boundary treatment)
+ * are the ones listed in the project's design notes; each is restated where
+ * it is used below.
+ *
+ * Voigt function: H(a,v) = Re w(v + i a), w the Faddeeva function.
+ *   |z| <  7 : H, L = Im w and dH/da from the Fourier representation
+ *              H + iL = pi^-1/2 Int_0^inf exp(-a t - t^2/4) exp(i v t) dt,
+ *              by composite Gauss-Legendre quadrature (12 panels x 16 nodes
+ *              on [0, 12.5]; the integrand there is below 1e-16 of its peak).
+ *   |z| >= 7 : the Laplace continued fraction
+ *              w(z) = (i/sqrt(pi)) / (z - (1/2)/(z - (2/2)/(z - (3/2)/(z - ...)))),
+ *              evaluated bottom-up, and dH/da = 2 (v L + a H) - 2/sqrt(pi)
+ *              (from w' = -2 z w + 2i/sqrt(pi)).
+ * Exponential integrals E_n: the power series (Abramowitz & Stegun 5.1.12)
+ * for x <= 1 and the modified-Lentz continued fraction for x > 1.
+ */
+#define _GNU_SOURCE
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- constants: CODATA 2018, cgs -------------------------------------- */
+#define O_H      6.62607015e-27      /* erg s */
+#define O_KB     1.380649e-16        /* erg K^-1 */
+#define O_C      2.99792458e10       /* cm s^-1 */
+#define O_E      4.80320471e-10      /* esu */
+#define O_ME     9.1093837015e-28    /* g */
+#define O_EV     1.602176634e-12     /* erg */
+#define O_AMU    1.66053906660e-24   /* g */
+#define O_PI     3.14159265358979323846
+#define O_SQRTPI 1.77245385090551602730
+#define O_LN10   2.30258509299404568402
+#define O_EULER  0.57721566490153286061
+
+/* ======================================================================= */
+/* Gauss-Legendre nodes by Newton iteration on P_n (plain textbook method). */
+/* ======================================================================= */
+#define GL_N 16
+#define GL_PANELS 12
+#define GL_TMAX 12.5
+static double gl_x[GL_N], gl_w[GL_N];
+static double fq_t[GL_N * GL_PANELS], fq_w[GL_N * GL_PANELS], fq_g[GL_N * GL_PANELS];
+
+static void gl_init(void) {
+    int n = GL_N;
+    for (int i = 0; i < n; ++i) {
+        double x = cos(O_PI * (i + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            double dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1; p1 = p2;
+        }
+        double dp = n * (x * p1 - p0) / (x * x - 1.0);
+        gl_x[i] = x;
+        gl_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    double h = GL_TMAX / GL_PANELS;
+    for (int p = 0; p < GL_PANELS; ++p)
+        for (int i = 0; i < n; ++i) {
+            double t = p * h + 0.5 * h * (gl_x[i] + 1.0);
+            fq_t[p * n + i] = t;
+            fq_w[p * n + i] = 0.5 * h * gl_w[i];
+            fq_g[p * n + i] = exp(-0.25 * t * t);
+        }
+}
+
+__attribute__((constructor)) static void oracle_init(void) { gl_init(); }
+
+/* ======================================================================= */
+/* Voigt function H(a,v), L = Im w, dH/da                                   */
+/* ======================================================================= */
+void pzo_voigt(double a, double v, double *H, double *L, double *dHda) {
+    double x = fabs(v);
+    double sgn = v < 0.0 ? -1.0 : 1.0;
+    if (x * x + a * a < 49.0) {
+        double sh = 0.0, sl = 0.0, sd = 0.0;
+        for (int k = 0; k < GL_N * GL_PANELS; ++k) {
+            double t = fq_t[k];
+            double e = fq_w[k] * fq_g[k] * exp(-a * t);
+            double s, c;
+            sincos(x * t, &s, &c);
+            sh += e * c;
+            sl += e * s;
+            sd -= t * e * c;
+        }
+        *H = sh / O_SQRTPI;
+        if (L) *L = sgn * sl / O_SQRTPI;
+        if (dHda) *dHda = sd / O_SQRTPI;
+        return;
+    }
+    /* bottom-up continued fraction in real arithmetic: r <- (k/2) / (z - r) */
+    double r2 = x * x + a * a;
+    int depth = r2 < 100.0 ? 24 : (r2 < 900.0 ? 12 : (r2 < 1e4 ? 8 : 6));
+    double rr = 0.0, ri = 0.0;
+    for (int k = depth; k >= 0; --k) {
+        double dr = x - rr, di = a - ri;
+        double q = (k > 0 ? 0.5 * k : 1.0) / (dr * dr + di * di);
+        rr = q * dr;
+        ri = -q * di;
+    }
+    /* after the k = 0 step, (rr, ri) = 1/(z - r); w = (i/sqrt(pi)) (rr + i ri) */
+    double complex w = (-ri + I * rr) / O_SQRTPI;
+    *H = creal(w);
+    if (L) *L = sgn * cimag(w);
+    if (dHda) *dHda = 2.0 * (x * cimag(w) + a * creal(w)) - 2.0 / O_SQRTPI;
+}
+
+/* ======================================================================= */
+/* Exponential integral E_n(x), n >= 0, x >= 0                              */
+/* ======================================================================= */
+double pzo_expn(int n, double x) {
+    if (n == 0) return exp(-x) / x;
+    if (x == 0.0) return n > 1 ? 1.0 / (n - 1) : INFINITY;
+    if (x > 1.0) {
+        /* modified Lentz evaluation of
+           E_n(x) = e^-x ( 1/(x+n-) 1*n/(x+n+2-) 2(n+1)/(x+n+4-) ... )            */
+        const double tiny = 1e-300;
+        double b = x + n, c = 1.0 / tiny, d = 1.0 / b, h = d;
+        for (int i = 1; i < 100000; ++i) {
+            double an = -(double)i * (n - 1 + i);
+            b += 2.0;
+            d = 1.0 / (an * d + b);
+            c = b + an / c;
+            double del = c * d;
+            h *= del;
+            if (fabs(del - 1.0) < 1e-16) break;
+        }
+        return h * exp(-x);
+    }
+    /* A&S 5.1.12: E_n(x) = (-x)^{n-1}/(n-1)! [-ln x + psi(n)]
+                           - sum_{m>=0, m != n-1} (-x)^m / ((m-n+1) m!)        */
+    double psi = -O_EULER;
+    for (int k = 1; k <= n - 1; ++k) psi += 1.0 / k;
+    double sum = 0.0, term = 1.0;  /* term = (-x)^m / m! */
+    double lead = 0.0;
+    for (int m = 0; m < 200; ++m) {
+        if (m > 0) term *= -x / m;
+        if (m == n - 1) {
+            lead = term * (-log(x) + psi);
+        } else {
+            double t = term / (m - n + 1);
+            sum -= t;
+            if (m > n && fabs(t) < 1e-18 * fabs(sum)) break;
+        }
+    }
+    return lead + sum;
+}
+
+/* ======================================================================= */
+/* Problem description (mirrors the ctypes structure in oracle.py)          */
+/* ======================================================================= */
+typedef struct {
+    int32_t n_depth, n_species;
+    const double *m, *T, *rho, *n_e, *n_pert, *pop, *mass_amu;
+    double xi_cms;
+    const double *kappa_c;          /* [n_depth][n_lambda] */
+    double lambda0_nm, R_grid;
+    int64_t n_lambda;
+    int64_t n_lines;
+    const double *lambda_nm;
+    const float *log_gf, *E_low_eV, *log_gamma_rad, *log_gamma4, *log_gamma6;
+    const int32_t *species;
+    int32_t half_window;
+    /* optional calibration corrections (Eq. 10); NULL means zero */
+    const double *dlog_gf, *dlog_gamma6;   /* [n_lines] */
+    const double *dabund;                  /* [n_elem] */
+    const int32_t *elem_of_species;        /* [n_species] */
+} pzo_problem;
+
+/* Eq. 1 */
+static double grid_lambda_cm(const pzo_problem *P, int64_t i) {
+    return P->lambda0_nm * 1e-7 * exp((double)i * log1p(1.0 / P->R_grid));
+}
+
+/* fractional centre index x_l and integer placement i_l = floor(x_l + 1/2) */
+static double centre_x(const pzo_problem *P, int64_t l) {
+    return log(P->lambda_nm[l] / P->lambda0_nm) / log1p(1.0 / P->R_grid);
+}
+
+/* Planck function per nanometre, B_lambda(T) = 2hc^2 lambda^-5 / (e^{hc/lambda kT} - 1) x 1e-7 */
+static double planck_nm(double lambda_cm, double T) {
+    double x = O_H * O_C / (lambda_cm * O_KB * T);
+    return 2.0 * O_H * O_C * O_C / pow(lambda_cm, 5.0) / expm1(x) * 1e-7;
+}
+
+/* Per (line, depth) quantities of Eqs. 4-5 and the line term at one lambda. */
+typedef struct {
+    double A;        /* (pi e^2/m_e c) gf n/(rho U) e^{-E/kT} / (sqrt(pi) dnu_D) */
+    double a;        /* damping parameter */
+    double a6;       /* van der Waals part of a (for d a / d Delta log gamma_6 = ln10 a6) */
+    double dvD;      /* Doppler velocity width, cm/s */
+} line_depth;
+
+static line_depth line_at_depth(const pzo_problem *P, int64_t l, int d) {
+    line_depth q;
+    int s = P->species[l];
+    double T = P->T[d];
+    double lam_cm = P->lambda_nm[l] * 1e-7;
+    double dvD = sqrt(2.0 * O_KB * T / (P->mass_amu[s] * O_AMU) + P->xi_cms * P->xi_cms);
+    double dnuD = dvD / lam_cm;                           /* nu_l dv_D / c */
+    double dgf = P->dlog_gf ? P->dlog_gf[l] : 0.0;
+    double dg6 = P->dlog_gamma6 ? P->dlog_gamma6[l] : 0.0;
+    double dab = (P->dabund && P->elem_of_species) ? P->dabund[P->elem_of_species[s]] : 0.0;
+    double gf = pow(10.0, (double)P->log_gf[l] + dgf);
+    double pop = P->pop[(int64_t)s * P->n_depth + d] * pow(10.0, dab);
+    double boltz = exp(-(double)P->E_low_eV[l] * O_EV / (O_KB * T));
+    double pie2mc = O_PI * O_E * O_E / (O_ME * O_C);
+    q.A = pie2mc * gf * (pop / P->rho[d]) * boltz / (O_SQRTPI * dnuD);
+    double g_rad = pow(10.0, (double)P->log_gamma_rad[l]);
+    double g4 = pow(10.0, (double)P->log_gamma4[l]);
+    double g6 = pow(10.0, (double)P->log_gamma6[l] + dg6);
+    q.a = (g_rad + g4 * P->n_e[d] + g6 * P->n_pert[d]) / (4.0 * O_PI * dnuD);
+    q.a6 = g6 * P->n_pert[d] / (4.0 * O_PI * dnuD);
+    q.dvD = dvD;
+    return q;
+}
+
+/* 1 - exp(-h nu / kT) at the sample frequency (Eq. 4, factored out of the sum) */
+static double stim_emission(const pzo_problem *P, int64_t i, int d) {
+    return -expm1(-O_H * O_C / (grid_lambda_cm(P, i) * O_KB * P->T[d]));
+}
+
+/* kappa_line(i, d) for the requested columns; out[d * n_cols + c].
+ * Sum over every line whose window |i - i_l| <= W contains column i
+ * (window clipped to the grid; centre test off). */
+void pzo_kappa_line(const pzo_problem *P, int64_t n_cols, const int64_t *cols, double *out) {
+    int nd = P->n_depth;
+    int64_t nl = P->n_lines;
+    int W = P->half_window;
+    int64_t *il = (int64_t *)malloc(sizeof(int64_t) * (nl > 0 ? nl : 1));
+    double *xl = (double *)malloc(sizeof(double) * (nl > 0 ? nl : 1));
+    for (int64_t l = 0; l < nl; ++l) {
+        xl[l] = centre_x(P, l);
+        il[l] = (int64_t)floor(xl[l] + 0.5);
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t c = 0; c < n_cols; ++c) {
+        int64_t i = cols[c];
+        double lam_i = grid_lambda_cm(P, i);
+        for (int d = 0; d < nd; ++d) out[(int64_t)d * n_cols + c] = 0.0;
+        for (int64_t l = 0; l < nl; ++l) {
+            int64_t di = i - il[l];
+            if (di < -W || di > W) continue;
+            double lam_l = P->lambda_nm[l] * 1e-7;
+            for (int d = 0; d < nd; ++d) {
+                line_depth q = line_at_depth(P, l, d);
+                double v = (lam_l / lam_i - 1.0) * O_C / q.dvD;   /* (nu - nu_l)/dnu_D */
+                double H;
+                pzo_voigt(q.a, v, &H, NULL, NULL);
+                out[(int64_t)d * n_cols + c] += q.A * H;
+            }
+        }
+        for (int d = 0; d < nd; ++d) out[(int64_t)d * n_cols + c] *= stim_emission(P, i, d);
+    }
+    free(il);
+    free(xl);
+}
+
+/* ---- formal solution ----------------------------------------------------- */
+
+/* Int_{ta}^{tb} S E_2 dtau for S linear from Sa to Sb:
+ *   Sa (E3(ta) - E3(tb)) + s (E4(ta) - E4(tb) - (tb - ta) E3(tb)),  s = (Sb-Sa)/(tb-ta) */
+static double interval_integral(double ta, double tb, double Sa, double Sb) {
+    double s = (Sb - Sa) / (tb - ta);
+    double e3a = pzo_expn(3, ta), e3b = pzo_expn(3, tb);
+    double e4a = pzo_expn(4, ta), e4b = pzo_expn(4, tb);
+    return Sa * (e3a - e3b) + s * (e4a - e4b - (tb - ta) * e3b);
+}
+
+/* tau by the trapezoid on column mass, tau_0 = chi_0 m_0 (constant opacity above layer 0) */
+static void optical_depth(int nd, const double *m, const double *chi, double *tau) {
+    tau[0] = chi[0] * m[0];
+    for (int d = 0; d + 1 < nd; ++d) tau[d + 1] = tau[d] + 0.5 * (chi[d] + chi[d + 1]) * (m[d + 1] - m[d]);
+}
+
+/* F_lambda = 2 pi Int_0^{tau_max} S E_2 dtau; S linear in tau between layers, the first
+ * segment extrapolated linearly to tau = 0, nothing below the bottom layer. */
+static double flux_from(int nd, const double *tau, const double *S) {
+    double s0 = (S[1] - S[0]) / (tau[1] - tau[0]);
+    double S_top = S[0] - s0 * tau[0];
+    double F = interval_integral(0.0, tau[0], S_top, S[0]);
+    for (int d = 0; d + 1 < nd; ++d) F += interval_integral(tau[d], tau[d + 1], S[d], S[d + 1]);
+    return 2.0 * O_PI * F;
+}
+
+/* F and F_c for the requested columns given kappa_line there (same layout as pzo_kappa_line). */
+void pzo_flux(const pzo_problem *P, int64_t n_cols, const int64_t *cols, const double *kline,
+              double *F, double *Fc) {
+    int nd = P->n_depth;
+#pragma omp parallel for schedule(static)
+    for (int64_t c = 0; c < n_cols; ++c) {
+        int64_t i = cols[c];
+        double *chi = (double *)malloc(sizeof(double) * nd * 4);
+        double *chic = chi + nd, *tau = chi + 2 * nd, *S = chi + 3 * nd;
+        double lam = grid_lambda_cm(P, i);
+        for (int d = 0; d < nd; ++d) {
+            chic[d] = P->kappa_c[(int64_t)d * P->n_lambda + i];
+            chi[d] = chic[d] + kline[(int64_t)d * n_cols + c];
+            S[d] = planck_nm(lam, P->T[d]);
+        }
+        optical_depth(nd, P->m, chi, tau);
+        F[c] = flux_from(nd, tau, S);
+        optical_depth(nd, P->m, chic, tau);
+        Fc[c] = flux_from(nd, tau, S);
+        free(chi);
+    }
+}
+
+/* ---- instrument (Sec. 7): row-normalised Gaussian taps ------------------- */
+/* Pixel p at observed wavelength lambda_p samples rest wavelength
+ * lambda_p / (1 + v_r/c).  Gaussian in ln(lambda) with sigma^2 = sigma_LSF^2 + sigma_b^2,
+ * sigma_LSF = 1/(2 sqrt(2 ln 2) R_LSF), sigma_b = v_b/c; taps |ln lambda_i - ln lambda'_p| <= 5 sigma
+ * clipped to the grid and renormalised over the in-grid taps; point sampling. */
+int pzo_instrument_taps(const pzo_problem *P, double v_r_kms, double v_b_kms, double R_lsf,
+                        int64_t n_pix, const double *pix_nm, int64_t *tap0, int32_t *ntap,
+                        double *weights, int32_t max_taps) {
+    double lnr = log1p(1.0 / P->R_grid);
+    double sig_lsf = 1.0 / (2.0 * sqrt(2.0 * log(2.0)) * R_lsf);
+    double sig_b = v_b_kms * 1e5 / O_C;
+    double sig = sqrt(sig_lsf * sig_lsf + sig_b * sig_b) / lnr;   /* grid points */
+    for (int64_t p = 0; p < n_pix; ++p) {
+        double rest = pix_nm[p] / (1.0 + v_r_kms * 1e5 / O_C);
+        double cp = log(rest / P->lambda0_nm) / lnr;
+        int64_t i0 = (int64_t)ceil(cp - 5.0 * sig);
+        int64_t i1 = (int64_t)floor(cp + 5.0 * sig);
+        if (i0 < 0) i0 = 0;
+        if (i1 > P->n_lambda - 1) i1 = P->n_lambda - 1;
+        if (i1 < i0) return -1;
+        if (i1 - i0 + 1 > max_taps) return -2;
+        double sum = 0.0;
+        for (int64_t i = i0; i <= i1; ++i) {
+            double u = ((double)i - cp) / sig;
+            double w = exp(-0.5 * u * u);
+            weights[p * max_taps + (i - i0)] = w;
+            sum += w;
+        }
+        for (int64_t i = i0; i <= i1; ++i) weights[p * max_taps + (i - i0)] /= sum;
+        tap0[p] = i0;
+        ntap[p] = (int32_t)(i1 - i0 + 1);
+    }
+    return 0;
+}
+
+/* ---- adjoint (Sec. 6) ------------------------------------------------------ */
+
+/* d/dtau_a and d/dtau_b of the interval integral at fixed Sa, Sb. */
+static void interval_partials(double ta, double tb, double Sa, double Sb, double *dta, double *dtb) {
+    double D = tb - ta;
+    double s = (Sb - Sa) / D;
+    double e2a = pzo_expn(2, ta), e2b = pzo_expn(2, tb);
+    double e3a = pzo_expn(3, ta), e3b = pzo_expn(3, tb);
+    double e4a = pzo_expn(4, ta), e4b = pzo_expn(4, tb);
+    double Pd = e3a - e3b;
+    double Bq = e4a - e4b - D * e3b;
+    *dta = -Sa * e2a + (s / D) * Bq - s * Pd;
+    *dtb = Sb * e2b - (s / D) * Bq;
+}
+
+/* dF/dtau_j (j = 0..nd-1) of flux_from(). */
+static void flux_dtau(int nd, const double *tau, const double *S, double *dF) {
+    for (int j = 0; j < nd; ++j) dF[j] = 0.0;
+    /* top interval: Sa = S0 - s tau0, s = (S1-S0)/(tau1-tau0) */
+    double t0 = tau[0], t1 = tau[1];
+    double s = (S[1] - S[0]) / (t1 - t0);
+    double sp = s / (t1 - t0);
+    double Pt = 0.5 - pzo_expn(3, t0);
+    double Bt = 1.0 / 3.0 - pzo_expn(4, t0) - t0 * pzo_expn(3, t0);
+    dF[0] += -s * Pt + sp * (Bt - t0 * Pt) + S[0] * pzo_expn(2, t0);
+    dF[1] += -sp * (Bt - t0 * Pt);
+    for (int d = 0; d + 1 < nd; ++d) {
+        double da, db;
+        interval_partials(tau[d], tau[d + 1], S[d], S[d + 1], &da, &db);
+        dF[d] += da;
+        dF[d + 1] += db;
+    }
+    for (int j = 0; j < nd; ++j) dF[j] *= 2.0 * O_PI;
+}
+
+/* dL/dchi(i, d) for every column, given dL/dF_i (total branch; F_c does not depend on
+ * line opacity).  G[d * n_lambda + i].  Chain rule written with the explicit Jacobian
+ * d tau_j / d chi_d of the trapezoid. */
+void pzo_rt_adjoint(const pzo_problem *P, const double *kline_full, const double *dLdF, double *G) {
+    int nd = P->n_depth;
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < P->n_lambda; ++i) {
+        double *chi = (double *)malloc(sizeof(double) * nd * 4);
+        double *tau = chi + nd, *S = chi + 2 * nd, *dF = chi + 3 * nd;
+        double lam = grid_lambda_cm(P, i);
+        for (int d = 0; d < nd; ++d) {
+            chi[d] = P->kappa_c[(int64_t)d * P->n_lambda + i] + kline_full[(int64_t)d * P->n_lambda + i];
+            S[d] = planck_nm(lam, P->T[d]);
+        }
+        optical_depth(nd, P->m, chi, tau);
+        flux_dtau(nd, tau, S, dF);
+        for (int d = 0; d < nd; ++d) {
+            double g = 0.0;
+            for (int j = 0; j < nd; ++j) {
+                /* d tau_j / d chi_d */
+                double J = 0.0;
+                if (d == 0) J += P->m[0];
+                for (int k = 0; k < j; ++k) {
+                    double hm = 0.5 * (P->m[k + 1] - P->m[k]);
+                    if (d == k) J += hm;
+                    if (d == k + 1) J += hm;
+                }
+                g += dF[j] * J;
+            }
+            G[(int64_t)d * P->n_lambda + i] = dLdF[i] * g;
+        }
+        free(chi);
+    }
+}
+
+/* Per-line gradients from G = dL/dkappa_line (all columns):
+ *   dL/dDelta log gf_l      = ln10 sum_{i in win, d} G stim A H
+ *   dL/dDelta log gamma6_l  = ln10 sum_{i in win, d} G stim A (dH/da) a6
+ * (the abundance gradient is the species-to-element sum of the first). */
+void pzo_line_grad(const pzo_problem *P, const double *G, double *g_gf, double *g_g6) {
+    int nd = P->n_depth;
+    int W = P->half_window;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t l = 0; l < P->n_lines; ++l) {
+        double x = centre_x(P, l);
+        int64_t il = (int64_t)floor(x + 0.5);
+        int64_t i0 = il - W, i1 = il + W;
+        if (i0 < 0) i0 = 0;
+        if (i1 > P->n_lambda - 1) i1 = P->n_lambda - 1;
+        double lam_l = P->lambda_nm[l] * 1e-7;
+        double sgf = 0.0, sg6 = 0.0;
+        for (int d = 0; d < nd; ++d) {
+            line_depth q = line_at_depth(P, l, d);
+            for (int64_t i = i0; i <= i1; ++i) {
+                double v = (lam_l / grid_lambda_cm(P, i) - 1.0) * O_C / q.dvD;
+                double H, dH;
+                pzo_voigt(q.a, v, &H, NULL, &dH);
+                double gs = G[(int64_t)d * P->n_lambda + i] * stim_emission(P, i, d);
+                sgf += gs * q.A * H;
+                sg6 += gs * q.A * dH * q.a6;
+            }
+        }
+        g_gf[l] = O_LN10 * sgf;
+        g_g6[l] = O_LN10 * sg6;
+    }
+}
+
+/* chi^2 loss L = sum_p w_p (y_p - f_p)^2 and its seed dL/df_p = -2 w_p (y_p - f_p). */
+double pzo_chi2(int64_t n, const double *y, const double *w, const double *f, double *dLdf) {
+    double L = 0.0;
+    for (int64_t p = 0; p < n; ++p) {
+        double r = y[p] - f[p];
+        L += w[p] * r * r;
+        if (dLdf) dLdf[p] = -2.0 * w[p] * r;
+    }
+    return L;
+}
+
+/* ---- vector helpers for the Python wrapper -------------------------------- */
+void pzo_voigt_vec(int64_t n, const double *a, const double *v, double *H, double *L, double *dH) {
+#pragma omp parallel for schedule(static)
+    for (int64_t k = 0; k < n; ++k) pzo_voigt(a[k], v[k], &H[k], L ? &L[k] : NULL, dH ? &dH[k] : NULL);
+}
+
+void pzo_expn_vec(int n, int64_t cnt, const double *x, double *out) {
+    for (int64_t k = 0; k < cnt; ++k) out[k] = pzo_expn(n, x[k]);
+}
+
+/* flux of one column from explicit tau/S (for the closed-form pins) */
+double pzo_flux_tau(int nd, const double *tau, const double *S) { return flux_from(nd, tau, S); }
+
+/* dF/dtau of one column (for the adjoint pins) */
+void pzo_flux_dtau(int nd, const double *tau, const double *S, double *dF) { flux_dtau(nd, tau, S, dF); }
+
+double pzo_planck_nm(double lambda_nm, double T) { return planck_nm(lambda_nm * 1e-7, T); }

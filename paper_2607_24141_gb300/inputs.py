@@ -1,0 +1,336 @@
+"""Seeded synthetic atmospheres, line lists and pixel grids.
+
+This module only *generates inputs*; it holds none of the synthesis
+arithmetic (no line opacity, transfer or instrument maths).  Both the FP64
+CPU oracle (``oracle/``) and the CUDA library read the arrays it returns, so
+the two implementations see bit-identical inputs.
+
+The recipes stand in for the paper's Kurucz atmospheres, line catalogs and
+APOGEE pixel grids, none of which are available.  They take only the paper's
+shapes: a logarithmic grid at R_grid = 300,000 (Sec. 2.1, Eqs. 1-2), a
+72-layer plane-parallel atmosphere, Voigt lines described by
+(lambda, log gf, E_low, gamma_rad, gamma_4, gamma_6, species) (Eqs. 4-5),
+1500-1700 nm APOGEE-like windows with an 8,575-pixel log-uniform detector
+grid (Sec. 7, Eq. for f_p), and the Sun/Arcturus-like labels of Sec. 6.
+
+Atmosphere recipe (every config):
+  x_j = -6.875 + 0.125 j (j = 0..71), tau_j = 10**x_j
+  T_j**4 = 0.75 Teff**4 (tau_j + 2/3)                       (grey Eddington)
+  m_j = m_ref tau_j**0.7,  m_ref = 3 * 10**(-0.4 (log g - 4.44))  g cm^-2
+  P_gas = g m;  P_e = 1e-4 g m_ref tau (Teff/5777)**4
+  n_e = P_e/kT, n_pert = (P_gas - P_e)/kT, rho = 1.3 m_u P_gas/kT
+  kappa_c(d, i) = kappa0(d) (lambda_i / 500 nm)**-1, kappa0 = tau**0.3/(0.7 m_ref)
+  species: log10 abundance f_s ~ N(-6, 1); per-layer jitter 10**N(0, 0.1);
+           pop_{s,d} = f_s 10**[M/H] n_tot(d) / U_s, U_s = 10**U[0, 1.5]
+  masses U[12, 60] amu; band (molecule-like) species U[26, 28] amu
+  microturbulence xi = 1 km/s
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Optional
+
+import numpy as np
+
+# CODATA 2018, cgs.  Only used to build the input atmosphere (pressures to
+# number densities); the synthesis constants live separately in each
+# implementation.
+_K_B = 1.380649e-16
+_M_U = 1.66053906660e-24
+
+N_DEPTH = 72
+R_GRID = 300_000.0
+
+
+@dataclasses.dataclass
+class Atmosphere:
+    """One star's depth structure, FP64, depth index 0 = top of the atmosphere."""
+    teff: float
+    logg: float
+    m: np.ndarray          # [n_depth] column mass, g cm^-2 (increasing)
+    T: np.ndarray          # [n_depth] K
+    rho: np.ndarray        # [n_depth] g cm^-3
+    n_e: np.ndarray        # [n_depth] cm^-3
+    n_pert: np.ndarray     # [n_depth] cm^-3
+    pop: np.ndarray        # [n_species, n_depth] n_s/U_s, cm^-3
+    mass_amu: np.ndarray   # [n_species]
+    xi_cms: float
+    kappa0: np.ndarray     # [n_depth] continuum at 500 nm, cm^2 g^-1
+
+    @property
+    def n_depth(self) -> int:
+        return int(self.m.shape[0])
+
+    @property
+    def n_species(self) -> int:
+        return int(self.pop.shape[0])
+
+
+@dataclasses.dataclass
+class Grid:
+    """Logarithmic synthesis grid lambda_i = lambda0 (1 + 1/R)^i (Eq. 1)."""
+    lambda0_nm: float
+    R_grid: float
+    n_lambda: int
+
+
+@dataclasses.dataclass
+class LineList:
+    """Structure-of-arrays line list in caller order (unsorted)."""
+    lambda_nm: np.ndarray      # float64 [n_lines]
+    log_gf: np.ndarray         # float32
+    E_low_eV: np.ndarray       # float32
+    log_gamma_rad: np.ndarray  # float32, log10 s^-1
+    log_gamma4: np.ndarray     # float32, log10 cm^3 s^-1
+    log_gamma6: np.ndarray     # float32, log10 cm^3 s^-1
+    species: np.ndarray        # int32
+    half_window: int           # W, grid points
+
+    @property
+    def n_lines(self) -> int:
+        return int(self.lambda_nm.shape[0])
+
+    def subset(self, idx: np.ndarray) -> "LineList":
+        return LineList(self.lambda_nm[idx].copy(), self.log_gf[idx].copy(),
+                        self.E_low_eV[idx].copy(), self.log_gamma_rad[idx].copy(),
+                        self.log_gamma4[idx].copy(), self.log_gamma6[idx].copy(),
+                        self.species[idx].copy(), self.half_window)
+
+
+@dataclasses.dataclass
+class Instrument:
+    """Doppler shift, Gaussian broadening and Gaussian LSF onto detector pixels."""
+    v_r_kms: float
+    v_b_kms: float
+    R_lsf: float
+    pix_lambda_nm: np.ndarray  # float64 [n_pix]
+
+
+@dataclasses.dataclass
+class Problem:
+    """One synthesis problem: atmosphere + grid + lines (+ instrument)."""
+    name: str
+    atmos: Atmosphere
+    grid: Grid
+    lines: LineList
+    kappa_c: np.ndarray                 # float64 [n_depth, n_lambda]
+    instrument: Optional[Instrument] = None
+    elem_of_species: Optional[np.ndarray] = None   # int32 [n_species]
+    n_elem: int = 0
+
+    @property
+    def n_evals(self) -> int:
+        """(line, lambda, depth) Voigt evaluations inside the clipped windows."""
+        return int(window_points(self.grid, self.lines).sum()) * self.atmos.n_depth
+
+
+def n_lambda_for(lmin_nm: float, lmax_nm: float, R: float = R_GRID) -> int:
+    """Number of grid points spanning [lmin, lmax] (Eq. 2, exact form)."""
+    return int(math.floor(math.log(lmax_nm / lmin_nm) / math.log1p(1.0 / R))) + 1
+
+
+def center_index(grid: Grid, lambda_nm: np.ndarray) -> np.ndarray:
+    """Integer centre placement i_l = floor(x_l + 1/2), x_l = ln(lambda_l/lambda_0)/ln r.
+
+    This is the generator's own copy of the placement rule, used only to count
+    work (``window_points``) and to pick sampled columns in tests.
+    """
+    x = np.log(lambda_nm / grid.lambda0_nm) / math.log1p(1.0 / grid.R_grid)
+    return np.floor(x + 0.5).astype(np.int64)
+
+
+def window_points(grid: Grid, lines: LineList) -> np.ndarray:
+    """Grid points inside each line's window |i - i_l| <= W, clipped to the grid."""
+    il = center_index(grid, lines.lambda_nm)
+    lo = np.maximum(il - lines.half_window, 0)
+    hi = np.minimum(il + lines.half_window, grid.n_lambda - 1)
+    return np.maximum(hi - lo + 1, 0)
+
+
+def grid_lambda_nm(grid: Grid) -> np.ndarray:
+    return grid.lambda0_nm * np.exp(np.arange(grid.n_lambda) * math.log1p(1.0 / grid.R_grid))
+
+
+# ----------------------------------------------------------------------------
+# atmosphere
+# ----------------------------------------------------------------------------
+
+def make_atmosphere(teff: float, logg: float, n_species: int, seed: int,
+                    metallicity: float = 0.0, band_species=(), xi_kms: float = 1.0,
+                    n_depth: int = N_DEPTH) -> Atmosphere:
+    rng = np.random.default_rng(seed)
+    j = np.arange(n_depth)
+    x = -6.875 + 0.125 * j if n_depth == 72 else np.linspace(-6.875, 2.0, n_depth)
+    tau = 10.0 ** x
+    T = (0.75 * teff ** 4 * (tau + 2.0 / 3.0)) ** 0.25
+    g = 10.0 ** logg
+    m_ref = 3.0 * 10.0 ** (-0.4 * (logg - 4.44))
+    m = m_ref * tau ** 0.7
+    P_gas = g * m
+    P_e = 1e-4 * g * m_ref * tau * (teff / 5777.0) ** 4
+    kT = _K_B * T
+    n_e = P_e / kT
+    n_pert = (P_gas - P_e) / kT
+    n_tot = P_gas / kT
+    rho = 1.3 * _M_U * P_gas / kT
+    kappa0 = tau ** 0.3 / (0.7 * m_ref)
+
+    log_f = rng.normal(-6.0, 1.0, n_species)
+    jitter = rng.normal(0.0, 0.1, (n_species, n_depth))
+    U = 10.0 ** rng.uniform(0.0, 1.5, n_species)
+    mass = rng.uniform(12.0, 60.0, n_species)
+    for s in band_species:
+        mass[s] = rng.uniform(26.0, 28.0)
+    pop = (10.0 ** (log_f[:, None] + jitter + metallicity)) * n_tot[None, :] / U[:, None]
+    return Atmosphere(teff=teff, logg=logg, m=m, T=T, rho=rho, n_e=n_e, n_pert=n_pert,
+                      pop=pop, mass_amu=mass, xi_cms=xi_kms * 1e5, kappa0=kappa0)
+
+
+def make_kappa_c(atmos: Atmosphere, grid: Grid) -> np.ndarray:
+    lam = grid_lambda_nm(grid)
+    return np.ascontiguousarray(atmos.kappa0[:, None] * (lam[None, :] / 500.0) ** -1.0)
+
+
+# ----------------------------------------------------------------------------
+# line lists
+# ----------------------------------------------------------------------------
+
+def _atomic_lines(rng, n, lam_lo, lam_hi, species_choices, centres="loguniform"):
+    if centres == "loguniform":
+        lam = np.exp(rng.uniform(math.log(lam_lo), math.log(lam_hi), n))
+    elif centres == "inv_uniform":   # pdf ~ lambda^-2
+        lam = 1.0 / rng.uniform(1.0 / lam_hi, 1.0 / lam_lo, n)
+    else:
+        raise ValueError(centres)
+    log_gf = np.clip(rng.normal(-2.0, 1.5, n), -6.0, 1.0)
+    E = rng.uniform(0.0, 10.0, n)
+    sp = rng.choice(np.asarray(species_choices), n)
+    g_rad = rng.normal(8.0, 0.5, n)
+    g4 = rng.normal(-5.5, 0.5, n)
+    g6 = rng.normal(-7.5, 0.5, n)
+    return lam, log_gf, E, sp, g_rad, g4, g6
+
+
+def _band_lines(rng, n_bands, per_band, spacing_nm, lam_lo, lam_hi, band_species):
+    starts = rng.uniform(lam_lo, lam_hi - per_band * spacing_nm, n_bands)
+    lam = (starts[:, None] + spacing_nm * np.arange(per_band)[None, :]).ravel()
+    n = lam.size
+    log_gf = rng.normal(-3.0, 1.0, n)
+    E = rng.uniform(0.0, 3.0, n)
+    sp = np.repeat(rng.choice(np.asarray(band_species), n_bands), per_band)
+    g_rad = rng.normal(8.0, 0.5, n)
+    g4 = rng.normal(-5.5, 0.5, n)
+    g6 = rng.normal(-7.5, 0.5, n)
+    return lam, log_gf, E, sp, g_rad, g4, g6
+
+
+def _pack(parts, W) -> LineList:
+    cols = [np.concatenate([p[k] for p in parts]) for k in range(7)]
+    lam, log_gf, E, sp, g_rad, g4, g6 = cols
+    return LineList(lambda_nm=lam.astype(np.float64), log_gf=log_gf.astype(np.float32),
+                    E_low_eV=E.astype(np.float32), log_gamma_rad=g_rad.astype(np.float32),
+                    log_gamma4=g4.astype(np.float32), log_gamma6=g6.astype(np.float32),
+                    species=sp.astype(np.int32), half_window=int(W))
+
+
+def apogee_pixels(n_pix: int = 8575) -> np.ndarray:
+    """APOGEE-like detector grid: log10(lambda/A) = 4.179 + 6e-6 p."""
+    return 10.0 ** (4.179 + 6e-6 * np.arange(n_pix)) / 10.0
+
+
+# ----------------------------------------------------------------------------
+# the five workloads (and scaled-down variants for element-wise parity)
+# ----------------------------------------------------------------------------
+
+def config0(seed: int = 0, n_lambda: int = 4000, n_lines: int = 2000, W: int = 1000) -> Problem:
+    """Tiny forward: solar atmosphere, 4,000 points from 500 nm, 2,000 lines, W = 1,000."""
+    n_species = 12
+    atmos = make_atmosphere(5777.0, 4.44, n_species, seed)
+    grid = Grid(500.0, R_GRID, n_lambda)
+    lam_hi = float(grid_lambda_nm(grid)[-1])
+    rng = np.random.default_rng(seed + 1000)
+    lines = _pack([_atomic_lines(rng, n_lines, 500.0, lam_hi, np.arange(n_species))], W)
+    return Problem("config0", atmos, grid, lines, make_kappa_c(atmos, grid))
+
+
+def config1(seed: int = 1, lam_lo: float = 1500.0, lam_hi: float = 1700.0,
+            n_bands: int = 133, per_band: int = 500, n_atomic: int = 133_500, W: int = 1500,
+            n_pix: Optional[int] = 8575, name: str = "config1") -> Problem:
+    """APOGEE-like window: Teff 4500, log g 2, 1500-1700 nm, 2e5 lines over 40 species
+    (one third in 133 molecule-like bands of 500 lines at 0.02 nm spacing), W = 1,500,
+    instrument v_r = 12.3 km/s, Gaussian LSF R = 22,500, 8,575 pixels."""
+    n_species = 40
+    band_sp = (36, 37, 38, 39)
+    atmos = make_atmosphere(4500.0, 2.0, n_species, seed, band_species=band_sp)
+    grid = Grid(lam_lo, R_GRID, n_lambda_for(lam_lo, lam_hi))
+    rng = np.random.default_rng(seed + 1000)
+    parts = [_atomic_lines(rng, n_atomic, lam_lo, lam_hi, np.arange(36))]
+    if n_bands:
+        parts.append(_band_lines(rng, n_bands, per_band, 0.02, lam_lo, lam_hi, band_sp))
+    lines = _pack(parts, W)
+    inst = None
+    if n_pix:
+        pix = apogee_pixels(8575)
+        if lam_lo != 1500.0 or lam_hi != 1700.0:   # scaled variant: pixels inside the grid
+            pix = pix[(pix > lam_lo * 1.0005) & (pix < lam_hi * 0.9995)][:n_pix]
+        inst = Instrument(12.3, 0.0, 22_500.0, pix)
+    elem = (np.arange(n_species) % 20).astype(np.int32)
+    return Problem(name, atmos, grid, lines, make_kappa_c(atmos, grid), inst, elem, 20)
+
+
+def config2(seed: int = 2, lam_lo: float = 300.0, lam_hi: float = 1000.0,
+            n_lines: int = 3_000_000, W: int = 2000) -> Problem:
+    """Broad optical: solar atmosphere, 300-1000 nm, 3e6 lines over 80 species with
+    centre density proportional to lambda^-2, W = 2,000, full-resolution output."""
+    n_species = 80
+    atmos = make_atmosphere(5777.0, 4.44, n_species, seed)
+    grid = Grid(lam_lo, R_GRID, n_lambda_for(lam_lo, lam_hi))
+    rng = np.random.default_rng(seed + 1000)
+    lines = _pack([_atomic_lines(rng, n_lines, lam_lo, lam_hi, np.arange(n_species),
+                                 centres="inv_uniform")], W)
+    return Problem("config2", atmos, grid, lines, make_kappa_c(atmos, grid))
+
+
+def config3(seed: int = 3, lam_lo: float = 1500.0, lam_hi: float = 1700.0,
+            n_bands: int = 80, per_band: int = 500, n_atomic: int = 80_000, W: int = 1500,
+            n_pix: Optional[int] = 8575):
+    """Differentiable calibration: config-1 grid and instrument with 1.2e5 lines.
+    Returns (problem, truth) where truth holds the seeded Delta log gf ~ N(0, 0.1),
+    Delta log gamma6 ~ N(0, 0.2) and the noise draw (seed 7, sigma = 1/200)."""
+    prob = config1(seed=seed, lam_lo=lam_lo, lam_hi=lam_hi, n_bands=n_bands, per_band=per_band,
+                   n_atomic=n_atomic, W=W, n_pix=n_pix, name="config3")
+    rng = np.random.default_rng(7)
+    nl = prob.lines.n_lines
+    truth = {
+        "dlog_gf": rng.normal(0.0, 0.1, nl).astype(np.float32),
+        "dlog_gamma6": rng.normal(0.0, 0.2, nl).astype(np.float32),
+        "noise": rng.normal(0.0, 1.0 / 200.0, prob.instrument.pix_lambda_nm.size
+                            if prob.instrument is not None else prob.grid.n_lambda),
+        "weight": 200.0 ** 2,
+    }
+    return prob, truth
+
+
+def small_config1(n_lambda_span_nm: float = 2.0, lines_scale: float = 0.01, seed: int = 11,
+                  W: int = 1500, with_instrument: bool = True) -> Problem:
+    """Scaled-down config 1 for element-wise parity: same recipe, a ~2 nm slice."""
+    lam_lo = 1600.0
+    lam_hi = lam_lo + n_lambda_span_nm
+    frac = n_lambda_span_nm / 200.0
+    n_atomic = max(8, int(round(133_500 * frac)))
+    n_bands = max(1, int(round(133 * frac))) if n_lambda_span_nm > 10.5 else 0
+    return config1(seed=seed, lam_lo=lam_lo, lam_hi=lam_hi, n_bands=n_bands, per_band=500,
+                   n_atomic=n_atomic, W=W, n_pix=8575 if with_instrument else None,
+                   name="config1-small")
+
+
+def config4_stars(seed: int = 4, n_stars: int = 64):
+    """Per-star labels for the batched workload: Teff ~ U[3500, 7000], log g ~ U[1, 5],
+    [M/H] ~ U[-2, 0.5], plus line-count draws N_k = round(exp U[ln 2e4, ln 3e5])."""
+    rng = np.random.default_rng(seed)
+    teff = rng.uniform(3500.0, 7000.0, n_stars)
+    logg = rng.uniform(1.0, 5.0, n_stars)
+    mh = rng.uniform(-2.0, 0.5, n_stars)
+    nk = np.round(np.exp(rng.uniform(math.log(2e4), math.log(3e5), n_stars))).astype(np.int64)
+    return teff, logg, mh, nk

@@ -1,0 +1,116 @@
+"""Pins of the oracle's line opacity (Sec. 2.1, Eqs. 1, 4, 5)."""
+import numpy as np
+from scipy.special import wofz
+
+from paper_2607_24141_gb300 import inputs as I
+from tiny import tiny_problem
+
+# CODATA 2018 cgs, typed independently of the oracle source
+H_ = 6.62607015e-27
+K_ = 1.380649e-16
+C_ = 2.99792458e10
+E_ = 4.80320471e-10
+ME = 9.1093837015e-28
+EV = 1.602176634e-12
+AMU = 1.66053906660e-24
+
+
+def brute_kappa(prob):
+    """Triple loop over (lambda, depth, line), written in frequency variables."""
+    at, ll, g = prob.atmos, prob.lines, prob.grid
+    r = 1.0 + 1.0 / g.R_grid
+    out = np.zeros((at.n_depth, g.n_lambda))
+    il = [int(np.floor(np.log(ll.lambda_nm[l] / g.lambda0_nm) / np.log(r) + 0.5)) for l in range(ll.n_lines)]
+    for i in range(g.n_lambda):
+        lam_i = g.lambda0_nm * 1e-7 * r ** i
+        nu = C_ / lam_i
+        for d in range(at.n_depth):
+            T = at.T[d]
+            s = 0.0
+            for l in range(ll.n_lines):
+                if abs(i - il[l]) > ll.half_window:
+                    continue
+                sp = ll.species[l]
+                nu_l = C_ / (ll.lambda_nm[l] * 1e-7)
+                dv = np.sqrt(2 * K_ * T / (at.mass_amu[sp] * AMU) + at.xi_cms ** 2)
+                dnu = nu_l * dv / C_
+                gam = 10.0 ** float(ll.log_gamma_rad[l]) + 10.0 ** float(ll.log_gamma4[l]) * at.n_e[d] \
+                    + 10.0 ** float(ll.log_gamma6[l]) * at.n_pert[d]
+                a = gam / (4 * np.pi * dnu)
+                v = (nu - nu_l) / dnu
+                phi = wofz(v + 1j * a).real / (np.sqrt(np.pi) * dnu)
+                s += (np.pi * E_ ** 2 / (ME * C_)) * 10.0 ** float(ll.log_gf[l]) * at.pop[sp, d] / at.rho[d] \
+                    * np.exp(-float(ll.E_low_eV[l]) * EV / (K_ * T)) * phi
+            out[d, i] = s * (1.0 - np.exp(-H_ * nu / (K_ * T)))
+    return out
+
+
+def test_kappa_matches_brute_force(oracle):
+    prob = tiny_problem()
+    ref = brute_kappa(prob)
+    got = oracle.kappa_line(prob)
+    m = ref > 0
+    assert np.all((got > 0) == m)
+    assert np.max(np.abs(got[m] / ref[m] - 1)) < 1e-9
+
+
+def test_kappa_column_subset_equals_full(oracle):
+    prob = tiny_problem(n_lambda=80, n_lines=10, seed=9)
+    full = oracle.kappa_line(prob)
+    cols = np.array([0, 7, 33, 79])
+    sub = oracle.kappa_line(prob, cols)
+    assert np.array_equal(sub, full[:, cols])
+
+
+def test_window_rule_and_dropped_lines(oracle):
+    prob = tiny_problem(n_lambda=50, n_lines=1, W=5, seed=1)
+    lam = I.grid_lambda_nm(prob.grid)
+    # integer centre placement i_l = floor(x_l + 1/2), window |i - i_l| <= W
+    for x, (lo, hi) in [(10.6, (6, 16)), (10.4, (5, 15)), (2.2, (0, 7))]:
+        prob.lines.lambda_nm[:] = prob.grid.lambda0_nm * np.exp(x * np.log1p(1 / prob.grid.R_grid))
+        nz = np.nonzero(oracle.kappa_line(prob)[0] > 0)[0]
+        assert nz.min() == lo and nz.max() == hi
+    # a line whose window misses the grid contributes nothing
+    prob.lines.lambda_nm[:] = lam[-1] * np.exp(7 * np.log1p(1 / prob.grid.R_grid))
+    assert np.all(oracle.kappa_line(prob) == 0)
+
+
+def test_integrated_line_strength(oracle):
+    """Int kappa dnu over an isolated weak line = (pi e^2/m c) gf n/(rho U) e^{-E/kT}
+    times the fraction of the normalised profile inside the window (Eq. 4, Int phi dnu = 1)."""
+    W = 3000
+    prob = tiny_problem(n_lambda=2 * W + 1, n_depth=2, n_lines=1, W=W, seed=2)
+    lam = I.grid_lambda_nm(prob.grid)
+    prob.lines.lambda_nm[:] = lam[W]
+    at, ll = prob.atmos, prob.lines
+    k = oracle.kappa_line(prob)
+    lnr = np.log1p(1 / prob.grid.R_grid)
+    nu = C_ / (lam * 1e-7)
+    sp = ll.species[0]
+    for d in range(at.n_depth):
+        T = at.T[d]
+        stim = 1.0 - np.exp(-H_ * nu / (K_ * T))
+        integral = np.sum(k[d] / stim * nu * lnr)       # Int dnu = Int nu dln(nu)
+        S = (np.pi * E_ ** 2 / (ME * C_)) * 10.0 ** float(ll.log_gf[0]) * at.pop[sp, d] / at.rho[d] \
+            * np.exp(-float(ll.E_low_eV[0]) * EV / (K_ * T))
+        nu_l = nu[W]
+        dv = np.sqrt(2 * K_ * T / (at.mass_amu[sp] * AMU) + at.xi_cms ** 2)
+        dnu = nu_l * dv / C_
+        gam = 10.0 ** float(ll.log_gamma_rad[0]) + 10.0 ** float(ll.log_gamma4[0]) * at.n_e[d] \
+            + 10.0 ** float(ll.log_gamma6[0]) * at.n_pert[d]
+        a = gam / (4 * np.pi * dnu)
+        v_hi = (nu[0] - nu_l) / dnu                  # window edges in Doppler units
+        v_lo = (nu_l - nu[-1]) / dnu
+        tail = a / np.pi * (1 / v_hi + 1 / v_lo)     # Lorentz wings outside the window
+        assert abs(integral / (S * (1 - tail)) - 1) < 1e-6
+
+
+def test_abundance_and_gf_corrections_scale(oracle):
+    prob = tiny_problem(seed=4)
+    base = oracle.kappa_line(prob)
+    nl = prob.lines.n_lines
+    # Delta log gf = c for every line scales kappa by 10^c; Delta [X/H] = c likewise (Eq. 10)
+    k1 = oracle.kappa_line(prob, corrections={"dlog_gf": np.full(nl, 0.3)})
+    assert np.allclose(k1, base * 10 ** 0.3, rtol=1e-13, atol=0)
+    k2 = oracle.kappa_line(prob, corrections={"dabund": np.full(prob.n_elem, -0.2)})
+    assert np.allclose(k2, base * 10 ** -0.2, rtol=1e-13, atol=0)
