@@ -1,0 +1,407 @@
+#!/usr/bin/env python
+"""Benchmark of the synthesis hot path on the APOGEE-like workload.
+
+Workload: 1500-1700 nm at R_grid = 300,000 (37,550 points), 2e5 Voigt lines
+over 40 species (one third in molecule-like bands), 72 depths, W = 1,500,
+Doppler shift 12.3 km/s, Gaussian LSF R = 22,500 onto 8,575 pixels.
+
+One step = one pass of the whole hot path for one spectrum:
+  corrections -> line opacity -> tau + flux (total and continuum) ->
+  instrument + normalisation -> chi^2 against a synthetic target ->
+  reverse pass to per-line Delta log gf, Delta log gamma6 and 20 abundances.
+The metric counts (line, lambda, depth) Voigt evaluations of the forward
+window sum per spectrum; value = evaluations of all ranks / max rank time.
+
+``--impl reference`` times the FP64 CPU oracle (forward + adjoint) on a
+bounded slice of the same recipe on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "s per spectrum & line-pt-depth evals/s (fwd, fwd+bwd) vs FP64 GPU form, % roofline"
+UNIT = "line-pt-depth evals/s"
+WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts) x 2e5 Voigt lines "
+            "(40 species, 1/3 in bands) x 72 depths, W=1,500, v_r=12.3 km/s, LSF R=22,500 -> 8,575 px, "
+            "chi^2 vs synthetic target, gradients for 2e5 dlog_gf + 2e5 dlog_gamma6 + 20 abundances")
+
+# algorithmic per-evaluation instruction counts of the far-wing forms (>99% of evaluations)
+OPS = {"line_fwd": {"fp32": 7, "mufu": 1}, "line_bwd": {"fp32": 14, "mufu": 1}}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.bus_id and self.bus_id[-12:] not in parts[0].lower():
+                continue
+            rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=reasons, samples=len(rows),
+                   power_w_max=max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit())
+                   if any(r[3].replace(".", "").isdigit() for r in rows) else None)
+        return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reported baseline, and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(span_nm=4.0):
+    """FP64 oracle forward + adjoint on a slice of the same recipe; returns (evals, seconds, desc)."""
+    import numpy as np
+
+    from oracle import oracle
+    from paper_2607_24141_gb300 import inputs as I
+    oracle.build()
+    prob = I.small_config1(n_lambda_span_nm=span_nm, seed=1)
+    n_out = prob.instrument.pix_lambda_nm.size
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    fwd = oracle.forward(prob)
+    y = fwd["f"] + rng.normal(0, 1 / 200, n_out)
+    oracle.gradient(prob, y, np.full(n_out, 4e4), fwd=fwd)
+    dt = time.perf_counter() - t0
+    desc = ("FP64 oracle forward + adjoint on a %.1f nm slice of the same recipe (1600-%.1f nm: %d points x %d "
+            "lines x 72 depths, %d pixels; %.3g evals)" % (span_nm, 1600 + span_nm, prob.grid.n_lambda,
+                                                          prob.lines.n_lines, n_out, prob.n_evals))
+    return prob.n_evals, dt, desc
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    # size each step's slice so the whole run stays near two minutes of host time
+    _, t1, _ = oracle_sample(span_nm=1.0)
+    budget = 120.0 / max(args.steps + args.warmup, 1)
+    span = min(4.0, max(0.5, math.sqrt(budget / t1)))
+    steps = []
+    desc = ""
+    ev = 0
+    for k in range(args.warmup + args.steps):
+        ev, dt, desc = oracle_sample(span_nm=span)
+        if k >= args.warmup:
+            steps.append(dt)
+    total = sum(steps)
+    value = ev * len(steps) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(steps),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    import paper_2607_24141_gb300 as pz
+    from paper_2607_24141_gb300 import inputs as I
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    # CPU baseline first (rank 0, before the GPU work of this process starts)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        ev, dt, desc = oracle_sample()
+        cpu = {"value": ev / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc}
+
+    prob = I.config1(seed=1)
+    inst = prob.instrument
+    nl, n_pix, n_elem = prob.lines.n_lines, inst.pix_lambda_nm.size, prob.n_elem
+    s = pz.Synthesizer(prob, pz.PZ_MIXED, device=local)
+    evals = s.n_evals
+    stream = torch.cuda.current_stream()
+
+    # synthetic target: the model at seeded "true" corrections plus S/N-200 noise
+    rng = np.random.default_rng(7)
+    truth_gf = rng.normal(0, 0.1, nl).astype(np.float32)
+    truth_g6 = rng.normal(0, 0.2, nl).astype(np.float32)
+    s.set_corrections(truth_gf, truth_g6, None)
+    f_true = s.forward().cpu().numpy()
+    y_host = (f_true + rng.normal(0, 1 / 200, n_pix)).astype(np.float32)
+    eos = prob.elem_of_species
+
+    dgf = torch.zeros(nl, dtype=torch.float32, device=dev)
+    dg6 = torch.zeros(nl, dtype=torch.float32, device=dev)
+    dab = torch.zeros(n_elem, dtype=torch.float32, device=dev)
+    y = torch.tensor(y_host, device=dev)
+    w = torch.full((n_pix,), 200.0 ** 2, dtype=torch.float32, device=dev)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    dLdf = torch.empty(n_pix, dtype=torch.float32, device=dev)
+    f = torch.empty(n_pix, dtype=torch.float32, device=dev)
+    g_gf = torch.empty(nl, dtype=torch.float32, device=dev)
+    g_g6 = torch.empty(nl, dtype=torch.float32, device=dev)
+    g_ab = torch.empty(n_elem, dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MiB > L2
+    launches = [0]
+
+    def fwd_only():
+        pz.pz_line_opacity(s.ctx, None, stream)
+        launches[0] += pz.pz_last_launch_count(s.ctx)
+        pz.pz_flux(s.ctx, None, None, stream)
+        launches[0] += pz.pz_last_launch_count(s.ctx)
+        pz.pz_instrument(s.ctx, inst.v_r_kms, inst.v_b_kms, inst.R_lsf, inst.pix_lambda_nm, f, stream)
+        launches[0] += pz.pz_last_launch_count(s.ctx)
+
+    def step():
+        pz.pz_set_corrections(s.ctx, dgf, dg6, dab, eos, n_elem, stream)
+        launches[0] += pz.pz_last_launch_count(s.ctx)
+        fwd_only()
+        pz.pz_loss_chi2(s.ctx, y, w, loss, dLdf, stream)
+        launches[0] += pz.pz_last_launch_count(s.ctx)
+        pz.pz_backward(s.ctx, dLdf, g_gf, g_g6, g_ab, stream)
+        launches[0] += pz.pz_last_launch_count(s.ctx)
+        flush.zero_()
+
+    def timed(fn, k):
+        barrier()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return a.elapsed_time(b)
+
+    # ---- fwd+bwd (headline) ----
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(getattr(torch.cuda.get_device_properties(local), "pci_bus_id", None))
+    clk.start()
+    pz.pz_set_profiling(s.ctx, True)
+    launches[0] = 0
+    ms = timed(step, args.steps)
+    ktimes = pz.pz_kernel_times(s.ctx)
+    pz.pz_set_profiling(s.ctx, False)
+    n_launch = launches[0] + 0
+    clocks = clk.stop()
+    ms_max = max_over_ranks(ms)
+    ms_step = ms_max / args.steps
+    value = ws * evals * args.steps / (ms_max * 1e-3)
+
+    # ---- fwd only ----
+    for _ in range(2):
+        fwd_only()
+    ms_fwd = max_over_ranks(timed(lambda: (fwd_only(), flush.zero_()), args.steps)) / args.steps
+
+    # ---- end to end through the C ABI with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        h_gf = torch.zeros(nl, dtype=torch.float32).pin_memory()
+        h_g6 = torch.zeros(nl, dtype=torch.float32).pin_memory()
+        h_ab = torch.zeros(n_elem, dtype=torch.float32).pin_memory()
+        h_y = torch.tensor(y_host).pin_memory()
+        o_gf = torch.empty(nl, dtype=torch.float32).pin_memory()
+        o_g6 = torch.empty(nl, dtype=torch.float32).pin_memory()
+        o_ab = torch.empty(n_elem, dtype=torch.float32).pin_memory()
+        o_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            # host corrections go straight into the C ABI (it copies them); the target goes up too
+            pz.pz_set_corrections(s.ctx, h_gf.numpy(), h_g6.numpy(), h_ab.numpy(), eos, n_elem, stream)
+            y.copy_(h_y, non_blocking=True)
+            fwd_only()
+            pz.pz_loss_chi2(s.ctx, y, w, loss, dLdf, stream)
+            pz.pz_backward(s.ctx, dLdf, g_gf, g_g6, g_ab, stream)
+            o_gf.copy_(g_gf, non_blocking=True)
+            o_g6.copy_(g_g6, non_blocking=True)
+            o_ab.copy_(g_ab, non_blocking=True)
+            o_loss.copy_(loss, non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+            flush.zero_()
+
+        for _ in range(2):
+            e2e_step()
+        ms_e2e = max_over_ranks(timed(e2e_step, args.steps))
+        e2e = {"value": ws * evals * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": 4 * (2 * nl + n_elem + n_pix),
+               "d2h_bytes_per_step": 4 * (2 * nl + n_elem) + 8,
+               "ms_per_step": ms_e2e / args.steps}
+
+    # ---- plain FP64 GPU form ----
+    fp64 = None
+    if not args.no_fp64 and args.fp64_steps > 0:
+        s.close()
+        s64 = pz.Synthesizer(prob, pz.PZ_FP64, device=local)
+
+        def step64():
+            pz.pz_set_corrections(s64.ctx, dgf, dg6, dab, eos, n_elem, stream)
+            pz.pz_line_opacity(s64.ctx, None, stream)
+            pz.pz_flux(s64.ctx, None, None, stream)
+            pz.pz_instrument(s64.ctx, inst.v_r_kms, inst.v_b_kms, inst.R_lsf, inst.pix_lambda_nm, f, stream)
+            pz.pz_loss_chi2(s64.ctx, y, w, loss, dLdf, stream)
+            pz.pz_backward(s64.ctx, dLdf, g_gf, g_g6, g_ab, stream)
+        step64()
+        torch.cuda.synchronize()
+        pz.pz_set_profiling(s64.ctx, True)
+        ms64 = max_over_ranks(timed(step64, args.fp64_steps)) / args.fp64_steps
+        k64 = pz.pz_kernel_times(s64.ctx)
+        s64.close()
+        fwd64 = sum(k64[k][0] for k in ("line_fwd", "flux", "instrument")) / args.fp64_steps
+        fp64 = {"s_per_spectrum_fwdbwd": ms64 * 1e-3, "s_per_spectrum_fwd": fwd64 * 1e-3,
+                "evals_per_s_fwdbwd": evals / (ms64 * 1e-3), "steps": args.fp64_steps}
+
+    # ---- roofline of the dominant kernel ----
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    clk_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
+    share = {k: v[0] for k, v in ktimes.items()}
+    dom = max(("line_fwd", "line_bwd"), key=lambda k: share[k])
+    t_dom = share[dom] * 1e-3 / max(ktimes[dom][1], 1)          # s per launch
+    ops = OPS[dom]
+    fp32_clk, mufu_clk = ops["fp32"] / 128.0, ops["mufu"] / 16.0    # issue cycles per evaluation per SM
+    pipe = "fp32" if fp32_clk >= mufu_clk else "mufu"
+    lanes = 128 if pipe == "fp32" else 16
+    peak_ops = n_sm * lanes * clk_max * 1e6
+    achieved_ops = evals * ops[pipe] / t_dom
+    total_k = sum(share.values())
+    roofline = {
+        "bound": "alu", "kernel": "k_line_bwd" if dom == "line_bwd" else "k_line_fwd", "pipe": pipe,
+        "achieved": achieved_ops * 1e-9, "peak": peak_ops * 1e-9, "unit": "Gop/s",
+        "frac": achieved_ops / peak_ops, "traffic": None,
+        "peak_source": "derived: %d SMs x %d %s lanes x %.0f MHz (max SM clock)" % (n_sm, lanes, pipe, clk_max),
+        "ops_per_eval": ops, "evals_per_s": evals / t_dom, "ms_per_launch": t_dom * 1e3,
+        "kernel_share": {k: round(v / total_k, 4) for k, v in share.items() if total_k > 0},
+        "hbm_gbs_peak": peaks.get("hbm_gbs"),
+    }
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "spectra_per_step": ws, "evals_per_spectrum": evals,
+                   "l2": "256 MiB buffer written between steps (inside the timed region)",
+                   "precision": "FP32 Voigt + compensated FP32 sums; FP64 tau, E_n and flux"},
+        "s_per_spectrum_fwdbwd": ms_step * 1e-3, "s_per_spectrum_fwd": ms_fwd * 1e-3,
+        "evals_per_s_fwd": ws * evals / (ms_fwd * 1e-3),
+        "fp64_form": fp64,
+        "speedup_vs_fp64_form": (fp64["s_per_spectrum_fwdbwd"] / (ms_step * 1e-3)) if fp64 else None,
+        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

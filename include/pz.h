@@ -1,0 +1,237 @@
+/*
+ * pz.h -- C ABI of libpz, the GB300 (sm_103a) spectral-synthesis hot path.
+ *
+ * The calls follow the paper's statement of the problem (arXiv:2607.24141,
+ * "The Payne Zero Project I", Sec. 2.1 Eqs. 1-9, Sec. 6 Eq. 10, Sec. 7):
+ *
+ *   pz_create          one-time window preparation (Sec. 2.2, Table 1 "Window
+ *                      preparation"): copies the atmosphere, grid and line list to
+ *                      the device, sorts lines by centre, builds per-tile line ranges.
+ *   pz_set_corrections calibration corrections of Eq. 10 (Delta log gf,
+ *                      Delta log gamma_6) and abundance offsets.
+ *   pz_line_opacity    kappa_line(lambda, d), Eqs. 4-5 summed inside each line's
+ *                      fixed window (Sec. 2.2 "Line opacity").
+ *   pz_flux            chi = kappa_c + kappa_line (Eq. 3), tau by trapezoid on
+ *                      column mass, F_lambda and F_lambda,c from F = 2 pi Int S E_2 dtau
+ *                      on piecewise-linear S (Eqs. 6-8, sigma_c = 0 so S = B_lambda).
+ *   pz_instrument      f_p = {K S(v_r) B(v_b) F}_p / {K S(v_r) B(v_b) F_c}_p (Sec. 7),
+ *                      or f = F/F_c at full resolution (Eq. 9 without K).
+ *   pz_loss_chi2       L = sum_p w_p (y_p - f_p)^2 and dL/df (objective of Sec. 6).
+ *   pz_backward        reverse pass to per-line Delta log gf, Delta log gamma_6 and
+ *                      per-element abundance gradients (Sec. 6).
+ *
+ * Conventions (every call):
+ *  - Return value: PZ_OK or an error code; on error pz_last_error() gives a
+ *    message (thread-local).  A call that fails validation launches nothing.
+ *  - "host" pointers are read during the call only; the library copies them.
+ *    "device" pointers are caller-owned device memory (e.g. torch.empty on
+ *    cuda), read or written asynchronously on `stream`.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    All work of a call is enqueued on that stream; calls do not synchronise
+ *    the host except where stated.
+ *  - Arrays are C-contiguous.  [n_depth][n_lambda] means depth-major with the
+ *    wavelength index contiguous.  Depth index 0 is the top of the atmosphere.
+ *  - A context is not thread-safe: calls on one context must be serialised by
+ *    the caller (one stream at a time).
+ */
+#ifndef PZ_H
+#define PZ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pz_ctx pz_ctx;
+
+typedef enum {
+    PZ_OK = 0,
+    PZ_EINVAL = 1,    /* invalid argument (nothing launched) */
+    PZ_ENOMEM = 2,    /* device or host allocation failed */
+    PZ_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+    PZ_ETIMEOUT = 4,  /* a bounded device-side wait gave up (batched scheduler) */
+    PZ_ESTATE = 5     /* call order violated (e.g. pz_flux before pz_line_opacity) */
+} pz_status;
+
+typedef enum {
+    PZ_FP64 = 0,   /* plain FP64 GPU form: one thread per (lambda, depth), FP64 Voigt */
+    PZ_MIXED = 1   /* FP32 Voigt + compensated FP32 accumulation; FP64 tau and flux */
+} pz_precision;
+
+/* Atmosphere and synthesis grid (host pointers, FP64, copied by pz_create).
+ * Units: m column mass g cm^-2 (strictly increasing with depth), T K,
+ * rho g cm^-3, n_e and n_pert cm^-3, pop = n_s/U_s cm^-3 (partition-normalised
+ * number density of species s), mass_amu per species, xi_cms microturbulence
+ * cm s^-1, kappa_c continuum absorption cm^2 g^-1 (> 0).
+ * Grid (Eq. 1): lambda_i = lambda0_nm (1 + 1/R_grid)^i, i = 0..n_lambda-1. */
+typedef struct {
+    int32_t n_depth;            /* >= 2 */
+    int32_t n_species;          /* >= 1 */
+    const double *m;            /* [n_depth] */
+    const double *T;            /* [n_depth] */
+    const double *rho;          /* [n_depth] */
+    const double *n_e;          /* [n_depth] */
+    const double *n_pert;       /* [n_depth] */
+    const double *pop;          /* [n_species][n_depth] */
+    const double *mass_amu;     /* [n_species] */
+    double xi_cms;
+    const double *kappa_c;      /* [n_depth][n_lambda] */
+    double lambda0_nm;
+    double R_grid;
+    int64_t n_lambda;           /* >= 1 */
+} pz_atmos;
+
+/* Line list (host pointers, caller order, copied and sorted by pz_create).
+ * log_gamma_rad in log10 s^-1; log_gamma4 and log_gamma6 in log10 cm^3 s^-1
+ * per perturber (Eq. 5, no temperature scaling).  species in [0, n_species).
+ * half_window W: a line deposits at grid points |i - i_l| <= W where
+ * i_l = floor(ln(lambda_l/lambda0)/ln(1 + 1/R) + 1/2) (integer centre
+ * placement, Sec. 6); lines whose window misses the grid are dropped. */
+typedef struct {
+    int64_t n_lines;            /* >= 0 */
+    const double *lambda_nm;    /* [n_lines] */
+    const float *log_gf;        /* [n_lines] */
+    const float *E_low_eV;      /* [n_lines] */
+    const float *log_gamma_rad; /* [n_lines] */
+    const float *log_gamma4;    /* [n_lines] */
+    const float *log_gamma6;    /* [n_lines] */
+    const int32_t *species;     /* [n_lines] */
+    int32_t half_window;        /* W >= 0 */
+} pz_linelist;
+
+/* Allocate a context on the current CUDA device and upload everything.
+ * Synchronous (returns when the device copies are complete).
+ * Errors: PZ_EINVAL (sizes, non-finite or non-positive inputs, unsorted m,
+ * species out of range), PZ_ENOMEM, PZ_ECUDA. */
+pz_status pz_create(const pz_atmos *atmos, const pz_linelist *lines, pz_precision precision,
+                    pz_ctx **out);
+
+/* Free every device and host resource of the context.  NULL is accepted. */
+pz_status pz_destroy(pz_ctx *ctx);
+
+/* Calibration corrections of Eq. 10 and abundance offsets, in caller line order.
+ * (gf)' = gf 10^dlog_gf[l]; gamma6' = gamma6 10^dlog_gamma6[l];
+ * pop'_{s,d} = pop_{s,d} 10^dabund[elem_of_species[s]].
+ * Each pointer may be host or device memory (detected) or NULL (= zeros; for
+ * dabund NULL also clears the element map).  elem_of_species is a host array
+ * [n_species] with values in [0, n_elem).  Device inputs are read on `stream`.
+ * Errors: PZ_EINVAL (n_elem < 0, map out of range), PZ_ECUDA. */
+pz_status pz_set_corrections(pz_ctx *ctx, const float *dlog_gf, const float *dlog_gamma6,
+                             const float *dabund, const int32_t *elem_of_species, int32_t n_elem,
+                             void *stream);
+
+/* Line opacity kappa_line(lambda_i, d) = (1 - e^{-h nu_i/kT_d})
+ *   sum_{l : |i - i_l| <= W} (pi e^2/m_e c) gf_l (n_{s,d}/(rho_d U_s)) e^{-E_l/kT_d}
+ *   H(a_ld, v_ild) / (sqrt(pi) dnu_D,ld)              (Eqs. 4-5)
+ * computed into the context's resident buffer.  If kappa_line is not NULL it
+ * also receives a copy: device, FP32, [n_depth][n_lambda]. */
+pz_status pz_line_opacity(pz_ctx *ctx, float *kappa_line, void *stream);
+
+/* Emergent flux of the total and continuum branches (Eqs. 6-8):
+ * tau_0 = chi_0 m_0, tau_{j+1} = tau_j + (chi_j + chi_{j+1})(m_{j+1} - m_j)/2;
+ * F = 2 pi [ sum over layers of Int S E_2 dtau ] with S = B_lambda(T) per nm,
+ * linear in tau between layers, the first segment extrapolated to tau = 0 and
+ * nothing below the bottom layer.  F, Fc: device FP64 [n_lambda] or NULL
+ * (the context keeps its own copy).  Requires pz_line_opacity (PZ_ESTATE). */
+pz_status pz_flux(pz_ctx *ctx, double *F, double *Fc, void *stream);
+
+/* Instrument stage and normalisation (Sec. 7):
+ *   f_p = sum_i K_pi F_i / sum_i K_pi F_c,i
+ * with pixel p at observed wavelength pix_lambda_nm[p] sampling rest wavelength
+ * lambda_p / (1 + v_r/c); K_pi a Gaussian in ln(lambda) with
+ * sigma^2 = (1/(2 sqrt(2 ln 2) R_lsf))^2 + (v_b/c)^2, truncated at 5 sigma,
+ * clipped to the grid and normalised over the in-grid taps.  The weights are
+ * rebuilt on the device only when (v_r, v_b, R_lsf, pixels) change.
+ * n_pix = 0 (pix_lambda_nm NULL): identity instrument, f_i = F_i / F_c,i on
+ * the synthesis grid.  f_norm: device FP32 [n_pix] (or [n_lambda]).
+ * pix_lambda_nm: host FP64 [n_pix], strictly increasing.
+ * Requires pz_flux (PZ_ESTATE).  Errors: PZ_EINVAL (R_lsf <= 0, a pixel with
+ * no in-grid tap, more than 4096 taps per pixel). */
+pz_status pz_instrument(pz_ctx *ctx, double v_r_kms, double v_b_kms, double R_lsf,
+                        const double *pix_lambda_nm, int64_t n_pix, float *f_norm, void *stream);
+
+/* Chi-square objective on the last pz_instrument output f:
+ *   L = sum_p w_p (y_p - f_p)^2,  dL/df_p = -2 w_p (y_p - f_p).
+ * y, w: device FP32 [n] (w may be NULL = all ones); n must equal the output
+ * size of the last pz_instrument.  loss: device FP64 scalar or NULL;
+ * dL_df: device FP32 [n] or NULL.  Requires pz_instrument (PZ_ESTATE). */
+pz_status pz_loss_chi2(pz_ctx *ctx, const float *y, const float *w, int64_t n, double *loss,
+                       float *dL_df, void *stream);
+
+/* Reverse pass (Sec. 6) for dL/df of the last pz_instrument output:
+ * instrument adjoint -> dL/dF -> adjoint of the closed-form flux and of the
+ * trapezoid tau -> G = dL/dkappa_line(lambda, d) -> per-line windowed
+ * reduction with the Voigt term recomputed (never stored):
+ *   g_dlog_gf[l]     = ln10 sum_{i in win, d} G stim kappa-term_l
+ *   g_dlog_gamma6[l] = ln10 sum_{i in win, d} G stim A_ld (dH/da) a6_ld
+ *   g_dabund[e]      = sum over lines of species in element e of g_dlog_gf
+ * dL_df: device FP32 [n_out].  Outputs: device FP32 in caller line order
+ * ([n_lines], [n_lines], [n_elem]); any may be NULL.  Lines dropped at
+ * pz_create get 0.  Requires pz_instrument since the last forward (PZ_ESTATE).
+ * Wavelength derivatives are not provided (integer centre placement, Sec. 6). */
+pz_status pz_backward(pz_ctx *ctx, const float *dL_df, float *g_dlog_gf, float *g_dlog_gamma6,
+                      float *g_dabund, void *stream);
+
+/* ---- introspection -------------------------------------------------------- */
+
+/* Thread-local message of the last failing call on this thread ("" if none). */
+const char *pz_last_error(void);
+
+/* Number of (line, lambda, depth) Voigt evaluations one pz_line_opacity performs
+ * (lines in the grid x clipped window points x n_depth). */
+int64_t pz_eval_count(const pz_ctx *ctx);
+
+/* Number of kernel launches issued by the most recent pz_* call on this context. */
+int32_t pz_last_launch_count(const pz_ctx *ctx);
+
+/* Kernel tiling of the mixed-precision line kernels: lambda points per tile,
+ * depths per CTA and lines per shared-memory chunk.  Values <= 0 keep the
+ * current setting.  Must be called between forwards (PZ_ESTATE otherwise is
+ * not raised; the next pz_line_opacity uses the new tiling).
+ * Errors: PZ_EINVAL for an unsupported combination. */
+pz_status pz_set_tiling(pz_ctx *ctx, int32_t lambda_per_thread, int32_t depth_per_warp,
+                        int32_t warps_per_cta, int32_t lines_per_chunk);
+
+/* ---- profiling ------------------------------------------------------------- */
+
+/* Kernel families timed by the built-in CUDA-event profiler. */
+typedef enum {
+    PZ_K_LINE_FWD = 0,     /* windowed Voigt sum (mixed or FP64 form) */
+    PZ_K_LINE_BWD = 1,     /* per-line windowed gradient reduction */
+    PZ_K_FLUX = 2,         /* tau + closed-form flux, both branches */
+    PZ_K_RT_ADJOINT = 3,   /* adjoint of flux and tau */
+    PZ_K_INSTRUMENT = 4,   /* weight build + apply (or identity) */
+    PZ_K_INST_ADJOINT = 5, /* transpose of the instrument */
+    PZ_K_LOSS = 6,         /* chi-square and its seed */
+    PZ_K_OTHER = 7,        /* corrections, finalisation, copies */
+    PZ_NK = 8
+} pz_kernel_id;
+
+/* enable != 0: every kernel launch of this context is bracketed by CUDA events
+ * recorded on the launching stream.  Disabling (or re-enabling) clears the
+ * accumulated times.  Host-side overhead: two event records per launch. */
+pz_status pz_set_profiling(pz_ctx *ctx, int32_t enable);
+
+/* Accumulated device time (ms) and launch count per kernel family since
+ * profiling was enabled, for the first nk families (ms, counts: host arrays
+ * [nk]).  Synchronises on the recorded events. */
+pz_status pz_kernel_times(pz_ctx *ctx, double *ms, int64_t *counts, int32_t nk);
+
+/* ---- device-function probes (same device code as the hot path) ------------- */
+
+/* FP32 Voigt H(a,v) and dH/da exactly as the mixed-precision kernels evaluate
+ * them, for n device-resident (a, v) pairs.  a, v, H: device FP32 [n]; dHda
+ * device FP32 [n] or NULL. */
+pz_status pz_probe_voigt(const float *a, const float *v, int64_t n, float *H, float *dHda,
+                         void *stream);
+
+/* FP64 E_2, E_3, E_4 exactly as the flux kernels evaluate them.  x: device
+ * FP64 [n] (x >= 0); out: device FP64 [3][n]. */
+pz_status pz_probe_expn(const double *x, int64_t n, double *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PZ_H */

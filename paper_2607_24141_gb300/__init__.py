@@ -1,0 +1,335 @@
+"""GB300-native synthesis hot path of arXiv:2607.24141 ("The Payne Zero Project I").
+
+The compute lives in ``libpz.so`` (CUDA, sm_103a) behind the C ABI declared in
+``include/pz.h``.  This module only marshals arguments:
+
+* ``pz_create``, ``pz_line_opacity``, ``pz_flux``, ``pz_instrument``,
+  ``pz_loss_chi2``, ``pz_backward``, ... -- one Python function per C entry
+  point, same name, raising :class:`PzError` on a non-zero status;
+* :class:`Synthesizer` -- owns one context plus the host arrays it was built
+  from, with torch CUDA tensors as device buffers;
+* :class:`SynthesisFunction` -- a ``torch.autograd.Function`` whose forward is
+  line opacity -> flux -> instrument and whose backward is ``pz_backward``.
+
+There is no CPU fallback: if the library cannot be loaded every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import inputs  # noqa: F401  (seeded generators; no synthesis arithmetic)
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libpz.so")
+_lib = None
+
+PZ_OK, PZ_EINVAL, PZ_ENOMEM, PZ_ECUDA, PZ_ETIMEOUT, PZ_ESTATE = range(6)
+PZ_FP64, PZ_MIXED = 0, 1
+_STATUS = {1: "PZ_EINVAL", 2: "PZ_ENOMEM", 3: "PZ_ECUDA", 4: "PZ_ETIMEOUT", 5: "PZ_ESTATE"}
+
+_dp = C.POINTER(C.c_double)
+_fp = C.POINTER(C.c_float)
+_ip = C.POINTER(C.c_int32)
+_vp = C.c_void_p
+
+
+class PzError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (_STATUS.get(status, str(status)), msg))
+        self.status = status
+
+
+class pz_atmos(C.Structure):
+    _fields_ = [("n_depth", C.c_int32), ("n_species", C.c_int32),
+                ("m", _dp), ("T", _dp), ("rho", _dp), ("n_e", _dp), ("n_pert", _dp),
+                ("pop", _dp), ("mass_amu", _dp), ("xi_cms", C.c_double), ("kappa_c", _dp),
+                ("lambda0_nm", C.c_double), ("R_grid", C.c_double), ("n_lambda", C.c_int64)]
+
+
+class pz_linelist(C.Structure):
+    _fields_ = [("n_lines", C.c_int64), ("lambda_nm", _dp), ("log_gf", _fp), ("E_low_eV", _fp),
+                ("log_gamma_rad", _fp), ("log_gamma4", _fp), ("log_gamma6", _fp),
+                ("species", _ip), ("half_window", C.c_int32)]
+
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "pz_create": (C.c_int, [C.POINTER(pz_atmos), C.POINTER(pz_linelist), C.c_int, C.POINTER(_vp)]),
+    "pz_destroy": (C.c_int, [_vp]),
+    "pz_set_corrections": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int32, _vp]),
+    "pz_line_opacity": (C.c_int, [_vp, _vp, _vp]),
+    "pz_flux": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "pz_instrument": (C.c_int, [_vp, C.c_double, C.c_double, C.c_double, _vp, C.c_int64, _vp, _vp]),
+    "pz_loss_chi2": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp]),
+    "pz_backward": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    "pz_last_error": (C.c_char_p, []),
+    "pz_eval_count": (C.c_int64, [_vp]),
+    "pz_last_launch_count": (C.c_int32, [_vp]),
+    "pz_set_tiling": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "pz_set_profiling": (C.c_int, [_vp, C.c_int32]),
+    "pz_kernel_times": (C.c_int, [_vp, _dp, C.POINTER(C.c_int64), C.c_int32]),
+    "pz_probe_voigt": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
+    "pz_probe_expn": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
+}
+EXPORTED = tuple(_SIGS)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load(build_if_missing: bool = True):
+    """Load libpz.so (building it in-tree with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        from . import build as _build
+        if not _build.up_to_date():
+            _build.build()
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError("libpz.so is not built (run __graft_entry__.build()); there is no CPU fallback")
+    lib = C.CDLL(_LIB_PATH)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(st: int):
+    if st != PZ_OK:
+        raise PzError(st, load().pz_last_error().decode())
+
+
+def _ptr(t) -> Optional[int]:
+    """Device pointer of a torch tensor (or None)."""
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+# ---------------------------------------------------------------------------
+# one function per C entry point (argument marshalling only)
+# ---------------------------------------------------------------------------
+
+def pz_create(atmos: pz_atmos, lines: pz_linelist, precision: int = PZ_MIXED) -> int:
+    ctx = _vp()
+    _check(load().pz_create(C.byref(atmos), C.byref(lines), int(precision), C.byref(ctx)))
+    return ctx.value
+
+
+def pz_destroy(ctx: int):
+    _check(load().pz_destroy(ctx))
+
+
+def pz_set_corrections(ctx, dlog_gf=None, dlog_gamma6=None, dabund=None, elem_of_species=None,
+                       n_elem: int = 0, stream=None):
+    """Pointers may be torch CUDA tensors or numpy arrays (host)."""
+    keep = []
+
+    def p(x, dt):
+        if x is None:
+            return None
+        if isinstance(x, np.ndarray):
+            a = np.ascontiguousarray(x, dtype=dt)
+            keep.append(a)
+            return a.ctypes.data
+        return x.data_ptr()
+    _check(load().pz_set_corrections(ctx, p(dlog_gf, np.float32), p(dlog_gamma6, np.float32),
+                                     p(dabund, np.float32), p(elem_of_species, np.int32), int(n_elem),
+                                     _stream(stream)))
+
+
+def pz_line_opacity(ctx, kappa_line=None, stream=None):
+    _check(load().pz_line_opacity(ctx, _ptr(kappa_line), _stream(stream)))
+
+
+def pz_flux(ctx, F=None, Fc=None, stream=None):
+    _check(load().pz_flux(ctx, _ptr(F), _ptr(Fc), _stream(stream)))
+
+
+def pz_instrument(ctx, v_r_kms, v_b_kms, R_lsf, pix_lambda_nm, f_norm=None, stream=None):
+    if pix_lambda_nm is None:
+        _check(load().pz_instrument(ctx, 0.0, 0.0, 0.0, None, 0, _ptr(f_norm), _stream(stream)))
+        return
+    pix = np.ascontiguousarray(pix_lambda_nm, dtype=np.float64)
+    _check(load().pz_instrument(ctx, float(v_r_kms), float(v_b_kms), float(R_lsf), pix.ctypes.data,
+                                pix.size, _ptr(f_norm), _stream(stream)))
+
+
+def pz_loss_chi2(ctx, y, w=None, loss=None, dL_df=None, stream=None):
+    _check(load().pz_loss_chi2(ctx, _ptr(y), _ptr(w), y.numel(), _ptr(loss), _ptr(dL_df), _stream(stream)))
+
+
+def pz_backward(ctx, dL_df, g_dlog_gf=None, g_dlog_gamma6=None, g_dabund=None, stream=None):
+    _check(load().pz_backward(ctx, _ptr(dL_df), _ptr(g_dlog_gf), _ptr(g_dlog_gamma6), _ptr(g_dabund),
+                              _stream(stream)))
+
+
+def pz_eval_count(ctx) -> int:
+    return int(load().pz_eval_count(ctx))
+
+
+def pz_last_launch_count(ctx) -> int:
+    return int(load().pz_last_launch_count(ctx))
+
+
+def pz_set_tiling(ctx, lambda_per_thread=0, depth_per_warp=0, warps_per_cta=0, lines_per_chunk=0):
+    _check(load().pz_set_tiling(ctx, lambda_per_thread, depth_per_warp, warps_per_cta, lines_per_chunk))
+
+
+KERNEL_NAMES = ("line_fwd", "line_bwd", "flux", "rt_adjoint", "instrument", "inst_adjoint", "loss", "other")
+
+
+def pz_set_profiling(ctx, enable=True):
+    _check(load().pz_set_profiling(ctx, 1 if enable else 0))
+
+
+def pz_kernel_times(ctx):
+    """{family: (total_ms, launches)} accumulated since profiling was enabled."""
+    n = len(KERNEL_NAMES)
+    ms = (C.c_double * n)()
+    cnt = (C.c_int64 * n)()
+    _check(load().pz_kernel_times(ctx, ms, cnt, n))
+    return {KERNEL_NAMES[k]: (ms[k], cnt[k]) for k in range(n)}
+
+
+def pz_probe_voigt(a, v, H, dHda=None, stream=None):
+    _check(load().pz_probe_voigt(_ptr(a), _ptr(v), a.numel(), _ptr(H), _ptr(dHda), _stream(stream)))
+
+
+def pz_probe_expn(x, out, stream=None):
+    _check(load().pz_probe_expn(_ptr(x), x.numel(), _ptr(out), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper
+# ---------------------------------------------------------------------------
+
+class Synthesizer:
+    """One context for a :class:`inputs.Problem` (atmosphere + grid + lines)."""
+
+    def __init__(self, prob, precision: int = PZ_MIXED, device: int = 0):
+        import torch
+        torch.cuda.set_device(device)
+        self.prob = prob
+        self.precision = precision
+        at, ll = prob.atmos, prob.lines
+        f64 = lambda a: np.ascontiguousarray(a, np.float64)  # noqa: E731
+        f32 = lambda a: np.ascontiguousarray(a, np.float32)  # noqa: E731
+        self._keep = dict(m=f64(at.m), T=f64(at.T), rho=f64(at.rho), ne=f64(at.n_e), np=f64(at.n_pert),
+                          pop=f64(at.pop), mass=f64(at.mass_amu), kc=f64(prob.kappa_c),
+                          lam=f64(ll.lambda_nm), gf=f32(ll.log_gf), E=f32(ll.E_low_eV),
+                          gr=f32(ll.log_gamma_rad), g4=f32(ll.log_gamma4), g6=f32(ll.log_gamma6),
+                          sp=np.ascontiguousarray(ll.species, np.int32))
+        k = self._keep
+        A = pz_atmos()
+        A.n_depth, A.n_species = at.n_depth, at.n_species
+        A.m, A.T, A.rho = [k[n].ctypes.data_as(_dp) for n in ("m", "T", "rho")]
+        A.n_e, A.n_pert, A.pop, A.mass_amu = [k[n].ctypes.data_as(_dp) for n in ("ne", "np", "pop", "mass")]
+        A.xi_cms = at.xi_cms
+        A.kappa_c = k["kc"].ctypes.data_as(_dp)
+        A.lambda0_nm, A.R_grid, A.n_lambda = prob.grid.lambda0_nm, prob.grid.R_grid, prob.grid.n_lambda
+        L = pz_linelist()
+        L.n_lines = ll.n_lines
+        L.lambda_nm = k["lam"].ctypes.data_as(_dp)
+        L.log_gf, L.E_low_eV = k["gf"].ctypes.data_as(_fp), k["E"].ctypes.data_as(_fp)
+        L.log_gamma_rad, L.log_gamma4, L.log_gamma6 = [k[n].ctypes.data_as(_fp) for n in ("gr", "g4", "g6")]
+        L.species = k["sp"].ctypes.data_as(_ip)
+        L.half_window = ll.half_window
+        self._atmos, self._lines = A, L
+        self.ctx = pz_create(A, L, precision)
+        self.device = torch.device("cuda", device)
+        self.n_lambda = prob.grid.n_lambda
+        self.n_depth = at.n_depth
+        self.n_out = prob.instrument.pix_lambda_nm.size if prob.instrument is not None else self.n_lambda
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            pz_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_evals(self) -> int:
+        return pz_eval_count(self.ctx)
+
+    def set_corrections(self, dlog_gf=None, dlog_gamma6=None, dabund=None, stream=None):
+        eos = self.prob.elem_of_species if dabund is not None else None
+        pz_set_corrections(self.ctx, dlog_gf, dlog_gamma6, dabund, eos,
+                           self.prob.n_elem if dabund is not None else 0, stream)
+
+    def forward(self, kappa=None, F=None, Fc=None, f=None, stream=None):
+        """line opacity -> flux -> instrument; returns f (allocated if not given)."""
+        import torch
+        if f is None:
+            f = torch.empty(self.n_out, dtype=torch.float32, device=self.device)
+        pz_line_opacity(self.ctx, kappa, stream)
+        pz_flux(self.ctx, F, Fc, stream)
+        inst = self.prob.instrument
+        if inst is None:
+            pz_instrument(self.ctx, 0, 0, 0, None, f, stream)
+        else:
+            pz_instrument(self.ctx, inst.v_r_kms, inst.v_b_kms, inst.R_lsf, inst.pix_lambda_nm, f, stream)
+        return f
+
+    def loss(self, y, w=None, loss=None, dL_df=None, stream=None):
+        pz_loss_chi2(self.ctx, y, w, loss, dL_df, stream)
+
+    def backward(self, dL_df, g_gf=None, g_g6=None, g_ab=None, stream=None):
+        pz_backward(self.ctx, dL_df, g_gf, g_g6, g_ab, stream)
+
+
+def _torch_function():
+    import torch
+
+    class SynthesisFunction(torch.autograd.Function):
+        """f = instrument(flux(line_opacity(corrections))) with a hand-written backward.
+
+        Inputs are the corrections (Delta log gf, Delta log gamma6, Delta abundance)
+        as float32 CUDA tensors; gradients come from ``pz_backward``."""
+
+        @staticmethod
+        def forward(ctx, synth, dlog_gf, dlog_gamma6, dabund):
+            synth.set_corrections(dlog_gf, dlog_gamma6, dabund)
+            f = synth.forward()
+            ctx.synth = synth
+            ctx.has_ab = dabund is not None
+            return f
+
+        @staticmethod
+        def backward(ctx, grad_f):
+            s = ctx.synth
+            grad_f = grad_f.contiguous().to(torch.float32)
+            nl = s.prob.lines.n_lines
+            g_gf = torch.empty(nl, dtype=torch.float32, device=grad_f.device)
+            g_g6 = torch.empty(nl, dtype=torch.float32, device=grad_f.device)
+            g_ab = torch.empty(s.prob.n_elem, dtype=torch.float32, device=grad_f.device) if ctx.has_ab else None
+            s.backward(grad_f, g_gf, g_g6, g_ab)
+            return None, g_gf, g_g6, g_ab
+
+    return SynthesisFunction
+
+
+def __getattr__(name):
+    if name == "SynthesisFunction":
+        return _torch_function()
+    raise AttributeError(name)

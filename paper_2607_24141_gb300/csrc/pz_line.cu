@@ -1,0 +1,783 @@
+// pz_line.cu -- windowed Voigt line-opacity sum (Eqs. 4-5) and its adjoint
+// (Sec. 6), FP32-mixed and plain FP64 forms, plus the per-device Voigt tables.
+//
+// Mixed-precision kernels.  A CTA owns a wavelength tile of T = 32 J grid
+// points and a depth range of GW x DS layers; warp w sweeps layers
+// [d0 + w DS, d0 + (w+1) DS) and lane l owns the J contiguous points
+// t0 + l J + [0, J).  Lines are sorted by centre; the CTA's line range
+// [tile_lo, tile_hi) (all lines whose window |i - i_l| <= W touches the tile)
+// is found on the host by binary search.  Lines are staged into shared memory
+// LC at a time: the CTA first computes the per-(line, depth) prefactors of
+// Eqs. 4-5 (strength A, damping a, Doppler factor c/dv_D and the pre-scaled
+// far-wing polynomial coefficients) once for the whole tile, then every
+// thread accumulates its J x DS (lambda, depth) sums in registers.  Whether a
+// line is entirely inside its window and in the far wing (|v| >= 20 at every
+// depth) over the whole tile is decided once per line for the CTA, so that
+// branch is uniform across warps.  Per-chunk FP32 partial sums are folded into
+// a compensated (hi, lo) pair (2Sum).  The frequency offset is formed in index
+// space: v = expm1((x_l - i) ln r) c/dv_D with x_l - i = (i_l - i) + frac_l,
+// the integer part exact, avoiding the cancellation of lambda_l/lambda_i - 1.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+#include <vector>
+
+#include "pz_internal.h"
+#include "pz_voigt.cuh"
+
+namespace pz {
+
+// ---------------------------------------------------------------------------
+// Host construction of the tables (FP64), once per device.
+// ---------------------------------------------------------------------------
+
+// Weideman coefficients: Fourier cosine coefficients of psi(t) = (L^2 + t^2) e^{-t^2}
+// under t = L tan(theta/2), L = (N/sqrt 2)^(1/2), by the midpoint rule on 8N points.
+static void weideman_coeffs(int N, std::vector<double> &a, double &L) {
+    L = std::sqrt(N / std::sqrt(2.0));
+    int M = 4 * N;
+    a.assign(N + 1, 0.0);
+    for (int k = 0; k < 2 * M; ++k) {
+        double th = kPI * (k - M + 0.5) / M;
+        double t = L * std::tan(0.5 * th);
+        double psi = (L * L + t * t) * std::exp(-t * t);
+        for (int n = 0; n <= N; ++n) a[n] += psi * std::cos(n * th);
+    }
+    for (int n = 0; n <= N; ++n) a[n] /= 2 * M;
+}
+
+// Dawson's integral D(x) = e^{-x^2} Int_0^x e^{t^2} dt = x Int_0^1 e^{-x^2 (1 - s^2)} ds,
+// composite 8-point Gauss-Legendre on 256 panels.
+static double dawson_quad(double x) {
+    static const double gx[8] = {-0.9602898564975363, -0.7966664774136267, -0.5255324099163290,
+                                 -0.1834346424956498, 0.1834346424956498,  0.5255324099163290,
+                                 0.7966664774136267,  0.9602898564975363};
+    static const double gw[8] = {0.1012285362903763, 0.2223810344533745, 0.3137066458778873,
+                                 0.3626837833783620, 0.3626837833783620, 0.3137066458778873,
+                                 0.2223810344533745, 0.1012285362903763};
+    const int P = 256;
+    double sum = 0.0, h = 1.0 / P;
+    for (int p = 0; p < P; ++p)
+        for (int k = 0; k < 8; ++k) {
+            double s = (p + 0.5 * (gx[k] + 1.0)) * h;
+            sum += 0.5 * h * gw[k] * std::exp(-x * x * (1.0 - s * s));
+        }
+    return x * sum;
+}
+
+// Node coefficients D^(k)(x_j)/k! from D' = 1 - 2xD, D^(k+1) = -2x D^(k) - 2k D^(k-1).
+static void dawson_table(std::vector<float> &tab) {
+    tab.assign(kDawsonNodes * (kDawsonK + 1), 0.0f);
+    for (int j = 0; j < kDawsonNodes; ++j) {
+        double x = (double)j / kDawsonPerUnit;
+        double D[kDawsonK + 2];
+        D[0] = dawson_quad(x);
+        D[1] = 1.0 - 2.0 * x * D[0];
+        for (int k = 1; k < kDawsonK; ++k) D[k + 1] = -2.0 * x * D[k] - 2.0 * k * D[k - 1];
+        double fact = 1.0;
+        for (int k = 0; k <= kDawsonK; ++k) {
+            if (k > 0) fact *= k;
+            tab[j * (kDawsonK + 1) + k] = (float)(D[k] / fact);
+        }
+    }
+}
+
+pz_status ensure_device_tables() {
+    static std::mutex mu;
+    static bool host_ready = false;
+    static std::vector<float> weid, daw;
+    static std::vector<double> weid64;
+    static float weidL;
+    static double weidL64;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
+    std::lock_guard<std::mutex> lk(mu);
+    if (!host_ready) {
+        std::vector<double> a;
+        double L;
+        weideman_coeffs(kWeidN, a, L);
+        weid.assign(a.begin(), a.end());
+        weidL = (float)L;
+        weideman_coeffs(kWeidN64, weid64, weidL64);
+        dawson_table(daw);
+        host_ready = true;
+    }
+    if (dev < 0 || dev >= 64) return fail(PZ_EINVAL, "device ordinal out of range");
+    if (done[dev]) return PZ_OK;
+    if ((e = cudaMemcpyToSymbol(c_weid, weid.data(), sizeof(float) * (kWeidN + 1))) != cudaSuccess ||
+        (e = cudaMemcpyToSymbol(c_weidL, &weidL, sizeof(float))) != cudaSuccess ||
+        (e = cudaMemcpyToSymbol(c_weid64, weid64.data(), sizeof(double) * (kWeidN64 + 1))) != cudaSuccess ||
+        (e = cudaMemcpyToSymbol(c_weidL64, &weidL64, sizeof(double))) != cudaSuccess ||
+        (e = cudaMemcpyToSymbol(g_dawson, daw.data(), sizeof(float) * daw.size())) != cudaSuccess)
+        return cuda_check(e, "upload Voigt tables");
+    done[dev] = true;
+    return PZ_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Mixed-precision kernels
+// ---------------------------------------------------------------------------
+
+struct LineArgs {
+    int64_t nlam, ld;
+    int nd, W;
+    float lnr, lam0cm;
+    const int32_t *tile_lo, *tile_hi;
+    const float *ilf, *frac, *E, *lamcm, *grad, *g4, *g6, *Q;
+    const int32_t *sp;
+    const float *R, *invdv, *thr;                   // [ns][nd], [ns][nd], [ns]
+    const float *beta_hi, *beta_lo, *ne, *npert, *c2T;
+    float *kline;                                   // forward output [nd][ld]
+    const float *Gt;                                // backward input [nd][ld]
+    double *gacc;                                   // backward output [2][nl]
+    int64_t nl;
+};
+
+// Per-(line, depth) prefactors.  NP = 8 (forward) or 16 (backward):
+//  [0] k = c/dv_D   [1] a^2   [2..6] B1..B5 = A a/sqrt(pi) x (1, 1.5, 3.75-2a^2, -15a^2, 12a^4)
+//  [7] A            (backward:) [8..13] C1..C6 = A a6/sqrt(pi) x (1, 1.5-2a^2, 3.75-12a^2,
+//  12a^4-67.5a^2, 180a^4, -120a^6)   [14] A a6   [15] a
+template <int NP>
+__device__ __forceinline__ void line_params(const LineArgs &g, int64_t l, int d, float *out) {
+    if (d >= g.nd) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) out[k] = 0.0f;
+        out[1] = 1.0f;
+        return;
+    }
+    int s = g.sp[l];
+    int id = s * g.nd + d;
+    float invdv = __ldg(g.invdv + id);
+    float E = g.E[l];
+    float bh = __ldg(g.beta_hi + d), bl = __ldg(g.beta_lo + d);
+    float p = E * bh;
+    float r = fmaf(E, bh, -p) + E * bl;              // E beta = p + r
+    float boltz = expf(-p) * (1.0f - r);
+    float A = g.Q[l] * __ldg(g.R + id) * boltz;
+    float lw = g.lamcm[l] * invdv * (float)(1.0 / (4.0 * kPI));
+    float g6n = g.g6[l] * __ldg(g.npert + d);
+    float a = fmaf(g.g4[l], __ldg(g.ne + d), g.grad[l] + g6n) * lw;
+    float a2 = a * a;
+    float B1 = A * a * kInvSqrtPiF;
+    out[0] = (float)kC * invdv;
+    out[1] = a2;
+    out[2] = B1;
+    out[3] = 1.5f * B1;
+    out[4] = fmaf(-2.0f, a2, 3.75f) * B1;
+    out[5] = -15.0f * a2 * B1;
+    out[6] = 12.0f * a2 * a2 * B1;
+    out[7] = A;
+    if (NP == 16) {
+        float Aa6 = A * g6n * lw;
+        float C1 = Aa6 * kInvSqrtPiF;
+        out[8] = C1;
+        out[9] = fmaf(-2.0f, a2, 1.5f) * C1;
+        out[10] = fmaf(-12.0f, a2, 3.75f) * C1;
+        out[11] = a2 * fmaf(12.0f, a2, -67.5f) * C1;
+        out[12] = 180.0f * a2 * a2 * C1;
+        out[13] = -120.0f * a2 * a2 * a2 * C1;
+        out[14] = Aa6;
+        out[15] = a;
+    }
+}
+
+// index-space frequency offset u = lambda_l/lambda_i - 1 = expm1(Delta ln r)
+__device__ __forceinline__ float offset_u(float delta, float lnr) {
+    float y = delta * lnr;
+    return fmaf(y * y, fmaf(y, 0.16666667f, 0.5f), y);
+}
+
+struct alignas(16) LineInfo {
+    float ilf, frac, thr, pad;
+};
+
+template <int J, int DS>
+__global__ void __launch_bounds__(128, 1) k_line_fwd(LineArgs g, int GW, int LC) {
+    extern __shared__ float4 smem4[];
+    const int T = 32 * J;
+    const int DC = GW * DS;
+    float4 *s_par = smem4;                                  // [LC][DC][2]
+    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * DC * 2);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    const int d0 = blockIdx.y * DC;
+    const int t0 = tile * T;
+    const float t0f = (float)t0, tendf = (float)(t0 + T - 1);
+    const int lam_thr = t0 + lane * J;
+    const float lamf = (float)lam_thr;
+    const int lo = g.tile_lo[tile], hi = g.tile_hi[tile];
+
+    float acc[DS][J], shi[DS][J], slo[DS][J];
+#pragma unroll
+    for (int dd = 0; dd < DS; ++dd)
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[dd][j] = shi[dd][j] = slo[dd][j] = 0.0f;
+
+    for (int c0 = lo; c0 < hi; c0 += LC) {
+        const int nl = min(LC, hi - c0);
+        __syncthreads();
+        for (int idx = tid; idx < nl * DC; idx += blockDim.x) {
+            int li = idx / DC, dd = idx - li * DC;
+            float p[8];
+            line_params<8>(g, c0 + li, d0 + dd, p);
+            float4 *dst = s_par + ((size_t)li * DC + dd) * 2;
+            dst[0] = make_float4(p[0], p[1], p[2], p[3]);
+            dst[1] = make_float4(p[4], p[5], p[6], p[7]);
+        }
+        for (int li = tid; li < nl; li += blockDim.x) {
+            int64_t l = c0 + li;
+            LineInfo info;
+            info.ilf = g.ilf[l];
+            info.frac = g.frac[l];
+            info.thr = __ldg(g.thr + g.sp[l]);
+            info.pad = 0.0f;
+            s_line[li] = info;
+        }
+        __syncthreads();
+
+        for (int li = 0; li < nl; ++li) {
+            const LineInfo info = s_line[li];
+            const float dlo = info.ilf - t0f + info.frac;     // x_l - t0
+            const float dhi = info.ilf - tendf + info.frac;   // x_l - (t0 + T - 1)
+            const float dmin = fmaxf(0.0f, fmaxf(-dlo, dhi));
+            const bool full = (info.ilf - (float)g.W <= t0f) && (info.ilf + (float)g.W >= tendf);
+            const float delta0 = (info.ilf - lamf) + info.frac;
+            float u[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) u[j] = offset_u(delta0 - (float)j, g.lnr);
+            const float4 *par = s_par + ((size_t)li * DC + warp * DS) * 2;
+            if (full && dmin >= info.thr) {
+#pragma unroll
+                for (int dd = 0; dd < DS; ++dd) {
+                    const float4 p0 = par[2 * dd], p1 = par[2 * dd + 1];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        float x = u[j] * p0.x;
+                        float t = rcp_approx(fmaf(x, x, p0.y));
+                        float h = fmaf(t, p1.z, p1.y);
+                        h = fmaf(t, h, p1.x);
+                        h = fmaf(t, h, p0.w);
+                        h = fmaf(t, h, p0.z);
+                        acc[dd][j] = fmaf(t, h, acc[dd][j]);
+                    }
+                }
+            } else {
+                const int il = (int)info.ilf;
+#pragma unroll
+                for (int dd = 0; dd < DS; ++dd) {
+                    const float4 p0 = par[2 * dd], p1 = par[2 * dd + 1];
+                    const float a = sqrtf(p0.y);
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        int di = lam_thr + j - il;
+                        if (di >= -g.W && di <= g.W) {
+                            float x = fabsf(u[j] * p0.x);
+                            float r2 = fmaf(x, x, p0.y);
+                            float term;
+                            if (r2 >= kFar2) {
+                                float t = rcp_approx(r2);
+                                float h = fmaf(t, p1.z, p1.y);
+                                h = fmaf(t, h, p1.x);
+                                h = fmaf(t, h, p0.w);
+                                h = fmaf(t, h, p0.z);
+                                term = t * h;
+                            } else {
+                                float H, dH;
+                                voigt_general<false>(x, a, H, dH);
+                                term = p1.w * H;
+                            }
+                            acc[dd][j] += term;
+                        }
+                    }
+                }
+            }
+        }
+        // fold the chunk partials into the compensated sums (2Sum)
+#pragma unroll
+        for (int dd = 0; dd < DS; ++dd)
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                float p = acc[dd][j], h = shi[dd][j];
+                float s = h + p;
+                float bp = s - h;
+                float e = (h - (s - bp)) + (p - bp);
+                shi[dd][j] = s;
+                slo[dd][j] += e;
+                acc[dd][j] = 0.0f;
+            }
+    }
+
+    // epilogue: stimulated-emission factor at the sample frequency, store
+#pragma unroll
+    for (int dd = 0; dd < DS; ++dd) {
+        int d = d0 + warp * DS + dd;
+        if (d >= g.nd) continue;
+        float c2T = __ldg(g.c2T + d);
+        float v[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            float lam = g.lam0cm * expf((float)(lam_thr + j) * g.lnr);
+            float stim = -expm1f(-c2T / lam);
+            v[j] = stim * (shi[dd][j] + slo[dd][j]);
+        }
+        float *row = g.kline + (int64_t)d * g.ld + lam_thr;
+        if (J == 4) {
+            *reinterpret_cast<float4 *>(row) = make_float4(v[0], v[1 % J], v[2 % J], v[3 % J]);
+        } else if (J == 2) {
+            *reinterpret_cast<float2 *>(row) = make_float2(v[0], v[1 % J]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < J; ++j) row[j] = v[j];
+        }
+    }
+}
+
+template <int J, int DS>
+__global__ void __launch_bounds__(128, 1) k_line_bwd(LineArgs g, int GW, int LC) {
+    extern __shared__ float4 smem4[];
+    const int T = 32 * J;
+    const int DC = GW * DS;
+    float4 *s_par = smem4;                                              // [LC][DC][4]
+    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * DC * 4);
+    float2 *s_red = reinterpret_cast<float2 *>(s_line + LC);            // [LC][GW]
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tile = blockIdx.x;
+    const int d0 = blockIdx.y * DC;
+    const int t0 = tile * T;
+    const float t0f = (float)t0, tendf = (float)(t0 + T - 1);
+    const int lam_thr = t0 + lane * J;
+    const float lamf = (float)lam_thr;
+    const int lo = g.tile_lo[tile], hi = g.tile_hi[tile];
+
+    // G * stim for the thread's (depth, lambda) cells; zero outside the grid
+    float gv[DS][J];
+#pragma unroll
+    for (int dd = 0; dd < DS; ++dd) {
+        int d = d0 + warp * DS + dd;
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            gv[dd][j] = (d < g.nd && lam_thr + j < g.nlam) ? g.Gt[(int64_t)d * g.ld + lam_thr + j] : 0.0f;
+    }
+
+    for (int c0 = lo; c0 < hi; c0 += LC) {
+        const int nl = min(LC, hi - c0);
+        __syncthreads();
+        for (int idx = tid; idx < nl * DC; idx += blockDim.x) {
+            int li = idx / DC, dd = idx - li * DC;
+            float p[16];
+            line_params<16>(g, c0 + li, d0 + dd, p);
+            float4 *dst = s_par + ((size_t)li * DC + dd) * 4;
+            dst[0] = make_float4(p[0], p[1], p[2], p[3]);
+            dst[1] = make_float4(p[4], p[5], p[6], p[7]);
+            dst[2] = make_float4(p[8], p[9], p[10], p[11]);
+            dst[3] = make_float4(p[12], p[13], p[14], p[15]);
+        }
+        for (int li = tid; li < nl; li += blockDim.x) {
+            int64_t l = c0 + li;
+            LineInfo info;
+            info.ilf = g.ilf[l];
+            info.frac = g.frac[l];
+            info.thr = __ldg(g.thr + g.sp[l]);
+            info.pad = 0.0f;
+            s_line[li] = info;
+        }
+        __syncthreads();
+
+        for (int li = 0; li < nl; ++li) {
+            const LineInfo info = s_line[li];
+            const float dlo = info.ilf - t0f + info.frac;
+            const float dhi = info.ilf - tendf + info.frac;
+            const float dmin = fmaxf(0.0f, fmaxf(-dlo, dhi));
+            const bool full = (info.ilf - (float)g.W <= t0f) && (info.ilf + (float)g.W >= tendf);
+            const float delta0 = (info.ilf - lamf) + info.frac;
+            float u[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) u[j] = offset_u(delta0 - (float)j, g.lnr);
+            const float4 *par = s_par + ((size_t)li * DC + warp * DS) * 4;
+            float s1 = 0.0f, s2 = 0.0f;
+            if (full && dmin >= info.thr) {
+#pragma unroll
+                for (int dd = 0; dd < DS; ++dd) {
+                    const float4 p0 = par[4 * dd], p1 = par[4 * dd + 1];
+                    const float4 p2 = par[4 * dd + 2], p3 = par[4 * dd + 3];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        float x = u[j] * p0.x;
+                        float t = rcp_approx(fmaf(x, x, p0.y));
+                        float h = fmaf(t, p1.z, p1.y);
+                        h = fmaf(t, h, p1.x);
+                        h = fmaf(t, h, p0.w);
+                        h = fmaf(t, h, p0.z);
+                        float q = fmaf(t, p3.y, p3.x);
+                        q = fmaf(t, q, p2.w);
+                        q = fmaf(t, q, p2.z);
+                        q = fmaf(t, q, p2.y);
+                        q = fmaf(t, q, p2.x);
+                        float gt = gv[dd][j] * t;
+                        s1 = fmaf(gt, h, s1);
+                        s2 = fmaf(gt, q, s2);
+                    }
+                }
+            } else {
+                const int il = (int)info.ilf;
+#pragma unroll
+                for (int dd = 0; dd < DS; ++dd) {
+                    const float4 p0 = par[4 * dd], p1 = par[4 * dd + 1];
+                    const float4 p2 = par[4 * dd + 2], p3 = par[4 * dd + 3];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        int di = lam_thr + j - il;
+                        if (di >= -g.W && di <= g.W) {
+                            float x = fabsf(u[j] * p0.x);
+                            float r2 = fmaf(x, x, p0.y);
+                            float th, tq;
+                            if (r2 >= kFar2) {
+                                float t = rcp_approx(r2);
+                                float h = fmaf(t, p1.z, p1.y);
+                                h = fmaf(t, h, p1.x);
+                                h = fmaf(t, h, p0.w);
+                                h = fmaf(t, h, p0.z);
+                                float q = fmaf(t, p3.y, p3.x);
+                                q = fmaf(t, q, p2.w);
+                                q = fmaf(t, q, p2.z);
+                                q = fmaf(t, q, p2.y);
+                                q = fmaf(t, q, p2.x);
+                                th = t * h;
+                                tq = t * q;
+                            } else {
+                                float H, dH;
+                                voigt_general<true>(x, p3.w, H, dH);
+                                th = p1.w * H;
+                                tq = p3.z * dH;
+                            }
+                            s1 = fmaf(gv[dd][j], th, s1);
+                            s2 = fmaf(gv[dd][j], tq, s2);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            }
+            if (lane == 0) s_red[li * GW + warp] = make_float2(s1, s2);
+        }
+        __syncthreads();
+        for (int li = tid; li < nl; li += blockDim.x) {
+            double a1 = 0.0, a2 = 0.0;
+            for (int w = 0; w < GW; ++w) {
+                float2 r = s_red[li * GW + w];
+                a1 += r.x;
+                a2 += r.y;
+            }
+            atomicAdd(g.gacc + c0 + li, a1);
+            atomicAdd(g.gacc + g.nl + c0 + li, a2);
+        }
+    }
+}
+
+static LineArgs make_args(pz_ctx *c) {
+    LineArgs g;
+    g.nlam = c->nlam;
+    g.ld = c->ld;
+    g.nd = c->nd;
+    g.W = c->W;
+    g.lnr = (float)c->lnr;
+    g.lam0cm = (float)(c->lambda0_nm * 1e-7);
+    g.tile_lo = c->d_tile_lo;
+    g.tile_hi = c->d_tile_hi;
+    g.ilf = c->L.ilf;
+    g.frac = c->L.frac;
+    g.E = c->L.E;
+    g.lamcm = c->L.lamcm;
+    g.grad = c->L.grad;
+    g.g4 = c->L.g4;
+    g.g6 = c->L.g6;
+    g.Q = c->L.Q;
+    g.sp = c->L.sp;
+    g.R = c->d_R;
+    g.invdv = c->d_invdv;
+    g.thr = c->d_thr;
+    g.beta_hi = c->d_beta_hi;
+    g.beta_lo = c->d_beta_lo;
+    g.ne = c->d_ne;
+    g.npert = c->d_npert;
+    g.c2T = c->d_c2T;
+    g.kline = (float *)c->d_kline;
+    g.Gt = c->d_Gt;
+    g.gacc = c->d_gacc;
+    g.nl = c->L.n;
+    return g;
+}
+
+template <int J, int DS>
+static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
+    const Tiling &t = c->tiling;
+    LineArgs g = make_args(c);
+    size_t smem = (size_t)t.LC * t.depth_per_cta() * 2 * sizeof(float4) + t.LC * sizeof(LineInfo);
+    static bool attr_set[64] = {false};
+    if (!attr_set[c->device]) {
+        cudaFuncSetAttribute(k_line_fwd<J, DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set[c->device] = true;
+    }
+    dim3 grid(c->ntiles, (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta());
+    k_line_fwd<J, DS><<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LC);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+template <int J, int DS>
+static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
+    const Tiling &t = c->tiling;
+    LineArgs g = make_args(c);
+    size_t smem = (size_t)t.LC * t.depth_per_cta() * 4 * sizeof(float4) + t.LC * sizeof(LineInfo) +
+                  (size_t)t.LC * t.GW * sizeof(float2);
+    static bool attr_set[64] = {false};
+    if (!attr_set[c->device]) {
+        cudaFuncSetAttribute(k_line_bwd<J, DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set[c->device] = true;
+    }
+    dim3 grid(c->ntiles, (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta());
+    k_line_bwd<J, DS><<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LC);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+#define PZ_TILE_DISPATCH(FN)                                  \
+    const Tiling &t = c->tiling;                              \
+    if (t.J == 4 && t.DS == 9) return FN<4, 9>(c, s);         \
+    if (t.J == 4 && t.DS == 6) return FN<4, 6>(c, s);         \
+    if (t.J == 2 && t.DS == 9) return FN<2, 9>(c, s);         \
+    if (t.J == 2 && t.DS == 12) return FN<2, 12>(c, s);       \
+    if (t.J == 4 && t.DS == 12) return FN<4, 12>(c, s);       \
+    return cudaErrorInvalidConfiguration;
+
+cudaError_t launch_line_fwd_mixed(pz_ctx *c, cudaStream_t s) { PZ_TILE_DISPATCH(launch_fwd_t) }
+cudaError_t launch_line_bwd_mixed(pz_ctx *c, cudaStream_t s) { PZ_TILE_DISPATCH(launch_bwd_t) }
+
+bool tiling_supported(int J, int DS) {
+    return (J == 4 && (DS == 9 || DS == 6 || DS == 12)) || (J == 2 && (DS == 9 || DS == 12));
+}
+
+// ---------------------------------------------------------------------------
+// Plain FP64 GPU form: one thread per (lambda, depth), FP64 Voigt, no shared
+// memory, no compensation; every line term is evaluated from the line table.
+// ---------------------------------------------------------------------------
+
+struct Fp64Args {
+    int64_t nlam, ld, nl;
+    int nd, W;
+    double lnr, lam0cm, xi2;
+    const int32_t *il;       // sorted integer centres (int)
+    const double *x64;       // fractional centre
+    const int32_t *sp;
+    const float *lg_gf, *dgf, *E, *lg_rad, *lg_4, *lg_6, *dg6;
+    const double *T, *rho, *ne, *npert, *pop, *mass, *dab;
+    const int32_t *eos;
+    double *kline;
+    const double *Gt;
+    double *gacc;
+};
+
+struct LineTerm64 {
+    double A, a, a6, kv;   // strength, damping, vdW damping, c/dv_D
+};
+
+__device__ __forceinline__ LineTerm64 term64(const Fp64Args &g, int64_t l, int d) {
+    LineTerm64 q;
+    int s = g.sp[l];
+    double T = g.T[d];
+    double dv = sqrt(2.0 * kKB * T / (g.mass[s] * kAMU) + g.xi2);
+    double lamcm = g.lam0cm * exp(g.x64[l] * g.lnr);
+    double inv_dnu = lamcm / dv;
+    double gf = exp10((double)g.lg_gf[l] + (double)g.dgf[l]);
+    double dab = (g.eos && g.eos[s] >= 0) ? g.dab[g.eos[s]] : 0.0;
+    double pop = g.pop[(int64_t)s * g.nd + d] * exp10(dab);
+    double boltz = exp(-(double)g.E[l] * kEV / (kKB * T));
+    q.A = (kPI * kE * kE / (kME * kC)) / kSQRTPI * gf * (pop / g.rho[d]) * boltz * inv_dnu;
+    double g6n = exp10((double)g.lg_6[l] + (double)g.dg6[l]) * g.npert[d];
+    q.a = (exp10((double)g.lg_rad[l]) + exp10((double)g.lg_4[l]) * g.ne[d] + g6n) * inv_dnu / (4.0 * kPI);
+    q.a6 = g6n * inv_dnu / (4.0 * kPI);
+    q.kv = kC / dv;
+    return q;
+}
+
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, int32_t key) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if (a[mid] < key) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_line_fwd_fp64(Fp64Args g) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int d = blockIdx.y;
+    if (i >= g.nlam) return;
+    int64_t l0 = lower_bound_i32(g.il, g.nl, (int32_t)(i - g.W));
+    int64_t l1 = lower_bound_i32(g.il, g.nl, (int32_t)(i + g.W + 1));
+    double sum = 0.0;
+    for (int64_t l = l0; l < l1; ++l) {
+        LineTerm64 q = term64(g, l, d);
+        double u = expm1((g.x64[l] - (double)i) * g.lnr);   // lambda_l/lambda_i - 1
+        double H, dH;
+        voigt64(u * q.kv, q.a, H, dH, false);
+        sum += q.A * H;
+    }
+    double lam = g.lam0cm * exp((double)i * g.lnr);
+    double stim = -expm1(-kC2 / (lam * g.T[d]));
+    g.kline[(int64_t)d * g.ld + i] = stim * sum;
+}
+
+// one thread per (line, depth); loops over the line's window
+__global__ void k_line_bwd_fp64(Fp64Args g) {
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int d = blockIdx.y;
+    if (l >= g.nl) return;
+    LineTerm64 q = term64(g, l, d);
+    int64_t il = g.il[l];
+    int64_t i0 = max((int64_t)0, il - g.W), i1 = min(g.nlam - 1, il + g.W);
+    double s1 = 0.0, s2 = 0.0;
+    for (int64_t i = i0; i <= i1; ++i) {
+        double u = expm1((g.x64[l] - (double)i) * g.lnr);
+        double H, dH;
+        voigt64(u * q.kv, q.a, H, dH, true);
+        double gs = g.Gt[(int64_t)d * g.ld + i];
+        s1 += gs * q.A * H;
+        s2 += gs * q.A * dH * q.a6;
+    }
+    atomicAdd(g.gacc + l, s1);
+    atomicAdd(g.gacc + g.nl + l, s2);
+}
+
+static Fp64Args make_args64(pz_ctx *c) {
+    Fp64Args g;
+    g.nlam = c->nlam;
+    g.ld = c->ld;
+    g.nl = c->L.n;
+    g.nd = c->nd;
+    g.W = c->W;
+    g.lnr = c->lnr;
+    g.lam0cm = c->lambda0_nm * 1e-7;
+    g.xi2 = c->xi * c->xi;
+    g.il = c->L.il32;
+    g.x64 = c->L.x64;
+    g.sp = c->L.sp;
+    g.lg_gf = c->L.lg_gf;
+    g.dgf = c->L.dgf;
+    g.E = c->L.E;
+    g.lg_rad = c->L.lg_rad;
+    g.lg_4 = c->L.lg_4;
+    g.lg_6 = c->L.lg_6;
+    g.dg6 = c->L.dg6;
+    g.T = c->d_T;
+    g.rho = c->d_rho64;
+    g.ne = c->d_ne64;
+    g.npert = c->d_npert64;
+    g.pop = c->d_pop64;
+    g.mass = c->d_mass64;
+    g.dab = c->d_dab;
+    g.eos = c->n_elem > 0 ? c->d_eos : nullptr;
+    g.kline = (double *)c->d_kline;
+    g.Gt = c->d_Gt64;
+    g.gacc = c->d_gacc;
+    return g;
+}
+
+cudaError_t launch_line_fwd_fp64(pz_ctx *c, cudaStream_t s) {
+    Fp64Args g = make_args64(c);
+    dim3 grid((unsigned)((c->nlam + 127) / 128), c->nd);
+    k_line_fwd_fp64<<<grid, 128, 0, s>>>(g);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_line_bwd_fp64(pz_ctx *c, cudaStream_t s) {
+    if (c->L.n == 0) return cudaSuccess;
+    Fp64Args g = make_args64(c);
+    dim3 grid((unsigned)((c->L.n + 127) / 128), c->nd);
+    k_line_bwd_fp64<<<grid, 128, 0, s>>>(g);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// corrections: Q_l = Qbase_l 10^dgf, g6_l = g6base_l 10^dg6, R_sd = Rbase_sd 10^dab
+// ---------------------------------------------------------------------------
+__global__ void k_apply_line_corr(int64_t n, const double *Qbase, const float *g6base, const float *dgf,
+                                  const float *dg6, float *Q, float *g6) {
+    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n) return;
+    Q[l] = (float)(Qbase[l] * exp10((double)dgf[l]));
+    g6[l] = (float)((double)g6base[l] * exp10((double)dg6[l]));
+}
+
+__global__ void k_apply_abund(int ns, int nd, const double *Rbase, const double *dab, const int32_t *eos,
+                              int use, float *R) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ns * nd) return;
+    int s = idx / nd;
+    double f = (use && eos[s] >= 0) ? exp10(dab[eos[s]]) : 1.0;
+    R[idx] = (float)(Rbase[idx] * f);
+}
+
+cudaError_t launch_apply_corrections(pz_ctx *c, cudaStream_t s) {
+    if (c->L.n > 0) {
+        k_apply_line_corr<<<(unsigned)((c->L.n + 255) / 256), 256, 0, s>>>(c->L.n, c->L.Qbase, c->L.g6base, c->L.dgf,
+                                                                          c->L.dg6, c->L.Q, c->L.g6);
+        c->launches++;
+    }
+    int n = c->ns * c->nd;
+    k_apply_abund<<<(n + 255) / 256, 256, 0, s>>>(c->ns, c->nd, c->d_Rbase, c->d_dab, c->d_eos, c->n_elem > 0,
+                                                  c->d_R);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// probe: the FP32 Voigt exactly as the mixed kernels evaluate it
+// (far region through the same pre-scaled polynomial with A = 1, a6 = 1)
+// ---------------------------------------------------------------------------
+__global__ void k_probe_voigt(const float *a, const float *v, int64_t n, float *H, float *dH) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float aa = a[k], x = fabsf(v[k]);
+    float a2 = aa * aa;
+    float r2 = fmaf(x, x, a2);
+    float h, dh;
+    if (r2 >= kFar2) {
+        float B1 = aa * kInvSqrtPiF;
+        float t = rcp_approx(r2);
+        float p = fmaf(t, 12.0f * a2 * a2 * B1, -15.0f * a2 * B1);
+        p = fmaf(t, p, fmaf(-2.0f, a2, 3.75f) * B1);
+        p = fmaf(t, p, 1.5f * B1);
+        p = fmaf(t, p, B1);
+        h = t * p;
+        float C1 = kInvSqrtPiF;
+        float q = fmaf(t, -120.0f * a2 * a2 * a2 * C1, 180.0f * a2 * a2 * C1);
+        q = fmaf(t, q, a2 * fmaf(12.0f, a2, -67.5f) * C1);
+        q = fmaf(t, q, fmaf(-12.0f, a2, 3.75f) * C1);
+        q = fmaf(t, q, fmaf(-2.0f, a2, 1.5f) * C1);
+        q = fmaf(t, q, C1);
+        dh = t * q;
+    } else {
+        voigt_general<true>(x, aa, h, dh);
+    }
+    H[k] = h;
+    if (dH) dH[k] = dh;
+}
+
+cudaError_t launch_probe_voigt(const float *a, const float *v, int64_t n, float *H, float *dH, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_probe_voigt<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, v, n, H, dH);
+    return cudaGetLastError();
+}
+
+}  // namespace pz

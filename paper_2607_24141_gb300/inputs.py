@@ -272,8 +272,9 @@ def config1(seed: int = 1, lam_lo: float = 1500.0, lam_hi: float = 1700.0,
     inst = None
     if n_pix:
         pix = apogee_pixels(8575)
-        if lam_lo != 1500.0 or lam_hi != 1700.0:   # scaled variant: pixels inside the grid
-            pix = pix[(pix > lam_lo * 1.0005) & (pix < lam_hi * 0.9995)][:n_pix]
+        if lam_lo != 1500.0 or lam_hi != 1700.0:   # scaled variant: pixels 100 grid points inside
+            margin = (1.0 + 1.0 / R_GRID) ** 100
+            pix = pix[(pix > lam_lo * margin) & (pix < lam_hi / margin)][:n_pix]
         inst = Instrument(12.3, 0.0, 22_500.0, pix)
     elem = (np.arange(n_species) % 20).astype(np.int32)
     return Problem(name, atmos, grid, lines, make_kappa_c(atmos, grid), inst, elem, 20)

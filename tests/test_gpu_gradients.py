@@ -1,0 +1,72 @@
+"""Parity of the hand-written CUDA reverse pass with the oracle's adjoint."""
+import numpy as np
+import pytest
+
+import paper_2607_24141_gb300 as pz
+from paper_2607_24141_gb300 import inputs as I
+from gpu_util import rel_metric, run_gradient
+from tiny import tiny_problem
+
+pytestmark = pytest.mark.gpu
+G_TOL = 1e-3
+
+
+def _check(prob, oracle, corr, instrument_noise=1.0 / 200):
+    rng = np.random.default_rng(7)
+    n_out = prob.instrument.pix_lambda_nm.size if prob.instrument is not None else prob.grid.n_lambda
+    f0 = oracle.forward(prob, corr)
+    y = f0["f"] + rng.normal(0, instrument_noise, n_out)
+    w = 200.0 ** 2
+    L, ggf, gg6, gab, _ = oracle.gradient(prob, y, np.full(n_out, w), corr, fwd=f0)
+    c32 = {k: v.astype(np.float32) for k, v in corr.items()}
+    out = {}
+    for prec in (pz.PZ_MIXED, pz.PZ_FP64):
+        got = run_gradient(prob, y.astype(np.float32), np.float32(w), prec, c32)
+        tol = G_TOL if prec == pz.PZ_MIXED else 1e-5
+        e1 = rel_metric(got["g_gf"], ggf).max()
+        e2 = rel_metric(got["g_g6"], gg6).max()
+        e3 = rel_metric(got["g_ab"][:prob.n_elem], gab).max()
+        assert e1 < tol and e2 < tol and e3 < tol, (prec, e1, e2, e3)
+        out[prec] = (e1, e2, e3)
+    return out
+
+
+def test_small_calibration_gradients(oracle):
+    prob = I.small_config1(n_lambda_span_nm=3.0, seed=13)
+    nl = prob.lines.n_lines
+    rng = np.random.default_rng(5)
+    corr = {"dlog_gf": np.zeros(nl), "dlog_gamma6": np.zeros(nl), "dabund": np.zeros(prob.n_elem)}
+    print(_check(prob, oracle, corr))
+    corr = {"dlog_gf": rng.normal(0, 0.1, nl), "dlog_gamma6": rng.normal(0, 0.2, nl),
+            "dabund": rng.normal(0, 0.1, prob.n_elem)}
+    print(_check(prob, oracle, corr))
+
+
+def test_identity_instrument_gradients(oracle):
+    prob = tiny_problem(n_lambda=900, n_depth=20, n_lines=60, W=350, seed=31)
+    prob.lines.log_gf[:] -= 4.0
+    rng = np.random.default_rng(6)
+    corr = {"dlog_gf": rng.normal(0, 0.1, 60), "dlog_gamma6": rng.normal(0, 0.2, 60),
+            "dabund": rng.normal(0, 0.1, prob.n_elem)}
+    print(_check(prob, oracle, corr))
+
+
+def test_autograd_function_matches_direct_call(oracle):
+    import torch
+    prob = tiny_problem(n_lambda=500, n_depth=12, n_lines=30, W=200, seed=9, instrument=True)
+    prob.lines.log_gf[:] -= 4.0
+    s = pz.Synthesizer(prob)
+    Fn = pz.SynthesisFunction
+    nl = prob.lines.n_lines
+    dgf = torch.zeros(nl, dtype=torch.float32, device="cuda", requires_grad=True)
+    dg6 = torch.zeros(nl, dtype=torch.float32, device="cuda", requires_grad=True)
+    dab = torch.zeros(prob.n_elem, dtype=torch.float32, device="cuda", requires_grad=True)
+    f = Fn.apply(s, dgf, dg6, dab)
+    y = torch.ones_like(f)
+    L = ((y - f) ** 2).sum() * 4e4
+    L.backward()
+    ref = oracle.gradient(prob, np.ones(f.numel()), np.full(f.numel(), 4e4),
+                          {"dlog_gf": np.zeros(nl), "dlog_gamma6": np.zeros(nl), "dabund": np.zeros(prob.n_elem)})
+    assert rel_metric(dgf.grad.cpu().numpy().astype(np.float64), ref[1]).max() < G_TOL
+    assert rel_metric(dg6.grad.cpu().numpy().astype(np.float64), ref[2]).max() < G_TOL
+    assert rel_metric(dab.grad.cpu().numpy().astype(np.float64), ref[3]).max() < G_TOL

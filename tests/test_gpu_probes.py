@@ -1,0 +1,52 @@
+"""Device Voigt and E_n, called through the C ABI probes (same device code as
+the kernels), against the FP64 oracle at the same (FP32-rounded) inputs."""
+import numpy as np
+import pytest
+
+import paper_2607_24141_gb300 as pz
+
+pytestmark = pytest.mark.gpu
+
+
+def voigt_gpu(a, v):
+    import torch
+    at = torch.tensor(a, dtype=torch.float32, device="cuda")
+    vt = torch.tensor(v, dtype=torch.float32, device="cuda")
+    H = torch.empty_like(at)
+    dH = torch.empty_like(at)
+    pz.pz_probe_voigt(at, vt, H, dH)
+    torch.cuda.synchronize()
+    return H.cpu().numpy().astype(np.float64), dH.cpu().numpy().astype(np.float64)
+
+
+def test_fp32_voigt_accuracy(oracle):
+    a = np.logspace(-4, 1.5, 90).astype(np.float32)
+    v = np.concatenate([np.linspace(0, 8, 321), np.linspace(8, 30, 177),
+                        np.logspace(np.log10(30), np.log10(2500), 80)]).astype(np.float32)
+    A, V = np.meshgrid(a, v, indexing="ij")
+    A, V = A.ravel(), V.ravel()
+    H, dH = voigt_gpu(A, V)
+    Hr, _, dHr = oracle.voigt(A.astype(np.float64), V.astype(np.float64))
+    x2 = V.astype(np.float64) ** 2
+    # the Gaussian core's condition number w.r.t. an FP32 input is ~2 v^2
+    bound = 2e-6 + 2 * x2 * 6e-8 * np.exp(-x2) / Hr
+    err = np.abs(H / Hr - 1)
+    assert np.all(err < bound), (float(err.max()), A[np.argmax(err / bound)], V[np.argmax(err / bound)])
+    # dH/da: relative to the local scale |dH/da| + H/max(a, 1)
+    scale = np.abs(dHr) + Hr / np.maximum(A, 1.0)
+    derr = np.abs(dH - dHr) / scale
+    assert derr.max() < 3e-5, (float(derr.max()), A[np.argmax(derr)], V[np.argmax(derr)])
+
+
+def test_fp64_expn(oracle):
+    import torch
+    x = np.concatenate([[0.0], np.logspace(-12, 0, 200), np.linspace(1, 3, 200), np.linspace(3, 745, 400)])
+    xt = torch.tensor(x, dtype=torch.float64, device="cuda")
+    out = torch.empty(3 * x.size, dtype=torch.float64, device="cuda")
+    pz.pz_probe_expn(xt, out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(3, -1)
+    for k, n in enumerate((2, 3, 4)):
+        ref = oracle.expn(n, x)
+        m = ref > 1e-290
+        assert np.max(np.abs(got[k][m] / ref[m] - 1)) < 5e-14, n
