@@ -185,13 +185,16 @@ int64_t pz_eval_count(const pz_ctx *ctx);
 /* Number of kernel launches issued by the most recent pz_* call on this context. */
 int32_t pz_last_launch_count(const pz_ctx *ctx);
 
-/* Kernel tiling of the mixed-precision line kernels: lambda points per tile,
- * depths per CTA and lines per shared-memory chunk.  Values <= 0 keep the
- * current setting.  Must be called between forwards (PZ_ESTATE otherwise is
- * not raised; the next pz_line_opacity uses the new tiling).
- * Errors: PZ_EINVAL for an unsupported combination. */
+/* Kernel tiling of the mixed-precision line kernels: lambda points per thread
+ * (2 or 4), depths per warp, warps per CTA (1-4), lines per shared-memory chunk
+ * (the backward uses half) and the minimum number of resident CTAs per SM the
+ * kernels are compiled for (a register budget).  Values <= 0 keep the current
+ * setting; the next launch uses the new tiling.  Supported (lambda, depth,
+ * CTAs) triples: (4,9,1-3) (4,6,1-4) (4,12,1-2) (2,9,1-4) (2,12,1-3) (2,6,4).
+ * Errors: PZ_EINVAL for an unsupported combination or a chunk that does not fit
+ * in shared memory. */
 pz_status pz_set_tiling(pz_ctx *ctx, int32_t lambda_per_thread, int32_t depth_per_warp,
-                        int32_t warps_per_cta, int32_t lines_per_chunk);
+                        int32_t warps_per_cta, int32_t lines_per_chunk, int32_t ctas_per_sm);
 
 /* ---- profiling ------------------------------------------------------------- */
 

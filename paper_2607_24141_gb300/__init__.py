@@ -69,7 +69,7 @@ _SIGS = {
     "pz_last_error": (C.c_char_p, []),
     "pz_eval_count": (C.c_int64, [_vp]),
     "pz_last_launch_count": (C.c_int32, [_vp]),
-    "pz_set_tiling": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "pz_set_tiling": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "pz_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "pz_kernel_times": (C.c_int, [_vp, _dp, C.POINTER(C.c_int64), C.c_int32]),
     "pz_probe_voigt": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
@@ -187,8 +187,8 @@ def pz_last_launch_count(ctx) -> int:
     return int(load().pz_last_launch_count(ctx))
 
 
-def pz_set_tiling(ctx, lambda_per_thread=0, depth_per_warp=0, warps_per_cta=0, lines_per_chunk=0):
-    _check(load().pz_set_tiling(ctx, lambda_per_thread, depth_per_warp, warps_per_cta, lines_per_chunk))
+def pz_set_tiling(ctx, lambda_per_thread=0, depth_per_warp=0, warps_per_cta=0, lines_per_chunk=0, ctas_per_sm=0):
+    _check(load().pz_set_tiling(ctx, lambda_per_thread, depth_per_warp, warps_per_cta, lines_per_chunk, ctas_per_sm))
 
 
 KERNEL_NAMES = ("line_fwd", "line_bwd", "flux", "rt_adjoint", "instrument", "inst_adjoint", "loss", "other")

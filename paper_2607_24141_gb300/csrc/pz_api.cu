@@ -124,28 +124,55 @@ static pz_status build_tiles(pz_ctx *c) {
         hi[t] = (int32_t)(std::upper_bound(c->h_il.begin(), c->h_il.end(), (int32_t)std::min<int64_t>(b, INT32_MAX)) -
                           c->h_il.begin());
     }
+    // near-core line ranges: x_l within 20 Doppler widths (the widest over species and
+    // depths) of the tile, plus a margin
+    double kmin = 1e300;
+    for (float v : c->h_invdv) kmin = std::min(kmin, kC * (double)v);
+    const double hw = 20.0 / (kmin * c->lnr) * 1.02 + 4.0;
+    std::vector<int32_t> nlo(nt), nhi(nt);
+    for (int t = 0; t < nt; ++t) {
+        double a = (double)t * T - hw, b = (double)t * T + T - 1 + hw;
+        a = std::max(a, (double)INT32_MIN / 2);
+        b = std::min(b, (double)INT32_MAX / 2);
+        nlo[t] = (int32_t)(std::lower_bound(c->h_il.begin(), c->h_il.end(), (int32_t)std::floor(a)) - c->h_il.begin());
+        nhi[t] = (int32_t)(std::upper_bound(c->h_il.begin(), c->h_il.end(), (int32_t)std::ceil(b)) - c->h_il.begin());
+    }
     dfree(c->d_tile_lo);
     dfree(c->d_tile_hi);
-    c->d_tile_lo = c->d_tile_hi = nullptr;
+    dfree(c->d_near_lo);
+    dfree(c->d_near_hi);
+    c->d_tile_lo = c->d_tile_hi = c->d_near_lo = c->d_near_hi = nullptr;
     PZ_TRY(upload(&c->d_tile_lo, lo, "tile ranges"));
     PZ_TRY(upload(&c->d_tile_hi, hi, "tile ranges"));
+    PZ_TRY(upload(&c->d_near_lo, nlo, "tile ranges"));
+    PZ_TRY(upload(&c->d_near_hi, nhi, "tile ranges"));
     c->ntiles = nt;
     c->tileT = T;
     return PZ_OK;
 }
 
-// fast-path threshold per species: |x_l - i| >= thr guarantees |v| >= 20 at every depth
-static std::vector<float> fast_thresholds(pz_ctx *c, const std::vector<float> &invdv) {
-    std::vector<float> thr(c->ns);
-    double shrink = 1.0 - 0.5 * (c->W + 1024.0) * c->lnr;  // |expm1(y)| >= |y| (1 - |y|/2)
+// Fast-path threshold per (species, depth slab of DS layers): a line whose distance
+// from every point of the tile is >= thr (grid units) has |v| >= 20 at every depth of
+// the slab, because |v| = |expm1(Delta ln r)| c/dv_D >= |Delta| ln r (1 - |Delta| ln r / 2) c/dv_D.
+// Slabs past the last layer (grid padding) get 0.
+static pz_status build_thresholds(pz_ctx *c) {
+    const int DS = c->tiling.DS, DC = c->tiling.depth_per_cta();
+    const int nslab = ((c->nd + DC - 1) / DC) * c->tiling.GW;
+    double shrink = 1.0 - 0.5 * (c->W + 1024.0) * c->lnr;
     if (shrink < 0.5) shrink = 0.5;
-    for (int s = 0; s < c->ns; ++s) {
-        double mn = 1e300;
-        for (int d = 0; d < c->nd; ++d) mn = std::min(mn, (double)invdv[(size_t)s * c->nd + d]);
-        double kmin = kC * mn;
-        thr[s] = (float)(20.0 / (kmin * c->lnr * shrink) * (1.0 + 1e-4) + 1e-3);
-    }
-    return thr;
+    std::vector<float> thr((size_t)c->ns * nslab, 0.0f);
+    for (int s = 0; s < c->ns; ++s)
+        for (int b = 0; b < nslab; ++b) {
+            double mn = 1e300;
+            for (int d = b * DS; d < std::min(c->nd, (b + 1) * DS); ++d)
+                mn = std::min(mn, (double)c->h_invdv[(size_t)s * c->nd + d]);
+            if (mn < 1e300) thr[(size_t)s * nslab + b] = (float)(20.0 / (kC * mn * c->lnr * shrink) * (1.0 + 1e-4) + 1e-3);
+        }
+    dfree(c->d_thr);
+    c->d_thr = nullptr;
+    PZ_TRY(upload(&c->d_thr, thr, "thresholds"));
+    c->nslab = nslab;
+    return PZ_OK;
 }
 
 static void destroy_ctx(pz_ctx *c) {
@@ -155,7 +182,7 @@ static void destroy_ctx(pz_ctx *c) {
                     c->d_kc, c->d_dab, c->d_eos, c->L.orig, c->L.ilf, c->L.il32, c->L.frac, c->L.sp, c->L.E,
                     c->L.lamcm, c->L.grad, c->L.g4, c->L.g6base, c->L.g6, c->L.Q, c->L.Qbase, c->L.x64,
                     c->L.lg_gf, c->L.lg_rad, c->L.lg_4, c->L.lg_6, c->L.dgf, c->L.dg6, c->d_tile_lo, c->d_tile_hi,
-                    c->d_kline, c->d_F, c->d_Fc, c->d_g, c->d_gc, c->d_tap0, c->d_ntap, c->d_tapw, c->d_dFbar,
+                    c->d_kline, c->d_knear, c->d_near_lo, c->d_near_hi, c->d_F, c->d_Fc, c->d_g, c->d_gc, c->d_tap0, c->d_ntap, c->d_tapw, c->d_dFbar,
                     c->d_Gt, c->d_Gt64, c->d_gacc, c->d_gab};
     for (void *p : ptrs) dfree(p);
     for (auto &m : c->marks) {
@@ -309,7 +336,7 @@ static pz_status create_impl(const pz_atmos *at, const pz_linelist *ll, pz_preci
             Rb[id] = (1.0 / dv) * at->pop[id] / at->rho[d];
             Rf[id] = (float)Rb[id];
         }
-    std::vector<float> thr = fast_thresholds(c, invdv);
+    c->h_invdv = invdv;
     std::vector<double> dab(1, 0.0);
     std::vector<int32_t> eos(ns, -1);
     if (upload(&c->d_m, c->h_m, "depth") || upload(&c->d_T, c->h_T, "depth") || upload(&c->d_beta_hi, bh, "depth") ||
@@ -317,7 +344,7 @@ static pz_status create_impl(const pz_atmos *at, const pz_linelist *ll, pz_preci
         upload(&c->d_c2T, c2T, "depth") || upload(&c->d_ne64, ne64, "depth") || upload(&c->d_npert64, np64, "depth") ||
         upload(&c->d_rho64, rho64, "depth") || upload(&c->d_invdv, invdv, "species") || upload(&c->d_R, Rf, "species") ||
         upload(&c->d_Rbase, Rb, "species") || upload(&c->d_pop64, pop64, "species") ||
-        upload(&c->d_mass64, mass64, "species") || upload(&c->d_thr, thr, "species") || upload(&c->d_dab, dab, "abund") ||
+        upload(&c->d_mass64, mass64, "species") || build_thresholds(c) || upload(&c->d_dab, dab, "abund") ||
         upload(&c->d_eos, eos, "abund"))
         return bail(PZ_ENOMEM);
 
@@ -332,6 +359,7 @@ static pz_status create_impl(const pz_atmos *at, const pz_linelist *ll, pz_preci
     // ---- resident buffers ----
     size_t ksz = (prec == PZ_MIXED) ? sizeof(float) : sizeof(double);
     if (cuda_check(cudaMalloc(&c->d_kline, ksz * nd * c->ld), "kappa_line buffer") ||
+        (prec == PZ_MIXED && dalloc(&c->d_knear, (size_t)nd * c->ld, "kappa_line buffer")) ||
         dalloc(&c->d_F, nlam, "flux") || dalloc(&c->d_Fc, nlam, "flux"))
         return bail(PZ_ENOMEM);
     if (build_tiles(c) != PZ_OK) return bail(PZ_ENOMEM);
@@ -390,21 +418,29 @@ int64_t pz_eval_count(const pz_ctx *ctx) { return ctx ? ctx->n_evals : 0; }
 
 int32_t pz_last_launch_count(const pz_ctx *ctx) { return ctx ? ctx->launches : 0; }
 
-pz_status pz_set_tiling(pz_ctx *c, int32_t J, int32_t DS, int32_t GW, int32_t LC) {
+pz_status pz_set_tiling(pz_ctx *c, int32_t J, int32_t DS, int32_t GW, int32_t LC, int32_t MINB) {
     if (!c) return fail(PZ_EINVAL, "pz_set_tiling: ctx is NULL");
     Tiling t = c->tiling;
     if (J > 0) t.J = J;
     if (DS > 0) t.DS = DS;
     if (GW > 0) t.GW = GW;
     if (LC > 0) t.LC = LC;
-    if (!tiling_supported(t.J, t.DS)) return fail(PZ_EINVAL, "pz_set_tiling: unsupported (J, DS) pair");
+    if (MINB > 0) t.minb = MINB;
+    if (!tiling_supported(t.J, t.DS, t.minb))
+        return fail(PZ_EINVAL, "pz_set_tiling: unsupported (lambda_per_thread, depth_per_warp, ctas_per_sm)");
     if (t.GW < 1 || t.GW > 4) return fail(PZ_EINVAL, "pz_set_tiling: warps_per_cta must be in [1, 4]");
     if (t.LC < 1 || t.LC > 512) return fail(PZ_EINVAL, "pz_set_tiling: lines_per_chunk must be in [1, 512]");
-    size_t smem_bwd = (size_t)t.LC * t.DS * t.GW * 64 + t.LC * 16 + (size_t)t.LC * t.GW * 8;
-    if (smem_bwd > 200 * 1024) return fail(PZ_EINVAL, "pz_set_tiling: shared-memory chunk too large");
+    if (LC > 0) t.LCB = std::max(1, t.LC / 2);
+    size_t gen = (size_t)t.DS * 32 * t.GW * 16;
+    size_t smem_fwd = (size_t)t.LC * t.DS * t.GW * 32 + t.LC * 16 + gen;
+    size_t smem_bwd = (size_t)t.LCB * t.DS * t.GW * 64 + t.LCB * 16 + (size_t)t.LCB * t.GW * 8;
+    if (smem_fwd > 200 * 1024 || smem_bwd > 200 * 1024)
+        return fail(PZ_EINVAL, "pz_set_tiling: shared-memory chunk too large");
     bool retile = t.J != c->tiling.J;
+    bool reslab = t.DS != c->tiling.DS || t.GW != c->tiling.GW;
     c->tiling = t;
     if (retile) PZ_TRY(build_tiles(c));
+    if (reslab) PZ_TRY(build_thresholds(c));
     return PZ_OK;
 }
 

@@ -46,7 +46,9 @@ struct Tiling {
     int J = 4;       // lambda points per thread (contiguous)
     int DS = 9;      // depths per warp
     int GW = 4;      // warps per CTA (each a depth slab)
-    int LC = 32;     // lines per shared-memory chunk
+    int LC = 32;     // lines per shared-memory chunk (forward)
+    int LCB = 16;    // lines per shared-memory chunk (backward)
+    int minb = 1;    // minimum resident CTAs per SM the kernels are compiled for
     int lambda_per_tile() const { return 32 * J; }
     int depth_per_cta() const { return DS * GW; }
 };
@@ -101,7 +103,9 @@ struct pz_ctx {
     double *d_Rbase = nullptr;      // [ns][nd] (1/dv_D)(pop/rho), FP64
     float *d_invdv = nullptr;       // [ns][nd] 1/dv_D (s/cm)
     double *d_pop64 = nullptr, *d_mass64 = nullptr;
-    float *d_thr = nullptr;         // [ns] fast-path distance threshold (grid units)
+    float *d_thr = nullptr;         // [ns][nslab] fast-path distance threshold (grid units)
+    int nslab = 0;                  // depth slabs of DS layers covered by the launch grid
+    std::vector<float> h_invdv;     // [ns][nd] host copy of 1/dv_D (thresholds)
     double *d_kc = nullptr;         // [nd][ld] continuum opacity FP64
     double *d_dab = nullptr;        // [n_elem_max] current abundance offsets
     int32_t *d_eos = nullptr;       // [ns] element of species (or -1)
@@ -109,6 +113,8 @@ struct pz_ctx {
 
     pz::LineTable L;
     int32_t *d_tile_lo = nullptr, *d_tile_hi = nullptr;
+    int32_t *d_near_lo = nullptr, *d_near_hi = nullptr;   // lines whose near zone can reach a tile
+    float *d_knear = nullptr;       // [nd][ld] near-core sums of the forward
     int ntiles = 0, tileT = 0;
 
     // resident buffers
@@ -181,6 +187,6 @@ cudaError_t launch_inst_adjoint(pz_ctx *c, const float *dLdf, cudaStream_t s);
 cudaError_t launch_rt_adjoint(pz_ctx *c, cudaStream_t s);
 cudaError_t launch_grad_finalize(pz_ctx *c, float *g_gf, float *g_g6, float *g_ab, cudaStream_t s);
 cudaError_t launch_probe_expn(const double *x, int64_t n, double *out, cudaStream_t s);
-bool tiling_supported(int J, int DS);
+bool tiling_supported(int J, int DS, int minb);
 
 }  // namespace pz

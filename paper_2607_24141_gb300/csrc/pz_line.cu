@@ -128,9 +128,12 @@ struct LineArgs {
     const int32_t *tile_lo, *tile_hi;
     const float *ilf, *frac, *E, *lamcm, *grad, *g4, *g6, *Q;
     const int32_t *sp;
-    const float *R, *invdv, *thr;                   // [ns][nd], [ns][nd], [ns]
+    const float *R, *invdv, *thr;                   // [ns][nd], [ns][nd], [ns][nslab]
+    int nslab;
     const float *beta_hi, *beta_lo, *ne, *npert, *c2T;
     float *kline;                                   // forward output [nd][ld]
+    float *knear;                                   // near-core sums [nd][ld]
+    const int32_t *near_lo, *near_hi;               // per tile: lines whose near zone can reach it
     const float *Gt;                                // backward input [nd][ld]
     double *gacc;                                   // backward output [2][nl]
     int64_t nl;
@@ -191,36 +194,72 @@ __device__ __forceinline__ float offset_u(float delta, float lnr) {
 }
 
 struct alignas(16) LineInfo {
-    float ilf, frac, thr, pad;
+    float ilf, frac;
+    int sp, pad;
 };
 
-template <int J, int DS>
-__global__ void __launch_bounds__(128, 1) k_line_fwd(LineArgs g, int GW, int LC) {
+// Far-wing term A H for one evaluation from the pre-scaled coefficients
+// p0 = (k, a^2, B1, B2), p1 = (B3, B4, B5, A): t (B1 + t (B2 + t (B3 + t (B4 + t B5)))),
+// added to acc (7 FP32-pipe instructions + 1 MUFU with the caller's x = u k).
+__device__ __forceinline__ float far_acc(float x, const float4 &p0, const float4 &p1, float acc) {
+    float t = rcp_approx(fmaf(x, x, p0.y));
+    float h = fmaf(t, p1.z, p1.y);
+    h = fmaf(t, h, p1.x);
+    h = fmaf(t, h, p0.w);
+    h = fmaf(t, h, p0.z);
+    return fmaf(t, h, acc);
+}
+
+// Per-warp decision: the line is inside its window over the whole tile and every
+// (lambda, depth) cell of this warp's depth slab is in the far wing (|v| >= 20).
+__device__ __forceinline__ bool fast_line(const LineArgs &g, const LineInfo &info, float t0f, float tendf, int slab) {
+    const float dlo = info.ilf - t0f + info.frac;      // x_l - t0
+    const float dhi = info.ilf - tendf + info.frac;    // x_l - (t0 + T - 1)
+    const float dmin = fmaxf(0.0f, fmaxf(-dlo, dhi));
+    const bool full = (info.ilf - (float)g.W <= t0f) && (info.ilf + (float)g.W >= tendf);
+    return full && dmin >= __ldg(g.thr + info.sp * g.nslab + slab);
+}
+
+// Compensation-term slot of cell (dd, j) of thread tid (the J points of a thread are
+// contiguous: one vector access per depth).
+__device__ __forceinline__ int lo_slot(int dd, int tid, int nthr) { return (dd * nthr + tid) << 2; }
+
+// Far-wing kernel (forward).  Every cell with |v|^2 + a^2 >= 400 inside its window is
+// evaluated here with the far polynomial; the near-core cells are summed by
+// k_line_near_fwd into knear, which this kernel adds before applying stim.
+template <int J, int DS, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int LC) {
+    static_assert(J == 2 || J == 4, "J must be 2 or 4");
     extern __shared__ float4 smem4[];
     const int T = 32 * J;
     const int DC = GW * DS;
-    float4 *s_par = smem4;                                  // [LC][DC][2]
+    const int nthr = blockDim.x;
+    float4 *s_par = smem4;                                              // [LC][DC][2]
     LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * DC * 2);
+    float *s_lo = reinterpret_cast<float *>(s_line + LC);               // [DS][nthr][4] compensation terms
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
     const int d0 = blockIdx.y * DC;
+    const int slab = (d0 + warp * DS) / DS;
     const int t0 = tile * T;
     const float t0f = (float)t0, tendf = (float)(t0 + T - 1);
     const int lam_thr = t0 + lane * J;
     const float lamf = (float)lam_thr;
     const int lo = g.tile_lo[tile], hi = g.tile_hi[tile];
 
-    float acc[DS][J], shi[DS][J], slo[DS][J];
+    float acc[DS][J], shi[DS][J];
 #pragma unroll
-    for (int dd = 0; dd < DS; ++dd)
+    for (int dd = 0; dd < DS; ++dd) {
 #pragma unroll
-        for (int j = 0; j < J; ++j) acc[dd][j] = shi[dd][j] = slo[dd][j] = 0.0f;
+        for (int j = 0; j < J; ++j) acc[dd][j] = shi[dd][j] = 0.0f;
+        *reinterpret_cast<float4 *>(s_lo + lo_slot(dd, tid, nthr)) = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
 
     for (int c0 = lo; c0 < hi; c0 += LC) {
         const int nl = min(LC, hi - c0);
         __syncthreads();
-        for (int idx = tid; idx < nl * DC; idx += blockDim.x) {
+        for (int idx = tid; idx < nl * DC; idx += nthr) {
             int li = idx / DC, dd = idx - li * DC;
             float p[8];
             line_params<8>(g, c0 + li, d0 + dd, p);
@@ -228,77 +267,58 @@ __global__ void __launch_bounds__(128, 1) k_line_fwd(LineArgs g, int GW, int LC)
             dst[0] = make_float4(p[0], p[1], p[2], p[3]);
             dst[1] = make_float4(p[4], p[5], p[6], p[7]);
         }
-        for (int li = tid; li < nl; li += blockDim.x) {
+        for (int li = tid; li < nl; li += nthr) {
             int64_t l = c0 + li;
             LineInfo info;
             info.ilf = g.ilf[l];
             info.frac = g.frac[l];
-            info.thr = __ldg(g.thr + g.sp[l]);
-            info.pad = 0.0f;
+            info.sp = g.sp[l];
+            info.pad = 0;
             s_line[li] = info;
         }
         __syncthreads();
 
         for (int li = 0; li < nl; ++li) {
             const LineInfo info = s_line[li];
-            const float dlo = info.ilf - t0f + info.frac;     // x_l - t0
-            const float dhi = info.ilf - tendf + info.frac;   // x_l - (t0 + T - 1)
-            const float dmin = fmaxf(0.0f, fmaxf(-dlo, dhi));
-            const bool full = (info.ilf - (float)g.W <= t0f) && (info.ilf + (float)g.W >= tendf);
-            const float delta0 = (info.ilf - lamf) + info.frac;
+            const float4 *par = s_par + ((size_t)li * DC + warp * DS) * 2;
             float u[J];
 #pragma unroll
-            for (int j = 0; j < J; ++j) u[j] = offset_u(delta0 - (float)j, g.lnr);
-            const float4 *par = s_par + ((size_t)li * DC + warp * DS) * 2;
-            if (full && dmin >= info.thr) {
+            for (int j = 0; j < J; ++j) u[j] = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
+            if (fast_line(g, info, t0f, tendf, slab)) {
 #pragma unroll
                 for (int dd = 0; dd < DS; ++dd) {
                     const float4 p0 = par[2 * dd], p1 = par[2 * dd + 1];
 #pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        float x = u[j] * p0.x;
-                        float t = rcp_approx(fmaf(x, x, p0.y));
-                        float h = fmaf(t, p1.z, p1.y);
-                        h = fmaf(t, h, p1.x);
-                        h = fmaf(t, h, p0.w);
-                        h = fmaf(t, h, p0.z);
-                        acc[dd][j] = fmaf(t, h, acc[dd][j]);
-                    }
+                    for (int j = 0; j < J; ++j) acc[dd][j] = far_acc(u[j] * p0.x, p0, p1, acc[dd][j]);
                 }
             } else {
+                // line near the tile or partly outside its window: far cells inside the window only
                 const int il = (int)info.ilf;
+                bool inwin[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const int di = lam_thr + j - il;
+                    inwin[j] = di >= -g.W && di <= g.W;
+                }
 #pragma unroll
                 for (int dd = 0; dd < DS; ++dd) {
                     const float4 p0 = par[2 * dd], p1 = par[2 * dd + 1];
-                    const float a = sqrtf(p0.y);
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        int di = lam_thr + j - il;
-                        if (di >= -g.W && di <= g.W) {
-                            float x = fabsf(u[j] * p0.x);
-                            float r2 = fmaf(x, x, p0.y);
-                            float term;
-                            if (r2 >= kFar2) {
-                                float t = rcp_approx(r2);
-                                float h = fmaf(t, p1.z, p1.y);
-                                h = fmaf(t, h, p1.x);
-                                h = fmaf(t, h, p0.w);
-                                h = fmaf(t, h, p0.z);
-                                term = t * h;
-                            } else {
-                                float H, dH;
-                                voigt_general<false>(x, a, H, dH);
-                                term = p1.w * H;
-                            }
-                            acc[dd][j] += term;
-                        }
+                        const float x = u[j] * p0.x;
+                        const float r = far_acc(x, p0, p1, acc[dd][j]);
+                        acc[dd][j] = (inwin[j] && fmaf(x, x, p0.y) >= kFar2) ? r : acc[dd][j];
                     }
                 }
             }
         }
-        // fold the chunk partials into the compensated sums (2Sum)
+        // fold the chunk partials into the compensated sums (2Sum; the rounding
+        // terms accumulate in this thread's shared-memory slots)
 #pragma unroll
-        for (int dd = 0; dd < DS; ++dd)
+        for (int dd = 0; dd < DS; ++dd) {
+            float4 *lslot = reinterpret_cast<float4 *>(s_lo + lo_slot(dd, tid, nthr));
+            float4 lsum = *lslot;
+            float lj[4] = {lsum.x, lsum.y, lsum.z, lsum.w};
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 float p = acc[dd][j], h = shi[dd][j];
@@ -306,41 +326,50 @@ __global__ void __launch_bounds__(128, 1) k_line_fwd(LineArgs g, int GW, int LC)
                 float bp = s - h;
                 float e = (h - (s - bp)) + (p - bp);
                 shi[dd][j] = s;
-                slo[dd][j] += e;
+                lj[j] += e;
                 acc[dd][j] = 0.0f;
             }
+            *lslot = make_float4(lj[0], lj[1], lj[2], lj[3]);
+        }
     }
 
-    // epilogue: stimulated-emission factor at the sample frequency, store
+    // epilogue: near-core sums, stimulated-emission factor at the sample frequency, vector store
 #pragma unroll
     for (int dd = 0; dd < DS; ++dd) {
         int d = d0 + warp * DS + dd;
         if (d >= g.nd) continue;
         float c2T = __ldg(g.c2T + d);
+        const float4 lsum = *reinterpret_cast<const float4 *>(s_lo + lo_slot(dd, tid, nthr));
+        const float lj[4] = {lsum.x, lsum.y, lsum.z, lsum.w};
+        const float *nrow = g.knear + (int64_t)d * g.ld + lam_thr;
         float v[J];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
             float lam = g.lam0cm * expf((float)(lam_thr + j) * g.lnr);
             float stim = -expm1f(-c2T / lam);
-            v[j] = stim * (shi[dd][j] + slo[dd][j]);
+            float hi2 = shi[dd][j], nj = nrow[j];
+            float s = hi2 + nj;                    // 2Sum of the near-core sum into the total
+            float bp = s - hi2;
+            float e = (hi2 - (s - bp)) + (nj - bp);
+            v[j] = stim * (s + (lj[j] + e));
         }
         float *row = g.kline + (int64_t)d * g.ld + lam_thr;
-        if (J == 4) {
+        if (J == 4)
             *reinterpret_cast<float4 *>(row) = make_float4(v[0], v[1 % J], v[2 % J], v[3 % J]);
-        } else if (J == 2) {
+        else
             *reinterpret_cast<float2 *>(row) = make_float2(v[0], v[1 % J]);
-        } else {
-#pragma unroll
-            for (int j = 0; j < J; ++j) row[j] = v[j];
-        }
     }
 }
 
-template <int J, int DS>
-__global__ void __launch_bounds__(128, 1) k_line_bwd(LineArgs g, int GW, int LC) {
+// Far-wing kernel (backward): the per-line sums over the tile's far cells of
+// G stim A H and G stim A a6 dH/da, reduced over the CTA and added to gacc.
+template <int J, int DS, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int LC) {
+    static_assert(J == 2 || J == 4, "J must be 2 or 4");
     extern __shared__ float4 smem4[];
     const int T = 32 * J;
     const int DC = GW * DS;
+    const int nthr = blockDim.x;
     float4 *s_par = smem4;                                              // [LC][DC][4]
     LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * DC * 4);
     float2 *s_red = reinterpret_cast<float2 *>(s_line + LC);            // [LC][GW]
@@ -348,13 +377,14 @@ __global__ void __launch_bounds__(128, 1) k_line_bwd(LineArgs g, int GW, int LC)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int tile = blockIdx.x;
     const int d0 = blockIdx.y * DC;
+    const int slab = (d0 + warp * DS) / DS;
     const int t0 = tile * T;
     const float t0f = (float)t0, tendf = (float)(t0 + T - 1);
     const int lam_thr = t0 + lane * J;
     const float lamf = (float)lam_thr;
     const int lo = g.tile_lo[tile], hi = g.tile_hi[tile];
 
-    // G * stim for the thread's (depth, lambda) cells; zero outside the grid
+    // G * stim of the thread's cells; zero outside the grid
     float gv[DS][J];
 #pragma unroll
     for (int dd = 0; dd < DS; ++dd) {
@@ -367,7 +397,7 @@ __global__ void __launch_bounds__(128, 1) k_line_bwd(LineArgs g, int GW, int LC)
     for (int c0 = lo; c0 < hi; c0 += LC) {
         const int nl = min(LC, hi - c0);
         __syncthreads();
-        for (int idx = tid; idx < nl * DC; idx += blockDim.x) {
+        for (int idx = tid; idx < nl * DC; idx += nthr) {
             int li = idx / DC, dd = idx - li * DC;
             float p[16];
             line_params<16>(g, c0 + li, d0 + dd, p);
@@ -377,88 +407,54 @@ __global__ void __launch_bounds__(128, 1) k_line_bwd(LineArgs g, int GW, int LC)
             dst[2] = make_float4(p[8], p[9], p[10], p[11]);
             dst[3] = make_float4(p[12], p[13], p[14], p[15]);
         }
-        for (int li = tid; li < nl; li += blockDim.x) {
+        for (int li = tid; li < nl; li += nthr) {
             int64_t l = c0 + li;
             LineInfo info;
             info.ilf = g.ilf[l];
             info.frac = g.frac[l];
-            info.thr = __ldg(g.thr + g.sp[l]);
-            info.pad = 0.0f;
+            info.sp = g.sp[l];
+            info.pad = 0;
             s_line[li] = info;
         }
         __syncthreads();
 
         for (int li = 0; li < nl; ++li) {
             const LineInfo info = s_line[li];
-            const float dlo = info.ilf - t0f + info.frac;
-            const float dhi = info.ilf - tendf + info.frac;
-            const float dmin = fmaxf(0.0f, fmaxf(-dlo, dhi));
-            const bool full = (info.ilf - (float)g.W <= t0f) && (info.ilf + (float)g.W >= tendf);
-            const float delta0 = (info.ilf - lamf) + info.frac;
+            const float4 *par = s_par + ((size_t)li * DC + warp * DS) * 4;
             float u[J];
 #pragma unroll
-            for (int j = 0; j < J; ++j) u[j] = offset_u(delta0 - (float)j, g.lnr);
-            const float4 *par = s_par + ((size_t)li * DC + warp * DS) * 4;
+            for (int j = 0; j < J; ++j) u[j] = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
             float s1 = 0.0f, s2 = 0.0f;
-            if (full && dmin >= info.thr) {
+            const bool fast = fast_line(g, info, t0f, tendf, slab);
+            bool inwin[J];
+            const int il = (int)info.ilf;
 #pragma unroll
-                for (int dd = 0; dd < DS; ++dd) {
-                    const float4 p0 = par[4 * dd], p1 = par[4 * dd + 1];
-                    const float4 p2 = par[4 * dd + 2], p3 = par[4 * dd + 3];
+            for (int j = 0; j < J; ++j) {
+                const int di = lam_thr + j - il;
+                inwin[j] = fast || (di >= -g.W && di <= g.W);
+            }
 #pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        float x = u[j] * p0.x;
-                        float t = rcp_approx(fmaf(x, x, p0.y));
-                        float h = fmaf(t, p1.z, p1.y);
-                        h = fmaf(t, h, p1.x);
-                        h = fmaf(t, h, p0.w);
-                        h = fmaf(t, h, p0.z);
-                        float q = fmaf(t, p3.y, p3.x);
-                        q = fmaf(t, q, p2.w);
-                        q = fmaf(t, q, p2.z);
-                        q = fmaf(t, q, p2.y);
-                        q = fmaf(t, q, p2.x);
-                        float gt = gv[dd][j] * t;
-                        s1 = fmaf(gt, h, s1);
-                        s2 = fmaf(gt, q, s2);
-                    }
-                }
-            } else {
-                const int il = (int)info.ilf;
+            for (int dd = 0; dd < DS; ++dd) {
+                const float4 p0 = par[4 * dd], p1 = par[4 * dd + 1];
+                const float4 p2 = par[4 * dd + 2], p3 = par[4 * dd + 3];
 #pragma unroll
-                for (int dd = 0; dd < DS; ++dd) {
-                    const float4 p0 = par[4 * dd], p1 = par[4 * dd + 1];
-                    const float4 p2 = par[4 * dd + 2], p3 = par[4 * dd + 3];
-#pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        int di = lam_thr + j - il;
-                        if (di >= -g.W && di <= g.W) {
-                            float x = fabsf(u[j] * p0.x);
-                            float r2 = fmaf(x, x, p0.y);
-                            float th, tq;
-                            if (r2 >= kFar2) {
-                                float t = rcp_approx(r2);
-                                float h = fmaf(t, p1.z, p1.y);
-                                h = fmaf(t, h, p1.x);
-                                h = fmaf(t, h, p0.w);
-                                h = fmaf(t, h, p0.z);
-                                float q = fmaf(t, p3.y, p3.x);
-                                q = fmaf(t, q, p2.w);
-                                q = fmaf(t, q, p2.z);
-                                q = fmaf(t, q, p2.y);
-                                q = fmaf(t, q, p2.x);
-                                th = t * h;
-                                tq = t * q;
-                            } else {
-                                float H, dH;
-                                voigt_general<true>(x, p3.w, H, dH);
-                                th = p1.w * H;
-                                tq = p3.z * dH;
-                            }
-                            s1 = fmaf(gv[dd][j], th, s1);
-                            s2 = fmaf(gv[dd][j], tq, s2);
-                        }
-                    }
+                for (int j = 0; j < J; ++j) {
+                    const float x = u[j] * p0.x;
+                    const float r2 = fmaf(x, x, p0.y);
+                    const float t = rcp_approx(r2);
+                    float h = fmaf(t, p1.z, p1.y);
+                    h = fmaf(t, h, p1.x);
+                    h = fmaf(t, h, p0.w);
+                    h = fmaf(t, h, p0.z);
+                    float q = fmaf(t, p3.y, p3.x);
+                    q = fmaf(t, q, p2.w);
+                    q = fmaf(t, q, p2.z);
+                    q = fmaf(t, q, p2.y);
+                    q = fmaf(t, q, p2.x);
+                    const bool use = fast || (inwin[j] && r2 >= kFar2);
+                    const float gt = use ? gv[dd][j] * t : 0.0f;
+                    s1 = fmaf(gt, h, s1);
+                    s2 = fmaf(gt, q, s2);
                 }
             }
 #pragma unroll
@@ -469,7 +465,7 @@ __global__ void __launch_bounds__(128, 1) k_line_bwd(LineArgs g, int GW, int LC)
             if (lane == 0) s_red[li * GW + warp] = make_float2(s1, s2);
         }
         __syncthreads();
-        for (int li = tid; li < nl; li += blockDim.x) {
+        for (int li = tid; li < nl; li += nthr) {
             double a1 = 0.0, a2 = 0.0;
             for (int w = 0; w < GW; ++w) {
                 float2 r = s_red[li * GW + w];
@@ -478,6 +474,237 @@ __global__ void __launch_bounds__(128, 1) k_line_bwd(LineArgs g, int GW, int LC)
             }
             atomicAdd(g.gacc + c0 + li, a1);
             atomicAdd(g.gacc + g.nl + c0 + li, a2);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Near-core kernels: the cells with |v|^2 + a^2 < 400 (mid wing and core).  A CTA owns
+// the same wavelength tile as the far kernels and every depth; its warps take
+// (line, depth) items of the lines whose near zone can reach the tile, clip the
+// item's near span analytically, and let the lanes sweep the span 32 points at a
+// time.  Each cell is classified with the far kernels' own arithmetic (same
+// prefactors, same offset and the same |v|^2 + a^2 test), so every cell is counted
+// exactly once across the two kernels.
+// ---------------------------------------------------------------------------
+
+// Near span of an item clipped to the tile and the window; returns false if empty.
+__device__ __forceinline__ bool near_span(const LineArgs &g, float ilf, float frac, float k, float a2, int t0, int T,
+                                          int &lo, int &hi) {
+    const float r2 = kFar2 - a2;
+    if (!(k > 0.0f) || !(r2 > 0.0f)) return false;
+    const float xl = ilf + frac;
+    const int il = (int)ilf;
+    const float span = sqrtf(r2) / (k * g.lnr) * 1.01f + 1.0f;
+    lo = max(max(t0, (int)floorf(xl - span)), il - g.W);
+    hi = min(min(t0 + T - 1, (int)ceilf(xl + span)), il + g.W);
+    return lo <= hi;
+}
+
+// One near-core item (a line at one depth) after its lane-parallel set-up.
+struct alignas(16) NearItem {
+    float ilf, frac, k, a2;      // centre, Doppler factor c/dv_D, a^2
+    float a, A, Aa6;             // damping, strength, strength x vdW damping
+    int lo, hi, dl, lb, pad;     // clipped span, local depth, local line (batch) index
+};
+
+constexpr int kNearBatch = 512;      // lines per shared-memory batch of the backward sums
+constexpr int kNearDepthsFwd = 8;    // depths per CTA of the near-core forward
+constexpr int kNearDepthsBwd = 24;   // depths per CTA of the near-core backward
+constexpr int kCoreQueue = 512;      // core cells queued per warp before a dense pass
+
+// Near-core sweep shared by the forward (D = false) and the backward (D = true).
+// Each warp takes rounds of 32 (line, depth) items: lanes set up one item each
+// (coarse span from c/dv_D alone, then the exact prefactors and span), the survivors
+// are kept in shared memory, then the warp sweeps each item's span 32 points at a time.
+// Mid-wing cells (36 <= |z|^2 < 400) are evaluated in place; core cells (|z|^2 < 36)
+// are queued (in item order) and evaluated densely.
+//   forward:  cell(item, i, H, dH) adds the cell's term where it belongs;
+//   backward: val(item, i, H, dH) returns the cell's (G A H, G A a6 dH) pair and
+//             done(lb, sum) receives the per-item (or per-queue-segment) sums.
+template <int T, bool D, class Cell, class Val, class Done>
+__device__ __forceinline__ void near_sweep(const LineArgs &g, int t0, int64_t nlo, int64_t nitems, int ndg, int dbase,
+                                           NearItem *s_items, int *s_queue, Cell &&cell, Val &&val, Done &&done) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    NearItem *mine = s_items + warp * 32;
+    int *queue = s_queue + warp * kCoreQueue;
+    int nq = 0;
+    auto flush_core = [&]() {
+        __syncwarp();
+        for (int e0 = 0; e0 < nq; e0 += 32) {
+            const int e = e0 + lane;
+            int src = -1;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (e < nq) {
+                const int code = queue[e];
+                src = code >> 16;
+                const NearItem &it = mine[src];
+                const int i = t0 + (code & 0xffff);
+                const float x = fabsf(offset_u((it.ilf - (float)i) + it.frac, g.lnr) * it.k);
+                float H, dH;
+                voigt_core<D>(x, it.a, H, dH);
+                if (D)
+                    v = val(it, i, H, dH);
+                else
+                    cell(it, i, H, dH);
+            }
+            if (D) {
+                // segmented sum over runs of equal items (entries are in item order)
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float nx = __shfl_up_sync(0xffffffffu, v.x, o);
+                    const float ny = __shfl_up_sync(0xffffffffu, v.y, o);
+                    const int ns = __shfl_up_sync(0xffffffffu, src, o);
+                    if (lane >= o && ns == src) {
+                        v.x += nx;
+                        v.y += ny;
+                    }
+                }
+                const int next = __shfl_down_sync(0xffffffffu, src, 1);
+                if (src >= 0 && (lane == 31 || next != src)) done(mine[src].lb, v);
+            }
+        }
+        nq = 0;
+        __syncwarp();
+    };
+    for (int64_t r0 = (int64_t)warp * 32; r0 < nitems; r0 += (int64_t)nwarp * 32) {
+        // lane-parallel set-up of 32 items
+        const int64_t it = r0 + lane;
+        bool ok = false;
+        NearItem item;
+        if (it < nitems) {
+            const int64_t l = nlo + it / ndg;
+            const int dl = (int)(it % ndg), d = dbase + dl;
+            item.ilf = g.ilf[l];
+            item.frac = g.frac[l];
+            item.dl = dl;
+            item.lb = (int)(it / ndg);
+            const float k = (float)kC * __ldg(g.invdv + g.sp[l] * g.nd + d);
+            int lo, hi;
+            if (near_span(g, item.ilf, item.frac, k, 0.0f, t0, T, lo, hi)) {
+                float p[16];
+                line_params<D ? 16 : 8>(g, l, d, p);
+                if (near_span(g, item.ilf, item.frac, p[0], p[1], t0, T, lo, hi)) {
+                    ok = true;
+                    item.k = p[0];
+                    item.a2 = p[1];
+                    item.A = p[7];
+                    item.a = D ? p[15] : sqrtf(p[1]);
+                    item.Aa6 = D ? p[14] : 0.0f;
+                    item.lo = lo;
+                    item.hi = hi;
+                }
+            }
+        }
+        const unsigned okm = __ballot_sync(0xffffffffu, ok);
+        __syncwarp();
+        if (ok) mine[lane] = item;
+        __syncwarp();
+        // sweep the surviving items' spans
+        for (unsigned m = okm; m; m &= m - 1) {
+            const int src = __ffs(m) - 1;
+            const NearItem &itm = mine[src];
+            if (nq + (itm.hi - itm.lo + 1) > kCoreQueue) flush_core();
+            float2 acc = make_float2(0.0f, 0.0f);
+            for (int i0 = itm.lo; i0 <= itm.hi; i0 += 32) {
+                const int i = i0 + lane;
+                bool core = false;
+                if (i <= itm.hi) {
+                    const float x = fabsf(offset_u((itm.ilf - (float)i) + itm.frac, g.lnr) * itm.k);
+                    const float r2 = fmaf(x, x, itm.a2);
+                    if (r2 < kFar2) {
+                        if (r2 >= kMid2) {
+                            float H, dH;
+                            voigt_mid<D>(x, itm.a, H, dH);
+                            if (D) {
+                                const float2 v = val(itm, i, H, dH);
+                                acc.x += v.x;
+                                acc.y += v.y;
+                            } else {
+                                cell(itm, i, H, dH);
+                            }
+                        } else {
+                            core = true;
+                        }
+                    }
+                }
+                const unsigned cm = __ballot_sync(0xffffffffu, core);
+                if (core) queue[nq + __popc(cm & ((1u << lane) - 1u))] = (src << 16) | (i - t0);
+                nq += __popc(cm);
+            }
+            if (D) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+                }
+                if (lane == 0 && (acc.x != 0.0f || acc.y != 0.0f)) done(itm.lb, acc);
+            }
+        }
+        flush_core();
+    }
+}
+
+// Forward near-core sums into knear.  Grid: (tile, depth group of NDG layers).
+template <int T, int NDG>
+__global__ void __launch_bounds__(256) k_line_near_fwd(LineArgs g) {
+    __shared__ float s_acc[NDG * T];
+    __shared__ NearItem s_items[8 * 32];
+    __shared__ int s_queue[8 * kCoreQueue];
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x, t0 = tile * T;
+    const int dbase = blockIdx.y * NDG, ndg = min(NDG, g.nd - dbase);
+    for (int k = tid; k < NDG * T; k += blockDim.x) s_acc[k] = 0.0f;
+    __syncthreads();
+    const int nlo = g.near_lo[tile], nhi = g.near_hi[tile];
+    near_sweep<T, false>(
+        g, t0, nlo, (int64_t)(nhi - nlo) * ndg, ndg, dbase, s_items, s_queue,
+        [&](const NearItem &it, int i, float H, float) { atomicAdd(s_acc + it.dl * T + (i - t0), it.A * H); },
+        [&](const NearItem &, int, float, float) { return make_float2(0.0f, 0.0f); }, [&](int, float2) {});
+    __syncthreads();
+    for (int k = tid; k < ndg * T; k += blockDim.x) {
+        const int dl = k / T, q = k - dl * T;
+        g.knear[(int64_t)(dbase + dl) * g.ld + t0 + q] = s_acc[k];
+    }
+}
+
+// Backward: per-line sums over the near cells of G stim A H and G stim A a6 dH/da.
+// Lines are processed in batches whose per-line sums live in shared memory; one
+// global atomic per (line, tile, depth group) at the end of each batch.
+template <int T, int NDG>
+__global__ void __launch_bounds__(256) k_line_near_bwd(LineArgs g) {
+    __shared__ float s_g[NDG * T];                                      // G * stim
+    __shared__ float2 s_sum[kNearBatch];
+    __shared__ NearItem s_items[8 * 32];
+    __shared__ int s_queue[8 * kCoreQueue];
+    const int tid = threadIdx.x;
+    const int tile = blockIdx.x, t0 = tile * T;
+    const int dbase = blockIdx.y * NDG, ndg = min(NDG, g.nd - dbase);
+    for (int k = tid; k < ndg * T; k += blockDim.x) {
+        const int dl = k / T, q = k - dl * T;
+        s_g[k] = (t0 + q < g.nlam) ? g.Gt[(int64_t)(dbase + dl) * g.ld + t0 + q] : 0.0f;
+    }
+    const int nlo = g.near_lo[tile], nhi = g.near_hi[tile];
+    for (int b0 = nlo; b0 < nhi; b0 += kNearBatch) {
+        const int nb = min(kNearBatch, nhi - b0);
+        __syncthreads();
+        for (int k = tid; k < nb; k += blockDim.x) s_sum[k] = make_float2(0.0f, 0.0f);
+        __syncthreads();
+        near_sweep<T, true>(
+            g, t0, b0, (int64_t)nb * ndg, ndg, dbase, s_items, s_queue, [&](const NearItem &, int, float, float) {},
+            [&](const NearItem &it, int i, float H, float dH) {
+                const float gs = s_g[it.dl * T + (i - t0)];
+                return make_float2(gs * it.A * H, gs * it.Aa6 * dH);
+            },
+            [&](int lb, float2 v) {
+                atomicAdd(&s_sum[lb].x, v.x);
+                atomicAdd(&s_sum[lb].y, v.y);
+            });
+        __syncthreads();
+        for (int k = tid; k < nb; k += blockDim.x) {
+            const float2 v = s_sum[k];
+            if (v.x != 0.0f) atomicAdd(g.gacc + b0 + k, (double)v.x);
+            if (v.y != 0.0f) atomicAdd(g.gacc + g.nl + b0 + k, (double)v.y);
         }
     }
 }
@@ -504,65 +731,96 @@ static LineArgs make_args(pz_ctx *c) {
     g.R = c->d_R;
     g.invdv = c->d_invdv;
     g.thr = c->d_thr;
+    g.nslab = c->nslab;
     g.beta_hi = c->d_beta_hi;
     g.beta_lo = c->d_beta_lo;
     g.ne = c->d_ne;
     g.npert = c->d_npert;
     g.c2T = c->d_c2T;
     g.kline = (float *)c->d_kline;
+    g.knear = c->d_knear;
+    g.near_lo = c->d_near_lo;
+    g.near_hi = c->d_near_hi;
     g.Gt = c->d_Gt;
     g.gacc = c->d_gacc;
     g.nl = c->L.n;
     return g;
 }
 
-template <int J, int DS>
+template <int T, bool BWD>
+static cudaError_t launch_near(pz_ctx *c, const LineArgs &g, cudaStream_t s) {
+    if (BWD) {
+        dim3 grid(c->ntiles, (c->nd + kNearDepthsBwd - 1) / kNearDepthsBwd);
+        k_line_near_bwd<T, kNearDepthsBwd><<<grid, 256, 0, s>>>(g);
+    } else {
+        dim3 grid(c->ntiles, (c->nd + kNearDepthsFwd - 1) / kNearDepthsFwd);
+        k_line_near_fwd<T, kNearDepthsFwd><<<grid, 256, 0, s>>>(g);
+    }
+    c->launches++;
+    return cudaGetLastError();
+}
+
+template <int J, int DS, int MINB>
 static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
     const Tiling &t = c->tiling;
     LineArgs g = make_args(c);
-    size_t smem = (size_t)t.LC * t.depth_per_cta() * 2 * sizeof(float4) + t.LC * sizeof(LineInfo);
+    size_t smem = (size_t)t.LC * t.depth_per_cta() * 2 * sizeof(float4) + t.LC * sizeof(LineInfo) +
+                  (size_t)DS * 32 * t.GW * sizeof(float4);
     static bool attr_set[64] = {false};
     if (!attr_set[c->device]) {
-        cudaFuncSetAttribute(k_line_fwd<J, DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_line_fwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set[c->device] = true;
     }
+    cudaError_t e = launch_near<32 * J, false>(c, g, s);
+    if (e != cudaSuccess) return e;
     dim3 grid(c->ntiles, (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta());
-    k_line_fwd<J, DS><<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LC);
+    k_line_fwd<J, DS, MINB><<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LC);
     c->launches++;
     return cudaGetLastError();
 }
 
-template <int J, int DS>
+template <int J, int DS, int MINB>
 static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
     const Tiling &t = c->tiling;
     LineArgs g = make_args(c);
-    size_t smem = (size_t)t.LC * t.depth_per_cta() * 4 * sizeof(float4) + t.LC * sizeof(LineInfo) +
-                  (size_t)t.LC * t.GW * sizeof(float2);
+    size_t smem = (size_t)t.LCB * t.depth_per_cta() * 4 * sizeof(float4) + t.LCB * sizeof(LineInfo) +
+                  (size_t)t.LCB * t.GW * sizeof(float2);
     static bool attr_set[64] = {false};
     if (!attr_set[c->device]) {
-        cudaFuncSetAttribute(k_line_bwd<J, DS>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_line_bwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set[c->device] = true;
     }
     dim3 grid(c->ntiles, (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta());
-    k_line_bwd<J, DS><<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LC);
+    k_line_bwd<J, DS, MINB><<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LCB);
     c->launches++;
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    return launch_near<32 * J, true>(c, g, s);
 }
 
-#define PZ_TILE_DISPATCH(FN)                                  \
-    const Tiling &t = c->tiling;                              \
-    if (t.J == 4 && t.DS == 9) return FN<4, 9>(c, s);         \
-    if (t.J == 4 && t.DS == 6) return FN<4, 6>(c, s);         \
-    if (t.J == 2 && t.DS == 9) return FN<2, 9>(c, s);         \
-    if (t.J == 2 && t.DS == 12) return FN<2, 12>(c, s);       \
-    if (t.J == 4 && t.DS == 12) return FN<4, 12>(c, s);       \
+// Supported (lambda points per thread, depths per warp, minimum resident CTAs per SM).
+#define PZ_TILE_LIST(X) \
+    X(4, 9, 1) X(4, 9, 2) X(4, 9, 3) X(4, 6, 1) X(4, 6, 2) X(4, 6, 3) X(4, 6, 4) X(4, 12, 1) X(4, 12, 2) \
+    X(2, 9, 1) X(2, 9, 2) X(2, 9, 3) X(2, 9, 4) X(2, 12, 1) X(2, 12, 2) X(2, 12, 3) X(2, 6, 4)
+
+#define PZ_TILE_DISPATCH(FN)                                                        \
+    const Tiling &t = c->tiling;                                                    \
+    PZ_TILE_LIST(PZ_TILE_CASE_##FN)                                                 \
     return cudaErrorInvalidConfiguration;
+#define PZ_TILE_CASE_launch_fwd_t(A, B, M) \
+    if (t.J == A && t.DS == B && t.minb == M) return launch_fwd_t<A, B, M>(c, s);
+#define PZ_TILE_CASE_launch_bwd_t(A, B, M) \
+    if (t.J == A && t.DS == B && t.minb == M) return launch_bwd_t<A, B, M>(c, s);
 
 cudaError_t launch_line_fwd_mixed(pz_ctx *c, cudaStream_t s) { PZ_TILE_DISPATCH(launch_fwd_t) }
 cudaError_t launch_line_bwd_mixed(pz_ctx *c, cudaStream_t s) { PZ_TILE_DISPATCH(launch_bwd_t) }
 
-bool tiling_supported(int J, int DS) {
-    return (J == 4 && (DS == 9 || DS == 6 || DS == 12)) || (J == 2 && (DS == 9 || DS == 12));
+bool tiling_supported(int J, int DS, int minb) {
+#define PZ_TILE_OK(A, B, M) \
+    if (J == A && DS == B && minb == M) return true;
+    PZ_TILE_LIST(PZ_TILE_OK)
+#undef PZ_TILE_OK
+    return false;
 }
 
 // ---------------------------------------------------------------------------

@@ -13,8 +13,8 @@
 //                      dH/da sqrt(pi) = t (1 + (1.5 - 2a^2) t + (3.75 - 12 a^2) t^2
 //                                       + (12 a^4 - 67.5 a^2) t^3 + 180 a^4 t^4 - 120 a^6 t^5)
 //                    (relative truncation error < 3e-7).
-//   6 <= |z| < 20    the same series to eight corrections, summed as
-//                    -Im q^(2n+1) with q = 1/z in real arithmetic.
+//   6 <= |z| < 20    the same series to six corrections in real arithmetic
+//                    through the Chebyshev recurrences of sin/cos((2n+1) arg z).
 //   |z| < 6, a < 0.5 w = exp(-z^2) + (2i/sqrt(pi)) D(z), D Dawson's integral.
 //                    Re/Im D(x + i a) from a Taylor expansion of D about the
 //                    nearest table node x_j = j/16 in the complex offset
@@ -55,7 +55,7 @@ __device__ __forceinline__ float rcp_approx(float x) {
 // Asymptotic series with NC corrections in real arithmetic.  H and (if D) dH/da.
 template <int NC, bool D>
 __device__ __forceinline__ void voigt_asym(float x, float a, float &H, float &dH) {
-    float t = 1.0f / fmaf(x, x, a * a);
+    float t = rcp_approx(fmaf(x, x, a * a));
     float qr = x * t, qi = -a * t;                 // q = 1/z
     float q2r = fmaf(qr, qr, -qi * qi), q2i = 2.0f * qr * qi;
     float kr = qr, ki = qi;                        // q^(2n+1)
@@ -71,6 +71,40 @@ __device__ __forceinline__ void voigt_asym(float x, float a, float &H, float &dH
     }
     H = sH * kInvSqrtPiF;
     if (D) dH = sD * kInvSqrtPiF;
+}
+
+// Mid wing, 6 <= |z| < 20: the Laplace series to NC corrections in real arithmetic.
+// With t = 1/|z|^2, s = a^2 t, cos(theta) = v/|z|, w = 2 - 4s:
+//   H sqrt(pi)     = a sum_n c_n t^(n+1) U_2n(cos theta),   U_2n+2 = w U_2n - U_2n-2, U_0 = 1, U_-2 = -1
+//   dH/da sqrt(pi) =   sum_n c_n (2n+1) t^(n+1) T_2n+2(cos theta), T_2m+2 = w T_2m - T_2m-2, T_0 = 1, T_2 = w/2
+// (c_0 = 1, c_n+1 = c_n (2n+1)/2; U and T Chebyshev polynomials: sin((2n+1)theta) = sin(theta) U_2n,
+// cos(2m theta) = T_2m).  NC = 6 keeps the truncation below 2e-7 relative at |z| = 6.
+template <bool D>
+__device__ __forceinline__ void voigt_mid(float x, float a, float &H, float &dH) {
+    constexpr int NC = 6;
+    const float t = rcp_approx(fmaf(x, x, a * a));
+    const float s = a * a * t;
+    const float w = fmaf(-4.0f, s, 2.0f);
+    float u0 = 1.0f, um = -1.0f;              // U_2n, U_2n-2
+    float g0 = fmaf(0.5f, w, 0.0f), gm = 1.0f; // T_2n+2, T_2n
+    float tp = t, c = 1.0f, sh = 0.0f, sd = 0.0f;
+#pragma unroll
+    for (int n = 0; n <= NC; ++n) {
+        sh = fmaf(c * tp, u0, sh);
+        if (D) sd = fmaf(c * (2.0f * n + 1.0f) * tp, g0, sd);
+        const float un = fmaf(w, u0, -um);
+        um = u0;
+        u0 = un;
+        if (D) {
+            const float gn = fmaf(w, g0, -gm);
+            gm = g0;
+            g0 = gn;
+        }
+        c *= (2.0f * n + 1.0f) * 0.5f;
+        tp *= t;
+    }
+    H = a * sh * kInvSqrtPiF;
+    if (D) dH = sd * kInvSqrtPiF;
 }
 
 // Core, small a: Dawson-derivative table.  x >= 0, x*x + a*a < 36, a < 0.5.
@@ -117,6 +151,17 @@ __device__ __forceinline__ void voigt_core_weideman(float x, float a, float &H, 
     L = fmaf(2.0f, fmaf(pr, i2i, pi * i2r), idi * kInvSqrtPiF);
 }
 
+// Core region |z| < 6 (both sub-regions), H and, if D, dH/da.
+template <bool D>
+__device__ __forceinline__ void voigt_core(float x, float a, float &H, float &dH) {
+    float L;
+    if (a < kCoreA)
+        voigt_core_table(x, a, H, L);
+    else
+        voigt_core_weideman(x, a, H, L);
+    if (D) dH = 2.0f * fmaf(x, L, a * H) - kTwoInvSqrtPiF;
+}
+
 // General evaluation (any region).  x >= 0.  Returns H and, if D, dH/da.
 template <bool D>
 __device__ __forceinline__ void voigt_general(float x, float a, float &H, float &dH) {
@@ -125,15 +170,10 @@ __device__ __forceinline__ void voigt_general(float x, float a, float &H, float 
         if (r2 >= kFar2)
             voigt_asym<2, D>(x, a, H, dH);
         else
-            voigt_asym<8, D>(x, a, H, dH);
+            voigt_mid<D>(x, a, H, dH);
         return;
     }
-    float L;
-    if (a < kCoreA)
-        voigt_core_table(x, a, H, L);
-    else
-        voigt_core_weideman(x, a, H, L);
-    if (D) dH = 2.0f * fmaf(x, L, a * H) - kTwoInvSqrtPiF;
+    voigt_core<D>(x, a, H, dH);
 }
 
 // ---- FP64 plain form --------------------------------------------------------

@@ -10,7 +10,7 @@ pytestmark = pytest.mark.gpu
 
 def test_invalid_inputs_rejected():
     prob = tiny_problem()
-    prob.atmos.m[3] = prob.atmos.m[2]           # not strictly increasing
+    prob.atmos.m[2] = prob.atmos.m[1]           # not strictly increasing
     with pytest.raises(pz.PzError) as e:
         pz.Synthesizer(prob)
     assert e.value.status == pz.PZ_EINVAL
@@ -55,5 +55,5 @@ def test_launch_count_and_eval_count():
     prob = tiny_problem(n_lambda=400, n_lines=12, W=30)
     s = pz.Synthesizer(prob)
     pz.pz_line_opacity(s.ctx)
-    assert pz.pz_last_launch_count(s.ctx) == 1
+    assert pz.pz_last_launch_count(s.ctx) == 2      # near-core + far-wing kernels
     assert s.n_evals == prob.n_evals

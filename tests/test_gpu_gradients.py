@@ -12,10 +12,13 @@ G_TOL = 1e-3
 
 
 def _check(prob, oracle, corr, instrument_noise=1.0 / 200):
+    # the device reads FP32 corrections: give the oracle the same rounded values
+    corr = {k: np.asarray(v, np.float32).astype(np.float64) for k, v in corr.items()}
     rng = np.random.default_rng(7)
     n_out = prob.instrument.pix_lambda_nm.size if prob.instrument is not None else prob.grid.n_lambda
     f0 = oracle.forward(prob, corr)
-    y = f0["f"] + rng.normal(0, instrument_noise, n_out)
+    # the device objective reads FP32 targets: give the oracle the same rounded values
+    y = (f0["f"] + rng.normal(0, instrument_noise, n_out)).astype(np.float32).astype(np.float64)
     w = 200.0 ** 2
     L, ggf, gg6, gab, _ = oracle.gradient(prob, y, np.full(n_out, w), corr, fwd=f0)
     c32 = {k: v.astype(np.float32) for k, v in corr.items()}

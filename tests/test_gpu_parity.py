@@ -65,6 +65,7 @@ def test_corrections_forward(oracle):
     rng = np.random.default_rng(4)
     corr = {"dlog_gf": rng.normal(0, 0.3, 40), "dlog_gamma6": rng.normal(0, 0.5, 40),
             "dabund": rng.normal(0, 0.2, prob.n_elem)}
+    corr = {k: v.astype(np.float32).astype(np.float64) for k, v in corr.items()}
     ref = oracle.forward(prob, corr)
     c32 = {k: v.astype(np.float32) for k, v in corr.items()}
     got = run_forward(prob, pz.PZ_MIXED, corrections=c32)
