@@ -221,6 +221,30 @@ pz_status pz_set_profiling(pz_ctx *ctx, int32_t enable);
  * [nk]).  Synchronises on the recorded events. */
 pz_status pz_kernel_times(pz_ctx *ctx, double *ms, int64_t *counts, int32_t nk);
 
+/* ---- allocation-free variant -------------------------------------------------- */
+
+/* Per-element abundance gradient from per-line oscillator-strength gradients,
+ *   g_dabund[e] = sum over lines l with elem_of_species[species[l]] == e of g_dlog_gf[l],
+ * without allocating any device memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc where they need the
+ * reduction -- a framework that owns all device memory through its own pool (an
+ * outside allocation escapes its accounting or fails under its memory cap), or a
+ * tight optimiser loop that cannot accept cudaMalloc's implicit synchronisation.
+ * Its FP64 accumulators are a fixed array inside the library (4096 entries,
+ * 32 KiB, held on every GPU that loads the library until the process exits).
+ * All pointers are device memory: g_dlog_gf [n_lines] FP32 and species [n_lines]
+ * int32 (caller line order, e.g. the pz_backward output and the list's
+ * species), elem_of_species [n_species] int32, g_dabund [n_elem] FP32 output.
+ * Lines whose species or element is out of range are skipped.
+ * The first call on each device looks up the array's device address with that
+ * device current (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call clears and reuses the same array, so calls that overlap
+ * on the GPU (unordered streams) race and give wrong sums.
+ * Errors: PZ_EINVAL (n_elem outside [1, 4096], NULL pointer), PZ_ECUDA. */
+pz_status pz_abundance_grad_noalloc(const float *g_dlog_gf, const int32_t *species,
+                                    const int32_t *elem_of_species, int64_t n_lines, int32_t n_species,
+                                    int32_t n_elem, float *g_dabund, void *stream);
+
 /* ---- device-function probes (same device code as the hot path) ------------- */
 
 /* FP32 Voigt H(a,v) and dH/da exactly as the mixed-precision kernels evaluate

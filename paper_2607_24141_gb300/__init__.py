@@ -72,6 +72,7 @@ _SIGS = {
     "pz_set_tiling": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "pz_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "pz_kernel_times": (C.c_int, [_vp, _dp, C.POINTER(C.c_int64), C.c_int32]),
+    "pz_abundance_grad_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int32, C.c_int32, _vp, _vp]),
     "pz_probe_voigt": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
     "pz_probe_expn": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
 }
@@ -205,6 +206,13 @@ def pz_kernel_times(ctx):
     cnt = (C.c_int64 * n)()
     _check(load().pz_kernel_times(ctx, ms, cnt, n))
     return {KERNEL_NAMES[k]: (ms[k], cnt[k]) for k in range(n)}
+
+
+def pz_abundance_grad_noalloc(g_dlog_gf, species, elem_of_species, n_elem, g_dabund, stream=None):
+    """Per-element sums of per-line gradients with no device allocation (device tensors)."""
+    _check(load().pz_abundance_grad_noalloc(_ptr(g_dlog_gf), _ptr(species), _ptr(elem_of_species),
+                                            g_dlog_gf.numel(), elem_of_species.numel(), int(n_elem),
+                                            _ptr(g_dabund), _stream(stream)))
 
 
 def pz_probe_voigt(a, v, H, dHda=None, stream=None):

@@ -14,7 +14,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libpz.so")
-SOURCES = ["pz_api.cu", "pz_line.cu", "pz_rt.cu"]
+SOURCES = ["pz_api.cu", "pz_line.cu", "pz_rt.cu", "pz_noalloc.cu"]
 HEADERS = ["pz_internal.h", "pz_voigt.cuh"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
