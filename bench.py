@@ -36,6 +36,12 @@ WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts
             "(40 species, 1/3 in bands) x 72 depths, W=1,500, v_r=12.3 km/s, LSF R=22,500 -> 8,575 px, "
             "chi^2 vs synthetic target, gradients for 2e5 dlog_gf + 2e5 dlog_gamma6 + 20 abundances")
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of each
+# kernel on this workload (profiles/k_line_*_apogee.md), valid only while the kernel sources hash to
+# the recorded value; otherwise the roofline's traffic is reported as null.
+TRAFFIC = {"k_line_bwd": (21.2928e6, "dbe4ec0a1012c883")}
+KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h")
+
 # algorithmic per-evaluation instruction counts of the far-wing forms (>99% of evaluations)
 OPS = {"line_fwd": {"fp32": 7, "mufu": 1}, "line_bwd": {"fp32": 14, "mufu": 1}}
 
@@ -372,10 +378,18 @@ def main():
     peak_ops = n_sm * lanes * clk_max * 1e6
     achieved_ops = evals * ops[pipe] / t_dom
     total_k = sum(share.values())
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2607_24141_gb300", "csrc", name), "rb").read())
+    kname = "k_line_bwd" if dom == "line_bwd" else "k_line_fwd"
+    traffic = None
+    if kname in TRAFFIC and TRAFFIC[kname][1] == h.hexdigest()[:16]:
+        traffic = TRAFFIC[kname][0]
     roofline = {
-        "bound": "alu", "kernel": "k_line_bwd" if dom == "line_bwd" else "k_line_fwd", "pipe": pipe,
+        "bound": "alu", "kernel": kname, "pipe": pipe,
         "achieved": achieved_ops * 1e-9, "peak": peak_ops * 1e-9, "unit": "Gop/s",
-        "frac": achieved_ops / peak_ops, "traffic": None,
+        "frac": achieved_ops / peak_ops, "traffic": traffic,
         "peak_source": "derived: %d SMs x %d %s lanes x %.0f MHz (max SM clock)" % (n_sm, lanes, pipe, clk_max),
         "ops_per_eval": ops, "evals_per_s": evals / t_dom, "ms_per_launch": t_dom * 1e3,
         "kernel_share": {k: round(v / total_k, 4) for k, v in share.items() if total_k > 0},

@@ -425,36 +425,59 @@ __global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int 
 #pragma unroll
             for (int j = 0; j < J; ++j) u[j] = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
             float s1 = 0.0f, s2 = 0.0f;
-            const bool fast = fast_line(g, info, t0f, tendf, slab);
-            bool inwin[J];
-            const int il = (int)info.ilf;
+            if (fast_line(g, info, t0f, tendf, slab)) {
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const int di = lam_thr + j - il;
-                inwin[j] = fast || (di >= -g.W && di <= g.W);
-            }
+                for (int dd = 0; dd < DS; ++dd) {
+                    const float4 p0 = par[4 * dd], p1 = par[4 * dd + 1];
+                    const float4 p2 = par[4 * dd + 2], p3 = par[4 * dd + 3];
 #pragma unroll
-            for (int dd = 0; dd < DS; ++dd) {
-                const float4 p0 = par[4 * dd], p1 = par[4 * dd + 1];
-                const float4 p2 = par[4 * dd + 2], p3 = par[4 * dd + 3];
+                    for (int j = 0; j < J; ++j) {
+                        const float x = u[j] * p0.x;
+                        const float t = rcp_approx(fmaf(x, x, p0.y));
+                        float h = fmaf(t, p1.z, p1.y);
+                        h = fmaf(t, h, p1.x);
+                        h = fmaf(t, h, p0.w);
+                        h = fmaf(t, h, p0.z);
+                        float q = fmaf(t, p3.y, p3.x);
+                        q = fmaf(t, q, p2.w);
+                        q = fmaf(t, q, p2.z);
+                        q = fmaf(t, q, p2.y);
+                        q = fmaf(t, q, p2.x);
+                        const float gt = gv[dd][j] * t;
+                        s1 = fmaf(gt, h, s1);
+                        s2 = fmaf(gt, q, s2);
+                    }
+                }
+            } else {
+                bool inwin[J];
+                const int il = (int)info.ilf;
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
-                    const float x = u[j] * p0.x;
-                    const float r2 = fmaf(x, x, p0.y);
-                    const float t = rcp_approx(r2);
-                    float h = fmaf(t, p1.z, p1.y);
-                    h = fmaf(t, h, p1.x);
-                    h = fmaf(t, h, p0.w);
-                    h = fmaf(t, h, p0.z);
-                    float q = fmaf(t, p3.y, p3.x);
-                    q = fmaf(t, q, p2.w);
-                    q = fmaf(t, q, p2.z);
-                    q = fmaf(t, q, p2.y);
-                    q = fmaf(t, q, p2.x);
-                    const bool use = fast || (inwin[j] && r2 >= kFar2);
-                    const float gt = use ? gv[dd][j] * t : 0.0f;
-                    s1 = fmaf(gt, h, s1);
-                    s2 = fmaf(gt, q, s2);
+                    const int di = lam_thr + j - il;
+                    inwin[j] = di >= -g.W && di <= g.W;
+                }
+#pragma unroll
+                for (int dd = 0; dd < DS; ++dd) {
+                    const float4 p0 = par[4 * dd], p1 = par[4 * dd + 1];
+                    const float4 p2 = par[4 * dd + 2], p3 = par[4 * dd + 3];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const float x = u[j] * p0.x;
+                        const float r2 = fmaf(x, x, p0.y);
+                        const float t = rcp_approx(r2);
+                        float h = fmaf(t, p1.z, p1.y);
+                        h = fmaf(t, h, p1.x);
+                        h = fmaf(t, h, p0.w);
+                        h = fmaf(t, h, p0.z);
+                        float q = fmaf(t, p3.y, p3.x);
+                        q = fmaf(t, q, p2.w);
+                        q = fmaf(t, q, p2.z);
+                        q = fmaf(t, q, p2.y);
+                        q = fmaf(t, q, p2.x);
+                        const float gt = (inwin[j] && r2 >= kFar2) ? gv[dd][j] * t : 0.0f;
+                        s1 = fmaf(gt, h, s1);
+                        s2 = fmaf(gt, q, s2);
+                    }
                 }
             }
 #pragma unroll
