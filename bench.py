@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched many-star measurement")
+    ap.add_argument("--batch-stars", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -180,6 +183,85 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ---------------------------------------------------------------------------
+# batched many-star workload: one CUDA-graph launch per calibration step
+# ---------------------------------------------------------------------------
+def run_batched(args, dev, barrier, max_over_ranks, ws):
+    """64 stars (seeded Teff, log g, [M/H]) on the APOGEE-like grid and instrument, each
+    with its own top-N_k subset (2e4-3e5) of a 3e5-line master list; one step =
+    pz_calib_step (corrections, fwd, chi^2, bwd, update) replayed as one graph launch.
+    Plus the joint two-star (solar-like + giant-like) step on 1e5 shared lines."""
+    import numpy as np
+    import torch
+
+    import paper_2607_24141_gb300 as pz
+    from paper_2607_24141_gb300 import inputs as I
+    stream = torch.cuda.current_stream()
+
+    def measure(batch, truth_gf, truth_g6, noise, steps, warmup):
+        t0 = time.perf_counter()
+        s = pz.Synthesizer(batch, pz.PZ_MIXED, device=dev.index)
+        t_create = time.perf_counter() - t0
+        S, n_out, nl = batch.n_stars, s.n_out, batch.lines.n_lines
+        s.set_corrections(truth_gf, truth_g6, None)
+        f_true = s.forward()
+        y = (f_true + torch.tensor(noise, dtype=torch.float32, device=dev)).contiguous()
+        w = torch.full_like(y, 200.0 ** 2)
+        s.set_corrections(None, None, np.zeros(batch.n_elem, np.float32))
+        s.forward()
+        loss = torch.zeros(1, dtype=torch.float64, device=dev)
+        g_gf = torch.empty(nl, dtype=torch.float32, device=dev)
+        g_g6 = torch.empty(nl, dtype=torch.float32, device=dev)
+        g_ab = torch.empty(batch.n_elem, dtype=torch.float32, device=dev)
+        s.calib_step(y, w, 0.0, 0.0, 0.0, loss, g_gf, g_g6, g_ab)
+        torch.cuda.synchronize()
+        L0 = loss.item()
+        gn, gmax = float(g_gf.double().norm().item()), float(g_gf.abs().max().item())
+        # plain gradient step: linear model lowers L by 5%, at most 0.01 dex per correction
+        lr = float(min(0.05 * L0 / max(gn * gn, 1e-300), 0.01 / max(gmax, 1e-300)))
+        for _ in range(warmup):
+            s.calib_step(y, w, lr, 0.0, 0.0, loss, g_gf, g_g6, g_ab)
+        barrier()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            s.calib_step(y, w, lr, 0.0, 0.0, loss, g_gf, g_g6, g_ab)
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = max_over_ranks(a.elapsed_time(b)) / steps
+        L1 = loss.item()
+        kernels = pz.pz_last_launch_count(s.ctx)
+        evals = s.n_evals
+        lines = [pz.pz_star_lines(s.ctx, k) for k in range(S)]
+        s.close()
+        return {"ms_per_step": ms, "evals_per_step": evals, "evals_per_s": ws * evals / (ms * 1e-3),
+                "stars": S, "lines_per_star_min_mean_max": [min(lines), float(np.mean(lines)), max(lines)],
+                "graph_launches_per_step": 1, "kernels_per_step": kernels, "create_s": t_create,
+                "loss_first_last": [L0, L1], "lr_gf": lr}
+
+    b = I.config4(n_stars=args.batch_stars)
+    rng = np.random.default_rng(7)
+    nl = b.lines.n_lines
+    n_out = b.instrument.pix_lambda_nm.size
+    tg, t6 = rng.normal(0, 0.1, nl).astype(np.float32), rng.normal(0, 0.2, nl).astype(np.float32)
+    big = measure(b, tg, t6, rng.normal(0, 1 / 200, (b.n_stars, n_out)), args.batch_steps, 3)
+    big["workload"] = ("%d stars (Teff U[3500,7000], log g U[1,5], [M/H] U[-2,0.5]) on the APOGEE-like grid and "
+                       "instrument, per-star top-N_k (N_k = exp U[ln 2e4, ln 3e5]) of a 3e5-line master list; "
+                       "one step = pz_calib_step (corrections, fwd, chi^2, bwd, update) as one CUDA-graph launch"
+                       % b.n_stars)
+    big["l2"] = "inputs larger than L2 (line tables and [star][depth][lambda] buffers, > 1 GB)"
+    del b
+    jb, tr = I.config4_joint()
+    joint = measure(jb, tr["dlog_gf"], tr["dlog_gamma6"], tr["noise"], max(args.batch_steps, 5), 3)
+    joint["workload"] = ("joint two-star calibration step: solar-like (5777, 4.44) + giant-like (4286, 1.66), "
+                         "1e5 shared lines, shared dlog_gf/dlog_gamma6 corrections, gradients summed, one update")
+    big["joint_two_star"] = joint
+    return big
 
 
 # ---------------------------------------------------------------------------
@@ -359,6 +441,13 @@ def main():
         fp64 = {"s_per_spectrum_fwdbwd": ms64 * 1e-3, "s_per_spectrum_fwd": fwd64 * 1e-3,
                 "evals_per_s_fwdbwd": evals / (ms64 * 1e-3), "steps": args.fp64_steps}
 
+    # ---- batched many-star workload ----
+    batched = None
+    if not args.no_batch and args.batch_stars > 0:
+        if fp64 is None:
+            s.close()
+        batched = run_batched(args, dev, barrier, max_over_ranks, ws)
+
     # ---- roofline of the dominant kernel ----
     props = torch.cuda.get_device_properties(local)
     n_sm = props.multi_processor_count
@@ -409,6 +498,7 @@ def main():
         "speedup_vs_fp64_form": (fp64["s_per_spectrum_fwdbwd"] / (ms_step * 1e-3)) if fp64 else None,
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
+        "batched": batched,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -19,6 +19,13 @@
  *   pz_loss_chi2       L = sum_p w_p (y_p - f_p)^2 and dL/df (objective of Sec. 6).
  *   pz_backward        reverse pass to per-line Delta log gf, Delta log gamma_6 and
  *                      per-element abundance gradients (Sec. 6).
+ *   pz_create_batch    many stars in one context (stars are independent, Sec. 9):
+ *                      every stage above runs over all stars in the same launches,
+ *                      the line kernels as persistent work queues.
+ *   pz_calib_step      one captured calibration step over all stars with shared
+ *                      corrections (the joint Sun-Arcturus fit of Sec. 6): forward,
+ *                      objective, reverse pass and a gradient update in one CUDA
+ *                      graph launch.
  *
  * Conventions (every call):
  *  - Return value: PZ_OK or an error code; on error pz_last_error() gives a
@@ -33,6 +40,12 @@
  *    wavelength index contiguous.  Depth index 0 is the top of the atmosphere.
  *  - A context is not thread-safe: calls on one context must be serialised by
  *    the caller (one stream at a time).
+ *  - A context holds S >= 1 stars (S = 1 from pz_create).  Every per-star array
+ *    gains a leading [S] dimension: kappa_line [S][n_depth][n_lambda], F and F_c
+ *    [S][n_lambda], f, y, w and dL/df [S][n_out].  The corrections and the
+ *    gradients are per line of the caller's list and shared by the stars: a
+ *    gradient is the sum over the stars that hold the line, and the chi-square
+ *    objective is the sum over the stars.
  */
 #ifndef PZ_H
 #define PZ_H
@@ -173,6 +186,55 @@ pz_status pz_loss_chi2(pz_ctx *ctx, const float *y, const float *w, int64_t n, d
 pz_status pz_backward(pz_ctx *ctx, const float *dL_df, float *g_dlog_gf, float *g_dlog_gamma6,
                       float *g_dabund, void *stream);
 
+/* ---- batches of stars ------------------------------------------------------ */
+
+/* A context over n_stars independent stars (Sec. 9: stars are independent, so a
+ * batch is the same calculation for each).  atmos: host array [n_stars]; every
+ * star must share n_depth, n_species and the wavelength grid (lambda0_nm, R_grid,
+ * n_lambda); everything else (T, rho, n_e, n_pert, pop, mass_amu, xi, kappa_c)
+ * is per star.  lines: the master line list (caller order), shared.  Star k uses
+ * the master lines subset_index[subset_offsets[k] .. subset_offsets[k+1]) (host
+ * arrays, [n_stars + 1] int64 starting at 0 and non-decreasing, and int32
+ * indices in [0, n_lines); a line may appear in any number of stars).
+ * subset_offsets NULL: every star uses every line.  Synchronous like pz_create.
+ * Errors: PZ_EINVAL (n_stars outside [1, 512], grids differ, a subset index out
+ * of range, anything pz_create rejects), PZ_ENOMEM, PZ_ECUDA. */
+pz_status pz_create_batch(int32_t n_stars, const pz_atmos *atmos, const pz_linelist *lines,
+                          const int64_t *subset_offsets, const int32_t *subset_index,
+                          pz_precision precision, pz_ctx **out);
+
+/* Number of stars of the context (0 for NULL). */
+int32_t pz_n_stars(const pz_ctx *ctx);
+
+/* Lines of star k kept at creation (windows intersecting the grid); -1 if k is
+ * out of range. */
+int64_t pz_star_lines(const pz_ctx *ctx, int32_t star);
+
+/* Current corrections in caller line order (after pz_set_corrections and any
+ * pz_calib_step updates): dlog_gf, dlog_gamma6 [n_lines] and dabund [n_elem],
+ * FP32, host or device memory, each may be NULL.  Synchronises `stream`. */
+pz_status pz_get_corrections(pz_ctx *ctx, float *dlog_gf, float *dlog_gamma6, float *dabund,
+                             void *stream);
+
+/* One calibration step on the chi-square objective over all stars (Sec. 6,
+ * the shared fit of both standards): corrections applied to the line data,
+ * pz_line_opacity, pz_flux and the instrument last configured by pz_instrument,
+ * L = sum_stars sum_p w (y - f)^2, the reverse pass, and the plain gradient update
+ *   dlog_gf -= lr_gf g_dlog_gf, dlog_gamma6 -= lr_g6 g_dlog_gamma6,
+ *   dabund -= lr_ab g_dabund,
+ * with the gradients taken before the update.  The paper drives its updates
+ * with L-BFGS; this call is the device-side step such a driver repeats.
+ * y, w: device FP32 [S][n] (w may be NULL), n the instrument output size.
+ * loss: device FP64 scalar or NULL.  g_*: device FP32 outputs (caller order) or
+ * NULL.  The whole step is captured once in a CUDA graph and replayed by one
+ * graph launch on `stream`; it is re-captured when an argument changes (or after
+ * pz_set_tiling, pz_instrument with new settings, or a new element count).
+ * Requires one earlier pz_instrument call (PZ_ESTATE).  Errors: PZ_EINVAL (n,
+ * non-finite learning rate), PZ_ECUDA. */
+pz_status pz_calib_step(pz_ctx *ctx, const float *y, const float *w, int64_t n, float lr_gf,
+                        float lr_g6, float lr_ab, double *loss, float *g_dlog_gf,
+                        float *g_dlog_gamma6, float *g_dabund, void *stream);
+
 /* ---- introspection -------------------------------------------------------- */
 
 /* Thread-local message of the last failing call on this thread ("" if none). */
@@ -208,7 +270,8 @@ typedef enum {
     PZ_K_INST_ADJOINT = 5, /* transpose of the instrument */
     PZ_K_LOSS = 6,         /* chi-square and its seed */
     PZ_K_OTHER = 7,        /* corrections, finalisation, copies */
-    PZ_NK = 8
+    PZ_K_STEP = 8,         /* a whole pz_calib_step graph launch */
+    PZ_NK = 9
 } pz_kernel_id;
 
 /* enable != 0: every kernel launch of this context is bracketed by CUDA events

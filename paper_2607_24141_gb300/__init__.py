@@ -73,6 +73,13 @@ _SIGS = {
     "pz_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "pz_kernel_times": (C.c_int, [_vp, _dp, C.POINTER(C.c_int64), C.c_int32]),
     "pz_abundance_grad_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int32, C.c_int32, _vp, _vp]),
+    "pz_create_batch": (C.c_int, [C.c_int32, C.POINTER(pz_atmos), C.POINTER(pz_linelist), _vp, _vp, C.c_int,
+                                  C.POINTER(_vp)]),
+    "pz_n_stars": (C.c_int32, [_vp]),
+    "pz_star_lines": (C.c_int64, [_vp, C.c_int32]),
+    "pz_get_corrections": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
+    "pz_calib_step": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_float, C.c_float, C.c_float, _vp, _vp, _vp, _vp,
+                                _vp]),
     "pz_probe_voigt": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
     "pz_probe_expn": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
 }
@@ -132,6 +139,47 @@ def pz_create(atmos: pz_atmos, lines: pz_linelist, precision: int = PZ_MIXED) ->
     return ctx.value
 
 
+def pz_create_batch(atmos_list, lines: pz_linelist, subset_offsets=None, subset_index=None,
+                    precision: int = PZ_MIXED) -> int:
+    """atmos_list: sequence of pz_atmos; subset_offsets int64 [S+1] and subset_index int32
+    (host numpy) or None (every star uses every line)."""
+    S = len(atmos_list)
+    arr = (pz_atmos * S)(*atmos_list)
+    off = idx = None
+    if subset_offsets is not None:
+        off = np.ascontiguousarray(subset_offsets, dtype=np.int64)
+        idx = np.ascontiguousarray(subset_index, dtype=np.int32)
+    ctx = _vp()
+    _check(load().pz_create_batch(S, arr, C.byref(lines), None if off is None else off.ctypes.data,
+                                  None if idx is None or idx.size == 0 else idx.ctypes.data, int(precision),
+                                  C.byref(ctx)))
+    return ctx.value
+
+
+def pz_n_stars(ctx) -> int:
+    return int(load().pz_n_stars(ctx))
+
+
+def pz_star_lines(ctx, star: int) -> int:
+    return int(load().pz_star_lines(ctx, int(star)))
+
+
+def pz_get_corrections(ctx, dlog_gf=None, dlog_gamma6=None, dabund=None, stream=None):
+    """Outputs may be torch tensors (device) or numpy float32 arrays (host)."""
+    def p(x):
+        if x is None:
+            return None
+        return x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+    _check(load().pz_get_corrections(ctx, p(dlog_gf), p(dlog_gamma6), p(dabund), _stream(stream)))
+
+
+def pz_calib_step(ctx, y, w=None, lr_gf=0.0, lr_g6=0.0, lr_ab=0.0, loss=None, g_dlog_gf=None,
+                  g_dlog_gamma6=None, g_dabund=None, stream=None):
+    _check(load().pz_calib_step(ctx, _ptr(y), _ptr(w), y.shape[-1], float(lr_gf), float(lr_g6), float(lr_ab),
+                                _ptr(loss), _ptr(g_dlog_gf), _ptr(g_dlog_gamma6), _ptr(g_dabund),
+                                _stream(stream)))
+
+
 def pz_destroy(ctx: int):
     _check(load().pz_destroy(ctx))
 
@@ -172,7 +220,7 @@ def pz_instrument(ctx, v_r_kms, v_b_kms, R_lsf, pix_lambda_nm, f_norm=None, stre
 
 
 def pz_loss_chi2(ctx, y, w=None, loss=None, dL_df=None, stream=None):
-    _check(load().pz_loss_chi2(ctx, _ptr(y), _ptr(w), y.numel(), _ptr(loss), _ptr(dL_df), _stream(stream)))
+    _check(load().pz_loss_chi2(ctx, _ptr(y), _ptr(w), y.shape[-1], _ptr(loss), _ptr(dL_df), _stream(stream)))
 
 
 def pz_backward(ctx, dL_df, g_dlog_gf=None, g_dlog_gamma6=None, g_dabund=None, stream=None):
@@ -192,7 +240,8 @@ def pz_set_tiling(ctx, lambda_per_thread=0, depth_per_warp=0, warps_per_cta=0, l
     _check(load().pz_set_tiling(ctx, lambda_per_thread, depth_per_warp, warps_per_cta, lines_per_chunk, ctas_per_sm))
 
 
-KERNEL_NAMES = ("line_fwd", "line_bwd", "flux", "rt_adjoint", "instrument", "inst_adjoint", "loss", "other")
+KERNEL_NAMES = ("line_fwd", "line_bwd", "flux", "rt_adjoint", "instrument", "inst_adjoint", "loss", "other",
+                "step")
 
 
 def pz_set_profiling(ctx, enable=True):
@@ -227,42 +276,64 @@ def pz_probe_expn(x, out, stream=None):
 # convenience wrapper
 # ---------------------------------------------------------------------------
 
+def _atmos_struct(at, kappa_c, grid, keep: list) -> pz_atmos:
+    f64 = lambda a: np.ascontiguousarray(a, np.float64)  # noqa: E731
+    arrs = [f64(at.m), f64(at.T), f64(at.rho), f64(at.n_e), f64(at.n_pert), f64(at.pop), f64(at.mass_amu),
+            f64(kappa_c)]
+    keep.extend(arrs)
+    A = pz_atmos()
+    A.n_depth, A.n_species = at.n_depth, at.n_species
+    A.m, A.T, A.rho, A.n_e, A.n_pert, A.pop, A.mass_amu, A.kappa_c = [x.ctypes.data_as(_dp) for x in arrs]
+    A.xi_cms = at.xi_cms
+    A.lambda0_nm, A.R_grid, A.n_lambda = grid.lambda0_nm, grid.R_grid, grid.n_lambda
+    return A
+
+
+def _lines_struct(ll, keep: list) -> pz_linelist:
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)  # noqa: E731
+    lam = np.ascontiguousarray(ll.lambda_nm, np.float64)
+    cols = [f32(ll.log_gf), f32(ll.E_low_eV), f32(ll.log_gamma_rad), f32(ll.log_gamma4), f32(ll.log_gamma6)]
+    sp = np.ascontiguousarray(ll.species, np.int32)
+    keep.extend([lam, sp] + cols)
+    L = pz_linelist()
+    L.n_lines = ll.n_lines
+    L.lambda_nm = lam.ctypes.data_as(_dp)
+    L.log_gf, L.E_low_eV, L.log_gamma_rad, L.log_gamma4, L.log_gamma6 = [x.ctypes.data_as(_fp) for x in cols]
+    L.species = sp.ctypes.data_as(_ip)
+    L.half_window = ll.half_window
+    return L
+
+
 class Synthesizer:
-    """One context for a :class:`inputs.Problem` (atmosphere + grid + lines)."""
+    """One context for an :class:`inputs.Problem` (one star) or an :class:`inputs.Batch`
+    (many stars sharing a grid and a master line list).  For a batch every per-star
+    output gains a leading [n_stars] dimension."""
 
     def __init__(self, prob, precision: int = PZ_MIXED, device: int = 0):
         import torch
         torch.cuda.set_device(device)
         self.prob = prob
         self.precision = precision
-        at, ll = prob.atmos, prob.lines
-        f64 = lambda a: np.ascontiguousarray(a, np.float64)  # noqa: E731
-        f32 = lambda a: np.ascontiguousarray(a, np.float32)  # noqa: E731
-        self._keep = dict(m=f64(at.m), T=f64(at.T), rho=f64(at.rho), ne=f64(at.n_e), np=f64(at.n_pert),
-                          pop=f64(at.pop), mass=f64(at.mass_amu), kc=f64(prob.kappa_c),
-                          lam=f64(ll.lambda_nm), gf=f32(ll.log_gf), E=f32(ll.E_low_eV),
-                          gr=f32(ll.log_gamma_rad), g4=f32(ll.log_gamma4), g6=f32(ll.log_gamma6),
-                          sp=np.ascontiguousarray(ll.species, np.int32))
-        k = self._keep
-        A = pz_atmos()
-        A.n_depth, A.n_species = at.n_depth, at.n_species
-        A.m, A.T, A.rho = [k[n].ctypes.data_as(_dp) for n in ("m", "T", "rho")]
-        A.n_e, A.n_pert, A.pop, A.mass_amu = [k[n].ctypes.data_as(_dp) for n in ("ne", "np", "pop", "mass")]
-        A.xi_cms = at.xi_cms
-        A.kappa_c = k["kc"].ctypes.data_as(_dp)
-        A.lambda0_nm, A.R_grid, A.n_lambda = prob.grid.lambda0_nm, prob.grid.R_grid, prob.grid.n_lambda
-        L = pz_linelist()
-        L.n_lines = ll.n_lines
-        L.lambda_nm = k["lam"].ctypes.data_as(_dp)
-        L.log_gf, L.E_low_eV = k["gf"].ctypes.data_as(_fp), k["E"].ctypes.data_as(_fp)
-        L.log_gamma_rad, L.log_gamma4, L.log_gamma6 = [k[n].ctypes.data_as(_fp) for n in ("gr", "g4", "g6")]
-        L.species = k["sp"].ctypes.data_as(_ip)
-        L.half_window = ll.half_window
-        self._atmos, self._lines = A, L
-        self.ctx = pz_create(A, L, precision)
+        keep = []
+        self.batched = hasattr(prob, "subsets")
+        if self.batched:
+            atl = [_atmos_struct(a, kc, prob.grid, keep) for a, kc in zip(prob.atmos, prob.kappa_c)]
+            L = _lines_struct(prob.lines, keep)
+            off = np.concatenate([[0], np.cumsum([len(x) for x in prob.subsets])]).astype(np.int64)
+            idx = (np.concatenate(prob.subsets) if len(prob.subsets) else np.zeros(0)).astype(np.int32)
+            self.ctx = pz_create_batch(atl, L, off, idx, precision)
+            self.n_stars = len(atl)
+            self.n_depth = prob.atmos[0].n_depth
+        else:
+            A = _atmos_struct(prob.atmos, prob.kappa_c, prob.grid, keep)
+            L = _lines_struct(prob.lines, keep)
+            self.ctx = pz_create(A, L, precision)
+            self.n_stars = 1
+            self.n_depth = prob.atmos.n_depth
+        self._keep = keep
         self.device = torch.device("cuda", device)
         self.n_lambda = prob.grid.n_lambda
-        self.n_depth = at.n_depth
+        self.n_lines = prob.lines.n_lines
         self.n_out = prob.instrument.pix_lambda_nm.size if prob.instrument is not None else self.n_lambda
 
     def close(self):
@@ -280,16 +351,27 @@ class Synthesizer:
     def n_evals(self) -> int:
         return pz_eval_count(self.ctx)
 
+    def _shape(self, n):
+        return (self.n_stars, n) if self.batched else (n,)
+
     def set_corrections(self, dlog_gf=None, dlog_gamma6=None, dabund=None, stream=None):
         eos = self.prob.elem_of_species if dabund is not None else None
         pz_set_corrections(self.ctx, dlog_gf, dlog_gamma6, dabund, eos,
                            self.prob.n_elem if dabund is not None else 0, stream)
 
+    def configure_instrument(self, stream=None):
+        """Run the instrument once on the current flux so that pz_calib_step can use it."""
+        inst = self.prob.instrument
+        if inst is None:
+            pz_instrument(self.ctx, 0, 0, 0, None, None, stream)
+        else:
+            pz_instrument(self.ctx, inst.v_r_kms, inst.v_b_kms, inst.R_lsf, inst.pix_lambda_nm, None, stream)
+
     def forward(self, kappa=None, F=None, Fc=None, f=None, stream=None):
         """line opacity -> flux -> instrument; returns f (allocated if not given)."""
         import torch
         if f is None:
-            f = torch.empty(self.n_out, dtype=torch.float32, device=self.device)
+            f = torch.empty(self._shape(self.n_out), dtype=torch.float32, device=self.device)
         pz_line_opacity(self.ctx, kappa, stream)
         pz_flux(self.ctx, F, Fc, stream)
         inst = self.prob.instrument
@@ -304,6 +386,18 @@ class Synthesizer:
 
     def backward(self, dL_df, g_gf=None, g_g6=None, g_ab=None, stream=None):
         pz_backward(self.ctx, dL_df, g_gf, g_g6, g_ab, stream)
+
+    def calib_step(self, y, w=None, lr_gf=0.0, lr_g6=0.0, lr_ab=0.0, loss=None, g_gf=None, g_g6=None, g_ab=None,
+                   stream=None):
+        pz_calib_step(self.ctx, y, w, lr_gf, lr_g6, lr_ab, loss, g_gf, g_g6, g_ab, stream)
+
+    def get_corrections(self):
+        """(dlog_gf, dlog_gamma6, dabund or None) as host float32 arrays."""
+        gf = np.empty(self.n_lines, np.float32)
+        g6 = np.empty(self.n_lines, np.float32)
+        ab = np.empty(self.prob.n_elem, np.float32) if self.prob.n_elem else None
+        pz_get_corrections(self.ctx, gf, g6, ab)
+        return gf, g6, ab
 
 
 def _torch_function():
@@ -327,7 +421,7 @@ def _torch_function():
         def backward(ctx, grad_f):
             s = ctx.synth
             grad_f = grad_f.contiguous().to(torch.float32)
-            nl = s.prob.lines.n_lines
+            nl = s.n_lines
             g_gf = torch.empty(nl, dtype=torch.float32, device=grad_f.device)
             g_g6 = torch.empty(nl, dtype=torch.float32, device=grad_f.device)
             g_ab = torch.empty(s.prob.n_elem, dtype=torch.float32, device=grad_f.device) if ctx.has_ab else None

@@ -53,14 +53,14 @@ static void prof_fold(pz_ctx *c) {
 }
 
 void prof_begin(pz_ctx *c, cudaStream_t s) {
-    if (!c->profiling) return;
+    if (!c->profiling || c->capturing) return;
     cudaEvent_t a = prof_event(c);
     cudaEventRecord(a, s);
     c->pending_begin = a;
 }
 
 void prof_end(pz_ctx *c, cudaStream_t s, int kid) {
-    if (!c->profiling || !c->pending_begin) return;
+    if (!c->profiling || c->capturing || !c->pending_begin) return;
     cudaEvent_t b = prof_event(c);
     cudaEventRecord(b, s);
     c->marks.push_back({c->pending_begin, b, kid});
@@ -113,61 +113,98 @@ static void dfree(void *p) {
     if (p) cudaFree(p);
 }
 
-static pz_status build_tiles(pz_ctx *c) {
-    int T = c->tiling.lambda_per_tile();
-    int nt = (int)((c->nlam + T - 1) / T);
-    std::vector<int32_t> lo(nt), hi(nt);
-    for (int t = 0; t < nt; ++t) {
-        int64_t a = (int64_t)t * T - c->W, b = (int64_t)t * T + T - 1 + c->W;
-        lo[t] = (int32_t)(std::lower_bound(c->h_il.begin(), c->h_il.end(), (int32_t)std::max<int64_t>(a, INT32_MIN)) -
-                          c->h_il.begin());
-        hi[t] = (int32_t)(std::upper_bound(c->h_il.begin(), c->h_il.end(), (int32_t)std::min<int64_t>(b, INT32_MAX)) -
-                          c->h_il.begin());
+// Work items of the persistent line kernels: (star, tile * groups + group, lo, hi) with
+// [lo, hi) the star's lines that the item must visit, ordered by estimated cost,
+// longest first, so that the queue balances uneven stars and tiles.
+//   far:  lines whose window |i - i_l| <= W touches the tile; one item per depth
+//         group of DS x GW layers, every (star, tile, group) present (the far
+//         forward writes every cell of kappa_line);
+//   near: lines whose centre lies within 20 Doppler widths (the widest of the star)
+//         of the tile plus a margin; forward items for every (star, tile, group of
+//         8 layers) (they write the near-core buffer), backward items of 24 layers
+//         only where the range is not empty.
+static pz_status build_items(pz_ctx *c) {
+    const int T = c->tiling.lambda_per_tile();
+    const int nt = (int)((c->nlam + T - 1) / T);
+    const int DC = c->tiling.depth_per_cta();
+    const int ngf = (c->nd + DC - 1) / DC;
+    const int nnf = (c->nd + 7) / 8, nnb = (c->nd + 23) / 24;
+    struct Item {
+        int4 v;
+        double cost;
+    };
+    std::vector<Item> fi, nf, nb;
+    fi.reserve((size_t)c->S * nt * ngf);
+    nf.reserve((size_t)c->S * nt * nnf);
+    for (int st = 0; st < c->S; ++st) {
+        auto b0 = c->h_il.begin() + c->h_line_off[st], b1 = c->h_il.begin() + c->h_line_off[st + 1];
+        double kmin = 1e300;
+        for (int k = 0; k < c->ns * c->nd; ++k)
+            kmin = std::min(kmin, kC * (double)c->h_invdv[(size_t)st * c->ns * c->nd + k]);
+        const double hw = 20.0 / (kmin * c->lnr) * 1.02 + 4.0;
+        for (int t = 0; t < nt; ++t) {
+            const int64_t a = (int64_t)t * T - c->W, b = (int64_t)t * T + T - 1 + c->W;
+            const int lo = (int)(std::lower_bound(b0, b1, (int32_t)std::max<int64_t>(a, INT32_MIN)) - c->h_il.begin());
+            const int hi = (int)(std::upper_bound(b0, b1, (int32_t)std::min<int64_t>(b, INT32_MAX)) - c->h_il.begin());
+            for (int g = 0; g < ngf; ++g)
+                fi.push_back({make_int4(st, t * ngf + g, lo, hi), (double)(hi - lo) * std::min(DC, c->nd - g * DC)});
+            double na = (double)t * T - hw, nb_ = (double)t * T + T - 1 + hw;
+            na = std::max(na, (double)INT32_MIN / 2);
+            nb_ = std::min(nb_, (double)INT32_MAX / 2);
+            const int nlo = (int)(std::lower_bound(b0, b1, (int32_t)std::floor(na)) - c->h_il.begin());
+            const int nhi = (int)(std::upper_bound(b0, b1, (int32_t)std::ceil(nb_)) - c->h_il.begin());
+            for (int g = 0; g < nnf; ++g)
+                nf.push_back({make_int4(st, t * nnf + g, nlo, nhi), (double)(nhi - nlo) * std::min(8, c->nd - g * 8)});
+            if (nhi > nlo)
+                for (int g = 0; g < nnb; ++g)
+                    nb.push_back({make_int4(st, t * nnb + g, nlo, nhi), (double)(nhi - nlo) * std::min(24, c->nd - g * 24)});
+        }
     }
-    // near-core line ranges: x_l within 20 Doppler widths (the widest over species and
-    // depths) of the tile, plus a margin
-    double kmin = 1e300;
-    for (float v : c->h_invdv) kmin = std::min(kmin, kC * (double)v);
-    const double hw = 20.0 / (kmin * c->lnr) * 1.02 + 4.0;
-    std::vector<int32_t> nlo(nt), nhi(nt);
-    for (int t = 0; t < nt; ++t) {
-        double a = (double)t * T - hw, b = (double)t * T + T - 1 + hw;
-        a = std::max(a, (double)INT32_MIN / 2);
-        b = std::min(b, (double)INT32_MAX / 2);
-        nlo[t] = (int32_t)(std::lower_bound(c->h_il.begin(), c->h_il.end(), (int32_t)std::floor(a)) - c->h_il.begin());
-        nhi[t] = (int32_t)(std::upper_bound(c->h_il.begin(), c->h_il.end(), (int32_t)std::ceil(b)) - c->h_il.begin());
-    }
-    dfree(c->d_tile_lo);
-    dfree(c->d_tile_hi);
-    dfree(c->d_near_lo);
-    dfree(c->d_near_hi);
-    c->d_tile_lo = c->d_tile_hi = c->d_near_lo = c->d_near_hi = nullptr;
-    PZ_TRY(upload(&c->d_tile_lo, lo, "tile ranges"));
-    PZ_TRY(upload(&c->d_tile_hi, hi, "tile ranges"));
-    PZ_TRY(upload(&c->d_near_lo, nlo, "tile ranges"));
-    PZ_TRY(upload(&c->d_near_hi, nhi, "tile ranges"));
+    auto order = [](std::vector<Item> &v) {
+        std::stable_sort(v.begin(), v.end(), [](const Item &x, const Item &y) { return x.cost > y.cost; });
+        std::vector<int4> out(v.size());
+        for (size_t k = 0; k < v.size(); ++k) out[k] = v[k].v;
+        return out;
+    };
+    int nbusy = 0;
+    for (const Item &it : fi) nbusy += it.v.w > it.v.z;
+    std::vector<int4> hf = order(fi), hn = order(nf), hb = order(nb);
+    dfree(c->d_fitems);
+    dfree(c->d_nitems_f);
+    dfree(c->d_nitems_b);
+    c->d_fitems = c->d_nitems_f = c->d_nitems_b = nullptr;
+    PZ_TRY(upload(&c->d_fitems, hf, "work items"));
+    PZ_TRY(upload(&c->d_nitems_f, hn, "work items"));
+    PZ_TRY(upload(&c->d_nitems_b, hb, "work items"));
+    c->n_fitems = (int)hf.size();
+    c->n_bitems = nbusy;
+    c->n_nitems_f = (int)hn.size();
+    c->n_nitems_b = (int)hb.size();
     c->ntiles = nt;
     c->tileT = T;
     return PZ_OK;
 }
 
-// Fast-path threshold per (species, depth slab of DS layers): a line whose distance
-// from every point of the tile is >= thr (grid units) has |v| >= 20 at every depth of
-// the slab, because |v| = |expm1(Delta ln r)| c/dv_D >= |Delta| ln r (1 - |Delta| ln r / 2) c/dv_D.
+// Fast-path threshold per (star, species, depth slab of DS layers): a line whose
+// distance from every point of the tile is >= thr (grid units) has |v| >= 20 at every
+// depth of the slab, because |v| = |expm1(Delta ln r)| c/dv_D >= |Delta| ln r (1 - |Delta| ln r / 2) c/dv_D.
 // Slabs past the last layer (grid padding) get 0.
 static pz_status build_thresholds(pz_ctx *c) {
     const int DS = c->tiling.DS, DC = c->tiling.depth_per_cta();
     const int nslab = ((c->nd + DC - 1) / DC) * c->tiling.GW;
     double shrink = 1.0 - 0.5 * (c->W + 1024.0) * c->lnr;
     if (shrink < 0.5) shrink = 0.5;
-    std::vector<float> thr((size_t)c->ns * nslab, 0.0f);
-    for (int s = 0; s < c->ns; ++s)
-        for (int b = 0; b < nslab; ++b) {
-            double mn = 1e300;
-            for (int d = b * DS; d < std::min(c->nd, (b + 1) * DS); ++d)
-                mn = std::min(mn, (double)c->h_invdv[(size_t)s * c->nd + d]);
-            if (mn < 1e300) thr[(size_t)s * nslab + b] = (float)(20.0 / (kC * mn * c->lnr * shrink) * (1.0 + 1e-4) + 1e-3);
-        }
+    std::vector<float> thr((size_t)c->S * c->ns * nslab, 0.0f);
+    for (int st = 0; st < c->S; ++st)
+        for (int s = 0; s < c->ns; ++s)
+            for (int b = 0; b < nslab; ++b) {
+                double mn = 1e300;
+                for (int d = b * DS; d < std::min(c->nd, (b + 1) * DS); ++d)
+                    mn = std::min(mn, (double)c->h_invdv[((size_t)st * c->ns + s) * c->nd + d]);
+                if (mn < 1e300)
+                    thr[((size_t)st * c->ns + s) * nslab + b] =
+                        (float)(20.0 / (kC * mn * c->lnr * shrink) * (1.0 + 1e-4) + 1e-3);
+            }
     dfree(c->d_thr);
     c->d_thr = nullptr;
     PZ_TRY(upload(&c->d_thr, thr, "thresholds"));
@@ -175,81 +212,117 @@ static pz_status build_thresholds(pz_ctx *c) {
     return PZ_OK;
 }
 
+static void drop_graph(pz_ctx *c) {
+    if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+    c->graph = StepGraph();
+}
+
 static void destroy_ctx(pz_ctx *c) {
     if (!c) return;
+    drop_graph(c);
     void *ptrs[] = {c->d_m, c->d_T, c->d_beta_hi, c->d_beta_lo, c->d_ne, c->d_npert, c->d_c2T, c->d_ne64,
-                    c->d_npert64, c->d_rho64, c->d_R, c->d_Rbase, c->d_invdv, c->d_pop64, c->d_mass64, c->d_thr,
-                    c->d_kc, c->d_dab, c->d_eos, c->L.orig, c->L.ilf, c->L.il32, c->L.frac, c->L.sp, c->L.E,
-                    c->L.lamcm, c->L.grad, c->L.g4, c->L.g6base, c->L.g6, c->L.Q, c->L.Qbase, c->L.x64,
-                    c->L.lg_gf, c->L.lg_rad, c->L.lg_4, c->L.lg_6, c->L.dgf, c->L.dg6, c->d_tile_lo, c->d_tile_hi,
-                    c->d_kline, c->d_knear, c->d_near_lo, c->d_near_hi, c->d_F, c->d_Fc, c->d_g, c->d_gc, c->d_tap0, c->d_ntap, c->d_tapw, c->d_dFbar,
-                    c->d_Gt, c->d_Gt64, c->d_gacc, c->d_gab};
+                    c->d_npert64, c->d_rho64, c->d_R, c->d_Rbase, c->d_invdv, c->d_pop64, c->d_mass64, c->d_xi64,
+                    c->d_thr, c->d_kc, c->d_dab, c->d_mdgf, c->d_mdg6, c->d_eos, c->L.orig, c->L.star, c->L.ilf,
+                    c->L.il32, c->L.frac, c->L.sp, c->L.E, c->L.lamcm, c->L.grad, c->L.g4, c->L.g6base, c->L.g6,
+                    c->L.Q, c->L.Qbase, c->L.x64, c->L.lg_gf, c->L.lg_rad, c->L.lg_4, c->L.lg_6, c->L.dgf, c->L.dg6,
+                    c->d_line_off, c->d_fitems, c->d_nitems_f, c->d_nitems_b, c->d_ctr, c->d_knear, c->d_kline,
+                    c->d_F, c->d_Fc, c->d_g, c->d_gc, c->d_tap0, c->d_ntap, c->d_tapw, c->d_dFbar, c->d_Gt,
+                    c->d_Gt64, c->d_gacc, c->d_gline, c->d_gab, c->d_dLdf};
     for (void *p : ptrs) dfree(p);
     for (auto &m : c->marks) {
         cudaEventDestroy(m.a);
         cudaEventDestroy(m.b);
     }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
-static pz_status create_impl(const pz_atmos *at, const pz_linelist *ll, pz_precision prec, pz_ctx **out) {
-    if (!out) return fail(PZ_EINVAL, "pz_create: out is NULL");
-    *out = nullptr;
-    if (!at || !ll) return fail(PZ_EINVAL, "pz_create: atmos or lines is NULL");
-    if (prec != PZ_FP64 && prec != PZ_MIXED) return fail(PZ_EINVAL, "pz_create: unknown precision");
+// Validation of one atmosphere; shared fields are checked against ref (star 0).
+static pz_status check_atmos(const pz_atmos *at, const pz_atmos *ref, const char *who) {
+    const std::string w(who);
+    if (!at) return fail(PZ_EINVAL, w + ": atmos is NULL");
     const int nd = at->n_depth, ns = at->n_species;
-    if (nd < 2 || nd > kMaxDepth) return fail(PZ_EINVAL, "pz_create: n_depth must be in [2, 128]");
-    if (ns < 1) return fail(PZ_EINVAL, "pz_create: n_species must be >= 1");
-    if (at->n_lambda < 1 || at->n_lambda > 16000000) return fail(PZ_EINVAL, "pz_create: n_lambda must be in [1, 1.6e7]");
-    if (ll->n_lines < 0 || ll->n_lines > 2000000000) return fail(PZ_EINVAL, "pz_create: n_lines out of range");
-    if (ll->half_window < 0 || ll->half_window > 500000) return fail(PZ_EINVAL, "pz_create: half_window must be in [0, 5e5]");
+    if (nd < 2 || nd > kMaxDepth) return fail(PZ_EINVAL, w + ": n_depth must be in [2, 128]");
+    if (ns < 1) return fail(PZ_EINVAL, w + ": n_species must be >= 1");
+    if (at->n_lambda < 1 || at->n_lambda > 16000000) return fail(PZ_EINVAL, w + ": n_lambda must be in [1, 1.6e7]");
     if (!at->m || !at->T || !at->rho || !at->n_e || !at->n_pert || !at->pop || !at->mass_amu || !at->kappa_c)
-        return fail(PZ_EINVAL, "pz_create: an atmosphere array is NULL");
-    if (!finite_pos(at->lambda0_nm) || !finite_pos(at->R_grid)) return fail(PZ_EINVAL, "pz_create: lambda0 and R_grid must be > 0");
-    if (!(std::isfinite(at->xi_cms) && at->xi_cms >= 0)) return fail(PZ_EINVAL, "pz_create: xi must be finite and >= 0");
+        return fail(PZ_EINVAL, w + ": an atmosphere array is NULL");
+    if (!finite_pos(at->lambda0_nm) || !finite_pos(at->R_grid)) return fail(PZ_EINVAL, w + ": lambda0 and R_grid must be > 0");
+    if (!(std::isfinite(at->xi_cms) && at->xi_cms >= 0)) return fail(PZ_EINVAL, w + ": xi must be finite and >= 0");
+    if (ref && (at->n_depth != ref->n_depth || at->n_species != ref->n_species || at->n_lambda != ref->n_lambda ||
+                at->lambda0_nm != ref->lambda0_nm || at->R_grid != ref->R_grid))
+        return fail(PZ_EINVAL, w + ": every star must share n_depth, n_species and the wavelength grid");
     for (int d = 0; d < nd; ++d) {
         if (!finite_pos(at->m[d]) || !finite_pos(at->T[d]) || !finite_pos(at->rho[d]))
-            return fail(PZ_EINVAL, "pz_create: m, T, rho must be finite and > 0");
+            return fail(PZ_EINVAL, w + ": m, T, rho must be finite and > 0");
         if (!(std::isfinite(at->n_e[d]) && at->n_e[d] >= 0) || !(std::isfinite(at->n_pert[d]) && at->n_pert[d] >= 0))
-            return fail(PZ_EINVAL, "pz_create: n_e and n_pert must be finite and >= 0");
-        if (d > 0 && !(at->m[d] > at->m[d - 1])) return fail(PZ_EINVAL, "pz_create: m must be strictly increasing");
+            return fail(PZ_EINVAL, w + ": n_e and n_pert must be finite and >= 0");
+        if (d > 0 && !(at->m[d] > at->m[d - 1])) return fail(PZ_EINVAL, w + ": m must be strictly increasing");
     }
     for (int s = 0; s < ns; ++s) {
-        if (!finite_pos(at->mass_amu[s])) return fail(PZ_EINVAL, "pz_create: mass_amu must be > 0");
+        if (!finite_pos(at->mass_amu[s])) return fail(PZ_EINVAL, w + ": mass_amu must be > 0");
         for (int d = 0; d < nd; ++d) {
             double p = at->pop[(size_t)s * nd + d];
-            if (!(std::isfinite(p) && p >= 0)) return fail(PZ_EINVAL, "pz_create: pop must be finite and >= 0");
+            if (!(std::isfinite(p) && p >= 0)) return fail(PZ_EINVAL, w + ": pop must be finite and >= 0");
         }
     }
-    const int64_t nlam = at->n_lambda;
-    for (int64_t k = 0; k < (int64_t)nd * nlam; ++k)
-        if (!finite_pos(at->kappa_c[k])) return fail(PZ_EINVAL, "pz_create: kappa_c must be finite and > 0");
+    for (int64_t k = 0; k < (int64_t)nd * at->n_lambda; ++k)
+        if (!finite_pos(at->kappa_c[k])) return fail(PZ_EINVAL, w + ": kappa_c must be finite and > 0");
+    return PZ_OK;
+}
+
+static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, const int64_t *sub_off,
+                             const int32_t *sub_idx, pz_precision prec, pz_ctx **out, const char *who) {
+    const std::string w(who);
+    if (!out) return fail(PZ_EINVAL, w + ": out is NULL");
+    *out = nullptr;
+    if (!atv || !ll) return fail(PZ_EINVAL, w + ": atmos or lines is NULL");
+    if (S < 1 || S > 512) return fail(PZ_EINVAL, w + ": n_stars must be in [1, 512]");
+    if (prec != PZ_FP64 && prec != PZ_MIXED) return fail(PZ_EINVAL, w + ": unknown precision");
+    for (int st = 0; st < S; ++st) PZ_TRY(check_atmos(atv + st, st ? atv : nullptr, who));
+    const pz_atmos *at0 = atv;
+    const int nd = at0->n_depth, ns = at0->n_species;
+    const int64_t nlam = at0->n_lambda;
+    if (ll->n_lines < 0 || ll->n_lines > 2000000000) return fail(PZ_EINVAL, w + ": n_lines out of range");
+    if (ll->half_window < 0 || ll->half_window > 500000) return fail(PZ_EINVAL, w + ": half_window must be in [0, 5e5]");
     const int64_t nl = ll->n_lines;
     if (nl > 0 && (!ll->lambda_nm || !ll->log_gf || !ll->E_low_eV || !ll->log_gamma_rad || !ll->log_gamma4 ||
                    !ll->log_gamma6 || !ll->species))
-        return fail(PZ_EINVAL, "pz_create: a line array is NULL");
+        return fail(PZ_EINVAL, w + ": a line array is NULL");
     for (int64_t l = 0; l < nl; ++l) {
-        if (!finite_pos(ll->lambda_nm[l])) return fail(PZ_EINVAL, "pz_create: lambda_nm must be finite and > 0");
+        if (!finite_pos(ll->lambda_nm[l])) return fail(PZ_EINVAL, w + ": lambda_nm must be finite and > 0");
         if (!std::isfinite(ll->log_gf[l]) || !std::isfinite(ll->E_low_eV[l]) || !std::isfinite(ll->log_gamma_rad[l]) ||
             !std::isfinite(ll->log_gamma4[l]) || !std::isfinite(ll->log_gamma6[l]))
-            return fail(PZ_EINVAL, "pz_create: non-finite line parameter");
-        if (ll->species[l] < 0 || ll->species[l] >= ns) return fail(PZ_EINVAL, "pz_create: species out of range");
+            return fail(PZ_EINVAL, w + ": non-finite line parameter");
+        if (ll->species[l] < 0 || ll->species[l] >= ns) return fail(PZ_EINVAL, w + ": species out of range");
+    }
+    if (sub_off) {
+        if (sub_off[0] != 0) return fail(PZ_EINVAL, w + ": subset_offsets[0] must be 0");
+        for (int st = 0; st < S; ++st)
+            if (sub_off[st + 1] < sub_off[st]) return fail(PZ_EINVAL, w + ": subset_offsets must be non-decreasing");
+        if (sub_off[S] > 0 && !sub_idx) return fail(PZ_EINVAL, w + ": subset_index is NULL");
+        if (sub_off[S] > 2000000000) return fail(PZ_EINVAL, w + ": too many subset entries");
+        for (int64_t k = 0; k < sub_off[S]; ++k)
+            if (sub_idx[k] < 0 || sub_idx[k] >= nl) return fail(PZ_EINVAL, w + ": subset_index out of range");
+    } else if ((int64_t)S * nl > 2000000000) {
+        return fail(PZ_EINVAL, w + ": n_stars x n_lines too large");
     }
 
     pz_ctx *c = new pz_ctx();
     int dev = 0;
     cudaGetDevice(&dev);
     c->device = dev;
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
     c->prec = prec;
+    c->S = S;
     c->nd = nd;
     c->ns = ns;
     c->nlam = nlam;
     c->ld = ((nlam + 511) / 512) * 512;
-    c->lambda0_nm = at->lambda0_nm;
-    c->R = at->R_grid;
-    c->lnr = std::log1p(1.0 / at->R_grid);
-    c->xi = at->xi_cms;
+    c->lambda0_nm = at0->lambda0_nm;
+    c->R = at0->R_grid;
+    c->lnr = std::log1p(1.0 / at0->R_grid);
     c->W = ll->half_window;
     c->nl_caller = nl;
 
@@ -258,18 +331,31 @@ static pz_status create_impl(const pz_atmos *at, const pz_linelist *ll, pz_preci
         return st;
     };
     if (ensure_device_tables() != PZ_OK) return bail(PZ_ECUDA);
+    if (cuda_check(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "stream")) return bail(PZ_ECUDA);
 
-    // ---- lines: centre placement, drop, sort ----
+    // ---- lines: centre placement, drop, sort within each star ----
     const double W = c->W;
     std::vector<double> x(nl);
-    std::vector<int64_t> keep;
-    keep.reserve(nl);
+    std::vector<char> inwin(nl);
     for (int64_t l = 0; l < nl; ++l) {
-        x[l] = std::log(ll->lambda_nm[l] / at->lambda0_nm) / c->lnr;
+        x[l] = std::log(ll->lambda_nm[l] / at0->lambda0_nm) / c->lnr;
         double il = std::floor(x[l] + 0.5);
-        if (il >= -W && il <= (double)(nlam - 1) + W) keep.push_back(l);
+        inwin[l] = il >= -W && il <= (double)(nlam - 1) + W;
     }
-    std::stable_sort(keep.begin(), keep.end(), [&](int64_t a, int64_t b) { return x[a] < x[b]; });
+    std::vector<int64_t> keep;
+    std::vector<int32_t> kstar;
+    c->h_line_off.assign(S + 1, 0);
+    for (int st = 0; st < S; ++st) {
+        const size_t first = keep.size();
+        const int64_t a = sub_off ? sub_off[st] : 0, b = sub_off ? sub_off[st + 1] : nl;
+        for (int64_t k = a; k < b; ++k) {
+            const int64_t l = sub_off ? (int64_t)sub_idx[k] : k;
+            if (inwin[l]) keep.push_back(l);
+        }
+        std::stable_sort(keep.begin() + first, keep.end(), [&](int64_t p, int64_t q) { return x[p] < x[q]; });
+        kstar.resize(keep.size(), st);
+        c->h_line_off[st + 1] = (int64_t)keep.size();
+    }
     const int64_t n = (int64_t)keep.size();
     c->L.n = n;
     std::vector<int32_t> orig(n), il32(n), sp(n);
@@ -304,38 +390,53 @@ static pz_status create_impl(const pz_atmos *at, const pz_linelist *ll, pz_preci
     }
     c->n_evals = evals * nd;
     c->h_il = il32;
-    if (upload(&c->L.orig, orig, "lines") || upload(&c->L.il32, il32, "lines") || upload(&c->L.ilf, ilf, "lines") ||
-        upload(&c->L.frac, frac, "lines") || upload(&c->L.sp, sp, "lines") || upload(&c->L.E, E, "lines") ||
-        upload(&c->L.lamcm, lamcm, "lines") || upload(&c->L.grad, grad, "lines") || upload(&c->L.g4, g4, "lines") ||
-        upload(&c->L.g6base, g6, "lines") || upload(&c->L.g6, g6, "lines") || upload(&c->L.Q, Qf, "lines") ||
-        upload(&c->L.Qbase, Qb, "lines") || upload(&c->L.x64, x64, "lines") || upload(&c->L.lg_gf, lg_gf, "lines") ||
-        upload(&c->L.lg_rad, lg_rad, "lines") || upload(&c->L.lg_4, lg_4, "lines") ||
-        upload(&c->L.lg_6, lg_6, "lines") || upload(&c->L.dgf, zeros, "lines") || upload(&c->L.dg6, zeros, "lines"))
+    std::vector<float> mzeros(std::max<int64_t>(nl, 1), 0.0f);
+    if (upload(&c->L.orig, orig, "lines") || upload(&c->L.star, kstar, "lines") || upload(&c->L.il32, il32, "lines") ||
+        upload(&c->L.ilf, ilf, "lines") || upload(&c->L.frac, frac, "lines") || upload(&c->L.sp, sp, "lines") ||
+        upload(&c->L.E, E, "lines") || upload(&c->L.lamcm, lamcm, "lines") || upload(&c->L.grad, grad, "lines") ||
+        upload(&c->L.g4, g4, "lines") || upload(&c->L.g6base, g6, "lines") || upload(&c->L.g6, g6, "lines") ||
+        upload(&c->L.Q, Qf, "lines") || upload(&c->L.Qbase, Qb, "lines") || upload(&c->L.x64, x64, "lines") ||
+        upload(&c->L.lg_gf, lg_gf, "lines") || upload(&c->L.lg_rad, lg_rad, "lines") ||
+        upload(&c->L.lg_4, lg_4, "lines") || upload(&c->L.lg_6, lg_6, "lines") || upload(&c->L.dgf, zeros, "lines") ||
+        upload(&c->L.dg6, zeros, "lines") || upload(&c->d_mdgf, mzeros, "corrections") ||
+        upload(&c->d_mdg6, mzeros, "corrections") || upload(&c->d_line_off, c->h_line_off, "lines"))
         return bail(PZ_ENOMEM);
 
-    // ---- depth and species tables ----
-    c->h_m.assign(at->m, at->m + nd);
-    c->h_T.assign(at->T, at->T + nd);
-    std::vector<float> bh(nd), bl(nd), ne(nd), npert(nd), c2T(nd);
-    std::vector<double> ne64(at->n_e, at->n_e + nd), np64(at->n_pert, at->n_pert + nd), rho64(at->rho, at->rho + nd);
-    for (int d = 0; d < nd; ++d) {
-        double beta = kEV / (kKB * at->T[d]);
-        bh[d] = (float)beta;
-        bl[d] = (float)(beta - (double)bh[d]);
-        ne[d] = (float)at->n_e[d];
-        npert[d] = (float)at->n_pert[d];
-        c2T[d] = (float)(kC2 / at->T[d]);
-    }
-    std::vector<float> invdv((size_t)ns * nd), Rf((size_t)ns * nd);
-    std::vector<double> Rb((size_t)ns * nd), pop64(at->pop, at->pop + (size_t)ns * nd), mass64(at->mass_amu, at->mass_amu + ns);
-    for (int s = 0; s < ns; ++s)
+    // ---- depth and species tables, [S][...] ----
+    const size_t SD = (size_t)S * nd, SSD = (size_t)S * ns * nd;
+    c->h_m.resize(SD);
+    c->h_T.resize(SD);
+    std::vector<float> bh(SD), bl(SD), ne(SD), npert(SD), c2T(SD), invdv(SSD), Rf(SSD);
+    std::vector<double> ne64(SD), np64(SD), rho64(SD), Rb(SSD), pop64(SSD), mass64((size_t)S * ns), xi64(S);
+    for (int st = 0; st < S; ++st) {
+        const pz_atmos *at = atv + st;
+        xi64[st] = at->xi_cms;
         for (int d = 0; d < nd; ++d) {
-            double dv = std::sqrt(2.0 * kKB * at->T[d] / (at->mass_amu[s] * kAMU) + c->xi * c->xi);
-            size_t id = (size_t)s * nd + d;
-            invdv[id] = (float)(1.0 / dv);
-            Rb[id] = (1.0 / dv) * at->pop[id] / at->rho[d];
-            Rf[id] = (float)Rb[id];
+            const size_t o = (size_t)st * nd + d;
+            c->h_m[o] = at->m[d];
+            c->h_T[o] = at->T[d];
+            double beta = kEV / (kKB * at->T[d]);
+            bh[o] = (float)beta;
+            bl[o] = (float)(beta - (double)bh[o]);
+            ne[o] = (float)at->n_e[d];
+            npert[o] = (float)at->n_pert[d];
+            c2T[o] = (float)(kC2 / at->T[d]);
+            ne64[o] = at->n_e[d];
+            np64[o] = at->n_pert[d];
+            rho64[o] = at->rho[d];
         }
+        for (int s = 0; s < ns; ++s) {
+            mass64[(size_t)st * ns + s] = at->mass_amu[s];
+            for (int d = 0; d < nd; ++d) {
+                double dv = std::sqrt(2.0 * kKB * at->T[d] / (at->mass_amu[s] * kAMU) + at->xi_cms * at->xi_cms);
+                const size_t id = (size_t)s * nd + d, o = (size_t)st * ns * nd + id;
+                invdv[o] = (float)(1.0 / dv);
+                pop64[o] = at->pop[id];
+                Rb[o] = (1.0 / dv) * at->pop[id] / at->rho[d];
+                Rf[o] = (float)Rb[o];
+            }
+        }
+    }
     c->h_invdv = invdv;
     std::vector<double> dab(1, 0.0);
     std::vector<int32_t> eos(ns, -1);
@@ -344,44 +445,75 @@ static pz_status create_impl(const pz_atmos *at, const pz_linelist *ll, pz_preci
         upload(&c->d_c2T, c2T, "depth") || upload(&c->d_ne64, ne64, "depth") || upload(&c->d_npert64, np64, "depth") ||
         upload(&c->d_rho64, rho64, "depth") || upload(&c->d_invdv, invdv, "species") || upload(&c->d_R, Rf, "species") ||
         upload(&c->d_Rbase, Rb, "species") || upload(&c->d_pop64, pop64, "species") ||
-        upload(&c->d_mass64, mass64, "species") || build_thresholds(c) || upload(&c->d_dab, dab, "abund") ||
-        upload(&c->d_eos, eos, "abund"))
+        upload(&c->d_mass64, mass64, "species") || upload(&c->d_xi64, xi64, "species") || build_thresholds(c) ||
+        upload(&c->d_dab, dab, "abund") || upload(&c->d_eos, eos, "abund"))
         return bail(PZ_ENOMEM);
 
-    // ---- continuum opacity [nd][ld] ----
-    if (dalloc(&c->d_kc, (size_t)nd * c->ld, "kappa_c")) return bail(PZ_ENOMEM);
-    if (cuda_check(cudaMemset(c->d_kc, 0, sizeof(double) * nd * c->ld), "kappa_c") ||
-        cuda_check(cudaMemcpy2D(c->d_kc, c->ld * sizeof(double), at->kappa_c, nlam * sizeof(double),
-                                nlam * sizeof(double), nd, cudaMemcpyHostToDevice),
-                   "kappa_c"))
-        return bail(PZ_ECUDA);
+    // ---- continuum opacity [S][nd][ld] ----
+    if (dalloc(&c->d_kc, SD * c->ld, "kappa_c")) return bail(PZ_ENOMEM);
+    if (cuda_check(cudaMemset(c->d_kc, 0, sizeof(double) * SD * c->ld), "kappa_c")) return bail(PZ_ECUDA);
+    for (int st = 0; st < S; ++st)
+        if (cuda_check(cudaMemcpy2D(c->d_kc + (size_t)st * nd * c->ld, c->ld * sizeof(double), atv[st].kappa_c,
+                                    nlam * sizeof(double), nlam * sizeof(double), nd, cudaMemcpyHostToDevice),
+                       "kappa_c"))
+            return bail(PZ_ECUDA);
 
     // ---- resident buffers ----
     size_t ksz = (prec == PZ_MIXED) ? sizeof(float) : sizeof(double);
-    if (cuda_check(cudaMalloc(&c->d_kline, ksz * nd * c->ld), "kappa_line buffer") ||
-        (prec == PZ_MIXED && dalloc(&c->d_knear, (size_t)nd * c->ld, "kappa_line buffer")) ||
-        dalloc(&c->d_F, nlam, "flux") || dalloc(&c->d_Fc, nlam, "flux"))
+    if (cuda_check(cudaMalloc(&c->d_kline, ksz * SD * c->ld), "kappa_line buffer") ||
+        (prec == PZ_MIXED && dalloc(&c->d_knear, SD * c->ld, "kappa_line buffer")) ||
+        dalloc(&c->d_F, (size_t)S * nlam, "flux") || dalloc(&c->d_Fc, (size_t)S * nlam, "flux") ||
+        dalloc(&c->d_ctr, 4, "work counters"))
         return bail(PZ_ENOMEM);
-    if (build_tiles(c) != PZ_OK) return bail(PZ_ENOMEM);
-    if (cuda_check(cudaDeviceSynchronize(), "pz_create")) return bail(PZ_ECUDA);
+    if (prec == PZ_MIXED && cuda_check(cudaMemset(c->d_knear, 0, sizeof(float) * SD * c->ld), "kappa_line buffer"))
+        return bail(PZ_ECUDA);
+    if (build_items(c) != PZ_OK) return bail(PZ_ENOMEM);
+    if (cuda_check(cudaDeviceSynchronize(), who)) return bail(PZ_ECUDA);
     *out = c;
     return PZ_OK;
 }
 
+// instrument outputs [S][n]
 static pz_status ensure_out_buffers(pz_ctx *c, int64_t n) {
     if (c->d_g && c->pix_cap >= n) return PZ_OK;
+    drop_graph(c);
     dfree(c->d_g);
     dfree(c->d_gc);
+    dfree(c->d_dLdf);
     c->d_g = c->d_gc = nullptr;
-    PZ_TRY(dalloc(&c->d_g, n, "instrument output"));
-    PZ_TRY(dalloc(&c->d_gc, n, "instrument output"));
+    c->d_dLdf = nullptr;
+    PZ_TRY(dalloc(&c->d_g, (size_t)c->S * n, "instrument output"));
+    PZ_TRY(dalloc(&c->d_gc, (size_t)c->S * n, "instrument output"));
     c->pix_cap = n;
     return PZ_OK;
 }
 
-__global__ void k_gather_f32(int64_t n, const int32_t *orig, const float *src, float *dst) {
-    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l < n) dst[l] = src[orig[l]];
+static pz_status ensure_backward_buffers(pz_ctx *c) {
+    const size_t SD = (size_t)c->S * c->nd;
+    if (!c->d_dFbar) PZ_TRY(dalloc(&c->d_dFbar, (size_t)c->S * c->nlam, "backward scratch"));
+    if (c->prec == PZ_MIXED && !c->d_Gt) PZ_TRY(dalloc(&c->d_Gt, SD * c->ld, "backward scratch"));
+    if (c->prec == PZ_FP64 && !c->d_Gt64) PZ_TRY(dalloc(&c->d_Gt64, SD * c->ld, "backward scratch"));
+    if (!c->d_gacc) PZ_TRY(dalloc(&c->d_gacc, 2 * std::max<int64_t>(c->L.n, 1), "backward scratch"));
+    if (!c->d_gline) PZ_TRY(dalloc(&c->d_gline, 2 * std::max<int64_t>(c->nl_caller, 1), "backward scratch"));
+    if (c->n_elem > 0 && !c->d_gab) PZ_TRY(dalloc(&c->d_gab, c->n_elem, "backward scratch"));
+    return PZ_OK;
+}
+
+// The backward stages after the objective's seed dL/df: instrument adjoint, transfer
+// adjoint, line gradients, finalisation into caller order.
+static pz_status enqueue_backward(pz_ctx *c, const float *dLdf, float *g_gf, float *g_g6, float *g_ab,
+                                  cudaStream_t s) {
+    PZ_CUDA(timed(c, s, PZ_K_INST_ADJOINT, [&] { return launch_inst_adjoint(c, dLdf, s); }), "instrument adjoint");
+    PZ_CUDA(timed(c, s, PZ_K_RT_ADJOINT, [&] { return launch_rt_adjoint(c, s); }), "transfer adjoint");
+    PZ_CUDA(cudaMemsetAsync(c->d_gacc, 0, sizeof(double) * 2 * std::max<int64_t>(c->L.n, 1), s), "backward");
+    if (c->L.n > 0) {
+        PZ_CUDA(timed(c, s, PZ_K_LINE_BWD,
+                      [&] { return c->prec == PZ_MIXED ? launch_line_bwd_mixed(c, s) : launch_line_bwd_fp64(c, s); }),
+                "line gradient kernel");
+    }
+    PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_grad_finalize(c, g_gf, g_g6, g_ab, s); }),
+            "gradient finalize");
+    return PZ_OK;
 }
 
 __global__ void k_f32_to_f64(int n, const float *a, double *b) {
@@ -389,10 +521,11 @@ __global__ void k_f32_to_f64(int n, const float *a, double *b) {
     if (k < n) b[k] = (double)a[k];
 }
 
-__global__ void k_d2f_2d(int64_t nlam, int64_t ld, int nd, const double *a, float *b) {
+// rows of [rows][ld] FP64 -> [rows][nlam] FP32; row = blockIdx.y
+__global__ void k_d2f_2d(int64_t nlam, int64_t ld, const double *a, float *b) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int d = blockIdx.y;
-    if (i < nlam) b[(int64_t)d * nlam + i] = (float)a[(int64_t)d * ld + i];
+    int64_t r = blockIdx.y;
+    if (i < nlam) b[r * nlam + i] = (float)a[r * ld + i];
 }
 
 }  // namespace pz
@@ -402,7 +535,13 @@ using namespace pz;
 extern "C" {
 
 pz_status pz_create(const pz_atmos *atmos, const pz_linelist *lines, pz_precision precision, pz_ctx **out) {
-    return create_impl(atmos, lines, precision, out);
+    return create_impl(1, atmos, lines, nullptr, nullptr, precision, out, "pz_create");
+}
+
+pz_status pz_create_batch(int32_t n_stars, const pz_atmos *atmos, const pz_linelist *lines,
+                          const int64_t *subset_offsets, const int32_t *subset_index, pz_precision precision,
+                          pz_ctx **out) {
+    return create_impl(n_stars, atmos, lines, subset_offsets, subset_index, precision, out, "pz_create_batch");
 }
 
 pz_status pz_destroy(pz_ctx *ctx) {
@@ -417,6 +556,13 @@ const char *pz_last_error(void) { return g_err.c_str(); }
 int64_t pz_eval_count(const pz_ctx *ctx) { return ctx ? ctx->n_evals : 0; }
 
 int32_t pz_last_launch_count(const pz_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+int32_t pz_n_stars(const pz_ctx *ctx) { return ctx ? ctx->S : 0; }
+
+int64_t pz_star_lines(const pz_ctx *ctx, int32_t star) {
+    if (!ctx || star < 0 || star >= ctx->S) return -1;
+    return ctx->h_line_off[star + 1] - ctx->h_line_off[star];
+}
 
 pz_status pz_set_tiling(pz_ctx *c, int32_t J, int32_t DS, int32_t GW, int32_t LC, int32_t MINB) {
     if (!c) return fail(PZ_EINVAL, "pz_set_tiling: ctx is NULL");
@@ -436,11 +582,10 @@ pz_status pz_set_tiling(pz_ctx *c, int32_t J, int32_t DS, int32_t GW, int32_t LC
     size_t smem_bwd = (size_t)t.LCB * t.DS * t.GW * 64 + t.LCB * 16 + (size_t)t.LCB * t.GW * 8;
     if (smem_fwd > 200 * 1024 || smem_bwd > 200 * 1024)
         return fail(PZ_EINVAL, "pz_set_tiling: shared-memory chunk too large");
-    bool retile = t.J != c->tiling.J;
-    bool reslab = t.DS != c->tiling.DS || t.GW != c->tiling.GW;
+    drop_graph(c);
     c->tiling = t;
-    if (retile) PZ_TRY(build_tiles(c));
-    if (reslab) PZ_TRY(build_thresholds(c));
+    PZ_TRY(build_thresholds(c));
+    PZ_TRY(build_items(c));
     return PZ_OK;
 }
 
@@ -455,32 +600,21 @@ pz_status pz_set_corrections(pz_ctx *c, const float *dgf, const float *dg6, cons
     }
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
-    const int64_t n = c->L.n;
-    std::vector<int32_t> horig;
-    auto set_line = [&](const float *src, float *dst, const char *what) -> pz_status {
+    const int64_t n = c->nl_caller;
+    auto set_master = [&](const float *src, float *dst, const char *what) -> pz_status {
         if (!src) return cuda_check(cudaMemsetAsync(dst, 0, sizeof(float) * std::max<int64_t>(n, 1), s), what);
         if (n == 0) return PZ_OK;
-        if (is_device_ptr(src)) {
-            cudaError_t e = timed(c, s, PZ_K_OTHER, [&] {
-                k_gather_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c->L.orig, src, dst);
-                return cudaGetLastError();
-            });
-            c->launches++;
-            return cuda_check(e, what);
-        }
-        if (horig.empty()) {
-            horig.resize(n);
-            PZ_CUDA(cudaMemcpy(horig.data(), c->L.orig, sizeof(int32_t) * n, cudaMemcpyDeviceToHost), what);
-        }
-        std::vector<float> tmp(n);
-        for (int64_t k = 0; k < n; ++k) tmp[k] = src[horig[k]];
-        PZ_CUDA(cudaMemcpy(dst, tmp.data(), sizeof(float) * n, cudaMemcpyHostToDevice), what);
-        return PZ_OK;
+        if (is_device_ptr(src))
+            return cuda_check(cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyDeviceToDevice, s), what);
+        PZ_CUDA(cudaStreamSynchronize(s), what);
+        return cuda_check(cudaMemcpy(dst, src, sizeof(float) * n, cudaMemcpyHostToDevice), what);
     };
-    PZ_TRY(set_line(dgf, c->L.dgf, "dlog_gf"));
-    PZ_TRY(set_line(dg6, c->L.dg6, "dlog_gamma6"));
+    PZ_TRY(set_master(dgf, c->d_mdgf, "dlog_gf"));
+    PZ_TRY(set_master(dg6, c->d_mdg6, "dlog_gamma6"));
     if (dab) {
         if (n_elem != c->n_elem) {
+            drop_graph(c);
+            PZ_CUDA(cudaStreamSynchronize(s), "dabund");
             dfree(c->d_dab);
             dfree(c->d_gab);
             c->d_dab = nullptr;
@@ -488,6 +622,7 @@ pz_status pz_set_corrections(pz_ctx *c, const float *dgf, const float *dg6, cons
             PZ_TRY(dalloc(&c->d_dab, n_elem, "dabund"));
         }
         std::vector<int32_t> heos(eos, eos + c->ns);
+        PZ_CUDA(cudaStreamSynchronize(s), "elem_of_species");
         PZ_CUDA(cudaMemcpy(c->d_eos, heos.data(), sizeof(int32_t) * c->ns, cudaMemcpyHostToDevice), "elem_of_species");
         if (is_device_ptr(dab)) {
             PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] {
@@ -502,12 +637,31 @@ pz_status pz_set_corrections(pz_ctx *c, const float *dgf, const float *dg6, cons
         }
         c->n_elem = n_elem;
     } else {
+        if (c->n_elem != 0) drop_graph(c);
         c->n_elem = 0;
         std::vector<int32_t> heos(c->ns, -1);
+        PZ_CUDA(cudaStreamSynchronize(s), "elem_of_species");
         PZ_CUDA(cudaMemcpy(c->d_eos, heos.data(), sizeof(int32_t) * c->ns, cudaMemcpyHostToDevice), "elem_of_species");
     }
     PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_apply_corrections(c, s); }), "apply corrections");
     c->have_kline = c->have_flux = c->have_inst = false;
+    return PZ_OK;
+}
+
+pz_status pz_get_corrections(pz_ctx *c, float *dgf, float *dg6, float *dab, void *stream) {
+    if (!c) return fail(PZ_EINVAL, "pz_get_corrections: ctx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->nl_caller;
+    if (dgf && n > 0) PZ_CUDA(cudaMemcpyAsync(dgf, c->d_mdgf, sizeof(float) * n, cudaMemcpyDefault, s), "dlog_gf");
+    if (dg6 && n > 0) PZ_CUDA(cudaMemcpyAsync(dg6, c->d_mdg6, sizeof(float) * n, cudaMemcpyDefault, s), "dlog_gamma6");
+    if (dab && c->n_elem > 0) {
+        std::vector<double> h(c->n_elem);
+        PZ_CUDA(cudaMemcpyAsync(h.data(), c->d_dab, sizeof(double) * c->n_elem, cudaMemcpyDeviceToHost, s), "dabund");
+        PZ_CUDA(cudaStreamSynchronize(s), "dabund");
+        std::vector<float> f(h.begin(), h.end());
+        PZ_CUDA(cudaMemcpy(dab, f.data(), sizeof(float) * c->n_elem, cudaMemcpyDefault), "dabund");
+    }
+    PZ_CUDA(cudaStreamSynchronize(s), "pz_get_corrections");
     return PZ_OK;
 }
 
@@ -519,14 +673,15 @@ pz_status pz_line_opacity(pz_ctx *c, float *kappa, void *stream) {
                   [&] { return c->prec == PZ_MIXED ? launch_line_fwd_mixed(c, s) : launch_line_fwd_fp64(c, s); }),
             "line opacity kernel");
     if (kappa) {
+        const size_t rows = (size_t)c->S * c->nd;
         if (c->prec == PZ_MIXED) {
             PZ_CUDA(cudaMemcpy2DAsync(kappa, c->nlam * sizeof(float), c->d_kline, c->ld * sizeof(float),
-                                      c->nlam * sizeof(float), c->nd, cudaMemcpyDeviceToDevice, s),
+                                      c->nlam * sizeof(float), rows, cudaMemcpyDeviceToDevice, s),
                     "copy kappa_line");
         } else {
-            dim3 grid((unsigned)((c->nlam + 255) / 256), c->nd);
+            dim3 grid((unsigned)((c->nlam + 255) / 256), (unsigned)rows);
             PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] {
-                        k_d2f_2d<<<grid, 256, 0, s>>>(c->nlam, c->ld, c->nd, (const double *)c->d_kline, kappa);
+                        k_d2f_2d<<<grid, 256, 0, s>>>(c->nlam, c->ld, (const double *)c->d_kline, kappa);
                         return cudaGetLastError();
                     }),
                     "copy kappa_line");
@@ -544,8 +699,9 @@ pz_status pz_flux(pz_ctx *c, double *F, double *Fc, void *stream) {
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
     PZ_CUDA(timed(c, s, PZ_K_FLUX, [&] { return launch_flux(c, s); }), "flux kernel");
-    if (F) PZ_CUDA(cudaMemcpyAsync(F, c->d_F, sizeof(double) * c->nlam, cudaMemcpyDeviceToDevice, s), "copy F");
-    if (Fc) PZ_CUDA(cudaMemcpyAsync(Fc, c->d_Fc, sizeof(double) * c->nlam, cudaMemcpyDeviceToDevice, s), "copy Fc");
+    const size_t nb = sizeof(double) * c->S * c->nlam;
+    if (F) PZ_CUDA(cudaMemcpyAsync(F, c->d_F, nb, cudaMemcpyDeviceToDevice, s), "copy F");
+    if (Fc) PZ_CUDA(cudaMemcpyAsync(Fc, c->d_Fc, nb, cudaMemcpyDeviceToDevice, s), "copy Fc");
     c->have_flux = true;
     c->have_inst = false;
     return PZ_OK;
@@ -559,6 +715,7 @@ pz_status pz_instrument(pz_ctx *c, double v_r, double v_b, double R_lsf, const d
     c->launches = 0;
     if (n_pix < 0) return fail(PZ_EINVAL, "pz_instrument: n_pix < 0");
     if (n_pix == 0) {
+        if (!c->identity_inst) drop_graph(c);
         PZ_TRY(ensure_out_buffers(c, c->nlam));
         c->identity_inst = true;
         c->n_out = c->nlam;
@@ -579,7 +736,9 @@ pz_status pz_instrument(pz_ctx *c, double v_r, double v_b, double R_lsf, const d
         bool same = !c->identity_inst && c->inst_key[0] == v_r && c->inst_key[1] == v_b && c->inst_key[2] == R_lsf &&
                     (int64_t)c->pix_key.size() == n_pix && std::equal(pix, pix + n_pix, c->pix_key.begin());
         if (!same) {
+            drop_graph(c);
             if (c->n_pix < n_pix || c->max_taps < mt) {
+                PZ_CUDA(cudaStreamSynchronize(s), "instrument");
                 dfree(c->d_tap0);
                 dfree(c->d_ntap);
                 dfree(c->d_tapw);
@@ -611,6 +770,7 @@ pz_status pz_instrument(pz_ctx *c, double v_r, double v_b, double R_lsf, const d
             if (st != PZ_OK) return st;
             if (herr) {
                 c->identity_inst = true;
+                c->n_out = 0;
                 c->pix_key.clear();
                 return fail(PZ_EINVAL, "pz_instrument: a pixel has no tap inside the synthesis grid");
             }
@@ -636,7 +796,8 @@ pz_status pz_loss_chi2(pz_ctx *c, const float *y, const float *w, int64_t n, dou
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
     if (loss) PZ_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s), "loss");
-    PZ_CUDA(timed(c, s, PZ_K_LOSS, [&] { return launch_loss(c, y, w, n, loss, dLdf, s); }), "loss kernel");
+    PZ_CUDA(timed(c, s, PZ_K_LOSS, [&] { return launch_loss(c, y, w, (int64_t)c->S * n, loss, dLdf, s); }),
+            "loss kernel");
     return PZ_OK;
 }
 
@@ -646,25 +807,73 @@ pz_status pz_backward(pz_ctx *c, const float *dLdf, float *g_gf, float *g_g6, fl
     if (!dLdf) return fail(PZ_EINVAL, "pz_backward: dL_df is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
-    if (!c->d_dFbar) PZ_TRY(dalloc(&c->d_dFbar, c->nlam, "backward scratch"));
-    if (c->prec == PZ_MIXED && !c->d_Gt) PZ_TRY(dalloc(&c->d_Gt, (size_t)c->nd * c->ld, "backward scratch"));
-    if (c->prec == PZ_FP64 && !c->d_Gt64) PZ_TRY(dalloc(&c->d_Gt64, (size_t)c->nd * c->ld, "backward scratch"));
-    if (!c->d_gacc) PZ_TRY(dalloc(&c->d_gacc, 2 * std::max<int64_t>(c->L.n, 1), "backward scratch"));
-    if (c->n_elem > 0 && !c->d_gab) PZ_TRY(dalloc(&c->d_gab, c->n_elem, "backward scratch"));
+    PZ_TRY(ensure_backward_buffers(c));
+    return enqueue_backward(c, dLdf, g_gf, g_g6, g_ab, s);
+}
 
-    PZ_CUDA(timed(c, s, PZ_K_INST_ADJOINT, [&] { return launch_inst_adjoint(c, dLdf, s); }), "instrument adjoint");
-    PZ_CUDA(timed(c, s, PZ_K_RT_ADJOINT, [&] { return launch_rt_adjoint(c, s); }), "transfer adjoint");
-    PZ_CUDA(cudaMemsetAsync(c->d_gacc, 0, sizeof(double) * 2 * std::max<int64_t>(c->L.n, 1), s), "backward");
-    if (c->L.n > 0) {
-        PZ_CUDA(timed(c, s, PZ_K_LINE_BWD,
-                      [&] { return c->prec == PZ_MIXED ? launch_line_bwd_mixed(c, s) : launch_line_bwd_fp64(c, s); }),
-                "line gradient kernel");
+// One calibration step: corrections -> line opacity -> flux -> instrument -> chi^2 ->
+// adjoint -> gradients -> delta -= lr * gradient, enqueued on the capture stream.
+static pz_status enqueue_step(pz_ctx *c, const float *y, const float *w, double *loss, float *g_gf, float *g_g6,
+                              float *g_ab, float lr_gf, float lr_g6, float lr_ab, cudaStream_t s) {
+    PZ_CUDA(launch_apply_corrections(c, s), "apply corrections");
+    PZ_CUDA(c->prec == PZ_MIXED ? launch_line_fwd_mixed(c, s) : launch_line_fwd_fp64(c, s), "line opacity kernel");
+    PZ_CUDA(launch_flux(c, s), "flux kernel");
+    PZ_CUDA(launch_inst_apply(c, nullptr, s), "instrument apply");
+    if (loss) PZ_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s), "loss");
+    PZ_CUDA(launch_loss(c, y, w, (int64_t)c->S * c->n_out, loss, c->d_dLdf, s), "loss kernel");
+    PZ_TRY(enqueue_backward(c, c->d_dLdf, g_gf, g_g6, g_ab, s));
+    PZ_CUDA(launch_update(c, lr_gf, lr_g6, lr_ab, s), "update");
+    return PZ_OK;
+}
+
+pz_status pz_calib_step(pz_ctx *c, const float *y, const float *w, int64_t n, float lr_gf, float lr_g6, float lr_ab,
+                        double *loss, float *g_gf, float *g_g6, float *g_ab, void *stream) {
+    if (!c) return fail(PZ_EINVAL, "pz_calib_step: ctx is NULL");
+    if (c->n_out <= 0) return fail(PZ_ESTATE, "pz_calib_step: call pz_instrument once first");
+    if (!y) return fail(PZ_EINVAL, "pz_calib_step: y is NULL");
+    if (n != c->n_out) return fail(PZ_EINVAL, "pz_calib_step: n differs from the instrument output size");
+    if (!std::isfinite(lr_gf) || !std::isfinite(lr_g6) || !std::isfinite(lr_ab))
+        return fail(PZ_EINVAL, "pz_calib_step: learning rates must be finite");
+    cudaStream_t s = (cudaStream_t)stream;
+    PZ_TRY(ensure_backward_buffers(c));
+    if (!c->d_dLdf) PZ_TRY(dalloc(&c->d_dLdf, (size_t)c->S * c->pix_cap, "step seed"));
+    StepGraph &G = c->graph;
+    const void *key[6] = {y, w, loss, g_gf, g_g6, g_ab};
+    bool same = G.exec && G.n == n && G.lr[0] == lr_gf && G.lr[1] == lr_g6 && G.lr[2] == lr_ab;
+    for (int k = 0; k < 6 && same; ++k) same = G.key[k] == key[k];
+    if (!same) {
+        drop_graph(c);
+        PZ_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "pz_calib_step: capture");
+        c->capturing = true;
+        c->launches = 0;
+        pz_status st = enqueue_step(c, y, w, loss, g_gf, g_g6, g_ab, lr_gf, lr_g6, lr_ab, c->cap_stream);
+        c->capturing = false;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (st != PZ_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_check(e, "pz_calib_step: end capture");
+        e = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            G.exec = nullptr;
+            return cuda_check(e, "pz_calib_step: instantiate");
+        }
+        for (int k = 0; k < 6; ++k) G.key[k] = key[k];
+        G.lr[0] = lr_gf;
+        G.lr[1] = lr_g6;
+        G.lr[2] = lr_ab;
+        G.n = n;
+        G.launches = c->launches;
     }
-    if (g_gf) PZ_CUDA(cudaMemsetAsync(g_gf, 0, sizeof(float) * c->nl_caller, s), "backward");
-    if (g_g6) PZ_CUDA(cudaMemsetAsync(g_g6, 0, sizeof(float) * c->nl_caller, s), "backward");
-    if (g_ab && c->n_elem > 0) PZ_CUDA(cudaMemsetAsync(c->d_gab, 0, sizeof(double) * c->n_elem, s), "backward");
-    PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_grad_finalize(c, g_gf, g_g6, g_ab, s); }),
-            "gradient finalize");
+    prof_begin(c, s);
+    cudaError_t e = cudaGraphLaunch(G.exec, s);
+    prof_end(c, s, PZ_K_STEP);
+    PZ_CUDA(e, "pz_calib_step: graph launch");
+    c->launches = G.launches;
+    c->have_kline = c->have_flux = c->have_inst = true;
     return PZ_OK;
 }
 

@@ -53,10 +53,12 @@ struct Tiling {
     int depth_per_cta() const { return DS * GW; }
 };
 
-// Device copy of the per-line data, sorted by fractional centre index.
+// Device copy of the per-line data.  Every star owns a contiguous segment of lines
+// sorted by fractional centre index; orig maps a line to its master (caller) index.
 struct LineTable {
-    int64_t n = 0;              // lines kept (window intersects the grid)
-    int32_t *orig = nullptr;    // caller index of each sorted line
+    int64_t n = 0;              // lines kept over all stars (windows intersect the grid)
+    int32_t *orig = nullptr;    // master index of each line
+    int32_t *star = nullptr;    // star of each line
     float *ilf = nullptr;       // integer centre i_l as float (exact, |i_l| < 2^24)
     int32_t *il32 = nullptr;    // integer centre i_l
     float *frac = nullptr;      // x_l - i_l in [-1/2, 1/2)
@@ -72,58 +74,77 @@ struct LineTable {
     double *x64 = nullptr;      // x_l, FP64 (plain FP64 form)
     float *lg_gf = nullptr;     // log10 gf (caller value; FP64 form)
     float *lg_rad = nullptr, *lg_4 = nullptr, *lg_6 = nullptr;
-    float *dgf = nullptr, *dg6 = nullptr;  // current corrections (sorted order)
+    float *dgf = nullptr, *dg6 = nullptr;  // current corrections (per line)
 };
 
-struct pz_ctx_impl;
+// Captured corrections + fwd + loss + bwd + update step (pz_calib_step), re-captured
+// when any of its arguments changes.
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    const void *key[6] = {nullptr};
+    float lr[3] = {0.0f, 0.0f, 0.0f};
+    int64_t n = -1;
+    int32_t launches = 0;
+};
 
 }  // namespace pz
 
 struct pz_ctx {
     int device = 0;
     pz_precision prec = PZ_MIXED;
+    int S = 1;                    // stars
     int nd = 0, ns = 0;
     int64_t nlam = 0, ld = 0;     // grid points, padded row stride of [nd][ld] buffers
-    double lambda0_nm = 0, R = 0, lnr = 0, xi = 0;
+    double lambda0_nm = 0, R = 0, lnr = 0;
     int W = 0;
-    int64_t nl_caller = 0;
+    int64_t nl_caller = 0;        // master lines (gradient output size)
     int64_t n_evals = 0;
     pz::Tiling tiling;
+    int n_sm = 0;
 
     // host copies (small)
-    std::vector<double> h_m, h_T;
-    std::vector<int32_t> h_il;      // sorted integer centres (for tile ranges)
+    std::vector<double> h_m, h_T;          // [S][nd]
+    std::vector<int32_t> h_il;             // [L.n] integer centres, sorted within each star
+    std::vector<int64_t> h_line_off;       // [S+1] star segments of the line table
+    std::vector<float> h_invdv;            // [S][ns][nd] 1/dv_D (thresholds)
 
-    // device: depth and species tables
-    double *d_m = nullptr, *d_T = nullptr;
-    float *d_beta_hi = nullptr, *d_beta_lo = nullptr;   // eV/(k T) split hi + lo
-    float *d_ne = nullptr, *d_npert = nullptr, *d_c2T = nullptr;
-    double *d_ne64 = nullptr, *d_npert64 = nullptr, *d_rho64 = nullptr;
-    float *d_R = nullptr;           // [ns][nd] (1/dv_D) (pop/rho) 10^dabund
-    double *d_Rbase = nullptr;      // [ns][nd] (1/dv_D)(pop/rho), FP64
-    float *d_invdv = nullptr;       // [ns][nd] 1/dv_D (s/cm)
-    double *d_pop64 = nullptr, *d_mass64 = nullptr;
-    float *d_thr = nullptr;         // [ns][nslab] fast-path distance threshold (grid units)
+    // device: depth and species tables, strided by star
+    double *d_m = nullptr, *d_T = nullptr;                      // [S][nd]
+    float *d_beta_hi = nullptr, *d_beta_lo = nullptr;           // [S][nd] eV/(k T) split hi + lo
+    float *d_ne = nullptr, *d_npert = nullptr, *d_c2T = nullptr; // [S][nd]
+    double *d_ne64 = nullptr, *d_npert64 = nullptr, *d_rho64 = nullptr;  // [S][nd]
+    float *d_R = nullptr;           // [S][ns][nd] (1/dv_D) (pop/rho) 10^dabund
+    double *d_Rbase = nullptr;      // [S][ns][nd] (1/dv_D)(pop/rho), FP64
+    float *d_invdv = nullptr;       // [S][ns][nd] 1/dv_D (s/cm)
+    double *d_pop64 = nullptr;      // [S][ns][nd]
+    double *d_mass64 = nullptr;     // [S][ns]
+    double *d_xi64 = nullptr;       // [S]
+    float *d_thr = nullptr;         // [S][ns][nslab] fast-path distance threshold (grid units)
     int nslab = 0;                  // depth slabs of DS layers covered by the launch grid
-    std::vector<float> h_invdv;     // [ns][nd] host copy of 1/dv_D (thresholds)
-    double *d_kc = nullptr;         // [nd][ld] continuum opacity FP64
-    double *d_dab = nullptr;        // [n_elem_max] current abundance offsets
+    double *d_kc = nullptr;         // [S][nd][ld] continuum opacity FP64
+    double *d_dab = nullptr;        // [n_elem] current abundance offsets
+    float *d_mdgf = nullptr, *d_mdg6 = nullptr;   // [nl_caller] current line corrections, caller order
     int32_t *d_eos = nullptr;       // [ns] element of species (or -1)
     int n_elem = 0;
 
     pz::LineTable L;
-    int32_t *d_tile_lo = nullptr, *d_tile_hi = nullptr;
-    int32_t *d_near_lo = nullptr, *d_near_hi = nullptr;   // lines whose near zone can reach a tile
-    float *d_knear = nullptr;       // [nd][ld] near-core sums of the forward
+    int64_t *d_line_off = nullptr;  // [S+1]
+    // work items (star, tile * groups + group, lo, hi), longest first
+    int4 *d_fitems = nullptr;       // far-wing kernels
+    int4 *d_nitems_f = nullptr;     // near-core forward
+    int4 *d_nitems_b = nullptr;     // near-core backward
+    int n_fitems = 0, n_bitems = 0, n_nitems_f = 0, n_nitems_b = 0;  // n_bitems: far items holding lines
+    int *d_ctr = nullptr;           // [4] work-queue counters
     int ntiles = 0, tileT = 0;
+    float *d_knear = nullptr;       // [S][nd][ld] near-core sums of the forward
 
     // resident buffers
-    void *d_kline = nullptr;        // [nd][ld] float (MIXED) or double (FP64)
-    double *d_F = nullptr, *d_Fc = nullptr;
-    double *d_g = nullptr, *d_gc = nullptr;   // instrument outputs (n_out)
+    void *d_kline = nullptr;        // [S][nd][ld] float (MIXED) or double (FP64)
+    double *d_F = nullptr, *d_Fc = nullptr;   // [S][nlam]
+    double *d_g = nullptr, *d_gc = nullptr;   // [S][n_out] instrument outputs
     int64_t n_out = 0;
     bool identity_inst = true;
-    // instrument weights
+    // instrument weights (shared by all stars)
     int64_t n_pix = 0, pix_cap = 0;
     int32_t max_taps = 0;
     int32_t *d_tap0 = nullptr, *d_ntap = nullptr;
@@ -132,15 +153,20 @@ struct pz_ctx {
     std::vector<double> pix_key;
 
     // backward scratch
-    double *d_dFbar = nullptr;      // [nlam]
-    float *d_Gt = nullptr;          // [nd][ld] G * stim (FP32, MIXED)
-    double *d_Gt64 = nullptr;       // [nd][ld] (FP64 form)
-    double *d_gacc = nullptr;       // [2][nl]
+    double *d_dFbar = nullptr;      // [S][nlam]
+    float *d_Gt = nullptr;          // [S][nd][ld] G * stim (FP32, MIXED)
+    double *d_Gt64 = nullptr;       // [S][nd][ld] (FP64 form)
+    double *d_gacc = nullptr;       // [2][L.n] per table line
+    double *d_gline = nullptr;      // [2][nl_caller] summed over stars, caller order
     double *d_gab = nullptr;        // [n_elem]
+    float *d_dLdf = nullptr;        // [S][n_out] seed of the captured step
 
     // state
     bool have_kline = false, have_flux = false, have_inst = false;
     int32_t launches = 0;
+    pz::StepGraph graph;
+    cudaStream_t cap_stream = nullptr;   // private stream the step graph is captured on
+    bool capturing = false;              // profiler off while capturing
 
     // CUDA-event profiler (pz_set_profiling)
     bool profiling = false;
@@ -186,6 +212,7 @@ cudaError_t launch_loss(pz_ctx *c, const float *y, const float *w, int64_t n, do
 cudaError_t launch_inst_adjoint(pz_ctx *c, const float *dLdf, cudaStream_t s);
 cudaError_t launch_rt_adjoint(pz_ctx *c, cudaStream_t s);
 cudaError_t launch_grad_finalize(pz_ctx *c, float *g_gf, float *g_g6, float *g_ab, cudaStream_t s);
+cudaError_t launch_update(pz_ctx *c, float lr_gf, float lr_g6, float lr_ab, cudaStream_t s);
 cudaError_t launch_probe_expn(const double *x, int64_t n, double *out, cudaStream_t s);
 bool tiling_supported(int J, int DS, int minb);
 

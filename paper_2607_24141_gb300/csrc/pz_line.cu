@@ -1,24 +1,29 @@
 // pz_line.cu -- windowed Voigt line-opacity sum (Eqs. 4-5) and its adjoint
 // (Sec. 6), FP32-mixed and plain FP64 forms, plus the per-device Voigt tables.
 //
-// Mixed-precision kernels.  A CTA owns a wavelength tile of T = 32 J grid
-// points and a depth range of GW x DS layers; warp w sweeps layers
+// Mixed-precision kernels.  The work is a queue of items (star, lambda tile,
+// depth group, line range) built on the host: lines are sorted by centre
+// within each star, and an item's range [lo, hi) holds the star's lines whose
+// window |i - i_l| <= W touches the tile (binary search).  The kernels are
+// persistent: every CTA takes the next item from an atomic counter until the
+// queue is empty, and the items are ordered longest first, so stars and tiles
+// of very different line counts share one launch.  A far-wing item covers a
+// tile of T = 32 J grid points and GW x DS layers; warp w sweeps layers
 // [d0 + w DS, d0 + (w+1) DS) and lane l owns the J contiguous points
-// t0 + l J + [0, J).  Lines are sorted by centre; the CTA's line range
-// [tile_lo, tile_hi) (all lines whose window |i - i_l| <= W touches the tile)
-// is found on the host by binary search.  Lines are staged into shared memory
-// LC at a time: the CTA first computes the per-(line, depth) prefactors of
-// Eqs. 4-5 (strength A, damping a, Doppler factor c/dv_D and the pre-scaled
-// far-wing polynomial coefficients) once for the whole tile, then every
-// thread accumulates its J x DS (lambda, depth) sums in registers.  Whether a
-// line is entirely inside its window and in the far wing (|v| >= 20 at every
-// depth) over the whole tile is decided once per line for the CTA, so that
-// branch is uniform across warps.  Per-chunk FP32 partial sums are folded into
-// a compensated (hi, lo) pair (2Sum).  The frequency offset is formed in index
-// space: v = expm1((x_l - i) ln r) c/dv_D with x_l - i = (i_l - i) + frac_l,
-// the integer part exact, avoiding the cancellation of lambda_l/lambda_i - 1.
+// t0 + l J + [0, J).  Lines are staged into shared memory LC at a time: the
+// CTA first computes the per-(line, depth) prefactors of Eqs. 4-5 (strength A,
+// damping a, Doppler factor c/dv_D and the pre-scaled far-wing polynomial
+// coefficients) once for the whole tile, then every thread accumulates its
+// J x DS (lambda, depth) sums in registers.  Whether a line is entirely inside
+// its window and in the far wing (|v| >= 20 at every depth of the warp's slab)
+// over the whole tile is decided once per line and warp.  Per-chunk FP32
+// partial sums are folded into a compensated (hi, lo) pair (2Sum).  The
+// frequency offset is formed in index space: v = expm1((x_l - i) ln r) c/dv_D
+// with x_l - i = (i_l - i) + frac_l, the integer part exact, avoiding the
+// cancellation of lambda_l/lambda_i - 1.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -121,23 +126,59 @@ pz_status ensure_device_tables() {
 // Mixed-precision kernels
 // ---------------------------------------------------------------------------
 
+// Kernel arguments.  Line arrays are indexed by absolute line; the per-star tables
+// and buffers point at star 0 and are advanced by star_view().
 struct LineArgs {
     int64_t nlam, ld;
     int nd, W;
     float lnr, lam0cm;
-    const int32_t *tile_lo, *tile_hi;
     const float *ilf, *frac, *E, *lamcm, *grad, *g4, *g6, *Q;
     const int32_t *sp;
-    const float *R, *invdv, *thr;                   // [ns][nd], [ns][nd], [ns][nslab]
+    const float *R, *invdv, *thr;                   // [ns][nd], [ns][nd], [ns][nslab] of the star
     int nslab;
-    const float *beta_hi, *beta_lo, *ne, *npert, *c2T;
-    float *kline;                                   // forward output [nd][ld]
-    float *knear;                                   // near-core sums [nd][ld]
-    const int32_t *near_lo, *near_hi;               // per tile: lines whose near zone can reach it
-    const float *Gt;                                // backward input [nd][ld]
+    const float *beta_hi, *beta_lo, *ne, *npert, *c2T;   // [nd] of the star
+    float *kline;                                   // forward output [nd][ld] of the star
+    float *knear;                                   // near-core sums [nd][ld] of the star
+    const float *Gt;                                // backward input [nd][ld] of the star
     double *gacc;                                   // backward output [2][nl]
     int64_t nl;
+    // work queue: items (star, tile * ngroups + group, lo, hi), longest first
+    const int4 *items;
+    int n_items, ngroups;
+    int *ctr;
+    int64_t sstride, dstride, bstride, tstride;     // per-star strides of the tables above
 };
+
+__device__ __forceinline__ LineArgs star_view(const LineArgs &g, int s) {
+    LineArgs v = g;
+    v.R += s * g.sstride;
+    v.invdv += s * g.sstride;
+    v.thr += s * g.tstride;
+    v.beta_hi += s * g.dstride;
+    v.beta_lo += s * g.dstride;
+    v.ne += s * g.dstride;
+    v.npert += s * g.dstride;
+    v.c2T += s * g.dstride;
+    v.kline += s * g.bstride;
+    v.knear += s * g.bstride;
+    v.Gt += s * g.bstride;
+    return v;
+}
+
+// Persistent work loop: every CTA takes the next item of the queue until it is empty.
+template <class F>
+__device__ __forceinline__ void for_each_item(const LineArgs &g, F &&f) {
+    __shared__ int s_it;
+    for (;;) {
+        if (threadIdx.x == 0) s_it = atomicAdd(g.ctr, 1);
+        __syncthreads();
+        const int it = s_it;
+        __syncthreads();
+        if (it >= g.n_items) break;
+        const int4 item = g.items[it];
+        f(star_view(g, item.x), item.y / g.ngroups, item.y % g.ngroups, item.z, item.w);
+    }
+}
 
 // Per-(line, depth) prefactors.  NP = 8 (forward) or 16 (backward):
 //  [0] k = c/dv_D   [1] a^2   [2..6] B1..B5 = A a/sqrt(pi) x (1, 1.5, 3.75-2a^2, -15a^2, 12a^4)
@@ -227,8 +268,9 @@ __device__ __forceinline__ int lo_slot(int dd, int tid, int nthr) { return (dd *
 // Far-wing kernel (forward).  Every cell with |v|^2 + a^2 >= 400 inside its window is
 // evaluated here with the far polynomial; the near-core cells are summed by
 // k_line_near_fwd into knear, which this kernel adds before applying stim.
-template <int J, int DS, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int LC) {
+template <int J, int DS>
+__device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, const int group, const int lo,
+                                             const int hi, const int GW, const int LC) {
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
     extern __shared__ float4 smem4[];
     const int T = 32 * J;
@@ -239,14 +281,12 @@ __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int 
     float *s_lo = reinterpret_cast<float *>(s_line + LC);               // [DS][nthr][4] compensation terms
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
-    const int d0 = blockIdx.y * DC;
+    const int d0 = group * DC;
     const int slab = (d0 + warp * DS) / DS;
     const int t0 = tile * T;
     const float t0f = (float)t0, tendf = (float)(t0 + T - 1);
     const int lam_thr = t0 + lane * J;
     const float lamf = (float)lam_thr;
-    const int lo = g.tile_lo[tile], hi = g.tile_hi[tile];
 
     float acc[DS][J], shi[DS][J];
 #pragma unroll
@@ -361,10 +401,18 @@ __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int 
     }
 }
 
+template <int J, int DS, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int LC) {
+    for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi) {
+        far_fwd_item<J, DS>(v, tile, group, lo, hi, GW, LC);
+    });
+}
+
 // Far-wing kernel (backward): the per-line sums over the tile's far cells of
 // G stim A H and G stim A a6 dH/da, reduced over the CTA and added to gacc.
-template <int J, int DS, int MINB>
-__global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int LC) {
+template <int J, int DS>
+__device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, const int group, const int lo,
+                                             const int hi, const int GW, const int LC) {
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
     extern __shared__ float4 smem4[];
     const int T = 32 * J;
@@ -375,14 +423,12 @@ __global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int 
     float2 *s_red = reinterpret_cast<float2 *>(s_line + LC);            // [LC][GW]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int tile = blockIdx.x;
-    const int d0 = blockIdx.y * DC;
+    const int d0 = group * DC;
     const int slab = (d0 + warp * DS) / DS;
     const int t0 = tile * T;
     const float t0f = (float)t0, tendf = (float)(t0 + T - 1);
     const int lam_thr = t0 + lane * J;
     const float lamf = (float)lam_thr;
-    const int lo = g.tile_lo[tile], hi = g.tile_hi[tile];
 
     // G * stim of the thread's cells; zero outside the grid
     float gv[DS][J];
@@ -499,6 +545,13 @@ __global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int 
             atomicAdd(g.gacc + g.nl + c0 + li, a2);
         }
     }
+}
+
+template <int J, int DS, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int LC) {
+    for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi) {
+        far_bwd_item<J, DS>(v, tile, group, lo, hi, GW, LC);
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -668,18 +721,18 @@ __device__ __forceinline__ void near_sweep(const LineArgs &g, int t0, int64_t nl
     }
 }
 
-// Forward near-core sums into knear.  Grid: (tile, depth group of NDG layers).
+// Forward near-core sums into knear.  Work items: (star, tile, depth group of NDG layers).
 template <int T, int NDG>
-__global__ void __launch_bounds__(256) k_line_near_fwd(LineArgs g) {
+__global__ void __launch_bounds__(256) k_line_near_fwd(LineArgs gq) {
     __shared__ float s_acc[NDG * T];
     __shared__ NearItem s_items[8 * 32];
     __shared__ int s_queue[8 * kCoreQueue];
+    for_each_item(gq, [&](const LineArgs &g, int tile, int group, int nlo, int nhi) {
     const int tid = threadIdx.x;
-    const int tile = blockIdx.x, t0 = tile * T;
-    const int dbase = blockIdx.y * NDG, ndg = min(NDG, g.nd - dbase);
+    const int t0 = tile * T;
+    const int dbase = group * NDG, ndg = min(NDG, g.nd - dbase);
     for (int k = tid; k < NDG * T; k += blockDim.x) s_acc[k] = 0.0f;
     __syncthreads();
-    const int nlo = g.near_lo[tile], nhi = g.near_hi[tile];
     near_sweep<T, false>(
         g, t0, nlo, (int64_t)(nhi - nlo) * ndg, ndg, dbase, s_items, s_queue,
         [&](const NearItem &it, int i, float H, float) { atomicAdd(s_acc + it.dl * T + (i - t0), it.A * H); },
@@ -689,25 +742,26 @@ __global__ void __launch_bounds__(256) k_line_near_fwd(LineArgs g) {
         const int dl = k / T, q = k - dl * T;
         g.knear[(int64_t)(dbase + dl) * g.ld + t0 + q] = s_acc[k];
     }
+    });
 }
 
 // Backward: per-line sums over the near cells of G stim A H and G stim A a6 dH/da.
 // Lines are processed in batches whose per-line sums live in shared memory; one
 // global atomic per (line, tile, depth group) at the end of each batch.
 template <int T, int NDG>
-__global__ void __launch_bounds__(256) k_line_near_bwd(LineArgs g) {
+__global__ void __launch_bounds__(256) k_line_near_bwd(LineArgs gq) {
     __shared__ float s_g[NDG * T];                                      // G * stim
     __shared__ float2 s_sum[kNearBatch];
     __shared__ NearItem s_items[8 * 32];
     __shared__ int s_queue[8 * kCoreQueue];
+    for_each_item(gq, [&](const LineArgs &g, int tile, int group, int nlo, int nhi) {
     const int tid = threadIdx.x;
-    const int tile = blockIdx.x, t0 = tile * T;
-    const int dbase = blockIdx.y * NDG, ndg = min(NDG, g.nd - dbase);
+    const int t0 = tile * T;
+    const int dbase = group * NDG, ndg = min(NDG, g.nd - dbase);
     for (int k = tid; k < ndg * T; k += blockDim.x) {
         const int dl = k / T, q = k - dl * T;
         s_g[k] = (t0 + q < g.nlam) ? g.Gt[(int64_t)(dbase + dl) * g.ld + t0 + q] : 0.0f;
     }
-    const int nlo = g.near_lo[tile], nhi = g.near_hi[tile];
     for (int b0 = nlo; b0 < nhi; b0 += kNearBatch) {
         const int nb = min(kNearBatch, nhi - b0);
         __syncthreads();
@@ -730,6 +784,8 @@ __global__ void __launch_bounds__(256) k_line_near_bwd(LineArgs g) {
             if (v.y != 0.0f) atomicAdd(g.gacc + g.nl + b0 + k, (double)v.y);
         }
     }
+    __syncthreads();
+    });
 }
 
 static LineArgs make_args(pz_ctx *c) {
@@ -740,8 +796,6 @@ static LineArgs make_args(pz_ctx *c) {
     g.W = c->W;
     g.lnr = (float)c->lnr;
     g.lam0cm = (float)(c->lambda0_nm * 1e-7);
-    g.tile_lo = c->d_tile_lo;
-    g.tile_hi = c->d_tile_hi;
     g.ilf = c->L.ilf;
     g.frac = c->L.frac;
     g.E = c->L.E;
@@ -762,21 +816,49 @@ static LineArgs make_args(pz_ctx *c) {
     g.c2T = c->d_c2T;
     g.kline = (float *)c->d_kline;
     g.knear = c->d_knear;
-    g.near_lo = c->d_near_lo;
-    g.near_hi = c->d_near_hi;
     g.Gt = c->d_Gt;
     g.gacc = c->d_gacc;
     g.nl = c->L.n;
+    g.items = nullptr;
+    g.n_items = 0;
+    g.ngroups = 1;
+    g.ctr = nullptr;
+    g.sstride = (int64_t)c->ns * c->nd;
+    g.dstride = c->nd;
+    g.bstride = (int64_t)c->nd * c->ld;
+    g.tstride = (int64_t)c->ns * c->nslab;
     return g;
 }
 
+// Persistent grid: as many CTAs as fit on the GPU at once, at most one per item.
+template <class K>
+static int persistent_grid(pz_ctx *c, K kernel, int threads, size_t smem, int n_items) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    int64_t n = (int64_t)per_sm * std::max(c->n_sm, 1);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(n, n_items));
+}
+
 template <int T, bool BWD>
-static cudaError_t launch_near(pz_ctx *c, const LineArgs &g, cudaStream_t s) {
+static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
     if (BWD) {
-        dim3 grid(c->ntiles, (c->nd + kNearDepthsBwd - 1) / kNearDepthsBwd);
+        if (c->n_nitems_b == 0) return cudaSuccess;
+        g.items = c->d_nitems_b;
+        g.n_items = c->n_nitems_b;
+        g.ngroups = (c->nd + kNearDepthsBwd - 1) / kNearDepthsBwd;
+        g.ctr = c->d_ctr + 3;
+        int grid = persistent_grid(c, k_line_near_bwd<T, kNearDepthsBwd>, 256, 0, g.n_items);
         k_line_near_bwd<T, kNearDepthsBwd><<<grid, 256, 0, s>>>(g);
     } else {
-        dim3 grid(c->ntiles, (c->nd + kNearDepthsFwd - 1) / kNearDepthsFwd);
+        if (c->n_nitems_f == 0) return cudaSuccess;
+        g.items = c->d_nitems_f;
+        g.n_items = c->n_nitems_f;
+        g.ngroups = (c->nd + kNearDepthsFwd - 1) / kNearDepthsFwd;
+        g.ctr = c->d_ctr + 0;
+        int grid = persistent_grid(c, k_line_near_fwd<T, kNearDepthsFwd>, 256, 0, g.n_items);
         k_line_near_fwd<T, kNearDepthsFwd><<<grid, 256, 0, s>>>(g);
     }
     c->launches++;
@@ -794,9 +876,15 @@ static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
         cudaFuncSetAttribute(k_line_fwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set[c->device] = true;
     }
-    cudaError_t e = launch_near<32 * J, false>(c, g, s);
+    cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    dim3 grid(c->ntiles, (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta());
+    e = launch_near<32 * J, false>(c, g, s);
+    if (e != cudaSuccess || c->n_fitems == 0) return e;
+    g.items = c->d_fitems;
+    g.n_items = c->n_fitems;
+    g.ngroups = (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta();
+    g.ctr = c->d_ctr + 1;
+    int grid = persistent_grid(c, k_line_fwd<J, DS, MINB>, 32 * t.GW, smem, g.n_items);
     k_line_fwd<J, DS, MINB><<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LC);
     c->launches++;
     return cudaGetLastError();
@@ -813,11 +901,20 @@ static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
         cudaFuncSetAttribute(k_line_bwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set[c->device] = true;
     }
-    dim3 grid(c->ntiles, (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta());
-    k_line_bwd<J, DS, MINB><<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LCB);
-    c->launches++;
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaMemsetAsync(c->d_ctr + 2, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
+    if (c->n_bitems > 0) {
+        LineArgs gb = g;
+        gb.items = c->d_fitems;
+        gb.n_items = c->n_bitems;   // the far items with lines come first
+        gb.ngroups = (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta();
+        gb.ctr = c->d_ctr + 2;
+        int grid = persistent_grid(c, k_line_bwd<J, DS, MINB>, 32 * t.GW, smem, gb.n_items);
+        k_line_bwd<J, DS, MINB><<<grid, 32 * t.GW, smem, s>>>(gb, t.GW, t.LCB);
+        c->launches++;
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     return launch_near<32 * J, true>(c, g, s);
 }
 
@@ -853,16 +950,18 @@ bool tiling_supported(int J, int DS, int minb) {
 
 struct Fp64Args {
     int64_t nlam, ld, nl;
-    int nd, W;
-    double lnr, lam0cm, xi2;
-    const int32_t *il;       // sorted integer centres (int)
+    int nd, ns, W;
+    double lnr, lam0cm;
+    const int32_t *il;       // integer centres, sorted within each star's segment
+    const int64_t *line_off; // [S+1] star segments
+    const int32_t *star;
     const double *x64;       // fractional centre
     const int32_t *sp;
     const float *lg_gf, *dgf, *E, *lg_rad, *lg_4, *lg_6, *dg6;
-    const double *T, *rho, *ne, *npert, *pop, *mass, *dab;
+    const double *T, *rho, *ne, *npert, *pop, *mass, *xi, *dab;   // [S][nd], [S][ns][nd], [S][ns], [S]
     const int32_t *eos;
-    double *kline;
-    const double *Gt;
+    double *kline;           // [S][nd][ld]
+    const double *Gt;        // [S][nd][ld]
     double *gacc;
 };
 
@@ -870,27 +969,28 @@ struct LineTerm64 {
     double A, a, a6, kv;   // strength, damping, vdW damping, c/dv_D
 };
 
-__device__ __forceinline__ LineTerm64 term64(const Fp64Args &g, int64_t l, int d) {
+__device__ __forceinline__ LineTerm64 term64(const Fp64Args &g, int64_t l, int st, int d) {
     LineTerm64 q;
-    int s = g.sp[l];
-    double T = g.T[d];
-    double dv = sqrt(2.0 * kKB * T / (g.mass[s] * kAMU) + g.xi2);
-    double lamcm = g.lam0cm * exp(g.x64[l] * g.lnr);
-    double inv_dnu = lamcm / dv;
-    double gf = exp10((double)g.lg_gf[l] + (double)g.dgf[l]);
-    double dab = (g.eos && g.eos[s] >= 0) ? g.dab[g.eos[s]] : 0.0;
-    double pop = g.pop[(int64_t)s * g.nd + d] * exp10(dab);
-    double boltz = exp(-(double)g.E[l] * kEV / (kKB * T));
-    q.A = (kPI * kE * kE / (kME * kC)) / kSQRTPI * gf * (pop / g.rho[d]) * boltz * inv_dnu;
-    double g6n = exp10((double)g.lg_6[l] + (double)g.dg6[l]) * g.npert[d];
-    q.a = (exp10((double)g.lg_rad[l]) + exp10((double)g.lg_4[l]) * g.ne[d] + g6n) * inv_dnu / (4.0 * kPI);
+    const int s = g.sp[l];
+    const int64_t sd = (int64_t)st * g.nd + d;
+    const double T = g.T[sd];
+    const double xi = g.xi[st];
+    const double dv = sqrt(2.0 * kKB * T / (g.mass[(int64_t)st * g.ns + s] * kAMU) + xi * xi);
+    const double lamcm = g.lam0cm * exp(g.x64[l] * g.lnr);
+    const double inv_dnu = lamcm / dv;
+    const double gf = exp10((double)g.lg_gf[l] + (double)g.dgf[l]);
+    const double dab = (g.eos && g.eos[s] >= 0) ? g.dab[g.eos[s]] : 0.0;
+    const double pop = g.pop[((int64_t)st * g.ns + s) * g.nd + d] * exp10(dab);
+    const double boltz = exp(-(double)g.E[l] * kEV / (kKB * T));
+    q.A = (kPI * kE * kE / (kME * kC)) / kSQRTPI * gf * (pop / g.rho[sd]) * boltz * inv_dnu;
+    const double g6n = exp10((double)g.lg_6[l] + (double)g.dg6[l]) * g.npert[sd];
+    q.a = (exp10((double)g.lg_rad[l]) + exp10((double)g.lg_4[l]) * g.ne[sd] + g6n) * inv_dnu / (4.0 * kPI);
     q.a6 = g6n * inv_dnu / (4.0 * kPI);
     q.kv = kC / dv;
     return q;
 }
 
-__device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, int32_t key) {
-    int64_t lo = 0, hi = n;
+__device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t lo, int64_t hi, int32_t key) {
     while (lo < hi) {
         int64_t mid = (lo + hi) >> 1;
         if (a[mid] < key) lo = mid + 1; else hi = mid;
@@ -898,39 +998,43 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t *a, int64_t n, 
     return lo;
 }
 
+// one thread per (lambda, depth, star); loops over the star's lines whose window covers lambda
 __global__ void k_line_fwd_fp64(Fp64Args g) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int d = blockIdx.y;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.y, st = blockIdx.z;
     if (i >= g.nlam) return;
-    int64_t l0 = lower_bound_i32(g.il, g.nl, (int32_t)(i - g.W));
-    int64_t l1 = lower_bound_i32(g.il, g.nl, (int32_t)(i + g.W + 1));
+    const int64_t b0 = g.line_off[st], b1 = g.line_off[st + 1];
+    const int64_t l0 = lower_bound_i32(g.il, b0, b1, (int32_t)(i - g.W));
+    const int64_t l1 = lower_bound_i32(g.il, b0, b1, (int32_t)(i + g.W + 1));
     double sum = 0.0;
     for (int64_t l = l0; l < l1; ++l) {
-        LineTerm64 q = term64(g, l, d);
+        LineTerm64 q = term64(g, l, st, d);
         double u = expm1((g.x64[l] - (double)i) * g.lnr);   // lambda_l/lambda_i - 1
         double H, dH;
         voigt64(u * q.kv, q.a, H, dH, false);
         sum += q.A * H;
     }
-    double lam = g.lam0cm * exp((double)i * g.lnr);
-    double stim = -expm1(-kC2 / (lam * g.T[d]));
-    g.kline[(int64_t)d * g.ld + i] = stim * sum;
+    const double lam = g.lam0cm * exp((double)i * g.lnr);
+    const double stim = -expm1(-kC2 / (lam * g.T[(int64_t)st * g.nd + d]));
+    g.kline[((int64_t)st * g.nd + d) * g.ld + i] = stim * sum;
 }
 
 // one thread per (line, depth); loops over the line's window
 __global__ void k_line_bwd_fp64(Fp64Args g) {
-    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int d = blockIdx.y;
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int d = blockIdx.y;
     if (l >= g.nl) return;
-    LineTerm64 q = term64(g, l, d);
-    int64_t il = g.il[l];
-    int64_t i0 = max((int64_t)0, il - g.W), i1 = min(g.nlam - 1, il + g.W);
+    const int st = g.star[l];
+    LineTerm64 q = term64(g, l, st, d);
+    const int64_t il = g.il[l];
+    const int64_t i0 = max((int64_t)0, il - g.W), i1 = min(g.nlam - 1, il + g.W);
+    const double *Grow = g.Gt + ((int64_t)st * g.nd + d) * g.ld;
     double s1 = 0.0, s2 = 0.0;
     for (int64_t i = i0; i <= i1; ++i) {
         double u = expm1((g.x64[l] - (double)i) * g.lnr);
         double H, dH;
         voigt64(u * q.kv, q.a, H, dH, true);
-        double gs = g.Gt[(int64_t)d * g.ld + i];
+        double gs = Grow[i];
         s1 += gs * q.A * H;
         s2 += gs * q.A * dH * q.a6;
     }
@@ -944,11 +1048,13 @@ static Fp64Args make_args64(pz_ctx *c) {
     g.ld = c->ld;
     g.nl = c->L.n;
     g.nd = c->nd;
+    g.ns = c->ns;
     g.W = c->W;
     g.lnr = c->lnr;
     g.lam0cm = c->lambda0_nm * 1e-7;
-    g.xi2 = c->xi * c->xi;
     g.il = c->L.il32;
+    g.line_off = c->d_line_off;
+    g.star = c->L.star;
     g.x64 = c->L.x64;
     g.sp = c->L.sp;
     g.lg_gf = c->L.lg_gf;
@@ -964,6 +1070,7 @@ static Fp64Args make_args64(pz_ctx *c) {
     g.npert = c->d_npert64;
     g.pop = c->d_pop64;
     g.mass = c->d_mass64;
+    g.xi = c->d_xi64;
     g.dab = c->d_dab;
     g.eos = c->n_elem > 0 ? c->d_eos : nullptr;
     g.kline = (double *)c->d_kline;
@@ -974,7 +1081,7 @@ static Fp64Args make_args64(pz_ctx *c) {
 
 cudaError_t launch_line_fwd_fp64(pz_ctx *c, cudaStream_t s) {
     Fp64Args g = make_args64(c);
-    dim3 grid((unsigned)((c->nlam + 127) / 128), c->nd);
+    dim3 grid((unsigned)((c->nlam + 127) / 128), c->nd, c->S);
     k_line_fwd_fp64<<<grid, 128, 0, s>>>(g);
     c->launches++;
     return cudaGetLastError();
@@ -990,35 +1097,67 @@ cudaError_t launch_line_bwd_fp64(pz_ctx *c, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// corrections: Q_l = Qbase_l 10^dgf, g6_l = g6base_l 10^dg6, R_sd = Rbase_sd 10^dab
+// corrections: the per-line values are gathered from the caller-order (master)
+// corrections, Q_l = Qbase_l 10^dgf, g6_l = g6base_l 10^dg6, R_sd = Rbase_sd 10^dab
 // ---------------------------------------------------------------------------
-__global__ void k_apply_line_corr(int64_t n, const double *Qbase, const float *g6base, const float *dgf,
-                                  const float *dg6, float *Q, float *g6) {
+__global__ void k_apply_line_corr(int64_t n, const int32_t *orig, const double *Qbase, const float *g6base,
+                                  const float *mdgf, const float *mdg6, float *dgf, float *dg6, float *Q, float *g6) {
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= n) return;
-    Q[l] = (float)(Qbase[l] * exp10((double)dgf[l]));
-    g6[l] = (float)((double)g6base[l] * exp10((double)dg6[l]));
+    const int32_t o = orig[l];
+    const float a = mdgf[o], b = mdg6[o];
+    dgf[l] = a;
+    dg6[l] = b;
+    Q[l] = (float)(Qbase[l] * exp10((double)a));
+    g6[l] = (float)((double)g6base[l] * exp10((double)b));
 }
 
-__global__ void k_apply_abund(int ns, int nd, const double *Rbase, const double *dab, const int32_t *eos,
+// R over [S][ns][nd]
+__global__ void k_apply_abund(int64_t n, int ns, int nd, const double *Rbase, const double *dab, const int32_t *eos,
                               int use, float *R) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= ns * nd) return;
-    int s = idx / nd;
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n) return;
+    int s = (int)((idx / nd) % ns);
     double f = (use && eos[s] >= 0) ? exp10(dab[eos[s]]) : 1.0;
     R[idx] = (float)(Rbase[idx] * f);
 }
 
 cudaError_t launch_apply_corrections(pz_ctx *c, cudaStream_t s) {
     if (c->L.n > 0) {
-        k_apply_line_corr<<<(unsigned)((c->L.n + 255) / 256), 256, 0, s>>>(c->L.n, c->L.Qbase, c->L.g6base, c->L.dgf,
-                                                                          c->L.dg6, c->L.Q, c->L.g6);
+        k_apply_line_corr<<<(unsigned)((c->L.n + 255) / 256), 256, 0, s>>>(
+            c->L.n, c->L.orig, c->L.Qbase, c->L.g6base, c->d_mdgf, c->d_mdg6, c->L.dgf, c->L.dg6, c->L.Q, c->L.g6);
         c->launches++;
     }
-    int n = c->ns * c->nd;
-    k_apply_abund<<<(n + 255) / 256, 256, 0, s>>>(c->ns, c->nd, c->d_Rbase, c->d_dab, c->d_eos, c->n_elem > 0,
-                                                  c->d_R);
+    int64_t n = (int64_t)c->S * c->ns * c->nd;
+    k_apply_abund<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c->ns, c->nd, c->d_Rbase, c->d_dab, c->d_eos,
+                                                             c->n_elem > 0, c->d_R);
     c->launches++;
+    return cudaGetLastError();
+}
+
+// plain gradient step on the caller-order corrections: delta -= lr * dL/ddelta
+__global__ void k_update_corr(int64_t n, const double *gline, float lr_gf, float lr_g6, float *mdgf, float *mdg6) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    mdgf[k] = (float)((double)mdgf[k] - (double)lr_gf * gline[k]);
+    mdg6[k] = (float)((double)mdg6[k] - (double)lr_g6 * gline[n + k]);
+}
+
+__global__ void k_update_abund(int n, const double *gab, double lr, double *dab) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dab[k] -= lr * gab[k];
+}
+
+cudaError_t launch_update(pz_ctx *c, float lr_gf, float lr_g6, float lr_ab, cudaStream_t s) {
+    if (c->nl_caller > 0) {
+        k_update_corr<<<(unsigned)((c->nl_caller + 255) / 256), 256, 0, s>>>(c->nl_caller, c->d_gline, lr_gf, lr_g6,
+                                                                            c->d_mdgf, c->d_mdg6);
+        c->launches++;
+    }
+    if (c->n_elem > 0) {
+        k_update_abund<<<(c->n_elem + 255) / 256, 256, 0, s>>>(c->n_elem, c->d_gab, (double)lr_ab, c->d_dab);
+        c->launches++;
+    }
     return cudaGetLastError();
 }
 

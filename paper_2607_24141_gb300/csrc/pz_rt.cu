@@ -12,6 +12,8 @@
 // the bottom layer.  Total and continuum branches share the walk.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "pz_internal.h"
 
 namespace pz {
@@ -79,10 +81,20 @@ struct FluxArgs {
     double *F, *Fc;
 };
 
+// one thread per (lambda, star); star = blockIdx.y
 template <typename KT>
 __global__ void k_flux(FluxArgs g) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nlam) return;
+    {
+        const int st = blockIdx.y;
+        g.m += (int64_t)st * g.nd;
+        g.T += (int64_t)st * g.nd;
+        g.kc += (int64_t)st * g.nd * g.ld;
+        g.kline = reinterpret_cast<const KT *>(g.kline) + (int64_t)st * g.nd * g.ld;
+        g.F += (int64_t)st * g.nlam;
+        g.Fc += (int64_t)st * g.nlam;
+    }
     const KT *kl = reinterpret_cast<const KT *>(g.kline);
     const double lam = g.lam0cm * exp((double)i * g.lnr);
     double chi_p = 0, chic_p = 0, tau_p = 0, tauc_p = 0, S_p = 0, m_p = 0;
@@ -140,7 +152,7 @@ cudaError_t launch_flux(pz_ctx *c, cudaStream_t s) {
     g.kline = c->d_kline;
     g.F = c->d_F;
     g.Fc = c->d_Fc;
-    unsigned nb = (unsigned)((c->nlam + 127) / 128);
+    dim3 nb((unsigned)((c->nlam + 127) / 128), c->S);
     if (c->prec == PZ_MIXED)
         k_flux<float><<<nb, 128, 0, s>>>(g);
     else
@@ -196,12 +208,20 @@ cudaError_t launch_inst_build(pz_ctx *c, const double *d_pix, double v_r, double
     return cudaGetLastError();
 }
 
-// one warp per pixel: lanes stride over the taps, FP64 sums reduced by shuffles
-__global__ void k_inst_apply(int64_t n_pix, int32_t max_taps, const int32_t *tap0, const int32_t *ntap,
+// one warp per (pixel, star): lanes stride over the taps, FP64 sums reduced by shuffles
+__global__ void k_inst_apply(int64_t nlam, int64_t n_pix, int32_t max_taps, const int32_t *tap0, const int32_t *ntap,
                              const float *w, const double *F, const double *Fc, double *g, double *gc, float *f) {
     int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (p >= n_pix) return;
+    {
+        const int64_t st = blockIdx.y;
+        F += st * nlam;
+        Fc += st * nlam;
+        g += st * n_pix;
+        gc += st * n_pix;
+        if (f) f += st * n_pix;
+    }
     int32_t i0 = tap0[p], n = ntap[p];
     const float *row = w + p * max_taps;
     double s = 0.0, sc = 0.0;
@@ -232,11 +252,13 @@ __global__ void k_identity_apply(int64_t n, const double *F, const double *Fc, d
 
 cudaError_t launch_inst_apply(pz_ctx *c, float *f, cudaStream_t s) {
     if (c->identity_inst) {
-        k_identity_apply<<<(unsigned)((c->nlam + 255) / 256), 256, 0, s>>>(c->nlam, c->d_F, c->d_Fc, c->d_g, c->d_gc, f);
+        const int64_t n = (int64_t)c->S * c->nlam;
+        k_identity_apply<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c->d_F, c->d_Fc, c->d_g, c->d_gc, f);
     } else {
         int64_t threads = c->n_pix * 32;
-        k_inst_apply<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(c->n_pix, c->max_taps, c->d_tap0, c->d_ntap,
-                                                                      c->d_tapw, c->d_F, c->d_Fc, c->d_g, c->d_gc, f);
+        dim3 grid((unsigned)((threads + 255) / 256), c->S);
+        k_inst_apply<<<grid, 256, 0, s>>>(c->nlam, c->n_pix, c->max_taps, c->d_tap0, c->d_ntap, c->d_tapw, c->d_F,
+                                          c->d_Fc, c->d_g, c->d_gc, f);
     }
     c->launches++;
     return cudaGetLastError();
@@ -287,6 +309,12 @@ __global__ void k_inst_adjoint(int64_t nlam, int64_t n_pix, int32_t max_taps, co
                                double *dFbar) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nlam) return;
+    {
+        const int64_t st = blockIdx.y;
+        gc += st * n_pix;
+        dLdf += st * n_pix;
+        dFbar += st * nlam;
+    }
     // first pixel with tap0 + ntap - 1 >= i
     int64_t lo = 0, hi = n_pix;
     while (lo < hi) {
@@ -308,12 +336,14 @@ __global__ void k_identity_adjoint(int64_t n, const double *Fc, const float *dLd
 }
 
 cudaError_t launch_inst_adjoint(pz_ctx *c, const float *dLdf, cudaStream_t s) {
-    unsigned nb = (unsigned)((c->nlam + 255) / 256);
-    if (c->identity_inst)
-        k_identity_adjoint<<<nb, 256, 0, s>>>(c->nlam, c->d_Fc, dLdf, c->d_dFbar);
-    else
+    if (c->identity_inst) {
+        const int64_t n = (int64_t)c->S * c->nlam;
+        k_identity_adjoint<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c->d_Fc, dLdf, c->d_dFbar);
+    } else {
+        dim3 nb((unsigned)((c->nlam + 255) / 256), c->S);
         k_inst_adjoint<<<nb, 256, 0, s>>>(c->nlam, c->n_pix, c->max_taps, c->d_tap0, c->d_ntap, c->d_tapw, c->d_gc,
                                           dLdf, c->d_dFbar);
+    }
     c->launches++;
     return cudaGetLastError();
 }
@@ -343,10 +373,20 @@ __device__ __forceinline__ void interval_grad(double ta, double tb, double Sa, d
     db = Sb * e2b - (s / D) * Bq;
 }
 
+// one thread per (lambda, star); star = blockIdx.y
 template <typename KT, typename GT>
 __global__ void k_rt_adjoint(RtAdjArgs g) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= g.nlam) return;
+    {
+        const int64_t st = blockIdx.y;
+        g.m += st * g.nd;
+        g.T += st * g.nd;
+        g.kc += st * g.nd * g.ld;
+        g.kline = reinterpret_cast<const KT *>(g.kline) + st * g.nd * g.ld;
+        g.dFbar += st * g.nlam;
+        g.Gt = reinterpret_cast<GT *>(g.Gt) + st * g.nd * g.ld;
+    }
     const KT *kl = reinterpret_cast<const KT *>(g.kline);
     GT *Gt = reinterpret_cast<GT *>(g.Gt);
     const double lam = g.lam0cm * exp((double)i * g.lnr);
@@ -411,7 +451,7 @@ cudaError_t launch_rt_adjoint(pz_ctx *c, cudaStream_t s) {
     g.kc = c->d_kc;
     g.kline = c->d_kline;
     g.dFbar = c->d_dFbar;
-    unsigned nb = (unsigned)((c->nlam + 127) / 128);
+    dim3 nb((unsigned)((c->nlam + 127) / 128), c->S);
     if (c->prec == PZ_MIXED) {
         g.Gt = c->d_Gt;
         k_rt_adjoint<float, float><<<nb, 128, 0, s>>>(g);
@@ -424,36 +464,49 @@ cudaError_t launch_rt_adjoint(pz_ctx *c, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// gradient finalisation: ln10 scale, caller order, species -> element sums
+// gradient finalisation: ln10 scale, sum over the stars that hold each caller line,
+// species -> element sums
 // ---------------------------------------------------------------------------
-__global__ void k_grad_finalize(int64_t nl, const double *gacc, const int32_t *orig, const int32_t *sp,
-                                const int32_t *eos, int use_ab, float *g_gf, float *g_g6, double *gab) {
+__global__ void k_grad_finalize(int64_t nl, int64_t nl_caller, const double *gacc, const int32_t *orig,
+                                const int32_t *sp, const int32_t *eos, int use_ab, double *gline, double *gab) {
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nl) return;
-    double ggf = kLN10 * gacc[l];
-    double gg6 = kLN10 * gacc[nl + l];
-    int32_t o = orig[l];
-    if (g_gf) g_gf[o] = (float)ggf;
-    if (g_g6) g_g6[o] = (float)gg6;
+    const double ggf = kLN10 * gacc[l];
+    const double gg6 = kLN10 * gacc[nl + l];
+    const int32_t o = orig[l];
+    atomicAdd(gline + o, ggf);
+    atomicAdd(gline + nl_caller + o, gg6);
     if (use_ab) {
         int e = eos[sp[l]];
         if (e >= 0) atomicAdd(gab + e, ggf);
     }
 }
 
-__global__ void k_copy_d2f(int n, const double *a, float *b) {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void k_copy_d2f(int64_t n, const double *a, float *b) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) b[k] = (float)a[k];
 }
 
 cudaError_t launch_grad_finalize(pz_ctx *c, float *g_gf, float *g_g6, float *g_ab, cudaStream_t s) {
-    int use_ab = (g_ab && c->n_elem > 0) ? 1 : 0;
+    const int use_ab = c->n_elem > 0 ? 1 : 0;
+    cudaError_t e = cudaMemsetAsync(c->d_gline, 0, sizeof(double) * 2 * std::max<int64_t>(c->nl_caller, 1), s);
+    if (e != cudaSuccess) return e;
+    if (use_ab && (e = cudaMemsetAsync(c->d_gab, 0, sizeof(double) * c->n_elem, s)) != cudaSuccess) return e;
     if (c->L.n > 0) {
-        k_grad_finalize<<<(unsigned)((c->L.n + 255) / 256), 256, 0, s>>>(c->L.n, c->d_gacc, c->L.orig, c->L.sp,
-                                                                        c->d_eos, use_ab, g_gf, g_g6, c->d_gab);
+        k_grad_finalize<<<(unsigned)((c->L.n + 255) / 256), 256, 0, s>>>(
+            c->L.n, c->nl_caller, c->d_gacc, c->L.orig, c->L.sp, c->d_eos, use_ab, c->d_gline, c->d_gab);
         c->launches++;
     }
-    if (use_ab) {
+    const int64_t n = c->nl_caller;
+    if (n > 0 && g_gf) {
+        k_copy_d2f<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c->d_gline, g_gf);
+        c->launches++;
+    }
+    if (n > 0 && g_g6) {
+        k_copy_d2f<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c->d_gline + n, g_g6);
+        c->launches++;
+    }
+    if (g_ab && use_ab) {
         k_copy_d2f<<<(c->n_elem + 255) / 256, 256, 0, s>>>(c->n_elem, c->d_gab, g_ab);
         c->launches++;
     }

@@ -20,8 +20,17 @@ Atmosphere recipe (every config):
   P_gas = g m;  P_e = 1e-4 g m_ref tau (Teff/5777)**4
   n_e = P_e/kT, n_pert = (P_gas - P_e)/kT, rho = 1.3 m_u P_gas/kT
   kappa_c(d, i) = kappa0(d) (lambda_i / 500 nm)**-1, kappa0 = tau**0.3/(0.7 m_ref)
-  species: log10 abundance f_s ~ N(-6, 1); per-layer jitter 10**N(0, 0.1);
+  species: log10 f_s ~ N(mu, 1); per-layer jitter 10**N(0, 0.1);
            pop_{s,d} = f_s 10**[M/H] n_tot(d) / U_s, U_s = 10**U[0, 1.5]
+           f_s is the absorbing lower level's share of all particles (abundance,
+           ionisation and excitation folded together).  mu sets the line strength
+           against the continuum; it is chosen per workload so that the normalised
+           spectrum has a realistic line-depth distribution (median f ~ 0.9-0.95,
+           strongest lines saturated, 5th percentile ~ 0.4-0.5) rather than a
+           saturated line forest: mu = -9.5 (solar optical, 500 nm, config 0),
+           -12.5 (300-1000 nm, 3e6 lines, config 2), -14 (APOGEE-like H band,
+           2e5-3e5 lines at 4-5x the line density, configs 1, 3, 4); -6 for the
+           hand-sized test problems.
   masses U[12, 60] amu; band (molecule-like) species U[26, 28] amu
   microturbulence xi = 1 km/s
 """
@@ -156,9 +165,15 @@ def grid_lambda_nm(grid: Grid) -> np.ndarray:
 # atmosphere
 # ----------------------------------------------------------------------------
 
+# mean log10 population share mu of the absorbing levels per workload (module docstring)
+MU_OPTICAL = -9.5
+MU_BROAD = -12.5
+MU_HBAND = -14.0
+
+
 def make_atmosphere(teff: float, logg: float, n_species: int, seed: int,
                     metallicity: float = 0.0, band_species=(), xi_kms: float = 1.0,
-                    n_depth: int = N_DEPTH) -> Atmosphere:
+                    n_depth: int = N_DEPTH, log_abund_mean: float = -6.0) -> Atmosphere:
     rng = np.random.default_rng(seed)
     j = np.arange(n_depth)
     x = -6.875 + 0.125 * j if n_depth == 72 else np.linspace(-6.875, 2.0, n_depth)
@@ -176,7 +191,7 @@ def make_atmosphere(teff: float, logg: float, n_species: int, seed: int,
     rho = 1.3 * _M_U * P_gas / kT
     kappa0 = tau ** 0.3 / (0.7 * m_ref)
 
-    log_f = rng.normal(-6.0, 1.0, n_species)
+    log_f = rng.normal(log_abund_mean, 1.0, n_species)
     jitter = rng.normal(0.0, 0.1, (n_species, n_depth))
     U = 10.0 ** rng.uniform(0.0, 1.5, n_species)
     mass = rng.uniform(12.0, 60.0, n_species)
@@ -246,7 +261,7 @@ def apogee_pixels(n_pix: int = 8575) -> np.ndarray:
 def config0(seed: int = 0, n_lambda: int = 4000, n_lines: int = 2000, W: int = 1000) -> Problem:
     """Tiny forward: solar atmosphere, 4,000 points from 500 nm, 2,000 lines, W = 1,000."""
     n_species = 12
-    atmos = make_atmosphere(5777.0, 4.44, n_species, seed)
+    atmos = make_atmosphere(5777.0, 4.44, n_species, seed, log_abund_mean=MU_OPTICAL)
     grid = Grid(500.0, R_GRID, n_lambda)
     lam_hi = float(grid_lambda_nm(grid)[-1])
     rng = np.random.default_rng(seed + 1000)
@@ -262,7 +277,7 @@ def config1(seed: int = 1, lam_lo: float = 1500.0, lam_hi: float = 1700.0,
     instrument v_r = 12.3 km/s, Gaussian LSF R = 22,500, 8,575 pixels."""
     n_species = 40
     band_sp = (36, 37, 38, 39)
-    atmos = make_atmosphere(4500.0, 2.0, n_species, seed, band_species=band_sp)
+    atmos = make_atmosphere(4500.0, 2.0, n_species, seed, band_species=band_sp, log_abund_mean=MU_HBAND)
     grid = Grid(lam_lo, R_GRID, n_lambda_for(lam_lo, lam_hi))
     rng = np.random.default_rng(seed + 1000)
     parts = [_atomic_lines(rng, n_atomic, lam_lo, lam_hi, np.arange(36))]
@@ -285,7 +300,7 @@ def config2(seed: int = 2, lam_lo: float = 300.0, lam_hi: float = 1000.0,
     """Broad optical: solar atmosphere, 300-1000 nm, 3e6 lines over 80 species with
     centre density proportional to lambda^-2, W = 2,000, full-resolution output."""
     n_species = 80
-    atmos = make_atmosphere(5777.0, 4.44, n_species, seed)
+    atmos = make_atmosphere(5777.0, 4.44, n_species, seed, log_abund_mean=MU_BROAD)
     grid = Grid(lam_lo, R_GRID, n_lambda_for(lam_lo, lam_hi))
     rng = np.random.default_rng(seed + 1000)
     lines = _pack([_atomic_lines(rng, n_lines, lam_lo, lam_hi, np.arange(n_species),
@@ -335,3 +350,127 @@ def config4_stars(seed: int = 4, n_stars: int = 64):
     mh = rng.uniform(-2.0, 0.5, n_stars)
     nk = np.round(np.exp(rng.uniform(math.log(2e4), math.log(3e5), n_stars))).astype(np.int64)
     return teff, logg, mh, nk
+
+
+@dataclasses.dataclass
+class Batch:
+    """Many stars on one grid with one master line list; star k uses the master
+    lines ``subsets[k]`` (indices, any order).  Corrections are per master line."""
+    name: str
+    atmos: list                 # [S] Atmosphere (shared n_depth and species set)
+    grid: Grid
+    lines: LineList             # master list, caller order
+    kappa_c: list               # [S] float64 [n_depth, n_lambda]
+    subsets: list               # [S] int32 index arrays into the master list
+    instrument: Optional[Instrument] = None
+    elem_of_species: Optional[np.ndarray] = None
+    n_elem: int = 0
+
+    @property
+    def n_stars(self) -> int:
+        return len(self.atmos)
+
+    def star(self, k: int) -> Problem:
+        """Star k as a single-star problem (its own line subset, caller order kept)."""
+        return Problem("%s[%d]" % (self.name, k), self.atmos[k], self.grid, self.lines.subset(self.subsets[k]),
+                       self.kappa_c[k], self.instrument, self.elem_of_species, self.n_elem)
+
+    @property
+    def n_evals(self) -> int:
+        wp = window_points(self.grid, self.lines)
+        return int(sum(int(wp[s].sum()) for s in self.subsets)) * self.atmos[0].n_depth
+
+
+def _tau1_layer(atmos: Atmosphere) -> int:
+    """Layer whose recipe optical depth is closest to tau = 1 (log tau = 0)."""
+    nd = atmos.n_depth
+    x = -6.875 + 0.125 * np.arange(nd) if nd == 72 else np.linspace(-6.875, 2.0, nd)
+    return int(np.argmin(np.abs(x)))
+
+
+def strength_proxy(atmos: Atmosphere, lines: LineList) -> np.ndarray:
+    """Line-strength proxy log gf + log10(pop_s/rho at tau = 1) - 5040 E_low / T(tau = 1),
+    a simplified keep test (lines selected by strength, Sec. 2.2)."""
+    j = _tau1_layer(atmos)
+    pr = np.log10(np.maximum(atmos.pop[:, j], 1e-300) / atmos.rho[j])
+    return lines.log_gf.astype(np.float64) + pr[lines.species] - 5040.0 * lines.E_low_eV.astype(np.float64) / atmos.T[j]
+
+
+def _batch_atmospheres(teff, logg, mh, n_species, band_species, chem_seed, grid):
+    """One atmosphere per star from the shared recipe: the same species set (abundance
+    pattern, partition functions, masses: one chemistry seed) scaled by [M/H]."""
+    atm = [make_atmosphere(float(t), float(g), n_species, chem_seed, metallicity=float(z),
+                           band_species=band_species, log_abund_mean=MU_HBAND) for t, g, z in zip(teff, logg, mh)]
+    return atm, [make_kappa_c(a, grid) for a in atm]
+
+
+def config4(seed: int = 4, n_stars: int = 64, n_atomic: int = 200_000, n_bands: int = 200,
+            per_band: int = 500, lam_lo: float = 1500.0, lam_hi: float = 1700.0, W: int = 1500,
+            n_pix: Optional[int] = 8575, nk_scale: float = 1.0) -> Batch:
+    """Batched many-star workload: 64 stars with seeded (Teff, log g, [M/H]) on the
+    config-1 grid and instrument; a master list of 3e5 lines (config-1 recipe: 2e5
+    atomic + 200 bands of 500); star k keeps its top-N_k lines by the strength proxy,
+    N_k = round(exp U[ln 2e4, ln 3e5]) (times nk_scale, for scaled-down variants)."""
+    base = config1(seed=seed, lam_lo=lam_lo, lam_hi=lam_hi, n_bands=n_bands, per_band=per_band,
+                   n_atomic=n_atomic, W=W, n_pix=n_pix, name="config4")
+    teff, logg, mh, nk = config4_stars(seed, n_stars)
+    atm, kc = _batch_atmospheres(teff, logg, mh, base.atmos.n_species, (36, 37, 38, 39), seed + 500, base.grid)
+    nl = base.lines.n_lines
+    subsets = []
+    for a, n in zip(atm, nk):
+        n = int(min(nl, max(1, round(n * nk_scale))))
+        order = np.argsort(-strength_proxy(a, base.lines), kind="stable")
+        subsets.append(np.sort(order[:n]).astype(np.int32))
+    return Batch("config4", atm, base.grid, base.lines, kc, subsets, base.instrument, base.elem_of_species,
+                 base.n_elem)
+
+
+def config4_joint(seed: int = 4, n_common: int = 100_000, **kw):
+    """Joint two-star calibration step: solar-like (5777, 4.44, 0.0) and giant-like
+    (4286, 1.66, -0.52) stars on the config-4 master list, both using the n_common
+    lines with the highest mean strength proxy, shared corrections.  Returns
+    (batch, truth) with truth corrections Delta log gf ~ N(0, 0.1), Delta log gamma6
+    ~ N(0, 0.2) on the master list and per-star pixel noise (seed 7, sigma 1/200)."""
+    full = config4(seed=seed, n_stars=1, **kw)
+    teff, logg, mh = np.array([5777.0, 4286.0]), np.array([4.44, 1.66]), np.array([0.0, -0.52])
+    atm, kc = _batch_atmospheres(teff, logg, mh, full.atmos[0].n_species, (36, 37, 38, 39), seed + 500, full.grid)
+    score = 0.5 * (strength_proxy(atm[0], full.lines) + strength_proxy(atm[1], full.lines))
+    n = int(min(n_common, full.lines.n_lines))
+    common = np.sort(np.argsort(-score, kind="stable")[:n]).astype(np.int32)
+    b = Batch("config4-joint", atm, full.grid, full.lines, kc, [common, common.copy()], full.instrument,
+              full.elem_of_species, full.n_elem)
+    rng = np.random.default_rng(7)
+    nl = full.lines.n_lines
+    n_out = full.instrument.pix_lambda_nm.size if full.instrument is not None else full.grid.n_lambda
+    truth = {"dlog_gf": rng.normal(0.0, 0.1, nl).astype(np.float32),
+             "dlog_gamma6": rng.normal(0.0, 0.2, nl).astype(np.float32),
+             "noise": rng.normal(0.0, 1.0 / 200.0, (2, n_out)),
+             "weight": 200.0 ** 2}
+    return b, truth
+
+
+def small_batch(n_stars: int = 3, span_nm: float = 2.0, seed: int = 21, W: int = 1500,
+                with_instrument: bool = True) -> Batch:
+    """Scaled-down config 4 for element-wise parity: a ~2 nm slice of the config-1
+    recipe, stars with uneven line subsets (one empty-ish, one full, one random)."""
+    lam_lo = 1600.0
+    lam_hi = lam_lo + span_nm
+    frac = span_nm / 200.0
+    base = config1(seed=seed, lam_lo=lam_lo, lam_hi=lam_hi, n_bands=0, per_band=500,
+                   n_atomic=max(8, int(round(200_000 * frac))), W=W,
+                   n_pix=8575 if with_instrument else None, name="batch-small")
+    teff, logg, mh, _ = config4_stars(seed, n_stars)
+    atm, kc = _batch_atmospheres(teff, logg, mh, base.atmos.n_species, (36, 37, 38, 39), seed + 500, base.grid)
+    nl = base.lines.n_lines
+    rng = np.random.default_rng(seed + 9)
+    subsets = []
+    for k in range(n_stars):
+        if k % 3 == 0:
+            idx = np.arange(nl)
+        elif k % 3 == 1:
+            idx = np.sort(rng.choice(nl, max(1, nl // 7), replace=False))
+        else:
+            idx = np.sort(rng.choice(nl, nl // 2, replace=False))
+        subsets.append(idx.astype(np.int32))
+    return Batch("batch-small", atm, base.grid, base.lines, kc, subsets, base.instrument, base.elem_of_species,
+                 base.n_elem)

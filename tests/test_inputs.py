@@ -44,3 +44,47 @@ def test_atmosphere_physical_ranges():
     assert np.all(at.T > 2000) and np.all(at.T < 20000)
     assert np.all(at.n_pert > at.n_e)
     assert np.all(at.pop > 0)
+
+
+def test_config4_batch_recipe():
+    b = I.config4()
+    assert b.n_stars == 64 and b.lines.n_lines == 300_000
+    teff, logg, mh, nk = I.config4_stars(4, 64)
+    sizes = np.array([len(s) for s in b.subsets])
+    assert np.array_equal(sizes, np.minimum(nk, 300_000))
+    assert sizes.min() >= 20_000 and sizes.max() <= 300_000
+    for s in b.subsets[:5]:
+        assert np.all(np.diff(s) > 0) and s.min() >= 0 and s.max() < 300_000
+    # each star keeps its strongest lines by the proxy
+    p = I.strength_proxy(b.atmos[0], b.lines)
+    kept = np.zeros(300_000, bool)
+    kept[b.subsets[0]] = True
+    assert p[kept].min() >= p[~kept].max()
+    assert [a.teff for a in b.atmos] == list(teff)
+    # one chemistry for every star: same masses and partition pattern, scaled by [M/H]
+    assert np.array_equal(b.atmos[0].mass_amu, b.atmos[7].mass_amu)
+    c = I.config4()
+    assert all(np.array_equal(x, y) for x, y in zip(b.subsets, c.subsets))
+
+
+def test_config4_joint_and_small_batch():
+    jb, truth = I.config4_joint()
+    assert jb.n_stars == 2 and len(jb.subsets[0]) == 100_000
+    assert np.array_equal(jb.subsets[0], jb.subsets[1])
+    assert (jb.atmos[0].teff, jb.atmos[1].teff) == (5777.0, 4286.0)
+    assert truth["noise"].shape == (2, 8575)
+    sb = I.small_batch(n_stars=3)
+    assert [len(s) for s in sb.subsets][0] == sb.lines.n_lines
+    st = sb.star(1)
+    assert st.lines.n_lines == len(sb.subsets[1])
+    assert np.array_equal(st.lines.lambda_nm, sb.lines.lambda_nm[sb.subsets[1]])
+
+
+def test_recipes_give_realistic_line_depths(oracle):
+    """The population scale of each workload gives a spectrum with continuum windows and
+    saturated cores, not a saturated line forest (checked on small slices with the oracle)."""
+    for prob in (I.config0(n_lambda=1500, n_lines=750),
+                 I.small_config1(n_lambda_span_nm=3.0, seed=13, with_instrument=False)):
+        f = oracle.forward(prob)["f"]
+        p5, p50 = np.percentile(f, [5, 50])
+        assert 0.8 < p50 < 0.995 and p5 < 0.8, (prob.name, p5, p50)
