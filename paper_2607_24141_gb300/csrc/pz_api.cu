@@ -330,7 +330,7 @@ static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, 
         destroy_ctx(c);
         return st;
     };
-    if (ensure_device_tables() != PZ_OK) return bail(PZ_ECUDA);
+    if (ensure_device_tables() != PZ_OK || ensure_expn_table() != PZ_OK) return bail(PZ_ECUDA);
     if (cuda_check(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking), "stream")) return bail(PZ_ECUDA);
 
     // ---- lines: centre placement, drop, sort within each star ----

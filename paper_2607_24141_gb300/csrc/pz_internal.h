@@ -191,8 +191,9 @@ void prof_end(pz_ctx *c, cudaStream_t s, int kid);
 pz_status fail(pz_status st, const std::string &msg);
 pz_status cuda_check(cudaError_t e, const char *what);
 
-// one-time per-device constant tables (pz_line.cu)
+// one-time per-device constant tables (pz_line.cu: Voigt; pz_rt.cu: E_n)
 pz_status ensure_device_tables();
+pz_status ensure_expn_table();
 
 // launches (return cudaGetLastError() of the launch)
 cudaError_t launch_line_fwd_mixed(pz_ctx *c, cudaStream_t s);

@@ -13,6 +13,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <vector>
 
 #include "pz_internal.h"
 
@@ -20,10 +23,105 @@ namespace pz {
 
 constexpr double kEuler = 0.57721566490153286061;
 
-// E_2, E_3, E_4 at x >= 0.
-//   x <= 2 : E_1 from its power series, then E_{n+1} = (e^-x - x E_n)/n upward;
-//   x  > 2 : E_4 from its continued fraction (bottom-up, depth by range), then
-//            E_n = (e^-x - n E_{n+1})/x downward (stable for x > n).
+// ---------------------------------------------------------------------------
+// E_2, E_3, E_4 from a Taylor table of E_4 (FP64).
+//
+// The FP64 units of this GPU are few, so the exponential integrals (two calls per
+// wavelength and layer in the flux, one in its adjoint) must cost few FP64
+// instructions and no divides.  E_4 is expanded about table nodes x0,
+//   E_4(x0 + t) = sum_k c_k t^k,  c_k = E_4^(k)(x0) / k!,
+// and E_3 = -E_4', E_2 = E_4'' come from the same polynomial (Horner with
+// derivatives), using E_n' = -E_{n-1}.  The coefficients are exact derivatives:
+//   E_4^(k) = (-1)^k E_{4-k} (k <= 4, E_0 = e^-x / x),
+//   E_0^(m) = (-1)^m e^-x m! sum_{i=0..m} x^-(i+1) / (m-i)!   (all terms positive).
+// Nodes: 2^-40 <= x < 2: eight per binade at the centres of the binade's eighths
+// (|t| / x0 <= 1/17, inside the radius of convergence x0 of the logarithmic
+// singularity at 0); 2 <= x < 40: spacing 1/8 (|t| <= 1/16).  Fourteen terms
+// leave a truncation error below 1e-16 relative in both ranges.  Outside them:
+// x < 2^-40 the leading terms of the small-x expansion, x >= 40 the continued
+// fraction of E_4 (8 levels), x > 740 zero.
+// ---------------------------------------------------------------------------
+constexpr int kExpnK = 14;                      // Taylor terms per node
+constexpr int kExpnMinExp = -40;                // smallest binade 2^-40
+constexpr int kExpnGeo = (1 - kExpnMinExp) * 8; // nodes below 2: binades -40..0
+constexpr double kExpnUni0 = 2.0, kExpnUni1 = 40.0;
+constexpr int kExpnUni = (int)((kExpnUni1 - kExpnUni0) * 8);   // nodes on [2, 40)
+constexpr int kExpnNodes = kExpnGeo + kExpnUni;
+
+__device__ double g_expn_tab[kExpnNodes * kExpnK];
+
+// host: E_1..E_4 at x > 0 in extended precision (series below 2, continued fraction above)
+static void expn_host(long double x, long double E[5]) {
+    const long double ex = expl(-x);
+    if (x <= 2.0L) {
+        long double term = 1.0L, s = 0.0L;
+        for (int k = 1; k < 200; ++k) {
+            term *= -x / k;
+            s += term / k;
+            if (fabsl(term) < 1e-30L) break;
+        }
+        E[1] = -(long double)kEuler - logl(x) - s;
+        for (int n = 1; n < 4; ++n) E[n + 1] = (ex - x * E[n]) / n;
+    } else {
+        const int K = 600;
+        long double f = x + 4.0L + 2.0L * K;
+        for (int k = K; k >= 1; --k) f = x + 4.0L + 2.0L * (k - 1) - (long double)k * (3.0L + k) / f;
+        E[4] = ex / f;
+        for (int n = 3; n >= 1; --n) E[n] = (ex - n * E[n + 1]) / x;
+    }
+    E[0] = ex / x;
+}
+
+static void expn_node_coeffs(long double x0, double *c) {
+    long double E[5];
+    expn_host(x0, E);
+    long double fact = 1.0L;   // k!
+    for (int k = 0; k < kExpnK; ++k) {
+        if (k > 0) fact *= k;
+        long double d;
+        if (k <= 4) {
+            d = ((k & 1) ? -1.0L : 1.0L) * E[4 - k];
+        } else {
+            const int m = k - 4;
+            long double sum = 0.0L, mf = 1.0L;   // m! / (m - i)! built as a running product
+            for (int i = 0; i <= m; ++i) {
+                if (i > 0) mf *= (m - i + 1);
+                sum += mf * powl(x0, -(long double)(i + 1));
+            }
+            d = ((m & 1) ? -1.0L : 1.0L) * expl(-x0) * sum;
+        }
+        c[k] = (double)(d / fact);
+    }
+}
+
+static double expn_node_x0(int j) {
+    if (j < kExpnGeo) {
+        const int e = kExpnMinExp + j / 8, m = j % 8;
+        return std::ldexp(1.0 + (m + 0.5) / 8.0, e);
+    }
+    return kExpnUni0 + (j - kExpnGeo + 0.5) / 8.0;
+}
+
+pz_status ensure_expn_table() {
+    static std::mutex mu;
+    static std::vector<double> tab;
+    static bool done[64] = {false};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_check(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) return fail(PZ_EINVAL, "device ordinal out of range");
+    std::lock_guard<std::mutex> lk(mu);
+    if (done[dev]) return PZ_OK;
+    if (tab.empty()) {
+        tab.resize((size_t)kExpnNodes * kExpnK);
+        for (int j = 0; j < kExpnNodes; ++j) expn_node_coeffs((long double)expn_node_x0(j), &tab[(size_t)j * kExpnK]);
+    }
+    e = cudaMemcpyToSymbol(g_expn_tab, tab.data(), sizeof(double) * tab.size());
+    if (e != cudaSuccess) return cuda_check(e, "upload E_n table");
+    done[dev] = true;
+    return PZ_OK;
+}
+
 __device__ __forceinline__ void expn234(double x, double &E2, double &E3, double &E4) {
     if (x <= 0.0) {
         E2 = 1.0;
@@ -31,29 +129,47 @@ __device__ __forceinline__ void expn234(double x, double &E2, double &E3, double
         E4 = 1.0 / 3.0;
         return;
     }
+    if (x < kExpnUni1) {
+        int j;
+        double x0;
+        if (x < kExpnUni0) {
+            if (x < 0x1p-40) {
+                // E_2 = 1 + x (ln x + gamma - 1) + O(x^2), E_3 = 1/2 - x + O(x^2 ln x), E_4 = 1/3 - x/2 + O(x^2)
+                E2 = 1.0 + x * (log(x) + (kEuler - 1.0));
+                E3 = 0.5 - x;
+                E4 = 1.0 / 3.0 - 0.5 * x;
+                return;
+            }
+            const long long bits = __double_as_longlong(x);
+            const int ex = (int)((bits >> 52) & 0x7ff) - 1023, m = (int)((bits >> 49) & 7);
+            j = (ex - kExpnMinExp) * 8 + m;
+            x0 = __longlong_as_double((bits & ~((1LL << 49) - 1)) | (1LL << 48));
+        } else {
+            j = kExpnGeo + (int)((x - kExpnUni0) * 8.0);
+            x0 = kExpnUni0 + ((j - kExpnGeo) + 0.5) * 0.125;
+        }
+        const double t = x - x0;                       // exact
+        const double *c = g_expn_tab + j * kExpnK;
+        double p = __ldg(c + kExpnK - 1), d1 = 0.0, d2 = 0.0;
+#pragma unroll
+        for (int k = kExpnK - 2; k >= 0; --k) {
+            d2 = fma(d2, t, d1);
+            d1 = fma(d1, t, p);
+            p = fma(p, t, __ldg(c + k));
+        }
+        E4 = p;
+        E3 = -d1;
+        E2 = 2.0 * d2;
+        return;
+    }
     if (x > 740.0) {
         E2 = E3 = E4 = 0.0;
         return;
     }
-    double ex = exp(-x);
-    if (x <= 2.0) {
-        // E_1 = -gamma - ln x - sum_{k>=1} (-x)^k / (k k!)
-        double term = 1.0, s = 0.0;
-#pragma unroll 4
-        for (int k = 1; k <= 32; ++k) {
-            term *= -x / k;
-            s += term / k;
-        }
-        double E1 = -kEuler - log(x) - s;
-        E2 = ex - x * E1;
-        E3 = 0.5 * (ex - x * E2);
-        E4 = (ex - x * E3) * (1.0 / 3.0);
-        return;
-    }
-    int K = x < 3.0 ? 64 : (x < 5.0 ? 40 : (x < 10.0 ? 24 : (x < 30.0 ? 16 : 8)));
-    // E_4(x) = e^-x / (x + 4 - 1*4/(x + 6 - 2*5/(x + 8 - ...)))
-    double f = x + 4.0 + 2.0 * K;
-    for (int k = K; k >= 1; --k) f = x + 4.0 + 2.0 * (k - 1) - (double)k * (3.0 + k) / f;
+    // E_4(x) = e^-x / (x + 4 - 1*4/(x + 6 - 2*5/(x + 8 - ...))), then downward
+    const double ex = exp(-x);
+    double f = x + 4.0 + 16.0;
+    for (int k = 8; k >= 1; --k) f = x + 4.0 + 2.0 * (k - 1) - (double)k * (3.0 + k) / f;
     E4 = ex / f;
     E3 = (ex - 3.0 * E4) / x;
     E2 = (ex - 2.0 * E3) / x;
@@ -526,6 +642,7 @@ __global__ void k_probe_expn(const double *x, int64_t n, double *out) {
 
 cudaError_t launch_probe_expn(const double *x, int64_t n, double *out, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    if (ensure_expn_table() != PZ_OK) return cudaErrorInitializationError;
     k_probe_expn<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, n, out);
     return cudaGetLastError();
 }

@@ -137,7 +137,7 @@ def test_batch_gradients_are_star_sums(oracle):
         gab_t = torch.empty(b.n_elem, dtype=torch.float32, device=dev)
         s.backward(dLdf, g[0], g[1], gab_t)
         torch.cuda.synchronize()
-        assert abs(loss.item() / L - 1) < (1e-4 if prec == pz.PZ_MIXED else 1e-9)
+        assert abs(loss.item() / L - 1) < (1e-4 if prec == pz.PZ_MIXED else 1e-7)
         e1 = rel_metric(g[0].cpu().numpy().astype(np.float64), ggf).max()
         e2 = rel_metric(g[1].cpu().numpy().astype(np.float64), gg6).max()
         e3 = rel_metric(gab_t.cpu().numpy().astype(np.float64), gab).max()
@@ -174,7 +174,7 @@ def test_calib_step_graph_matches_eager_calls():
     gab_s = torch.empty(b.n_elem, dtype=torch.float32, device=dev)
     s.calib_step(y, None, *lr, loss_s, g_s[0], g_s[1], gab_s)
     torch.cuda.synchronize()
-    assert abs(loss_s.item() / L_e - 1) < 1e-9
+    assert abs(loss_s.item() / L_e - 1) < 1e-7      # near-core sums: last-bit order effects only
     for a, c in zip(g_s + [gab_s], g_e + [gab_e]):
         a, c = a.cpu().numpy().astype(np.float64), c.cpu().numpy().astype(np.float64)
         assert np.max(np.abs(a - c)) <= 1e-5 * np.max(np.abs(c)) + 1e-30

@@ -40,7 +40,11 @@ def test_fp32_voigt_accuracy(oracle):
 
 def test_fp64_expn(oracle):
     import torch
-    x = np.concatenate([[0.0], np.logspace(-12, 0, 200), np.linspace(1, 3, 200), np.linspace(3, 745, 400)])
+    edges = np.array([2.0 ** -40, 2.0, 40.0, 0.5, 1.0, 0.25])
+    x = np.concatenate([[0.0], np.logspace(-16, -11, 40), np.logspace(-12, 0, 200), np.linspace(1, 3, 200),
+                        np.linspace(3, 745, 400), np.linspace(38.0, 42.0, 64),
+                        edges * (1 - 1e-15), edges, edges * (1 + 1e-15),
+                        np.random.default_rng(3).uniform(0.0, 50.0, 500)])
     xt = torch.tensor(x, dtype=torch.float64, device="cuda")
     out = torch.empty(3 * x.size, dtype=torch.float64, device="cuda")
     pz.pz_probe_expn(xt, out)
