@@ -457,7 +457,8 @@ def main():
     except Exception:
         pass
     clk_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
-    share = {k: v[0] for k, v in ktimes.items()}
+    # near_* are the near-core parts already inside line_fwd / line_bwd; step is unused here
+    share = {k: v[0] for k, v in ktimes.items() if k not in ("near_fwd", "near_bwd", "step")}
     dom = max(("line_fwd", "line_bwd"), key=lambda k: share[k])
     t_dom = share[dom] * 1e-3 / max(ktimes[dom][1], 1)          # s per launch
     ops = OPS[dom]

@@ -252,7 +252,8 @@ int32_t pz_last_launch_count(const pz_ctx *ctx);
  * (the backward uses half) and the minimum number of resident CTAs per SM the
  * kernels are compiled for (a register budget).  Values <= 0 keep the current
  * setting; the next launch uses the new tiling.  Supported (lambda, depth,
- * CTAs) triples: (4,9,1-3) (4,6,1-4) (4,12,1-2) (2,9,1-4) (2,12,1-3) (2,6,4).
+ * CTAs) triples: (4,6,1-4) (4,8,1-3) (4,12,1-2) (2,6,4) (2,8,2-4) (2,12,1-3);
+ * depths per warp are even (the far-wing kernels evaluate depth pairs).
  * Errors: PZ_EINVAL for an unsupported combination or a chunk that does not fit
  * in shared memory. */
 pz_status pz_set_tiling(pz_ctx *ctx, int32_t lambda_per_thread, int32_t depth_per_warp,
@@ -262,8 +263,8 @@ pz_status pz_set_tiling(pz_ctx *ctx, int32_t lambda_per_thread, int32_t depth_pe
 
 /* Kernel families timed by the built-in CUDA-event profiler. */
 typedef enum {
-    PZ_K_LINE_FWD = 0,     /* windowed Voigt sum (mixed or FP64 form) */
-    PZ_K_LINE_BWD = 1,     /* per-line windowed gradient reduction */
+    PZ_K_LINE_FWD = 0,     /* windowed Voigt sum (mixed or FP64 form; mixed: far-wing + near-core) */
+    PZ_K_LINE_BWD = 1,     /* per-line windowed gradient reduction (mixed: far-wing + near-core) */
     PZ_K_FLUX = 2,         /* tau + closed-form flux, both branches */
     PZ_K_RT_ADJOINT = 3,   /* adjoint of flux and tau */
     PZ_K_INSTRUMENT = 4,   /* weight build + apply (or identity) */
@@ -271,7 +272,9 @@ typedef enum {
     PZ_K_LOSS = 6,         /* chi-square and its seed */
     PZ_K_OTHER = 7,        /* corrections, finalisation, copies */
     PZ_K_STEP = 8,         /* a whole pz_calib_step graph launch */
-    PZ_NK = 9
+    PZ_K_NEAR_FWD = 9,     /* the near-core part of PZ_K_LINE_FWD (mixed form; also counted there) */
+    PZ_K_NEAR_BWD = 10,    /* the near-core part of PZ_K_LINE_BWD (mixed form; also counted there) */
+    PZ_NK = 11
 } pz_kernel_id;
 
 /* enable != 0: every kernel launch of this context is bracketed by CUDA events

@@ -241,7 +241,7 @@ def pz_set_tiling(ctx, lambda_per_thread=0, depth_per_warp=0, warps_per_cta=0, l
 
 
 KERNEL_NAMES = ("line_fwd", "line_bwd", "flux", "rt_adjoint", "instrument", "inst_adjoint", "loss", "other",
-                "step")
+                "step", "near_fwd", "near_bwd")
 
 
 def pz_set_profiling(ctx, enable=True):

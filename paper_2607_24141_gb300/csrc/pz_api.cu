@@ -52,27 +52,26 @@ static void prof_fold(pz_ctx *c) {
     c->marks.clear();
 }
 
-void prof_begin(pz_ctx *c, cudaStream_t s) {
-    if (!c->profiling || c->capturing) return;
+cudaEvent_t prof_begin(pz_ctx *c, cudaStream_t s) {
+    if (!c->profiling || c->capturing) return nullptr;
     cudaEvent_t a = prof_event(c);
     cudaEventRecord(a, s);
-    c->pending_begin = a;
+    return a;
 }
 
-void prof_end(pz_ctx *c, cudaStream_t s, int kid) {
-    if (!c->profiling || c->capturing || !c->pending_begin) return;
+void prof_end(pz_ctx *c, cudaStream_t s, int kid, cudaEvent_t a) {
+    if (!a) return;
     cudaEvent_t b = prof_event(c);
     cudaEventRecord(b, s);
-    c->marks.push_back({c->pending_begin, b, kid});
-    c->pending_begin = nullptr;
+    c->marks.push_back({a, b, kid});
     if (c->marks.size() > 8192) prof_fold(c);
 }
 
 template <class Fn>
 static cudaError_t timed(pz_ctx *c, cudaStream_t s, int kid, Fn &&fn) {
-    prof_begin(c, s);
+    cudaEvent_t a = prof_begin(c, s);
     cudaError_t e = fn();
-    prof_end(c, s, kid);
+    prof_end(c, s, kid, a);
     return e;
 }
 
@@ -577,9 +576,9 @@ pz_status pz_set_tiling(pz_ctx *c, int32_t J, int32_t DS, int32_t GW, int32_t LC
     if (t.GW < 1 || t.GW > 4) return fail(PZ_EINVAL, "pz_set_tiling: warps_per_cta must be in [1, 4]");
     if (t.LC < 1 || t.LC > 512) return fail(PZ_EINVAL, "pz_set_tiling: lines_per_chunk must be in [1, 512]");
     if (LC > 0) t.LCB = std::max(1, t.LC / 2);
-    size_t gen = (size_t)t.DS * 32 * t.GW * 16;
+    size_t gen = (size_t)t.DS * 32 * t.GW * 32;
     size_t smem_fwd = (size_t)t.LC * t.DS * t.GW * 32 + t.LC * 16 + gen;
-    size_t smem_bwd = (size_t)t.LCB * t.DS * t.GW * 64 + t.LCB * 16 + (size_t)t.LCB * t.GW * 8;
+    size_t smem_bwd = (size_t)t.LCB * t.DS * t.GW * 56 + t.LCB * 16 + (size_t)t.LCB * t.GW * 8;
     if (smem_fwd > 200 * 1024 || smem_bwd > 200 * 1024)
         return fail(PZ_EINVAL, "pz_set_tiling: shared-memory chunk too large");
     drop_graph(c);
@@ -868,9 +867,9 @@ pz_status pz_calib_step(pz_ctx *c, const float *y, const float *w, int64_t n, fl
         G.n = n;
         G.launches = c->launches;
     }
-    prof_begin(c, s);
+    cudaEvent_t ev = prof_begin(c, s);
     cudaError_t e = cudaGraphLaunch(G.exec, s);
-    prof_end(c, s, PZ_K_STEP);
+    prof_end(c, s, PZ_K_STEP, ev);
     PZ_CUDA(e, "pz_calib_step: graph launch");
     c->launches = G.launches;
     c->have_kline = c->have_flux = c->have_inst = true;

@@ -44,11 +44,11 @@ constexpr int kWeidN64 = 32;      // Weideman rational order (FP64 plain form)
 // Mixed-precision line-kernel tiling.
 struct Tiling {
     int J = 4;       // lambda points per thread (contiguous)
-    int DS = 9;      // depths per warp
+    int DS = 6;      // depths per warp (even: the far-wing kernels work on depth pairs)
     int GW = 4;      // warps per CTA (each a depth slab)
-    int LC = 32;     // lines per shared-memory chunk (forward)
-    int LCB = 16;    // lines per shared-memory chunk (backward)
-    int minb = 1;    // minimum resident CTAs per SM the kernels are compiled for
+    int LC = 64;     // lines per shared-memory chunk (forward)
+    int LCB = 32;    // lines per shared-memory chunk (backward)
+    int minb = 4;    // minimum resident CTAs per SM the kernels are compiled for
     int lambda_per_tile() const { return 32 * J; }
     int depth_per_cta() const { return DS * GW; }
 };
@@ -176,7 +176,6 @@ struct pz_ctx {
     };
     std::vector<Mark> marks;          // recorded, not yet folded
     std::vector<cudaEvent_t> ev_pool; // free events
-    cudaEvent_t pending_begin = nullptr;
     double k_ms[PZ_NK] = {0};
     int64_t k_count[PZ_NK] = {0};
 };
@@ -184,8 +183,8 @@ struct pz_ctx {
 namespace pz {
 
 // profiler brackets around a launch (pz_api.cu); no-ops unless profiling is on
-void prof_begin(pz_ctx *c, cudaStream_t s);
-void prof_end(pz_ctx *c, cudaStream_t s, int kid);
+cudaEvent_t prof_begin(pz_ctx *c, cudaStream_t s);
+void prof_end(pz_ctx *c, cudaStream_t s, int kid, cudaEvent_t begin);
 
 // error reporting (pz_api.cu)
 pz_status fail(pz_status st, const std::string &msg);

@@ -261,9 +261,91 @@ __device__ __forceinline__ bool fast_line(const LineArgs &g, const LineInfo &inf
     return full && dmin >= __ldg(g.thr + info.sp * g.nslab + slab);
 }
 
-// Compensation-term slot of cell (dd, j) of thread tid (the J points of a thread are
-// contiguous: one vector access per depth).
-__device__ __forceinline__ int lo_slot(int dd, int tid, int nthr) { return (dd * nthr + tid) << 2; }
+// ---- packed FP32 pairs ------------------------------------------------------
+// The far-wing kernels evaluate two depths of one (line, lambda) cell with one
+// instruction: a register pair {value at depth d, value at depth d + 1} and the
+// f32x2 forms of mul and fma (each half rounded exactly as the scalar op).  This
+// halves the FP32 issue slots of the inner loop; the two reciprocals stay scalar.
+typedef unsigned long long f2_t;
+
+__device__ __forceinline__ f2_t f2_pack(float lo, float hi) {
+    f2_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f2_t v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2_t f2_mul(f2_t a, f2_t b) {
+    f2_t r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2_t f2_fma(f2_t a, f2_t b, f2_t c) {
+    f2_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+// reciprocal of both halves (rcp.approx.ftz, as rcp_approx)
+__device__ __forceinline__ f2_t f2_rcp(f2_t a) {
+    f2_t r;
+    asm("{\n\t.reg .f32 lo, hi;\n\tmov.b64 {lo, hi}, %1;\n\trcp.approx.ftz.f32 lo, lo;\n\t"
+        "rcp.approx.ftz.f32 hi, hi;\n\tmov.b64 %0, {lo, hi};\n\t}"
+        : "=l"(r) : "l"(a));
+    return r;
+}
+
+// Shared-memory layout of the per-(line, depth) prefactors for the packed kernels:
+// per line and depth pair, parameter m of both depths sits at float offset
+// (m >> 1) * 4 + (m & 1) * 2 + (depth & 1), so one 16-byte load returns the pairs of
+// parameters 2q and 2q + 1.
+//   forward  (8):  k, a^2, B1, B2, B3, B4, B5, A
+//   backward (14): k, a^2, B1, B2, B3, B4, B5, C1, C2, C3, C4, C5, C6, (pad)
+__device__ __forceinline__ int par_off(int m, int dd) { return ((m >> 1) << 2) + ((m & 1) << 1) + (dd & 1); }
+
+// Compensated-sum slots of depth dd of thread tid: the (hi, lo) pairs of its J points,
+// hi at [0, 4) and lo at [4, 8) (the J points of a thread are contiguous: one vector
+// access each).  They live in shared memory and are touched once per line chunk.
+__device__ __forceinline__ int comp_slot(int dd, int tid, int nthr) { return (dd * nthr + tid) << 3; }
+
+// Reduced far-wing form.  Far from the core the polynomial in t = 1/|z|^2 is cut
+// after its t^2 term: H sqrt(pi)/(A a) = t (1 + 1.5 t) and, for dH/da, C1 t (1 +
+// (1.5 - 2a^2) t).  With |v| >= 100 (t <= 1e-4) and a^2 <= 1.5 (s = a^2 t <= 1.5e-4)
+// the dropped terms, (3.75 t^2 + 2 s t + 15 s t^2 + 12 s^2 t^2) relative for H, stay
+// below 7e-8 (about one FP32 rounding) and below 2.2e-7 for dH/da.
+constexpr float kFast2V = 5.0f;      // distance threshold factor: |v| >= 5 x 20
+constexpr float kFast2A2 = 1.5f;     // a^2 bound
+
+// Per-warp fast-path flags of staged line l: bit w set if the line is entirely inside
+// its window over the tile and in the far wing (|v| >= 20) at every depth of warp w's
+// slab; bit 8 + w if, in addition, |v| >= 100 and a^2 <= kFast2A2 at every depth of
+// the slab (reduced form).
+__device__ __forceinline__ int fast_mask(const LineArgs &g, int64_t l, const LineInfo &info, float t0f, float tendf,
+                                         int d0, int DS, int GW) {
+    const float dlo = info.ilf - t0f + info.frac;
+    const float dhi = info.ilf - tendf + info.frac;
+    const float dmin = fmaxf(0.0f, fmaxf(-dlo, dhi));
+    const bool full = (info.ilf - (float)g.W <= t0f) && (info.ilf + (float)g.W >= tendf);
+    if (!full) return 0;
+    int m = 0;
+    for (int w = 0; w < GW; ++w) {
+        const int slab = (d0 + w * DS) / DS;
+        const float thr = __ldg(g.thr + info.sp * g.nslab + slab);
+        if (!(dmin >= thr)) continue;
+        m |= 1 << w;
+        if (!(dmin >= kFast2V * thr)) continue;
+        const float lw = g.lamcm[l] * (float)(1.0 / (4.0 * kPI));
+        const float g4 = g.g4[l], grad = g.grad[l], g6 = g.g6[l];
+        bool ok = true;
+        for (int d = d0 + w * DS; d < min(d0 + (w + 1) * DS, g.nd); ++d) {
+            const float a = fmaf(g4, __ldg(g.ne + d), grad + g6 * __ldg(g.npert + d)) * lw *
+                            __ldg(g.invdv + info.sp * g.nd + d);
+            ok = ok && a * a <= kFast2A2;
+        }
+        if (ok) m |= 1 << (8 + w);
+    }
+    return m;
+}
 
 // Far-wing kernel (forward).  Every cell with |v|^2 + a^2 >= 400 inside its window is
 // evaluated here with the far polynomial; the near-core cells are summed by
@@ -272,28 +354,35 @@ template <int J, int DS>
 __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, const int group, const int lo,
                                              const int hi, const int GW, const int LC) {
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
+    static_assert(DS % 2 == 0, "DS must be even (depth pairs)");
+    constexpr int DP = DS / 2;          // depth pairs per warp
+    constexpr int NPF = 8;              // floats per (line, depth) in shared memory
     extern __shared__ float4 smem4[];
     const int T = 32 * J;
     const int DC = GW * DS;
     const int nthr = blockDim.x;
-    float4 *s_par = smem4;                                              // [LC][DC][2]
-    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * DC * 2);
-    float *s_lo = reinterpret_cast<float *>(s_line + LC);               // [DS][nthr][4] compensation terms
+    float *s_parf = reinterpret_cast<float *>(smem4);                   // [LC][DC/2][2 * NPF]
+    const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(smem4);
+    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * DC * NPF / 4);
+    float *s_comp = reinterpret_cast<float *>(s_line + LC);             // [DS][nthr][8] compensated sums
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int d0 = group * DC;
-    const int slab = (d0 + warp * DS) / DS;
     const int t0 = tile * T;
     const float t0f = (float)t0, tendf = (float)(t0 + T - 1);
     const int lam_thr = t0 + lane * J;
     const float lamf = (float)lam_thr;
 
-    float acc[DS][J], shi[DS][J];
+    f2_t acc[DP][J];
+#pragma unroll
+    for (int dp = 0; dp < DP; ++dp)
+#pragma unroll
+        for (int j = 0; j < J; ++j) acc[dp][j] = 0ull;
 #pragma unroll
     for (int dd = 0; dd < DS; ++dd) {
-#pragma unroll
-        for (int j = 0; j < J; ++j) acc[dd][j] = shi[dd][j] = 0.0f;
-        *reinterpret_cast<float4 *>(s_lo + lo_slot(dd, tid, nthr)) = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 *cs = reinterpret_cast<float4 *>(s_comp + comp_slot(dd, tid, nthr));
+        cs[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+        cs[1] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
     for (int c0 = lo; c0 < hi; c0 += LC) {
@@ -303,9 +392,9 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
             int li = idx / DC, dd = idx - li * DC;
             float p[8];
             line_params<8>(g, c0 + li, d0 + dd, p);
-            float4 *dst = s_par + ((size_t)li * DC + dd) * 2;
-            dst[0] = make_float4(p[0], p[1], p[2], p[3]);
-            dst[1] = make_float4(p[4], p[5], p[6], p[7]);
+            float *dst = s_parf + ((size_t)li * (DC / 2) + (dd >> 1)) * (2 * NPF);
+#pragma unroll
+            for (int m = 0; m < NPF; ++m) dst[par_off(m, dd)] = p[m];
         }
         for (int li = tid; li < nl; li += nthr) {
             int64_t l = c0 + li;
@@ -313,23 +402,48 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
             info.ilf = g.ilf[l];
             info.frac = g.frac[l];
             info.sp = g.sp[l];
-            info.pad = 0;
+            info.pad = fast_mask(g, l, info, t0f, tendf, d0, DS, GW);
             s_line[li] = info;
         }
         __syncthreads();
 
         for (int li = 0; li < nl; ++li) {
             const LineInfo info = s_line[li];
-            const float4 *par = s_par + ((size_t)li * DC + warp * DS) * 2;
-            float u[J];
+            const ulonglong2 *par = s_par + ((size_t)li * (DC / 2) + warp * DP) * (NPF / 2);
+            f2_t u2[J];
 #pragma unroll
-            for (int j = 0; j < J; ++j) u[j] = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
-            if (fast_line(g, info, t0f, tendf, slab)) {
+            for (int j = 0; j < J; ++j) {
+                const float u = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
+                u2[j] = f2_pack(u, u);
+            }
+            if ((info.pad >> (8 + warp)) & 1) {
+                // reduced form: t (B1 + B2 t)
 #pragma unroll
-                for (int dd = 0; dd < DS; ++dd) {
-                    const float4 p0 = par[2 * dd], p1 = par[2 * dd + 1];
+                for (int dp = 0; dp < DP; ++dp) {
+                    const ulonglong2 q0 = par[4 * dp], q1 = par[4 * dp + 1];
 #pragma unroll
-                    for (int j = 0; j < J; ++j) acc[dd][j] = far_acc(u[j] * p0.x, p0, p1, acc[dd][j]);
+                    for (int j = 0; j < J; ++j) {
+                        const f2_t x = f2_mul(u2[j], q0.x);
+                        const f2_t t = f2_rcp(f2_fma(x, x, q0.y));
+                        acc[dp][j] = f2_fma(t, f2_fma(t, q1.y, q1.x), acc[dp][j]);
+                    }
+                }
+            } else if ((info.pad >> warp) & 1) {
+#pragma unroll
+                for (int dp = 0; dp < DP; ++dp) {
+                    const ulonglong2 q0 = par[4 * dp], q1 = par[4 * dp + 1], q2 = par[4 * dp + 2];
+                    const ulonglong2 q3 = par[4 * dp + 3];
+                    // q0 = (k, a^2), q1 = (B1, B2), q2 = (B3, B4), q3 = (B5, A)
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const f2_t x = f2_mul(u2[j], q0.x);
+                        const f2_t t = f2_rcp(f2_fma(x, x, q0.y));
+                        f2_t h = f2_fma(t, q3.x, q2.y);
+                        h = f2_fma(t, h, q2.x);
+                        h = f2_fma(t, h, q1.y);
+                        h = f2_fma(t, h, q1.x);
+                        acc[dp][j] = f2_fma(t, h, acc[dp][j]);
+                    }
                 }
             } else {
                 // line near the tile or partly outside its window: far cells inside the window only
@@ -341,13 +455,26 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
                     inwin[j] = di >= -g.W && di <= g.W;
                 }
 #pragma unroll
-                for (int dd = 0; dd < DS; ++dd) {
-                    const float4 p0 = par[2 * dd], p1 = par[2 * dd + 1];
+                for (int dp = 0; dp < DP; ++dp) {
+                    const ulonglong2 q0 = par[4 * dp], q1 = par[4 * dp + 1], q2 = par[4 * dp + 2];
+                    const ulonglong2 q3 = par[4 * dp + 3];
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        const float x = u[j] * p0.x;
-                        const float r = far_acc(x, p0, p1, acc[dd][j]);
-                        acc[dd][j] = (inwin[j] && fmaf(x, x, p0.y) >= kFar2) ? r : acc[dd][j];
+                        const f2_t x = f2_mul(u2[j], q0.x);
+                        const f2_t r2 = f2_fma(x, x, q0.y);
+                        const f2_t t = f2_rcp(r2);
+                        f2_t h = f2_fma(t, q3.x, q2.y);
+                        h = f2_fma(t, h, q2.x);
+                        h = f2_fma(t, h, q1.y);
+                        h = f2_fma(t, h, q1.x);
+                        const f2_t r = f2_fma(t, h, acc[dp][j]);
+                        float r2a, r2b, ra, rb, aa, ab;
+                        f2_unpack(r2, r2a, r2b);
+                        f2_unpack(r, ra, rb);
+                        f2_unpack(acc[dp][j], aa, ab);
+                        aa = (inwin[j] && r2a >= kFar2) ? ra : aa;
+                        ab = (inwin[j] && r2b >= kFar2) ? rb : ab;
+                        acc[dp][j] = f2_pack(aa, ab);
                     }
                 }
             }
@@ -355,21 +482,32 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
         // fold the chunk partials into the compensated sums (2Sum; the rounding
         // terms accumulate in this thread's shared-memory slots)
 #pragma unroll
-        for (int dd = 0; dd < DS; ++dd) {
-            float4 *lslot = reinterpret_cast<float4 *>(s_lo + lo_slot(dd, tid, nthr));
-            float4 lsum = *lslot;
-            float lj[4] = {lsum.x, lsum.y, lsum.z, lsum.w};
+        for (int dp = 0; dp < DP; ++dp) {
+            float pa[J], pb[J];
 #pragma unroll
             for (int j = 0; j < J; ++j) {
-                float p = acc[dd][j], h = shi[dd][j];
-                float s = h + p;
-                float bp = s - h;
-                float e = (h - (s - bp)) + (p - bp);
-                shi[dd][j] = s;
-                lj[j] += e;
-                acc[dd][j] = 0.0f;
+                f2_unpack(acc[dp][j], pa[j], pb[j]);
+                acc[dp][j] = 0ull;
             }
-            *lslot = make_float4(lj[0], lj[1], lj[2], lj[3]);
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int dd = 2 * dp + h2;
+                float4 *cs = reinterpret_cast<float4 *>(s_comp + comp_slot(dd, tid, nthr));
+                const float4 hsum = cs[0], lsum = cs[1];
+                float hj[4] = {hsum.x, hsum.y, hsum.z, hsum.w};
+                float lj[4] = {lsum.x, lsum.y, lsum.z, lsum.w};
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    float p = h2 ? pb[j] : pa[j], h = hj[j];
+                    float s = h + p;
+                    float bp = s - h;
+                    float e = (h - (s - bp)) + (p - bp);
+                    hj[j] = s;
+                    lj[j] += e;
+                }
+                cs[0] = make_float4(hj[0], hj[1], hj[2], hj[3]);
+                cs[1] = make_float4(lj[0], lj[1], lj[2], lj[3]);
+            }
         }
     }
 
@@ -379,7 +517,9 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
         int d = d0 + warp * DS + dd;
         if (d >= g.nd) continue;
         float c2T = __ldg(g.c2T + d);
-        const float4 lsum = *reinterpret_cast<const float4 *>(s_lo + lo_slot(dd, tid, nthr));
+        const float4 *cs = reinterpret_cast<const float4 *>(s_comp + comp_slot(dd, tid, nthr));
+        const float4 hsum = cs[0], lsum = cs[1];
+        const float hj[4] = {hsum.x, hsum.y, hsum.z, hsum.w};
         const float lj[4] = {lsum.x, lsum.y, lsum.z, lsum.w};
         const float *nrow = g.knear + (int64_t)d * g.ld + lam_thr;
         float v[J];
@@ -387,7 +527,7 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
         for (int j = 0; j < J; ++j) {
             float lam = g.lam0cm * expf((float)(lam_thr + j) * g.lnr);
             float stim = -expm1f(-c2T / lam);
-            float hi2 = shi[dd][j], nj = nrow[j];
+            float hi2 = hj[j], nj = nrow[j];
             float s = hi2 + nj;                    // 2Sum of the near-core sum into the total
             float bp = s - hi2;
             float e = (hi2 - (s - bp)) + (nj - bp);
@@ -408,36 +548,103 @@ __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int 
     });
 }
 
+// Reduced far-wing backward form (lines flagged for it): H and dH/da polynomials cut
+// after their t^2 terms.
+template <int J, int DP>
+__device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, const f2_t (&u2)[J],
+                                                     const f2_t (&gv)[DP][J], f2_t &S1, f2_t &S2) {
+#pragma unroll
+    for (int dp = 0; dp < DP; ++dp) {
+        const ulonglong2 q0 = par[7 * dp], q1 = par[7 * dp + 1], q2 = par[7 * dp + 2];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const f2_t x = f2_mul(u2[j], q0.x);
+            const f2_t t = f2_rcp(f2_fma(x, x, q0.y));
+            const f2_t gt = f2_mul(gv[dp][j], t);
+            S1 = f2_fma(gt, f2_fma(t, q1.y, q1.x), S1);
+            S2 = f2_fma(gt, f2_fma(t, q2.y, q2.x), S2);
+        }
+    }
+}
+
+// One line's far-wing backward sums over a warp's J x DS cells (depth pairs):
+// S1 += G stim A H, S2 += G stim A a6 dH/da.  MASK: keep only the far cells inside
+// the window (inwin per lambda point).
+template <int J, int DP, bool MASK>
+__device__ __forceinline__ void far_bwd_line(const ulonglong2 *par, const f2_t (&u2)[J], const f2_t (&gv)[DP][J],
+                                             const bool *inwin, f2_t &S1, f2_t &S2) {
+#pragma unroll
+    for (int dp = 0; dp < DP; ++dp) {
+        // (k, a^2) (B1, B2) (C1, C2) (B3, B4) (B5, C3) (C4, C5) (C6, -)
+        const ulonglong2 q0 = par[7 * dp], q1 = par[7 * dp + 1], q2 = par[7 * dp + 2];
+        const ulonglong2 q3 = par[7 * dp + 3], q4 = par[7 * dp + 4], q5 = par[7 * dp + 5];
+        const ulonglong2 q6 = par[7 * dp + 6];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const f2_t x = f2_mul(u2[j], q0.x);
+            const f2_t r2 = f2_fma(x, x, q0.y);
+            const f2_t t = f2_rcp(r2);
+            f2_t h = f2_fma(t, q4.x, q3.y);
+            h = f2_fma(t, h, q3.x);
+            h = f2_fma(t, h, q1.y);
+            h = f2_fma(t, h, q1.x);
+            f2_t q = f2_fma(t, q6.x, q5.y);
+            q = f2_fma(t, q, q5.x);
+            q = f2_fma(t, q, q4.y);
+            q = f2_fma(t, q, q2.y);
+            q = f2_fma(t, q, q2.x);
+            f2_t gt = f2_mul(gv[dp][j], t);
+            if (MASK) {
+                float r2a, r2b, ga, gb;
+                f2_unpack(r2, r2a, r2b);
+                f2_unpack(gt, ga, gb);
+                ga = (inwin[j] && r2a >= kFar2) ? ga : 0.0f;
+                gb = (inwin[j] && r2b >= kFar2) ? gb : 0.0f;
+                gt = f2_pack(ga, gb);
+            }
+            S1 = f2_fma(gt, h, S1);
+            S2 = f2_fma(gt, q, S2);
+        }
+    }
+}
+
 // Far-wing kernel (backward): the per-line sums over the tile's far cells of
 // G stim A H and G stim A a6 dH/da, reduced over the CTA and added to gacc.
 template <int J, int DS>
 __device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, const int group, const int lo,
                                              const int hi, const int GW, const int LC) {
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
+    static_assert(DS % 2 == 0, "DS must be even (depth pairs)");
+    constexpr int DP = DS / 2;
+    constexpr int NPB = 14;             // floats per (line, depth) in shared memory
     extern __shared__ float4 smem4[];
     const int T = 32 * J;
     const int DC = GW * DS;
     const int nthr = blockDim.x;
-    float4 *s_par = smem4;                                              // [LC][DC][4]
-    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * DC * 4);
+    float *s_parf = reinterpret_cast<float *>(smem4);                   // [LC][DC/2][2 * NPB]
+    const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(smem4);
+    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * DC * NPB / 4);
     float2 *s_red = reinterpret_cast<float2 *>(s_line + LC);            // [LC][GW]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int d0 = group * DC;
-    const int slab = (d0 + warp * DS) / DS;
     const int t0 = tile * T;
     const float t0f = (float)t0, tendf = (float)(t0 + T - 1);
     const int lam_thr = t0 + lane * J;
     const float lamf = (float)lam_thr;
 
-    // G * stim of the thread's cells; zero outside the grid
-    float gv[DS][J];
+    // G * stim of the thread's cells as depth pairs; zero outside the grid
+    f2_t gv[DP][J];
 #pragma unroll
-    for (int dd = 0; dd < DS; ++dd) {
-        int d = d0 + warp * DS + dd;
+    for (int dp = 0; dp < DP; ++dp) {
+        const int da = d0 + warp * DS + 2 * dp, db = da + 1;
 #pragma unroll
-        for (int j = 0; j < J; ++j)
-            gv[dd][j] = (d < g.nd && lam_thr + j < g.nlam) ? g.Gt[(int64_t)d * g.ld + lam_thr + j] : 0.0f;
+        for (int j = 0; j < J; ++j) {
+            const bool inl = lam_thr + j < g.nlam;
+            const float ga = (da < g.nd && inl) ? g.Gt[(int64_t)da * g.ld + lam_thr + j] : 0.0f;
+            const float gb = (db < g.nd && inl) ? g.Gt[(int64_t)db * g.ld + lam_thr + j] : 0.0f;
+            gv[dp][j] = f2_pack(ga, gb);
+        }
     }
 
     for (int c0 = lo; c0 < hi; c0 += LC) {
@@ -447,11 +654,12 @@ __device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, 
             int li = idx / DC, dd = idx - li * DC;
             float p[16];
             line_params<16>(g, c0 + li, d0 + dd, p);
-            float4 *dst = s_par + ((size_t)li * DC + dd) * 4;
-            dst[0] = make_float4(p[0], p[1], p[2], p[3]);
-            dst[1] = make_float4(p[4], p[5], p[6], p[7]);
-            dst[2] = make_float4(p[8], p[9], p[10], p[11]);
-            dst[3] = make_float4(p[12], p[13], p[14], p[15]);
+            float *dst = s_parf + ((size_t)li * (DC / 2) + (dd >> 1)) * (2 * NPB);
+            // (k, a^2) (B1, B2) (C1, C2) (B3, B4) (B5, C3) (C4, C5) (C6, -)
+            constexpr int src[14] = {0, 1, 2, 3, 8, 9, 4, 5, 6, 10, 11, 12, 13, 0};
+#pragma unroll
+            for (int m = 0; m < 13; ++m) dst[par_off(m, dd)] = p[src[m]];
+            dst[par_off(13, dd)] = 0.0f;
         }
         for (int li = tid; li < nl; li += nthr) {
             int64_t l = c0 + li;
@@ -459,42 +667,27 @@ __device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, 
             info.ilf = g.ilf[l];
             info.frac = g.frac[l];
             info.sp = g.sp[l];
-            info.pad = 0;
+            info.pad = fast_mask(g, l, info, t0f, tendf, d0, DS, GW);
             s_line[li] = info;
         }
         __syncthreads();
 
         for (int li = 0; li < nl; ++li) {
             const LineInfo info = s_line[li];
-            const float4 *par = s_par + ((size_t)li * DC + warp * DS) * 4;
-            float u[J];
+            const ulonglong2 *par = s_par + ((size_t)li * (DC / 2) + warp * DP) * (NPB / 2);
+            f2_t u2[J];
 #pragma unroll
-            for (int j = 0; j < J; ++j) u[j] = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
-            float s1 = 0.0f, s2 = 0.0f;
-            if (fast_line(g, info, t0f, tendf, slab)) {
-#pragma unroll
-                for (int dd = 0; dd < DS; ++dd) {
-                    const float4 p0 = par[4 * dd], p1 = par[4 * dd + 1];
-                    const float4 p2 = par[4 * dd + 2], p3 = par[4 * dd + 3];
-#pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        const float x = u[j] * p0.x;
-                        const float t = rcp_approx(fmaf(x, x, p0.y));
-                        float h = fmaf(t, p1.z, p1.y);
-                        h = fmaf(t, h, p1.x);
-                        h = fmaf(t, h, p0.w);
-                        h = fmaf(t, h, p0.z);
-                        float q = fmaf(t, p3.y, p3.x);
-                        q = fmaf(t, q, p2.w);
-                        q = fmaf(t, q, p2.z);
-                        q = fmaf(t, q, p2.y);
-                        q = fmaf(t, q, p2.x);
-                        const float gt = gv[dd][j] * t;
-                        s1 = fmaf(gt, h, s1);
-                        s2 = fmaf(gt, q, s2);
-                    }
-                }
+            for (int j = 0; j < J; ++j) {
+                const float u = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
+                u2[j] = f2_pack(u, u);
+            }
+            f2_t S1 = 0ull, S2 = 0ull;
+            if ((info.pad >> (8 + warp)) & 1) {
+                far_bwd_line_reduced<J, DP>(par, u2, gv, S1, S2);
+            } else if ((info.pad >> warp) & 1) {
+                far_bwd_line<J, DP, false>(par, u2, gv, nullptr, S1, S2);
             } else {
+                // line near the tile or partly outside its window: far cells inside the window only
                 bool inwin[J];
                 const int il = (int)info.ilf;
 #pragma unroll
@@ -502,30 +695,12 @@ __device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, 
                     const int di = lam_thr + j - il;
                     inwin[j] = di >= -g.W && di <= g.W;
                 }
-#pragma unroll
-                for (int dd = 0; dd < DS; ++dd) {
-                    const float4 p0 = par[4 * dd], p1 = par[4 * dd + 1];
-                    const float4 p2 = par[4 * dd + 2], p3 = par[4 * dd + 3];
-#pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        const float x = u[j] * p0.x;
-                        const float r2 = fmaf(x, x, p0.y);
-                        const float t = rcp_approx(r2);
-                        float h = fmaf(t, p1.z, p1.y);
-                        h = fmaf(t, h, p1.x);
-                        h = fmaf(t, h, p0.w);
-                        h = fmaf(t, h, p0.z);
-                        float q = fmaf(t, p3.y, p3.x);
-                        q = fmaf(t, q, p2.w);
-                        q = fmaf(t, q, p2.z);
-                        q = fmaf(t, q, p2.y);
-                        q = fmaf(t, q, p2.x);
-                        const float gt = (inwin[j] && r2 >= kFar2) ? gv[dd][j] * t : 0.0f;
-                        s1 = fmaf(gt, h, s1);
-                        s2 = fmaf(gt, q, s2);
-                    }
-                }
+                far_bwd_line<J, DP, true>(par, u2, gv, inwin, S1, S2);
             }
+            float s1a, s1b, s2a, s2b;
+            f2_unpack(S1, s1a, s1b);
+            f2_unpack(S2, s2a, s2b);
+            float s1 = s1a + s1b, s2 = s2a + s2b;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
                 s1 += __shfl_xor_sync(0xffffffffu, s1, o);
@@ -851,7 +1026,9 @@ static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
         g.ngroups = (c->nd + kNearDepthsBwd - 1) / kNearDepthsBwd;
         g.ctr = c->d_ctr + 3;
         int grid = persistent_grid(c, k_line_near_bwd<T, kNearDepthsBwd>, 256, 0, g.n_items);
+        cudaEvent_t ev = prof_begin(c, s);
         k_line_near_bwd<T, kNearDepthsBwd><<<grid, 256, 0, s>>>(g);
+        prof_end(c, s, PZ_K_NEAR_BWD, ev);
     } else {
         if (c->n_nitems_f == 0) return cudaSuccess;
         g.items = c->d_nitems_f;
@@ -859,7 +1036,9 @@ static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
         g.ngroups = (c->nd + kNearDepthsFwd - 1) / kNearDepthsFwd;
         g.ctr = c->d_ctr + 0;
         int grid = persistent_grid(c, k_line_near_fwd<T, kNearDepthsFwd>, 256, 0, g.n_items);
+        cudaEvent_t ev = prof_begin(c, s);
         k_line_near_fwd<T, kNearDepthsFwd><<<grid, 256, 0, s>>>(g);
+        prof_end(c, s, PZ_K_NEAR_FWD, ev);
     }
     c->launches++;
     return cudaGetLastError();
@@ -869,8 +1048,8 @@ template <int J, int DS, int MINB>
 static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
     const Tiling &t = c->tiling;
     LineArgs g = make_args(c);
-    size_t smem = (size_t)t.LC * t.depth_per_cta() * 2 * sizeof(float4) + t.LC * sizeof(LineInfo) +
-                  (size_t)DS * 32 * t.GW * sizeof(float4);
+    size_t smem = (size_t)t.LC * t.depth_per_cta() * 8 * sizeof(float) + t.LC * sizeof(LineInfo) +
+                  (size_t)DS * 32 * t.GW * 2 * sizeof(float4);
     static bool attr_set[64] = {false};
     if (!attr_set[c->device]) {
         cudaFuncSetAttribute(k_line_fwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -894,7 +1073,7 @@ template <int J, int DS, int MINB>
 static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
     const Tiling &t = c->tiling;
     LineArgs g = make_args(c);
-    size_t smem = (size_t)t.LCB * t.depth_per_cta() * 4 * sizeof(float4) + t.LCB * sizeof(LineInfo) +
+    size_t smem = (size_t)t.LCB * t.depth_per_cta() * 14 * sizeof(float) + t.LCB * sizeof(LineInfo) +
                   (size_t)t.LCB * t.GW * sizeof(float2);
     static bool attr_set[64] = {false};
     if (!attr_set[c->device]) {
@@ -920,8 +1099,8 @@ static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
 
 // Supported (lambda points per thread, depths per warp, minimum resident CTAs per SM).
 #define PZ_TILE_LIST(X) \
-    X(4, 9, 1) X(4, 9, 2) X(4, 9, 3) X(4, 6, 1) X(4, 6, 2) X(4, 6, 3) X(4, 6, 4) X(4, 12, 1) X(4, 12, 2) \
-    X(2, 9, 1) X(2, 9, 2) X(2, 9, 3) X(2, 9, 4) X(2, 12, 1) X(2, 12, 2) X(2, 12, 3) X(2, 6, 4)
+    X(4, 6, 1) X(4, 6, 2) X(4, 6, 3) X(4, 6, 4) X(4, 8, 1) X(4, 8, 2) X(4, 8, 3) X(4, 12, 1) X(4, 12, 2) \
+    X(2, 6, 4) X(2, 8, 2) X(2, 8, 3) X(2, 8, 4) X(2, 12, 1) X(2, 12, 2) X(2, 12, 3)
 
 #define PZ_TILE_DISPATCH(FN)                                                        \
     const Tiling &t = c->tiling;                                                    \
