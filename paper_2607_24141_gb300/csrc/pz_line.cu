@@ -71,7 +71,8 @@ static double dawson_quad(double x) {
     return x * sum;
 }
 
-// Node coefficients D^(k)(x_j)/k! from D' = 1 - 2xD, D^(k+1) = -2x D^(k) - 2k D^(k-1).
+// Node coefficients D^(k)(x_j)/k! from D' = 1 - 2xD, D^(k+1) = -2x D^(k) - 2k D^(k-1),
+// stored coefficient-major: tab[k * kDawsonNodes + j].
 static void dawson_table(std::vector<float> &tab) {
     tab.assign(kDawsonNodes * (kDawsonK + 1), 0.0f);
     for (int j = 0; j < kDawsonNodes; ++j) {
@@ -83,7 +84,7 @@ static void dawson_table(std::vector<float> &tab) {
         double fact = 1.0;
         for (int k = 0; k <= kDawsonK; ++k) {
             if (k > 0) fact *= k;
-            tab[j * (kDawsonK + 1) + k] = (float)(D[k] / fact);
+            tab[k * kDawsonNodes + j] = (float)(D[k] / fact);
         }
     }
 }
@@ -762,60 +763,76 @@ struct alignas(16) NearItem {
 constexpr int kNearBatch = 512;      // lines per shared-memory batch of the backward sums
 constexpr int kNearDepthsFwd = 8;    // depths per CTA of the near-core forward
 constexpr int kNearDepthsBwd = 24;   // depths per CTA of the near-core backward
-constexpr int kCoreQueue = 512;      // core cells queued per warp before a dense pass
+constexpr int kNearQueue = 768;      // queued cells per warp before a dense pass (mid from the front, core from the back)
+constexpr int kNearWarps = 8;        // warps per near-core CTA
 
 // Near-core sweep shared by the forward (D = false) and the backward (D = true).
 // Each warp takes rounds of 32 (line, depth) items: lanes set up one item each
 // (coarse span from c/dv_D alone, then the exact prefactors and span), the survivors
-// are kept in shared memory, then the warp sweeps each item's span 32 points at a time.
-// Mid-wing cells (36 <= |z|^2 < 400) are evaluated in place; core cells (|z|^2 < 36)
-// are queued (in item order) and evaluated densely.
+// are kept in shared memory, then the warp classifies each item's span 32 points at
+// a time and queues the cells: mid-wing cells (36 <= |z|^2 < 400) from the front of
+// the warp's queue, core cells (|z|^2 < 36) from the back, both in item order.  When
+// the queue is full (and at the end of the round) the warp evaluates the mid entries
+// and then the core entries densely, 32 at a time, so the two Voigt forms never
+// diverge within a warp.
 //   forward:  cell(item, i, H, dH) adds the cell's term where it belongs;
 //   backward: val(item, i, H, dH) returns the cell's (G A H, G A a6 dH) pair and
-//             done(lb, sum) receives the per-item (or per-queue-segment) sums.
+//             done(lb, sum) receives the per-queue-segment sums of each item.
+template <int T, bool D, bool CORE, class Cell, class Val, class Done>
+__device__ __forceinline__ void near_eval(const LineArgs &g, int t0, const NearItem *mine, const int *q, int n,
+                                          const float *s_daw, Cell &cell, Val &val, Done &done) {
+    const int lane = threadIdx.x & 31;
+    for (int e0 = 0; e0 < n; e0 += 32) {
+        const int e = e0 + lane;
+        int src = -1;
+        float2 v = make_float2(0.0f, 0.0f);
+        if (e < n) {
+            const int code = q[e];
+            src = code >> 16;
+            const NearItem &it = mine[src];
+            const int i = t0 + (code & 0xffff);
+            const float x = fabsf(offset_u((it.ilf - (float)i) + it.frac, g.lnr) * it.k);
+            float H, dH;
+            if (CORE)
+                voigt_core<D>(x, it.a, H, dH, s_daw);
+            else
+                voigt_mid<D>(x, it.a, H, dH);
+            if (D)
+                v = val(it, i, H, dH);
+            else
+                cell(it, i, H, dH);
+        }
+        if (D) {
+            // segmented sum over runs of equal items (entries are grouped by item)
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float nx = __shfl_up_sync(0xffffffffu, v.x, o);
+                const float ny = __shfl_up_sync(0xffffffffu, v.y, o);
+                const int ns = __shfl_up_sync(0xffffffffu, src, o);
+                if (lane >= o && ns == src) {
+                    v.x += nx;
+                    v.y += ny;
+                }
+            }
+            const int next = __shfl_down_sync(0xffffffffu, src, 1);
+            if (src >= 0 && (lane == 31 || next != src)) done(mine[src].lb, v);
+        }
+    }
+}
+
 template <int T, bool D, class Cell, class Val, class Done>
 __device__ __forceinline__ void near_sweep(const LineArgs &g, int t0, int64_t nlo, int64_t nitems, int ndg, int dbase,
-                                           NearItem *s_items, int *s_queue, Cell &&cell, Val &&val, Done &&done) {
+                                           NearItem *s_items, int *s_queue, const float *s_daw, Cell &&cell, Val &&val,
+                                           Done &&done) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     NearItem *mine = s_items + warp * 32;
-    int *queue = s_queue + warp * kCoreQueue;
-    int nq = 0;
-    auto flush_core = [&]() {
+    int *queue = s_queue + warp * kNearQueue;
+    int nm = 0, nc = 0;          // mid entries [0, nm), core entries [kNearQueue - nc, kNearQueue)
+    auto flush = [&]() {
         __syncwarp();
-        for (int e0 = 0; e0 < nq; e0 += 32) {
-            const int e = e0 + lane;
-            int src = -1;
-            float2 v = make_float2(0.0f, 0.0f);
-            if (e < nq) {
-                const int code = queue[e];
-                src = code >> 16;
-                const NearItem &it = mine[src];
-                const int i = t0 + (code & 0xffff);
-                const float x = fabsf(offset_u((it.ilf - (float)i) + it.frac, g.lnr) * it.k);
-                float H, dH;
-                voigt_core<D>(x, it.a, H, dH);
-                if (D)
-                    v = val(it, i, H, dH);
-                else
-                    cell(it, i, H, dH);
-            }
-            if (D) {
-                // segmented sum over runs of equal items (entries are in item order)
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const float nx = __shfl_up_sync(0xffffffffu, v.x, o);
-                    const float ny = __shfl_up_sync(0xffffffffu, v.y, o);
-                    const int ns = __shfl_up_sync(0xffffffffu, src, o);
-                    if (lane >= o && ns == src) {
-                        v.x += nx;
-                        v.y += ny;
-                    }
-                }
-                const int next = __shfl_down_sync(0xffffffffu, src, 1);
-                if (src >= 0 && (lane == 31 || next != src)) done(mine[src].lb, v);
-            }
-        }
-        nq = 0;
+        near_eval<T, D, false>(g, t0, mine, queue, nm, s_daw, cell, val, done);
+        near_eval<T, D, true>(g, t0, mine, queue + kNearQueue - nc, nc, s_daw, cell, val, done);
+        nm = nc = 0;
         __syncwarp();
     };
     for (int64_t r0 = (int64_t)warp * 32; r0 < nitems; r0 += (int64_t)nwarp * 32) {
@@ -851,57 +868,43 @@ __device__ __forceinline__ void near_sweep(const LineArgs &g, int t0, int64_t nl
         __syncwarp();
         if (ok) mine[lane] = item;
         __syncwarp();
-        // sweep the surviving items' spans
+        // classify the surviving items' spans into the queue
         for (unsigned m = okm; m; m &= m - 1) {
             const int src = __ffs(m) - 1;
             const NearItem &itm = mine[src];
-            if (nq + (itm.hi - itm.lo + 1) > kCoreQueue) flush_core();
-            float2 acc = make_float2(0.0f, 0.0f);
+            if (nm + nc + (itm.hi - itm.lo + 1) > kNearQueue) flush();
             for (int i0 = itm.lo; i0 <= itm.hi; i0 += 32) {
                 const int i = i0 + lane;
-                bool core = false;
+                bool mid = false, core = false;
                 if (i <= itm.hi) {
                     const float x = fabsf(offset_u((itm.ilf - (float)i) + itm.frac, g.lnr) * itm.k);
                     const float r2 = fmaf(x, x, itm.a2);
-                    if (r2 < kFar2) {
-                        if (r2 >= kMid2) {
-                            float H, dH;
-                            voigt_mid<D>(x, itm.a, H, dH);
-                            if (D) {
-                                const float2 v = val(itm, i, H, dH);
-                                acc.x += v.x;
-                                acc.y += v.y;
-                            } else {
-                                cell(itm, i, H, dH);
-                            }
-                        } else {
-                            core = true;
-                        }
-                    }
+                    mid = r2 < kFar2 && r2 >= kMid2;
+                    core = r2 < kMid2;
                 }
+                const int code = (src << 16) | (i - t0);
+                const unsigned mm = __ballot_sync(0xffffffffu, mid);
                 const unsigned cm = __ballot_sync(0xffffffffu, core);
-                if (core) queue[nq + __popc(cm & ((1u << lane) - 1u))] = (src << 16) | (i - t0);
-                nq += __popc(cm);
-            }
-            if (D) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
-                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
-                }
-                if (lane == 0 && (acc.x != 0.0f || acc.y != 0.0f)) done(itm.lb, acc);
+                const unsigned below = (1u << lane) - 1u;
+                if (mid) queue[nm + __popc(mm & below)] = code;
+                if (core) queue[kNearQueue - 1 - (nc + __popc(cm & below))] = code;
+                nm += __popc(mm);
+                nc += __popc(cm);
             }
         }
-        flush_core();
+        flush();
     }
 }
 
 // Forward near-core sums into knear.  Work items: (star, tile, depth group of NDG layers).
 template <int T, int NDG>
-__global__ void __launch_bounds__(256) k_line_near_fwd(LineArgs gq) {
-    __shared__ float s_acc[NDG * T];
-    __shared__ NearItem s_items[8 * 32];
-    __shared__ int s_queue[8 * kCoreQueue];
+__global__ void __launch_bounds__(32 * kNearWarps) k_line_near_fwd(LineArgs gq) {
+    extern __shared__ float4 smem4[];
+    float *s_acc = reinterpret_cast<float *>(smem4);                               // [NDG][T]
+    NearItem *s_items = reinterpret_cast<NearItem *>(s_acc + NDG * T);             // [warps][32]
+    int *s_queue = reinterpret_cast<int *>(s_items + kNearWarps * 32);             // [warps][kNearQueue]
+    float *s_daw = reinterpret_cast<float *>(s_queue + kNearWarps * kNearQueue);   // Dawson table
+    for (int k = threadIdx.x; k < kDawsonNodes * (kDawsonK + 1); k += blockDim.x) s_daw[k] = g_dawson[k];
     for_each_item(gq, [&](const LineArgs &g, int tile, int group, int nlo, int nhi) {
     const int tid = threadIdx.x;
     const int t0 = tile * T;
@@ -909,7 +912,7 @@ __global__ void __launch_bounds__(256) k_line_near_fwd(LineArgs gq) {
     for (int k = tid; k < NDG * T; k += blockDim.x) s_acc[k] = 0.0f;
     __syncthreads();
     near_sweep<T, false>(
-        g, t0, nlo, (int64_t)(nhi - nlo) * ndg, ndg, dbase, s_items, s_queue,
+        g, t0, nlo, (int64_t)(nhi - nlo) * ndg, ndg, dbase, s_items, s_queue, s_daw,
         [&](const NearItem &it, int i, float H, float) { atomicAdd(s_acc + it.dl * T + (i - t0), it.A * H); },
         [&](const NearItem &, int, float, float) { return make_float2(0.0f, 0.0f); }, [&](int, float2) {});
     __syncthreads();
@@ -924,11 +927,14 @@ __global__ void __launch_bounds__(256) k_line_near_fwd(LineArgs gq) {
 // Lines are processed in batches whose per-line sums live in shared memory; one
 // global atomic per (line, tile, depth group) at the end of each batch.
 template <int T, int NDG>
-__global__ void __launch_bounds__(256) k_line_near_bwd(LineArgs gq) {
-    __shared__ float s_g[NDG * T];                                      // G * stim
-    __shared__ float2 s_sum[kNearBatch];
-    __shared__ NearItem s_items[8 * 32];
-    __shared__ int s_queue[8 * kCoreQueue];
+__global__ void __launch_bounds__(32 * kNearWarps) k_line_near_bwd(LineArgs gq) {
+    extern __shared__ float4 smem4[];
+    float *s_g = reinterpret_cast<float *>(smem4);                                 // [NDG][T] G * stim
+    float2 *s_sum = reinterpret_cast<float2 *>(s_g + NDG * T);                     // [kNearBatch]
+    NearItem *s_items = reinterpret_cast<NearItem *>(s_sum + kNearBatch);          // [warps][32]
+    int *s_queue = reinterpret_cast<int *>(s_items + kNearWarps * 32);             // [warps][kNearQueue]
+    float *s_daw = reinterpret_cast<float *>(s_queue + kNearWarps * kNearQueue);   // Dawson table
+    for (int k = threadIdx.x; k < kDawsonNodes * (kDawsonK + 1); k += blockDim.x) s_daw[k] = g_dawson[k];
     for_each_item(gq, [&](const LineArgs &g, int tile, int group, int nlo, int nhi) {
     const int tid = threadIdx.x;
     const int t0 = tile * T;
@@ -943,7 +949,7 @@ __global__ void __launch_bounds__(256) k_line_near_bwd(LineArgs gq) {
         for (int k = tid; k < nb; k += blockDim.x) s_sum[k] = make_float2(0.0f, 0.0f);
         __syncthreads();
         near_sweep<T, true>(
-            g, t0, b0, (int64_t)nb * ndg, ndg, dbase, s_items, s_queue, [&](const NearItem &, int, float, float) {},
+            g, t0, b0, (int64_t)nb * ndg, ndg, dbase, s_items, s_queue, s_daw, [&](const NearItem &, int, float, float) {},
             [&](const NearItem &it, int i, float H, float dH) {
                 const float gs = s_g[it.dl * T + (i - t0)];
                 return make_float2(gs * it.A * H, gs * it.Aa6 * dH);
@@ -961,6 +967,13 @@ __global__ void __launch_bounds__(256) k_line_near_bwd(LineArgs gq) {
     }
     __syncthreads();
     });
+}
+
+template <int T, int NDG, bool BWD>
+constexpr size_t near_smem() {
+    return (size_t)NDG * T * sizeof(float) + (BWD ? kNearBatch * sizeof(float2) : 0) +
+           (size_t)kNearWarps * 32 * sizeof(NearItem) + (size_t)kNearWarps * kNearQueue * sizeof(int) +
+           (size_t)kDawsonNodes * (kDawsonK + 1) * sizeof(float);
 }
 
 static LineArgs make_args(pz_ctx *c) {
@@ -1025,9 +1038,16 @@ static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
         g.n_items = c->n_nitems_b;
         g.ngroups = (c->nd + kNearDepthsBwd - 1) / kNearDepthsBwd;
         g.ctr = c->d_ctr + 3;
-        int grid = persistent_grid(c, k_line_near_bwd<T, kNearDepthsBwd>, 256, 0, g.n_items);
+        constexpr size_t smem = near_smem<T, kNearDepthsBwd, true>();
+        static bool attr_set[64] = {false};
+        if (!attr_set[c->device]) {
+            cudaFuncSetAttribute(k_line_near_bwd<T, kNearDepthsBwd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            attr_set[c->device] = true;
+        }
+        int grid = persistent_grid(c, k_line_near_bwd<T, kNearDepthsBwd>, 32 * kNearWarps, smem, g.n_items);
         cudaEvent_t ev = prof_begin(c, s);
-        k_line_near_bwd<T, kNearDepthsBwd><<<grid, 256, 0, s>>>(g);
+        k_line_near_bwd<T, kNearDepthsBwd><<<grid, 32 * kNearWarps, smem, s>>>(g);
         prof_end(c, s, PZ_K_NEAR_BWD, ev);
     } else {
         if (c->n_nitems_f == 0) return cudaSuccess;
@@ -1035,9 +1055,16 @@ static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
         g.n_items = c->n_nitems_f;
         g.ngroups = (c->nd + kNearDepthsFwd - 1) / kNearDepthsFwd;
         g.ctr = c->d_ctr + 0;
-        int grid = persistent_grid(c, k_line_near_fwd<T, kNearDepthsFwd>, 256, 0, g.n_items);
+        constexpr size_t smem = near_smem<T, kNearDepthsFwd, false>();
+        static bool attr_set[64] = {false};
+        if (!attr_set[c->device]) {
+            cudaFuncSetAttribute(k_line_near_fwd<T, kNearDepthsFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+            attr_set[c->device] = true;
+        }
+        int grid = persistent_grid(c, k_line_near_fwd<T, kNearDepthsFwd>, 32 * kNearWarps, smem, g.n_items);
         cudaEvent_t ev = prof_begin(c, s);
-        k_line_near_fwd<T, kNearDepthsFwd><<<grid, 256, 0, s>>>(g);
+        k_line_near_fwd<T, kNearDepthsFwd><<<grid, 32 * kNearWarps, smem, s>>>(g);
         prof_end(c, s, PZ_K_NEAR_FWD, ev);
     }
     c->launches++;

@@ -41,6 +41,8 @@ __constant__ float c_weid[kWeidN + 1];
 __constant__ float c_weidL;
 __constant__ double c_weid64[kWeidN64 + 1];
 __constant__ double c_weidL64;
+// Dawson-derivative table, coefficient-major: g_dawson[k * kDawsonNodes + j] = D^(k)(x_j)/k!.
+// Lanes evaluating nearby x read adjacent words of each coefficient row.
 __device__ float g_dawson[kDawsonNodes * (kDawsonK + 1)];
 
 constexpr float kInvSqrtPiF = 0.564189583547756287f;
@@ -107,16 +109,17 @@ __device__ __forceinline__ void voigt_mid(float x, float a, float &H, float &dH)
     if (D) dH = sd * kInvSqrtPiF;
 }
 
-// Core, small a: Dawson-derivative table.  x >= 0, x*x + a*a < 36, a < 0.5.
-__device__ __forceinline__ void voigt_core_table(float x, float a, float &H, float &L) {
+// Core, small a: Dawson-derivative table (coefficient-major, in global or shared
+// memory).  x >= 0, x*x + a*a < 36, a < 0.5.
+__device__ __forceinline__ void voigt_core_table(float x, float a, float &H, float &L, const float *tab) {
     int j = __float2int_rn(x * (float)kDawsonPerUnit);
     j = min(max(j, 0), kDawsonNodes - 1);
     float d = x - (float)j * (1.0f / kDawsonPerUnit);
-    const float *T = g_dawson + j * (kDawsonK + 1);
-    float pr = __ldg(T + kDawsonK), pi = 0.0f;
+    const float *T = tab + j;
+    float pr = T[kDawsonK * kDawsonNodes], pi = 0.0f;
 #pragma unroll
     for (int k = kDawsonK - 1; k >= 0; --k) {
-        float nr = fmaf(pr, d, fmaf(-pi, a, __ldg(T + k)));
+        float nr = fmaf(pr, d, fmaf(-pi, a, T[k * kDawsonNodes]));
         pi = fmaf(pr, a, pi * d);
         pr = nr;
     }
@@ -151,12 +154,12 @@ __device__ __forceinline__ void voigt_core_weideman(float x, float a, float &H, 
     L = fmaf(2.0f, fmaf(pr, i2i, pi * i2r), idi * kInvSqrtPiF);
 }
 
-// Core region |z| < 6 (both sub-regions), H and, if D, dH/da.
+// Core region |z| < 6 (both sub-regions), H and, if D, dH/da.  tab: the Dawson table.
 template <bool D>
-__device__ __forceinline__ void voigt_core(float x, float a, float &H, float &dH) {
+__device__ __forceinline__ void voigt_core(float x, float a, float &H, float &dH, const float *tab) {
     float L;
     if (a < kCoreA)
-        voigt_core_table(x, a, H, L);
+        voigt_core_table(x, a, H, L, tab);
     else
         voigt_core_weideman(x, a, H, L);
     if (D) dH = 2.0f * fmaf(x, L, a * H) - kTwoInvSqrtPiF;
@@ -173,7 +176,7 @@ __device__ __forceinline__ void voigt_general(float x, float a, float &H, float 
             voigt_mid<D>(x, a, H, dH);
         return;
     }
-    voigt_core<D>(x, a, H, dH);
+    voigt_core<D>(x, a, H, dH, g_dawson);
 }
 
 // ---- FP64 plain form --------------------------------------------------------
