@@ -42,8 +42,13 @@ WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts
 TRAFFIC = {"k_line_bwd": (21.2928e6, "dbe4ec0a1012c883")}
 KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h")
 
-# algorithmic per-evaluation instruction counts of the far-wing forms (>99% of evaluations)
-OPS = {"line_fwd": {"fp32": 7, "mufu": 1}, "line_bwd": {"fp32": 14, "mufu": 1}}
+# Per-evaluation pipe work of the far-wing kernels, which evaluate every in-window cell:
+# one MUFU reciprocal per evaluation in every form, and FP32-pipe operations of 4 (forward)
+# or 7 (backward) in the reduced form used for lines >= 100 Doppler widths from the whole
+# tile (most cells of this workload), 7 / 14 in the full far-wing form.  With
+# 16 MUFU and 128 FP32 lanes per SM both kernels are MUFU-bound in the reduced form.
+OPS = {"line_fwd": {"mufu": 1, "fp32_reduced": 4, "fp32_full": 7},
+       "line_bwd": {"mufu": 1, "fp32_reduced": 7, "fp32_full": 14}}
 
 
 def parse():
@@ -59,6 +64,7 @@ def parse():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched many-star measurement")
     ap.add_argument("--batch-stars", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default line-kernel tiling")
     return ap.parse_args()
 
 
@@ -188,11 +194,13 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 # batched many-star workload: one CUDA-graph launch per calibration step
 # ---------------------------------------------------------------------------
-def run_batched(args, dev, barrier, max_over_ranks, ws):
+def run_batched(args, dev, barrier, max_over_ranks, ws, tiling=None):
     """64 stars (seeded Teff, log g, [M/H]) on the APOGEE-like grid and instrument, each
     with its own top-N_k subset (2e4-3e5) of a 3e5-line master list; one step =
     pz_calib_step (corrections, fwd, chi^2, bwd, update) replayed as one graph launch.
-    Plus the joint two-star (solar-like + giant-like) step on 1e5 shared lines."""
+    Plus the joint two-star (solar-like + giant-like) step on 1e5 shared lines.
+    tiling: the line-kernel tiling tuned on the single-star workload (same grid and
+    line density), applied to both contexts."""
     import numpy as np
     import torch
 
@@ -204,6 +212,8 @@ def run_batched(args, dev, barrier, max_over_ranks, ws):
         t0 = time.perf_counter()
         s = pz.Synthesizer(batch, pz.PZ_MIXED, device=dev.index)
         t_create = time.perf_counter() - t0
+        if tiling is not None:
+            pz.pz_set_tiling(s.ctx, *tiling)
         S, n_out, nl = batch.n_stars, s.n_out, batch.lines.n_lines
         s.set_corrections(truth_gf, truth_g6, None)
         f_true = s.forward()
@@ -307,6 +317,12 @@ def main():
     s = pz.Synthesizer(prob, pz.PZ_MIXED, device=local)
     evals = s.n_evals
     stream = torch.cuda.current_stream()
+    # tiling of the line kernels: measured on this workload before any timing
+    tune = None
+    if not args.no_autotune:
+        t0 = time.perf_counter()
+        tune = pz.pz_autotune(s.ctx, with_backward=True, reps=2, stream=stream)
+        tune["seconds"] = time.perf_counter() - t0
 
     # synthetic target: the model at seeded "true" corrections plus S/N-200 noise
     rng = np.random.default_rng(7)
@@ -446,7 +462,7 @@ def main():
     if not args.no_batch and args.batch_stars > 0:
         if fp64 is None:
             s.close()
-        batched = run_batched(args, dev, barrier, max_over_ranks, ws)
+        batched = run_batched(args, dev, barrier, max_over_ranks, ws, tune["tiling"] if tune else None)
 
     # ---- roofline of the dominant kernel ----
     props = torch.cuda.get_device_properties(local)
@@ -459,14 +475,14 @@ def main():
     clk_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
     # near_* are the near-core parts already inside line_fwd / line_bwd; step is unused here
     share = {k: v[0] for k, v in ktimes.items() if k not in ("near_fwd", "near_bwd", "step")}
-    dom = max(("line_fwd", "line_bwd"), key=lambda k: share[k])
-    t_dom = share[dom] * 1e-3 / max(ktimes[dom][1], 1)          # s per launch
+    far = {"line_fwd": ktimes["line_fwd"][0] - ktimes["near_fwd"][0],
+           "line_bwd": ktimes["line_bwd"][0] - ktimes["near_bwd"][0]}
+    dom = max(far, key=far.get)
+    t_dom = far[dom] * 1e-3 / max(ktimes[dom][1], 1)            # s per launch of the far-wing kernel
     ops = OPS[dom]
-    fp32_clk, mufu_clk = ops["fp32"] / 128.0, ops["mufu"] / 16.0    # issue cycles per evaluation per SM
-    pipe = "fp32" if fp32_clk >= mufu_clk else "mufu"
-    lanes = 128 if pipe == "fp32" else 16
-    peak_ops = n_sm * lanes * clk_max * 1e6
-    achieved_ops = evals * ops[pipe] / t_dom
+    peak_mufu = n_sm * 16 * clk_max * 1e6
+    peak_fp32 = n_sm * 128 * clk_max * 1e6
+    achieved = evals * ops["mufu"] / t_dom
     total_k = sum(share.values())
     import hashlib
     h = hashlib.sha256()
@@ -477,12 +493,16 @@ def main():
     if kname in TRAFFIC and TRAFFIC[kname][1] == h.hexdigest()[:16]:
         traffic = TRAFFIC[kname][0]
     roofline = {
-        "bound": "alu", "kernel": kname, "pipe": pipe,
-        "achieved": achieved_ops * 1e-9, "peak": peak_ops * 1e-9, "unit": "Gop/s",
-        "frac": achieved_ops / peak_ops, "traffic": traffic,
-        "peak_source": "derived: %d SMs x %d %s lanes x %.0f MHz (max SM clock)" % (n_sm, lanes, pipe, clk_max),
+        "bound": "alu", "kernel": kname + " (far wing)", "pipe": "mufu",
+        "achieved": achieved * 1e-9, "peak": peak_mufu * 1e-9, "unit": "Gop/s",
+        "frac": achieved / peak_mufu, "traffic": traffic,
+        "peak_source": "derived: %d SMs x 16 MUFU lanes x %.0f MHz (max SM clock)" % (n_sm, clk_max),
         "ops_per_eval": ops, "evals_per_s": evals / t_dom, "ms_per_launch": t_dom * 1e3,
+        "fp32_pipe_frac_range": [evals * ops["fp32_reduced"] / t_dom / peak_fp32,
+                                 evals * ops["fp32_full"] / t_dom / peak_fp32],
         "kernel_share": {k: round(v / total_k, 4) for k, v in share.items() if total_k > 0},
+        "far_ms_per_launch": {k: v / max(ktimes[k][1], 1) for k, v in far.items()},
+        "near_ms_per_launch": {k: ktimes[k][0] / max(ktimes[k][1], 1) for k in ("near_fwd", "near_bwd")},
         "hbm_gbs_peak": peaks.get("hbm_gbs"),
     }
 
@@ -500,6 +520,7 @@ def main():
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
         "batched": batched,
+        "autotune": tune,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

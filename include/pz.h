@@ -259,6 +259,31 @@ int32_t pz_last_launch_count(const pz_ctx *ctx);
 pz_status pz_set_tiling(pz_ctx *ctx, int32_t lambda_per_thread, int32_t depth_per_warp,
                         int32_t warps_per_cta, int32_t lines_per_chunk, int32_t ctas_per_sm);
 
+/* Autotuner of the mixed-precision line kernels.  The paper sizes its line
+ * chunks per device by hand (2,000 / 4,000 / 8,000 lines on V100 / A100 / H100,
+ * Sec. 2.3); here the tiling is measured instead.  Starting from the current
+ * tiling, a coordinate search times, on this context's own stars, line lists and
+ * atmospheres: every compiled (lambda points per thread, depths per warp, CTAs
+ * per SM) triple, then warps per CTA 1-4, then lines per chunk 16-256.  Each
+ * candidate gets one untimed pass, then `reps` forward line launches (far wing +
+ * near core) and, if with_backward != 0, `reps` backward line launches, timed
+ * with CUDA events on `stream`.  The tiling with the smallest forward (+ backward)
+ * time per pass is kept.
+ *   best:    host int32[6] or NULL: (lambda points per thread, depths per warp,
+ *            warps per CTA, lines per chunk, CTAs per SM, candidates timed);
+ *   best_ms: host double[2] or NULL: forward and backward line-kernel ms per
+ *            pass of the kept tiling (backward 0 without with_backward).
+ * The call synchronises `stream`.  It overwrites the line-opacity buffers (and
+ * the backward's line accumulators), so pz_line_opacity must run again before
+ * pz_flux (PZ_ESTATE otherwise).  The backward timing uses G of the last
+ * pz_backward, or zeros if none ran (the kernels' cost does not depend on G).
+ * Cost: about 25 candidates x (1 + reps) passes.
+ * Errors: PZ_EINVAL for the plain FP64 form (it has no tiling) or reps outside
+ * [1, 100]; PZ_ECUDA if a launch fails (the context keeps the last tiling that
+ * was applied). */
+pz_status pz_autotune(pz_ctx *ctx, int32_t with_backward, int32_t reps, int32_t *best, double *best_ms,
+                      void *stream);
+
 /* ---- profiling ------------------------------------------------------------- */
 
 /* Kernel families timed by the built-in CUDA-event profiler. */

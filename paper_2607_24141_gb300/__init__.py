@@ -70,6 +70,7 @@ _SIGS = {
     "pz_eval_count": (C.c_int64, [_vp]),
     "pz_last_launch_count": (C.c_int32, [_vp]),
     "pz_set_tiling": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
+    "pz_autotune": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
     "pz_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "pz_kernel_times": (C.c_int, [_vp, _dp, C.POINTER(C.c_int64), C.c_int32]),
     "pz_abundance_grad_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int32, C.c_int32, _vp, _vp]),
@@ -238,6 +239,17 @@ def pz_last_launch_count(ctx) -> int:
 
 def pz_set_tiling(ctx, lambda_per_thread=0, depth_per_warp=0, warps_per_cta=0, lines_per_chunk=0, ctas_per_sm=0):
     _check(load().pz_set_tiling(ctx, lambda_per_thread, depth_per_warp, warps_per_cta, lines_per_chunk, ctas_per_sm))
+
+
+def pz_autotune(ctx, with_backward=True, reps=2, stream=None):
+    """Measure the line-kernel tilings on this context and keep the fastest.
+
+    Returns {"tiling": (lambda_per_thread, depth_per_warp, warps_per_cta,
+    lines_per_chunk, ctas_per_sm), "candidates": n, "fwd_ms": f, "bwd_ms": b}."""
+    best = (C.c_int32 * 6)()
+    ms = (C.c_double * 2)()
+    _check(load().pz_autotune(ctx, 1 if with_backward else 0, int(reps), best, ms, _stream(stream)))
+    return {"tiling": tuple(best[:5]), "candidates": best[5], "fwd_ms": ms[0], "bwd_ms": ms[1]}
 
 
 KERNEL_NAMES = ("line_fwd", "line_bwd", "flux", "rt_adjoint", "instrument", "inst_adjoint", "loss", "other",

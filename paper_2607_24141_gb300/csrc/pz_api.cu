@@ -498,12 +498,29 @@ static pz_status ensure_backward_buffers(pz_ctx *c) {
     return PZ_OK;
 }
 
+// Validate a tiling and make it current: thresholds and work items are rebuilt and
+// the captured calibration graph is dropped.
+static pz_status apply_tiling(pz_ctx *c, const Tiling &t, const char *who) {
+    const std::string w(who);
+    if (!tiling_supported(t.J, t.DS, t.minb))
+        return fail(PZ_EINVAL, w + ": unsupported (lambda_per_thread, depth_per_warp, ctas_per_sm)");
+    if (t.GW < 1 || t.GW > 4) return fail(PZ_EINVAL, w + ": warps_per_cta must be in [1, 4]");
+    if (t.LC < 1 || t.LC > 512) return fail(PZ_EINVAL, w + ": lines_per_chunk must be in [1, 512]");
+    if (!tiling_fits(t)) return fail(PZ_EINVAL, w + ": shared-memory chunk too large");
+    drop_graph(c);
+    c->tiling = t;
+    PZ_TRY(build_thresholds(c));
+    PZ_TRY(build_items(c));
+    return PZ_OK;
+}
+
 // The backward stages after the objective's seed dL/df: instrument adjoint, transfer
 // adjoint, line gradients, finalisation into caller order.
 static pz_status enqueue_backward(pz_ctx *c, const float *dLdf, float *g_gf, float *g_g6, float *g_ab,
                                   cudaStream_t s) {
     PZ_CUDA(timed(c, s, PZ_K_INST_ADJOINT, [&] { return launch_inst_adjoint(c, dLdf, s); }), "instrument adjoint");
     PZ_CUDA(timed(c, s, PZ_K_RT_ADJOINT, [&] { return launch_rt_adjoint(c, s); }), "transfer adjoint");
+    c->have_gt = true;
     PZ_CUDA(cudaMemsetAsync(c->d_gacc, 0, sizeof(double) * 2 * std::max<int64_t>(c->L.n, 1), s), "backward");
     if (c->L.n > 0) {
         PZ_CUDA(timed(c, s, PZ_K_LINE_BWD,
@@ -571,20 +588,116 @@ pz_status pz_set_tiling(pz_ctx *c, int32_t J, int32_t DS, int32_t GW, int32_t LC
     if (GW > 0) t.GW = GW;
     if (LC > 0) t.LC = LC;
     if (MINB > 0) t.minb = MINB;
-    if (!tiling_supported(t.J, t.DS, t.minb))
-        return fail(PZ_EINVAL, "pz_set_tiling: unsupported (lambda_per_thread, depth_per_warp, ctas_per_sm)");
-    if (t.GW < 1 || t.GW > 4) return fail(PZ_EINVAL, "pz_set_tiling: warps_per_cta must be in [1, 4]");
-    if (t.LC < 1 || t.LC > 512) return fail(PZ_EINVAL, "pz_set_tiling: lines_per_chunk must be in [1, 512]");
     if (LC > 0) t.LCB = std::max(1, t.LC / 2);
-    size_t gen = (size_t)t.DS * 32 * t.GW * 32;
-    size_t smem_fwd = (size_t)t.LC * t.DS * t.GW * 32 + t.LC * 16 + gen;
-    size_t smem_bwd = (size_t)t.LCB * t.DS * t.GW * 56 + t.LCB * 16 + (size_t)t.LCB * t.GW * 8;
-    if (smem_fwd > 200 * 1024 || smem_bwd > 200 * 1024)
-        return fail(PZ_EINVAL, "pz_set_tiling: shared-memory chunk too large");
-    drop_graph(c);
-    c->tiling = t;
-    PZ_TRY(build_thresholds(c));
-    PZ_TRY(build_items(c));
+    return apply_tiling(c, t, "pz_set_tiling");
+}
+
+pz_status pz_autotune(pz_ctx *c, int32_t with_backward, int32_t reps, int32_t *best, double *best_ms, void *stream) {
+    if (!c) return fail(PZ_EINVAL, "pz_autotune: ctx is NULL");
+    if (c->prec != PZ_MIXED) return fail(PZ_EINVAL, "pz_autotune: only the mixed-precision form has tilings");
+    if (reps < 1 || reps > 100) return fail(PZ_EINVAL, "pz_autotune: reps must be in [1, 100]");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->launches = 0;
+    if (with_backward) {
+        PZ_TRY(ensure_backward_buffers(c));
+        // G of the last reverse pass, or zeros: the kernels' cost does not depend on G
+        if (!c->have_gt)
+            PZ_CUDA(cudaMemsetAsync(c->d_Gt, 0, sizeof(float) * (size_t)c->S * c->nd * c->ld, s), "pz_autotune");
+    }
+    cudaEvent_t ev[4];
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return cuda_check(cudaGetLastError(), "pz_autotune: events");
+    const size_t gbytes = sizeof(double) * 2 * std::max<int64_t>(c->L.n, 1);
+    // time one tiling: one untimed pass, then reps forward launches and reps backward launches
+    auto measure = [&](const Tiling &t, double &fwd_ms, double &bwd_ms) -> pz_status {
+        PZ_TRY(apply_tiling(c, t, "pz_autotune"));
+        auto bwd = [&]() -> cudaError_t {
+            cudaError_t e = cudaMemsetAsync(c->d_gacc, 0, gbytes, s);
+            return e != cudaSuccess ? e : launch_line_bwd_mixed(c, s);
+        };
+        PZ_CUDA(launch_line_fwd_mixed(c, s), "pz_autotune: forward");
+        if (with_backward) PZ_CUDA(bwd(), "pz_autotune: backward");
+        PZ_CUDA(cudaEventRecord(ev[0], s), "pz_autotune");
+        for (int r = 0; r < reps; ++r) PZ_CUDA(launch_line_fwd_mixed(c, s), "pz_autotune: forward");
+        PZ_CUDA(cudaEventRecord(ev[1], s), "pz_autotune");
+        for (int r = 0; r < reps && with_backward; ++r) PZ_CUDA(bwd(), "pz_autotune: backward");
+        PZ_CUDA(cudaEventRecord(ev[2], s), "pz_autotune");
+        PZ_CUDA(cudaEventSynchronize(ev[2]), "pz_autotune");
+        float a = 0.0f, b = 0.0f;
+        PZ_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]), "pz_autotune");
+        PZ_CUDA(cudaEventElapsedTime(&b, ev[1], ev[2]), "pz_autotune");
+        fwd_ms = a / reps;
+        bwd_ms = with_backward ? b / reps : 0.0;
+        return PZ_OK;
+    };
+    // coordinate search from the current tiling: (lambda points, depths, CTAs per SM)
+    // over the compiled list, then warps per CTA, then lines per chunk
+    Tiling cur = c->tiling;
+    double cf = 0, cb = 0;
+    pz_status st = measure(cur, cf, cb);
+    int tried = 1;
+    auto consider = [&](Tiling t) -> pz_status {
+        if (!tiling_supported(t.J, t.DS, t.minb) || t.GW < 1 || t.GW > 4 || !tiling_fits(t)) return PZ_OK;
+        double f = 0, b = 0;
+        PZ_TRY(measure(t, f, b));
+        ++tried;
+        if (f + b < cf + cb) {
+            cur = t;
+            cf = f;
+            cb = b;
+        }
+        return PZ_OK;
+    };
+    static const int kJDM[][3] = {{4, 6, 1}, {4, 6, 2}, {4, 6, 3}, {4, 6, 4}, {4, 8, 1},  {4, 8, 2},
+                                  {4, 8, 3}, {4, 12, 1}, {4, 12, 2}, {2, 6, 4}, {2, 8, 2}, {2, 8, 3},
+                                  {2, 8, 4}, {2, 12, 1}, {2, 12, 2}, {2, 12, 3}};
+    if (st == PZ_OK) {
+        const Tiling base = cur;
+        for (const auto &q : kJDM) {
+            Tiling t = base;
+            t.J = q[0];
+            t.DS = q[1];
+            t.minb = q[2];
+            if (t.J == base.J && t.DS == base.DS && t.minb == base.minb) continue;
+            if ((st = consider(t)) != PZ_OK) break;
+        }
+    }
+    if (st == PZ_OK) {
+        const Tiling base = cur;
+        for (int gw = 1; gw <= 4 && st == PZ_OK; ++gw)
+            if (gw != base.GW) {
+                Tiling t = base;
+                t.GW = gw;
+                st = consider(t);
+            }
+    }
+    if (st == PZ_OK) {
+        const Tiling base = cur;
+        for (int lc : {16, 32, 64, 128, 256})
+            if (lc != base.LC && st == PZ_OK) {
+                Tiling t = base;
+                t.LC = lc;
+                t.LCB = std::max(1, lc / 2);
+                st = consider(t);
+            }
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    if (st != PZ_OK) return st;
+    PZ_TRY(apply_tiling(c, cur, "pz_autotune"));
+    // the buffers hold the last candidate's results: the forward must run again
+    c->have_kline = c->have_flux = c->have_inst = false;
+    if (best) {
+        best[0] = cur.J;
+        best[1] = cur.DS;
+        best[2] = cur.GW;
+        best[3] = cur.LC;
+        best[4] = cur.minb;
+        best[5] = tried;
+    }
+    if (best_ms) {
+        best_ms[0] = cf;
+        best_ms[1] = cb;
+    }
     return PZ_OK;
 }
 

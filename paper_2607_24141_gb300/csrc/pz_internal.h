@@ -163,6 +163,7 @@ struct pz_ctx {
 
     // state
     bool have_kline = false, have_flux = false, have_inst = false;
+    bool have_gt = false;                // G (dL/dkappa_line) holds a reverse pass
     int32_t launches = 0;
     pz::StepGraph graph;
     cudaStream_t cap_stream = nullptr;   // private stream the step graph is captured on
@@ -215,5 +216,6 @@ cudaError_t launch_grad_finalize(pz_ctx *c, float *g_gf, float *g_g6, float *g_a
 cudaError_t launch_update(pz_ctx *c, float lr_gf, float lr_g6, float lr_ab, cudaStream_t s);
 cudaError_t launch_probe_expn(const double *x, int64_t n, double *out, cudaStream_t s);
 bool tiling_supported(int J, int DS, int minb);
+bool tiling_fits(const Tiling &t);   // both far-wing chunks fit in shared memory
 
 }  // namespace pz

@@ -1071,15 +1071,28 @@ static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Dynamic shared memory of the far-wing kernels: staged prefactors, line records and
+// (forward) the compensated sums of every thread, or (backward) the per-line sums.
+static size_t far_fwd_smem(const Tiling &t) {
+    return (size_t)t.LC * t.depth_per_cta() * 8 * sizeof(float) + t.LC * sizeof(LineInfo) +
+           (size_t)t.DS * 32 * t.GW * 2 * sizeof(float4);
+}
+static size_t far_bwd_smem(const Tiling &t) {
+    return (size_t)t.LCB * t.depth_per_cta() * 14 * sizeof(float) + t.LCB * sizeof(LineInfo) +
+           (size_t)t.LCB * t.GW * sizeof(float2);
+}
+constexpr size_t kFarSmemMax = 200 * 1024;   // the opt-in size the far-wing kernels are given
+
+bool tiling_fits(const Tiling &t) { return far_fwd_smem(t) <= kFarSmemMax && far_bwd_smem(t) <= kFarSmemMax; }
+
 template <int J, int DS, int MINB>
 static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
     const Tiling &t = c->tiling;
     LineArgs g = make_args(c);
-    size_t smem = (size_t)t.LC * t.depth_per_cta() * 8 * sizeof(float) + t.LC * sizeof(LineInfo) +
-                  (size_t)DS * 32 * t.GW * 2 * sizeof(float4);
+    const size_t smem = far_fwd_smem(t);
     static bool attr_set[64] = {false};
     if (!attr_set[c->device]) {
-        cudaFuncSetAttribute(k_line_fwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_line_fwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFarSmemMax);
         attr_set[c->device] = true;
     }
     cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, 2 * sizeof(int), s);
@@ -1100,11 +1113,10 @@ template <int J, int DS, int MINB>
 static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
     const Tiling &t = c->tiling;
     LineArgs g = make_args(c);
-    size_t smem = (size_t)t.LCB * t.depth_per_cta() * 14 * sizeof(float) + t.LCB * sizeof(LineInfo) +
-                  (size_t)t.LCB * t.GW * sizeof(float2);
+    const size_t smem = far_bwd_smem(t);
     static bool attr_set[64] = {false};
     if (!attr_set[c->device]) {
-        cudaFuncSetAttribute(k_line_bwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        cudaFuncSetAttribute(k_line_bwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFarSmemMax);
         attr_set[c->device] = true;
     }
     cudaError_t e = cudaMemsetAsync(c->d_ctr + 2, 0, 2 * sizeof(int), s);
