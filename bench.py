@@ -75,6 +75,31 @@ def dist_env():
     return ws, rank, local
 
 
+def make_collectives(ws, device):
+    """barrier() and max_over_ranks(x) over the default process group (no-ops for one
+    rank).  device: where the reduction tensor lives (cuda for NCCL, cpu for gloo).
+    Weak scaling over spectra: the ranks exchange nothing but these timings."""
+    import torch
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    return barrier, max_over_ranks
+
+
+def aggregate_value(units_per_rank, ws, steps, ms_max):
+    """Whole-job throughput: the units every rank processed / the slowest rank's time."""
+    return ws * units_per_rank * steps / (ms_max * 1e-3)
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -294,16 +319,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
 
-    def barrier():
-        if ws > 1:
-            torch.distributed.barrier()
-
-    def max_over_ranks(x):
-        if ws == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = make_collectives(ws, dev)
 
     # CPU baseline first (rank 0, before the GPU work of this process starts)
     cpu = None
@@ -378,6 +394,13 @@ def main():
         barrier()
         return a.elapsed_time(b)
 
+    # ---- pipe peaks (roofline denominators of the ALU-bound line kernels) ----
+    pipe_peaks = {}
+    try:
+        pipe_peaks = {"fp32": pz.pz_probe_pipe(0, 4096, stream), "mufu": pz.pz_probe_pipe(1, 4096, stream)}
+    except Exception:
+        pipe_peaks = {}
+
     # ---- fwd+bwd (headline) ----
     for _ in range(args.warmup):
         step()
@@ -393,7 +416,7 @@ def main():
     clocks = clk.stop()
     ms_max = max_over_ranks(ms)
     ms_step = ms_max / args.steps
-    value = ws * evals * args.steps / (ms_max * 1e-3)
+    value = aggregate_value(evals, ws, args.steps, ms_max)
 
     # ---- fwd only ----
     for _ in range(2):
@@ -480,8 +503,12 @@ def main():
     dom = max(far, key=far.get)
     t_dom = far[dom] * 1e-3 / max(ktimes[dom][1], 1)            # s per launch of the far-wing kernel
     ops = OPS[dom]
-    peak_mufu = n_sm * 16 * clk_max * 1e6
-    peak_fp32 = n_sm * 128 * clk_max * 1e6
+    # pipe peaks measured on this GPU by the library's probe kernels (independent
+    # reciprocal / packed-FMA chains on every SM), next to the lane-count derivation
+    peak_mufu_lanes = n_sm * 16 * clk_max * 1e6
+    peak_fp32_lanes = n_sm * 128 * clk_max * 1e6
+    peak_mufu = pipe_peaks.get("mufu") or peak_mufu_lanes
+    peak_fp32 = pipe_peaks.get("fp32") or peak_fp32_lanes
     achieved = evals * ops["mufu"] / t_dom
     total_k = sum(share.values())
     import hashlib
@@ -496,7 +523,10 @@ def main():
         "bound": "alu", "kernel": kname + " (far wing)", "pipe": "mufu",
         "achieved": achieved * 1e-9, "peak": peak_mufu * 1e-9, "unit": "Gop/s",
         "frac": achieved / peak_mufu, "traffic": traffic,
-        "peak_source": "derived: %d SMs x 16 MUFU lanes x %.0f MHz (max SM clock)" % (n_sm, clk_max),
+        "peak_source": ("measured: pz_probe_pipe rcp.approx throughput (%d SMs); 16-lane derivation %.0f Gop/s"
+                        % (n_sm, peak_mufu_lanes * 1e-9)) if pipe_peaks.get("mufu") else
+                       "derived: %d SMs x 16 MUFU lanes x %.0f MHz (max SM clock)" % (n_sm, clk_max),
+        "pipe_peaks_measured": {k: v * 1e-9 for k, v in pipe_peaks.items()},
         "ops_per_eval": ops, "evals_per_s": evals / t_dom, "ms_per_launch": t_dom * 1e3,
         "fp32_pipe_frac_range": [evals * ops["fp32_reduced"] / t_dom / peak_fp32,
                                  evals * ops["fp32_full"] / t_dom / peak_fp32],

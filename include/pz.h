@@ -348,6 +348,21 @@ pz_status pz_probe_voigt(const float *a, const float *v, int64_t n, float *H, fl
  * FP64 [n] (x >= 0); out: device FP64 [3][n]. */
 pz_status pz_probe_expn(const double *x, int64_t n, double *out, void *stream);
 
+/* Measured throughput of the two arithmetic pipes the line kernels are bound by,
+ * for the roofline denominators of an ALU-bound path (the paper reports wall
+ * times only; Sec. 2.3 notes its line kernels use no tensor cores).
+ *   pipe 0: FP32 FMA issued as packed f32x2 fma, counted as 2 FP32 operations
+ *           per lane per instruction;
+ *   pipe 1: MUFU reciprocal (rcp.approx.ftz.f32 of x + 1, so that the chain cannot
+ *           be simplified), 1 operation per lane.
+ * 8 CTAs x 256 threads per SM each run 8 independent dependency chains for
+ * `iters` rounds; one warm-up launch, then one launch timed with CUDA events on
+ * `stream`.  *ops_per_s (host) receives operations per second over the device.
+ * Allocates and frees a small device buffer; synchronises `stream`.
+ * Errors: PZ_EINVAL for pipe outside {0, 1}, iters outside [1, 2^20] or a NULL
+ * ops_per_s. */
+pz_status pz_probe_pipe(int32_t pipe, int32_t iters, double *ops_per_s, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

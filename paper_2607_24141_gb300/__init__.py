@@ -83,6 +83,7 @@ _SIGS = {
                                 _vp]),
     "pz_probe_voigt": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
     "pz_probe_expn": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
+    "pz_probe_pipe": (C.c_int, [C.c_int32, C.c_int32, _dp, _vp]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -282,6 +283,13 @@ def pz_probe_voigt(a, v, H, dHda=None, stream=None):
 
 def pz_probe_expn(x, out, stream=None):
     _check(load().pz_probe_expn(_ptr(x), x.numel(), _ptr(out), _stream(stream)))
+
+
+def pz_probe_pipe(pipe, iters=4096, stream=None) -> float:
+    """Measured operations per second of pipe 0 (FP32 FMA) or 1 (MUFU reciprocal)."""
+    r = C.c_double(0.0)
+    _check(load().pz_probe_pipe(int(pipe), int(iters), C.byref(r), _stream(stream)))
+    return r.value
 
 
 # ---------------------------------------------------------------------------

@@ -1021,6 +1021,37 @@ pz_status pz_probe_voigt(const float *a, const float *v, int64_t n, float *H, fl
     return PZ_OK;
 }
 
+pz_status pz_probe_pipe(int32_t pipe, int32_t iters, double *ops_per_s, void *stream) {
+    if (pipe < 0 || pipe > 1) return fail(PZ_EINVAL, "pz_probe_pipe: pipe must be 0 (FP32 FMA) or 1 (MUFU)");
+    if (iters < 1 || iters > (1 << 20)) return fail(PZ_EINVAL, "pz_probe_pipe: iters must be in [1, 2^20]");
+    if (!ops_per_s) return fail(PZ_EINVAL, "pz_probe_pipe: ops_per_s is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, nsm = 0;
+    PZ_CUDA(cudaGetDevice(&dev), "pz_probe_pipe");
+    PZ_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev), "pz_probe_pipe");
+    const int blocks = 8 * nsm;
+    float *out = nullptr;
+    PZ_TRY(dalloc(&out, (size_t)blocks * kProbeThreads, "pz_probe_pipe"));
+    cudaEvent_t a = nullptr, b = nullptr;
+    pz_status st = PZ_OK;
+    float ms = 0.0f;
+    if ((st = cuda_check(cudaEventCreate(&a), "pz_probe_pipe")) == PZ_OK &&
+        (st = cuda_check(cudaEventCreate(&b), "pz_probe_pipe")) == PZ_OK &&
+        (st = cuda_check(launch_probe_pipe(pipe, iters, blocks, out, s), "pz_probe_pipe")) == PZ_OK &&   // warm-up
+        (st = cuda_check(cudaEventRecord(a, s), "pz_probe_pipe")) == PZ_OK &&
+        (st = cuda_check(launch_probe_pipe(pipe, iters, blocks, out, s), "pz_probe_pipe")) == PZ_OK &&
+        (st = cuda_check(cudaEventRecord(b, s), "pz_probe_pipe")) == PZ_OK &&
+        (st = cuda_check(cudaEventSynchronize(b), "pz_probe_pipe")) == PZ_OK)
+        st = cuda_check(cudaEventElapsedTime(&ms, a, b), "pz_probe_pipe");
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    dfree(out);
+    if (st != PZ_OK) return st;
+    const double per_thread = pipe == 0 ? 16.0 : 8.0;
+    *ops_per_s = (double)blocks * kProbeThreads * per_thread * (double)iters / (ms * 1e-3);
+    return PZ_OK;
+}
+
 pz_status pz_probe_expn(const double *x, int64_t n, double *out, void *stream) {
     if (n < 0 || (n > 0 && (!x || !out))) return fail(PZ_EINVAL, "pz_probe_expn: bad arguments");
     PZ_CUDA(launch_probe_expn(x, n, out, (cudaStream_t)stream), "probe expn");

@@ -215,6 +215,8 @@ cudaError_t launch_rt_adjoint(pz_ctx *c, cudaStream_t s);
 cudaError_t launch_grad_finalize(pz_ctx *c, float *g_gf, float *g_g6, float *g_ab, cudaStream_t s);
 cudaError_t launch_update(pz_ctx *c, float lr_gf, float lr_g6, float lr_ab, cudaStream_t s);
 cudaError_t launch_probe_expn(const double *x, int64_t n, double *out, cudaStream_t s);
+constexpr int kProbeThreads = 256;   // threads per CTA of the pipe-throughput probe
+cudaError_t launch_probe_pipe(int kind, int iters, int blocks, float *out, cudaStream_t s);
 bool tiling_supported(int J, int DS, int minb);
 bool tiling_fits(const Tiling &t);   // both far-wing chunks fit in shared memory
 

@@ -148,6 +148,7 @@ struct LineArgs {
     int n_items, ngroups;
     int *ctr;
     int64_t sstride, dstride, bstride, tstride;     // per-star strides of the tables above
+    float rj[4], rm1j[4];                           // r^-j and r^-j - 1, j = 0..3 (r = 1 + 1/R)
 };
 
 __device__ __forceinline__ LineArgs star_view(const LineArgs &g, int s) {
@@ -185,29 +186,47 @@ __device__ __forceinline__ void for_each_item(const LineArgs &g, F &&f) {
 //  [0] k = c/dv_D   [1] a^2   [2..6] B1..B5 = A a/sqrt(pi) x (1, 1.5, 3.75-2a^2, -15a^2, 12a^4)
 //  [7] A            (backward:) [8..13] C1..C6 = A a6/sqrt(pi) x (1, 1.5-2a^2, 3.75-12a^2,
 //  12a^4-67.5a^2, 180a^4, -120a^6)   [14] A a6   [15] a
+// Per-line scalars of the prefactors (one load per line, shared by its depths).
+struct LineScalars {
+    int sp;
+    float E, Q, lamcm, g4, grad, g6;
+};
+__device__ __forceinline__ LineScalars load_line(const LineArgs &g, int64_t l) {
+    LineScalars L;
+    L.sp = g.sp[l];
+    L.E = g.E[l];
+    L.Q = g.Q[l];
+    L.lamcm = g.lamcm[l];
+    L.g4 = g.g4[l];
+    L.grad = g.grad[l];
+    L.g6 = g.g6[l];
+    return L;
+}
+
+// The damping products are rounded explicitly (no contraction), so that every kernel
+// that classifies a cell by |v|^2 + a^2 -- the far-wing and near-core passes -- forms
+// k and a^2 with identical roundings.
 template <int NP>
-__device__ __forceinline__ void line_params(const LineArgs &g, int64_t l, int d, float *out) {
+__device__ __forceinline__ void depth_params(const LineArgs &g, const LineScalars &L, int d, float *out) {
     if (d >= g.nd) {
 #pragma unroll
         for (int k = 0; k < NP; ++k) out[k] = 0.0f;
         out[1] = 1.0f;
         return;
     }
-    int s = g.sp[l];
-    int id = s * g.nd + d;
-    float invdv = __ldg(g.invdv + id);
-    float E = g.E[l];
-    float bh = __ldg(g.beta_hi + d), bl = __ldg(g.beta_lo + d);
-    float p = E * bh;
-    float r = fmaf(E, bh, -p) + E * bl;              // E beta = p + r
-    float boltz = expf(-p) * (1.0f - r);
-    float A = g.Q[l] * __ldg(g.R + id) * boltz;
-    float lw = g.lamcm[l] * invdv * (float)(1.0 / (4.0 * kPI));
-    float g6n = g.g6[l] * __ldg(g.npert + d);
-    float a = fmaf(g.g4[l], __ldg(g.ne + d), g.grad[l] + g6n) * lw;
-    float a2 = a * a;
-    float B1 = A * a * kInvSqrtPiF;
-    out[0] = (float)kC * invdv;
+    const int id = L.sp * g.nd + d;
+    const float invdv = __ldg(g.invdv + id);
+    const float bh = __ldg(g.beta_hi + d), bl = __ldg(g.beta_lo + d);
+    const float p = L.E * bh;
+    const float r = fmaf(L.E, bh, -p) + L.E * bl;      // E beta = p + r
+    const float boltz = expf(-p) * (1.0f - r);
+    const float A = L.Q * __ldg(g.R + id) * boltz;
+    const float lw = __fmul_rn(__fmul_rn(L.lamcm, invdv), (float)(1.0 / (4.0 * kPI)));
+    const float g6n = __fmul_rn(L.g6, __ldg(g.npert + d));
+    const float a = __fmul_rn(fmaf(L.g4, __ldg(g.ne + d), __fadd_rn(L.grad, g6n)), lw);
+    const float a2 = __fmul_rn(a, a);
+    const float B1 = A * a * kInvSqrtPiF;
+    out[0] = __fmul_rn((float)kC, invdv);
     out[1] = a2;
     out[2] = B1;
     out[3] = 1.5f * B1;
@@ -216,8 +235,8 @@ __device__ __forceinline__ void line_params(const LineArgs &g, int64_t l, int d,
     out[6] = 12.0f * a2 * a2 * B1;
     out[7] = A;
     if (NP == 16) {
-        float Aa6 = A * g6n * lw;
-        float C1 = Aa6 * kInvSqrtPiF;
+        const float Aa6 = A * g6n * lw;
+        const float C1 = Aa6 * kInvSqrtPiF;
         out[8] = C1;
         out[9] = fmaf(-2.0f, a2, 1.5f) * C1;
         out[10] = fmaf(-12.0f, a2, 3.75f) * C1;
@@ -227,6 +246,18 @@ __device__ __forceinline__ void line_params(const LineArgs &g, int64_t l, int d,
         out[14] = Aa6;
         out[15] = a;
     }
+}
+
+template <int NP>
+__device__ __forceinline__ void line_params(const LineArgs &g, int64_t l, int d, float *out) {
+    depth_params<NP>(g, load_line(g, l), d, out);
+}
+
+// Shared-memory stride of one staged line, in 16-byte quads: DC/2 depth pairs of NQ
+// quads each, padded to an odd count so that the float4 stores of threads staging
+// consecutive lines (same depth pair) fall in distinct banks.
+__host__ __device__ constexpr int line_quads(int DC, int NQ) {
+    return (DC / 2) * NQ + ((((DC / 2) * NQ) & 1) ? 2 : 1);
 }
 
 // index-space frequency offset u = lambda_l/lambda_i - 1 = expm1(Delta ln r)
@@ -297,12 +328,11 @@ __device__ __forceinline__ f2_t f2_rcp(f2_t a) {
 }
 
 // Shared-memory layout of the per-(line, depth) prefactors for the packed kernels:
-// per line and depth pair, parameter m of both depths sits at float offset
-// (m >> 1) * 4 + (m & 1) * 2 + (depth & 1), so one 16-byte load returns the pairs of
-// parameters 2q and 2q + 1.
-//   forward  (8):  k, a^2, B1, B2, B3, B4, B5, A
-//   backward (14): k, a^2, B1, B2, B3, B4, B5, C1, C2, C3, C4, C5, C6, (pad)
-__device__ __forceinline__ int par_off(int m, int dd) { return ((m >> 1) << 2) + ((m & 1) << 1) + (dd & 1); }
+// per line, line_quads(DC, NQ) quads; per depth pair, NQ quads, quad q holding
+// {p_2q(d), p_2q(d + 1), p_2q+1(d), p_2q+1(d + 1)}, so one 16-byte load returns the
+// packed depth pairs of two parameters.
+//   forward  (NQ = 4): (k, a^2) (B1, B2) (B3, B4) (B5, A)
+//   backward (NQ = 7): (k, a^2) (B1, B2) (C1, C2) (B3, B4) (B5, C3) (C4, C5) (C6, -)
 
 // Compensated-sum slots of depth dd of thread tid: the (hi, lo) pairs of its J points,
 // hi at [0, 4) and lo at [4, 8) (the J points of a thread are contiguous: one vector
@@ -357,15 +387,22 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
     static_assert(DS % 2 == 0, "DS must be even (depth pairs)");
     constexpr int DP = DS / 2;          // depth pairs per warp
-    constexpr int NPF = 8;              // floats per (line, depth) in shared memory
+    constexpr int NQ = 4;               // quads per (line, depth pair) in shared memory
     extern __shared__ float4 smem4[];
     const int T = 32 * J;
     const int DC = GW * DS;
+    const int LQ = line_quads(DC, NQ);
     const int nthr = blockDim.x;
-    float *s_parf = reinterpret_cast<float *>(smem4);                   // [LC][DC/2][2 * NPF]
-    const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(smem4);
-    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * DC * NPF / 4);
+    const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(smem4);   // [LC][LQ] quads
+    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * LQ);
     float *s_comp = reinterpret_cast<float *>(s_line + LC);             // [DS][nthr][8] compensated sums
+    // offsets of the thread's other points from the first: u_j = u_0 r^-j + (r^-j - 1)
+    f2_t rj2[J], rm2[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        rj2[j] = f2_pack(g.rj[j], g.rj[j]);
+        rm2[j] = f2_pack(g.rm1j[j], g.rm1j[j]);
+    }
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int d0 = group * DC;
@@ -389,13 +426,17 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
     for (int c0 = lo; c0 < hi; c0 += LC) {
         const int nl = min(LC, hi - c0);
         __syncthreads();
-        for (int idx = tid; idx < nl * DC; idx += nthr) {
-            int li = idx / DC, dd = idx - li * DC;
-            float p[8];
-            line_params<8>(g, c0 + li, d0 + dd, p);
-            float *dst = s_parf + ((size_t)li * (DC / 2) + (dd >> 1)) * (2 * NPF);
+        // stage the prefactors: a thread takes one line and depth pair (consecutive
+        // threads, consecutive lines) and writes the pair's quads
+        for (int idx = tid; idx < nl * (DC / 2); idx += nthr) {
+            const int pr = idx / nl, li = idx - pr * nl;
+            const LineScalars L = load_line(g, c0 + li);
+            float p0[8], p1[8];
+            depth_params<8>(g, L, d0 + 2 * pr, p0);
+            depth_params<8>(g, L, d0 + 2 * pr + 1, p1);
+            float4 *dst = smem4 + (size_t)li * LQ + pr * NQ;
 #pragma unroll
-            for (int m = 0; m < NPF; ++m) dst[par_off(m, dd)] = p[m];
+            for (int q = 0; q < NQ; ++q) dst[q] = make_float4(p0[2 * q], p1[2 * q], p0[2 * q + 1], p1[2 * q + 1]);
         }
         for (int li = tid; li < nl; li += nthr) {
             int64_t l = c0 + li;
@@ -410,12 +451,21 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
 
         for (int li = 0; li < nl; ++li) {
             const LineInfo info = s_line[li];
-            const ulonglong2 *par = s_par + ((size_t)li * (DC / 2) + warp * DP) * (NPF / 2);
+            const ulonglong2 *par = s_par + (size_t)li * LQ + warp * DP * NQ;
             f2_t u2[J];
+            if ((info.pad >> warp) & 1) {
+                // the whole tile is in the line's far wing: offsets from the first point's
+                const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
+                u2[0] = f2_pack(u0, u0);
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const float u = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
-                u2[j] = f2_pack(u, u);
+                for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], rj2[j], rm2[j]);
+            } else {
+                // cells are classified near / far exactly as the near-core kernel does
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const float u = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
+                    u2[j] = f2_pack(u, u);
+                }
             }
             if ((info.pad >> (8 + warp)) & 1) {
                 // reduced form: t (B1 + B2 t)
@@ -617,14 +667,20 @@ __device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, 
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
     static_assert(DS % 2 == 0, "DS must be even (depth pairs)");
     constexpr int DP = DS / 2;
-    constexpr int NPB = 14;             // floats per (line, depth) in shared memory
+    constexpr int NQ = 7;               // quads per (line, depth pair) in shared memory
     extern __shared__ float4 smem4[];
     const int T = 32 * J;
     const int DC = GW * DS;
+    const int LQ = line_quads(DC, NQ);
     const int nthr = blockDim.x;
-    float *s_parf = reinterpret_cast<float *>(smem4);                   // [LC][DC/2][2 * NPB]
-    const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(smem4);
-    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * DC * NPB / 4);
+    const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(smem4);   // [LC][LQ] quads
+    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * LQ);
+    f2_t rj2[J], rm2[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        rj2[j] = f2_pack(g.rj[j], g.rj[j]);
+        rm2[j] = f2_pack(g.rm1j[j], g.rm1j[j]);
+    }
     float2 *s_red = reinterpret_cast<float2 *>(s_line + LC);            // [LC][GW]
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -651,16 +707,21 @@ __device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, 
     for (int c0 = lo; c0 < hi; c0 += LC) {
         const int nl = min(LC, hi - c0);
         __syncthreads();
-        for (int idx = tid; idx < nl * DC; idx += nthr) {
-            int li = idx / DC, dd = idx - li * DC;
-            float p[16];
-            line_params<16>(g, c0 + li, d0 + dd, p);
-            float *dst = s_parf + ((size_t)li * (DC / 2) + (dd >> 1)) * (2 * NPB);
-            // (k, a^2) (B1, B2) (C1, C2) (B3, B4) (B5, C3) (C4, C5) (C6, -)
-            constexpr int src[14] = {0, 1, 2, 3, 8, 9, 4, 5, 6, 10, 11, 12, 13, 0};
+        for (int idx = tid; idx < nl * (DC / 2); idx += nthr) {
+            const int pr = idx / nl, li = idx - pr * nl;
+            const LineScalars L = load_line(g, c0 + li);
+            float p0[16], p1[16];
+            depth_params<16>(g, L, d0 + 2 * pr, p0);
+            depth_params<16>(g, L, d0 + 2 * pr + 1, p1);
+            // quads (k, a^2) (B1, B2) (C1, C2) (B3, B4) (B5, C3) (C4, C5) (C6, -) of both depths
+            constexpr int src[14] = {0, 1, 2, 3, 8, 9, 4, 5, 6, 10, 11, 12, 13, 13};
+            float4 *dst = smem4 + (size_t)li * LQ + pr * NQ;
 #pragma unroll
-            for (int m = 0; m < 13; ++m) dst[par_off(m, dd)] = p[src[m]];
-            dst[par_off(13, dd)] = 0.0f;
+            for (int q = 0; q < NQ; ++q) {
+                const bool pad = 2 * q + 1 == 13;
+                dst[q] = make_float4(p0[src[2 * q]], p1[src[2 * q]], pad ? 0.0f : p0[src[2 * q + 1]],
+                                     pad ? 0.0f : p1[src[2 * q + 1]]);
+            }
         }
         for (int li = tid; li < nl; li += nthr) {
             int64_t l = c0 + li;
@@ -675,12 +736,19 @@ __device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, 
 
         for (int li = 0; li < nl; ++li) {
             const LineInfo info = s_line[li];
-            const ulonglong2 *par = s_par + ((size_t)li * (DC / 2) + warp * DP) * (NPB / 2);
+            const ulonglong2 *par = s_par + (size_t)li * LQ + warp * DP * NQ;
             f2_t u2[J];
+            if ((info.pad >> warp) & 1) {
+                const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
+                u2[0] = f2_pack(u0, u0);
 #pragma unroll
-            for (int j = 0; j < J; ++j) {
-                const float u = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
-                u2[j] = f2_pack(u, u);
+                for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], rj2[j], rm2[j]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const float u = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
+                    u2[j] = f2_pack(u, u);
+                }
             }
             f2_t S1 = 0ull, S2 = 0ull;
             if ((info.pad >> (8 + warp)) & 1) {
@@ -753,146 +821,153 @@ __device__ __forceinline__ bool near_span(const LineArgs &g, float ilf, float fr
     return lo <= hi;
 }
 
-// One near-core item (a line at one depth) after its lane-parallel set-up.
+// One near-core item (a line at one depth) after its lane-parallel set-up.  Its near
+// span [lo, hi] (clipped to the tile and the window) is split analytically into the
+// core segment (|z|^2 < 36, cells [c0, r0)) and the mid-wing cells on either side
+// (nl cells from lo, then the cells from r0 to hi).
 struct alignas(16) NearItem {
     float ilf, frac, k, a2;      // centre, Doppler factor c/dv_D, a^2
     float a, A, Aa6;             // damping, strength, strength x vdW damping
-    int lo, hi, dl, lb, pad;     // clipped span, local depth, local line (batch) index
+    int lo, nl, c0, r0;          // span start, mid cells left of the core, core segment [c0, r0)
+    int dlb;                     // local depth | (local line index << 8)
 };
 
 constexpr int kNearBatch = 512;      // lines per shared-memory batch of the backward sums
 constexpr int kNearDepthsFwd = 8;    // depths per CTA of the near-core forward
 constexpr int kNearDepthsBwd = 24;   // depths per CTA of the near-core backward
-constexpr int kNearQueue = 768;      // queued cells per warp before a dense pass (mid from the front, core from the back)
 constexpr int kNearWarps = 8;        // warps per near-core CTA
 
-// Near-core sweep shared by the forward (D = false) and the backward (D = true).
-// Each warp takes rounds of 32 (line, depth) items: lanes set up one item each
-// (coarse span from c/dv_D alone, then the exact prefactors and span), the survivors
-// are kept in shared memory, then the warp classifies each item's span 32 points at
-// a time and queues the cells: mid-wing cells (36 <= |z|^2 < 400) from the front of
-// the warp's queue, core cells (|z|^2 < 36) from the back, both in item order.  When
-// the queue is full (and at the end of the round) the warp evaluates the mid entries
-// and then the core entries densely, 32 at a time, so the two Voigt forms never
-// diverge within a warp.
+// Dense pass over the concatenated cells of one segment kind of the warp's 32 items:
+// cell n of the concatenation belongs to item src with pref[src] <= n < pref[src + 1]
+// (each lane advances its own cursor; consecutive lanes hold consecutive cells, so
+// the items of one iteration form ordered runs).
 //   forward:  cell(item, i, H, dH) adds the cell's term where it belongs;
 //   backward: val(item, i, H, dH) returns the cell's (G A H, G A a6 dH) pair and
-//             done(lb, sum) receives the per-queue-segment sums of each item.
+//             done(item, sum) receives the per-run sums of each item.
 template <int T, bool D, bool CORE, class Cell, class Val, class Done>
-__device__ __forceinline__ void near_eval(const LineArgs &g, int t0, const NearItem *mine, const int *q, int n,
-                                          const float *s_daw, Cell &cell, Val &val, Done &done) {
+__device__ __forceinline__ void near_pass(const LineArgs &g, const NearItem *mine, const int *pref, const float *s_daw,
+                                          Cell &cell, Val &val, Done &done) {
     const int lane = threadIdx.x & 31;
-    for (int e0 = 0; e0 < n; e0 += 32) {
-        const int e = e0 + lane;
-        int src = -1;
+    const int total = pref[32];
+    int src = 0;
+    for (int n0 = 0; n0 < total; n0 += 32) {
+        const int n = n0 + lane;
+        int run = -1;
         float2 v = make_float2(0.0f, 0.0f);
-        if (e < n) {
-            const int code = q[e];
-            src = code >> 16;
+        if (n < total) {
+            while (pref[src + 1] <= n) ++src;
             const NearItem &it = mine[src];
-            const int i = t0 + (code & 0xffff);
+            const int off = n - pref[src];
+            const int i = CORE ? it.c0 + off : (off < it.nl ? it.lo + off : it.r0 + (off - it.nl));
             const float x = fabsf(offset_u((it.ilf - (float)i) + it.frac, g.lnr) * it.k);
-            float H, dH;
-            if (CORE)
-                voigt_core<D>(x, it.a, H, dH, s_daw);
-            else
-                voigt_mid<D>(x, it.a, H, dH);
-            if (D)
-                v = val(it, i, H, dH);
-            else
-                cell(it, i, H, dH);
+            run = src;
+            // a mid-wing cell at |z| >= 20 belongs to the far-wing kernels (same test)
+            if (CORE || fmaf(x, x, it.a2) < kFar2) {
+                float H, dH;
+                if (CORE)
+                    voigt_core<D>(x, it.a, H, dH, s_daw);
+                else
+                    voigt_mid<D>(x, it.a, H, dH);
+                if (D)
+                    v = val(it, i, H, dH);
+                else
+                    cell(it, i, H, dH);
+            }
         }
         if (D) {
-            // segmented sum over runs of equal items (entries are grouped by item)
+            // segmented sum over the runs of equal items
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const float nx = __shfl_up_sync(0xffffffffu, v.x, o);
                 const float ny = __shfl_up_sync(0xffffffffu, v.y, o);
-                const int ns = __shfl_up_sync(0xffffffffu, src, o);
-                if (lane >= o && ns == src) {
+                const int ns = __shfl_up_sync(0xffffffffu, run, o);
+                if (lane >= o && ns == run) {
                     v.x += nx;
                     v.y += ny;
                 }
             }
-            const int next = __shfl_down_sync(0xffffffffu, src, 1);
-            if (src >= 0 && (lane == 31 || next != src)) done(mine[src].lb, v);
+            const int next = __shfl_down_sync(0xffffffffu, run, 1);
+            if (run >= 0 && (lane == 31 || next != run)) done(mine[run], v);
         }
     }
 }
 
+// Near-core sweep shared by the forward (D = false) and the backward (D = true).
+// Each warp takes rounds of 32 (line, depth) items: every lane sets up one item
+// (coarse span from c/dv_D alone, then the exact prefactors, the clipped span and
+// its core / mid split), a warp scan turns the per-item cell counts into offsets,
+// and the warp then sweeps all mid-wing cells of the round and all core cells of
+// the round, 32 consecutive cells at a time, so the two Voigt forms never diverge
+// within a warp and no lane idles while cells remain.
 template <int T, bool D, class Cell, class Val, class Done>
 __device__ __forceinline__ void near_sweep(const LineArgs &g, int t0, int64_t nlo, int64_t nitems, int ndg, int dbase,
-                                           NearItem *s_items, int *s_queue, const float *s_daw, Cell &&cell, Val &&val,
-                                           Done &&done) {
+                                           NearItem *s_items, int *s_pref, const float *s_daw, Cell &&cell,
+                                           Val &&val, Done &&done) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
     NearItem *mine = s_items + warp * 32;
-    int *queue = s_queue + warp * kNearQueue;
-    int nm = 0, nc = 0;          // mid entries [0, nm), core entries [kNearQueue - nc, kNearQueue)
-    auto flush = [&]() {
-        __syncwarp();
-        near_eval<T, D, false>(g, t0, mine, queue, nm, s_daw, cell, val, done);
-        near_eval<T, D, true>(g, t0, mine, queue + kNearQueue - nc, nc, s_daw, cell, val, done);
-        nm = nc = 0;
-        __syncwarp();
-    };
+    int *pm = s_pref + warp * 66, *pc = pm + 33;      // prefix counts of mid and core cells
     for (int64_t r0 = (int64_t)warp * 32; r0 < nitems; r0 += (int64_t)nwarp * 32) {
-        // lane-parallel set-up of 32 items
         const int64_t it = r0 + lane;
-        bool ok = false;
+        int nmid = 0, ncore = 0;
         NearItem item;
         if (it < nitems) {
             const int64_t l = nlo + it / ndg;
             const int dl = (int)(it % ndg), d = dbase + dl;
             item.ilf = g.ilf[l];
             item.frac = g.frac[l];
-            item.dl = dl;
-            item.lb = (int)(it / ndg);
+            item.dlb = dl | ((int)(it / ndg) << 8);
             const float k = (float)kC * __ldg(g.invdv + g.sp[l] * g.nd + d);
             int lo, hi;
             if (near_span(g, item.ilf, item.frac, k, 0.0f, t0, T, lo, hi)) {
                 float p[16];
                 line_params<D ? 16 : 8>(g, l, d, p);
                 if (near_span(g, item.ilf, item.frac, p[0], p[1], t0, T, lo, hi)) {
-                    ok = true;
                     item.k = p[0];
                     item.a2 = p[1];
                     item.A = p[7];
                     item.a = D ? p[15] : sqrtf(p[1]);
                     item.Aa6 = D ? p[14] : 0.0f;
+                    // core segment: |x| < sqrt(36 - a^2), x = u k, |u| ~ |x_l - i| ln r
+                    int c0 = hi + 1, c1 = hi;
+                    if (p[1] < kMid2) {
+                        const float w = sqrtf(kMid2 - p[1]) / (p[0] * g.lnr);
+                        const float xl = item.ilf + item.frac;
+                        c0 = max(lo, (int)ceilf(xl - w));
+                        c1 = min(hi, (int)floorf(xl + w));
+                        if (c0 > c1) {
+                            c0 = hi + 1;
+                            c1 = hi;
+                        }
+                    }
+                    ncore = c1 - c0 + 1;
+                    nmid = (hi - lo + 1) - ncore;
                     item.lo = lo;
-                    item.hi = hi;
+                    item.nl = ncore > 0 ? c0 - lo : nmid;
+                    item.c0 = c0;
+                    item.r0 = ncore > 0 ? c1 + 1 : hi + 1;
                 }
             }
         }
-        const unsigned okm = __ballot_sync(0xffffffffu, ok);
-        __syncwarp();
-        if (ok) mine[lane] = item;
-        __syncwarp();
-        // classify the surviving items' spans into the queue
-        for (unsigned m = okm; m; m &= m - 1) {
-            const int src = __ffs(m) - 1;
-            const NearItem &itm = mine[src];
-            if (nm + nc + (itm.hi - itm.lo + 1) > kNearQueue) flush();
-            for (int i0 = itm.lo; i0 <= itm.hi; i0 += 32) {
-                const int i = i0 + lane;
-                bool mid = false, core = false;
-                if (i <= itm.hi) {
-                    const float x = fabsf(offset_u((itm.ilf - (float)i) + itm.frac, g.lnr) * itm.k);
-                    const float r2 = fmaf(x, x, itm.a2);
-                    mid = r2 < kFar2 && r2 >= kMid2;
-                    core = r2 < kMid2;
-                }
-                const int code = (src << 16) | (i - t0);
-                const unsigned mm = __ballot_sync(0xffffffffu, mid);
-                const unsigned cm = __ballot_sync(0xffffffffu, core);
-                const unsigned below = (1u << lane) - 1u;
-                if (mid) queue[nm + __popc(mm & below)] = code;
-                if (core) queue[kNearQueue - 1 - (nc + __popc(cm & below))] = code;
-                nm += __popc(mm);
-                nc += __popc(cm);
-            }
+        // exclusive prefix of the packed counts (mid << 16 | core; a round holds < 2^16 cells)
+        const int own = (nmid << 16) | ncore;
+        int inc = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
         }
-        flush();
+        __syncwarp();
+        const int exc = inc - own;
+        pm[lane] = exc >> 16;
+        pc[lane] = exc & 0xffff;
+        if (lane == 31) {
+            pm[32] = inc >> 16;
+            pc[32] = inc & 0xffff;
+        }
+        if (own != 0) mine[lane] = item;
+        __syncwarp();
+        near_pass<T, D, false>(g, mine, pm, s_daw, cell, val, done);
+        near_pass<T, D, true>(g, mine, pc, s_daw, cell, val, done);
     }
 }
 
@@ -902,8 +977,8 @@ __global__ void __launch_bounds__(32 * kNearWarps) k_line_near_fwd(LineArgs gq) 
     extern __shared__ float4 smem4[];
     float *s_acc = reinterpret_cast<float *>(smem4);                               // [NDG][T]
     NearItem *s_items = reinterpret_cast<NearItem *>(s_acc + NDG * T);             // [warps][32]
-    int *s_queue = reinterpret_cast<int *>(s_items + kNearWarps * 32);             // [warps][kNearQueue]
-    float *s_daw = reinterpret_cast<float *>(s_queue + kNearWarps * kNearQueue);   // Dawson table
+    int *s_pref = reinterpret_cast<int *>(s_items + kNearWarps * 32);              // [warps][2][33]
+    float *s_daw = reinterpret_cast<float *>(s_pref + kNearWarps * 66);            // Dawson table
     for (int k = threadIdx.x; k < kDawsonNodes * (kDawsonK + 1); k += blockDim.x) s_daw[k] = g_dawson[k];
     for_each_item(gq, [&](const LineArgs &g, int tile, int group, int nlo, int nhi) {
     const int tid = threadIdx.x;
@@ -912,9 +987,12 @@ __global__ void __launch_bounds__(32 * kNearWarps) k_line_near_fwd(LineArgs gq) 
     for (int k = tid; k < NDG * T; k += blockDim.x) s_acc[k] = 0.0f;
     __syncthreads();
     near_sweep<T, false>(
-        g, t0, nlo, (int64_t)(nhi - nlo) * ndg, ndg, dbase, s_items, s_queue, s_daw,
-        [&](const NearItem &it, int i, float H, float) { atomicAdd(s_acc + it.dl * T + (i - t0), it.A * H); },
-        [&](const NearItem &, int, float, float) { return make_float2(0.0f, 0.0f); }, [&](int, float2) {});
+        g, t0, nlo, (int64_t)(nhi - nlo) * ndg, ndg, dbase, s_items, s_pref, s_daw,
+        [&](const NearItem &it, int i, float H, float) {
+            atomicAdd(s_acc + (it.dlb & 0xff) * T + (i - t0), it.A * H);
+        },
+        [&](const NearItem &, int, float, float) { return make_float2(0.0f, 0.0f); },
+        [&](const NearItem &, float2) {});
     __syncthreads();
     for (int k = tid; k < ndg * T; k += blockDim.x) {
         const int dl = k / T, q = k - dl * T;
@@ -932,8 +1010,8 @@ __global__ void __launch_bounds__(32 * kNearWarps) k_line_near_bwd(LineArgs gq) 
     float *s_g = reinterpret_cast<float *>(smem4);                                 // [NDG][T] G * stim
     float2 *s_sum = reinterpret_cast<float2 *>(s_g + NDG * T);                     // [kNearBatch]
     NearItem *s_items = reinterpret_cast<NearItem *>(s_sum + kNearBatch);          // [warps][32]
-    int *s_queue = reinterpret_cast<int *>(s_items + kNearWarps * 32);             // [warps][kNearQueue]
-    float *s_daw = reinterpret_cast<float *>(s_queue + kNearWarps * kNearQueue);   // Dawson table
+    int *s_pref = reinterpret_cast<int *>(s_items + kNearWarps * 32);              // [warps][2][33]
+    float *s_daw = reinterpret_cast<float *>(s_pref + kNearWarps * 66);            // Dawson table
     for (int k = threadIdx.x; k < kDawsonNodes * (kDawsonK + 1); k += blockDim.x) s_daw[k] = g_dawson[k];
     for_each_item(gq, [&](const LineArgs &g, int tile, int group, int nlo, int nhi) {
     const int tid = threadIdx.x;
@@ -949,12 +1027,14 @@ __global__ void __launch_bounds__(32 * kNearWarps) k_line_near_bwd(LineArgs gq) 
         for (int k = tid; k < nb; k += blockDim.x) s_sum[k] = make_float2(0.0f, 0.0f);
         __syncthreads();
         near_sweep<T, true>(
-            g, t0, b0, (int64_t)nb * ndg, ndg, dbase, s_items, s_queue, s_daw, [&](const NearItem &, int, float, float) {},
+            g, t0, b0, (int64_t)nb * ndg, ndg, dbase, s_items, s_pref, s_daw,
+            [&](const NearItem &, int, float, float) {},
             [&](const NearItem &it, int i, float H, float dH) {
-                const float gs = s_g[it.dl * T + (i - t0)];
+                const float gs = s_g[(it.dlb & 0xff) * T + (i - t0)];
                 return make_float2(gs * it.A * H, gs * it.Aa6 * dH);
             },
-            [&](int lb, float2 v) {
+            [&](const NearItem &it, float2 v) {
+                const int lb = it.dlb >> 8;
                 atomicAdd(&s_sum[lb].x, v.x);
                 atomicAdd(&s_sum[lb].y, v.y);
             });
@@ -972,7 +1052,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) k_line_near_bwd(LineArgs gq) 
 template <int T, int NDG, bool BWD>
 constexpr size_t near_smem() {
     return (size_t)NDG * T * sizeof(float) + (BWD ? kNearBatch * sizeof(float2) : 0) +
-           (size_t)kNearWarps * 32 * sizeof(NearItem) + (size_t)kNearWarps * kNearQueue * sizeof(int) +
+           (size_t)kNearWarps * 32 * sizeof(NearItem) + (size_t)kNearWarps * 66 * sizeof(int) +
            (size_t)kDawsonNodes * (kDawsonK + 1) * sizeof(float);
 }
 
@@ -983,6 +1063,10 @@ static LineArgs make_args(pz_ctx *c) {
     g.nd = c->nd;
     g.W = c->W;
     g.lnr = (float)c->lnr;
+    for (int j = 0; j < 4; ++j) {
+        g.rj[j] = (float)std::exp(-j * c->lnr);
+        g.rm1j[j] = (float)std::expm1(-j * c->lnr);
+    }
     g.lam0cm = (float)(c->lambda0_nm * 1e-7);
     g.ilf = c->L.ilf;
     g.frac = c->L.frac;
@@ -1074,11 +1158,11 @@ static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
 // Dynamic shared memory of the far-wing kernels: staged prefactors, line records and
 // (forward) the compensated sums of every thread, or (backward) the per-line sums.
 static size_t far_fwd_smem(const Tiling &t) {
-    return (size_t)t.LC * t.depth_per_cta() * 8 * sizeof(float) + t.LC * sizeof(LineInfo) +
+    return (size_t)t.LC * line_quads(t.depth_per_cta(), 4) * sizeof(float4) + t.LC * sizeof(LineInfo) +
            (size_t)t.DS * 32 * t.GW * 2 * sizeof(float4);
 }
 static size_t far_bwd_smem(const Tiling &t) {
-    return (size_t)t.LCB * t.depth_per_cta() * 14 * sizeof(float) + t.LCB * sizeof(LineInfo) +
+    return (size_t)t.LCB * line_quads(t.depth_per_cta(), 7) * sizeof(float4) + t.LCB * sizeof(LineInfo) +
            (size_t)t.LCB * t.GW * sizeof(float2);
 }
 constexpr size_t kFarSmemMax = 200 * 1024;   // the opt-in size the far-wing kernels are given
@@ -1415,6 +1499,49 @@ __global__ void k_probe_voigt(const float *a, const float *v, int64_t n, float *
 cudaError_t launch_probe_voigt(const float *a, const float *v, int64_t n, float *H, float *dH, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_probe_voigt<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, v, n, H, dH);
+    return cudaGetLastError();
+}
+
+// Pipe-throughput probes (roofline denominators).  Every thread runs 8 independent
+// dependency chains for `iters` rounds; the chains stay bounded (x -> 1/(x + 1), which
+// no algebraic rewrite removes, for the reciprocal; a contraction toward a fixed point
+// for the FMA) and one result per thread is stored so that the work is live.
+//   kind 0: packed f32x2 FMA, 16 FP32 operations per thread per round;
+//   kind 1: rcp.approx.ftz.f32 (plus one FP32 add), 8 MUFU operations per thread per round.
+__global__ void k_probe_pipe(int kind, int iters, float *out) {
+    const float seed = 1.0f + 1e-3f * (float)(threadIdx.x & 63);
+    float r = 0.0f;
+    if (kind == 0) {
+        f2_t x[8];
+        const f2_t m = f2_pack(0.999f, 0.998f), c = f2_pack(1e-3f, 2e-3f);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = f2_pack(seed + k, seed - k);
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = f2_fma(x[k], m, c);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            float lo, hi;
+            f2_unpack(x[k], lo, hi);
+            r += lo + hi;
+        }
+    } else {
+        float x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = seed + (float)k;
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = rcp_approx(x[k] + 1.0f);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r += x[k];
+    }
+    out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+cudaError_t launch_probe_pipe(int kind, int iters, int blocks, float *out, cudaStream_t s) {
+    k_probe_pipe<<<blocks, kProbeThreads, 0, s>>>(kind, iters, out);
     return cudaGetLastError();
 }
 

@@ -54,3 +54,16 @@ def test_fp64_expn(oracle):
         ref = oracle.expn(n, x)
         m = ref > 1e-290
         assert np.max(np.abs(got[k][m] / ref[m] - 1)) < 5e-14, n
+
+
+def test_pipe_probes_are_plausible():
+    import torch
+    n_sm = torch.cuda.get_device_properties(0).multi_processor_count
+    fma = pz.pz_probe_pipe(0, 2048)
+    rcp = pz.pz_probe_pipe(1, 2048)
+    # between a quarter of the lane-count rate at 1 GHz and the lane-count rate at 2.5 GHz
+    assert 0.25 * n_sm * 128 * 1e9 < fma < n_sm * 256 * 2.5e9
+    assert 0.25 * n_sm * 16 * 1e9 < rcp < n_sm * 64 * 2.5e9
+    with pytest.raises(pz.PzError) as e:
+        pz.pz_probe_pipe(2, 16)
+    assert e.value.status == pz.PZ_EINVAL
