@@ -249,7 +249,7 @@ int32_t pz_last_launch_count(const pz_ctx *ctx);
 
 /* Kernel tiling of the mixed-precision line kernels: lambda points per thread
  * (2 or 4), depths per warp, warps per CTA (1-4), lines per shared-memory chunk
- * (the backward uses half) and the minimum number of resident CTAs per SM the
+ * (forward and backward) and the minimum number of resident CTAs per SM the
  * kernels are compiled for (a register budget).  Values <= 0 keep the current
  * setting; the next launch uses the new tiling.  Supported (lambda, depth,
  * CTAs) triples: (4,6,1-4) (4,8,1-3) (4,12,1-2) (2,6,4) (2,8,2-4) (2,12,1-3);
@@ -283,6 +283,15 @@ pz_status pz_set_tiling(pz_ctx *ctx, int32_t lambda_per_thread, int32_t depth_pe
  * was applied). */
 pz_status pz_autotune(pz_ctx *ctx, int32_t with_backward, int32_t reps, int32_t *best, double *best_ms,
                       void *stream);
+
+/* Device status of the context's bounded waits.  The far-wing line kernels stage
+ * each chunk of line prefactors into shared memory with bulk copies that complete
+ * on an mbarrier; a CTA that waits longer than 1 s for a chunk gives up, records the
+ * failure in the context's device status word and stops (its outputs are then
+ * incomplete) instead of hanging the GPU.  This call synchronises `stream`, stores
+ * the status word in *flags (host, may be NULL; bit 0 = a far-wing chunk never
+ * arrived), clears it, and returns PZ_ETIMEOUT if it was non-zero, else PZ_OK. */
+pz_status pz_sync_status(pz_ctx *ctx, void *stream, int32_t *flags);
 
 /* ---- profiling ------------------------------------------------------------- */
 
@@ -362,6 +371,13 @@ pz_status pz_probe_expn(const double *x, int64_t n, double *out, void *stream);
  * Errors: PZ_EINVAL for pipe outside {0, 1}, iters outside [1, 2^20] or a NULL
  * ops_per_s. */
 pz_status pz_probe_pipe(int32_t pipe, int32_t iters, double *ops_per_s, void *stream);
+
+/* The bounded wait of the far-wing kernels, on a barrier phase that nothing
+ * completes: one CTA waits limit_ns (host, in [1, 1e9]) nanoseconds, gives up and
+ * sets bit 0 of a status word exactly as the line kernels do; *flags (host)
+ * receives that word.  Exercises the failure path without a fault or a hang.
+ * Synchronises `stream`; allocates and frees one device word. */
+pz_status pz_probe_wait(int64_t limit_ns, int32_t *flags, void *stream);
 
 #ifdef __cplusplus
 }

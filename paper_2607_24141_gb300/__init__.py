@@ -84,6 +84,8 @@ _SIGS = {
     "pz_probe_voigt": (C.c_int, [_vp, _vp, C.c_int64, _vp, _vp, _vp]),
     "pz_probe_expn": (C.c_int, [_vp, C.c_int64, _vp, _vp]),
     "pz_probe_pipe": (C.c_int, [C.c_int32, C.c_int32, _dp, _vp]),
+    "pz_probe_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), _vp]),
+    "pz_sync_status": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32)]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -283,6 +285,20 @@ def pz_probe_voigt(a, v, H, dHda=None, stream=None):
 
 def pz_probe_expn(x, out, stream=None):
     _check(load().pz_probe_expn(_ptr(x), x.numel(), _ptr(out), _stream(stream)))
+
+
+def pz_probe_wait(limit_ns, stream=None) -> int:
+    """Run the bounded-wait failure path on a barrier nothing completes; returns the status word."""
+    f = C.c_int32(0)
+    _check(load().pz_probe_wait(int(limit_ns), C.byref(f), _stream(stream)))
+    return f.value
+
+
+def pz_sync_status(ctx, stream=None) -> int:
+    """Synchronise, read and clear the context's device status word (raises PZ_ETIMEOUT if set)."""
+    f = C.c_int32(0)
+    _check(load().pz_sync_status(ctx, _stream(stream), C.byref(f)))
+    return f.value
 
 
 def pz_probe_pipe(pipe, iters=4096, stream=None) -> float:

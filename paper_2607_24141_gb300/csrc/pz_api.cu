@@ -226,7 +226,7 @@ static void destroy_ctx(pz_ctx *c) {
                     c->L.Q, c->L.Qbase, c->L.x64, c->L.lg_gf, c->L.lg_rad, c->L.lg_4, c->L.lg_6, c->L.dgf, c->L.dg6,
                     c->d_line_off, c->d_fitems, c->d_nitems_f, c->d_nitems_b, c->d_ctr, c->d_knear, c->d_kline,
                     c->d_F, c->d_Fc, c->d_g, c->d_gc, c->d_tap0, c->d_ntap, c->d_tapw, c->d_dFbar, c->d_Gt,
-                    c->d_Gt64, c->d_gacc, c->d_gline, c->d_gab, c->d_dLdf};
+                    c->d_Gt64, c->d_gacc, c->d_gline, c->d_gab, c->d_dLdf, c->d_ftab, c->d_finfo, c->d_status};
     for (void *p : ptrs) dfree(p);
     for (auto &m : c->marks) {
         cudaEventDestroy(m.a);
@@ -270,6 +270,8 @@ static pz_status check_atmos(const pz_atmos *at, const pz_atmos *ref, const char
         if (!finite_pos(at->kappa_c[k])) return fail(PZ_EINVAL, w + ": kappa_c must be finite and > 0");
     return PZ_OK;
 }
+
+static pz_status ensure_far_tables(pz_ctx *c);
 
 static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, const int64_t *sub_off,
                              const int32_t *sub_idx, pz_precision prec, pz_ctx **out, const char *who) {
@@ -462,11 +464,13 @@ static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, 
     if (cuda_check(cudaMalloc(&c->d_kline, ksz * SD * c->ld), "kappa_line buffer") ||
         (prec == PZ_MIXED && dalloc(&c->d_knear, SD * c->ld, "kappa_line buffer")) ||
         dalloc(&c->d_F, (size_t)S * nlam, "flux") || dalloc(&c->d_Fc, (size_t)S * nlam, "flux") ||
-        dalloc(&c->d_ctr, 4, "work counters"))
+        dalloc(&c->d_ctr, 4, "work counters") || dalloc(&c->d_status, 1, "status word"))
         return bail(PZ_ENOMEM);
+    if (cuda_check(cudaMemset(c->d_status, 0, sizeof(int32_t)), "status word")) return bail(PZ_ECUDA);
     if (prec == PZ_MIXED && cuda_check(cudaMemset(c->d_knear, 0, sizeof(float) * SD * c->ld), "kappa_line buffer"))
         return bail(PZ_ECUDA);
     if (build_items(c) != PZ_OK) return bail(PZ_ENOMEM);
+    if (prec == PZ_MIXED && ensure_far_tables(c) != PZ_OK) return bail(PZ_ENOMEM);
     if (cuda_check(cudaDeviceSynchronize(), who)) return bail(PZ_ECUDA);
     *out = c;
     return PZ_OK;
@@ -498,6 +502,33 @@ static pz_status ensure_backward_buffers(pz_ctx *c) {
     return PZ_OK;
 }
 
+// Far-wing prefactor table and line records for the current tiling (mixed form).
+// Allocated here, outside any stream capture, and grown only when a tiling needs more.
+static pz_status ensure_far_tables(pz_ctx *c) {
+    const size_t tb = far_table_bytes(c), ib = far_info_bytes(c);
+    if (c->ftab_cap < tb) {
+        dfree(c->d_ftab);
+        c->d_ftab = nullptr;
+        c->ftab_cap = 0;
+        if (cudaMalloc(&c->d_ftab, tb) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PZ_ENOMEM, "far-wing table: cudaMalloc failed");
+        }
+        c->ftab_cap = tb;
+    }
+    if (c->finfo_cap < ib) {
+        dfree(c->d_finfo);
+        c->d_finfo = nullptr;
+        c->finfo_cap = 0;
+        if (cudaMalloc(&c->d_finfo, ib) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PZ_ENOMEM, "far-wing line records: cudaMalloc failed");
+        }
+        c->finfo_cap = ib;
+    }
+    return PZ_OK;
+}
+
 // Validate a tiling and make it current: thresholds and work items are rebuilt and
 // the captured calibration graph is dropped.
 static pz_status apply_tiling(pz_ctx *c, const Tiling &t, const char *who) {
@@ -511,6 +542,7 @@ static pz_status apply_tiling(pz_ctx *c, const Tiling &t, const char *who) {
     c->tiling = t;
     PZ_TRY(build_thresholds(c));
     PZ_TRY(build_items(c));
+    if (c->prec == PZ_MIXED) PZ_TRY(ensure_far_tables(c));
     return PZ_OK;
 }
 
@@ -588,7 +620,7 @@ pz_status pz_set_tiling(pz_ctx *c, int32_t J, int32_t DS, int32_t GW, int32_t LC
     if (GW > 0) t.GW = GW;
     if (LC > 0) t.LC = LC;
     if (MINB > 0) t.minb = MINB;
-    if (LC > 0) t.LCB = std::max(1, t.LC / 2);
+    if (LC > 0) t.LCB = t.LC;
     return apply_tiling(c, t, "pz_set_tiling");
 }
 
@@ -677,7 +709,7 @@ pz_status pz_autotune(pz_ctx *c, int32_t with_backward, int32_t reps, int32_t *b
             if (lc != base.LC && st == PZ_OK) {
                 Tiling t = base;
                 t.LC = lc;
-                t.LCB = std::max(1, lc / 2);
+                t.LCB = lc;
                 st = consider(t);
             }
     }
@@ -1018,6 +1050,40 @@ pz_status pz_probe_voigt(const float *a, const float *v, int64_t n, float *H, fl
     if (n < 0 || (n > 0 && (!a || !v || !H))) return fail(PZ_EINVAL, "pz_probe_voigt: bad arguments");
     PZ_TRY(ensure_device_tables());
     PZ_CUDA(launch_probe_voigt(a, v, n, H, dH, (cudaStream_t)stream), "probe voigt");
+    return PZ_OK;
+}
+
+pz_status pz_sync_status(pz_ctx *c, void *stream, int32_t *flags) {
+    if (!c) return fail(PZ_EINVAL, "pz_sync_status: ctx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t h = 0;
+    PZ_CUDA(cudaMemcpyAsync(&h, c->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "pz_sync_status");
+    PZ_CUDA(cudaStreamSynchronize(s), "pz_sync_status");
+    if (flags) *flags = h;
+    if (h != 0) {
+        PZ_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), s), "pz_sync_status");
+        PZ_CUDA(cudaStreamSynchronize(s), "pz_sync_status");
+        return fail(PZ_ETIMEOUT, "pz_sync_status: a far-wing line kernel gave up waiting for a staged chunk "
+                                 "(its outputs are incomplete)");
+    }
+    return PZ_OK;
+}
+
+pz_status pz_probe_wait(int64_t limit_ns, int32_t *flags, void *stream) {
+    if (limit_ns < 1 || limit_ns > 1000000000) return fail(PZ_EINVAL, "pz_probe_wait: limit_ns must be in [1, 1e9]");
+    if (!flags) return fail(PZ_EINVAL, "pz_probe_wait: flags is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t *d = nullptr;
+    PZ_TRY(dalloc(&d, 1, "pz_probe_wait"));
+    pz_status st = PZ_OK;
+    int32_t h = 0;
+    if ((st = cuda_check(cudaMemsetAsync(d, 0, sizeof(int32_t), s), "pz_probe_wait")) == PZ_OK &&
+        (st = cuda_check(launch_probe_wait((uint64_t)limit_ns, d, s), "pz_probe_wait")) == PZ_OK &&
+        (st = cuda_check(cudaMemcpyAsync(&h, d, sizeof(int32_t), cudaMemcpyDeviceToHost, s), "pz_probe_wait")) == PZ_OK)
+        st = cuda_check(cudaStreamSynchronize(s), "pz_probe_wait");
+    dfree(d);
+    if (st != PZ_OK) return st;
+    *flags = h;
     return PZ_OK;
 }
 

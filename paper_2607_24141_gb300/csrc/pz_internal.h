@@ -46,7 +46,7 @@ struct Tiling {
     int J = 4;       // lambda points per thread (contiguous)
     int DS = 6;      // depths per warp (even: the far-wing kernels work on depth pairs)
     int GW = 4;      // warps per CTA (each a depth slab)
-    int LC = 64;     // lines per shared-memory chunk (forward)
+    int LC = 32;     // lines per shared-memory chunk (forward)
     int LCB = 32;    // lines per shared-memory chunk (backward)
     int minb = 4;    // minimum resident CTAs per SM the kernels are compiled for
     int lambda_per_tile() const { return 32 * J; }
@@ -164,6 +164,10 @@ struct pz_ctx {
     // state
     bool have_kline = false, have_flux = false, have_inst = false;
     bool have_gt = false;                // G (dL/dkappa_line) holds a reverse pass
+    void *d_ftab = nullptr;              // far-wing prefactor table (sized for the backward's layout)
+    void *d_finfo = nullptr;             // far-wing line records
+    size_t ftab_cap = 0, finfo_cap = 0;  // their sizes in bytes
+    int32_t *d_status = nullptr;         // device status word (bounded-wait failures), read by pz_sync_status
     int32_t launches = 0;
     pz::StepGraph graph;
     cudaStream_t cap_stream = nullptr;   // private stream the step graph is captured on
@@ -217,7 +221,10 @@ cudaError_t launch_update(pz_ctx *c, float lr_gf, float lr_g6, float lr_ab, cuda
 cudaError_t launch_probe_expn(const double *x, int64_t n, double *out, cudaStream_t s);
 constexpr int kProbeThreads = 256;   // threads per CTA of the pipe-throughput probe
 cudaError_t launch_probe_pipe(int kind, int iters, int blocks, float *out, cudaStream_t s);
+cudaError_t launch_probe_wait(uint64_t limit_ns, int32_t *status, cudaStream_t s);
 bool tiling_supported(int J, int DS, int minb);
 bool tiling_fits(const Tiling &t);   // both far-wing chunks fit in shared memory
+size_t far_table_bytes(const pz_ctx *c);   // far-wing table bytes for the current tiling
+size_t far_info_bytes(const pz_ctx *c);
 
 }  // namespace pz

@@ -26,6 +26,7 @@
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "pz_internal.h"
@@ -127,6 +128,8 @@ pz_status ensure_device_tables() {
 // Mixed-precision kernels
 // ---------------------------------------------------------------------------
 
+struct LineInfo;
+
 // Kernel arguments.  Line arrays are indexed by absolute line; the per-star tables
 // and buffers point at star 0 and are advanced by star_view().
 struct LineArgs {
@@ -149,6 +152,10 @@ struct LineArgs {
     int *ctr;
     int64_t sstride, dstride, bstride, tstride;     // per-star strides of the tables above
     float rj[4], rm1j[4];                           // r^-j and r^-j - 1, j = 0..3 (r = 1 + 1/R)
+    const int32_t *star;                            // [nl] star of each line
+    const float4 *ftab;                             // far-wing prefactor table (k_far_table)
+    const LineInfo *finfo;                          // far-wing line records
+    int *status;                                    // device status word (bounded-wait failures)
 };
 
 __device__ __forceinline__ LineArgs star_view(const LineArgs &g, int s) {
@@ -167,7 +174,8 @@ __device__ __forceinline__ LineArgs star_view(const LineArgs &g, int s) {
     return v;
 }
 
-// Persistent work loop: every CTA takes the next item of the queue until it is empty.
+// Persistent work loop: every CTA takes the next item of the queue until it is empty
+// (or until f, if it returns a flag, returns false -- uniformly over the CTA).
 template <class F>
 __device__ __forceinline__ void for_each_item(const LineArgs &g, F &&f) {
     __shared__ int s_it;
@@ -178,7 +186,12 @@ __device__ __forceinline__ void for_each_item(const LineArgs &g, F &&f) {
         __syncthreads();
         if (it >= g.n_items) break;
         const int4 item = g.items[it];
-        f(star_view(g, item.x), item.y / g.ngroups, item.y % g.ngroups, item.z, item.w);
+        using R = decltype(f(star_view(g, item.x), 0, 0, 0, 0));
+        if constexpr (std::is_same<R, bool>::value) {
+            if (!f(star_view(g, item.x), item.y / g.ngroups, item.y % g.ngroups, item.z, item.w)) break;
+        } else {
+            f(star_view(g, item.x), item.y / g.ngroups, item.y % g.ngroups, item.z, item.w);
+        }
     }
 }
 
@@ -253,45 +266,18 @@ __device__ __forceinline__ void line_params(const LineArgs &g, int64_t l, int d,
     depth_params<NP>(g, load_line(g, l), d, out);
 }
 
-// Shared-memory stride of one staged line, in 16-byte quads: DC/2 depth pairs of NQ
-// quads each, padded to an odd count so that the float4 stores of threads staging
-// consecutive lines (same depth pair) fall in distinct banks.
-__host__ __device__ constexpr int line_quads(int DC, int NQ) {
-    return (DC / 2) * NQ + ((((DC / 2) * NQ) & 1) ? 2 : 1);
-}
-
 // index-space frequency offset u = lambda_l/lambda_i - 1 = expm1(Delta ln r)
 __device__ __forceinline__ float offset_u(float delta, float lnr) {
     float y = delta * lnr;
     return fmaf(y * y, fmaf(y, 0.16666667f, 0.5f), y);
 }
 
+// Line record of the far-wing tables: centre, species and the per-slab reduced-form
+// mask of the line's depth group.
 struct alignas(16) LineInfo {
     float ilf, frac;
-    int sp, pad;
+    int sp, amask;
 };
-
-// Far-wing term A H for one evaluation from the pre-scaled coefficients
-// p0 = (k, a^2, B1, B2), p1 = (B3, B4, B5, A): t (B1 + t (B2 + t (B3 + t (B4 + t B5)))),
-// added to acc (7 FP32-pipe instructions + 1 MUFU with the caller's x = u k).
-__device__ __forceinline__ float far_acc(float x, const float4 &p0, const float4 &p1, float acc) {
-    float t = rcp_approx(fmaf(x, x, p0.y));
-    float h = fmaf(t, p1.z, p1.y);
-    h = fmaf(t, h, p1.x);
-    h = fmaf(t, h, p0.w);
-    h = fmaf(t, h, p0.z);
-    return fmaf(t, h, acc);
-}
-
-// Per-warp decision: the line is inside its window over the whole tile and every
-// (lambda, depth) cell of this warp's depth slab is in the far wing (|v| >= 20).
-__device__ __forceinline__ bool fast_line(const LineArgs &g, const LineInfo &info, float t0f, float tendf, int slab) {
-    const float dlo = info.ilf - t0f + info.frac;      // x_l - t0
-    const float dhi = info.ilf - tendf + info.frac;    // x_l - (t0 + T - 1)
-    const float dmin = fmaxf(0.0f, fmaxf(-dlo, dhi));
-    const bool full = (info.ilf - (float)g.W <= t0f) && (info.ilf + (float)g.W >= tendf);
-    return full && dmin >= __ldg(g.thr + info.sp * g.nslab + slab);
-}
 
 // ---- packed FP32 pairs ------------------------------------------------------
 // The far-wing kernels evaluate two depths of one (line, lambda) cell with one
@@ -326,18 +312,21 @@ __device__ __forceinline__ f2_t f2_rcp(f2_t a) {
         : "=l"(r) : "l"(a));
     return r;
 }
+__device__ __forceinline__ f2_t f2_splat(float v) { return f2_pack(v, v); }
 
-// Shared-memory layout of the per-(line, depth) prefactors for the packed kernels:
-// per line, line_quads(DC, NQ) quads; per depth pair, NQ quads, quad q holding
-// {p_2q(d), p_2q(d + 1), p_2q+1(d), p_2q+1(d + 1)}, so one 16-byte load returns the
-// packed depth pairs of two parameters.
-//   forward  (NQ = 4): (k, a^2) (B1, B2) (B3, B4) (B5, A)
-//   backward (NQ = 7): (k, a^2) (B1, B2) (C1, C2) (B3, B4) (B5, C3) (C4, C5) (C6, -)
-
-// Compensated-sum slots of depth dd of thread tid: the (hi, lo) pairs of its J points,
-// hi at [0, 4) and lo at [4, 8) (the J points of a thread are contiguous: one vector
-// access each).  They live in shared memory and are touched once per line chunk.
-__device__ __forceinline__ int comp_slot(int dd, int tid, int nthr) { return (dd * nthr + tid) << 3; }
+// ---- far-wing prefactor tables ----------------------------------------------
+// Before each far-wing launch k_far_table writes, for every depth group g of DC
+// layers and every line l, the (DC/2) depth pairs of NQ quads, quad q holding
+// {p_2q(d), p_2q(d + 1), p_2q+1(d), p_2q+1(d + 1)} (one 16-byte load returns the
+// packed depth pairs of two parameters):
+//   forward  (NQ = 2): (k, a^2) (B1, B2)
+//   backward (NQ = 3): (k, a^2) (B1, B2) (C1, C2)
+// at tab[(g n_lines + l) (DC/2) NQ + pair NQ + q], and the line record at
+// info[g n_lines + l].  The rest of the far polynomial (B3..B5, C3..C6) follows
+// from a^2, B1 and C1 in registers.  The chunk of LC lines a CTA needs is then
+// one contiguous block, which the kernels move into shared memory with bulk
+// copies (cp.async.bulk, completion on an mbarrier), double-buffered.
+constexpr int kNQF = 2, kNQB = 3;
 
 // Reduced far-wing form.  Far from the core the polynomial in t = 1/|z|^2 is cut
 // after its t^2 term: H sqrt(pi)/(A a) = t (1 + 1.5 t) and, for dH/da, C1 t (1 +
@@ -347,65 +336,192 @@ __device__ __forceinline__ int comp_slot(int dd, int tid, int nthr) { return (dd
 constexpr float kFast2V = 5.0f;      // distance threshold factor: |v| >= 5 x 20
 constexpr float kFast2A2 = 1.5f;     // a^2 bound
 
-// Per-warp fast-path flags of staged line l: bit w set if the line is entirely inside
-// its window over the tile and in the far wing (|v| >= 20) at every depth of warp w's
-// slab; bit 8 + w if, in addition, |v| >= 100 and a^2 <= kFast2A2 at every depth of
-// the slab (reduced form).
-__device__ __forceinline__ int fast_mask(const LineArgs &g, int64_t l, const LineInfo &info, float t0f, float tendf,
-                                         int d0, int DS, int GW) {
-    const float dlo = info.ilf - t0f + info.frac;
-    const float dhi = info.ilf - tendf + info.frac;
+// One thread per (group, line, depth pair); the thread of pair 0 also writes the
+// line record, whose amask has bit w set when a^2 <= kFast2A2 at every layer of
+// slab w (DS layers) of the group.
+template <int NQ>
+__global__ void k_far_table(LineArgs gq, int DC, int DS, int ngroups, float4 *tab, LineInfo *info) {
+    const int P = DC / 2;
+    const int64_t n = (int64_t)ngroups * gq.nl * P;
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int pr = (int)(idx % P);
+        const int64_t gl = idx / P;
+        const int64_t l = gl % gq.nl;
+        const int grp = (int)(gl / gq.nl);
+        const LineArgs g = star_view(gq, gq.star[l]);
+        const LineScalars L = load_line(g, l);
+        const int d = grp * DC + 2 * pr;
+        float p0[16], p1[16];
+        depth_params<NQ == kNQB ? 16 : 8>(g, L, d, p0);
+        depth_params<NQ == kNQB ? 16 : 8>(g, L, d + 1, p1);
+        float4 *dst = tab + gl * (P * NQ) + pr * NQ;
+        dst[0] = make_float4(p0[0], p1[0], p0[1], p1[1]);
+        dst[1] = make_float4(p0[2], p1[2], p0[3], p1[3]);
+        if (NQ == kNQB) dst[2] = make_float4(p0[8], p1[8], p0[9], p1[9]);
+        if (pr == 0) {
+            int amask = 0;
+            for (int w = 0; w < DC / DS; ++w) {
+                bool ok = true;
+                for (int dd = grp * DC + w * DS; dd < min(grp * DC + (w + 1) * DS, g.nd); ++dd) {
+                    float q[16];
+                    depth_params<8>(g, L, dd, q);
+                    ok = ok && q[1] <= kFast2A2;
+                }
+                amask |= ok ? 1 << w : 0;
+            }
+            LineInfo r;
+            r.ilf = g.ilf[l];
+            r.frac = g.frac[l];
+            r.sp = L.sp;
+            r.amask = amask;
+            info[gl] = r;
+        }
+    }
+}
+
+// ---- bulk-copy staging ------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for phase `parity` of the barrier to complete; false after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64_t limit_ns) {
+    if (mbar_test(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_test(bar, parity)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// One thread: copy a chunk (its quads, then its line records) into shared memory,
+// completing on `bar`.  The proxy fence orders the generic-proxy reads of the previous
+// use of the buffer (made visible by the CTA barrier the caller passed) before the
+// asynchronous writes.
+__device__ __forceinline__ void issue_chunk(uint64_t *bar, float4 *dst_par, const float4 *src_par, uint32_t par_bytes,
+                                            float4 *dst_info, const void *src_info, uint32_t info_bytes) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(par_bytes + info_bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst_par)),
+                 "l"(src_par), "r"(par_bytes), "r"(smem_addr(bar))
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst_info)),
+                 "l"(src_info), "r"(info_bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+// Double-buffered chunk pipeline of one CTA.  Buffer b holds [LC][PQ] quads followed
+// by [LC] line records.  cc counts the chunks the CTA has consumed (every thread keeps
+// the same count): chunk number cc uses buffer cc & 1 and phase (cc >> 1) & 1 of that
+// buffer's barrier.
+struct ChunkPipe {
+    uint64_t *bar;       // [2]
+    float4 *buf;         // 2 x LC x (PQ + 1) quads
+    int LC, PQ;
+    unsigned cc;
+    __device__ float4 *par(unsigned k) const { return buf + (size_t)(k & 1) * LC * (PQ + 1); }
+    __device__ const LineInfo *info(unsigned k) const {
+        return reinterpret_cast<const LineInfo *>(par(k) + (size_t)LC * PQ);
+    }
+    __device__ void issue(unsigned k, const float4 *tab, const LineInfo *linfo, int64_t first, int n) const {
+        issue_chunk(bar + (k & 1), par(k), tab + first * PQ, (uint32_t)(n * PQ * 16), par(k) + (size_t)LC * PQ,
+                    linfo + first, (uint32_t)(n * 16));
+    }
+};
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // bounded waits give up after 1 s
+constexpr int kStatusFarWait = 1;                   // status bit: a far-wing chunk never arrived
+
+// Give up after a timed-out wait: record it, let the CTA's copies in flight land
+// (bounded again) and tell the caller to stop.
+__device__ __forceinline__ void far_abort(const LineArgs &g, const ChunkPipe &cp, unsigned k) {
+    if (threadIdx.x == 0) {
+        atomicOr(g.status, kStatusFarWait);
+        mbar_wait(cp.bar + (k & 1), (k >> 1) & 1, kWaitLimitNs);
+    }
+    __syncthreads();
+}
+
+// Per-warp flags of a line over the tile: bit 0 if the line's window covers the tile
+// and every cell of the warp's slab is in the far wing (|v| >= 20); bit 1 if, in
+// addition, |v| >= 100 and a^2 <= kFast2A2 at every layer of the slab (reduced form).
+__device__ __forceinline__ int far_flags(const LineArgs &g, const LineInfo &info, float t0f, float tendf, int slab,
+                                         int w) {
+    const float dlo = info.ilf - t0f + info.frac;      // x_l - t0
+    const float dhi = info.ilf - tendf + info.frac;    // x_l - (t0 + T - 1)
     const float dmin = fmaxf(0.0f, fmaxf(-dlo, dhi));
     const bool full = (info.ilf - (float)g.W <= t0f) && (info.ilf + (float)g.W >= tendf);
-    if (!full) return 0;
-    int m = 0;
-    for (int w = 0; w < GW; ++w) {
-        const int slab = (d0 + w * DS) / DS;
-        const float thr = __ldg(g.thr + info.sp * g.nslab + slab);
-        if (!(dmin >= thr)) continue;
-        m |= 1 << w;
-        if (!(dmin >= kFast2V * thr)) continue;
-        const float lw = g.lamcm[l] * (float)(1.0 / (4.0 * kPI));
-        const float g4 = g.g4[l], grad = g.grad[l], g6 = g.g6[l];
-        bool ok = true;
-        for (int d = d0 + w * DS; d < min(d0 + (w + 1) * DS, g.nd); ++d) {
-            const float a = fmaf(g4, __ldg(g.ne + d), grad + g6 * __ldg(g.npert + d)) * lw *
-                            __ldg(g.invdv + info.sp * g.nd + d);
-            ok = ok && a * a <= kFast2A2;
-        }
-        if (ok) m |= 1 << (8 + w);
-    }
-    return m;
+    const float thr = __ldg(g.thr + info.sp * g.nslab + slab);
+    const bool fast = full && dmin >= thr;
+    const bool red = fast && dmin >= kFast2V * thr && ((info.amask >> w) & 1);
+    return (fast ? 1 : 0) | (red ? 2 : 0);
+}
+
+// Compensated-sum slots of depth dd of thread tid: the (hi, lo) pairs of its J points,
+// hi at [0, 4) and lo at [4, 8) (the J points of a thread are contiguous: one vector
+// access each).  They live in shared memory and are touched once per line chunk.
+__device__ __forceinline__ int comp_slot(int dd, int tid, int nthr) { return (dd * nthr + tid) << 3; }
+
+// Higher far-wing coefficients from a^2 and B1 (as depth_params forms them):
+// B3 = (3.75 - 2a^2) B1, B4 = -15 a^2 B1, B5 = 12 a^4 B1.
+__device__ __forceinline__ void far_b345(f2_t a2, f2_t B1, f2_t &B3, f2_t &B4, f2_t &B5) {
+    B3 = f2_mul(f2_fma(a2, f2_splat(-2.0f), f2_splat(3.75f)), B1);
+    B4 = f2_mul(f2_mul(a2, f2_splat(-15.0f)), B1);
+    B5 = f2_mul(f2_mul(f2_mul(a2, f2_splat(12.0f)), a2), B1);
+}
+// C3 = (3.75 - 12 a^2) C1, C4 = a^2 (12 a^2 - 67.5) C1, C5 = 180 a^4 C1, C6 = -120 a^6 C1.
+__device__ __forceinline__ void far_c3456(f2_t a2, f2_t C1, f2_t &C3, f2_t &C4, f2_t &C5, f2_t &C6) {
+    C3 = f2_mul(f2_fma(a2, f2_splat(-12.0f), f2_splat(3.75f)), C1);
+    C4 = f2_mul(f2_mul(a2, f2_fma(a2, f2_splat(12.0f), f2_splat(-67.5f))), C1);
+    const f2_t a4 = f2_mul(a2, a2);
+    C5 = f2_mul(f2_mul(a4, f2_splat(180.0f)), C1);
+    C6 = f2_mul(f2_mul(f2_mul(a4, f2_splat(-120.0f)), a2), C1);
 }
 
 // Far-wing kernel (forward).  Every cell with |v|^2 + a^2 >= 400 inside its window is
 // evaluated here with the far polynomial; the near-core cells are summed by
 // k_line_near_fwd into knear, which this kernel adds before applying stim.
+// Returns false if a chunk never arrived (the kernel stops).
 template <int J, int DS>
-__device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, const int group, const int lo,
-                                             const int hi, const int GW, const int LC) {
+__device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, const int group, const int lo,
+                                             const int hi, const int GW, ChunkPipe &cp) {
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
     static_assert(DS % 2 == 0, "DS must be even (depth pairs)");
     constexpr int DP = DS / 2;          // depth pairs per warp
-    constexpr int NQ = 4;               // quads per (line, depth pair) in shared memory
-    extern __shared__ float4 smem4[];
+    constexpr int NQ = kNQF;
     const int T = 32 * J;
     const int DC = GW * DS;
-    const int LQ = line_quads(DC, NQ);
     const int nthr = blockDim.x;
-    const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(smem4);   // [LC][LQ] quads
-    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * LQ);
-    float *s_comp = reinterpret_cast<float *>(s_line + LC);             // [DS][nthr][8] compensated sums
-    // offsets of the thread's other points from the first: u_j = u_0 r^-j + (r^-j - 1)
-    f2_t rj2[J], rm2[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-        rj2[j] = f2_pack(g.rj[j], g.rj[j]);
-        rm2[j] = f2_pack(g.rm1j[j], g.rm1j[j]);
-    }
+    float *s_comp = reinterpret_cast<float *>(cp.buf + (size_t)2 * cp.LC * (cp.PQ + 1));   // [DS][nthr][8]
+    const float4 *gtab = g.ftab + (int64_t)group * g.nl * cp.PQ;
+    const LineInfo *ginfo = g.finfo + (int64_t)group * g.nl;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int d0 = group * DC;
+    const int slab = group * GW + warp;
     const int t0 = tile * T;
     const float t0f = (float)t0, tendf = (float)(t0 + T - 1);
     const int lam_thr = t0 + lane * J;
@@ -423,55 +539,45 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
         cs[1] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
-    for (int c0 = lo; c0 < hi; c0 += LC) {
-        const int nl = min(LC, hi - c0);
-        __syncthreads();
-        // stage the prefactors: a thread takes one line and depth pair (consecutive
-        // threads, consecutive lines) and writes the pair's quads
-        for (int idx = tid; idx < nl * (DC / 2); idx += nthr) {
-            const int pr = idx / nl, li = idx - pr * nl;
-            const LineScalars L = load_line(g, c0 + li);
-            float p0[8], p1[8];
-            depth_params<8>(g, L, d0 + 2 * pr, p0);
-            depth_params<8>(g, L, d0 + 2 * pr + 1, p1);
-            float4 *dst = smem4 + (size_t)li * LQ + pr * NQ;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) dst[q] = make_float4(p0[2 * q], p1[2 * q], p0[2 * q + 1], p1[2 * q + 1]);
+    const int nch = (hi - lo + cp.LC - 1) / cp.LC;
+    if (tid == 0 && nch > 0) cp.issue(cp.cc, gtab, ginfo, lo, min(cp.LC, hi - lo));
+    for (int c = 0; c < nch; ++c) {
+        const unsigned k = cp.cc + c;
+        const bool ok = mbar_wait(cp.bar + (k & 1), (k >> 1) & 1, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            far_abort(g, cp, k);
+            return false;
         }
-        for (int li = tid; li < nl; li += nthr) {
-            int64_t l = c0 + li;
-            LineInfo info;
-            info.ilf = g.ilf[l];
-            info.frac = g.frac[l];
-            info.sp = g.sp[l];
-            info.pad = fast_mask(g, l, info, t0f, tendf, d0, DS, GW);
-            s_line[li] = info;
+        // the other buffer is free (every thread is past its chunk): prefetch the next chunk
+        if (tid == 0 && c + 1 < nch) {
+            const int n1 = lo + (c + 1) * cp.LC;
+            cp.issue(k + 1, gtab, ginfo, n1, min(cp.LC, hi - n1));
         }
-        __syncthreads();
-
+        const int nl = min(cp.LC, hi - (lo + c * cp.LC));
+        const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
+        const LineInfo *s_line = cp.info(k);
         for (int li = 0; li < nl; ++li) {
             const LineInfo info = s_line[li];
-            const ulonglong2 *par = s_par + (size_t)li * LQ + warp * DP * NQ;
+            const int fl = far_flags(g, info, t0f, tendf, slab, warp);
+            const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
             f2_t u2[J];
-            if ((info.pad >> warp) & 1) {
-                // the whole tile is in the line's far wing: offsets from the first point's
+            if (fl & 1) {
+                // the whole tile is in the line's far wing: offsets from the first point's,
+                // u_j = u_0 r^-j + (r^-j - 1)
                 const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
-                u2[0] = f2_pack(u0, u0);
+                u2[0] = f2_splat(u0);
 #pragma unroll
-                for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], rj2[j], rm2[j]);
+                for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j]));
             } else {
                 // cells are classified near / far exactly as the near-core kernel does
 #pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    const float u = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
-                    u2[j] = f2_pack(u, u);
-                }
+                for (int j = 0; j < J; ++j) u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
             }
-            if ((info.pad >> (8 + warp)) & 1) {
+            if (fl & 2) {
                 // reduced form: t (B1 + B2 t)
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
-                    const ulonglong2 q0 = par[4 * dp], q1 = par[4 * dp + 1];
+                    const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const f2_t x = f2_mul(u2[j], q0.x);
@@ -479,18 +585,19 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
                         acc[dp][j] = f2_fma(t, f2_fma(t, q1.y, q1.x), acc[dp][j]);
                     }
                 }
-            } else if ((info.pad >> warp) & 1) {
+            } else if (fl & 1) {
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
-                    const ulonglong2 q0 = par[4 * dp], q1 = par[4 * dp + 1], q2 = par[4 * dp + 2];
-                    const ulonglong2 q3 = par[4 * dp + 3];
-                    // q0 = (k, a^2), q1 = (B1, B2), q2 = (B3, B4), q3 = (B5, A)
+                    // q0 = (k, a^2), q1 = (B1, B2)
+                    const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
+                    f2_t B3, B4, B5;
+                    far_b345(q0.y, q1.x, B3, B4, B5);
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const f2_t x = f2_mul(u2[j], q0.x);
                         const f2_t t = f2_rcp(f2_fma(x, x, q0.y));
-                        f2_t h = f2_fma(t, q3.x, q2.y);
-                        h = f2_fma(t, h, q2.x);
+                        f2_t h = f2_fma(t, B5, B4);
+                        h = f2_fma(t, h, B3);
                         h = f2_fma(t, h, q1.y);
                         h = f2_fma(t, h, q1.x);
                         acc[dp][j] = f2_fma(t, h, acc[dp][j]);
@@ -507,15 +614,16 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
                 }
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
-                    const ulonglong2 q0 = par[4 * dp], q1 = par[4 * dp + 1], q2 = par[4 * dp + 2];
-                    const ulonglong2 q3 = par[4 * dp + 3];
+                    const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
+                    f2_t B3, B4, B5;
+                    far_b345(q0.y, q1.x, B3, B4, B5);
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const f2_t x = f2_mul(u2[j], q0.x);
                         const f2_t r2 = f2_fma(x, x, q0.y);
                         const f2_t t = f2_rcp(r2);
-                        f2_t h = f2_fma(t, q3.x, q2.y);
-                        h = f2_fma(t, h, q2.x);
+                        f2_t h = f2_fma(t, B5, B4);
+                        h = f2_fma(t, h, B3);
                         h = f2_fma(t, h, q1.y);
                         h = f2_fma(t, h, q1.x);
                         const f2_t r = f2_fma(t, h, acc[dp][j]);
@@ -561,6 +669,7 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
             }
         }
     }
+    cp.cc += nch;
 
     // epilogue: near-core sums, stimulated-emission factor at the sample frequency, vector store
 #pragma unroll
@@ -590,23 +699,38 @@ __device__ __forceinline__ void far_fwd_item(const LineArgs &g, const int tile, 
         else
             *reinterpret_cast<float2 *>(row) = make_float2(v[0], v[1 % J]);
     }
+    return true;
+}
+
+// Barriers of the chunk pipeline: initialised once per CTA, visible to the async proxy.
+__device__ __forceinline__ void pipe_init(uint64_t *bars) {
+    if (threadIdx.x == 0) {
+        mbar_init(bars);
+        mbar_init(bars + 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 }
 
 template <int J, int DS, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int LC) {
+    extern __shared__ float4 smem4[];
+    __shared__ uint64_t bars[2];
+    pipe_init(bars);
+    ChunkPipe cp{bars, smem4, LC, GW * DS / 2 * kNQF, 0u};
     for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi) {
-        far_fwd_item<J, DS>(v, tile, group, lo, hi, GW, LC);
+        return far_fwd_item<J, DS>(v, tile, group, lo, hi, GW, cp);
     });
 }
 
 // Reduced far-wing backward form (lines flagged for it): H and dH/da polynomials cut
-// after their t^2 terms.
+// after their t^2 terms.  par: the warp's depth pairs, (k, a^2) (B1, B2) (C1, C2).
 template <int J, int DP>
 __device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, const f2_t (&u2)[J],
                                                      const f2_t (&gv)[DP][J], f2_t &S1, f2_t &S2) {
 #pragma unroll
     for (int dp = 0; dp < DP; ++dp) {
-        const ulonglong2 q0 = par[7 * dp], q1 = par[7 * dp + 1], q2 = par[7 * dp + 2];
+        const ulonglong2 q0 = par[kNQB * dp], q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
             const f2_t x = f2_mul(u2[j], q0.x);
@@ -626,22 +750,23 @@ __device__ __forceinline__ void far_bwd_line(const ulonglong2 *par, const f2_t (
                                              const bool *inwin, f2_t &S1, f2_t &S2) {
 #pragma unroll
     for (int dp = 0; dp < DP; ++dp) {
-        // (k, a^2) (B1, B2) (C1, C2) (B3, B4) (B5, C3) (C4, C5) (C6, -)
-        const ulonglong2 q0 = par[7 * dp], q1 = par[7 * dp + 1], q2 = par[7 * dp + 2];
-        const ulonglong2 q3 = par[7 * dp + 3], q4 = par[7 * dp + 4], q5 = par[7 * dp + 5];
-        const ulonglong2 q6 = par[7 * dp + 6];
+        // (k, a^2) (B1, B2) (C1, C2); the higher coefficients from a^2, B1 and C1
+        const ulonglong2 q0 = par[kNQB * dp], q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
+        f2_t B3, B4, B5, C3, C4, C5, C6;
+        far_b345(q0.y, q1.x, B3, B4, B5);
+        far_c3456(q0.y, q2.x, C3, C4, C5, C6);
 #pragma unroll
         for (int j = 0; j < J; ++j) {
             const f2_t x = f2_mul(u2[j], q0.x);
             const f2_t r2 = f2_fma(x, x, q0.y);
             const f2_t t = f2_rcp(r2);
-            f2_t h = f2_fma(t, q4.x, q3.y);
-            h = f2_fma(t, h, q3.x);
+            f2_t h = f2_fma(t, B5, B4);
+            h = f2_fma(t, h, B3);
             h = f2_fma(t, h, q1.y);
             h = f2_fma(t, h, q1.x);
-            f2_t q = f2_fma(t, q6.x, q5.y);
-            q = f2_fma(t, q, q5.x);
-            q = f2_fma(t, q, q4.y);
+            f2_t q = f2_fma(t, C6, C5);
+            q = f2_fma(t, q, C4);
+            q = f2_fma(t, q, C3);
             q = f2_fma(t, q, q2.y);
             q = f2_fma(t, q, q2.x);
             f2_t gt = f2_mul(gv[dp][j], t);
@@ -662,29 +787,22 @@ __device__ __forceinline__ void far_bwd_line(const ulonglong2 *par, const f2_t (
 // Far-wing kernel (backward): the per-line sums over the tile's far cells of
 // G stim A H and G stim A a6 dH/da, reduced over the CTA and added to gacc.
 template <int J, int DS>
-__device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, const int group, const int lo,
-                                             const int hi, const int GW, const int LC) {
+__device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, const int group, const int lo,
+                                             const int hi, const int GW, ChunkPipe &cp) {
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
     static_assert(DS % 2 == 0, "DS must be even (depth pairs)");
     constexpr int DP = DS / 2;
-    constexpr int NQ = 7;               // quads per (line, depth pair) in shared memory
-    extern __shared__ float4 smem4[];
+    constexpr int NQ = kNQB;
     const int T = 32 * J;
     const int DC = GW * DS;
-    const int LQ = line_quads(DC, NQ);
     const int nthr = blockDim.x;
-    const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(smem4);   // [LC][LQ] quads
-    LineInfo *s_line = reinterpret_cast<LineInfo *>(smem4 + (size_t)LC * LQ);
-    f2_t rj2[J], rm2[J];
-#pragma unroll
-    for (int j = 0; j < J; ++j) {
-        rj2[j] = f2_pack(g.rj[j], g.rj[j]);
-        rm2[j] = f2_pack(g.rm1j[j], g.rm1j[j]);
-    }
-    float2 *s_red = reinterpret_cast<float2 *>(s_line + LC);            // [LC][GW]
+    float2 *s_red = reinterpret_cast<float2 *>(cp.buf + (size_t)2 * cp.LC * (cp.PQ + 1));   // [LC][GW]
+    const float4 *gtab = g.ftab + (int64_t)group * g.nl * cp.PQ;
+    const LineInfo *ginfo = g.finfo + (int64_t)group * g.nl;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int d0 = group * DC;
+    const int slab = group * GW + warp;
     const int t0 = tile * T;
     const float t0f = (float)t0, tendf = (float)(t0 + T - 1);
     const int lam_thr = t0 + lane * J;
@@ -704,56 +822,41 @@ __device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, 
         }
     }
 
-    for (int c0 = lo; c0 < hi; c0 += LC) {
-        const int nl = min(LC, hi - c0);
-        __syncthreads();
-        for (int idx = tid; idx < nl * (DC / 2); idx += nthr) {
-            const int pr = idx / nl, li = idx - pr * nl;
-            const LineScalars L = load_line(g, c0 + li);
-            float p0[16], p1[16];
-            depth_params<16>(g, L, d0 + 2 * pr, p0);
-            depth_params<16>(g, L, d0 + 2 * pr + 1, p1);
-            // quads (k, a^2) (B1, B2) (C1, C2) (B3, B4) (B5, C3) (C4, C5) (C6, -) of both depths
-            constexpr int src[14] = {0, 1, 2, 3, 8, 9, 4, 5, 6, 10, 11, 12, 13, 13};
-            float4 *dst = smem4 + (size_t)li * LQ + pr * NQ;
-#pragma unroll
-            for (int q = 0; q < NQ; ++q) {
-                const bool pad = 2 * q + 1 == 13;
-                dst[q] = make_float4(p0[src[2 * q]], p1[src[2 * q]], pad ? 0.0f : p0[src[2 * q + 1]],
-                                     pad ? 0.0f : p1[src[2 * q + 1]]);
-            }
+    const int nch = (hi - lo + cp.LC - 1) / cp.LC;
+    if (tid == 0 && nch > 0) cp.issue(cp.cc, gtab, ginfo, lo, min(cp.LC, hi - lo));
+    for (int c = 0; c < nch; ++c) {
+        const unsigned k = cp.cc + c;
+        const int c0 = lo + c * cp.LC;
+        const int nl = min(cp.LC, hi - c0);
+        const bool ok = mbar_wait(cp.bar + (k & 1), (k >> 1) & 1, kWaitLimitNs);
+        if (__syncthreads_or(!ok)) {
+            far_abort(g, cp, k);
+            return false;
         }
-        for (int li = tid; li < nl; li += nthr) {
-            int64_t l = c0 + li;
-            LineInfo info;
-            info.ilf = g.ilf[l];
-            info.frac = g.frac[l];
-            info.sp = g.sp[l];
-            info.pad = fast_mask(g, l, info, t0f, tendf, d0, DS, GW);
-            s_line[li] = info;
+        if (tid == 0 && c + 1 < nch) {
+            const int n1 = c0 + cp.LC;
+            cp.issue(k + 1, gtab, ginfo, n1, min(cp.LC, hi - n1));
         }
-        __syncthreads();
-
+        const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
+        const LineInfo *s_line = cp.info(k);
         for (int li = 0; li < nl; ++li) {
             const LineInfo info = s_line[li];
-            const ulonglong2 *par = s_par + (size_t)li * LQ + warp * DP * NQ;
+            const int fl = far_flags(g, info, t0f, tendf, slab, warp);
+            const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
             f2_t u2[J];
-            if ((info.pad >> warp) & 1) {
+            if (fl & 1) {
                 const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
-                u2[0] = f2_pack(u0, u0);
+                u2[0] = f2_splat(u0);
 #pragma unroll
-                for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], rj2[j], rm2[j]);
+                for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j]));
             } else {
 #pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    const float u = offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr);
-                    u2[j] = f2_pack(u, u);
-                }
+                for (int j = 0; j < J; ++j) u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
             }
             f2_t S1 = 0ull, S2 = 0ull;
-            if ((info.pad >> (8 + warp)) & 1) {
+            if (fl & 2) {
                 far_bwd_line_reduced<J, DP>(par, u2, gv, S1, S2);
-            } else if ((info.pad >> warp) & 1) {
+            } else if (fl & 1) {
                 far_bwd_line<J, DP, false>(par, u2, gv, nullptr, S1, S2);
             } else {
                 // line near the tile or partly outside its window: far cells inside the window only
@@ -789,12 +892,18 @@ __device__ __forceinline__ void far_bwd_item(const LineArgs &g, const int tile, 
             atomicAdd(g.gacc + g.nl + c0 + li, a2);
         }
     }
+    cp.cc += nch;
+    return true;
 }
 
 template <int J, int DS, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int LC) {
+    extern __shared__ float4 smem4[];
+    __shared__ uint64_t bars[2];
+    pipe_init(bars);
+    ChunkPipe cp{bars, smem4, LC, GW * DS / 2 * kNQB, 0u};
     for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi) {
-        far_bwd_item<J, DS>(v, tile, group, lo, hi, GW, LC);
+        return far_bwd_item<J, DS>(v, tile, group, lo, hi, GW, cp);
     });
 }
 
@@ -1067,6 +1176,10 @@ static LineArgs make_args(pz_ctx *c) {
         g.rj[j] = (float)std::exp(-j * c->lnr);
         g.rm1j[j] = (float)std::expm1(-j * c->lnr);
     }
+    g.star = c->L.star;
+    g.ftab = reinterpret_cast<const float4 *>(c->d_ftab);
+    g.finfo = reinterpret_cast<const LineInfo *>(c->d_finfo);
+    g.status = c->d_status;
     g.lam0cm = (float)(c->lambda0_nm * 1e-7);
     g.ilf = c->L.ilf;
     g.frac = c->L.frac;
@@ -1158,16 +1271,41 @@ static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
 // Dynamic shared memory of the far-wing kernels: staged prefactors, line records and
 // (forward) the compensated sums of every thread, or (backward) the per-line sums.
 static size_t far_fwd_smem(const Tiling &t) {
-    return (size_t)t.LC * line_quads(t.depth_per_cta(), 4) * sizeof(float4) + t.LC * sizeof(LineInfo) +
+    return (size_t)2 * t.LC * (t.depth_per_cta() / 2 * kNQF + 1) * sizeof(float4) +
            (size_t)t.DS * 32 * t.GW * 2 * sizeof(float4);
 }
 static size_t far_bwd_smem(const Tiling &t) {
-    return (size_t)t.LCB * line_quads(t.depth_per_cta(), 7) * sizeof(float4) + t.LCB * sizeof(LineInfo) +
-           (size_t)t.LCB * t.GW * sizeof(float2);
+    return (size_t)2 * t.LCB * (t.depth_per_cta() / 2 * kNQB + 1) * sizeof(float4) + (size_t)t.LCB * t.GW * sizeof(float2);
 }
 constexpr size_t kFarSmemMax = 200 * 1024;   // the opt-in size the far-wing kernels are given
 
 bool tiling_fits(const Tiling &t) { return far_fwd_smem(t) <= kFarSmemMax && far_bwd_smem(t) <= kFarSmemMax; }
+
+// Prefactor table of the far-wing kernels for the current tiling (forward NQ = kNQF,
+// backward kNQB), into the context's table buffers (sized by ensure_far_tables).
+template <int NQ>
+static cudaError_t launch_far_table(pz_ctx *c, LineArgs &g, int DS, cudaStream_t s) {
+    const int DC = c->tiling.depth_per_cta();
+    const int64_t n = (int64_t)g.ngroups * c->L.n * (DC / 2);
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->n_sm * 16);
+    g.ftab = reinterpret_cast<const float4 *>(c->d_ftab);
+    g.finfo = reinterpret_cast<const LineInfo *>(c->d_finfo);
+    k_far_table<NQ><<<grid, 256, 0, s>>>(g, DC, DS, g.ngroups, reinterpret_cast<float4 *>(c->d_ftab),
+                                         reinterpret_cast<LineInfo *>(c->d_finfo));
+    c->launches++;
+    return cudaGetLastError();
+}
+
+size_t far_table_bytes(const pz_ctx *c) {
+    const int DC = c->tiling.depth_per_cta();
+    const int ng = (c->nd + DC - 1) / DC;
+    return (size_t)ng * std::max<int64_t>(c->L.n, 1) * (DC / 2) * kNQB * sizeof(float4);
+}
+size_t far_info_bytes(const pz_ctx *c) {
+    const int DC = c->tiling.depth_per_cta();
+    const int ng = (c->nd + DC - 1) / DC;
+    return (size_t)ng * std::max<int64_t>(c->L.n, 1) * sizeof(LineInfo);
+}
 
 template <int J, int DS, int MINB>
 static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
@@ -1187,6 +1325,10 @@ static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
     g.n_items = c->n_fitems;
     g.ngroups = (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta();
     g.ctr = c->d_ctr + 1;
+    if (c->L.n > 0) {
+        e = launch_far_table<kNQF>(c, g, DS, s);
+        if (e != cudaSuccess) return e;
+    }
     int grid = persistent_grid(c, k_line_fwd<J, DS, MINB>, 32 * t.GW, smem, g.n_items);
     k_line_fwd<J, DS, MINB><<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LC);
     c->launches++;
@@ -1211,6 +1353,8 @@ static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
         gb.n_items = c->n_bitems;   // the far items with lines come first
         gb.ngroups = (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta();
         gb.ctr = c->d_ctr + 2;
+        e = launch_far_table<kNQB>(c, gb, DS, s);
+        if (e != cudaSuccess) return e;
         int grid = persistent_grid(c, k_line_bwd<J, DS, MINB>, 32 * t.GW, smem, gb.n_items);
         k_line_bwd<J, DS, MINB><<<grid, 32 * t.GW, smem, s>>>(gb, t.GW, t.LCB);
         c->launches++;
@@ -1542,6 +1686,24 @@ __global__ void k_probe_pipe(int kind, int iters, float *out) {
 
 cudaError_t launch_probe_pipe(int kind, int iters, int blocks, float *out, cudaStream_t s) {
     k_probe_pipe<<<blocks, kProbeThreads, 0, s>>>(kind, iters, out);
+    return cudaGetLastError();
+}
+
+// Bounded-wait probe: one CTA waits on an mbarrier phase that nothing completes, gives
+// up after limit_ns and records the failure exactly as the far-wing kernels do.
+__global__ void k_probe_wait(uint64_t limit_ns, int32_t *status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const bool ok = mbar_wait(&bar, 0, limit_ns);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, kStatusFarWait);
+}
+
+cudaError_t launch_probe_wait(uint64_t limit_ns, int32_t *status, cudaStream_t s) {
+    k_probe_wait<<<1, 32, 0, s>>>(limit_ns, status);
     return cudaGetLastError();
 }
 

@@ -55,5 +55,17 @@ def test_launch_count_and_eval_count():
     prob = tiny_problem(n_lambda=400, n_lines=12, W=30)
     s = pz.Synthesizer(prob)
     pz.pz_line_opacity(s.ctx)
-    assert pz.pz_last_launch_count(s.ctx) == 2      # near-core + far-wing kernels
+    assert pz.pz_last_launch_count(s.ctx) == 3      # near-core, far-wing prefactor table, far-wing kernels
     assert s.n_evals == prob.n_evals
+
+
+def test_bounded_wait_reports_instead_of_hanging():
+    # a barrier phase that nothing completes: the wait gives up after 2 ms and sets bit 0
+    assert pz.pz_probe_wait(2_000_000) == 1
+    # a context whose staged chunks all arrive reports a clean status
+    s = pz.Synthesizer(tiny_problem())
+    s.forward()
+    assert pz.pz_sync_status(s.ctx) == 0
+    with pytest.raises(pz.PzError) as e:
+        pz.pz_probe_wait(0)
+    assert e.value.status == pz.PZ_EINVAL
