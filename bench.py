@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--batch-stars", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=3)
     ap.add_argument("--no-autotune", action="store_true", help="keep the default line-kernel tiling")
+    ap.add_argument("--no-broad", action="store_true", help="skip the 300-1000 nm forward measurement")
+    ap.add_argument("--broad-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -300,6 +302,120 @@ def run_batched(args, dev, barrier, max_over_ranks, ws, tiling=None):
 
 
 # ---------------------------------------------------------------------------
+# broad optical forward: 300-1000 nm at R_grid = 3e5, 3e6 lines
+# ---------------------------------------------------------------------------
+def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None):
+    """Forward (line opacity -> tau + flux -> normalised flux at full resolution) of
+    the 300-1000 nm workload (361,193 points x 3e6 lines x 72 depths, W = 2,000),
+    timed with CUDA events; the plain FP64 GPU form is timed on a 1,200-point slice
+    at 600 nm of the same line list and compared per evaluation."""
+    import torch
+
+    import paper_2607_24141_gb300 as pz
+    from paper_2607_24141_gb300 import inputs as I
+    stream = torch.cuda.current_stream()
+    prob = I.config2()
+    t0 = time.perf_counter()
+    s = pz.Synthesizer(prob, pz.PZ_MIXED, device=dev.index)
+    t_create = time.perf_counter() - t0
+    if tiling is not None:
+        pz.pz_set_tiling(s.ctx, *tiling)
+    evals = s.n_evals
+    f = torch.empty(prob.grid.n_lambda, dtype=torch.float32, device=dev)
+
+    def fwd():
+        pz.pz_line_opacity(s.ctx, None, stream)
+        pz.pz_flux(s.ctx, None, None, stream)
+        pz.pz_instrument(s.ctx, 0.0, 0.0, 0.0, None, f, stream)
+
+    fwd()
+    torch.cuda.synchronize()
+    pz.pz_set_profiling(s.ctx, True)
+    barrier()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.broad_steps):
+        fwd()
+    b.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = max_over_ranks(a.elapsed_time(b)) / args.broad_steps
+    kt = pz.pz_kernel_times(s.ctx)
+    pz.pz_sync_status(s.ctx, stream)
+    s.close()
+    far_ms = (kt["line_fwd"][0] - kt["near_fwd"][0]) / max(kt["line_fwd"][1], 1)
+    out = {"workload": "300-1000 nm at R_grid=3e5 (%d pts) x %d lines (80 species, centres ~ lambda^-2) x 72 depths, "
+                       "W=2,000, f = F/F_c at full resolution" % (prob.grid.n_lambda, prob.lines.n_lines),
+           "s_per_spectrum_fwd": ms * 1e-3, "evals_per_spectrum": evals, "evals_per_s": ws * evals / (ms * 1e-3),
+           "create_s": t_create,
+           "kernel_ms_per_step": {k: v[0] / args.broad_steps for k, v in kt.items() if v[1] > 0},
+           "far_fwd_ms": far_ms, "far_fwd_mufu_ops_per_s": evals / (far_ms * 1e-3)}
+    # plain FP64 GPU form on a slice of the same line list
+    if not args.no_fp64:
+        sl = I.wavelength_slice(prob, 600.0, 1200)
+        s64 = pz.Synthesizer(sl, pz.PZ_FP64, device=dev.index)
+        f64 = torch.empty(sl.grid.n_lambda, dtype=torch.float32, device=dev)
+
+        def fwd64():
+            pz.pz_line_opacity(s64.ctx, None, stream)
+            pz.pz_flux(s64.ctx, None, None, stream)
+            pz.pz_instrument(s64.ctx, 0.0, 0.0, 0.0, None, f64, stream)
+
+        fwd64()
+        torch.cuda.synchronize()
+        a.record(stream)
+        fwd64()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms64 = a.elapsed_time(b)
+        ev64 = s64.n_evals
+        s64.close()
+        rate64 = ev64 / (ms64 * 1e-3)
+        out["fp64_form"] = {"sample": "plain FP64 GPU form on 1,200 points from 600 nm of the same line list "
+                                      "(%d lines, %.3g evals)" % (sl.lines.n_lines, ev64),
+                            "s": ms64 * 1e-3, "evals_per_s": rate64,
+                            "s_per_spectrum_fwd_extrapolated": evals / rate64}
+        out["speedup_vs_fp64_form"] = out["evals_per_s"] / ws / rate64
+    return out
+
+
+def fp64_batch_rate(dev):
+    """Evaluations per second of the plain FP64 GPU form on one graph-captured
+    calibration step (fwd + bwd) of a 3-star, 2 nm batch of the same recipe."""
+    import numpy as np
+    import torch
+
+    import paper_2607_24141_gb300 as pz
+    from paper_2607_24141_gb300 import inputs as I
+    b = I.small_batch(n_stars=3, span_nm=2.0)
+    s = pz.Synthesizer(b, pz.PZ_FP64, device=dev.index)
+    s.forward()
+    n_out = s.n_out
+    y = torch.ones((b.n_stars, n_out), dtype=torch.float32, device=dev)
+    w = torch.full_like(y, 200.0 ** 2)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    nl = b.lines.n_lines
+    g1 = torch.empty(nl, dtype=torch.float32, device=dev)
+    g2 = torch.empty(nl, dtype=torch.float32, device=dev)
+    g3 = torch.empty(max(b.n_elem, 1), dtype=torch.float32, device=dev)
+    s.calib_step(y, w, 0.0, 0.0, 0.0, loss, g1, g2, g3)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    s.calib_step(y, w, 0.0, 0.0, 0.0, loss, g1, g2, g3)
+    e.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(e)
+    ev = s.n_evals
+    s.close()
+    return {"sample": "plain FP64 GPU form, one calibration step of a 3-star 2 nm batch of the same recipe "
+                      "(%.3g evals)" % ev, "evals_per_s": ev / (ms * 1e-3), "ms": ms}
+
+
+# ---------------------------------------------------------------------------
 # native arm
 # ---------------------------------------------------------------------------
 def main():
@@ -412,6 +528,7 @@ def main():
     ms = timed(step, args.steps)
     ktimes = pz.pz_kernel_times(s.ctx)
     pz.pz_set_profiling(s.ctx, False)
+    pz.pz_sync_status(s.ctx, stream)            # raises if a bounded device wait gave up
     n_launch = launches[0] + 0
     clocks = clk.stop()
     ms_max = max_over_ranks(ms)
@@ -482,10 +599,19 @@ def main():
 
     # ---- batched many-star workload ----
     batched = None
+    if fp64 is None:
+        s.close()
     if not args.no_batch and args.batch_stars > 0:
-        if fp64 is None:
-            s.close()
         batched = run_batched(args, dev, barrier, max_over_ranks, ws, tune["tiling"] if tune else None)
+        if not args.no_fp64:
+            r64 = fp64_batch_rate(dev)
+            batched["fp64_form"] = r64
+            batched["speedup_vs_fp64_form"] = batched["evals_per_s"] / ws / r64["evals_per_s"]
+
+    # ---- broad optical forward ----
+    broad = None
+    if not args.no_broad:
+        broad = run_broad(args, dev, barrier, max_over_ranks, ws, tune["tiling"] if tune else None)
 
     # ---- roofline of the dominant kernel ----
     props = torch.cuda.get_device_properties(local)
@@ -550,6 +676,7 @@ def main():
         "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
         "batched": batched,
+        "broad_optical_fwd": broad,
         "autotune": tune,
     }
     if rank == 0:

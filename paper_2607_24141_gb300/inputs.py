@@ -328,6 +328,25 @@ def config3(seed: int = 3, lam_lo: float = 1500.0, lam_hi: float = 1700.0,
     return prob, truth
 
 
+def wavelength_slice(prob: Problem, lam_lo_nm: float, n_points: int) -> Problem:
+    """The same problem restricted to n_points grid points starting at the first grid
+    point >= lam_lo_nm: the grid keeps its step (lambda_0 moves to that point), the
+    lines are those whose windows reach the slice, kappa_c is cut to the slice, and
+    there is no instrument.  Pure data selection, used to time slow references on a
+    bounded part of a workload."""
+    g = prob.grid
+    lnr = math.log1p(1.0 / g.R_grid)
+    i0 = int(math.ceil(math.log(lam_lo_nm / g.lambda0_nm) / lnr - 1e-9))
+    i0 = max(0, min(i0, g.n_lambda - 1))
+    n = max(1, min(n_points, g.n_lambda - i0))
+    grid = Grid(g.lambda0_nm * math.exp(i0 * lnr), g.R_grid, n)
+    il = center_index(g, prob.lines.lambda_nm)
+    W = prob.lines.half_window
+    keep = np.nonzero((il + W >= i0) & (il - W <= i0 + n - 1))[0]
+    return Problem(prob.name + "-slice", prob.atmos, grid, prob.lines.subset(keep),
+                   np.ascontiguousarray(prob.kappa_c[:, i0:i0 + n]), None, prob.elem_of_species, prob.n_elem)
+
+
 def small_config1(n_lambda_span_nm: float = 2.0, lines_scale: float = 0.01, seed: int = 11,
                   W: int = 1500, with_instrument: bool = True) -> Problem:
     """Scaled-down config 1 for element-wise parity: same recipe, a ~2 nm slice."""

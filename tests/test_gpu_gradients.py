@@ -73,3 +73,31 @@ def test_autograd_function_matches_direct_call(oracle):
     assert rel_metric(dgf.grad.cpu().numpy().astype(np.float64), ref[1]).max() < G_TOL
     assert rel_metric(dg6.grad.cpu().numpy().astype(np.float64), ref[2]).max() < G_TOL
     assert rel_metric(dab.grad.cpu().numpy().astype(np.float64), ref[3]).max() < G_TOL
+
+
+def test_config3_full_size_gradients_match_the_fp64_form():
+    """The calibration workload at full size (37,550 points, 1.2e5 lines, 8,575 pixels):
+    mixed-path gradients for every line and element against the plain FP64 GPU form
+    (which the small cases pin to the oracle's adjoint), metric c17, at the seeded
+    S/N-200 target and at zero corrections."""
+    import torch
+    prob, truth = I.config3()
+    n_out = prob.instrument.pix_lambda_nm.size
+    s = pz.Synthesizer(prob, pz.PZ_MIXED)
+    s.set_corrections(truth["dlog_gf"], truth["dlog_gamma6"], None)
+    f_true = s.forward().cpu().numpy().astype(np.float64)
+    s.close()
+    y = (f_true + truth["noise"]).astype(np.float32)
+    w = np.float32(truth["weight"])
+    zero = {"dlog_gf": np.zeros(prob.lines.n_lines, np.float32),
+            "dlog_gamma6": np.zeros(prob.lines.n_lines, np.float32),
+            "dabund": np.zeros(prob.n_elem, np.float32)}
+    mixed = run_gradient(prob, y, w, pz.PZ_MIXED, zero)
+    ref = run_gradient(prob, y, w, pz.PZ_FP64, zero)
+    assert abs(mixed["loss"] / ref["loss"] - 1) < 1e-4
+    e1 = rel_metric(mixed["g_gf"], ref["g_gf"]).max()
+    e2 = rel_metric(mixed["g_g6"], ref["g_g6"]).max()
+    e3 = rel_metric(mixed["g_ab"][:prob.n_elem], ref["g_ab"][:prob.n_elem]).max()
+    print("config3 full size: loss %.6g, max rel err gf %.3g g6 %.3g abund %.3g" % (ref["loss"], e1, e2, e3))
+    assert e1 < G_TOL and e2 < G_TOL and e3 < G_TOL
+    torch.cuda.synchronize()

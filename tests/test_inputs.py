@@ -88,3 +88,23 @@ def test_recipes_give_realistic_line_depths(oracle):
         f = oracle.forward(prob)["f"]
         p5, p50 = np.percentile(f, [5, 50])
         assert 0.8 < p50 < 0.995 and p5 < 0.8, (prob.name, p5, p50)
+
+
+def test_wavelength_slice_keeps_exactly_the_lines_that_reach_it():
+    import math
+    p = I.config0()
+    q = I.wavelength_slice(p, 502.0, 700)
+    lnr = math.log1p(1.0 / p.grid.R_grid)
+    i0 = round(math.log(q.grid.lambda0_nm / p.grid.lambda0_nm) / lnr)
+    assert q.grid.lambda0_nm >= 502.0 and q.grid.lambda0_nm < 502.0 * (1 + 1.0 / p.grid.R_grid)
+    assert q.grid.n_lambda == 700 and q.grid.R_grid == p.grid.R_grid
+    assert np.array_equal(q.kappa_c, p.kappa_c[:, i0:i0 + 700])
+    il = I.center_index(p.grid, p.lines.lambda_nm)
+    W = p.lines.half_window
+    reach = (il + W >= i0) & (il - W <= i0 + 699)
+    assert q.lines.n_lines == int(reach.sum())
+    assert np.array_equal(np.sort(q.lines.lambda_nm), np.sort(p.lines.lambda_nm[reach]))
+    # the slice's own evaluation count equals the full problem's evaluations inside the slice
+    lo = np.maximum(il - W, i0)
+    hi = np.minimum(il + W, i0 + 699)
+    assert q.n_evals == int(np.maximum(hi - lo + 1, 0).sum()) * p.atmos.n_depth
