@@ -36,10 +36,10 @@ WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts
             "(40 species, 1/3 in bands) x 72 depths, W=1,500, v_r=12.3 km/s, LSF R=22,500 -> 8,575 px, "
             "chi^2 vs synthetic target, gradients for 2e5 dlog_gf + 2e5 dlog_gamma6 + 20 abundances")
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of each
-# kernel on this workload (profiles/k_line_*_apogee.md), valid only while the kernel sources hash to
-# the recorded value; otherwise the roofline's traffic is reported as null.
-TRAFFIC = {"k_line_bwd": (21.2928e6, "dbe4ec0a1012c883")}
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
+# kernel on this workload (profiles/k_line_bwd_apogee.md: 6.313 GB read + 84.5 MB written, default
+# tiling), valid only while the kernel sources hash to the recorded value; otherwise null.
+TRAFFIC = {"k_line_bwd": (6.3973e9, "4c425f93e52e2362")}
 KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h")
 
 # Per-evaluation pipe work of the far-wing kernels, which evaluate every in-window cell:
