@@ -252,7 +252,7 @@ int32_t pz_last_launch_count(const pz_ctx *ctx);
  * (forward and backward) and the minimum number of resident CTAs per SM the
  * kernels are compiled for (a register budget).  Values <= 0 keep the current
  * setting; the next launch uses the new tiling.  Supported (lambda, depth,
- * CTAs) triples: (4,6,1-4) (4,8,1-3) (4,12,1-2) (2,6,4) (2,8,2-4) (2,12,1-3);
+ * CTAs) triples: (4,6,1-6) (4,8,1-3) (4,12,1-2) (2,6,4) (2,6,6) (2,8,2-5) (2,12,1-3);
  * depths per warp are even (the far-wing kernels evaluate depth pairs).
  * Errors: PZ_EINVAL for an unsupported combination or a chunk that does not fit
  * in shared memory. */
@@ -264,7 +264,8 @@ pz_status pz_set_tiling(pz_ctx *ctx, int32_t lambda_per_thread, int32_t depth_pe
  * Sec. 2.3); here the tiling is measured instead.  Starting from the current
  * tiling, a coordinate search times, on this context's own stars, line lists and
  * atmospheres: every compiled (lambda points per thread, depths per warp, CTAs
- * per SM) triple, then warps per CTA 1-4, then lines per chunk 16-256.  Each
+ * per SM) triple, then warps per CTA 1-4, then lines per chunk 16-128, and runs
+ * these three phases twice.  Each
  * candidate gets one untimed pass, then `reps` forward line launches (far wing +
  * near core) and, if with_backward != 0, `reps` backward line launches, timed
  * with CUDA events on `stream`.  The tiling with the smallest forward (+ backward)
@@ -277,7 +278,7 @@ pz_status pz_set_tiling(pz_ctx *ctx, int32_t lambda_per_thread, int32_t depth_pe
  * the backward's line accumulators), so pz_line_opacity must run again before
  * pz_flux (PZ_ESTATE otherwise).  The backward timing uses G of the last
  * pz_backward, or zeros if none ran (the kernels' cost does not depend on G).
- * Cost: about 25 candidates x (1 + reps) passes.
+ * Cost: about 50 candidates x (1 + reps) passes.
  * Errors: PZ_EINVAL for the plain FP64 form (it has no tiling) or reps outside
  * [1, 100]; PZ_ECUDA if a launch fails (the context keeps the last tiling that
  * was applied). */

@@ -680,38 +680,42 @@ pz_status pz_autotune(pz_ctx *c, int32_t with_backward, int32_t reps, int32_t *b
         }
         return PZ_OK;
     };
-    static const int kJDM[][3] = {{4, 6, 1}, {4, 6, 2}, {4, 6, 3}, {4, 6, 4}, {4, 8, 1},  {4, 8, 2},
-                                  {4, 8, 3}, {4, 12, 1}, {4, 12, 2}, {2, 6, 4}, {2, 8, 2}, {2, 8, 3},
-                                  {2, 8, 4}, {2, 12, 1}, {2, 12, 2}, {2, 12, 3}};
-    if (st == PZ_OK) {
-        const Tiling base = cur;
-        for (const auto &q : kJDM) {
-            Tiling t = base;
-            t.J = q[0];
-            t.DS = q[1];
-            t.minb = q[2];
-            if (t.J == base.J && t.DS == base.DS && t.minb == base.minb) continue;
-            if ((st = consider(t)) != PZ_OK) break;
+    static const int kJDM[][3] = {{4, 6, 1}, {4, 6, 2}, {4, 6, 3}, {4, 6, 4}, {4, 6, 5}, {4, 6, 6},  {4, 8, 1},
+                                  {4, 8, 2}, {4, 8, 3}, {4, 12, 1}, {4, 12, 2}, {2, 6, 4}, {2, 6, 6},  {2, 8, 2},
+                                  {2, 8, 3}, {2, 8, 4}, {2, 8, 5}, {2, 12, 1}, {2, 12, 2}, {2, 12, 3}};
+    // two rounds of the three phases: a tiling that needs both a different register budget and
+    // a different chunk (or CTA width) is reachable only after the others have moved
+    for (int round = 0; round < 2 && st == PZ_OK; ++round) {
+        {
+            const Tiling base = cur;
+            for (const auto &q : kJDM) {
+                Tiling t = base;
+                t.J = q[0];
+                t.DS = q[1];
+                t.minb = q[2];
+                if (t.J == base.J && t.DS == base.DS && t.minb == base.minb) continue;
+                if ((st = consider(t)) != PZ_OK) break;
+            }
         }
-    }
-    if (st == PZ_OK) {
-        const Tiling base = cur;
-        for (int gw = 1; gw <= 4 && st == PZ_OK; ++gw)
-            if (gw != base.GW) {
-                Tiling t = base;
-                t.GW = gw;
-                st = consider(t);
-            }
-    }
-    if (st == PZ_OK) {
-        const Tiling base = cur;
-        for (int lc : {16, 32, 64, 128, 256})
-            if (lc != base.LC && st == PZ_OK) {
-                Tiling t = base;
-                t.LC = lc;
-                t.LCB = lc;
-                st = consider(t);
-            }
+        if (st == PZ_OK) {
+            const Tiling base = cur;
+            for (int gw = 1; gw <= 4 && st == PZ_OK; ++gw)
+                if (gw != base.GW) {
+                    Tiling t = base;
+                    t.GW = gw;
+                    st = consider(t);
+                }
+        }
+        if (st == PZ_OK) {
+            const Tiling base = cur;
+            for (int lc : {16, 32, 64, 128})
+                if (lc != base.LC && st == PZ_OK) {
+                    Tiling t = base;
+                    t.LC = lc;
+                    t.LCB = lc;
+                    st = consider(t);
+                }
+        }
     }
     for (auto &e : ev) cudaEventDestroy(e);
     if (st != PZ_OK) return st;

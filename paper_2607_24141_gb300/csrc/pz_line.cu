@@ -319,8 +319,10 @@ __device__ __forceinline__ f2_t f2_splat(float v) { return f2_pack(v, v); }
 // layers and every line l, the (DC/2) depth pairs of NQ quads, quad q holding
 // {p_2q(d), p_2q(d + 1), p_2q+1(d), p_2q+1(d + 1)} (one 16-byte load returns the
 // packed depth pairs of two parameters):
-//   forward  (NQ = 2): (k, a^2) (B1, B2)
-//   backward (NQ = 3): (k, a^2) (B1, B2) (C1, C2)
+//   forward  (NQ = 2): (k^2, a^2) (B1, B2)
+//   backward (NQ = 3): (k^2, a^2) (B1, B2) (C1, C2)
+// with k = c/dv_D: away from the masked lines |z|^2 = u^2 k^2 + a^2, u^2 formed once per
+// point and shared by all depths.
 // at tab[(g n_lines + l) (DC/2) NQ + pair NQ + q], and the line record at
 // info[g n_lines + l].  The rest of the far polynomial (B3..B5, C3..C6) follows
 // from a^2, B1 and C1 in registers.  The chunk of LC lines a CTA needs is then
@@ -356,7 +358,7 @@ __global__ void k_far_table(LineArgs gq, int DC, int DS, int ngroups, float4 *ta
         depth_params<NQ == kNQB ? 16 : 8>(g, L, d, p0);
         depth_params<NQ == kNQB ? 16 : 8>(g, L, d + 1, p1);
         float4 *dst = tab + gl * (P * NQ) + pr * NQ;
-        dst[0] = make_float4(p0[0], p1[0], p0[1], p1[1]);
+        dst[0] = make_float4(p0[0] * p0[0], p1[0] * p1[0], p0[1], p1[1]);
         dst[1] = make_float4(p0[2], p1[2], p0[3], p1[3]);
         if (NQ == kNQB) dst[2] = make_float4(p0[8], p1[8], p0[9], p1[9]);
         if (pr == 0) {
@@ -480,6 +482,20 @@ __device__ __forceinline__ int far_flags(const LineArgs &g, const LineInfo &info
     return (fast ? 1 : 0) | (red ? 2 : 0);
 }
 
+// k = c/dv_D of the warp's depth pairs, rounded exactly as depth_params forms it, for the
+// masked lines, whose cells are classified near / far with the near-core kernels' own
+// arithmetic (x = u k, |z|^2 = x^2 + a^2).  Layers past the last one get 0.
+template <int DP>
+__device__ __forceinline__ void far_kpairs(const LineArgs &g, int sp, int dfirst, f2_t (&kp)[DP]) {
+#pragma unroll
+    for (int dp = 0; dp < DP; ++dp) {
+        const int da = dfirst + 2 * dp, db = da + 1;
+        const float ka = da < g.nd ? __fmul_rn((float)kC, __ldg(g.invdv + sp * g.nd + da)) : 0.0f;
+        const float kb = db < g.nd ? __fmul_rn((float)kC, __ldg(g.invdv + sp * g.nd + db)) : 0.0f;
+        kp[dp] = f2_pack(ka, kb);
+    }
+}
+
 // Compensated-sum slots of depth dd of thread tid: the (hi, lo) pairs of its J points,
 // hi at [0, 4) and lo at [4, 8) (the J points of a thread are contiguous: one vector
 // access each).  They live in shared memory and are touched once per line chunk.
@@ -563,11 +579,13 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
             f2_t u2[J];
             if (fl & 1) {
                 // the whole tile is in the line's far wing: offsets from the first point's,
-                // u_j = u_0 r^-j + (r^-j - 1)
+                // u_j = u_0 r^-j + (r^-j - 1), and their squares
                 const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
                 u2[0] = f2_splat(u0);
 #pragma unroll
                 for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j]));
+#pragma unroll
+                for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
             } else {
                 // cells are classified near / far exactly as the near-core kernel does
 #pragma unroll
@@ -577,25 +595,23 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                 // reduced form: t (B1 + B2 t)
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
+                    // q0 = (k^2, a^2), q1 = (B1, B2)
                     const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        const f2_t x = f2_mul(u2[j], q0.x);
-                        const f2_t t = f2_rcp(f2_fma(x, x, q0.y));
+                        const f2_t t = f2_rcp(f2_fma(u2[j], q0.x, q0.y));
                         acc[dp][j] = f2_fma(t, f2_fma(t, q1.y, q1.x), acc[dp][j]);
                     }
                 }
             } else if (fl & 1) {
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
-                    // q0 = (k, a^2), q1 = (B1, B2)
                     const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
                     f2_t B3, B4, B5;
                     far_b345(q0.y, q1.x, B3, B4, B5);
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        const f2_t x = f2_mul(u2[j], q0.x);
-                        const f2_t t = f2_rcp(f2_fma(x, x, q0.y));
+                        const f2_t t = f2_rcp(f2_fma(u2[j], q0.x, q0.y));
                         f2_t h = f2_fma(t, B5, B4);
                         h = f2_fma(t, h, B3);
                         h = f2_fma(t, h, q1.y);
@@ -612,6 +628,8 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                     const int di = lam_thr + j - il;
                     inwin[j] = di >= -g.W && di <= g.W;
                 }
+                f2_t kp[DP];
+                far_kpairs<DP>(g, info.sp, d0 + warp * DS, kp);
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
                     const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
@@ -619,7 +637,7 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                     far_b345(q0.y, q1.x, B3, B4, B5);
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        const f2_t x = f2_mul(u2[j], q0.x);
+                        const f2_t x = f2_mul(u2[j], kp[dp]);
                         const f2_t r2 = f2_fma(x, x, q0.y);
                         const f2_t t = f2_rcp(r2);
                         f2_t h = f2_fma(t, B5, B4);
@@ -724,17 +742,17 @@ __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int 
 }
 
 // Reduced far-wing backward form (lines flagged for it): H and dH/da polynomials cut
-// after their t^2 terms.  par: the warp's depth pairs, (k, a^2) (B1, B2) (C1, C2).
+// after their t^2 terms.  par: the warp's depth pairs, (k^2, a^2) (B1, B2) (C1, C2);
+// usq: the squared offsets u^2 of the thread's points.
 template <int J, int DP>
-__device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, const f2_t (&u2)[J],
+__device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, const f2_t (&usq)[J],
                                                      const f2_t (&gv)[DP][J], f2_t &S1, f2_t &S2) {
 #pragma unroll
     for (int dp = 0; dp < DP; ++dp) {
         const ulonglong2 q0 = par[kNQB * dp], q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
-            const f2_t x = f2_mul(u2[j], q0.x);
-            const f2_t t = f2_rcp(f2_fma(x, x, q0.y));
+            const f2_t t = f2_rcp(f2_fma(usq[j], q0.x, q0.y));
             const f2_t gt = f2_mul(gv[dp][j], t);
             S1 = f2_fma(gt, f2_fma(t, q1.y, q1.x), S1);
             S2 = f2_fma(gt, f2_fma(t, q2.y, q2.x), S2);
@@ -743,22 +761,28 @@ __device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, cons
 }
 
 // One line's far-wing backward sums over a warp's J x DS cells (depth pairs):
-// S1 += G stim A H, S2 += G stim A a6 dH/da.  MASK: keep only the far cells inside
-// the window (inwin per lambda point).
+// S1 += G stim A H, S2 += G stim A a6 dH/da.  Without MASK, w holds the squared
+// offsets u^2; with MASK, w holds the offsets u and kp the depth pairs' k, and only
+// the far cells inside the window (inwin per lambda point) are kept.
 template <int J, int DP, bool MASK>
-__device__ __forceinline__ void far_bwd_line(const ulonglong2 *par, const f2_t (&u2)[J], const f2_t (&gv)[DP][J],
-                                             const bool *inwin, f2_t &S1, f2_t &S2) {
+__device__ __forceinline__ void far_bwd_line(const ulonglong2 *par, const f2_t (&w)[J], const f2_t (&gv)[DP][J],
+                                             const bool *inwin, const f2_t *kp, f2_t &S1, f2_t &S2) {
 #pragma unroll
     for (int dp = 0; dp < DP; ++dp) {
-        // (k, a^2) (B1, B2) (C1, C2); the higher coefficients from a^2, B1 and C1
+        // (k^2, a^2) (B1, B2) (C1, C2); the higher coefficients from a^2, B1 and C1
         const ulonglong2 q0 = par[kNQB * dp], q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
         f2_t B3, B4, B5, C3, C4, C5, C6;
         far_b345(q0.y, q1.x, B3, B4, B5);
         far_c3456(q0.y, q2.x, C3, C4, C5, C6);
 #pragma unroll
         for (int j = 0; j < J; ++j) {
-            const f2_t x = f2_mul(u2[j], q0.x);
-            const f2_t r2 = f2_fma(x, x, q0.y);
+            f2_t r2;
+            if (MASK) {
+                const f2_t x = f2_mul(w[j], kp[dp]);
+                r2 = f2_fma(x, x, q0.y);
+            } else {
+                r2 = f2_fma(w[j], q0.x, q0.y);
+            }
             const f2_t t = f2_rcp(r2);
             f2_t h = f2_fma(t, B5, B4);
             h = f2_fma(t, h, B3);
@@ -849,6 +873,8 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
                 u2[0] = f2_splat(u0);
 #pragma unroll
                 for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j]));
+#pragma unroll
+                for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
             } else {
 #pragma unroll
                 for (int j = 0; j < J; ++j) u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
@@ -857,7 +883,7 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
             if (fl & 2) {
                 far_bwd_line_reduced<J, DP>(par, u2, gv, S1, S2);
             } else if (fl & 1) {
-                far_bwd_line<J, DP, false>(par, u2, gv, nullptr, S1, S2);
+                far_bwd_line<J, DP, false>(par, u2, gv, nullptr, nullptr, S1, S2);
             } else {
                 // line near the tile or partly outside its window: far cells inside the window only
                 bool inwin[J];
@@ -867,7 +893,9 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
                     const int di = lam_thr + j - il;
                     inwin[j] = di >= -g.W && di <= g.W;
                 }
-                far_bwd_line<J, DP, true>(par, u2, gv, inwin, S1, S2);
+                f2_t kp[DP];
+                far_kpairs<DP>(g, info.sp, d0 + warp * DS, kp);
+                far_bwd_line<J, DP, true>(par, u2, gv, inwin, kp, S1, S2);
             }
             float s1a, s1b, s2a, s2b;
             f2_unpack(S1, s1a, s1b);
@@ -1367,7 +1395,7 @@ static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
 // Supported (lambda points per thread, depths per warp, minimum resident CTAs per SM).
 #define PZ_TILE_LIST(X) \
     X(4, 6, 1) X(4, 6, 2) X(4, 6, 3) X(4, 6, 4) X(4, 8, 1) X(4, 8, 2) X(4, 8, 3) X(4, 12, 1) X(4, 12, 2) \
-    X(2, 6, 4) X(2, 8, 2) X(2, 8, 3) X(2, 8, 4) X(2, 12, 1) X(2, 12, 2) X(2, 12, 3)
+    X(2, 6, 4) X(2, 8, 2) X(2, 8, 3) X(2, 8, 4) X(2, 12, 1) X(2, 12, 2) X(2, 12, 3) X(4, 6, 5) X(4, 6, 6) X(2, 6, 6) X(2, 8, 5)
 
 #define PZ_TILE_DISPATCH(FN)                                                        \
     const Tiling &t = c->tiling;                                                    \

@@ -9,8 +9,9 @@ from tiny import tiny_problem
 
 pytestmark = pytest.mark.gpu
 
-SUPPORTED = {(4, 6, 1), (4, 6, 2), (4, 6, 3), (4, 6, 4), (4, 8, 1), (4, 8, 2), (4, 8, 3), (4, 12, 1), (4, 12, 2),
-             (2, 6, 4), (2, 8, 2), (2, 8, 3), (2, 8, 4), (2, 12, 1), (2, 12, 2), (2, 12, 3)}
+SUPPORTED = {(4, 6, 1), (4, 6, 2), (4, 6, 3), (4, 6, 4), (4, 6, 5), (4, 6, 6), (4, 8, 1), (4, 8, 2), (4, 8, 3),
+             (4, 12, 1), (4, 12, 2), (2, 6, 4), (2, 6, 6), (2, 8, 2), (2, 8, 3), (2, 8, 4), (2, 8, 5), (2, 12, 1),
+             (2, 12, 2), (2, 12, 3)}
 
 
 def test_autotune_keeps_results(oracle):
@@ -40,7 +41,7 @@ def test_autotune_keeps_results(oracle):
     res = pz.pz_autotune(s.ctx, with_backward=True, reps=1)
     J, DS, GW, LC, MINB = res["tiling"]
     assert (J, DS, MINB) in SUPPORTED and 1 <= GW <= 4 and 16 <= LC <= 256
-    assert res["candidates"] >= 16
+    assert res["candidates"] >= 20
     assert res["fwd_ms"] > 0 and res["bwd_ms"] > 0
 
     # the forward state is invalidated by the tuning passes
