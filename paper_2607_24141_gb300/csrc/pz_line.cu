@@ -313,16 +313,22 @@ __device__ __forceinline__ f2_t f2_rcp(f2_t a) {
     return r;
 }
 __device__ __forceinline__ f2_t f2_splat(float v) { return f2_pack(v, v); }
+__device__ __forceinline__ float f2_lo(f2_t v) {
+    float lo, hi;
+    f2_unpack(v, lo, hi);
+    return lo;
+}
 
 // ---- far-wing prefactor tables ----------------------------------------------
 // Before each far-wing launch k_far_table writes, for every depth group g of DC
 // layers and every line l, the (DC/2) depth pairs of NQ quads, quad q holding
 // {p_2q(d), p_2q(d + 1), p_2q+1(d), p_2q+1(d + 1)} (one 16-byte load returns the
 // packed depth pairs of two parameters):
-//   forward  (NQ = 2): (k^2, a^2) (B1, B2)
-//   backward (NQ = 3): (k^2, a^2) (B1, B2) (C1, C2)
-// with k = c/dv_D: away from the masked lines |z|^2 = u^2 k^2 + a^2, u^2 formed once per
-// point and shared by all depths.
+//   forward  (NQ = 2): (1/k^2, a^2) (B1, B2')
+//   backward (NQ = 3): (1/k^2, a^2) (B1, B2') (C1, C2')
+// with k = c/dv_D, B2' = B2 - B1 a^2 = B1 (1.5 - a^2) and C2' = C2 - C1 a^2 = C1 (1.5 - 3a^2).
+// Away from the masked lines |z|^2 = (u^2 + a^2/k^2) k^2, u^2 formed once per point and
+// shared by all depths; B2 = 1.5 B1 and C2 = (1.5 - 2a^2) C1 are restored in registers.
 // at tab[(g n_lines + l) (DC/2) NQ + pair NQ + q], and the line record at
 // info[g n_lines + l].  The rest of the far polynomial (B3..B5, C3..C6) follows
 // from a^2, B1 and C1 in registers.  The chunk of LC lines a CTA needs is then
@@ -335,6 +341,12 @@ constexpr int kNQF = 2, kNQB = 3;
 // (1.5 - 2a^2) t).  With |v| >= 100 (t <= 1e-4) and a^2 <= 1.5 (s = a^2 t <= 1.5e-4)
 // the dropped terms, (3.75 t^2 + 2 s t + 15 s t^2 + 12 s^2 t^2) relative for H, stay
 // below 7e-8 (about one FP32 rounding) and below 2.2e-7 for dH/da.
+// In the same region t is expanded about p = 1/(u k)^2 = (1/u^2)(1/k^2):
+// t = p/(1 + a^2 p) = p - a^2 p^2 + O((a^2 p)^2 p), so that
+//   H sqrt(pi)/A = B1 p + B2' p^2,   dH/da sqrt(pi)/(A a6) = C1 p + C2' p^2
+// with B2' = B1 (1.5 - a^2), C2' = C1 (1.5 - 3a^2); the further dropped terms,
+// (a^2 p)^2 and 3 a^2 p^2 relative, stay below 5e-8.  1/u^2 depends on the line and the
+// point only, so one MUFU reciprocal serves all the depths of a warp.
 constexpr float kFast2V = 5.0f;      // distance threshold factor: |v| >= 5 x 20
 constexpr float kFast2A2 = 1.5f;     // a^2 bound
 
@@ -358,9 +370,14 @@ __global__ void k_far_table(LineArgs gq, int DC, int DS, int ngroups, float4 *ta
         depth_params<NQ == kNQB ? 16 : 8>(g, L, d, p0);
         depth_params<NQ == kNQB ? 16 : 8>(g, L, d + 1, p1);
         float4 *dst = tab + gl * (P * NQ) + pr * NQ;
-        dst[0] = make_float4(p0[0] * p0[0], p1[0] * p1[0], p0[1], p1[1]);
-        dst[1] = make_float4(p0[2], p1[2], p0[3], p1[3]);
-        if (NQ == kNQB) dst[2] = make_float4(p0[8], p1[8], p0[9], p1[9]);
+        // 1/k^2 (0 on the padding layers past the last one, whose coefficients are 0)
+        const float ik0 = p0[0] > 0.0f ? 1.0f / (p0[0] * p0[0]) : 0.0f;
+        const float ik1 = p1[0] > 0.0f ? 1.0f / (p1[0] * p1[0]) : 0.0f;
+        dst[0] = make_float4(ik0, ik1, p0[1], p1[1]);
+        // B2' = B2 - B1 a^2 and C2' = C2 - C1 a^2 (the reduced forms in p, see far_reduced)
+        dst[1] = make_float4(p0[2], p1[2], fmaf(-p0[2], p0[1], p0[3]), fmaf(-p1[2], p1[1], p1[3]));
+        if (NQ == kNQB)
+            dst[2] = make_float4(p0[8], p1[8], fmaf(-p0[8], p0[1], p0[9]), fmaf(-p1[8], p1[1], p1[9]));
         if (pr == 0) {
             int amask = 0;
             for (int w = 0; w < DC / DS; ++w) {
@@ -592,15 +609,18 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                 for (int j = 0; j < J; ++j) u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
             }
             if (fl & 2) {
-                // reduced form: t (B1 + B2 t)
+                // reduced form in p = (1/u^2)(1/k^2): B1 p + B2' p^2
+                f2_t sp[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(u2[j])));
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
-                    // q0 = (k^2, a^2), q1 = (B1, B2)
+                    // q0 = (1/k^2, a^2), q1 = (B1, B2')
                     const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        const f2_t t = f2_rcp(f2_fma(u2[j], q0.x, q0.y));
-                        acc[dp][j] = f2_fma(t, f2_fma(t, q1.y, q1.x), acc[dp][j]);
+                        const f2_t pp = f2_mul(sp[j], q0.x);
+                        acc[dp][j] = f2_fma(pp, f2_fma(pp, q1.y, q1.x), acc[dp][j]);
                     }
                 }
             } else if (fl & 1) {
@@ -609,12 +629,15 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                     const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
                     f2_t B3, B4, B5;
                     far_b345(q0.y, q1.x, B3, B4, B5);
+                    const f2_t B2 = f2_mul(q1.x, f2_splat(1.5f));
+                    const f2_t ak = f2_mul(q0.y, q0.x);          // a^2/k^2
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        const f2_t t = f2_rcp(f2_fma(u2[j], q0.x, q0.y));
+                        // t = 1/(u^2 k^2 + a^2) = (1/k^2)/(u^2 + a^2/k^2)
+                        const f2_t t = f2_mul(q0.x, f2_rcp(f2_fma(u2[j], f2_splat(1.0f), ak)));
                         f2_t h = f2_fma(t, B5, B4);
                         h = f2_fma(t, h, B3);
-                        h = f2_fma(t, h, q1.y);
+                        h = f2_fma(t, h, B2);
                         h = f2_fma(t, h, q1.x);
                         acc[dp][j] = f2_fma(t, h, acc[dp][j]);
                     }
@@ -635,6 +658,7 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                     const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
                     f2_t B3, B4, B5;
                     far_b345(q0.y, q1.x, B3, B4, B5);
+                    const f2_t B2 = f2_mul(q1.x, f2_splat(1.5f));
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const f2_t x = f2_mul(u2[j], kp[dp]);
@@ -642,7 +666,7 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                         const f2_t t = f2_rcp(r2);
                         f2_t h = f2_fma(t, B5, B4);
                         h = f2_fma(t, h, B3);
-                        h = f2_fma(t, h, q1.y);
+                        h = f2_fma(t, h, B2);
                         h = f2_fma(t, h, q1.x);
                         const f2_t r = f2_fma(t, h, acc[dp][j]);
                         float r2a, r2b, ra, rb, aa, ab;
@@ -747,15 +771,19 @@ __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int 
 template <int J, int DP>
 __device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, const f2_t (&usq)[J],
                                                      const f2_t (&gv)[DP][J], f2_t &S1, f2_t &S2) {
+    // reduced forms in p = (1/u^2)(1/k^2): G (B1 p + B2' p^2) and G (C1 p + C2' p^2)
+    f2_t sp[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(usq[j])));
 #pragma unroll
     for (int dp = 0; dp < DP; ++dp) {
         const ulonglong2 q0 = par[kNQB * dp], q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
 #pragma unroll
         for (int j = 0; j < J; ++j) {
-            const f2_t t = f2_rcp(f2_fma(usq[j], q0.x, q0.y));
-            const f2_t gt = f2_mul(gv[dp][j], t);
-            S1 = f2_fma(gt, f2_fma(t, q1.y, q1.x), S1);
-            S2 = f2_fma(gt, f2_fma(t, q2.y, q2.x), S2);
+            const f2_t pp = f2_mul(sp[j], q0.x);
+            const f2_t gp = f2_mul(gv[dp][j], pp);
+            S1 = f2_fma(gp, f2_fma(pp, q1.y, q1.x), S1);
+            S2 = f2_fma(gp, f2_fma(pp, q2.y, q2.x), S2);
         }
     }
 }
@@ -769,29 +797,32 @@ __device__ __forceinline__ void far_bwd_line(const ulonglong2 *par, const f2_t (
                                              const bool *inwin, const f2_t *kp, f2_t &S1, f2_t &S2) {
 #pragma unroll
     for (int dp = 0; dp < DP; ++dp) {
-        // (k^2, a^2) (B1, B2) (C1, C2); the higher coefficients from a^2, B1 and C1
+        // (1/k^2, a^2) (B1, B2') (C1, C2'); the other coefficients from a^2, B1 and C1
         const ulonglong2 q0 = par[kNQB * dp], q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
         f2_t B3, B4, B5, C3, C4, C5, C6;
         far_b345(q0.y, q1.x, B3, B4, B5);
         far_c3456(q0.y, q2.x, C3, C4, C5, C6);
+        const f2_t B2 = f2_mul(q1.x, f2_splat(1.5f));
+        const f2_t C2 = f2_mul(f2_fma(q0.y, f2_splat(-2.0f), f2_splat(1.5f)), q2.x);
+        const f2_t ak = f2_mul(q0.y, q0.x);          // a^2/k^2
 #pragma unroll
         for (int j = 0; j < J; ++j) {
-            f2_t r2;
+            f2_t r2, t;
             if (MASK) {
                 const f2_t x = f2_mul(w[j], kp[dp]);
                 r2 = f2_fma(x, x, q0.y);
+                t = f2_rcp(r2);
             } else {
-                r2 = f2_fma(w[j], q0.x, q0.y);
+                t = f2_mul(q0.x, f2_rcp(f2_fma(w[j], f2_splat(1.0f), ak)));
             }
-            const f2_t t = f2_rcp(r2);
             f2_t h = f2_fma(t, B5, B4);
             h = f2_fma(t, h, B3);
-            h = f2_fma(t, h, q1.y);
+            h = f2_fma(t, h, B2);
             h = f2_fma(t, h, q1.x);
             f2_t q = f2_fma(t, C6, C5);
             q = f2_fma(t, q, C4);
             q = f2_fma(t, q, C3);
-            q = f2_fma(t, q, q2.y);
+            q = f2_fma(t, q, C2);
             q = f2_fma(t, q, q2.x);
             f2_t gt = f2_mul(gv[dp][j], t);
             if (MASK) {
