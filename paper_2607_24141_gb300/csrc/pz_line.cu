@@ -894,6 +894,7 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
         }
         const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
         const LineInfo *s_line = cp.info(k);
+        float h1 = 0.0f, h2 = 0.0f;   // lane sums of the held even line
         for (int li = 0; li < nl; ++li) {
             const LineInfo info = s_line[li];
             const int fl = far_flags(g, info, t0f, tendf, slab, warp);
@@ -932,12 +933,33 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
             f2_unpack(S1, s1a, s1b);
             f2_unpack(S2, s2a, s2b);
             float s1 = s1a + s1b, s2 = s2a + s2b;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            if ((li & 1) == 0 && li + 1 < nl) {
+                // hold an even line's lane sums; they are reduced together with the next line's
+                h1 = s1;
+                h2 = s2;
+                continue;
             }
-            if (lane == 0) s_red[li * GW + warp] = make_float2(s1, s2);
+            if (li & 1) {
+                // two lines at once: the first exchange leaves lanes 0-15 with partial sums of
+                // line li - 1 and lanes 16-31 with those of line li
+                const bool up = (lane & 16) != 0;
+                float k1 = up ? s1 : h1, k2 = up ? s2 : h2;
+                k1 += __shfl_xor_sync(0xffffffffu, up ? h1 : s1, 16);
+                k2 += __shfl_xor_sync(0xffffffffu, up ? h2 : s2, 16);
+#pragma unroll
+                for (int o = 8; o > 0; o >>= 1) {
+                    k1 += __shfl_xor_sync(0xffffffffu, k1, o);
+                    k2 += __shfl_xor_sync(0xffffffffu, k2, o);
+                }
+                if ((lane & 15) == 0) s_red[(li - (up ? 0 : 1)) * GW + warp] = make_float2(k1, k2);
+            } else {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                }
+                if (lane == 0) s_red[li * GW + warp] = make_float2(s1, s2);
+            }
         }
         __syncthreads();
         for (int li = tid; li < nl; li += nthr) {
