@@ -42,13 +42,15 @@ WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts
 TRAFFIC = {"k_line_bwd": (6.3973e9, "4c425f93e52e2362")}
 KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h")
 
-# Per-evaluation pipe work of the far-wing kernels, which evaluate every in-window cell:
-# one MUFU reciprocal per evaluation in every form, and FP32-pipe operations of 4 (forward)
-# or 7 (backward) in the reduced form used for lines >= 100 Doppler widths from the whole
-# tile (most cells of this workload), 7 / 14 in the full far-wing form.  With
-# 16 MUFU and 128 FP32 lanes per SM both kernels are MUFU-bound in the reduced form.
-OPS = {"line_fwd": {"mufu": 1, "fp32_reduced": 4, "fp32_full": 7},
-       "line_bwd": {"mufu": 1, "fp32_reduced": 7, "fp32_full": 14}}
+# Per-evaluation pipe work of the far-wing kernels, which evaluate every in-window cell.
+# Reduced form (lines >= 100 Doppler widths from the whole tile, most cells of this
+# workload), written in p = (1/u^2)(1/k^2): forward 3 FP32-pipe lane operations
+# (p, B1 + B2' p, accumulate), backward 6 (p, G p, two polynomials, two accumulations),
+# and one MUFU reciprocal per line and point shared by the DS = 6 depths of a warp.
+# Full far form: 7 / 13 FP32-pipe operations and 1 MUFU reciprocal.  With 128 FP32
+# lanes and 16 MUFU lanes per SM the FP32 pipe binds.
+OPS = {"line_fwd": {"fp32_reduced": 3, "fp32_full": 7, "mufu_reduced": 1.0 / 6, "mufu_full": 1},
+       "line_bwd": {"fp32_reduced": 6, "fp32_full": 13, "mufu_reduced": 1.0 / 6, "mufu_full": 1}}
 
 
 def parse():
@@ -350,7 +352,8 @@ def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None):
            "s_per_spectrum_fwd": ms * 1e-3, "evals_per_spectrum": evals, "evals_per_s": ws * evals / (ms * 1e-3),
            "create_s": t_create,
            "kernel_ms_per_step": {k: v[0] / args.broad_steps for k, v in kt.items() if v[1] > 0},
-           "far_fwd_ms": far_ms, "far_fwd_mufu_ops_per_s": evals / (far_ms * 1e-3)}
+           "far_fwd_ms": far_ms,
+           "far_fwd_fp32_ops_per_s": evals * OPS["line_fwd"]["fp32_reduced"] / (far_ms * 1e-3)}
     # plain FP64 GPU form on a slice of the same line list
     if not args.no_fp64:
         sl = I.wavelength_slice(prob, 600.0, 1200)
@@ -635,7 +638,7 @@ def main():
     peak_fp32_lanes = n_sm * 128 * clk_max * 1e6
     peak_mufu = pipe_peaks.get("mufu") or peak_mufu_lanes
     peak_fp32 = pipe_peaks.get("fp32") or peak_fp32_lanes
-    achieved = evals * ops["mufu"] / t_dom
+    achieved = evals * ops["fp32_reduced"] / t_dom
     total_k = sum(share.values())
     import hashlib
     h = hashlib.sha256()
@@ -646,21 +649,24 @@ def main():
     if kname in TRAFFIC and TRAFFIC[kname][1] == h.hexdigest()[:16]:
         traffic = TRAFFIC[kname][0]
     roofline = {
-        "bound": "alu", "kernel": kname + " (far wing)", "pipe": "mufu",
-        "achieved": achieved * 1e-9, "peak": peak_mufu * 1e-9, "unit": "Gop/s",
-        "frac": achieved / peak_mufu, "traffic": traffic,
-        "peak_source": ("measured: pz_probe_pipe rcp.approx throughput (%d SMs); 16-lane derivation %.0f Gop/s"
-                        % (n_sm, peak_mufu_lanes * 1e-9)) if pipe_peaks.get("mufu") else
-                       "derived: %d SMs x 16 MUFU lanes x %.0f MHz (max SM clock)" % (n_sm, clk_max),
+        "bound": "alu", "kernel": kname + " (far wing)", "pipe": "fp32",
+        "achieved": achieved * 1e-9, "peak": peak_fp32 * 1e-9, "unit": "Gop/s",
+        "frac": achieved / peak_fp32, "traffic": traffic,
+        "peak_source": ("measured: pz_probe_pipe packed-FMA throughput (%d SMs); 128-lane derivation %.0f Gop/s"
+                        % (n_sm, peak_fp32_lanes * 1e-9)) if pipe_peaks.get("fp32") else
+                       "derived: %d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (n_sm, clk_max),
         "pipe_peaks_measured": {k: v * 1e-9 for k, v in pipe_peaks.items()},
         "ops_per_eval": ops, "evals_per_s": evals / t_dom, "ms_per_launch": t_dom * 1e3,
-        "fp32_pipe_frac_range": [evals * ops["fp32_reduced"] / t_dom / peak_fp32,
-                                 evals * ops["fp32_full"] / t_dom / peak_fp32],
+        "fp32_pipe_frac_full_form": evals * ops["fp32_full"] / t_dom / peak_fp32,
+        "mufu_pipe_frac_reduced_form": evals * ops["mufu_reduced"] / t_dom / peak_mufu,
         "kernel_share": {k: round(v / total_k, 4) for k, v in share.items() if total_k > 0},
         "far_ms_per_launch": {k: v / max(ktimes[k][1], 1) for k, v in far.items()},
         "near_ms_per_launch": {k: ktimes[k][0] / max(ktimes[k][1], 1) for k in ("near_fwd", "near_bwd")},
         "hbm_gbs_peak": peaks.get("hbm_gbs"),
     }
+
+    if broad is not None and pipe_peaks.get("fp32"):
+        broad["far_fwd_fp32_frac"] = broad["far_fwd_fp32_ops_per_s"] / pipe_peaks["fp32"]
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,

@@ -589,9 +589,16 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
         const int nl = min(cp.LC, hi - (lo + c * cp.LC));
         const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
         const LineInfo *s_line = cp.info(k);
+        unsigned m_fast = 0u, m_red = 0u;   // this warp's flags of 32 lines, decided one line per lane
         for (int li = 0; li < nl; ++li) {
+            if ((li & 31) == 0) {
+                const int lj = li + lane;
+                const int f = lj < nl ? far_flags(g, s_line[lj], t0f, tendf, slab, warp) : 0;
+                m_fast = __ballot_sync(0xffffffffu, f & 1);
+                m_red = __ballot_sync(0xffffffffu, (f & 2) != 0);
+            }
             const LineInfo info = s_line[li];
-            const int fl = far_flags(g, info, t0f, tendf, slab, warp);
+            const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1);
             const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
             f2_t u2[J];
             if (fl & 1) {
@@ -895,9 +902,16 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
         const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
         const LineInfo *s_line = cp.info(k);
         float h1 = 0.0f, h2 = 0.0f;   // lane sums of the held even line
+        unsigned m_fast = 0u, m_red = 0u;   // this warp's flags of 32 lines, decided one line per lane
         for (int li = 0; li < nl; ++li) {
+            if ((li & 31) == 0) {
+                const int lj = li + lane;
+                const int f = lj < nl ? far_flags(g, s_line[lj], t0f, tendf, slab, warp) : 0;
+                m_fast = __ballot_sync(0xffffffffu, f & 1);
+                m_red = __ballot_sync(0xffffffffu, (f & 2) != 0);
+            }
             const LineInfo info = s_line[li];
-            const int fl = far_flags(g, info, t0f, tendf, slab, warp);
+            const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1);
             const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
             f2_t u2[J];
             if (fl & 1) {
