@@ -485,8 +485,10 @@ __device__ __forceinline__ void far_abort(const LineArgs &g, const ChunkPipe &cp
 }
 
 // Per-warp flags of a line over the tile: bit 0 if the line's window covers the tile
-// and every cell of the warp's slab is in the far wing (|v| >= 20); bit 1 if, in
-// addition, |v| >= 100 and a^2 <= kFast2A2 at every layer of the slab (reduced form).
+// and every cell of the warp's slab is in the far wing (|v| >= 20); bit 1 if every
+// cell of the slab has |v| >= 100 and a^2 <= kFast2A2 at every layer (reduced form),
+// whether or not the window covers the tile: the reduced form masks the window per
+// point at no cost per cell (a zero reciprocal 1/u^2).
 __device__ __forceinline__ int far_flags(const LineArgs &g, const LineInfo &info, float t0f, float tendf, int slab,
                                          int w) {
     const float dlo = info.ilf - t0f + info.frac;      // x_l - t0
@@ -495,7 +497,7 @@ __device__ __forceinline__ int far_flags(const LineArgs &g, const LineInfo &info
     const bool full = (info.ilf - (float)g.W <= t0f) && (info.ilf + (float)g.W >= tendf);
     const float thr = __ldg(g.thr + info.sp * g.nslab + slab);
     const bool fast = full && dmin >= thr;
-    const bool red = fast && dmin >= kFast2V * thr && ((info.amask >> w) & 1);
+    const bool red = dmin >= kFast2V * thr && ((info.amask >> w) & 1);
     return (fast ? 1 : 0) | (red ? 2 : 0);
 }
 
@@ -601,7 +603,7 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
             const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1);
             const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
             f2_t u2[J];
-            if (fl & 1) {
+            if (fl != 0) {
                 // the whole tile is in the line's far wing: offsets from the first point's,
                 // u_j = u_0 r^-j + (r^-j - 1), and their squares
                 const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
@@ -616,10 +618,20 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                 for (int j = 0; j < J; ++j) u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
             }
             if (fl & 2) {
-                // reduced form in p = (1/u^2)(1/k^2): B1 p + B2' p^2
+                // reduced form in p = (1/u^2)(1/k^2): B1 p + B2' p^2; points outside the
+                // window (lines whose window edge crosses the tile) get 1/u^2 = 0
                 f2_t sp[J];
+                if (fl & 1) {
 #pragma unroll
-                for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(u2[j])));
+                    for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(u2[j])));
+                } else {
+                    const int il = (int)info.ilf;
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const int di = lam_thr + j - il;
+                        sp[j] = f2_splat(di >= -g.W && di <= g.W ? rcp_approx(f2_lo(u2[j])) : 0.0f);
+                    }
+                }
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
                     // q0 = (1/k^2, a^2), q1 = (B1, B2')
@@ -773,15 +785,23 @@ __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int 
 }
 
 // Reduced far-wing backward form (lines flagged for it): H and dH/da polynomials cut
-// after their t^2 terms.  par: the warp's depth pairs, (k^2, a^2) (B1, B2) (C1, C2);
+// after their t^2 terms.  par: the warp's depth pairs, (1/k^2, a^2) (B1, B2') (C1, C2');
 // usq: the squared offsets u^2 of the thread's points.
 template <int J, int DP>
 __device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, const f2_t (&usq)[J],
-                                                     const f2_t (&gv)[DP][J], f2_t &S1, f2_t &S2) {
-    // reduced forms in p = (1/u^2)(1/k^2): G (B1 p + B2' p^2) and G (C1 p + C2' p^2)
+                                                     const f2_t (&gv)[DP][J], bool full, int di0, int W, f2_t &S1,
+                                                     f2_t &S2) {
+    // reduced forms in p = (1/u^2)(1/k^2): G (B1 p + B2' p^2) and G (C1 p + C2' p^2);
+    // points outside the window (di0 + j = i - i_l) get 1/u^2 = 0 unless it covers the tile
     f2_t sp[J];
+    if (full) {
 #pragma unroll
-    for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(usq[j])));
+        for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(usq[j])));
+    } else {
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            sp[j] = f2_splat(di0 + j >= -W && di0 + j <= W ? rcp_approx(f2_lo(usq[j])) : 0.0f);
+    }
 #pragma unroll
     for (int dp = 0; dp < DP; ++dp) {
         const ulonglong2 q0 = par[kNQB * dp], q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
@@ -914,7 +934,7 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
             const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1);
             const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
             f2_t u2[J];
-            if (fl & 1) {
+            if (fl != 0) {
                 const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
                 u2[0] = f2_splat(u0);
 #pragma unroll
@@ -927,7 +947,7 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
             }
             f2_t S1 = 0ull, S2 = 0ull;
             if (fl & 2) {
-                far_bwd_line_reduced<J, DP>(par, u2, gv, S1, S2);
+                far_bwd_line_reduced<J, DP>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W, S1, S2);
             } else if (fl & 1) {
                 far_bwd_line<J, DP, false>(par, u2, gv, nullptr, nullptr, S1, S2);
             } else {
