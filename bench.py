@@ -37,9 +37,9 @@ WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts
             "chi^2 vs synthetic target, gradients for 2e5 dlog_gf + 2e5 dlog_gamma6 + 20 abundances")
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# kernel on this workload (profiles/k_line_bwd_apogee.md: 6.313 GB read + 84.5 MB written, default
+# kernel on this workload (profiles/k_line_bwd_apogee.md: 6.479 GB read + 86.0 MB written, default
 # tiling), valid only while the kernel sources hash to the recorded value; otherwise null.
-TRAFFIC = {"k_line_bwd": (6.3973e9, "4c425f93e52e2362")}
+TRAFFIC = {"k_line_bwd": (6.5652e9, "3a0f98c915da3681")}
 KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h")
 
 # Per-evaluation pipe work of the far-wing kernels, which evaluate every in-window cell.
