@@ -195,10 +195,12 @@ def run_reference(args):
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
-    # size each step's slice so the whole run stays near two minutes of host time
-    _, t1, _ = oracle_sample(span_nm=1.0)
+    # size each step's slice so the whole run stays near two minutes of host time; the
+    # cost grows as span^2 (points x lines), and slices under 2 nm hold too few pixels
+    # whose instrument kernel fits inside the grid
+    _, t2, _ = oracle_sample(span_nm=2.0)
     budget = 120.0 / max(args.steps + args.warmup, 1)
-    span = min(4.0, max(0.5, math.sqrt(budget / t1)))
+    span = min(4.0, max(2.0, 2.0 * math.sqrt(budget / t2)))
     steps = []
     desc = ""
     ev = 0
