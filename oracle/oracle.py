@@ -40,6 +40,7 @@ class _Problem(C.Structure):
         ("log_gf", _fp), ("E_low_eV", _fp), ("log_gamma_rad", _fp), ("log_gamma4", _fp),
         ("log_gamma6", _fp), ("species", _ip), ("half_window", C.c_int32),
         ("dlog_gf", _dp), ("dlog_gamma6", _dp), ("dabund", _dp), ("elem_of_species", _ip),
+        ("centre_eta", C.c_double),
     ]
 
 
@@ -138,6 +139,8 @@ class _Keep:
                 A["eos"] = np.ascontiguousarray(prob.elem_of_species, np.int32)
                 P.dabund = _ptr(A["dab"], _dp)
                 P.elem_of_species = _ptr(A["eos"], _ip)
+            # continuum-referenced centre test (0 = off)
+            P.centre_eta = float(corrections.get("centre_eta") or 0.0)
         self.P = P
 
 

@@ -203,6 +203,8 @@ typedef struct {
     const double *dlog_gf, *dlog_gamma6;   /* [n_lines] */
     const double *dabund;                  /* [n_elem] */
     const int32_t *elem_of_species;        /* [n_species] */
+    /* continuum-referenced centre test: selection fraction eta (0 = every pair kept) */
+    double centre_eta;
 } pzo_problem;
 
 /* Eq. 1 */
@@ -258,9 +260,22 @@ static double stim_emission(const pzo_problem *P, int64_t i, int d) {
     return -expm1(-O_H * O_C / (grid_lambda_cm(P, i) * O_KB * P->T[d]));
 }
 
+/* Continuum-referenced centre test (Sec. 2.2: weak depth-line pairs are rejected against
+ * the continuum; the threshold form follows the selection fraction eta of Sec. 3.2).
+ * Reading: the pair (l, d) is kept when the peak of its term at its centre grid point,
+ * bounded with H(a, 0) <= 1, reaches eta times the continuum there:
+ *   (1 - exp(-h nu_ic / k T_d)) A_ld >= eta kappa_c(ic, d),  ic = i_l clipped to the grid.
+ * eta = 0 keeps every pair. */
+static int centre_keep(const pzo_problem *P, int64_t il, int d, double A) {
+    if (!(P->centre_eta > 0.0)) return 1;
+    int64_t ic = il < 0 ? 0 : (il > P->n_lambda - 1 ? P->n_lambda - 1 : il);
+    double peak = stim_emission(P, ic, d) * A;
+    return peak >= P->centre_eta * P->kappa_c[(int64_t)d * P->n_lambda + ic];
+}
+
 /* kappa_line(i, d) for the requested columns; out[d * n_cols + c].
  * Sum over every line whose window |i - i_l| <= W contains column i
- * (window clipped to the grid; centre test off). */
+ * (window clipped to the grid), over the pairs the centre test keeps. */
 void pzo_kappa_line(const pzo_problem *P, int64_t n_cols, const int64_t *cols, double *out) {
     int nd = P->n_depth;
     int64_t nl = P->n_lines;
@@ -282,6 +297,7 @@ void pzo_kappa_line(const pzo_problem *P, int64_t n_cols, const int64_t *cols, d
             double lam_l = P->lambda_nm[l] * 1e-7;
             for (int d = 0; d < nd; ++d) {
                 line_depth q = line_at_depth(P, l, d);
+                if (!centre_keep(P, il[l], d, q.A)) continue;
                 double v = (lam_l / lam_i - 1.0) * O_C / q.dvD;   /* (nu - nu_l)/dnu_D */
                 double H;
                 pzo_voigt(q.a, v, &H, NULL, NULL);
@@ -467,6 +483,7 @@ void pzo_line_grad(const pzo_problem *P, const double *G, double *g_gf, double *
         double sgf = 0.0, sg6 = 0.0;
         for (int d = 0; d < nd; ++d) {
             line_depth q = line_at_depth(P, l, d);
+            if (!centre_keep(P, il, d, q.A)) continue;
             for (int64_t i = i0; i <= i1; ++i) {
                 double v = (lam_l / grid_lambda_cm(P, i) - 1.0) * O_C / q.dvD;
                 double H, dH;

@@ -15,11 +15,34 @@ EV = 1.602176634e-12
 AMU = 1.66053906660e-24
 
 
-def brute_kappa(prob):
-    """Triple loop over (lambda, depth, line), written in frequency variables."""
+def centre_ratios(prob):
+    """Per (line, depth): the peak of the line's term at its centre grid point, bounded with
+    H <= 1, over the continuum there: stim(ic, d) A_ld / kappa_c(ic, d), ic = i_l clipped."""
+    at, ll, g = prob.atmos, prob.lines, prob.grid
+    r = 1.0 + 1.0 / g.R_grid
+    out = np.zeros((ll.n_lines, at.n_depth))
+    for l in range(ll.n_lines):
+        il = int(np.floor(np.log(ll.lambda_nm[l] / g.lambda0_nm) / np.log(r) + 0.5))
+        ic = min(max(il, 0), g.n_lambda - 1)
+        nu_c = C_ / (g.lambda0_nm * 1e-7 * r ** ic)
+        nu_l = C_ / (ll.lambda_nm[l] * 1e-7)
+        sp = ll.species[l]
+        for d in range(at.n_depth):
+            T = at.T[d]
+            dnu = nu_l * np.sqrt(2 * K_ * T / (at.mass_amu[sp] * AMU) + at.xi_cms ** 2) / C_
+            A = (np.pi * E_ ** 2 / (ME * C_)) * 10.0 ** float(ll.log_gf[l]) * at.pop[sp, d] / at.rho[d] \
+                * np.exp(-float(ll.E_low_eV[l]) * EV / (K_ * T)) / (np.sqrt(np.pi) * dnu)
+            out[l, d] = (1.0 - np.exp(-H_ * nu_c / (K_ * T))) * A / prob.kappa_c[d, ic]
+    return out
+
+
+def brute_kappa(prob, eta=0.0):
+    """Triple loop over (lambda, depth, line), written in frequency variables; with eta > 0
+    only the (line, depth) pairs whose centre ratio reaches eta."""
     at, ll, g = prob.atmos, prob.lines, prob.grid
     r = 1.0 + 1.0 / g.R_grid
     out = np.zeros((at.n_depth, g.n_lambda))
+    keep = centre_ratios(prob) >= eta if eta > 0 else np.ones((ll.n_lines, at.n_depth), bool)
     il = [int(np.floor(np.log(ll.lambda_nm[l] / g.lambda0_nm) / np.log(r) + 0.5)) for l in range(ll.n_lines)]
     for i in range(g.n_lambda):
         lam_i = g.lambda0_nm * 1e-7 * r ** i
@@ -28,7 +51,7 @@ def brute_kappa(prob):
             T = at.T[d]
             s = 0.0
             for l in range(ll.n_lines):
-                if abs(i - il[l]) > ll.half_window:
+                if abs(i - il[l]) > ll.half_window or not keep[l, d]:
                     continue
                 sp = ll.species[l]
                 nu_l = C_ / (ll.lambda_nm[l] * 1e-7)
@@ -114,3 +137,30 @@ def test_abundance_and_gf_corrections_scale(oracle):
     assert np.allclose(k1, base * 10 ** 0.3, rtol=1e-13, atol=0)
     k2 = oracle.kappa_line(prob, corrections={"dabund": np.full(prob.n_elem, -0.2)})
     assert np.allclose(k2, base * 10 ** -0.2, rtol=1e-13, atol=0)
+
+
+def test_centre_test_matches_brute_force(oracle):
+    """Continuum-referenced centre test: eta strictly between two pair ratios, so that no
+    pair sits on the threshold; about half of the (line, depth) pairs are rejected."""
+    prob = tiny_problem(seed=4)
+    ratios = np.unique(centre_ratios(prob))
+    k = ratios.size // 2
+    eta = float(np.sqrt(ratios[k - 1] * ratios[k]))
+    ref = brute_kappa(prob, eta)
+    got = oracle.kappa_line(prob, corrections={"centre_eta": eta})
+    full = oracle.kappa_line(prob)
+    assert np.all((got > 0) == (ref > 0))
+    m = ref > 0
+    # the oracle's Voigt is pinned to 2e-8 near the core; partial sums expose it
+    assert np.max(np.abs(got[m] / ref[m] - 1)) < 1e-8
+    assert np.any(got < full * (1 - 1e-6))          # the cut removed something
+
+
+def test_centre_test_limits(oracle):
+    prob = tiny_problem(seed=5)
+    full = oracle.forward(prob)
+    off = oracle.forward(prob, {"centre_eta": 0.0})
+    assert np.array_equal(off["kline"], full["kline"]) and np.array_equal(off["f"], full["f"])
+    none = oracle.forward(prob, {"centre_eta": 1e300})
+    assert np.all(none["kline"] == 0.0)
+    assert np.array_equal(none["F"], none["Fc"])
