@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default line-kernel tiling")
     ap.add_argument("--no-broad", action="store_true", help="skip the 300-1000 nm forward measurement")
     ap.add_argument("--broad-steps", type=int, default=3)
+    ap.add_argument("--no-centre", action="store_true", help="skip the centre-test measurement")
+    ap.add_argument("--centre-eta", type=float, default=1e-3)
     return ap.parse_args()
 
 
@@ -385,6 +387,80 @@ def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None):
     return out
 
 
+def run_centre(args, dev, barrier, max_over_ranks, ws, tiling=None):
+    """The continuum-referenced centre test at the paper's selection fraction 1e-3: the
+    APOGEE-like fwd+bwd step and the 300-1000 nm forward with the test on, the fraction
+    of (line, depth) pairs kept, and the change of the normalised flux against the
+    uncut sum (the headline numbers above are the uncut sum)."""
+    import numpy as np
+    import torch
+
+    import paper_2607_24141_gb300 as pz
+    from paper_2607_24141_gb300 import inputs as I
+    stream = torch.cuda.current_stream()
+    eta = args.centre_eta
+    out = {"eta": eta}
+
+    def timed(fn, k):
+        barrier()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return max_over_ranks(a.elapsed_time(b)) / k
+
+    for name, prob, steps, grad in (("apogee_fwdbwd", I.config1(seed=1), 10, True),
+                                    ("broad_fwd", I.config2(), 2, False)):
+        s = pz.Synthesizer(prob, pz.PZ_MIXED, device=dev.index)
+        if tiling is not None:
+            pz.pz_set_tiling(s.ctx, *tiling)
+        f_full = s.forward().cpu().numpy().astype(np.float64)
+        kept = pz.pz_set_centre_test(s.ctx, eta, stream)
+        n_out = f_full.size
+        f = torch.empty(n_out, dtype=torch.float32, device=dev)
+        inst = prob.instrument
+
+        def fwd():
+            pz.pz_line_opacity(s.ctx, None, stream)
+            pz.pz_flux(s.ctx, None, None, stream)
+            if inst is None:
+                pz.pz_instrument(s.ctx, 0.0, 0.0, 0.0, None, f, stream)
+            else:
+                pz.pz_instrument(s.ctx, inst.v_r_kms, inst.v_b_kms, inst.R_lsf, inst.pix_lambda_nm, f, stream)
+
+        fwd()
+        f_cut = f.cpu().numpy().astype(np.float64)
+        rec = {"kept_pair_fraction": kept / float(prob.lines.n_lines * prob.atmos.n_depth),
+               "max_abs_df_vs_uncut": float(np.max(np.abs(f_cut - f_full))),
+               "rms_df_vs_uncut": float(np.sqrt(np.mean((f_cut - f_full) ** 2)))}
+        rec["s_fwd"] = timed(fwd, steps) * 1e-3
+        if grad:
+            nl = prob.lines.n_lines
+            y = torch.tensor(f_full.astype(np.float32), device=dev)
+            w = torch.full_like(y, 200.0 ** 2)
+            loss = torch.zeros(1, dtype=torch.float64, device=dev)
+            dLdf = torch.empty_like(y)
+            g1 = torch.empty(nl, dtype=torch.float32, device=dev)
+            g2 = torch.empty(nl, dtype=torch.float32, device=dev)
+
+            def step():
+                fwd()
+                pz.pz_loss_chi2(s.ctx, y, w, loss, dLdf, stream)
+                pz.pz_backward(s.ctx, dLdf, g1, g2, None, stream)
+
+            step()
+            rec["s_fwdbwd"] = timed(step, steps) * 1e-3
+        pz.pz_sync_status(s.ctx, stream)
+        s.close()
+        out[name] = rec
+    return out
+
+
 def fp64_batch_rate(dev):
     """Evaluations per second of the plain FP64 GPU form on one graph-captured
     calibration step (fwd + bwd) of a 3-star, 2 nm batch of the same recipe."""
@@ -667,6 +743,11 @@ def main():
         "hbm_gbs_peak": peaks.get("hbm_gbs"),
     }
 
+    # ---- continuum-referenced centre test (the paper's line rejection) ----
+    centre = None
+    if not args.no_centre:
+        centre = run_centre(args, dev, barrier, max_over_ranks, ws, tune["tiling"] if tune else None)
+
     if broad is not None and pipe_peaks.get("fp32"):
         broad["far_fwd_fp32_frac"] = broad["far_fwd_fp32_ops_per_s"] / pipe_peaks["fp32"]
 
@@ -685,6 +766,7 @@ def main():
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
         "batched": batched,
         "broad_optical_fwd": broad,
+        "centre_test": centre,
         "autotune": tune,
     }
     if rank == 0:

@@ -134,6 +134,24 @@ pz_status pz_set_corrections(pz_ctx *ctx, const float *dlog_gf, const float *dlo
                              const float *dabund, const int32_t *elem_of_species, int32_t n_elem,
                              void *stream);
 
+/* Continuum-referenced centre test.  The paper's line opacity rejects weak
+ * depth-line pairs against the continuum (Sec. 2.2) and applies its line keep test
+ * once per atmosphere with a fixed selection fraction (Sec. 3.2).  Here, with
+ * eta > 0, the pair (l, d) is kept when the peak of its term at its centre grid
+ * point ic (i_l clipped to the grid), bounded with H(a, 0) <= 1, reaches eta times
+ * the continuum there:
+ *   (1 - e^{-h nu_ic / k T_d}) A_ld >= eta kappa_c(ic, d),
+ *   A_ld = (pi e^2/m_e c) gf n/(rho U) e^{-E/kT} / (sqrt(pi) dnu_D)   (Eq. 4),
+ * decided once, in FP64 on the device, with the corrections set at the time of
+ * this call; the selection is then fixed until the next call (later corrections
+ * change the kept terms' values, not which pairs are kept).  Every later line
+ * opacity (both forms) and reverse pass sums only the kept pairs.  eta = 0 turns
+ * the test off.  kept_pairs (host, may be NULL): the number of kept (line, depth)
+ * pairs, over n_lines x n_depth (synchronises `stream` when not NULL).
+ * The forward must run again before pz_flux (PZ_ESTATE otherwise).
+ * Errors: PZ_EINVAL for a negative or non-finite eta; PZ_ENOMEM; PZ_ECUDA. */
+pz_status pz_set_centre_test(pz_ctx *ctx, double eta, int64_t *kept_pairs, void *stream);
+
 /* Line opacity kappa_line(lambda_i, d) = (1 - e^{-h nu_i/kT_d})
  *   sum_{l : |i - i_l| <= W} (pi e^2/m_e c) gf_l (n_{s,d}/(rho_d U_s)) e^{-E_l/kT_d}
  *   H(a_ld, v_ild) / (sqrt(pi) dnu_D,ld)              (Eqs. 4-5)

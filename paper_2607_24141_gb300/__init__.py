@@ -71,6 +71,7 @@ _SIGS = {
     "pz_last_launch_count": (C.c_int32, [_vp]),
     "pz_set_tiling": (C.c_int, [_vp, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32]),
     "pz_autotune": (C.c_int, [_vp, C.c_int32, C.c_int32, _vp, _vp, _vp]),
+    "pz_set_centre_test": (C.c_int, [_vp, C.c_double, C.POINTER(C.c_int64), _vp]),
     "pz_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "pz_kernel_times": (C.c_int, [_vp, _dp, C.POINTER(C.c_int64), C.c_int32]),
     "pz_abundance_grad_noalloc": (C.c_int, [_vp, _vp, _vp, C.c_int64, C.c_int32, C.c_int32, _vp, _vp]),
@@ -242,6 +243,14 @@ def pz_last_launch_count(ctx) -> int:
 
 def pz_set_tiling(ctx, lambda_per_thread=0, depth_per_warp=0, warps_per_cta=0, lines_per_chunk=0, ctas_per_sm=0):
     _check(load().pz_set_tiling(ctx, lambda_per_thread, depth_per_warp, warps_per_cta, lines_per_chunk, ctas_per_sm))
+
+
+def pz_set_centre_test(ctx, eta, stream=None) -> int:
+    """Continuum-referenced centre test with selection fraction eta (0 = off); returns
+    the number of kept (line, depth) pairs."""
+    n = C.c_int64(0)
+    _check(load().pz_set_centre_test(ctx, float(eta), C.byref(n), _stream(stream)))
+    return n.value
 
 
 def pz_autotune(ctx, with_backward=True, reps=2, stream=None):

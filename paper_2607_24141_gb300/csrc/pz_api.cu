@@ -226,7 +226,8 @@ static void destroy_ctx(pz_ctx *c) {
                     c->L.Q, c->L.Qbase, c->L.x64, c->L.lg_gf, c->L.lg_rad, c->L.lg_4, c->L.lg_6, c->L.dgf, c->L.dg6,
                     c->d_line_off, c->d_fitems, c->d_nitems_f, c->d_nitems_b, c->d_ctr, c->d_knear, c->d_kline,
                     c->d_F, c->d_Fc, c->d_g, c->d_gc, c->d_tap0, c->d_ntap, c->d_tapw, c->d_dFbar, c->d_Gt,
-                    c->d_Gt64, c->d_gacc, c->d_gline, c->d_gab, c->d_dLdf, c->d_ftab, c->d_finfo, c->d_status};
+                    c->d_Gt64, c->d_gacc, c->d_gline, c->d_gab, c->d_dLdf, c->d_ftab, c->d_finfo, c->d_status,
+                    c->d_keep};
     for (void *p : ptrs) dfree(p);
     for (auto &m : c->marks) {
         cudaEventDestroy(m.a);
@@ -734,6 +735,43 @@ pz_status pz_autotune(pz_ctx *c, int32_t with_backward, int32_t reps, int32_t *b
         best_ms[0] = cf;
         best_ms[1] = cb;
     }
+    return PZ_OK;
+}
+
+pz_status pz_set_centre_test(pz_ctx *c, double eta, int64_t *kept_pairs, void *stream) {
+    if (!c) return fail(PZ_EINVAL, "pz_set_centre_test: ctx is NULL");
+    if (!(std::isfinite(eta) && eta >= 0.0)) return fail(PZ_EINVAL, "pz_set_centre_test: eta must be finite and >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    drop_graph(c);
+    c->have_kline = c->have_flux = c->have_inst = false;
+    if (eta == 0.0) {
+        PZ_CUDA(cudaStreamSynchronize(s), "pz_set_centre_test");
+        dfree(c->d_keep);
+        c->d_keep = nullptr;
+        c->centre_eta = 0.0;
+        if (kept_pairs) *kept_pairs = c->L.n * (int64_t)c->nd;
+        return PZ_OK;
+    }
+    const size_t words = (size_t)std::max<int64_t>(c->L.n, 1) * kKeepWords;
+    if (!c->d_keep) PZ_TRY(dalloc(&c->d_keep, words, "centre-test mask"));
+    PZ_CUDA(cudaMemsetAsync(c->d_keep, 0, sizeof(uint32_t) * words, s), "pz_set_centre_test");
+    unsigned long long *d_cnt = nullptr;
+    if (kept_pairs) {
+        PZ_TRY(dalloc(&d_cnt, 1, "pz_set_centre_test"));
+        PZ_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), s), "pz_set_centre_test");
+    }
+    pz_status st = cuda_check(launch_centre_mask(c, eta, d_cnt, s), "pz_set_centre_test");
+    c->launches = 1;
+    if (st == PZ_OK && kept_pairs) {
+        unsigned long long h = 0;
+        if ((st = cuda_check(cudaMemcpyAsync(&h, d_cnt, sizeof(h), cudaMemcpyDeviceToHost, s), "pz_set_centre_test")) ==
+            PZ_OK)
+            st = cuda_check(cudaStreamSynchronize(s), "pz_set_centre_test");
+        *kept_pairs = (int64_t)h;
+    }
+    dfree(d_cnt);
+    if (st != PZ_OK) return st;
+    c->centre_eta = eta;
     return PZ_OK;
 }
 

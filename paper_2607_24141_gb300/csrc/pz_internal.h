@@ -168,6 +168,8 @@ struct pz_ctx {
     void *d_finfo = nullptr;             // far-wing line records
     size_t ftab_cap = 0, finfo_cap = 0;  // their sizes in bytes
     int32_t *d_status = nullptr;         // device status word (bounded-wait failures), read by pz_sync_status
+    uint32_t *d_keep = nullptr;          // centre test: bit d of word [l][d / 32] set if (l, d) is kept; NULL = off
+    double centre_eta = 0.0;             // its selection fraction (0 = off)
     int32_t launches = 0;
     pz::StepGraph graph;
     cudaStream_t cap_stream = nullptr;   // private stream the step graph is captured on
@@ -222,6 +224,8 @@ cudaError_t launch_probe_expn(const double *x, int64_t n, double *out, cudaStrea
 constexpr int kProbeThreads = 256;   // threads per CTA of the pipe-throughput probe
 cudaError_t launch_probe_pipe(int kind, int iters, int blocks, float *out, cudaStream_t s);
 cudaError_t launch_probe_wait(uint64_t limit_ns, int32_t *status, cudaStream_t s);
+constexpr int kKeepWords = kMaxDepth / 32;   // centre-test mask words per line
+cudaError_t launch_centre_mask(pz_ctx *c, double eta, unsigned long long *d_count, cudaStream_t s);
 bool tiling_supported(int J, int DS, int minb);
 bool tiling_fits(const Tiling &t);   // both far-wing chunks fit in shared memory
 size_t far_table_bytes(const pz_ctx *c);   // far-wing table bytes for the current tiling

@@ -156,7 +156,13 @@ struct LineArgs {
     const float4 *ftab;                             // far-wing prefactor table (k_far_table)
     const LineInfo *finfo;                          // far-wing line records
     int *status;                                    // device status word (bounded-wait failures)
+    const uint32_t *keep;                           // centre-test mask [nl][kKeepWords] or NULL (all kept)
 };
+
+// Centre-test decision of the pair (l, d): kept unless a mask is set and its bit is clear.
+__device__ __forceinline__ bool pair_kept(const uint32_t *keep, int64_t l, int d) {
+    return !keep || ((keep[l * kKeepWords + (d >> 5)] >> (d & 31)) & 1u);
+}
 
 __device__ __forceinline__ LineArgs star_view(const LineArgs &g, int s) {
     LineArgs v = g;
@@ -369,6 +375,9 @@ __global__ void k_far_table(LineArgs gq, int DC, int DS, int ngroups, float4 *ta
         float p0[16], p1[16];
         depth_params<NQ == kNQB ? 16 : 8>(g, L, d, p0);
         depth_params<NQ == kNQB ? 16 : 8>(g, L, d + 1, p1);
+        // pairs rejected by the centre test contribute nothing: zero strength coefficients
+        if (!pair_kept(g.keep, l, d)) p0[2] = p0[3] = p0[8] = p0[9] = 0.0f;
+        if (!pair_kept(g.keep, l, d + 1)) p1[2] = p1[3] = p1[8] = p1[9] = 0.0f;
         float4 *dst = tab + gl * (P * NQ) + pr * NQ;
         // 1/k^2 (0 on the padding layers past the last one, whose coefficients are 0)
         const float ik0 = p0[0] > 0.0f ? 1.0f / (p0[0] * p0[0]) : 0.0f;
@@ -379,15 +388,18 @@ __global__ void k_far_table(LineArgs gq, int DC, int DS, int ngroups, float4 *ta
         if (NQ == kNQB)
             dst[2] = make_float4(p0[8], p1[8], fmaf(-p0[8], p0[1], p0[9]), fmaf(-p1[8], p1[1], p1[9]));
         if (pr == 0) {
+            // bit w: a^2 <= kFast2A2 on every layer of slab w; bit 8 + w: the centre test
+            // rejects every layer of slab w (its warp skips the line)
             int amask = 0;
             for (int w = 0; w < DC / DS; ++w) {
-                bool ok = true;
+                bool ok = true, none = true;
                 for (int dd = grp * DC + w * DS; dd < min(grp * DC + (w + 1) * DS, g.nd); ++dd) {
                     float q[16];
                     depth_params<8>(g, L, dd, q);
                     ok = ok && q[1] <= kFast2A2;
+                    none = none && !pair_kept(g.keep, l, dd);
                 }
-                amask |= ok ? 1 << w : 0;
+                amask |= (ok ? 1 << w : 0) | (none ? 1 << (8 + w) : 0);
             }
             LineInfo r;
             r.ilf = g.ilf[l];
@@ -484,7 +496,8 @@ __device__ __forceinline__ void far_abort(const LineArgs &g, const ChunkPipe &cp
     __syncthreads();
 }
 
-// Per-warp flags of a line over the tile: bit 0 if the line's window covers the tile
+// Per-warp flags of a line over the tile (4: every layer of the slab rejected by the
+// centre test, nothing to evaluate): bit 0 if the line's window covers the tile
 // and every cell of the warp's slab is in the far wing (|v| >= 20); bit 1 if every
 // cell of the slab has |v| >= 100 and a^2 <= kFast2A2 at every layer (reduced form),
 // whether or not the window covers the tile: the reduced form masks the window per
@@ -495,6 +508,7 @@ __device__ __forceinline__ int far_flags(const LineArgs &g, const LineInfo &info
     const float dhi = info.ilf - tendf + info.frac;    // x_l - (t0 + T - 1)
     const float dmin = fmaxf(0.0f, fmaxf(-dlo, dhi));
     const bool full = (info.ilf - (float)g.W <= t0f) && (info.ilf + (float)g.W >= tendf);
+    if ((info.amask >> (8 + w)) & 1) return 4;        // the centre test rejects the whole slab
     const float thr = __ldg(g.thr + info.sp * g.nslab + slab);
     const bool fast = full && dmin >= thr;
     const bool red = dmin >= kFast2V * thr && ((info.amask >> w) & 1);
@@ -591,16 +605,18 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
         const int nl = min(cp.LC, hi - (lo + c * cp.LC));
         const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
         const LineInfo *s_line = cp.info(k);
-        unsigned m_fast = 0u, m_red = 0u;   // this warp's flags of 32 lines, decided one line per lane
+        unsigned m_fast = 0u, m_red = 0u, m_skip = 0u;   // this warp's flags of 32 lines, one line per lane
         for (int li = 0; li < nl; ++li) {
             if ((li & 31) == 0) {
                 const int lj = li + lane;
                 const int f = lj < nl ? far_flags(g, s_line[lj], t0f, tendf, slab, warp) : 0;
                 m_fast = __ballot_sync(0xffffffffu, f & 1);
                 m_red = __ballot_sync(0xffffffffu, (f & 2) != 0);
+                m_skip = __ballot_sync(0xffffffffu, (f & 4) != 0);
             }
             const LineInfo info = s_line[li];
             const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1);
+            if ((m_skip >> (li & 31)) & 1u) continue;        // every layer rejected by the centre test
             const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
             f2_t u2[J];
             if (fl != 0) {
@@ -922,46 +938,52 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
         const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
         const LineInfo *s_line = cp.info(k);
         float h1 = 0.0f, h2 = 0.0f;   // lane sums of the held even line
-        unsigned m_fast = 0u, m_red = 0u;   // this warp's flags of 32 lines, decided one line per lane
+        unsigned m_fast = 0u, m_red = 0u, m_skip = 0u;   // this warp's flags of 32 lines, one line per lane
         for (int li = 0; li < nl; ++li) {
             if ((li & 31) == 0) {
                 const int lj = li + lane;
                 const int f = lj < nl ? far_flags(g, s_line[lj], t0f, tendf, slab, warp) : 0;
                 m_fast = __ballot_sync(0xffffffffu, f & 1);
                 m_red = __ballot_sync(0xffffffffu, (f & 2) != 0);
+                m_skip = __ballot_sync(0xffffffffu, (f & 4) != 0);
             }
             const LineInfo info = s_line[li];
             const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1);
             const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
-            f2_t u2[J];
-            if (fl != 0) {
-                const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
-                u2[0] = f2_splat(u0);
-#pragma unroll
-                for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j]));
-#pragma unroll
-                for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < J; ++j) u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
-            }
             f2_t S1 = 0ull, S2 = 0ull;
-            if (fl & 2) {
-                far_bwd_line_reduced<J, DP>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W, S1, S2);
-            } else if (fl & 1) {
-                far_bwd_line<J, DP, false>(par, u2, gv, nullptr, nullptr, S1, S2);
-            } else {
-                // line near the tile or partly outside its window: far cells inside the window only
-                bool inwin[J];
-                const int il = (int)info.ilf;
+            // (a slab whose every layer the centre test rejects keeps zero sums; it still takes
+            // part in the pairwise reduction below)
+            if (!((m_skip >> (li & 31)) & 1u)) {
+                f2_t u2[J];
+                if (fl != 0) {
+                    const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
+                    u2[0] = f2_splat(u0);
 #pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    const int di = lam_thr + j - il;
-                    inwin[j] = di >= -g.W && di <= g.W;
+                    for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j]));
+#pragma unroll
+                    for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < J; ++j)
+                        u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
                 }
-                f2_t kp[DP];
-                far_kpairs<DP>(g, info.sp, d0 + warp * DS, kp);
-                far_bwd_line<J, DP, true>(par, u2, gv, inwin, kp, S1, S2);
+                if (fl & 2) {
+                    far_bwd_line_reduced<J, DP>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W, S1, S2);
+                } else if (fl & 1) {
+                    far_bwd_line<J, DP, false>(par, u2, gv, nullptr, nullptr, S1, S2);
+                } else {
+                    // line near the tile or partly outside its window: far cells inside the window only
+                    bool inwin[J];
+                    const int il = (int)info.ilf;
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const int di = lam_thr + j - il;
+                        inwin[j] = di >= -g.W && di <= g.W;
+                    }
+                    f2_t kp[DP];
+                    far_kpairs<DP>(g, info.sp, d0 + warp * DS, kp);
+                    far_bwd_line<J, DP, true>(par, u2, gv, inwin, kp, S1, S2);
+                }
             }
             float s1a, s1b, s2a, s2b;
             f2_unpack(S1, s1a, s1b);
@@ -1142,7 +1164,7 @@ __device__ __forceinline__ void near_sweep(const LineArgs &g, int t0, int64_t nl
             item.dlb = dl | ((int)(it / ndg) << 8);
             const float k = (float)kC * __ldg(g.invdv + g.sp[l] * g.nd + d);
             int lo, hi;
-            if (near_span(g, item.ilf, item.frac, k, 0.0f, t0, T, lo, hi)) {
+            if (pair_kept(g.keep, l, d) && near_span(g, item.ilf, item.frac, k, 0.0f, t0, T, lo, hi)) {
                 float p[16];
                 line_params<D ? 16 : 8>(g, l, d, p);
                 if (near_span(g, item.ilf, item.frac, p[0], p[1], t0, T, lo, hi)) {
@@ -1295,6 +1317,7 @@ static LineArgs make_args(pz_ctx *c) {
     g.ftab = reinterpret_cast<const float4 *>(c->d_ftab);
     g.finfo = reinterpret_cast<const LineInfo *>(c->d_finfo);
     g.status = c->d_status;
+    g.keep = c->d_keep;
     g.lam0cm = (float)(c->lambda0_nm * 1e-7);
     g.ilf = c->L.ilf;
     g.frac = c->L.frac;
@@ -1524,6 +1547,8 @@ struct Fp64Args {
     double *kline;           // [S][nd][ld]
     const double *Gt;        // [S][nd][ld]
     double *gacc;
+    const uint32_t *keep;    // centre-test mask [nl][kKeepWords] or NULL (all kept)
+    const double *kc;        // [S][nd][ld] continuum opacity (centre test)
 };
 
 struct LineTerm64 {
@@ -1569,6 +1594,7 @@ __global__ void k_line_fwd_fp64(Fp64Args g) {
     const int64_t l1 = lower_bound_i32(g.il, b0, b1, (int32_t)(i + g.W + 1));
     double sum = 0.0;
     for (int64_t l = l0; l < l1; ++l) {
+        if (!pair_kept(g.keep, l, d)) continue;
         LineTerm64 q = term64(g, l, st, d);
         double u = expm1((g.x64[l] - (double)i) * g.lnr);   // lambda_l/lambda_i - 1
         double H, dH;
@@ -1584,7 +1610,7 @@ __global__ void k_line_fwd_fp64(Fp64Args g) {
 __global__ void k_line_bwd_fp64(Fp64Args g) {
     const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int d = blockIdx.y;
-    if (l >= g.nl) return;
+    if (l >= g.nl || !pair_kept(g.keep, l, d)) return;
     const int st = g.star[l];
     LineTerm64 q = term64(g, l, st, d);
     const int64_t il = g.il[l];
@@ -1637,7 +1663,42 @@ static Fp64Args make_args64(pz_ctx *c) {
     g.kline = (double *)c->d_kline;
     g.Gt = c->d_Gt64;
     g.gacc = c->d_gacc;
+    g.keep = c->d_keep;
+    g.kc = c->d_kc;
     return g;
+}
+
+// Centre-test mask, once per call of pz_set_centre_test, in FP64 (the decision is the
+// same rule as the FP64 oracle's): the pair (l, d) is kept when the peak of its term at
+// its centre grid point ic (i_l clipped to the grid), bounded with H(a, 0) <= 1,
+// reaches eta times the continuum there:
+//   (1 - exp(-h c / (lambda_ic k T_d))) A_ld >= eta kappa_c(ic, d).
+// One thread per (line, depth); kept pairs set their bit and are counted.
+__global__ void k_centre_mask(Fp64Args g, double eta, uint32_t *keep, unsigned long long *count) {
+    const int64_t n = g.nl * g.nd;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t l = k / g.nd;
+        const int d = (int)(k - l * g.nd);
+        const int st = g.star[l];
+        const LineTerm64 q = term64(g, l, st, d);
+        const int64_t ic = min(max((int64_t)g.il[l], (int64_t)0), g.nlam - 1);
+        const double lam = g.lam0cm * exp((double)ic * g.lnr);
+        const double stim = -expm1(-kC2 / (lam * g.T[(int64_t)st * g.nd + d]));
+        const double kc = g.kc[((int64_t)st * g.nd + d) * g.ld + ic];
+        if (stim * q.A >= eta * kc) {
+            atomicOr(keep + l * kKeepWords + (d >> 5), 1u << (d & 31));
+            if (count) atomicAdd(count, 1ull);
+        }
+    }
+}
+
+cudaError_t launch_centre_mask(pz_ctx *c, double eta, unsigned long long *d_count, cudaStream_t s) {
+    Fp64Args g = make_args64(c);
+    const int64_t n = c->L.n * (int64_t)c->nd;
+    if (n == 0) return cudaSuccess;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)std::max(c->n_sm, 1) * 32);
+    k_centre_mask<<<grid, 256, 0, s>>>(g, eta, c->d_keep, d_count);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_line_fwd_fp64(pz_ctx *c, cudaStream_t s) {
