@@ -4,9 +4,11 @@ TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py``.  The product path never imports it.
 
 The wrapper only marshals numpy arrays; every arithmetic step of the oracle is
-in the C file, except two plain numpy steps that are themselves definitions:
-applying the instrument's banded weights (a weighted sum over taps) and the
-species-to-element sum of per-line gradients.
+in the C file, except plain numpy steps that are themselves definitions:
+applying the instrument's banded weights (a weighted sum over taps), the
+species-to-element sum of per-line gradients, the linked correction groups of
+Sec. 6 (a group's correction copied to its members, member gradients summed per
+group) and the greedy grouping pass that forms them (a plain loop over seeds).
 """
 from __future__ import annotations
 
@@ -41,6 +43,7 @@ class _Problem(C.Structure):
         ("log_gamma6", _fp), ("species", _ip), ("half_window", C.c_int32),
         ("dlog_gf", _dp), ("dlog_gamma6", _dp), ("dabund", _dp), ("elem_of_species", _ip),
         ("centre_eta", C.c_double),
+        ("dlog_gamma_rad", _dp), ("dlog_gamma4", _dp),
     ]
 
 
@@ -73,7 +76,7 @@ def lib():
                                           C.c_int64, _dp, _lp, _ip, _dp, C.c_int32]
         L.pzo_instrument_taps.restype = C.c_int
         L.pzo_rt_adjoint.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
-        L.pzo_line_grad.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
+        L.pzo_line_grad.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp, _dp, _dp]
         L.pzo_chi2.argtypes = [C.c_int64, _dp, _dp, _dp, _dp]
         L.pzo_chi2.restype = C.c_double
         L.pzo_flux_tau.argtypes = [C.c_int, _dp, _dp]
@@ -134,6 +137,10 @@ class _Keep:
             if corrections.get("dlog_gamma6") is not None:
                 A["dg6"] = _d(corrections["dlog_gamma6"])
                 P.dlog_gamma6 = _ptr(A["dg6"], _dp)
+            for key, field in (("dlog_gamma_rad", "dlog_gamma_rad"), ("dlog_gamma4", "dlog_gamma4")):
+                if corrections.get(key) is not None:
+                    A[key] = _d(corrections[key])
+                    setattr(P, field, _ptr(A[key], _dp))
             if corrections.get("dabund") is not None:
                 A["dab"] = _d(corrections["dabund"])
                 A["eos"] = np.ascontiguousarray(prob.elem_of_species, np.int32)
@@ -275,9 +282,70 @@ def gradient(prob, y, w, corrections=None, fwd=None):
     lib().pzo_rt_adjoint(C.byref(k.P), _ptr(kl, _dp), _ptr(_d(dLdF), _dp), _ptr(G, _dp))
     ggf = np.empty(prob.lines.n_lines)
     gg6 = np.empty(prob.lines.n_lines)
-    lib().pzo_line_grad(C.byref(k.P), _ptr(G, _dp), _ptr(ggf, _dp), _ptr(gg6, _dp))
+    grad = np.empty(prob.lines.n_lines)
+    gg4 = np.empty(prob.lines.n_lines)
+    lib().pzo_line_grad(C.byref(k.P), _ptr(G, _dp), _ptr(ggf, _dp), _ptr(gg6, _dp), _ptr(grad, _dp), _ptr(gg4, _dp))
     gab = None
     if prob.elem_of_species is not None:
         gab = np.zeros(prob.n_elem)
         np.add.at(gab, prob.elem_of_species[prob.lines.species], ggf)
+    fwd["g_gamma_rad"], fwd["g_gamma4"] = grad, gg4
     return L, ggf, gg6, gab, fwd
+
+
+def gradient4(prob, y, w, corrections=None, fwd=None):
+    """The four per-line gradients of Eq. 10 (gf and the three damping families):
+    {"L", "gf", "gamma_rad", "gamma4", "gamma6", "abund", "fwd"}."""
+    L, ggf, gg6, gab, fwd = gradient(prob, y, w, corrections, fwd)
+    return {"L": L, "gf": ggf, "gamma_rad": fwd["g_gamma_rad"], "gamma4": fwd["g_gamma4"], "gamma6": gg6,
+            "abund": gab, "fwd": fwd}
+
+
+# ---------------------------------------------------------------------------
+# linked correction groups (Sec. 6, Eq. 10 with q(l))
+# ---------------------------------------------------------------------------
+
+def expand_groups(x_group, group_of_line):
+    """Per-line corrections delta_{q(l)}: x_group [..., n_groups] -> [..., n_lines];
+    lines with q(l) = -1 take no correction."""
+    x_group = np.asarray(x_group, np.float64)
+    q = np.asarray(group_of_line, np.int64)
+    out = np.zeros(x_group.shape[:-1] + (q.size,))
+    m = q >= 0
+    out[..., m] = x_group[..., q[m]]
+    return out
+
+
+def group_sum(g_line, group_of_line, n_groups):
+    """dL/ddelta_q = sum over the members l of q of dL/ddelta_l (chain rule through the copy)."""
+    g_line = np.asarray(g_line, np.float64)
+    q = np.asarray(group_of_line, np.int64)
+    out = np.zeros(g_line.shape[:-1] + (int(n_groups),))
+    m = q >= 0
+    for k in np.nonzero(m)[0]:
+        out[..., q[k]] += g_line[..., k]
+    return out
+
+
+def build_line_groups(lambda_nm, E_low_eV, species, strength, dE_eV, dlam_nm):
+    """Greedy strength-ordered grouping (Sec. 6): take the lines from the strongest down
+    (equal strengths by index); a line not yet grouped opens a new group and takes every
+    line not yet grouped of the same species (ion stage included) whose lower-level energy
+    is within dE_eV of its own and whose wavelength is within dlam_nm of its own.  Groups
+    are numbered in the order they open.  Returns (group_of_line int32, n_groups)."""
+    lam = np.asarray(lambda_nm, np.float64)
+    E = np.asarray(E_low_eV, np.float32).astype(np.float64)
+    sp = np.asarray(species, np.int64)
+    st = np.asarray(strength, np.float32)
+    n = lam.size
+    order = sorted(range(n), key=lambda k: (-float(st[k]), k))
+    q = np.full(n, -1, np.int32)
+    G = 0
+    for s in order:
+        if q[s] >= 0:
+            continue
+        q[s] = G
+        free = (q < 0) & (sp == sp[s]) & (np.abs(E - E[s]) <= dE_eV) & (np.abs(lam - lam[s]) <= dlam_nm)
+        q[free] = G
+        G += 1
+    return q, G

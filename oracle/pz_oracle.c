@@ -205,6 +205,8 @@ typedef struct {
     const int32_t *elem_of_species;        /* [n_species] */
     /* continuum-referenced centre test: selection fraction eta (0 = every pair kept) */
     double centre_eta;
+    /* the other two damping families of Eq. 10 (radiative, Stark); NULL means zero */
+    const double *dlog_gamma_rad, *dlog_gamma4;   /* [n_lines] */
 } pzo_problem;
 
 /* Eq. 1 */
@@ -228,6 +230,8 @@ typedef struct {
     double A;        /* (pi e^2/m_e c) gf n/(rho U) e^{-E/kT} / (sqrt(pi) dnu_D) */
     double a;        /* damping parameter */
     double a6;       /* van der Waals part of a (for d a / d Delta log gamma_6 = ln10 a6) */
+    double arad;     /* radiative part of a (d a / d Delta log gamma_rad = ln10 arad) */
+    double a4;       /* Stark part of a (d a / d Delta log gamma_4 = ln10 a4) */
     double dvD;      /* Doppler velocity width, cm/s */
 } line_depth;
 
@@ -246,11 +250,15 @@ static line_depth line_at_depth(const pzo_problem *P, int64_t l, int d) {
     double boltz = exp(-(double)P->E_low_eV[l] * O_EV / (O_KB * T));
     double pie2mc = O_PI * O_E * O_E / (O_ME * O_C);
     q.A = pie2mc * gf * (pop / P->rho[d]) * boltz / (O_SQRTPI * dnuD);
-    double g_rad = pow(10.0, (double)P->log_gamma_rad[l]);
-    double g4 = pow(10.0, (double)P->log_gamma4[l]);
+    double drad = P->dlog_gamma_rad ? P->dlog_gamma_rad[l] : 0.0;
+    double dg4 = P->dlog_gamma4 ? P->dlog_gamma4[l] : 0.0;
+    double g_rad = pow(10.0, (double)P->log_gamma_rad[l] + drad);
+    double g4 = pow(10.0, (double)P->log_gamma4[l] + dg4);
     double g6 = pow(10.0, (double)P->log_gamma6[l] + dg6);
     q.a = (g_rad + g4 * P->n_e[d] + g6 * P->n_pert[d]) / (4.0 * O_PI * dnuD);
     q.a6 = g6 * P->n_pert[d] / (4.0 * O_PI * dnuD);
+    q.arad = g_rad / (4.0 * O_PI * dnuD);
+    q.a4 = g4 * P->n_e[d] / (4.0 * O_PI * dnuD);
     q.dvD = dvD;
     return q;
 }
@@ -465,11 +473,14 @@ void pzo_rt_adjoint(const pzo_problem *P, const double *kline_full, const double
     }
 }
 
-/* Per-line gradients from G = dL/dkappa_line (all columns):
- *   dL/dDelta log gf_l      = ln10 sum_{i in win, d} G stim A H
- *   dL/dDelta log gamma6_l  = ln10 sum_{i in win, d} G stim A (dH/da) a6
- * (the abundance gradient is the species-to-element sum of the first). */
-void pzo_line_grad(const pzo_problem *P, const double *G, double *g_gf, double *g_g6) {
+/* Per-line gradients from G = dL/dkappa_line (all columns), Eq. 10 differentiated:
+ *   dL/dDelta log gf_l         = ln10 sum_{i in win, d} G stim A H
+ *   dL/dDelta log gamma_beta_l = ln10 sum_{i in win, d} G stim A (dH/da) a_beta,
+ * a_beta the part of the damping parameter that family beta contributes (van der Waals
+ * a6, radiative arad, Stark a4), since 10^delta scales that part alone.  g_rad and g_4
+ * may be NULL.  (The abundance gradient is the species-to-element sum of the first.) */
+void pzo_line_grad(const pzo_problem *P, const double *G, double *g_gf, double *g_g6, double *g_rad,
+                   double *g_4) {
     int nd = P->n_depth;
     int W = P->half_window;
 #pragma omp parallel for schedule(dynamic, 16)
@@ -480,7 +491,7 @@ void pzo_line_grad(const pzo_problem *P, const double *G, double *g_gf, double *
         if (i0 < 0) i0 = 0;
         if (i1 > P->n_lambda - 1) i1 = P->n_lambda - 1;
         double lam_l = P->lambda_nm[l] * 1e-7;
-        double sgf = 0.0, sg6 = 0.0;
+        double sgf = 0.0, sg6 = 0.0, srad = 0.0, sg4 = 0.0;
         for (int d = 0; d < nd; ++d) {
             line_depth q = line_at_depth(P, l, d);
             if (!centre_keep(P, il, d, q.A)) continue;
@@ -491,10 +502,14 @@ void pzo_line_grad(const pzo_problem *P, const double *G, double *g_gf, double *
                 double gs = G[(int64_t)d * P->n_lambda + i] * stim_emission(P, i, d);
                 sgf += gs * q.A * H;
                 sg6 += gs * q.A * dH * q.a6;
+                srad += gs * q.A * dH * q.arad;
+                sg4 += gs * q.A * dH * q.a4;
             }
         }
         g_gf[l] = O_LN10 * sgf;
         g_g6[l] = O_LN10 * sg6;
+        if (g_rad) g_rad[l] = O_LN10 * srad;
+        if (g_4) g_4[l] = O_LN10 * sg4;
     }
 }
 
