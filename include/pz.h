@@ -26,6 +26,9 @@
  *                      corrections (the joint Sun-Arcturus fit of Sec. 6): forward,
  *                      objective, reverse pass and a gradient update in one CUDA
  *                      graph launch.
+ *   pz_group_eval      the four-parameter grouped calibration of Sec. 6 (Eq. 10 with
+ *                      linked groups q(l)): objective and group gradients in one
+ *                      graph launch, for an optimiser such as L-BFGS.
  *
  * Conventions (every call):
  *  - Return value: PZ_OK or an error code; on error pz_last_error() gives a
@@ -252,6 +255,66 @@ pz_status pz_get_corrections(pz_ctx *ctx, float *dlog_gf, float *dlog_gamma6, fl
 pz_status pz_calib_step(pz_ctx *ctx, const float *y, const float *w, int64_t n, float lr_gf,
                         float lr_g6, float lr_ab, double *loss, float *g_dlog_gf,
                         float *g_dlog_gamma6, float *g_dabund, void *stream);
+
+/* ---- four-parameter grouped calibration (Sec. 6, Eq. 10) --------------------- */
+
+/* Corrections of the other two damping families of Eq. 10: the radiative and Stark
+ * coefficients of line l become gamma_rad,l 10^dlog_gamma_rad[l] and
+ * gamma_4,l 10^dlog_gamma4[l].  Arrays [n_lines] in caller order, FP32, host or
+ * device memory, NULL = zero.  Applied like pz_set_corrections (the forward must
+ * run again).  Errors: PZ_ECUDA. */
+pz_status pz_set_damping_corrections(pz_ctx *ctx, const float *dlog_gamma_rad,
+                                     const float *dlog_gamma4, void *stream);
+
+/* Reverse pass to all four per-line gradients of Eq. 10 -- Delta log gf and the
+ * three damping families -- and the per-element abundance gradients:
+ *   dL/dDelta log gamma_beta,l = ln10 sum_{i in window, d} G stim A_ld (dH/da) a_beta,ld
+ * with a_beta the part of the damping parameter a that family beta contributes
+ * (radiative gamma_rad, Stark gamma_4 n_e, van der Waals gamma_6 n_pert, each over
+ * 4 pi dnu_D).  The line stage runs once per family (the van der Waals pass also
+ * gives the gf sums), so it costs three pz_backward line passes.  Outputs as
+ * pz_backward (device FP32, caller order, each may be NULL).  Requirements and
+ * errors as pz_backward. */
+pz_status pz_backward4(pz_ctx *ctx, const float *dL_df, float *g_dlog_gf, float *g_dlog_gamma_rad,
+                       float *g_dlog_gamma4, float *g_dlog_gamma6, float *g_dabund, void *stream);
+
+/* Linked correction groups q(l) (Sec. 6: every component of a group shares the
+ * group's four corrections).  group_of_line: host int32 [n_lines] in caller order,
+ * values in [0, n_groups) or -1 for a line that takes no correction; n_groups = 0
+ * removes the groups.  Synchronous; drops captured graphs.
+ * Errors: PZ_EINVAL (group id out of range), PZ_ENOMEM, PZ_ECUDA. */
+pz_status pz_set_line_groups(pz_ctx *ctx, const int32_t *group_of_line, int64_t n_groups);
+
+/* One objective and gradient evaluation of the grouped calibration over all stars,
+ * captured once in a CUDA graph and replayed by one graph launch (re-captured when
+ * an argument changes): delta_l = x[.][q(l)] for the four families, line opacity,
+ * flux, the instrument last configured by pz_instrument, L = sum w (y - f)^2, the
+ * four-family reverse pass and the group sums
+ *   g[.][q] = sum over the members l of q of dL/ddelta_l.
+ * x: device FP32 [4][n_groups] rows (Delta log gf, Delta log gamma_rad,
+ * Delta log gamma_4, Delta log gamma_6); g: device FP32 [4][n_groups], same rows,
+ * or NULL; y, w: device FP32 [S][n] (w may be NULL); loss: device FP64 scalar or
+ * NULL.  The corrections of the context are left at the expanded x; abundance
+ * offsets stay as last set.  An optimiser (the paper uses L-BFGS) proposes x
+ * between calls.  Requires pz_set_line_groups with n_groups > 0 and one earlier
+ * pz_instrument (PZ_ESTATE).  Errors: PZ_EINVAL (NULL y or x, n), PZ_ECUDA. */
+pz_status pz_group_eval(pz_ctx *ctx, const float *y, const float *w, int64_t n, const float *x,
+                        double *loss, float *g, void *stream);
+
+/* Greedy strength-ordered line grouping (Sec. 6), host only: lines are taken from
+ * the largest strength down (equal strengths in index order); a line not yet
+ * grouped opens the next group (ids from 0 in opening order) and takes every line
+ * not yet grouped of the same species (ion stage included) with
+ * |E_low,m - E_low,seed| <= dE_eV and |lambda_m - lambda_seed| <= dlam_nm (the
+ * paper uses 2.0 cm^-1 and 0.035 nm).  Differences are taken in FP64 (E_low read
+ * from FP32).  Inputs host [n]: lambda_nm FP64, E_low_eV FP32, species int32,
+ * strength FP32 (any monotone strength proxy, e.g. log gf - theta E_low);
+ * group_of_line host int32 [n] output; *n_groups the number of groups.
+ * Errors: PZ_EINVAL (NULL pointer, negative or non-finite tolerance, non-finite
+ * line data). */
+pz_status pz_build_line_groups(int64_t n, const double *lambda_nm, const float *E_low_eV,
+                               const int32_t *species, const float *strength, double dE_eV,
+                               double dlam_nm, int32_t *group_of_line, int64_t *n_groups);
 
 /* ---- introspection -------------------------------------------------------- */
 

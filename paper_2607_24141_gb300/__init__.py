@@ -87,6 +87,12 @@ _SIGS = {
     "pz_probe_pipe": (C.c_int, [C.c_int32, C.c_int32, _dp, _vp]),
     "pz_probe_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), _vp]),
     "pz_sync_status": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32)]),
+    "pz_set_damping_corrections": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "pz_backward4": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "pz_set_line_groups": (C.c_int, [_vp, _vp, C.c_int64]),
+    "pz_group_eval": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
+    "pz_build_line_groups": (C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp,
+                                       C.POINTER(C.c_int64)]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -231,6 +237,53 @@ def pz_loss_chi2(ctx, y, w=None, loss=None, dL_df=None, stream=None):
 def pz_backward(ctx, dL_df, g_dlog_gf=None, g_dlog_gamma6=None, g_dabund=None, stream=None):
     _check(load().pz_backward(ctx, _ptr(dL_df), _ptr(g_dlog_gf), _ptr(g_dlog_gamma6), _ptr(g_dabund),
                               _stream(stream)))
+
+
+def pz_set_damping_corrections(ctx, dlog_gamma_rad=None, dlog_gamma4=None, stream=None):
+    """Radiative and Stark corrections of Eq. 10 (caller order; numpy = host, torch = device)."""
+    keep = []
+
+    def p(x):
+        if x is None:
+            return None
+        if isinstance(x, np.ndarray):
+            a = np.ascontiguousarray(x, dtype=np.float32)
+            keep.append(a)
+            return a.ctypes.data
+        return x.data_ptr()
+    _check(load().pz_set_damping_corrections(ctx, p(dlog_gamma_rad), p(dlog_gamma4), _stream(stream)))
+
+
+def pz_backward4(ctx, dL_df, g_dlog_gf=None, g_dlog_gamma_rad=None, g_dlog_gamma4=None, g_dlog_gamma6=None,
+                 g_dabund=None, stream=None):
+    _check(load().pz_backward4(ctx, _ptr(dL_df), _ptr(g_dlog_gf), _ptr(g_dlog_gamma_rad), _ptr(g_dlog_gamma4),
+                               _ptr(g_dlog_gamma6), _ptr(g_dabund), _stream(stream)))
+
+
+def pz_set_line_groups(ctx, group_of_line, n_groups):
+    q = np.ascontiguousarray(group_of_line, dtype=np.int32)
+    _check(load().pz_set_line_groups(ctx, q.ctypes.data, int(n_groups)))
+
+
+def pz_group_eval(ctx, y, w, x, loss=None, g=None, stream=None):
+    """x, g: device FP32 [4][n_groups] (gf, rad, Stark, vdW); y, w: device FP32 [S][n]."""
+    _check(load().pz_group_eval(ctx, _ptr(y), _ptr(w), y.shape[-1], _ptr(x), _ptr(loss), _ptr(g), _stream(stream)))
+
+
+def pz_build_line_groups(lambda_nm, E_low_eV, species, strength, dE_eV, dlam_nm):
+    """Greedy strength-ordered grouping (host).  Returns (group_of_line int32, n_groups)."""
+    lam = np.ascontiguousarray(lambda_nm, dtype=np.float64)
+    E = np.ascontiguousarray(E_low_eV, dtype=np.float32)
+    sp = np.ascontiguousarray(species, dtype=np.int32)
+    st = np.ascontiguousarray(strength, dtype=np.float32)
+    n = lam.size
+    if not (E.size == sp.size == st.size == n):
+        raise ValueError("pz_build_line_groups: arrays differ in length")
+    q = np.empty(max(n, 1), np.int32)
+    G = C.c_int64(0)
+    _check(load().pz_build_line_groups(n, lam.ctypes.data, E.ctypes.data, sp.ctypes.data, st.ctypes.data,
+                                       float(dE_eV), float(dlam_nm), q.ctypes.data, C.byref(G)))
+    return q[:n], int(G.value)
 
 
 def pz_eval_count(ctx) -> int:

@@ -214,6 +214,8 @@ static pz_status build_thresholds(pz_ctx *c) {
 static void drop_graph(pz_ctx *c) {
     if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
     c->graph = StepGraph();
+    if (c->ggraph.exec) cudaGraphExecDestroy(c->ggraph.exec);
+    c->ggraph = StepGraph();
 }
 
 static void destroy_ctx(pz_ctx *c) {
@@ -227,7 +229,8 @@ static void destroy_ctx(pz_ctx *c) {
                     c->d_line_off, c->d_fitems, c->d_nitems_f, c->d_nitems_b, c->d_ctr, c->d_knear, c->d_kline,
                     c->d_F, c->d_Fc, c->d_g, c->d_gc, c->d_tap0, c->d_ntap, c->d_tapw, c->d_dFbar, c->d_Gt,
                     c->d_Gt64, c->d_gacc, c->d_gline, c->d_gab, c->d_dLdf, c->d_ftab, c->d_finfo, c->d_status,
-                    c->d_keep};
+                    c->d_keep, c->L.gradbase, c->L.g4base, c->L.dgrad, c->L.dg4, c->d_mdgrad, c->d_mdg4,
+                    c->d_grp_of, c->d_grp_off, c->d_grp_mem};
     for (void *p : ptrs) dfree(p);
     for (auto &m : c->marks) {
         cudaEventDestroy(m.a);
@@ -397,6 +400,9 @@ static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, 
         upload(&c->L.ilf, ilf, "lines") || upload(&c->L.frac, frac, "lines") || upload(&c->L.sp, sp, "lines") ||
         upload(&c->L.E, E, "lines") || upload(&c->L.lamcm, lamcm, "lines") || upload(&c->L.grad, grad, "lines") ||
         upload(&c->L.g4, g4, "lines") || upload(&c->L.g6base, g6, "lines") || upload(&c->L.g6, g6, "lines") ||
+        upload(&c->L.gradbase, grad, "lines") || upload(&c->L.g4base, g4, "lines") ||
+        upload(&c->L.dgrad, zeros, "lines") || upload(&c->L.dg4, zeros, "lines") ||
+        upload(&c->d_mdgrad, mzeros, "corrections") || upload(&c->d_mdg4, mzeros, "corrections") ||
         upload(&c->L.Q, Qf, "lines") || upload(&c->L.Qbase, Qb, "lines") || upload(&c->L.x64, x64, "lines") ||
         upload(&c->L.lg_gf, lg_gf, "lines") || upload(&c->L.lg_rad, lg_rad, "lines") ||
         upload(&c->L.lg_4, lg_4, "lines") || upload(&c->L.lg_6, lg_6, "lines") || upload(&c->L.dgf, zeros, "lines") ||
@@ -497,8 +503,9 @@ static pz_status ensure_backward_buffers(pz_ctx *c) {
     if (!c->d_dFbar) PZ_TRY(dalloc(&c->d_dFbar, (size_t)c->S * c->nlam, "backward scratch"));
     if (c->prec == PZ_MIXED && !c->d_Gt) PZ_TRY(dalloc(&c->d_Gt, SD * c->ld, "backward scratch"));
     if (c->prec == PZ_FP64 && !c->d_Gt64) PZ_TRY(dalloc(&c->d_Gt64, SD * c->ld, "backward scratch"));
-    if (!c->d_gacc) PZ_TRY(dalloc(&c->d_gacc, 2 * std::max<int64_t>(c->L.n, 1), "backward scratch"));
-    if (!c->d_gline) PZ_TRY(dalloc(&c->d_gline, 2 * std::max<int64_t>(c->nl_caller, 1), "backward scratch"));
+    // room for the four-family reverse pass (pz_backward4): six rows per line, four per caller line
+    if (!c->d_gacc) PZ_TRY(dalloc(&c->d_gacc, 6 * std::max<int64_t>(c->L.n, 1), "backward scratch"));
+    if (!c->d_gline) PZ_TRY(dalloc(&c->d_gline, 4 * std::max<int64_t>(c->nl_caller, 1), "backward scratch"));
     if (c->n_elem > 0 && !c->d_gab) PZ_TRY(dalloc(&c->d_gab, c->n_elem, "backward scratch"));
     return PZ_OK;
 }
@@ -550,17 +557,28 @@ static pz_status apply_tiling(pz_ctx *c, const Tiling &t, const char *who) {
 // The backward stages after the objective's seed dL/df: instrument adjoint, transfer
 // adjoint, line gradients, finalisation into caller order.
 static pz_status enqueue_backward(pz_ctx *c, const float *dLdf, float *g_gf, float *g_g6, float *g_ab,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, bool four = false, float *g_rad = nullptr, float *g_g4 = nullptr) {
     PZ_CUDA(timed(c, s, PZ_K_INST_ADJOINT, [&] { return launch_inst_adjoint(c, dLdf, s); }), "instrument adjoint");
     PZ_CUDA(timed(c, s, PZ_K_RT_ADJOINT, [&] { return launch_rt_adjoint(c, s); }), "transfer adjoint");
     c->have_gt = true;
-    PZ_CUDA(cudaMemsetAsync(c->d_gacc, 0, sizeof(double) * 2 * std::max<int64_t>(c->L.n, 1), s), "backward");
+    const int64_t nl1 = std::max<int64_t>(c->L.n, 1);
+    PZ_CUDA(cudaMemsetAsync(c->d_gacc, 0, sizeof(double) * (four ? 6 : 2) * nl1, s), "backward");
     if (c->L.n > 0) {
-        PZ_CUDA(timed(c, s, PZ_K_LINE_BWD,
-                      [&] { return c->prec == PZ_MIXED ? launch_line_bwd_mixed(c, s) : launch_line_bwd_fp64(c, s); }),
-                "line gradient kernel");
+        // one line pass per damping family: the first gives the gf and van der Waals sums,
+        // the radiative and Stark passes their second sums (rows 3 and 5)
+        const int passes = four ? 3 : 1;
+        for (int p = 0; p < passes; ++p) {
+            c->bwd_dsel = p;
+            c->gacc_off = 2 * p * c->L.n;
+            cudaError_t e = timed(c, s, PZ_K_LINE_BWD, [&] {
+                return c->prec == PZ_MIXED ? launch_line_bwd_mixed(c, s) : launch_line_bwd_fp64(c, s);
+            });
+            c->bwd_dsel = 0;
+            c->gacc_off = 0;
+            PZ_CUDA(e, "line gradient kernel");
+        }
     }
-    PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_grad_finalize(c, g_gf, g_g6, g_ab, s); }),
+    PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_grad_finalize(c, g_gf, g_g6, g_ab, s, four, g_rad, g_g4); }),
             "gradient finalize");
     return PZ_OK;
 }
@@ -997,6 +1015,17 @@ pz_status pz_backward(pz_ctx *c, const float *dLdf, float *g_gf, float *g_g6, fl
     return enqueue_backward(c, dLdf, g_gf, g_g6, g_ab, s);
 }
 
+pz_status pz_backward4(pz_ctx *c, const float *dLdf, float *g_gf, float *g_rad, float *g_g4, float *g_g6,
+                       float *g_ab, void *stream) {
+    if (!c) return fail(PZ_EINVAL, "pz_backward4: ctx is NULL");
+    if (!c->have_inst) return fail(PZ_ESTATE, "pz_backward4: call pz_instrument first");
+    if (!dLdf) return fail(PZ_EINVAL, "pz_backward4: dL_df is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->launches = 0;
+    PZ_TRY(ensure_backward_buffers(c));
+    return enqueue_backward(c, dLdf, g_gf, g_g6, g_ab, s, true, g_rad, g_g4);
+}
+
 // One calibration step: corrections -> line opacity -> flux -> instrument -> chi^2 ->
 // adjoint -> gradients -> delta -= lr * gradient, enqueued on the capture stream.
 static pz_status enqueue_step(pz_ctx *c, const float *y, const float *w, double *loss, float *g_gf, float *g_g6,
@@ -1060,6 +1089,180 @@ pz_status pz_calib_step(pz_ctx *c, const float *y, const float *w, int64_t n, fl
     PZ_CUDA(e, "pz_calib_step: graph launch");
     c->launches = G.launches;
     c->have_kline = c->have_flux = c->have_inst = true;
+    return PZ_OK;
+}
+
+// Caller-order master correction from host or device memory (NULL: zero).
+static pz_status set_master_corr(pz_ctx *c, const float *src, float *dst, cudaStream_t s, const char *what) {
+    const int64_t n = c->nl_caller;
+    if (!src) return cuda_check(cudaMemsetAsync(dst, 0, sizeof(float) * std::max<int64_t>(n, 1), s), what);
+    if (n == 0) return PZ_OK;
+    if (is_device_ptr(src))
+        return cuda_check(cudaMemcpyAsync(dst, src, sizeof(float) * n, cudaMemcpyDeviceToDevice, s), what);
+    PZ_CUDA(cudaStreamSynchronize(s), what);
+    return cuda_check(cudaMemcpy(dst, src, sizeof(float) * n, cudaMemcpyHostToDevice), what);
+}
+
+pz_status pz_set_damping_corrections(pz_ctx *c, const float *dgrad, const float *dg4, void *stream) {
+    if (!c) return fail(PZ_EINVAL, "pz_set_damping_corrections: ctx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    c->launches = 0;
+    PZ_TRY(set_master_corr(c, dgrad, c->d_mdgrad, s, "dlog_gamma_rad"));
+    PZ_TRY(set_master_corr(c, dg4, c->d_mdg4, s, "dlog_gamma4"));
+    PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_apply_corrections(c, s); }), "apply corrections");
+    c->have_kline = c->have_flux = c->have_inst = false;
+    return PZ_OK;
+}
+
+pz_status pz_set_line_groups(pz_ctx *c, const int32_t *group_of_line, int64_t n_groups) {
+    if (!c) return fail(PZ_EINVAL, "pz_set_line_groups: ctx is NULL");
+    if (n_groups < 0 || n_groups > INT32_MAX) return fail(PZ_EINVAL, "pz_set_line_groups: n_groups out of range");
+    if (n_groups > 0 && !group_of_line) return fail(PZ_EINVAL, "pz_set_line_groups: group_of_line is NULL");
+    const int64_t n = c->nl_caller;
+    std::vector<int32_t> q(std::max<int64_t>(n, 1), -1);
+    std::vector<int64_t> off(n_groups + 1, 0);
+    if (n_groups > 0) {
+        for (int64_t k = 0; k < n; ++k) {
+            const int32_t g = group_of_line[k];
+            if (g < -1 || g >= n_groups) return fail(PZ_EINVAL, "pz_set_line_groups: group id out of range");
+            q[k] = g;
+            if (g >= 0) off[g + 1]++;
+        }
+    }
+    for (int64_t g = 0; g < n_groups; ++g) off[g + 1] += off[g];
+    std::vector<int32_t> mem(std::max<int64_t>(off[n_groups], 1), 0);
+    std::vector<int64_t> fill(off.begin(), off.end() - 1);
+    for (int64_t k = 0; k < n && n_groups > 0; ++k)
+        if (q[k] >= 0) mem[fill[q[k]]++] = (int32_t)k;
+    drop_graph(c);
+    PZ_CUDA(cudaDeviceSynchronize(), "pz_set_line_groups");
+    dfree(c->d_grp_of);
+    dfree(c->d_grp_off);
+    dfree(c->d_grp_mem);
+    c->d_grp_of = nullptr;
+    c->d_grp_off = nullptr;
+    c->d_grp_mem = nullptr;
+    c->n_groups = 0;
+    if (n_groups == 0) return PZ_OK;
+    PZ_TRY(upload(&c->d_grp_of, q, "line groups"));
+    PZ_TRY(upload(&c->d_grp_off, off, "line groups"));
+    PZ_TRY(upload(&c->d_grp_mem, mem, "line groups"));
+    c->n_groups = n_groups;
+    return PZ_OK;
+}
+
+// Group evaluation: group corrections -> line opacity -> flux -> instrument -> chi^2 ->
+// four-family reverse pass -> group sums, enqueued on the capture stream.
+static pz_status enqueue_group_eval(pz_ctx *c, const float *y, const float *w, const float *x, double *loss, float *g,
+                                    cudaStream_t s) {
+    PZ_CUDA(launch_group_gather(c, x, s), "group corrections");
+    PZ_CUDA(launch_apply_corrections(c, s), "apply corrections");
+    PZ_CUDA(c->prec == PZ_MIXED ? launch_line_fwd_mixed(c, s) : launch_line_fwd_fp64(c, s), "line opacity kernel");
+    PZ_CUDA(launch_flux(c, s), "flux kernel");
+    PZ_CUDA(launch_inst_apply(c, nullptr, s), "instrument apply");
+    if (loss) PZ_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s), "loss");
+    PZ_CUDA(launch_loss(c, y, w, (int64_t)c->S * c->n_out, loss, c->d_dLdf, s), "loss kernel");
+    PZ_TRY(enqueue_backward(c, c->d_dLdf, nullptr, nullptr, nullptr, s, true, nullptr, nullptr));
+    if (g) PZ_CUDA(launch_group_reduce(c, g, s), "group gradients");
+    return PZ_OK;
+}
+
+pz_status pz_group_eval(pz_ctx *c, const float *y, const float *w, int64_t n, const float *x, double *loss, float *g,
+                        void *stream) {
+    if (!c) return fail(PZ_EINVAL, "pz_group_eval: ctx is NULL");
+    if (c->n_groups <= 0) return fail(PZ_ESTATE, "pz_group_eval: call pz_set_line_groups first");
+    if (c->n_out <= 0) return fail(PZ_ESTATE, "pz_group_eval: call pz_instrument once first");
+    if (!y || !x) return fail(PZ_EINVAL, "pz_group_eval: y and x are required");
+    if (n != c->n_out) return fail(PZ_EINVAL, "pz_group_eval: n differs from the instrument output size");
+    cudaStream_t s = (cudaStream_t)stream;
+    PZ_TRY(ensure_backward_buffers(c));
+    if (!c->d_dLdf) PZ_TRY(dalloc(&c->d_dLdf, (size_t)c->S * c->pix_cap, "step seed"));
+    StepGraph &G = c->ggraph;
+    const void *key[6] = {y, w, x, loss, g, nullptr};
+    bool same = G.exec && G.n == n;
+    for (int k = 0; k < 6 && same; ++k) same = G.key[k] == key[k];
+    if (!same) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        G = StepGraph();
+        PZ_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "pz_group_eval: capture");
+        c->capturing = true;
+        c->launches = 0;
+        pz_status st = enqueue_group_eval(c, y, w, x, loss, g, c->cap_stream);
+        c->capturing = false;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
+        if (st != PZ_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_check(e, "pz_group_eval: end capture");
+        e = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) {
+            G.exec = nullptr;
+            return cuda_check(e, "pz_group_eval: instantiate");
+        }
+        for (int k = 0; k < 6; ++k) G.key[k] = key[k];
+        G.n = n;
+        G.launches = c->launches;
+    }
+    cudaEvent_t ev = prof_begin(c, s);
+    cudaError_t e = cudaGraphLaunch(G.exec, s);
+    prof_end(c, s, PZ_K_STEP, ev);
+    PZ_CUDA(e, "pz_group_eval: graph launch");
+    c->launches = G.launches;
+    c->have_kline = c->have_flux = c->have_inst = true;
+    return PZ_OK;
+}
+
+pz_status pz_build_line_groups(int64_t n, const double *lambda_nm, const float *E_low_eV, const int32_t *species,
+                               const float *strength, double dE_eV, double dlam_nm, int32_t *group_of_line,
+                               int64_t *n_groups) {
+    if (n < 0 || (n > 0 && (!lambda_nm || !E_low_eV || !species || !strength || !group_of_line)) || !n_groups)
+        return fail(PZ_EINVAL, "pz_build_line_groups: bad arguments");
+    if (!(dE_eV >= 0.0) || !(dlam_nm >= 0.0) || !std::isfinite(dE_eV) || !std::isfinite(dlam_nm))
+        return fail(PZ_EINVAL, "pz_build_line_groups: tolerances must be finite and >= 0");
+    for (int64_t k = 0; k < n; ++k)
+        if (!std::isfinite(strength[k]) || !std::isfinite(lambda_nm[k]) || !std::isfinite(E_low_eV[k]))
+            return fail(PZ_EINVAL, "pz_build_line_groups: non-finite line data");
+    // seeds from the strongest down (equal strengths by index)
+    std::vector<int64_t> order(n);
+    std::iota(order.begin(), order.end(), (int64_t)0);
+    std::sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        return strength[a] > strength[b] || (strength[a] == strength[b] && a < b);
+    });
+    // candidates: lines by (species, wavelength); a seed scans its species' wavelength
+    // window, widened slightly so that the exact test below decides every boundary case
+    std::vector<int64_t> by(n);
+    std::iota(by.begin(), by.end(), (int64_t)0);
+    std::sort(by.begin(), by.end(), [&](int64_t a, int64_t b) {
+        if (species[a] != species[b]) return species[a] < species[b];
+        if (lambda_nm[a] != lambda_nm[b]) return lambda_nm[a] < lambda_nm[b];
+        return a < b;
+    });
+    std::vector<int32_t> q(n, -1);
+    const double pad = dlam_nm * 1e-9 + 1e-9;
+    int64_t G = 0;
+    for (int64_t s : order) {
+        if (q[s] >= 0) continue;
+        if (G >= INT32_MAX) return fail(PZ_EINVAL, "pz_build_line_groups: too many groups");
+        q[s] = (int32_t)G;
+        const int32_t sp = species[s];
+        const double ls = lambda_nm[s], es = (double)E_low_eV[s];
+        auto lo = std::lower_bound(by.begin(), by.end(), s, [&](int64_t m, int64_t) {
+            return species[m] < sp || (species[m] == sp && lambda_nm[m] < ls - dlam_nm - pad);
+        });
+        for (auto it = lo; it != by.end(); ++it) {
+            const int64_t m = *it;
+            if (species[m] != sp || lambda_nm[m] > ls + dlam_nm + pad) break;
+            if (q[m] >= 0) continue;
+            if (std::fabs((double)E_low_eV[m] - es) <= dE_eV && std::fabs(lambda_nm[m] - ls) <= dlam_nm)
+                q[m] = (int32_t)G;
+        }
+        ++G;
+    }
+    for (int64_t k = 0; k < n; ++k) group_of_line[k] = q[k];
+    *n_groups = G;
     return PZ_OK;
 }
 

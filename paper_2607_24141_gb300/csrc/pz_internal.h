@@ -65,8 +65,10 @@ struct LineTable {
     int32_t *sp = nullptr;      // species
     float *E = nullptr;         // E_low, eV
     float *lamcm = nullptr;     // lambda_l, cm (FP32)
-    float *grad = nullptr;      // gamma_rad, s^-1
-    float *g4 = nullptr;        // gamma_4
+    float *grad = nullptr;      // gamma_rad 10^dlog_gamma_rad, s^-1
+    float *g4 = nullptr;        // gamma_4 10^dlog_gamma4
+    float *gradbase = nullptr;  // 10^log_gamma_rad (uncorrected)
+    float *g4base = nullptr;    // 10^log_gamma4 (uncorrected)
     float *g6base = nullptr;    // 10^log_gamma6 (uncorrected)
     float *g6 = nullptr;        // 10^(log_gamma6 + dlog_gamma6)
     float *Q = nullptr;         // (pi e^2/m_e c)/sqrt(pi) lambda_l gf_l 10^dlog_gf (FP32)
@@ -75,6 +77,7 @@ struct LineTable {
     float *lg_gf = nullptr;     // log10 gf (caller value; FP64 form)
     float *lg_rad = nullptr, *lg_4 = nullptr, *lg_6 = nullptr;
     float *dgf = nullptr, *dg6 = nullptr;  // current corrections (per line)
+    float *dgrad = nullptr, *dg4 = nullptr;
 };
 
 // Captured corrections + fwd + loss + bwd + update step (pz_calib_step), re-captured
@@ -124,6 +127,13 @@ struct pz_ctx {
     double *d_kc = nullptr;         // [S][nd][ld] continuum opacity FP64
     double *d_dab = nullptr;        // [n_elem] current abundance offsets
     float *d_mdgf = nullptr, *d_mdg6 = nullptr;   // [nl_caller] current line corrections, caller order
+    float *d_mdgrad = nullptr, *d_mdg4 = nullptr; // [nl_caller] radiative and Stark corrections, caller order
+    // linked correction groups: group of each caller line (-1: none) and the members of
+    // each group as CSR over caller lines
+    int32_t *d_grp_of = nullptr;    // [nl_caller]
+    int64_t *d_grp_off = nullptr;   // [n_groups + 1]
+    int32_t *d_grp_mem = nullptr;   // [members]
+    int64_t n_groups = 0;
     int32_t *d_eos = nullptr;       // [ns] element of species (or -1)
     int n_elem = 0;
 
@@ -156,8 +166,11 @@ struct pz_ctx {
     double *d_dFbar = nullptr;      // [S][nlam]
     float *d_Gt = nullptr;          // [S][nd][ld] G * stim (FP32, MIXED)
     double *d_Gt64 = nullptr;       // [S][nd][ld] (FP64 form)
-    double *d_gacc = nullptr;       // [2][L.n] per table line
-    double *d_gline = nullptr;      // [2][nl_caller] summed over stars, caller order
+    double *d_gacc = nullptr;       // [6][L.n] per table line: (gf, vdW) of the first pass, then
+                                    // (unused, rad) and (unused, Stark) of the four-family passes
+    double *d_gline = nullptr;      // [4][nl_caller] summed over stars, caller order: gf, vdW, rad, Stark
+    int bwd_dsel = 0;               // damping family of the line backward pass (0 vdW, 1 rad, 2 Stark)
+    int64_t gacc_off = 0;           // its offset into d_gacc
     double *d_gab = nullptr;        // [n_elem]
     float *d_dLdf = nullptr;        // [S][n_out] seed of the captured step
 
@@ -172,6 +185,7 @@ struct pz_ctx {
     double centre_eta = 0.0;             // its selection fraction (0 = off)
     int32_t launches = 0;
     pz::StepGraph graph;
+    pz::StepGraph ggraph;                // captured group evaluation (pz_group_eval)
     cudaStream_t cap_stream = nullptr;   // private stream the step graph is captured on
     bool capturing = false;              // profiler off while capturing
 
@@ -218,7 +232,10 @@ cudaError_t launch_loss(pz_ctx *c, const float *y, const float *w, int64_t n, do
                         float *dLdf, cudaStream_t s);
 cudaError_t launch_inst_adjoint(pz_ctx *c, const float *dLdf, cudaStream_t s);
 cudaError_t launch_rt_adjoint(pz_ctx *c, cudaStream_t s);
-cudaError_t launch_grad_finalize(pz_ctx *c, float *g_gf, float *g_g6, float *g_ab, cudaStream_t s);
+cudaError_t launch_grad_finalize(pz_ctx *c, float *g_gf, float *g_g6, float *g_ab, cudaStream_t s, bool four = false,
+                                 float *g_rad = nullptr, float *g_g4 = nullptr);
+cudaError_t launch_group_gather(pz_ctx *c, const float *x, cudaStream_t s);
+cudaError_t launch_group_reduce(pz_ctx *c, float *g, cudaStream_t s);
 cudaError_t launch_update(pz_ctx *c, float lr_gf, float lr_g6, float lr_ab, cudaStream_t s);
 cudaError_t launch_probe_expn(const double *x, int64_t n, double *out, cudaStream_t s);
 constexpr int kProbeThreads = 256;   // threads per CTA of the pipe-throughput probe

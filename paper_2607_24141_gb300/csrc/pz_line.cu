@@ -157,6 +157,8 @@ struct LineArgs {
     const LineInfo *finfo;                          // far-wing line records
     int *status;                                    // device status word (bounded-wait failures)
     const uint32_t *keep;                           // centre-test mask [nl][kKeepWords] or NULL (all kept)
+    int dsel;                                       // backward: damping family of the second sum
+                                                    // (0 van der Waals, 1 radiative, 2 Stark)
 };
 
 // Centre-test decision of the pair (l, d): kept unless a mask is set and its bit is clear.
@@ -205,6 +207,9 @@ __device__ __forceinline__ void for_each_item(const LineArgs &g, F &&f) {
 //  [0] k = c/dv_D   [1] a^2   [2..6] B1..B5 = A a/sqrt(pi) x (1, 1.5, 3.75-2a^2, -15a^2, 12a^4)
 //  [7] A            (backward:) [8..13] C1..C6 = A a6/sqrt(pi) x (1, 1.5-2a^2, 3.75-12a^2,
 //  12a^4-67.5a^2, 180a^4, -120a^6)   [14] A a6   [15] a
+// where a6 is the part of a that the selected damping family contributes (Eq. 10 scales
+// one family by 10^delta, so d a / d delta = ln10 a6): van der Waals gamma6 n_pert,
+// radiative gamma_rad or Stark gamma4 n_e, over 4 pi dnu_D.
 // Per-line scalars of the prefactors (one load per line, shared by its depths).
 struct LineScalars {
     int sp;
@@ -254,7 +259,8 @@ __device__ __forceinline__ void depth_params(const LineArgs &g, const LineScalar
     out[6] = 12.0f * a2 * a2 * B1;
     out[7] = A;
     if (NP == 16) {
-        const float Aa6 = A * g6n * lw;
+        const float gb = g.dsel == 0 ? g6n : (g.dsel == 1 ? L.grad : __fmul_rn(L.g4, __ldg(g.ne + d)));
+        const float Aa6 = A * gb * lw;
         const float C1 = Aa6 * kInvSqrtPiF;
         out[8] = C1;
         out[9] = fmaf(-2.0f, a2, 1.5f) * C1;
@@ -1318,6 +1324,7 @@ static LineArgs make_args(pz_ctx *c) {
     g.finfo = reinterpret_cast<const LineInfo *>(c->d_finfo);
     g.status = c->d_status;
     g.keep = c->d_keep;
+    g.dsel = c->bwd_dsel;
     g.lam0cm = (float)(c->lambda0_nm * 1e-7);
     g.ilf = c->L.ilf;
     g.frac = c->L.frac;
@@ -1340,7 +1347,7 @@ static LineArgs make_args(pz_ctx *c) {
     g.kline = (float *)c->d_kline;
     g.knear = c->d_knear;
     g.Gt = c->d_Gt;
-    g.gacc = c->d_gacc;
+    g.gacc = c->d_gacc + c->gacc_off;
     g.nl = c->L.n;
     g.items = nullptr;
     g.n_items = 0;
@@ -1541,8 +1548,9 @@ struct Fp64Args {
     const int32_t *star;
     const double *x64;       // fractional centre
     const int32_t *sp;
-    const float *lg_gf, *dgf, *E, *lg_rad, *lg_4, *lg_6, *dg6;
+    const float *lg_gf, *dgf, *E, *lg_rad, *lg_4, *lg_6, *dg6, *dgrad, *dg4;
     const double *T, *rho, *ne, *npert, *pop, *mass, *xi, *dab;   // [S][nd], [S][ns][nd], [S][ns], [S]
+    int dsel;                // backward: damping family of the second sum (0 vdW, 1 rad, 2 Stark)
     const int32_t *eos;
     double *kline;           // [S][nd][ld]
     const double *Gt;        // [S][nd][ld]
@@ -1552,7 +1560,7 @@ struct Fp64Args {
 };
 
 struct LineTerm64 {
-    double A, a, a6, kv;   // strength, damping, vdW damping, c/dv_D
+    double A, a, a6, kv;   // strength, damping, the selected family's part of it, c/dv_D
 };
 
 __device__ __forceinline__ LineTerm64 term64(const Fp64Args &g, int64_t l, int st, int d) {
@@ -1570,8 +1578,10 @@ __device__ __forceinline__ LineTerm64 term64(const Fp64Args &g, int64_t l, int s
     const double boltz = exp(-(double)g.E[l] * kEV / (kKB * T));
     q.A = (kPI * kE * kE / (kME * kC)) / kSQRTPI * gf * (pop / g.rho[sd]) * boltz * inv_dnu;
     const double g6n = exp10((double)g.lg_6[l] + (double)g.dg6[l]) * g.npert[sd];
-    q.a = (exp10((double)g.lg_rad[l]) + exp10((double)g.lg_4[l]) * g.ne[sd] + g6n) * inv_dnu / (4.0 * kPI);
-    q.a6 = g6n * inv_dnu / (4.0 * kPI);
+    const double grad = exp10((double)g.lg_rad[l] + (double)g.dgrad[l]);
+    const double g4n = exp10((double)g.lg_4[l] + (double)g.dg4[l]) * g.ne[sd];
+    q.a = (grad + g4n + g6n) * inv_dnu / (4.0 * kPI);
+    q.a6 = (g.dsel == 0 ? g6n : (g.dsel == 1 ? grad : g4n)) * inv_dnu / (4.0 * kPI);
     q.kv = kC / dv;
     return q;
 }
@@ -1651,6 +1661,9 @@ static Fp64Args make_args64(pz_ctx *c) {
     g.lg_4 = c->L.lg_4;
     g.lg_6 = c->L.lg_6;
     g.dg6 = c->L.dg6;
+    g.dgrad = c->L.dgrad;
+    g.dg4 = c->L.dg4;
+    g.dsel = c->bwd_dsel;
     g.T = c->d_T;
     g.rho = c->d_rho64;
     g.ne = c->d_ne64;
@@ -1662,7 +1675,7 @@ static Fp64Args make_args64(pz_ctx *c) {
     g.eos = c->n_elem > 0 ? c->d_eos : nullptr;
     g.kline = (double *)c->d_kline;
     g.Gt = c->d_Gt64;
-    g.gacc = c->d_gacc;
+    g.gacc = c->d_gacc + c->gacc_off;
     g.keep = c->d_keep;
     g.kc = c->d_kc;
     return g;
@@ -1719,19 +1732,33 @@ cudaError_t launch_line_bwd_fp64(pz_ctx *c, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// corrections: the per-line values are gathered from the caller-order (master)
-// corrections, Q_l = Qbase_l 10^dgf, g6_l = g6base_l 10^dg6, R_sd = Rbase_sd 10^dab
+// corrections (Eq. 10): the per-line values are gathered from the caller-order (master)
+// corrections, Q_l = Qbase_l 10^dgf, gamma_beta,l = gamma_beta,l(base) 10^dbeta for the
+// three damping families, R_sd = Rbase_sd 10^dab
 // ---------------------------------------------------------------------------
-__global__ void k_apply_line_corr(int64_t n, const int32_t *orig, const double *Qbase, const float *g6base,
-                                  const float *mdgf, const float *mdg6, float *dgf, float *dg6, float *Q, float *g6) {
+struct CorrArgs {
+    int64_t n;
+    const int32_t *orig;
+    const double *Qbase;
+    const float *g6base, *gradbase, *g4base;
+    const float *mdgf, *mdg6, *mdgrad, *mdg4;   // caller order
+    float *dgf, *dg6, *dgrad, *dg4;             // per line
+    float *Q, *g6, *grad, *g4;
+};
+
+__global__ void k_apply_line_corr(CorrArgs a) {
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= n) return;
-    const int32_t o = orig[l];
-    const float a = mdgf[o], b = mdg6[o];
-    dgf[l] = a;
-    dg6[l] = b;
-    Q[l] = (float)(Qbase[l] * exp10((double)a));
-    g6[l] = (float)((double)g6base[l] * exp10((double)b));
+    if (l >= a.n) return;
+    const int32_t o = a.orig[l];
+    const float cgf = a.mdgf[o], c6 = a.mdg6[o], cr = a.mdgrad[o], c4 = a.mdg4[o];
+    a.dgf[l] = cgf;
+    a.dg6[l] = c6;
+    a.dgrad[l] = cr;
+    a.dg4[l] = c4;
+    a.Q[l] = (float)(a.Qbase[l] * exp10((double)cgf));
+    a.g6[l] = (float)((double)a.g6base[l] * exp10((double)c6));
+    a.grad[l] = (float)((double)a.gradbase[l] * exp10((double)cr));
+    a.g4[l] = (float)((double)a.g4base[l] * exp10((double)c4));
 }
 
 // R over [S][ns][nd]
@@ -1746,8 +1773,10 @@ __global__ void k_apply_abund(int64_t n, int ns, int nd, const double *Rbase, co
 
 cudaError_t launch_apply_corrections(pz_ctx *c, cudaStream_t s) {
     if (c->L.n > 0) {
-        k_apply_line_corr<<<(unsigned)((c->L.n + 255) / 256), 256, 0, s>>>(
-            c->L.n, c->L.orig, c->L.Qbase, c->L.g6base, c->d_mdgf, c->d_mdg6, c->L.dgf, c->L.dg6, c->L.Q, c->L.g6);
+        CorrArgs a{c->L.n,     c->L.orig,  c->L.Qbase, c->L.g6base, c->L.gradbase, c->L.g4base,
+                   c->d_mdgf,  c->d_mdg6,  c->d_mdgrad, c->d_mdg4, c->L.dgf,      c->L.dg6,
+                   c->L.dgrad, c->L.dg4,   c->L.Q,     c->L.g6,     c->L.grad,     c->L.g4};
+        k_apply_line_corr<<<(unsigned)((c->L.n + 255) / 256), 256, 0, s>>>(a);
         c->launches++;
     }
     int64_t n = (int64_t)c->S * c->ns * c->nd;
@@ -1780,6 +1809,61 @@ cudaError_t launch_update(pz_ctx *c, float lr_gf, float lr_g6, float lr_ab, cuda
         k_update_abund<<<(c->n_elem + 255) / 256, 256, 0, s>>>(c->n_elem, c->d_gab, (double)lr_ab, c->d_dab);
         c->launches++;
     }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// linked correction groups (Sec. 6): every member l of group q takes the group's four
+// corrections, delta_{q(l)}, and the group's gradient is the sum of its members'
+// ---------------------------------------------------------------------------
+// x: [4][G] (gf, rad, Stark, vdW) -> caller-order masters; lines without a group take 0
+__global__ void k_group_gather(int64_t n, int64_t G, const int32_t *grp, const float *x, float *mdgf, float *mdgrad,
+                               float *mdg4, float *mdg6) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int32_t q = grp[k];
+    const bool in = q >= 0;
+    mdgf[k] = in ? x[q] : 0.0f;
+    mdgrad[k] = in ? x[G + q] : 0.0f;
+    mdg4[k] = in ? x[2 * G + q] : 0.0f;
+    mdg6[k] = in ? x[3 * G + q] : 0.0f;
+}
+
+// one thread per group: FP64 sums over the members in CSR order (deterministic) of the
+// caller-order gradients gline [4][n] = (gf, vdW, rad, Stark) -> g [4][G] (gf, rad, Stark, vdW)
+__global__ void k_group_reduce(int64_t G, int64_t n, const int64_t *off, const int32_t *mem, const double *gline,
+                               float *g) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= G) return;
+    double sgf = 0.0, s6 = 0.0, sr = 0.0, s4 = 0.0;
+    for (int64_t k = off[q]; k < off[q + 1]; ++k) {
+        const int64_t l = mem[k];
+        sgf += gline[l];
+        s6 += gline[n + l];
+        sr += gline[2 * n + l];
+        s4 += gline[3 * n + l];
+    }
+    g[q] = (float)sgf;
+    g[G + q] = (float)sr;
+    g[2 * G + q] = (float)s4;
+    g[3 * G + q] = (float)s6;
+}
+
+cudaError_t launch_group_gather(pz_ctx *c, const float *x, cudaStream_t s) {
+    const int64_t n = c->nl_caller;
+    if (n == 0) return cudaSuccess;
+    k_group_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c->n_groups, c->d_grp_of, x, c->d_mdgf,
+                                                              c->d_mdgrad, c->d_mdg4, c->d_mdg6);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_group_reduce(pz_ctx *c, float *g, cudaStream_t s) {
+    const int64_t G = c->n_groups;
+    if (G == 0) return cudaSuccess;
+    k_group_reduce<<<(unsigned)((G + 255) / 256), 256, 0, s>>>(G, c->nl_caller, c->d_grp_off, c->d_grp_mem,
+                                                              c->d_gline, g);
+    c->launches++;
     return cudaGetLastError();
 }
 

@@ -584,7 +584,8 @@ cudaError_t launch_rt_adjoint(pz_ctx *c, cudaStream_t s) {
 // species -> element sums
 // ---------------------------------------------------------------------------
 __global__ void k_grad_finalize(int64_t nl, int64_t nl_caller, const double *gacc, const int32_t *orig,
-                                const int32_t *sp, const int32_t *eos, int use_ab, double *gline, double *gab) {
+                                const int32_t *sp, const int32_t *eos, int use_ab, int four, double *gline,
+                                double *gab) {
     int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= nl) return;
     const double ggf = kLN10 * gacc[l];
@@ -592,6 +593,11 @@ __global__ void k_grad_finalize(int64_t nl, int64_t nl_caller, const double *gac
     const int32_t o = orig[l];
     atomicAdd(gline + o, ggf);
     atomicAdd(gline + nl_caller + o, gg6);
+    if (four) {
+        // the second sums of the radiative and Stark passes
+        atomicAdd(gline + 2 * nl_caller + o, kLN10 * gacc[3 * nl + l]);
+        atomicAdd(gline + 3 * nl_caller + o, kLN10 * gacc[5 * nl + l]);
+    }
     if (use_ab) {
         int e = eos[sp[l]];
         if (e >= 0) atomicAdd(gab + e, ggf);
@@ -603,17 +609,27 @@ __global__ void k_copy_d2f(int64_t n, const double *a, float *b) {
     if (k < n) b[k] = (float)a[k];
 }
 
-cudaError_t launch_grad_finalize(pz_ctx *c, float *g_gf, float *g_g6, float *g_ab, cudaStream_t s) {
+cudaError_t launch_grad_finalize(pz_ctx *c, float *g_gf, float *g_g6, float *g_ab, cudaStream_t s, bool four,
+                                 float *g_rad, float *g_g4) {
     const int use_ab = c->n_elem > 0 ? 1 : 0;
-    cudaError_t e = cudaMemsetAsync(c->d_gline, 0, sizeof(double) * 2 * std::max<int64_t>(c->nl_caller, 1), s);
+    const int rows = four ? 4 : 2;
+    cudaError_t e = cudaMemsetAsync(c->d_gline, 0, sizeof(double) * rows * std::max<int64_t>(c->nl_caller, 1), s);
     if (e != cudaSuccess) return e;
     if (use_ab && (e = cudaMemsetAsync(c->d_gab, 0, sizeof(double) * c->n_elem, s)) != cudaSuccess) return e;
     if (c->L.n > 0) {
         k_grad_finalize<<<(unsigned)((c->L.n + 255) / 256), 256, 0, s>>>(
-            c->L.n, c->nl_caller, c->d_gacc, c->L.orig, c->L.sp, c->d_eos, use_ab, c->d_gline, c->d_gab);
+            c->L.n, c->nl_caller, c->d_gacc, c->L.orig, c->L.sp, c->d_eos, use_ab, four ? 1 : 0, c->d_gline, c->d_gab);
         c->launches++;
     }
     const int64_t n = c->nl_caller;
+    if (four && n > 0 && g_rad) {
+        k_copy_d2f<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c->d_gline + 2 * n, g_rad);
+        c->launches++;
+    }
+    if (four && n > 0 && g_g4) {
+        k_copy_d2f<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c->d_gline + 3 * n, g_g4);
+        c->launches++;
+    }
     if (n > 0 && g_gf) {
         k_copy_d2f<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, c->d_gline, g_gf);
         c->launches++;

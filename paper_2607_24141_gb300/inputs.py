@@ -468,6 +468,52 @@ def config4_joint(seed: int = 4, n_common: int = 100_000, **kw):
     return b, truth
 
 
+HC_EV_CM = 1.239841984e-4     # h c in eV cm: 1 cm^-1 of level energy in eV (CODATA 2018)
+
+
+def config4_joint_grouped(seed: int = 4, n_complexes: int = 25_281, n_records: int = 42_886, **kw):
+    """Four-parameter grouped calibration workload (Sec. 6: 42,886 catalog records in
+    25,281 correction groups over 1500-1700 nm): the solar-like and giant-like stars of
+    config4_joint on a list of component complexes.  The n_complexes strongest lines of
+    the config-4 master list (mean strength proxy of the two stars) each get k - 1
+    companions (k - 1 drawn so that the list holds n_records lines) of the same species,
+    within +-0.02 nm and +-1 cm^-1 of the parent, the parent's gf split evenly over the k
+    components and its damping constants copied (hyperfine- or isotope-like structure).
+    Returns (batch, truth): both stars use every record; truth holds "complex_of_line"
+    [n_records], per-complex corrections "x" [4][n_complexes] (Delta log gf ~ N(0, 0.1),
+    Delta log gamma_rad, gamma_4 ~ N(0, 0.3), Delta log gamma_6 ~ N(0, 0.2)), the per-line
+    "strength" (mean strength proxy, FP32) for the grouping pass, per-star pixel noise
+    (sigma 1/200) and the weight 200^2."""
+    full = config4(seed=seed, n_stars=1, **kw)
+    teff, logg, mh = np.array([5777.0, 4286.0]), np.array([4.44, 1.66]), np.array([0.0, -0.52])
+    atm, kc = _batch_atmospheres(teff, logg, mh, full.atmos[0].n_species, (36, 37, 38, 39), seed + 500, full.grid)
+    score = 0.5 * (strength_proxy(atm[0], full.lines) + strength_proxy(atm[1], full.lines))
+    parents = np.sort(np.argsort(-score, kind="stable")[:n_complexes])
+    rng = np.random.default_rng(seed + 900)
+    extra = np.bincount(rng.integers(0, parents.size, max(n_records - parents.size, 0)), minlength=parents.size)
+    k = 1 + extra
+    cid = np.repeat(np.arange(parents.size), k)
+    src = parents[cid]
+    first = np.concatenate([[True], cid[1:] != cid[:-1]])
+    L = full.lines.subset(src)
+    n = src.size
+    dl = rng.uniform(-0.02, 0.02, n)
+    dE = rng.uniform(-1.0, 1.0, n) * HC_EV_CM
+    L.lambda_nm = np.where(first, L.lambda_nm, L.lambda_nm + dl)
+    L.E_low_eV = np.where(first, L.E_low_eV, np.maximum(L.E_low_eV.astype(np.float64) + dE, 0.0)).astype(np.float32)
+    L.log_gf = (L.log_gf.astype(np.float64) - np.log10(k[cid])).astype(np.float32)
+    strength = (0.5 * (strength_proxy(atm[0], L) + strength_proxy(atm[1], L))).astype(np.float32)
+    allk = np.arange(n, dtype=np.int32)
+    b = Batch("config4-joint-grouped", atm, full.grid, L, kc, [allk, allk.copy()], full.instrument,
+              full.elem_of_species, full.n_elem)
+    n_out = full.instrument.pix_lambda_nm.size if full.instrument is not None else full.grid.n_lambda
+    x = np.stack([rng.normal(0.0, 0.1, parents.size), rng.normal(0.0, 0.3, parents.size),
+                  rng.normal(0.0, 0.3, parents.size), rng.normal(0.0, 0.2, parents.size)]).astype(np.float32)
+    truth = {"complex_of_line": cid.astype(np.int32), "x": x, "strength": strength,
+             "noise": rng.normal(0.0, 1.0 / 200.0, (2, n_out)), "weight": 200.0 ** 2}
+    return b, truth
+
+
 def small_batch(n_stars: int = 3, span_nm: float = 2.0, seed: int = 21, W: int = 1500,
                 with_instrument: bool = True) -> Batch:
     """Scaled-down config 4 for element-wise parity: a ~2 nm slice of the config-1

@@ -45,3 +45,45 @@ def test_lbfgs_calibration_recovers_the_fit():
     chi2 = float(((y - f) ** 2 * w).double().sum())
     assert abs(chi2 / res["loss_final"] - 1) < 1e-4
     s.close()
+
+
+def test_grouped_lbfgs_calibration():
+    """Four corrections per linked group (Eq. 10 with q(l)): L-BFGS over pz_group_eval
+    fits a two-star slice with true group corrections to below the chi-square of the
+    truth."""
+    import torch
+    b = I.small_batch(n_stars=2, span_nm=3.0, seed=33)
+    nl = b.lines.n_lines
+    rng = np.random.default_rng(14)
+    G = nl // 2
+    q = rng.integers(0, G, nl).astype(np.int32)
+    q[:G] = np.arange(G)
+    rng.shuffle(q)
+    x_true = np.stack([rng.normal(0, 0.1, G), rng.normal(0, 0.3, G), rng.normal(0, 0.3, G),
+                       rng.normal(0, 0.2, G)]).astype(np.float32)
+    s = pz.Synthesizer(b, pz.PZ_MIXED)
+    xl = x_true[:, q]
+    s.set_corrections(xl[0], xl[3], None)
+    pz.pz_set_damping_corrections(s.ctx, xl[1], xl[2])
+    f_true = s.forward()
+    sn = 1000.0
+    y = (f_true + torch.tensor(rng.normal(0, 1 / sn, tuple(f_true.shape)), dtype=torch.float32,
+                               device=f_true.device)).contiguous()
+    w = torch.full_like(y, sn ** 2)
+    pz.pz_set_line_groups(s.ctx, q, G)
+    loss = torch.zeros(1, dtype=torch.float64, device=y.device)
+    pz.pz_group_eval(s.ctx, y, w, torch.tensor(x_true, device=y.device), loss, None)
+    chi2_truth = float(loss.item())
+    res = calibrate.lbfgs_groups(s, y, w, q, G, n_updates=15)
+    print("grouped L-BFGS: chi2 %.4g -> %.4g (%.4g at the truth), %d updates, %d evaluations, %.3f s, %d groups"
+          % (res["loss_start"], res["loss_final"], chi2_truth, res["updates"], res["evals"], res["seconds"], G))
+    assert res["updates"] == 15
+    assert res["loss_start"] > 3.0 * chi2_truth
+    assert res["loss_final"] < 0.25 * res["loss_start"]
+    assert res["loss_final"] < 1.1 * chi2_truth
+    # the context holds the expanded fit
+    gf, g6, _ = s.get_corrections()
+    xf = res["x"].cpu().numpy()
+    np.testing.assert_array_equal(gf, xf[0][q])
+    np.testing.assert_array_equal(g6, xf[3][q])
+    s.close()
