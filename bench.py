@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--broad-steps", type=int, default=3)
     ap.add_argument("--no-centre", action="store_true", help="skip the centre-test measurement")
     ap.add_argument("--no-lbfgs", action="store_true", help="skip the L-BFGS calibration measurement")
+    ap.add_argument("--scaling", action="store_true", help="run the R_grid and span scaling sweeps (about a minute)")
+    ap.add_argument("--scaling-reps", type=int, default=3)
     ap.add_argument("--lbfgs-updates", type=int, default=40)
     ap.add_argument("--centre-eta", type=float, default=1e-3)
     return ap.parse_args()
@@ -559,6 +561,72 @@ def run_lbfgs_groups(args, dev, tiling=None):
             "paper_context": "40 shared Sun-Arcturus updates, 101,124 scalars: 64 s on one H100 (Sec. 6)"}
 
 
+def run_scaling(args, dev, tiling=None):
+    """The scaling sweeps of Sec. 3.2 on the config-2 recipe: grid sampling R_grid =
+    1e4 .. 3e5 over 300-1000 nm (windows of fixed width in wavelength), and span
+    300-400 .. 300-1000 nm at R_grid = 3e5 (the line density of the full list); per point
+    the wall of one spectrum (line opacity, flux, f) with every pair and with the centre
+    test at eta = 1e-3, CUDA events over `reps` forwards after one warm-up."""
+    import torch
+
+    import paper_2607_24141_gb300 as pz
+    from paper_2607_24141_gb300 import inputs as I
+    stream = torch.cuda.current_stream()
+    reps = max(1, args.scaling_reps)
+    pts = [("R_grid", R, dict(R=R)) for R in (1e4, 3e4, 1e5, 3e5)] + \
+          [("span_nm", hi - 300.0, dict(lam_hi=hi)) for hi in (400.0, 500.0, 700.0)]
+    out = []
+    for kind, val, kw in pts:
+        prob = I.config2_sweep_point(**kw)
+        s = pz.Synthesizer(prob, pz.PZ_MIXED, device=dev.index)
+        if tiling is not None:
+            pz.pz_set_tiling(s.ctx, *tiling)
+        f = torch.empty(prob.grid.n_lambda, dtype=torch.float32, device=dev)
+
+        def fwd():
+            pz.pz_line_opacity(s.ctx, None, stream)
+            pz.pz_flux(s.ctx, None, None, stream)
+            pz.pz_instrument(s.ctx, 0.0, 0.0, 0.0, None, f, stream)
+
+        def timed():
+            fwd()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                fwd()
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
+        ms_all = timed()
+        kept = pz.pz_set_centre_test(s.ctx, 1e-3, stream)
+        ms_cut = timed()
+        pz.pz_sync_status(s.ctx, stream)
+        row = {"sweep": kind, "value": val, "R_grid": prob.grid.R_grid, "n_lambda": prob.grid.n_lambda,
+               "n_lines": prob.lines.n_lines, "W": prob.lines.half_window, "evals": s.n_evals,
+               "ms_all_pairs": ms_all, "ms_centre_test": ms_cut,
+               "kept_pair_frac": kept / max(prob.lines.n_lines * prob.atmos.n_depth, 1)}
+        s.close()
+        del prob
+        out.append(row)
+    by = {(r["sweep"], r["value"]): r for r in out}
+    rs, sp = by[("R_grid", 1e4)], by[("R_grid", 3e5)]
+    s1 = by[("span_nm", 100.0)]
+    return {"workload": "config-2 recipe (solar, 80 species, centres ~ lambda^-2, 3e6 lines over 300-1000 nm): "
+                        "R_grid sweep with W = 2,000 R / 3e5 and span sweep from 300 nm at R_grid = 3e5; f at full "
+                        "resolution; mean of %d forwards after one warm-up" % reps,
+            "points": out,
+            "R_x30_wall_ratio_all_pairs": sp["ms_all_pairs"] / rs["ms_all_pairs"],
+            "R_x30_wall_ratio_centre_test": sp["ms_centre_test"] / rs["ms_centre_test"],
+            "span_100_to_700_lines_ratio": sp["n_lines"] / s1["n_lines"],
+            "span_100_to_700_wall_ratio_all_pairs": sp["ms_all_pairs"] / s1["ms_all_pairs"],
+            "span_100_to_700_wall_ratio_centre_test": sp["ms_centre_test"] / s1["ms_centre_test"],
+            "paper_context": "H100 (Sec. 3.2): R_grid x30 -> wall x3.1-5.0; span 100 -> 700 nm (retained catalog x25) "
+                             "-> wall x1.5-1.8"}
+
+
 def fp64_batch_rate(dev):
     """Evaluations per second of the plain FP64 GPU form on one graph-captured
     calibration step (fwd + bwd) of a 3-star, 2 nm batch of the same recipe."""
@@ -852,6 +920,9 @@ def main():
         lbfgs = run_lbfgs(args, dev, tune["tiling"] if tune else None)
         lbfgs["grouped_four_parameter"] = run_lbfgs_groups(args, dev, tune["tiling"] if tune else None)
 
+    # ---- scaling sweeps (opt-in) ----
+    scaling = run_scaling(args, dev, tune["tiling"] if tune else None) if args.scaling else None
+
     if broad is not None and pipe_peaks.get("fp32"):
         broad["far_fwd_fp32_frac"] = broad["far_fwd_fp32_ops_per_s"] / pipe_peaks["fp32"]
 
@@ -872,6 +943,7 @@ def main():
         "broad_optical_fwd": broad,
         "centre_test": centre,
         "lbfgs_calibration": lbfgs,
+        "scaling_sweeps": scaling,
         "autotune": tune,
     }
     if rank == 0:

@@ -296,16 +296,30 @@ def config1(seed: int = 1, lam_lo: float = 1500.0, lam_hi: float = 1700.0,
 
 
 def config2(seed: int = 2, lam_lo: float = 300.0, lam_hi: float = 1000.0,
-            n_lines: int = 3_000_000, W: int = 2000) -> Problem:
+            n_lines: int = 3_000_000, W: int = 2000, R: float = R_GRID) -> Problem:
     """Broad optical: solar atmosphere, 300-1000 nm, 3e6 lines over 80 species with
-    centre density proportional to lambda^-2, W = 2,000, full-resolution output."""
+    centre density proportional to lambda^-2, W = 2,000, full-resolution output
+    (R_grid = 3e5 unless R is given)."""
     n_species = 80
     atmos = make_atmosphere(5777.0, 4.44, n_species, seed, log_abund_mean=MU_BROAD)
-    grid = Grid(lam_lo, R_GRID, n_lambda_for(lam_lo, lam_hi))
+    grid = Grid(lam_lo, R, n_lambda_for(lam_lo, lam_hi, R))
     rng = np.random.default_rng(seed + 1000)
     lines = _pack([_atomic_lines(rng, n_lines, lam_lo, lam_hi, np.arange(n_species),
                                  centres="inv_uniform")], W)
     return Problem("config2", atmos, grid, lines, make_kappa_c(atmos, grid))
+
+
+def config2_sweep_point(R: float = R_GRID, lam_hi: float = 1000.0, seed: int = 2, lam_lo: float = 300.0,
+                        n_lines_full: int = 3_000_000) -> Problem:
+    """One point of the scaling sweeps of Sec. 3.2 on the config-2 recipe: grid sampling
+    R (the line windows keep their width in wavelength, W = 2,000 R / 3e5 grid points)
+    and span lam_lo..lam_hi (the line density of the 300-1000 nm list, proportional to
+    lambda^-2, so the list holds n_lines_full (1/lam_lo - 1/lam_hi) / (1/300 - 1/1000)
+    lines)."""
+    frac = (1.0 / lam_lo - 1.0 / lam_hi) / (1.0 / 300.0 - 1.0 / 1000.0)
+    W = max(1, int(round(2000.0 * R / R_GRID)))
+    return config2(seed=seed, lam_lo=lam_lo, lam_hi=lam_hi, n_lines=max(1, int(round(n_lines_full * frac))), W=W,
+                   R=R)
 
 
 def config3(seed: int = 3, lam_lo: float = 1500.0, lam_hi: float = 1700.0,
