@@ -44,6 +44,7 @@ class _Problem(C.Structure):
         ("dlog_gf", _dp), ("dlog_gamma6", _dp), ("dabund", _dp), ("elem_of_species", _ip),
         ("centre_eta", C.c_double),
         ("dlog_gamma_rad", _dp), ("dlog_gamma4", _dp),
+        ("sigma_c", _dp),
     ]
 
 
@@ -82,6 +83,8 @@ def lib():
         L.pzo_flux_tau.argtypes = [C.c_int, _dp, _dp]
         L.pzo_flux_tau.restype = C.c_double
         L.pzo_flux_dtau.argtypes = [C.c_int, _dp, _dp, _dp]
+        L.pzo_lambda_matrix.argtypes = [C.c_int, _dp, _dp]
+        L.pzo_scatter_source.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
         L.pzo_planck_nm.argtypes = [C.c_double, C.c_double]
         L.pzo_planck_nm.restype = C.c_double
         _lib = L
@@ -130,6 +133,9 @@ class _Keep:
         P.log_gamma_rad, P.log_gamma4, P.log_gamma6 = _ptr(A["grad"], _fp), _ptr(A["g4"], _fp), _ptr(A["g6"], _fp)
         P.species = _ptr(A["sp"], _ip)
         P.half_window = ll.half_window
+        if getattr(prob, "sigma_c", None) is not None:
+            A["sig"] = _d(prob.sigma_c)
+            P.sigma_c = _ptr(A["sig"], _dp)
         if corrections:
             if corrections.get("dlog_gf") is not None:
                 A["dgf"] = _d(corrections["dlog_gf"])
@@ -180,6 +186,22 @@ def flux_dtau(tau, S):
     tau, S = _d(tau), _d(S)
     out = np.empty_like(tau)
     lib().pzo_flux_dtau(tau.size, _ptr(tau, _dp), _ptr(S, _dp), _ptr(out, _dp))
+    return out
+
+
+def lambda_matrix(tau):
+    """Lambda [nd][nd] of the piecewise-linear source on the layers tau: J = Lambda S."""
+    tau = _d(tau)
+    out = np.empty((tau.size, tau.size))
+    lib().pzo_lambda_matrix(tau.size, _ptr(tau, _dp), _ptr(out, _dp))
+    return out
+
+
+def scatter_source(tau, eps, B):
+    """S solving S = eps B + (1 - eps) Lambda S on the layers tau."""
+    tau, eps, B = _d(tau), _d(eps), _d(B)
+    out = np.empty_like(tau)
+    lib().pzo_scatter_source(tau.size, _ptr(tau, _dp), _ptr(eps, _dp), _ptr(B, _dp), _ptr(out, _dp))
     return out
 
 

@@ -207,6 +207,8 @@ typedef struct {
     double centre_eta;
     /* the other two damping families of Eq. 10 (radiative, Stark); NULL means zero */
     const double *dlog_gamma_rad, *dlog_gamma4;   /* [n_lines] */
+    /* continuum scattering coefficient sigma_c [n_depth][n_lambda] cm^2/g; NULL: none (S = B) */
+    const double *sigma_c;
 } pzo_problem;
 
 /* Eq. 1 */
@@ -345,25 +347,131 @@ static double flux_from(int nd, const double *tau, const double *S) {
     return 2.0 * O_PI * F;
 }
 
-/* F and F_c for the requested columns given kappa_line there (same layout as pzo_kappa_line). */
+/* ---- scattering source function (Eq. 6 with the transfer equation of Sec. 2.3) ----
+ * S = eps B + (1 - eps) J, eps = (kappa_c + sum kappa_l)/chi, chi = kappa_c + sigma_c + sum kappa_l,
+ * J(tau) = 1/2 Int_0^{tau_max} S(t) E_1(|t - tau|) dt (the mean intensity of the same
+ * plane-parallel slab whose emergent flux is taken: S linear between layers, the first segment
+ * extrapolated to tau = 0, nothing below the bottom layer).  With S piecewise linear, J at a layer
+ * is a linear form in the layer values, J = Lambda S; the paper iterates the scattering term,
+ * S <- eps B + (1 - eps) Lambda S, whose fixed point solves (I - diag(1 - eps) Lambda) S = eps B.
+ * The oracle solves that system directly (Gaussian elimination with partial pivoting). */
+
+/* 1/2 Int_a^b S(t) E_1(|t - tj|) dt for S linear from Sa (at a) to Sb (at b), as weights
+ * (*wa, *wb) of Sa and Sb; [a, b] lies wholly below tj (a >= tj) or above it (b <= tj). */
+static void lambda_interval(double tj, double a, double b, double *wa, double *wb) {
+    double D = b - a;
+    if (a >= tj) {
+        /* t = tj + x:  Int (Sa + s(t - a)) E_1(x) = Sa (E2(xa) - E2(xb)) + s (E3(xa) - E3(xb) - D E2(xb)) */
+        double xa = a - tj, xb = b - tj;
+        double e2a = pzo_expn(2, xa), e2b = pzo_expn(2, xb), e3a = pzo_expn(3, xa), e3b = pzo_expn(3, xb);
+        double slope = (e3a - e3b - D * e2b) / D;
+        *wa = 0.5 * ((e2a - e2b) - slope);
+        *wb = 0.5 * slope;
+    } else {
+        /* t = tj - y:  Int (Sb - s(b - t)) E_1(y) = Sb (E2(yb) - E2(ya)) - s (E3(yb) - E3(ya) - D E2(ya)) */
+        double ya = tj - a, yb = tj - b;
+        double e2a = pzo_expn(2, ya), e2b = pzo_expn(2, yb), e3a = pzo_expn(3, ya), e3b = pzo_expn(3, yb);
+        double slope = (e3b - e3a - D * e2a) / D;
+        *wb = 0.5 * ((e2b - e2a) - slope);
+        *wa = 0.5 * slope;
+    }
+}
+
+/* Lambda [nd][nd]: row j gives J(tau_j) from the layer values of S. */
+void pzo_lambda_matrix(int nd, const double *tau, double *Lam) {
+    for (int64_t k = 0; k < (int64_t)nd * nd; ++k) Lam[k] = 0.0;
+    if (nd < 2) return;
+    double D1 = tau[1] - tau[0];
+    for (int j = 0; j < nd; ++j) {
+        double *row = Lam + (int64_t)j * nd;
+        double wa, wb;
+        for (int k = 0; k + 1 < nd; ++k) {
+            lambda_interval(tau[j], tau[k], tau[k + 1], &wa, &wb);
+            row[k] += wa;
+            row[k + 1] += wb;
+        }
+        /* top interval [0, tau_0]: S(0) = S_0 - s_0 tau_0 with s_0 = (S_1 - S_0)/D1 */
+        lambda_interval(tau[j], 0.0, tau[0], &wa, &wb);
+        row[0] += wa * (1.0 + tau[0] / D1) + wb;
+        row[1] += -wa * tau[0] / D1;
+    }
+}
+
+/* Solve (I - diag(1 - eps) Lambda) S = eps B for S. */
+void pzo_scatter_source(int nd, const double *tau, const double *eps, const double *B, double *S) {
+    double *A = (double *)malloc(sizeof(double) * (size_t)nd * (nd + 1));
+    double *Lam = (double *)malloc(sizeof(double) * (size_t)nd * nd);
+    pzo_lambda_matrix(nd, tau, Lam);
+    int W = nd + 1;
+    for (int j = 0; j < nd; ++j) {
+        for (int k = 0; k < nd; ++k) A[(int64_t)j * W + k] = (j == k ? 1.0 : 0.0) - (1.0 - eps[j]) * Lam[(int64_t)j * nd + k];
+        A[(int64_t)j * W + nd] = eps[j] * B[j];
+    }
+    for (int p = 0; p < nd; ++p) {
+        int piv = p;
+        for (int r = p + 1; r < nd; ++r)
+            if (fabs(A[(int64_t)r * W + p]) > fabs(A[(int64_t)piv * W + p])) piv = r;
+        if (piv != p)
+            for (int k = 0; k < W; ++k) {
+                double t = A[(int64_t)p * W + k];
+                A[(int64_t)p * W + k] = A[(int64_t)piv * W + k];
+                A[(int64_t)piv * W + k] = t;
+            }
+        for (int r = p + 1; r < nd; ++r) {
+            double f = A[(int64_t)r * W + p] / A[(int64_t)p * W + p];
+            for (int k = p; k < W; ++k) A[(int64_t)r * W + k] -= f * A[(int64_t)p * W + k];
+        }
+    }
+    for (int p = nd - 1; p >= 0; --p) {
+        double v = A[(int64_t)p * W + nd];
+        for (int k = p + 1; k < nd; ++k) v -= A[(int64_t)p * W + k] * S[k];
+        S[p] = v / A[(int64_t)p * W + p];
+    }
+    free(Lam);
+    free(A);
+}
+
+/* F and F_c for the requested columns given kappa_line there (same layout as pzo_kappa_line).
+ * Without sigma_c, S = B in both branches; with it, each branch solves its own scattering
+ * source (total: eps = (kappa_c + kappa_line)/chi; continuum: eps_c = kappa_c/(kappa_c + sigma_c)). */
 void pzo_flux(const pzo_problem *P, int64_t n_cols, const int64_t *cols, const double *kline,
               double *F, double *Fc) {
     int nd = P->n_depth;
 #pragma omp parallel for schedule(static)
     for (int64_t c = 0; c < n_cols; ++c) {
         int64_t i = cols[c];
-        double *chi = (double *)malloc(sizeof(double) * nd * 4);
-        double *chic = chi + nd, *tau = chi + 2 * nd, *S = chi + 3 * nd;
+        double *chi = (double *)malloc(sizeof(double) * nd * 7);
+        double *chic = chi + nd, *tau = chi + 2 * nd, *S = chi + 3 * nd, *B = chi + 4 * nd;
+        double *eps = chi + 5 * nd, *Ssc = chi + 6 * nd;
         double lam = grid_lambda_cm(P, i);
         for (int d = 0; d < nd; ++d) {
-            chic[d] = P->kappa_c[(int64_t)d * P->n_lambda + i];
-            chi[d] = chic[d] + kline[(int64_t)d * n_cols + c];
-            S[d] = planck_nm(lam, P->T[d]);
+            int64_t o = (int64_t)d * P->n_lambda + i;
+            double sig = P->sigma_c ? P->sigma_c[o] : 0.0;
+            double kl = kline[(int64_t)d * n_cols + c];
+            chic[d] = P->kappa_c[o] + sig;
+            chi[d] = P->kappa_c[o] + kl + sig;
+            B[d] = planck_nm(lam, P->T[d]);
+            S[d] = B[d];
+            eps[d] = (P->kappa_c[o] + kl) / chi[d];
         }
         optical_depth(nd, P->m, chi, tau);
-        F[c] = flux_from(nd, tau, S);
+        if (P->sigma_c) {
+            pzo_scatter_source(nd, tau, eps, B, Ssc);
+            F[c] = flux_from(nd, tau, Ssc);
+        } else {
+            F[c] = flux_from(nd, tau, S);
+        }
         optical_depth(nd, P->m, chic, tau);
-        Fc[c] = flux_from(nd, tau, S);
+        if (P->sigma_c) {
+            for (int d = 0; d < nd; ++d) {
+                int64_t o = (int64_t)d * P->n_lambda + i;
+                eps[d] = P->kappa_c[o] / chic[d];
+            }
+            pzo_scatter_source(nd, tau, eps, B, Ssc);
+            Fc[c] = flux_from(nd, tau, Ssc);
+        } else {
+            Fc[c] = flux_from(nd, tau, S);
+        }
         free(chi);
     }
 }

@@ -127,6 +127,7 @@ class Problem:
     instrument: Optional[Instrument] = None
     elem_of_species: Optional[np.ndarray] = None   # int32 [n_species]
     n_elem: int = 0
+    sigma_c: Optional[np.ndarray] = None   # float64 [n_depth, n_lambda] continuum scattering, or None
 
     @property
     def n_evals(self) -> int:
@@ -357,8 +358,22 @@ def wavelength_slice(prob: Problem, lam_lo_nm: float, n_points: int) -> Problem:
     il = center_index(g, prob.lines.lambda_nm)
     W = prob.lines.half_window
     keep = np.nonzero((il + W >= i0) & (il - W <= i0 + n - 1))[0]
+    sig = None if prob.sigma_c is None else np.ascontiguousarray(prob.sigma_c[:, i0:i0 + n])
     return Problem(prob.name + "-slice", prob.atmos, grid, prob.lines.subset(keep),
-                   np.ascontiguousarray(prob.kappa_c[:, i0:i0 + n]), None, prob.elem_of_species, prob.n_elem)
+                   np.ascontiguousarray(prob.kappa_c[:, i0:i0 + n]), None, prob.elem_of_species, prob.n_elem, sig)
+
+
+def with_scattering(prob: Problem, r0: float = 1.0, lam_ref_nm: float = 400.0) -> Problem:
+    """The same problem with a continuum scattering coefficient (Eq. 6 with sigma_c > 0):
+    sigma_c = kappa_c r0 (lambda / lam_ref)^-4 / (1 + tau_d), tau_d = 10^(-6.875 + 0.125 d)
+    the recipe's reference optical depth of layer d (linspace of the same range for other
+    layer counts): Rayleigh-like in wavelength, strongest in the upper layers, negligible
+    where the continuum thermalises."""
+    nd = prob.atmos.n_depth
+    x = -6.875 + 0.125 * np.arange(nd) if nd == 72 else np.linspace(-6.875, 2.0, nd)
+    lam = grid_lambda_nm(prob.grid)
+    ratio = r0 * (lam[None, :] / lam_ref_nm) ** -4.0 / (1.0 + 10.0 ** x[:, None])
+    return dataclasses.replace(prob, name=prob.name + "+scat", sigma_c=np.ascontiguousarray(prob.kappa_c * ratio))
 
 
 def small_config1(n_lambda_span_nm: float = 2.0, lines_scale: float = 0.01, seed: int = 11,

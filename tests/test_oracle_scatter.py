@@ -1,0 +1,104 @@
+"""Pins of the oracle's scattering source function (Eq. 6, S = eps B + (1 - eps) J, with
+J the mean intensity of the same slab): the Lambda operator against closed forms of
+J for constant and linear sources, against adaptive quadrature of the E_1 kernel, the
+solved source against the exact sqrt(eps) law of a scattering-dominated isothermal
+atmosphere, and sigma_c = 0 against the LTE flux."""
+import numpy as np
+import pytest
+
+from tiny import tiny_problem
+
+special = pytest.importorskip("scipy.special")
+integrate = pytest.importorskip("scipy.integrate")
+
+
+def _tau_grid(nd, lo=-6.0, hi=2.0, seed=0):
+    rng = np.random.default_rng(seed)
+    x = np.sort(np.concatenate([[lo, hi], rng.uniform(lo, hi, nd - 2)]))
+    return 10.0 ** x
+
+
+def test_lambda_of_constant_source(oracle):
+    """S = 1 on [0, T]: J(tau) = 1 - E2(tau)/2 - E2(T - tau)/2 (the linear extrapolation to
+    tau = 0 and the interpolation both represent a constant exactly)."""
+    tau = _tau_grid(40)
+    T = tau[-1]
+    Lam = oracle.lambda_matrix(tau)
+    J = Lam @ np.ones(tau.size)
+    ref = 1.0 - 0.5 * special.expn(2, tau) - 0.5 * special.expn(2, T - tau)
+    np.testing.assert_allclose(J, ref, rtol=1e-12, atol=1e-14)
+
+
+def test_lambda_of_linear_source(oracle):
+    """S = t on [0, T]: J(tau) = tau + E3(tau)/2 - T E2(T - tau)/2 - E3(T - tau)/2."""
+    tau = _tau_grid(35, seed=1)
+    T = tau[-1]
+    J = oracle.lambda_matrix(tau) @ tau
+    ref = tau + 0.5 * special.expn(3, tau) - 0.5 * T * special.expn(2, T - tau) - 0.5 * special.expn(3, T - tau)
+    np.testing.assert_allclose(J, ref, rtol=1e-11, atol=1e-13)
+
+
+def test_lambda_against_quadrature(oracle):
+    """An arbitrary piecewise-linear source: J = 1/2 Int S(t) E_1(|t - tau_j|) dt by
+    adaptive quadrature of each interval (the logarithmic singularity sits at an
+    interval end), with the first segment extrapolated to t = 0."""
+    tau = _tau_grid(12, lo=-3.0, hi=1.0, seed=2)
+    S = np.random.default_rng(3).uniform(0.5, 2.0, tau.size)
+    J = oracle.lambda_matrix(tau) @ S
+    s0 = (S[1] - S[0]) / (tau[1] - tau[0])
+    knots = np.concatenate([[0.0], tau])
+    vals = np.concatenate([[S[0] - s0 * tau[0]], S])
+    for j in range(tau.size):
+        tot = 0.0
+        for k in range(knots.size - 1):
+            a, b, Sa, Sb = knots[k], knots[k + 1], vals[k], vals[k + 1]
+
+            def f(t):
+                return (Sa + (Sb - Sa) * (t - a) / (b - a)) * special.exp1(abs(t - tau[j]))
+            tot += integrate.quad(f, a, b, limit=200, epsabs=1e-15, epsrel=1e-13)[0]
+        assert abs(J[j] - 0.5 * tot) <= 1e-10 * abs(0.5 * tot), (j, J[j], 0.5 * tot)
+
+
+def _isothermal(oracle, eps, n):
+    tau = np.concatenate([[1e-8], np.geomspace(1e-6, 1e6, n)])
+    return tau, oracle.scatter_source(tau, np.full(tau.size, eps), np.ones(tau.size))
+
+
+@pytest.mark.parametrize("eps", [0.5, 0.1, 1e-2])
+def test_sqrt_eps_law(oracle, eps):
+    """Isothermal (B = 1), constant eps, effectively semi-infinite: the exact solution
+    has S(0) = sqrt(eps) B, and S -> B deep inside (thermalisation depth ~ 1/sqrt(eps)).
+    The piecewise-linear source converges to it at second order in the grid step (the
+    small surface value carries the discretisation error of J relative to the deep B,
+    so small eps needs finer grids)."""
+    tau, S = _isothermal(oracle, eps, 800)
+    assert abs(S[0] / np.sqrt(eps) - 1) < 2.5e-3, S[0]
+    mid = np.argmin(np.abs(tau - 100.0 / np.sqrt(eps)))
+    assert abs(S[mid] - 1) < 1e-3
+    e1 = abs(_isothermal(oracle, eps, 400)[1][0] / np.sqrt(eps) - 1)
+    e2 = abs(S[0] / np.sqrt(eps) - 1)
+    assert e2 < e1 / 3.0 or e2 < 1e-5, (e1, e2)
+    # the fixed point of the iteration S <- eps B + (1 - eps) Lambda S
+    Lam = oracle.lambda_matrix(tau)
+    np.testing.assert_allclose(S, eps + (1 - eps) * (Lam @ S), rtol=1e-10, atol=1e-12)
+
+
+def test_no_scattering_is_lte(oracle):
+    """sigma_c = 0 everywhere gives eps = 1, S = B and the LTE flux bit for bit."""
+    prob = tiny_problem(n_lambda=150, n_depth=12, n_lines=10, W=60, seed=4)
+    import dataclasses
+    ref = oracle.forward(prob)
+    got = oracle.forward(dataclasses.replace(prob, sigma_c=np.zeros_like(prob.kappa_c)))
+    assert np.array_equal(got["F"], ref["F"]) and np.array_equal(got["Fc"], ref["Fc"])
+
+
+def test_scattering_lowers_the_surface_source(oracle):
+    """With sigma_c > 0 in the upper layers, the emergent continuum drops below the LTE
+    one where the scattering albedo is large (blue), and the line-to-continuum ratio
+    stays in (0, 1]."""
+    from paper_2607_24141_gb300 import inputs as I
+    prob = tiny_problem(n_lambda=150, n_depth=30, n_lines=10, W=60, seed=4, lam0=350.0)
+    sc = I.with_scattering(prob, r0=3.0)
+    lte, scat = oracle.forward(prob), oracle.forward(sc)
+    assert np.all(scat["Fc"] < lte["Fc"])
+    assert np.all(scat["f"] > 0) and np.all(scat["f"] <= 1 + 1e-12)
