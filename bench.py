@@ -69,6 +69,7 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default line-kernel tiling")
     ap.add_argument("--no-broad", action="store_true", help="skip the 300-1000 nm forward measurement")
     ap.add_argument("--broad-steps", type=int, default=3)
+    ap.add_argument("--no-scatter", action="store_true", help="skip the scattering forward of the 300-1000 nm spectrum")
     ap.add_argument("--no-centre", action="store_true", help="skip the centre-test measurement")
     ap.add_argument("--no-lbfgs", action="store_true", help="skip the L-BFGS calibration measurement")
     ap.add_argument("--scaling", action="store_true", help="run the R_grid and span scaling sweeps (about a minute)")
@@ -353,6 +354,31 @@ def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None):
     ms = max_over_ranks(a.elapsed_time(b)) / args.broad_steps
     kt = pz.pz_kernel_times(s.ctx)
     pz.pz_sync_status(s.ctx, stream)
+    # continuum scattering (Eq. 6) on the same spectrum: Rayleigh-like sigma_c, r0 = 1 at 400 nm
+    scat = None
+    if not args.no_scatter:
+        f_lte = f.clone()
+        pz.pz_set_scattering(s.ctx, I.with_scattering(prob, r0=1.0).sigma_c, stream)
+        fwd()
+        torch.cuda.synchronize()
+        pz.pz_set_profiling(s.ctx, False)
+        pz.pz_set_profiling(s.ctx, True)
+        a.record(stream)
+        for _ in range(args.broad_steps):
+            fwd()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms_sc = a.elapsed_time(b) / args.broad_steps
+        kt_sc = pz.pz_kernel_times(s.ctx)
+        df = (f - f_lte).abs()
+        scat = {"workload": "the same spectrum with sigma_c = kappa_c (lambda/400 nm)^-4 / (1 + tau_d): source "
+                            "S = eps B + (1 - eps) J solved per wavelength (72 x 72 FP64 system, both branches)",
+                "s_per_spectrum_fwd": ms_sc * 1e-3,
+                "flux_ms": kt_sc["flux"][0] / max(args.broad_steps, 1),
+                "flux_ms_lte": kt["flux"][0] / max(args.broad_steps, 1),
+                "max_abs_df_vs_lte": float(df.max()), "rms_df_vs_lte": float(df.double().pow(2).mean().sqrt())}
+        pz.pz_set_scattering(s.ctx, None)
+        pz.pz_sync_status(s.ctx, stream)
     s.close()
     far_ms = (kt["line_fwd"][0] - kt["near_fwd"][0]) / max(kt["line_fwd"][1], 1)
     out = {"workload": "300-1000 nm at R_grid=3e5 (%d pts) x %d lines (80 species, centres ~ lambda^-2) x 72 depths, "
@@ -361,7 +387,8 @@ def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None):
            "create_s": t_create,
            "kernel_ms_per_step": {k: v[0] / args.broad_steps for k, v in kt.items() if v[1] > 0},
            "far_fwd_ms": far_ms,
-           "far_fwd_fp32_ops_per_s": evals * OPS["line_fwd"]["fp32_reduced"] / (far_ms * 1e-3)}
+           "far_fwd_fp32_ops_per_s": evals * OPS["line_fwd"]["fp32_reduced"] / (far_ms * 1e-3),
+           "scattering": scat}
     # plain FP64 GPU form on a slice of the same line list
     if not args.no_fp64:
         sl = I.wavelength_slice(prob, 600.0, 1200)

@@ -256,6 +256,24 @@ pz_status pz_calib_step(pz_ctx *ctx, const float *y, const float *w, int64_t n, 
                         float lr_g6, float lr_ab, double *loss, float *g_dlog_gf,
                         float *g_dlog_gamma6, float *g_dabund, void *stream);
 
+/* ---- continuum scattering (Eq. 6) --------------------------------------------- */
+
+/* Continuum scattering in the formal solution.  With sigma_c set, the extinction is
+ * chi = kappa_c + sigma_c + kappa_line and the source function is
+ *   S = eps B + (1 - eps) J,   eps = (kappa_c + kappa_line) / chi        (Eq. 6),
+ * J the mean intensity of the same plane-parallel slab the flux is taken from (S linear
+ * in tau between layers, the first segment extrapolated to tau = 0, nothing below the
+ * bottom layer).  The paper iterates the scattering term; its fixed point, the solution
+ * of (I - diag(1 - eps) Lambda) S = eps B, is computed directly per wavelength in FP64
+ * (one CTA per wavelength and star).  The continuum branch uses
+ * eps_c = kappa_c / (kappa_c + sigma_c).  sigma_c: host FP64 [S][n_depth][n_lambda],
+ * cm^2/g, finite and >= 0, copied; NULL turns scattering off (S = B).  Synchronous.
+ * The forward must run again.  The reverse pass does not cover scattering: while it is
+ * on, pz_backward, pz_backward4, pz_calib_step and pz_group_eval return PZ_ESTATE.
+ * Errors: PZ_EINVAL (negative or non-finite sigma_c, fewer than two layers), PZ_ENOMEM,
+ * PZ_ECUDA. */
+pz_status pz_set_scattering(pz_ctx *ctx, const double *sigma_c, void *stream);
+
 /* ---- four-parameter grouped calibration (Sec. 6, Eq. 10) --------------------- */
 
 /* Corrections of the other two damping families of Eq. 10: the radiative and Stark

@@ -88,6 +88,7 @@ _SIGS = {
     "pz_probe_wait": (C.c_int, [C.c_int64, C.POINTER(C.c_int32), _vp]),
     "pz_sync_status": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32)]),
     "pz_set_damping_corrections": (C.c_int, [_vp, _vp, _vp, _vp]),
+    "pz_set_scattering": (C.c_int, [_vp, _vp, _vp]),
     "pz_backward4": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pz_set_line_groups": (C.c_int, [_vp, _vp, C.c_int64]),
     "pz_group_eval": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
@@ -252,6 +253,15 @@ def pz_set_damping_corrections(ctx, dlog_gamma_rad=None, dlog_gamma4=None, strea
             return a.ctypes.data
         return x.data_ptr()
     _check(load().pz_set_damping_corrections(ctx, p(dlog_gamma_rad), p(dlog_gamma4), _stream(stream)))
+
+
+def pz_set_scattering(ctx, sigma_c=None, stream=None):
+    """Continuum scattering coefficient, host FP64 [S][n_depth][n_lambda] (None: off)."""
+    if sigma_c is None:
+        _check(load().pz_set_scattering(ctx, None, _stream(stream)))
+        return
+    a = np.ascontiguousarray(sigma_c, dtype=np.float64)
+    _check(load().pz_set_scattering(ctx, a.ctypes.data, _stream(stream)))
 
 
 def pz_backward4(ctx, dL_df, g_dlog_gf=None, g_dlog_gamma_rad=None, g_dlog_gamma4=None, g_dlog_gamma6=None,
@@ -429,6 +439,8 @@ class Synthesizer:
             self.n_stars = 1
             self.n_depth = prob.atmos.n_depth
         self._keep = keep
+        if not self.batched and getattr(prob, "sigma_c", None) is not None:
+            pz_set_scattering(self.ctx, prob.sigma_c)
         self.device = torch.device("cuda", device)
         self.n_lambda = prob.grid.n_lambda
         self.n_lines = prob.lines.n_lines

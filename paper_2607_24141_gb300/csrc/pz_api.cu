@@ -230,7 +230,7 @@ static void destroy_ctx(pz_ctx *c) {
                     c->d_F, c->d_Fc, c->d_g, c->d_gc, c->d_tap0, c->d_ntap, c->d_tapw, c->d_dFbar, c->d_Gt,
                     c->d_Gt64, c->d_gacc, c->d_gline, c->d_gab, c->d_dLdf, c->d_ftab, c->d_finfo, c->d_status,
                     c->d_keep, c->L.gradbase, c->L.g4base, c->L.dgrad, c->L.dg4, c->d_mdgrad, c->d_mdg4,
-                    c->d_grp_of, c->d_grp_off, c->d_grp_mem};
+                    c->d_grp_of, c->d_grp_off, c->d_grp_mem, c->d_sigma};
     for (void *p : ptrs) dfree(p);
     for (auto &m : c->marks) {
         cudaEventDestroy(m.a);
@@ -1009,6 +1009,7 @@ pz_status pz_backward(pz_ctx *c, const float *dLdf, float *g_gf, float *g_g6, fl
     if (!c) return fail(PZ_EINVAL, "pz_backward: ctx is NULL");
     if (!c->have_inst) return fail(PZ_ESTATE, "pz_backward: call pz_instrument first");
     if (!dLdf) return fail(PZ_EINVAL, "pz_backward: dL_df is NULL");
+    if (c->d_sigma) return fail(PZ_ESTATE, "pz_backward: no reverse pass through continuum scattering");
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
     PZ_TRY(ensure_backward_buffers(c));
@@ -1020,6 +1021,7 @@ pz_status pz_backward4(pz_ctx *c, const float *dLdf, float *g_gf, float *g_rad, 
     if (!c) return fail(PZ_EINVAL, "pz_backward4: ctx is NULL");
     if (!c->have_inst) return fail(PZ_ESTATE, "pz_backward4: call pz_instrument first");
     if (!dLdf) return fail(PZ_EINVAL, "pz_backward4: dL_df is NULL");
+    if (c->d_sigma) return fail(PZ_ESTATE, "pz_backward4: no reverse pass through continuum scattering");
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
     PZ_TRY(ensure_backward_buffers(c));
@@ -1046,6 +1048,7 @@ pz_status pz_calib_step(pz_ctx *c, const float *y, const float *w, int64_t n, fl
     if (!c) return fail(PZ_EINVAL, "pz_calib_step: ctx is NULL");
     if (c->n_out <= 0) return fail(PZ_ESTATE, "pz_calib_step: call pz_instrument once first");
     if (!y) return fail(PZ_EINVAL, "pz_calib_step: y is NULL");
+    if (c->d_sigma) return fail(PZ_ESTATE, "pz_calib_step: no reverse pass through continuum scattering");
     if (n != c->n_out) return fail(PZ_EINVAL, "pz_calib_step: n differs from the instrument output size");
     if (!std::isfinite(lr_gf) || !std::isfinite(lr_g6) || !std::isfinite(lr_ab))
         return fail(PZ_EINVAL, "pz_calib_step: learning rates must be finite");
@@ -1173,6 +1176,7 @@ pz_status pz_group_eval(pz_ctx *c, const float *y, const float *w, int64_t n, co
     if (c->n_groups <= 0) return fail(PZ_ESTATE, "pz_group_eval: call pz_set_line_groups first");
     if (c->n_out <= 0) return fail(PZ_ESTATE, "pz_group_eval: call pz_instrument once first");
     if (!y || !x) return fail(PZ_EINVAL, "pz_group_eval: y and x are required");
+    if (c->d_sigma) return fail(PZ_ESTATE, "pz_group_eval: no reverse pass through continuum scattering");
     if (n != c->n_out) return fail(PZ_EINVAL, "pz_group_eval: n differs from the instrument output size");
     cudaStream_t s = (cudaStream_t)stream;
     PZ_TRY(ensure_backward_buffers(c));
@@ -1263,6 +1267,38 @@ pz_status pz_build_line_groups(int64_t n, const double *lambda_nm, const float *
     }
     for (int64_t k = 0; k < n; ++k) group_of_line[k] = q[k];
     *n_groups = G;
+    return PZ_OK;
+}
+
+pz_status pz_set_scattering(pz_ctx *c, const double *sigma_c, void *stream) {
+    if (!c) return fail(PZ_EINVAL, "pz_set_scattering: ctx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!sigma_c) {
+        if (c->d_sigma) {
+            PZ_CUDA(cudaStreamSynchronize(s), "pz_set_scattering");
+            dfree(c->d_sigma);
+            c->d_sigma = nullptr;
+        }
+        c->have_flux = c->have_inst = false;
+        return PZ_OK;
+    }
+    if (c->nd < 2) return fail(PZ_EINVAL, "pz_set_scattering: needs at least two layers");
+    const size_t n = (size_t)c->S * c->nd * c->nlam;
+    for (size_t k = 0; k < n; ++k)
+        if (!(sigma_c[k] >= 0.0) || !std::isfinite(sigma_c[k]))
+            return fail(PZ_EINVAL, "pz_set_scattering: sigma_c must be finite and >= 0");
+    drop_graph(c);
+    PZ_CUDA(cudaStreamSynchronize(s), "pz_set_scattering");
+    if (!c->d_sigma) {
+        PZ_TRY(dalloc(&c->d_sigma, (size_t)c->S * c->nd * c->ld, "sigma_c"));
+        PZ_CUDA(cudaMemset(c->d_sigma, 0, sizeof(double) * (size_t)c->S * c->nd * c->ld), "sigma_c");
+    }
+    for (int st = 0; st < c->S; ++st)
+        PZ_CUDA(cudaMemcpy2D(c->d_sigma + (size_t)st * c->nd * c->ld, c->ld * sizeof(double),
+                             sigma_c + (size_t)st * c->nd * c->nlam, c->nlam * sizeof(double),
+                             c->nlam * sizeof(double), c->nd, cudaMemcpyHostToDevice),
+                "sigma_c");
+    c->have_flux = c->have_inst = false;
     return PZ_OK;
 }
 

@@ -125,6 +125,7 @@ struct pz_ctx {
     float *d_thr = nullptr;         // [S][ns][nslab] fast-path distance threshold (grid units)
     int nslab = 0;                  // depth slabs of DS layers covered by the launch grid
     double *d_kc = nullptr;         // [S][nd][ld] continuum opacity FP64
+    double *d_sigma = nullptr;      // [S][nd][ld] continuum scattering FP64, or NULL (S = B)
     double *d_dab = nullptr;        // [n_elem] current abundance offsets
     float *d_mdgf = nullptr, *d_mdg6 = nullptr;   // [nl_caller] current line corrections, caller order
     float *d_mdgrad = nullptr, *d_mdg4 = nullptr; // [nl_caller] radiative and Stark corrections, caller order

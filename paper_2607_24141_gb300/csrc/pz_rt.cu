@@ -255,7 +255,10 @@ __global__ void k_flux(FluxArgs g) {
     g.Fc[i] = 2.0 * kPI * Fc;
 }
 
+cudaError_t launch_flux_scatter(pz_ctx *c, cudaStream_t s);
+
 cudaError_t launch_flux(pz_ctx *c, cudaStream_t s) {
+    if (c->d_sigma) return launch_flux_scatter(c, s);
     FluxArgs g;
     g.nlam = c->nlam;
     g.ld = c->ld;
@@ -273,6 +276,188 @@ cudaError_t launch_flux(pz_ctx *c, cudaStream_t s) {
         k_flux<float><<<nb, 128, 0, s>>>(g);
     else
         k_flux<double><<<nb, 128, 0, s>>>(g);
+    c->launches++;
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Scattering source function (Eq. 6): S = eps B + (1 - eps) J with eps the absorption
+// fraction of the extinction and J the mean intensity of the same slab the flux is
+// taken from (S linear between layers, first segment extrapolated to tau = 0, nothing
+// below the bottom layer).  J = Lambda S is linear in the layer values; the iteration
+// of the scattering term converges to the solution of (I - diag(1 - eps) Lambda) S = eps B,
+// which is solved here directly, one CTA per (wavelength, star), both branches in turn.
+//
+// Lambda row j: every segment [a, b] of the source contributes
+//   1/2 Int_a^b S E_1(|t - tau_j|) dt = P (Sa + Sb)/2 + Q (Sb - Sa)/2  (segment below tau_j)
+// with x = t - tau_j: P = E2(xa) - E2(xb) (the weight of a constant) and
+// Q = 2 (E3(xa) - E3(xb) - D E2(xb)) / D - P (the odd part), mirrored for segments above.
+// Errors of Q from cancellation at tiny D multiply Sb - Sa, which is small there.
+// The matrix is diagonally dominant (row sums of Lambda <= 1, 1 - eps < 1), so Gaussian
+// elimination runs without pivoting.
+// ---------------------------------------------------------------------------
+struct ScatArgs {
+    int64_t nlam, ld;
+    int nd;
+    double lam0cm, lnr;
+    const double *m, *T, *kc, *sig;
+    const void *kline;
+    double *F, *Fc;
+};
+
+constexpr int kScatThreads = 128;
+
+size_t scatter_smem(int nd) { return sizeof(double) * ((size_t)nd * (nd + 1) + 8 * (size_t)nd); }
+
+// weights of the near and far ends of a segment of length D seen from depth tj, from
+// E2, E3 at the distances of its near (n) and far (f) ends
+__device__ __forceinline__ void seg_weights(double D, double e2n, double e3n, double e2f, double e3f, double &wn,
+                                            double &wf) {
+    const double P = e2n - e2f;
+    const double Q = 2.0 * (e3n - e3f - D * e2f) / D - P;
+    wn = 0.25 * (P - Q);
+    wf = 0.25 * (P + Q);
+}
+
+template <typename KT>
+__global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
+    extern __shared__ double sm[];
+    const int nd = g.nd, W = nd + 1;
+    double *M = sm;                        // [nd][nd + 1], right-hand side in column nd
+    double *tau = M + (size_t)nd * W;
+    double *chi = tau + nd;
+    double *eps = chi + nd;
+    double *B = eps + nd;
+    double *S = B + nd;
+    double *fac = S + nd;
+    double *e3 = fac + nd;
+    double *e4 = e3 + nd;
+    const int64_t i = blockIdx.x;
+    const int st = blockIdx.y;
+    const int tid = threadIdx.x;
+    const double *m = g.m + (int64_t)st * nd;
+    const double *T = g.T + (int64_t)st * nd;
+    const int64_t base = (int64_t)st * nd * g.ld + i;
+    const KT *kl = reinterpret_cast<const KT *>(g.kline);
+    const double lam = g.lam0cm * exp((double)i * g.lnr);
+    for (int d = tid; d < nd; d += blockDim.x) B[d] = planck_nm(lam, T[d]);
+    for (int branch = 0; branch < 2; ++branch) {
+        for (int d = tid; d < nd; d += blockDim.x) {
+            const int64_t o = base + (int64_t)d * g.ld;
+            const double ka = g.kc[o] + (branch == 0 ? (double)kl[o] : 0.0);   // absorption
+            chi[d] = ka + g.sig[o];
+            eps[d] = ka / chi[d];
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double t = chi[0] * m[0];
+            tau[0] = t;
+            for (int d = 1; d < nd; ++d) {
+                t += 0.5 * (chi[d - 1] + chi[d]) * (m[d] - m[d - 1]);
+                tau[d] = t;
+            }
+        }
+        __syncthreads();
+        // rows of I - diag(1 - eps) Lambda and the right-hand side eps B
+        const double D1 = tau[1] - tau[0];
+        for (int j = tid; j < nd; j += blockDim.x) {
+            double *row = M + (size_t)j * W;
+            for (int k = 0; k < nd; ++k) row[k] = 0.0;
+            const double tj = tau[j];
+            // E2, E3 at each layer's distance from tau_j, each computed once and shared by
+            // the two segments that meet there
+            double e2p, e3p, e4;
+            expn234(fabs(tau[0] - tj), e2p, e3p, e4);
+            {
+                // top segment [0, tau_0] (above every layer): S(0) = S0 - tau_0 (S1 - S0)/D1
+                double e2z, e3z, wn, wf;
+                expn234(tj, e2z, e3z, e4);
+                seg_weights(tau[0], e2p, e3p, e2z, e3z, wn, wf);   // near: tau_0, far: 0
+                row[0] += wf * (1.0 + tau[0] / D1) + wn;
+                row[1] -= wf * (tau[0] / D1);
+            }
+            for (int k = 0; k + 1 < nd; ++k) {
+                double e2k, e3k, wn, wf;
+                expn234(fabs(tau[k + 1] - tj), e2k, e3k, e4);
+                const double D = tau[k + 1] - tau[k];
+                if (k >= j) {          // below tau_j: near end k, far end k + 1
+                    seg_weights(D, e2p, e3p, e2k, e3k, wn, wf);
+                    row[k] += wn;
+                    row[k + 1] += wf;
+                } else {               // above: near end k + 1, far end k
+                    seg_weights(D, e2k, e3k, e2p, e3p, wn, wf);
+                    row[k + 1] += wn;
+                    row[k] += wf;
+                }
+                e2p = e2k;
+                e3p = e3k;
+            }
+            const double w = 1.0 - eps[j];
+            for (int k = 0; k < nd; ++k) row[k] = (k == j ? 1.0 : 0.0) - w * row[k];
+            row[nd] = eps[j] * B[j];
+        }
+        __syncthreads();
+        // forward elimination
+        for (int p = 0; p + 1 < nd; ++p) {
+            const double inv = 1.0 / M[(size_t)p * W + p];
+            for (int r = p + 1 + tid; r < nd; r += blockDim.x) fac[r] = M[(size_t)r * W + p] * inv;
+            __syncthreads();
+            const int rows = nd - 1 - p, cols = nd - p;   // columns p+1 .. nd
+            for (int e = tid; e < rows * cols; e += blockDim.x) {
+                const int r = p + 1 + e / cols, cc = p + 1 + e % cols;
+                M[(size_t)r * W + cc] -= fac[r] * M[(size_t)p * W + cc];
+            }
+            __syncthreads();
+        }
+        // back substitution (column-oriented)
+        for (int p = nd - 1; p >= 0; --p) {
+            if (tid == 0) S[p] = M[(size_t)p * W + nd] / M[(size_t)p * W + p];
+            __syncthreads();
+            for (int r = tid; r < p; r += blockDim.x) M[(size_t)r * W + nd] -= M[(size_t)r * W + p] * S[p];
+            __syncthreads();
+        }
+        // emergent flux of the solved source, the closed form of the LTE kernel
+        for (int d = tid; d < nd; d += blockDim.x) {
+            double e2;
+            expn234(tau[d], e2, e3[d], e4[d]);
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const double s0 = (S[1] - S[0]) / D1;
+            double F = interval(0.0, tau[0], S[0] - s0 * tau[0], S[0], 0.5, 1.0 / 3.0, e3[0], e4[0]);
+            for (int d = 0; d + 1 < nd; ++d) F += interval(tau[d], tau[d + 1], S[d], S[d + 1], e3[d], e4[d], e3[d + 1], e4[d + 1]);
+            (branch == 0 ? g.F : g.Fc)[(int64_t)st * g.nlam + i] = 2.0 * kPI * F;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_flux_scatter(pz_ctx *c, cudaStream_t s) {
+    ScatArgs g;
+    g.nlam = c->nlam;
+    g.ld = c->ld;
+    g.nd = c->nd;
+    g.lam0cm = c->lambda0_nm * 1e-7;
+    g.lnr = c->lnr;
+    g.m = c->d_m;
+    g.T = c->d_T;
+    g.kc = c->d_kc;
+    g.sig = c->d_sigma;
+    g.kline = c->d_kline;
+    g.F = c->d_F;
+    g.Fc = c->d_Fc;
+    const size_t smem = scatter_smem(c->nd);
+    static bool attr_set[64] = {false};
+    if (!attr_set[c->device]) {
+        cudaFuncSetAttribute(k_flux_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        cudaFuncSetAttribute(k_flux_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        attr_set[c->device] = true;
+    }
+    dim3 nb((unsigned)c->nlam, c->S);
+    if (c->prec == PZ_MIXED)
+        k_flux_scatter<float><<<nb, kScatThreads, smem, s>>>(g);
+    else
+        k_flux_scatter<double><<<nb, kScatThreads, smem, s>>>(g);
     c->launches++;
     return cudaGetLastError();
 }
