@@ -305,21 +305,66 @@ struct ScatArgs {
     double *F, *Fc;
 };
 
-constexpr int kScatThreads = 128;
+constexpr int kScatThreads = 256;
+constexpr int kScatTableMaxDepth = 96;    // the E2/E3 pair table fits shared memory up to here
+constexpr int kScatMaxRefine = 12;        // iterative-refinement rounds at most
 
-size_t scatter_smem(int nd) { return sizeof(double) * ((size_t)nd * (nd + 1) + 8 * (size_t)nd); }
+// shared memory: the FP64 system [nd][nd + 1], ten FP64 vectors, the FP32 LU factors
+// [nd][nd], and with the table the packed upper triangle of (E2, E3) pairs plus (E2, E3)
+// at tau_j itself
+static size_t scatter_smem(int nd, bool table) {
+    size_t n = (size_t)nd * (nd + 1) + 10 * (size_t)nd;
+    if (table) n += (size_t)nd * (nd + 1) + 2 * (size_t)nd;
+    return sizeof(double) * n + sizeof(float) * (size_t)nd * nd;
+}
 
-// weights of the near and far ends of a segment of length D seen from depth tj, from
-// E2, E3 at the distances of its near (n) and far (f) ends
-__device__ __forceinline__ void seg_weights(double D, double e2n, double e3n, double e2f, double e3f, double &wn,
-                                            double &wf) {
+// One warp solves L U x = r with the FP32 factors (unit lower L and U in place in LU,
+// row stride nd); lane l holds rows l, l + 32, l + 64, l + 96.  r and the result in y.
+__device__ __forceinline__ float pick4(const float (&y)[4], int q) {
+    return q == 0 ? y[0] : (q == 1 ? y[1] : (q == 2 ? y[2] : y[3]));
+}
+__device__ __forceinline__ void lu_solve_warp(const float *LU, int nd, int lane, float (&y)[4]) {
+    for (int p = 0; p < nd; ++p) {
+        const float yp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int row = lane + 32 * q;
+            if (row > p && row < nd) y[q] = fmaf(-LU[row * nd + p], yp, y[q]);
+        }
+    }
+    for (int p = nd - 1; p >= 0; --p) {
+        const float xp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31) / LU[p * nd + p];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int row = lane + 32 * q;
+            if (row < p) y[q] = fmaf(-LU[row * nd + p], xp, y[q]);
+            if (row == p) y[q] = xp;
+        }
+    }
+}
+
+// E2, E3 at distance x; beyond x = 40 they are below e^-40 / 40 and are taken as zero
+// (a weight there is below 1e-19 of the local ones)
+__device__ __forceinline__ void e23(double x, double &e2, double &e3) {
+    if (x > 40.0) {
+        e2 = e3 = 0.0;
+        return;
+    }
+    double e4;
+    expn234(x, e2, e3, e4);
+}
+
+// weights of the near and far ends of a segment (inverse length invD) seen from depth
+// tau_j, from E2, E3 at the distances of its near (n) and far (f) ends
+__device__ __forceinline__ void seg_weights(double D, double invD, double e2n, double e3n, double e2f, double e3f,
+                                            double &wn, double &wf) {
     const double P = e2n - e2f;
-    const double Q = 2.0 * (e3n - e3f - D * e2f) / D - P;
+    const double Q = 2.0 * (e3n - e3f - D * e2f) * invD - P;
     wn = 0.25 * (P - Q);
     wf = 0.25 * (P + Q);
 }
 
-template <typename KT>
+template <typename KT, bool TABLE>
 __global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
     extern __shared__ double sm[];
     const int nd = g.nd, W = nd + 1;
@@ -332,6 +377,12 @@ __global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
     double *fac = S + nd;
     double *e3 = fac + nd;
     double *e4 = e3 + nd;
+    double *invD = e4 + nd;                // 1 / (tau_{k+1} - tau_k)
+    double *res = invD + nd;               // residual of the refinement
+    double *ET = res + nd;                 // TABLE: (E2, E3) of pair (j <= k) at 2 idx(j, k)
+    double *Etop = ET + (TABLE ? (size_t)nd * W : 0);   // TABLE: (E2, E3) at tau_j
+    float *LU = reinterpret_cast<float *>(Etop + (TABLE ? 2 * (size_t)nd : 0));   // [nd][nd] FP32
+    __shared__ int s_done;
     const int64_t i = blockIdx.x;
     const int st = blockIdx.y;
     const int tid = threadIdx.x;
@@ -358,34 +409,63 @@ __global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
             }
         }
         __syncthreads();
+        for (int k = tid; k + 1 < nd; k += blockDim.x) invD[k] = 1.0 / (tau[k + 1] - tau[k]);
+        const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+        if (TABLE) {
+            // E2, E3 at |tau_j - tau_k| for every pair once (the distance is symmetric):
+            // warps over j, lanes over k >= j
+            for (int j = warp; j < nd; j += nwarp) {
+                const size_t r0 = (size_t)j * nd - (size_t)j * (j - 1) / 2 - j;
+                for (int k = j + lane; k < nd; k += 32) {
+                    const size_t idx = r0 + k;
+                    e23(tau[k] - tau[j], ET[2 * idx], ET[2 * idx + 1]);
+                }
+            }
+            for (int j = tid; j < nd; j += blockDim.x) e23(tau[j], Etop[2 * j], Etop[2 * j + 1]);
+        }
+        __syncthreads();
         // rows of I - diag(1 - eps) Lambda and the right-hand side eps B
         const double D1 = tau[1] - tau[0];
         for (int j = tid; j < nd; j += blockDim.x) {
             double *row = M + (size_t)j * W;
             for (int k = 0; k < nd; ++k) row[k] = 0.0;
             const double tj = tau[j];
-            // E2, E3 at each layer's distance from tau_j, each computed once and shared by
-            // the two segments that meet there
-            double e2p, e3p, e4;
-            expn234(fabs(tau[0] - tj), e2p, e3p, e4);
+            auto E = [&](int k, double &e2, double &e3) {
+                if (TABLE) {
+                    const int a = min(j, k), b = max(j, k);
+                    const size_t idx = (size_t)a * nd - (size_t)a * (a - 1) / 2 + (b - a);
+                    e2 = ET[2 * idx];
+                    e3 = ET[2 * idx + 1];
+                } else {
+                    e23(fabs(tau[k] - tj), e2, e3);
+                }
+            };
+            // E2, E3 at each layer's distance from tau_j, shared by the two segments that meet there
+            double e2p, e3p;
+            E(0, e2p, e3p);
             {
                 // top segment [0, tau_0] (above every layer): S(0) = S0 - tau_0 (S1 - S0)/D1
                 double e2z, e3z, wn, wf;
-                expn234(tj, e2z, e3z, e4);
-                seg_weights(tau[0], e2p, e3p, e2z, e3z, wn, wf);   // near: tau_0, far: 0
+                if (TABLE) {
+                    e2z = Etop[2 * j];
+                    e3z = Etop[2 * j + 1];
+                } else {
+                    e23(tj, e2z, e3z);
+                }
+                seg_weights(tau[0], 1.0 / tau[0], e2p, e3p, e2z, e3z, wn, wf);   // near: tau_0, far: 0
                 row[0] += wf * (1.0 + tau[0] / D1) + wn;
                 row[1] -= wf * (tau[0] / D1);
             }
             for (int k = 0; k + 1 < nd; ++k) {
                 double e2k, e3k, wn, wf;
-                expn234(fabs(tau[k + 1] - tj), e2k, e3k, e4);
+                E(k + 1, e2k, e3k);
                 const double D = tau[k + 1] - tau[k];
                 if (k >= j) {          // below tau_j: near end k, far end k + 1
-                    seg_weights(D, e2p, e3p, e2k, e3k, wn, wf);
+                    seg_weights(D, invD[k], e2p, e3p, e2k, e3k, wn, wf);
                     row[k] += wn;
                     row[k + 1] += wf;
                 } else {               // above: near end k + 1, far end k
-                    seg_weights(D, e2k, e3k, e2p, e3p, wn, wf);
+                    seg_weights(D, invD[k], e2k, e3k, e2p, e3p, wn, wf);
                     row[k + 1] += wn;
                     row[k] += wf;
                 }
@@ -397,23 +477,64 @@ __global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
             row[nd] = eps[j] * B[j];
         }
         __syncthreads();
-        // forward elimination
+        // LU factors in FP32 (no pivoting: the system is diagonally dominant), then iterative
+        // refinement with FP64 residuals: S += (LU)^-1 (eps B - M S) until the correction is
+        // below 1e-14 of S
+        for (int r = warp; r < nd; r += nwarp)
+            for (int k = lane; k < nd; k += 32) LU[r * nd + k] = (float)M[(size_t)r * W + k];
+        __syncthreads();
         for (int p = 0; p + 1 < nd; ++p) {
-            const double inv = 1.0 / M[(size_t)p * W + p];
-            for (int r = p + 1 + tid; r < nd; r += blockDim.x) fac[r] = M[(size_t)r * W + p] * inv;
-            __syncthreads();
-            const int rows = nd - 1 - p, cols = nd - p;   // columns p+1 .. nd
-            for (int e = tid; e < rows * cols; e += blockDim.x) {
-                const int r = p + 1 + e / cols, cc = p + 1 + e % cols;
-                M[(size_t)r * W + cc] -= fac[r] * M[(size_t)p * W + cc];
+            // rows below the pivot: warps over rows, lanes over columns p+1 .. nd-1; each
+            // warp scales its row's multiplier itself (lane-uniform value)
+            const float inv = 1.0f / LU[p * nd + p];
+            for (int r = p + 1 + warp; r < nd; r += nwarp) {
+                const float f = LU[r * nd + p] * inv;
+                for (int k = p + 1 + lane; k < nd; k += 32) LU[r * nd + k] = fmaf(-f, LU[p * nd + k], LU[r * nd + k]);
+                __syncwarp();
+                if (lane == 0) LU[r * nd + p] = f;
             }
             __syncthreads();
         }
-        // back substitution (column-oriented)
-        for (int p = nd - 1; p >= 0; --p) {
-            if (tid == 0) S[p] = M[(size_t)p * W + nd] / M[(size_t)p * W + p];
+        for (int d = tid; d < nd; d += blockDim.x) {
+            S[d] = 0.0;
+            res[d] = M[(size_t)d * W + nd];
+        }
+        __syncthreads();
+        for (int it = 0; it < kScatMaxRefine; ++it) {
+            if (tid < 32) {
+                float y[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int row = tid + 32 * q;
+                    y[q] = row < nd ? (float)res[row] : 0.0f;
+                }
+                lu_solve_warp(LU, nd, tid, y);
+                double dmax = 0.0, smax = 0.0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int row = tid + 32 * q;
+                    if (row < nd) {
+                        const double v = S[row] + (double)y[q];
+                        S[row] = v;
+                        dmax = fmax(dmax, fabs((double)y[q]));
+                        smax = fmax(smax, fabs(v));
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+                    smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+                }
+                if (tid == 0) s_done = dmax <= 1e-14 * smax;
+            }
             __syncthreads();
-            for (int r = tid; r < p; r += blockDim.x) M[(size_t)r * W + nd] -= M[(size_t)r * W + p] * S[p];
+            if (s_done) break;
+            for (int j = tid; j < nd; j += blockDim.x) {
+                const double *row = M + (size_t)j * W;
+                double r = row[nd];
+                for (int k = 0; k < nd; ++k) r = fma(-row[k], S[k], r);
+                res[j] = r;
+            }
             __syncthreads();
         }
         // emergent flux of the solved source, the closed form of the LTE kernel
@@ -432,6 +553,29 @@ __global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
     }
 }
 
+template <bool TABLE>
+static cudaError_t launch_scatter_t(pz_ctx *c, const ScatArgs &g, cudaStream_t s) {
+    const size_t smem = scatter_smem(c->nd, TABLE);
+    static size_t attr_set[64] = {0};   // dynamic shared memory granted so far, per device
+    if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
+    if (smem > attr_set[c->device]) {
+        cudaError_t e = cudaFuncSetAttribute(k_flux_scatter<float, TABLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_flux_scatter<double, TABLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set[c->device] = smem;
+    }
+    dim3 nb((unsigned)c->nlam, c->S);
+    if (c->prec == PZ_MIXED)
+        k_flux_scatter<float, TABLE><<<nb, kScatThreads, smem, s>>>(g);
+    else
+        k_flux_scatter<double, TABLE><<<nb, kScatThreads, smem, s>>>(g);
+    c->launches++;
+    return cudaGetLastError();
+}
+
 cudaError_t launch_flux_scatter(pz_ctx *c, cudaStream_t s) {
     ScatArgs g;
     g.nlam = c->nlam;
@@ -446,20 +590,7 @@ cudaError_t launch_flux_scatter(pz_ctx *c, cudaStream_t s) {
     g.kline = c->d_kline;
     g.F = c->d_F;
     g.Fc = c->d_Fc;
-    const size_t smem = scatter_smem(c->nd);
-    static bool attr_set[64] = {false};
-    if (!attr_set[c->device]) {
-        cudaFuncSetAttribute(k_flux_scatter<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        cudaFuncSetAttribute(k_flux_scatter<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        attr_set[c->device] = true;
-    }
-    dim3 nb((unsigned)c->nlam, c->S);
-    if (c->prec == PZ_MIXED)
-        k_flux_scatter<float><<<nb, kScatThreads, smem, s>>>(g);
-    else
-        k_flux_scatter<double><<<nb, kScatThreads, smem, s>>>(g);
-    c->launches++;
-    return cudaGetLastError();
+    return c->nd <= kScatTableMaxDepth ? launch_scatter_t<true>(c, g, s) : launch_scatter_t<false>(c, g, s);
 }
 
 // ---------------------------------------------------------------------------
