@@ -372,7 +372,7 @@ def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None):
         kt_sc = pz.pz_kernel_times(s.ctx)
         df = (f - f_lte).abs()
         scat = {"workload": "the same spectrum with sigma_c = kappa_c (lambda/400 nm)^-4 / (1 + tau_d): source "
-                            "S = eps B + (1 - eps) J solved per wavelength (72 x 72 FP64 system, both branches)",
+                            "S = eps B + (1 - eps) J solved per wavelength (72 x 72 system: FP32 LU, FP64 refinement; both branches)",
                 "s_per_spectrum_fwd": ms_sc * 1e-3,
                 "flux_ms": kt_sc["flux"][0] / max(args.broad_steps, 1),
                 "flux_ms_lte": kt["flux"][0] / max(args.broad_steps, 1),
