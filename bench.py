@@ -39,7 +39,7 @@ WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
 # kernel on this workload (profiles/k_line_bwd_apogee.md: 6.479 GB read + 86.0 MB written, default
 # tiling), valid only while the kernel sources hash to the recorded value; otherwise null.
-TRAFFIC = {"k_line_bwd": (6.5652e9, "3a0f98c915da3681")}
+TRAFFIC = {"k_line_bwd": (6.5007e9, "cb477eccf9e280d5")}
 KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h")
 
 # Per-evaluation pipe work of the far-wing kernels, which evaluate every in-window cell.
