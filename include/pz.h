@@ -284,6 +284,12 @@ pz_status pz_set_scattering(pz_ctx *ctx, const double *sigma_c, void *stream);
 pz_status pz_set_damping_corrections(pz_ctx *ctx, const float *dlog_gamma_rad,
                                      const float *dlog_gamma4, void *stream);
 
+/* Current radiative and Stark corrections in caller order (after
+ * pz_set_damping_corrections or pz_group_eval): [n_lines] FP32, host or device
+ * memory, each may be NULL.  Synchronises `stream`.  Errors: PZ_ECUDA. */
+pz_status pz_get_damping_corrections(pz_ctx *ctx, float *dlog_gamma_rad, float *dlog_gamma4,
+                                     void *stream);
+
 /* Reverse pass to all four per-line gradients of Eq. 10 -- Delta log gf and the
  * three damping families -- and the per-element abundance gradients:
  *   dL/dDelta log gamma_beta,l = ln10 sum_{i in window, d} G stim A_ld (dH/da) a_beta,ld

@@ -8,7 +8,8 @@ The compute lives in ``libpz.so`` (CUDA, sm_103a) behind the C ABI declared in
   point, same name, raising :class:`PzError` on a non-zero status;
 * :class:`Synthesizer` -- owns one context plus the host arrays it was built
   from, with torch CUDA tensors as device buffers;
-* :class:`SynthesisFunction` -- a ``torch.autograd.Function`` whose forward is
+* :class:`SynthesisFunction` (and :class:`SynthesisFunction4`, all four corrections of
+  Eq. 10) -- a ``torch.autograd.Function`` whose forward is
   line opacity -> flux -> instrument and whose backward is ``pz_backward``.
 
 There is no CPU fallback: if the library cannot be loaded every call raises.
@@ -89,6 +90,7 @@ _SIGS = {
     "pz_sync_status": (C.c_int, [_vp, _vp, C.POINTER(C.c_int32)]),
     "pz_set_damping_corrections": (C.c_int, [_vp, _vp, _vp, _vp]),
     "pz_set_scattering": (C.c_int, [_vp, _vp, _vp]),
+    "pz_get_damping_corrections": (C.c_int, [_vp, _vp, _vp, _vp]),
     "pz_backward4": (C.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "pz_set_line_groups": (C.c_int, [_vp, _vp, C.c_int64]),
     "pz_group_eval": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
@@ -262,6 +264,15 @@ def pz_set_scattering(ctx, sigma_c=None, stream=None):
         return
     a = np.ascontiguousarray(sigma_c, dtype=np.float64)
     _check(load().pz_set_scattering(ctx, a.ctypes.data, _stream(stream)))
+
+
+def pz_get_damping_corrections(ctx, dlog_gamma_rad=None, dlog_gamma4=None, stream=None):
+    """Copy the radiative and Stark corrections into numpy (host) or torch (device) arrays."""
+    def p(x):
+        if x is None:
+            return None
+        return x.ctypes.data if isinstance(x, np.ndarray) else x.data_ptr()
+    _check(load().pz_get_damping_corrections(ctx, p(dlog_gamma_rad), p(dlog_gamma4), _stream(stream)))
 
 
 def pz_backward4(ctx, dL_df, g_dlog_gf=None, g_dlog_gamma_rad=None, g_dlog_gamma4=None, g_dlog_gamma6=None,
@@ -439,8 +450,10 @@ class Synthesizer:
             self.n_stars = 1
             self.n_depth = prob.atmos.n_depth
         self._keep = keep
-        if not self.batched and getattr(prob, "sigma_c", None) is not None:
-            pz_set_scattering(self.ctx, prob.sigma_c)
+        sig = getattr(prob, "sigma_c", None)
+        if sig is not None:
+            # one star: [n_depth][n_lambda]; a batch: one such array per star
+            pz_set_scattering(self.ctx, np.stack(sig) if self.batched else sig)
         self.device = torch.device("cuda", device)
         self.n_lambda = prob.grid.n_lambda
         self.n_lines = prob.lines.n_lines
@@ -501,6 +514,19 @@ class Synthesizer:
                    stream=None):
         pz_calib_step(self.ctx, y, w, lr_gf, lr_g6, lr_ab, loss, g_gf, g_g6, g_ab, stream)
 
+    def set_damping_corrections(self, dlog_gamma_rad=None, dlog_gamma4=None, stream=None):
+        pz_set_damping_corrections(self.ctx, dlog_gamma_rad, dlog_gamma4, stream)
+
+    def backward4(self, dL_df, g_gf=None, g_rad=None, g_g4=None, g_g6=None, g_ab=None, stream=None):
+        pz_backward4(self.ctx, dL_df, g_gf, g_rad, g_g4, g_g6, g_ab, stream)
+
+    def get_damping_corrections(self):
+        """(dlog_gamma_rad, dlog_gamma4) as host float32 arrays."""
+        r = np.empty(self.n_lines, np.float32)
+        s4 = np.empty(self.n_lines, np.float32)
+        pz_get_damping_corrections(self.ctx, r, s4)
+        return r, s4
+
     def get_corrections(self):
         """(dlog_gf, dlog_gamma6, dabund or None) as host float32 arrays."""
         gf = np.empty(self.n_lines, np.float32)
@@ -541,7 +567,40 @@ def _torch_function():
     return SynthesisFunction
 
 
+def _torch_function4():
+    import torch
+
+    class SynthesisFunction4(torch.autograd.Function):
+        """f = instrument(flux(line_opacity(corrections))) over the four per-line
+        corrections of Eq. 10 (Delta log gf, Delta log gamma_rad, Delta log gamma_4,
+        Delta log gamma_6) and the abundance offsets, float32 CUDA tensors; gradients
+        come from ``pz_backward4``."""
+
+        @staticmethod
+        def forward(ctx, synth, dlog_gf, dlog_gamma_rad, dlog_gamma4, dlog_gamma6, dabund):
+            synth.set_corrections(dlog_gf, dlog_gamma6, dabund)
+            synth.set_damping_corrections(dlog_gamma_rad, dlog_gamma4)
+            f = synth.forward()
+            ctx.synth = synth
+            ctx.has_ab = dabund is not None
+            return f
+
+        @staticmethod
+        def backward(ctx, grad_f):
+            s = ctx.synth
+            grad_f = grad_f.contiguous().to(torch.float32)
+            nl = s.n_lines
+            g = [torch.empty(nl, dtype=torch.float32, device=grad_f.device) for _ in range(4)]
+            g_ab = torch.empty(s.prob.n_elem, dtype=torch.float32, device=grad_f.device) if ctx.has_ab else None
+            s.backward4(grad_f, g[0], g[1], g[2], g[3], g_ab)
+            return None, g[0], g[1], g[2], g[3], g_ab
+
+    return SynthesisFunction4
+
+
 def __getattr__(name):
     if name == "SynthesisFunction":
         return _torch_function()
+    if name == "SynthesisFunction4":
+        return _torch_function4()
     raise AttributeError(name)

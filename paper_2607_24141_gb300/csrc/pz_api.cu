@@ -1117,6 +1117,17 @@ pz_status pz_set_damping_corrections(pz_ctx *c, const float *dgrad, const float 
     return PZ_OK;
 }
 
+pz_status pz_get_damping_corrections(pz_ctx *c, float *dgrad, float *dg4, void *stream) {
+    if (!c) return fail(PZ_EINVAL, "pz_get_damping_corrections: ctx is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = c->nl_caller;
+    if (dgrad && n > 0)
+        PZ_CUDA(cudaMemcpyAsync(dgrad, c->d_mdgrad, sizeof(float) * n, cudaMemcpyDefault, s), "dlog_gamma_rad");
+    if (dg4 && n > 0) PZ_CUDA(cudaMemcpyAsync(dg4, c->d_mdg4, sizeof(float) * n, cudaMemcpyDefault, s), "dlog_gamma4");
+    PZ_CUDA(cudaStreamSynchronize(s), "pz_get_damping_corrections");
+    return PZ_OK;
+}
+
 pz_status pz_set_line_groups(pz_ctx *c, const int32_t *group_of_line, int64_t n_groups) {
     if (!c) return fail(PZ_EINVAL, "pz_set_line_groups: ctx is NULL");
     if (n_groups < 0 || n_groups > INT32_MAX) return fail(PZ_EINVAL, "pz_set_line_groups: n_groups out of range");

@@ -363,6 +363,12 @@ def wavelength_slice(prob: Problem, lam_lo_nm: float, n_points: int) -> Problem:
                    np.ascontiguousarray(prob.kappa_c[:, i0:i0 + n]), None, prob.elem_of_species, prob.n_elem, sig)
 
 
+def with_scattering_batch(batch: "Batch", r0: float = 1.0, lam_ref_nm: float = 400.0) -> "Batch":
+    """with_scattering applied to every star of a batch (each star's own kappa_c and layers)."""
+    sig = [with_scattering(batch.star(k), r0, lam_ref_nm).sigma_c for k in range(batch.n_stars)]
+    return dataclasses.replace(batch, name=batch.name + "+scat", sigma_c=sig)
+
+
 def with_scattering(prob: Problem, r0: float = 1.0, lam_ref_nm: float = 400.0) -> Problem:
     """The same problem with a continuum scattering coefficient (Eq. 6 with sigma_c > 0):
     sigma_c = kappa_c r0 (lambda / lam_ref)^-4 / (1 + tau_d), tau_d = 10^(-6.875 + 0.125 d)
@@ -413,6 +419,7 @@ class Batch:
     instrument: Optional[Instrument] = None
     elem_of_species: Optional[np.ndarray] = None
     n_elem: int = 0
+    sigma_c: Optional[list] = None  # [S] float64 [n_depth, n_lambda] continuum scattering, or None
 
     @property
     def n_stars(self) -> int:
@@ -421,7 +428,8 @@ class Batch:
     def star(self, k: int) -> Problem:
         """Star k as a single-star problem (its own line subset, caller order kept)."""
         return Problem("%s[%d]" % (self.name, k), self.atmos[k], self.grid, self.lines.subset(self.subsets[k]),
-                       self.kappa_c[k], self.instrument, self.elem_of_species, self.n_elem)
+                       self.kappa_c[k], self.instrument, self.elem_of_species, self.n_elem,
+                       None if self.sigma_c is None else self.sigma_c[k])
 
     @property
     def n_evals(self) -> int:

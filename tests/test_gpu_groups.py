@@ -130,3 +130,69 @@ def test_group_eval_state_errors():
         pz.pz_set_line_groups(s.ctx, np.full(prob.lines.n_lines, 5, np.int32), 3)
     assert e.value.status == pz.PZ_EINVAL
     s.close()
+
+
+def test_group_eval_batch_parity(oracle):
+    """Two stars with uneven line subsets sharing the grouped corrections: the objective
+    is the sum over the stars and each group gradient sums its members over the stars."""
+    import torch
+    b = I.small_batch(n_stars=2, span_nm=1.5, seed=41)
+    nl = b.lines.n_lines
+    q, G = _grouping(nl, 5)
+    rng = np.random.default_rng(13)
+    x = rng.normal(0, [[0.1], [0.3], [0.3], [0.2]], (4, G)).astype(np.float32)
+    e = oracle.expand_groups(x.astype(np.float64), q)
+    L_ref, g_line = 0.0, np.zeros((4, nl))
+    ys = []
+    for k in range(b.n_stars):
+        pk = b.star(k)
+        sub = b.subsets[k]
+        corr = {key: e[j][sub] for j, key in enumerate(KEYS)}
+        y, w, f0 = _target(oracle, pk, corr, 20 + k)
+        ys.append(y)
+        r = oracle.gradient4(pk, y, w, corr, fwd=f0)
+        L_ref += r["L"]
+        for j, key in enumerate(("gf", "gamma_rad", "gamma4", "gamma6")):
+            np.add.at(g_line[j], sub, r[key])
+    g_ref = oracle.group_sum(g_line, q, G)
+    s = pz.Synthesizer(b, pz.PZ_MIXED)
+    s.forward()
+    pz.pz_set_line_groups(s.ctx, q, G)
+    dev = s.device
+    yt = torch.tensor(np.stack(ys), dtype=torch.float32, device=dev)
+    wt = torch.full_like(yt, 200.0 ** 2)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    g = torch.empty((4, G), dtype=torch.float32, device=dev)
+    pz.pz_group_eval(s.ctx, yt, wt, torch.tensor(x, device=dev), loss, g)
+    assert abs(loss.item() / L_ref - 1) < 1e-3
+    g1 = g.cpu().numpy().astype(np.float64)
+    errs = [rel_metric(g1[j], g_ref[j]).max() for j in range(4)]
+    print("group eval batch", errs)
+    assert max(errs) < 1e-3, errs
+    r_rad, r_4 = s.get_damping_corrections()
+    np.testing.assert_array_equal(r_rad, np.where(q >= 0, x[1][np.maximum(q, 0)], 0).astype(np.float32))
+    np.testing.assert_array_equal(r_4, np.where(q >= 0, x[2][np.maximum(q, 0)], 0).astype(np.float32))
+    s.close()
+
+
+def test_autograd_function4_matches_the_oracle(oracle):
+    import torch
+    prob = I.small_config1(n_lambda_span_nm=1.5, seed=19)
+    nl = prob.lines.n_lines
+    rng = np.random.default_rng(3)
+    c = {k: rng.normal(0, 0.2, nl).astype(np.float32) for k in KEYS}
+    c64 = {k: v.astype(np.float64) for k, v in c.items()}
+    y, w, f0 = _target(oracle, prob, c64, 9)
+    ref = oracle.gradient4(prob, y, w, c64, fwd=f0)
+    s = pz.Synthesizer(prob)
+    dev = s.device
+    t = {k: torch.tensor(v, device=dev, requires_grad=True) for k, v in c.items()}
+    f = pz.SynthesisFunction4.apply(s, t["dlog_gf"], t["dlog_gamma_rad"], t["dlog_gamma4"], t["dlog_gamma6"], None)
+    yt = torch.tensor(y, dtype=torch.float32, device=dev)
+    L = (((yt - f) ** 2) * float(w[0])).double().sum()
+    L.backward()
+    assert abs(L.item() / ref["L"] - 1) < 1e-3
+    for key, rk in zip(KEYS, ("gf", "gamma_rad", "gamma4", "gamma6")):
+        err = rel_metric(t[key].grad.cpu().numpy().astype(np.float64), ref[rk]).max()
+        assert err < 1e-3, (key, err)
+    s.close()

@@ -80,3 +80,13 @@ def test_scattering_state_rules():
     # the LTE spectrum again (up to the order of the near-core shared-memory atomics)
     np.testing.assert_allclose(s.forward().cpu().numpy(), f_lte, rtol=0, atol=1e-6)
     s.close()
+
+
+def test_scattering_batch_matches_the_oracle_per_star(oracle):
+    b = I.with_scattering_batch(I.small_batch(n_stars=2, span_nm=1.0, seed=23, with_instrument=False), r0=200.0)
+    s = pz.Synthesizer(b, pz.PZ_FP64)
+    f = s.forward().cpu().numpy().astype(np.float64)
+    for k in range(b.n_stars):
+        ref = oracle.forward(b.star(k))
+        assert np.max(np.abs(f[k] - ref["f"])) < 1e-6
+    s.close()
