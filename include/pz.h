@@ -304,9 +304,9 @@ pz_status pz_backward4(pz_ctx *ctx, const float *dL_df, float *g_dlog_gf, float 
 
 /* Linked correction groups q(l) (Sec. 6: every component of a group shares the
  * group's four corrections).  group_of_line: host int32 [n_lines] in caller order,
- * values in [0, n_groups) or -1 for a line that takes no correction; n_groups = 0
- * removes the groups.  Synchronous; drops captured graphs.
- * Errors: PZ_EINVAL (group id out of range), PZ_ENOMEM, PZ_ECUDA. */
+ * values in [0, n_groups) or -1 for a line that takes no correction; n_groups in
+ * [0, n_lines], 0 removes the groups.  Synchronous; drops captured graphs.
+ * Errors: PZ_EINVAL (n_groups or a group id out of range), PZ_ENOMEM, PZ_ECUDA. */
 pz_status pz_set_line_groups(pz_ctx *ctx, const int32_t *group_of_line, int64_t n_groups);
 
 /* One objective and gradient evaluation of the grouped calibration over all stars,

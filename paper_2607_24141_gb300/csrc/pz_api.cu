@@ -1130,7 +1130,8 @@ pz_status pz_get_damping_corrections(pz_ctx *c, float *dgrad, float *dg4, void *
 
 pz_status pz_set_line_groups(pz_ctx *c, const int32_t *group_of_line, int64_t n_groups) {
     if (!c) return fail(PZ_EINVAL, "pz_set_line_groups: ctx is NULL");
-    if (n_groups < 0 || n_groups > INT32_MAX) return fail(PZ_EINVAL, "pz_set_line_groups: n_groups out of range");
+    if (n_groups < 0 || n_groups > std::max<int64_t>(c->nl_caller, 1))
+        return fail(PZ_EINVAL, "pz_set_line_groups: n_groups must be in [0, n_lines]");
     if (n_groups > 0 && !group_of_line) return fail(PZ_EINVAL, "pz_set_line_groups: group_of_line is NULL");
     const int64_t n = c->nl_caller;
     std::vector<int32_t> q(std::max<int64_t>(n, 1), -1);
