@@ -41,6 +41,7 @@ WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts
 # tiling), valid only while the kernel sources hash to the recorded value; otherwise null.
 TRAFFIC = {"k_line_bwd": (6.5007e9, "cb477eccf9e280d5")}
 KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h")
+FMA_PER_EN = 39      # FP64 FMAs of one E_2/E_3/E_4 Taylor step (13 rounds of value + two derivatives)
 
 # Per-evaluation pipe work of the far-wing kernels, which evaluate every in-window cell.
 # Reduced form (lines >= 100 Doppler widths from the whole tile, most cells of this
@@ -315,7 +316,7 @@ def run_batched(args, dev, barrier, max_over_ranks, ws, tiling=None):
 # ---------------------------------------------------------------------------
 # broad optical forward: 300-1000 nm at R_grid = 3e5, 3e6 lines
 # ---------------------------------------------------------------------------
-def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None):
+def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None, pipe_peaks=None):
     """Forward (line opacity -> tau + flux -> normalised flux at full resolution) of
     the 300-1000 nm workload (361,193 points x 3e6 lines x 72 depths, W = 2,000),
     timed with CUDA events; the plain FP64 GPU form is timed on a 1,200-point slice
@@ -371,12 +372,20 @@ def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None):
         ms_sc = a.elapsed_time(b) / args.broad_steps
         kt_sc = pz.pz_kernel_times(s.ctx)
         df = (f - f_lte).abs()
+        nd = prob.atmos.n_depth
+        # E_n evaluations per wavelength and branch: every layer pair once, the top
+        # boundary and the flux
+        en_col = 2 * (nd * (nd + 1) // 2 + 2 * nd)
+        t_sc = kt_sc["flux"][0] * 1e-3 / max(args.broad_steps, 1)
+        scat_fma = en_col * prob.grid.n_lambda * FMA_PER_EN / t_sc
         scat = {"workload": "the same spectrum with sigma_c = kappa_c (lambda/400 nm)^-4 / (1 + tau_d): source "
                             "S = eps B + (1 - eps) J solved per wavelength (72 x 72 system: FP32 LU, FP64 refinement; both branches)",
                 "s_per_spectrum_fwd": ms_sc * 1e-3,
                 "flux_ms": kt_sc["flux"][0] / max(args.broad_steps, 1),
                 "flux_ms_lte": kt["flux"][0] / max(args.broad_steps, 1),
-                "max_abs_df_vs_lte": float(df.max()), "rms_df_vs_lte": float(df.double().pow(2).mean().sqrt())}
+                "max_abs_df_vs_lte": float(df.max()), "rms_df_vs_lte": float(df.double().pow(2).mean().sqrt()),
+                "En_per_wavelength": en_col, "En_fp64_fma_per_s": scat_fma,
+                "En_fp64_frac": scat_fma / pipe_peaks["fp64"] if (pipe_peaks or {}).get("fp64") else None}
         pz.pz_set_scattering(s.ctx, None)
         pz.pz_sync_status(s.ctx, stream)
     s.close()
@@ -787,7 +796,8 @@ def main():
     # ---- pipe peaks (roofline denominators of the ALU-bound line kernels) ----
     pipe_peaks = {}
     try:
-        pipe_peaks = {"fp32": pz.pz_probe_pipe(0, 4096, stream), "mufu": pz.pz_probe_pipe(1, 4096, stream)}
+        pipe_peaks = {"fp32": pz.pz_probe_pipe(0, 4096, stream), "mufu": pz.pz_probe_pipe(1, 4096, stream),
+                      "fp64": pz.pz_probe_pipe(2, 512, stream)}
     except Exception:
         pipe_peaks = {}
 
@@ -885,7 +895,7 @@ def main():
     # ---- broad optical forward ----
     broad = None
     if not args.no_broad:
-        broad = run_broad(args, dev, barrier, max_over_ranks, ws, tune["tiling"] if tune else None)
+        broad = run_broad(args, dev, barrier, max_over_ranks, ws, tune["tiling"] if tune else None, pipe_peaks)
 
     # ---- roofline of the dominant kernel ----
     props = torch.cuda.get_device_properties(local)
@@ -936,6 +946,21 @@ def main():
         "hbm_gbs_peak": peaks.get("hbm_gbs"),
     }
 
+    # ---- the FP64 transfer stage against the measured FP64 FMA peak ----
+    # E_n evaluations: two per (lambda, depth) in the flux (both branches), one in its
+    # adjoint; each is a Taylor step of FMA_PER_EN FP64 FMAs (the other FP64 work of the
+    # stage -- tau, Planck, the interval weights -- is not counted)
+    rt = None
+    if pipe_peaks.get("fp64") and ktimes["flux"][1] > 0:
+        cells = prob.grid.n_lambda * prob.atmos.n_depth
+        rt = {"bound": "fp64", "unit": "GFMA/s", "peak": pipe_peaks["fp64"] * 1e-9, "fma_per_En": FMA_PER_EN,
+              "peak_source": "measured: pz_probe_pipe FP64 FMA throughput (%d SMs)" % n_sm}
+        for name, per_cell in (("flux", 2), ("rt_adjoint", 1)):
+            t = ktimes[name][0] * 1e-3 / max(ktimes[name][1], 1)
+            ach = per_cell * cells * FMA_PER_EN / t
+            rt[name] = {"ms_per_launch": t * 1e3, "En_per_launch": per_cell * cells, "achieved": ach * 1e-9,
+                        "frac": ach / pipe_peaks["fp64"]}
+
     # ---- continuum-referenced centre test (the paper's line rejection) ----
     centre = None
     if not args.no_centre:
@@ -964,7 +989,8 @@ def main():
         "evals_per_s_fwd": ws * evals / (ms_fwd * 1e-3),
         "fp64_form": fp64,
         "speedup_vs_fp64_form": (fp64["s_per_spectrum_fwdbwd"] / (ms_step * 1e-3)) if fp64 else None,
-        "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clocks,
+        "roofline": roofline, "rt_roofline": rt, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
+        "clocks": clocks,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
         "batched": batched,
         "broad_optical_fwd": broad,

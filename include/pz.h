@@ -469,12 +469,14 @@ pz_status pz_probe_expn(const double *x, int64_t n, double *out, void *stream);
  *   pipe 0: FP32 FMA issued as packed f32x2 fma, counted as 2 FP32 operations
  *           per lane per instruction;
  *   pipe 1: MUFU reciprocal (rcp.approx.ftz.f32 of x + 1, so that the chain cannot
- *           be simplified), 1 operation per lane.
+ *           be simplified), 1 operation per lane;
+ *   pipe 2: FP64 FMA, 1 operation per lane (the denominator of the FP64 transfer
+ *           stage and the scattering solve).
  * 8 CTAs x 256 threads per SM each run 8 independent dependency chains for
  * `iters` rounds; one warm-up launch, then one launch timed with CUDA events on
  * `stream`.  *ops_per_s (host) receives operations per second over the device.
  * Allocates and frees a small device buffer; synchronises `stream`.
- * Errors: PZ_EINVAL for pipe outside {0, 1}, iters outside [1, 2^20] or a NULL
+ * Errors: PZ_EINVAL for pipe outside {0, 1, 2}, iters outside [1, 2^20] or a NULL
  * ops_per_s. */
 pz_status pz_probe_pipe(int32_t pipe, int32_t iters, double *ops_per_s, void *stream);
 

@@ -385,7 +385,7 @@ def pz_sync_status(ctx, stream=None) -> int:
 
 
 def pz_probe_pipe(pipe, iters=4096, stream=None) -> float:
-    """Measured operations per second of pipe 0 (FP32 FMA) or 1 (MUFU reciprocal)."""
+    """Measured operations per second of pipe 0 (FP32 FMA), 1 (MUFU reciprocal) or 2 (FP64 FMA)."""
     r = C.c_double(0.0)
     _check(load().pz_probe_pipe(int(pipe), int(iters), C.byref(r), _stream(stream)))
     return r.value

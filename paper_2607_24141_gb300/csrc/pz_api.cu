@@ -1381,7 +1381,8 @@ pz_status pz_probe_wait(int64_t limit_ns, int32_t *flags, void *stream) {
 }
 
 pz_status pz_probe_pipe(int32_t pipe, int32_t iters, double *ops_per_s, void *stream) {
-    if (pipe < 0 || pipe > 1) return fail(PZ_EINVAL, "pz_probe_pipe: pipe must be 0 (FP32 FMA) or 1 (MUFU)");
+    if (pipe < 0 || pipe > 2)
+        return fail(PZ_EINVAL, "pz_probe_pipe: pipe must be 0 (FP32 FMA), 1 (MUFU) or 2 (FP64 FMA)");
     if (iters < 1 || iters > (1 << 20)) return fail(PZ_EINVAL, "pz_probe_pipe: iters must be in [1, 2^20]");
     if (!ops_per_s) return fail(PZ_EINVAL, "pz_probe_pipe: ops_per_s is NULL");
     cudaStream_t s = (cudaStream_t)stream;

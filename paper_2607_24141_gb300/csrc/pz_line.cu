@@ -1911,7 +1911,8 @@ cudaError_t launch_probe_voigt(const float *a, const float *v, int64_t n, float 
 // no algebraic rewrite removes, for the reciprocal; a contraction toward a fixed point
 // for the FMA) and one result per thread is stored so that the work is live.
 //   kind 0: packed f32x2 FMA, 16 FP32 operations per thread per round;
-//   kind 1: rcp.approx.ftz.f32 (plus one FP32 add), 8 MUFU operations per thread per round.
+//   kind 1: rcp.approx.ftz.f32 (plus one FP32 add), 8 MUFU operations per thread per round;
+//   kind 2: FP64 FMA, 8 FP64 FMA operations per thread per round.
 __global__ void k_probe_pipe(int kind, int iters, float *out) {
     const float seed = 1.0f + 1e-3f * (float)(threadIdx.x & 63);
     float r = 0.0f;
@@ -1930,7 +1931,7 @@ __global__ void k_probe_pipe(int kind, int iters, float *out) {
             f2_unpack(x[k], lo, hi);
             r += lo + hi;
         }
-    } else {
+    } else if (kind == 1) {
         float x[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) x[k] = seed + (float)k;
@@ -1940,6 +1941,16 @@ __global__ void k_probe_pipe(int kind, int iters, float *out) {
         }
 #pragma unroll
         for (int k = 0; k < 8; ++k) r += x[k];
+    } else {
+        double x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = (double)seed + k;
+        for (int it = 0; it < iters; ++it) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) x[k] = fma(x[k], 0.999, 1e-3);
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) r += (float)x[k];
     }
     out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
 }

@@ -64,6 +64,10 @@ def test_pipe_probes_are_plausible():
     # between a quarter of the lane-count rate at 1 GHz and the lane-count rate at 2.5 GHz
     assert 0.25 * n_sm * 128 * 1e9 < fma < n_sm * 256 * 2.5e9
     assert 0.25 * n_sm * 16 * 1e9 < rcp < n_sm * 64 * 2.5e9
+    # FP64: at least one FMA per SM per 4 ns, and far below the FP32 rate on this part
+    dfma = pz.pz_probe_pipe(2, 256)
+    assert n_sm * 0.25e9 < dfma < fma / 4, (dfma, fma)
+    print("pipe probes: FP32 %.3g /s, MUFU %.3g /s, FP64 FMA %.3g /s" % (fma, rcp, dfma))
     with pytest.raises(pz.PzError) as e:
-        pz.pz_probe_pipe(2, 16)
+        pz.pz_probe_pipe(3, 16)
     assert e.value.status == pz.PZ_EINVAL
