@@ -85,6 +85,10 @@ def lib():
         L.pzo_flux_dtau.argtypes = [C.c_int, _dp, _dp, _dp]
         L.pzo_lambda_matrix.argtypes = [C.c_int, _dp, _dp]
         L.pzo_scatter_source.argtypes = [C.c_int, _dp, _dp, _dp, _dp]
+        L.pzo_scatter_adjoint.argtypes = [C.c_int, _dp, _dp, _dp, C.c_double, _dp, _dp]
+        L.pzo_scatter_flux.argtypes = [C.c_int, _dp, _dp, _dp]
+        L.pzo_scatter_flux.restype = C.c_double
+        L.pzo_lambda_dtau.argtypes = [C.c_int, _dp, _dp, _dp]
         L.pzo_planck_nm.argtypes = [C.c_double, C.c_double]
         L.pzo_planck_nm.restype = C.c_double
         _lib = L
@@ -202,6 +206,29 @@ def scatter_source(tau, eps, B):
     tau, eps, B = _d(tau), _d(eps), _d(B)
     out = np.empty_like(tau)
     lib().pzo_scatter_source(tau.size, _ptr(tau, _dp), _ptr(eps, _dp), _ptr(B, _dp), _ptr(out, _dp))
+    return out
+
+
+def scatter_flux(tau, eps, B):
+    """Emergent flux of the solved scattering source on explicit layers."""
+    tau, eps, B = _d(tau), _d(eps), _d(B)
+    return lib().pzo_scatter_flux(tau.size, _ptr(tau, _dp), _ptr(eps, _dp), _ptr(B, _dp))
+
+
+def scatter_adjoint(tau, eps, B, Fbar=1.0):
+    """(dL/dtau, dL/deps) of the scattering flux for dL/dF = Fbar."""
+    tau, eps, B = _d(tau), _d(eps), _d(B)
+    gt, ge = np.empty_like(tau), np.empty_like(tau)
+    lib().pzo_scatter_adjoint(tau.size, _ptr(tau, _dp), _ptr(eps, _dp), _ptr(B, _dp), float(Fbar), _ptr(gt, _dp),
+                              _ptr(ge, _dp))
+    return gt, ge
+
+
+def lambda_dtau(tau, S):
+    """dJ_j/dtau_m at fixed layer values S."""
+    tau, S = _d(tau), _d(S)
+    out = np.empty((tau.size, tau.size))
+    lib().pzo_lambda_dtau(tau.size, _ptr(tau, _dp), _ptr(S, _dp), _ptr(out, _dp))
     return out
 
 

@@ -549,19 +549,158 @@ static void flux_dtau(int nd, const double *tau, const double *S, double *dF) {
 /* dL/dchi(i, d) for every column, given dL/dF_i (total branch; F_c does not depend on
  * line opacity).  G[d * n_lambda + i].  Chain rule written with the explicit Jacobian
  * d tau_j / d chi_d of the trapezoid. */
+/* ---- reverse pass through the scattering source ------------------------------- */
+
+/* dF/dS_k of flux_from (F is linear in the layer values of S): 2 pi times each interval's
+ * coefficients, the top interval's extrapolated S(0) = S_0 - tau_0 (S_1 - S_0)/D1 chained
+ * to S_0 and S_1. */
+static void flux_dS(int nd, const double *tau, double *a) {
+    for (int k = 0; k < nd; ++k) a[k] = 0.0;
+    for (int d = 0; d + 1 < nd; ++d) {
+        double ta = tau[d], tb = tau[d + 1], D = tb - ta;
+        double q = (pzo_expn(4, ta) - pzo_expn(4, tb) - D * pzo_expn(3, tb)) / D;
+        a[d] += (pzo_expn(3, ta) - pzo_expn(3, tb)) - q;
+        a[d + 1] += q;
+    }
+    double t0 = tau[0], D1 = tau[1] - tau[0];
+    double q = (1.0 / 3.0 - pzo_expn(4, t0) - t0 * pzo_expn(3, t0)) / t0;
+    double a_zero = (0.5 - pzo_expn(3, t0)) - q;   /* coefficient of S(0) */
+    a[0] += q + a_zero * (1.0 + t0 / D1);
+    a[1] += -a_zero * t0 / D1;
+    for (int k = 0; k < nd; ++k) a[k] *= 2.0 * O_PI;
+}
+
+/* dJ[j][m] = d J_j / d tau_m at fixed layer values S, J = Lambda S.  Moving layer m with its
+ * value fixed reshapes the two segments that meet there: with s the segment slopes and w the
+ * layer's Lambda weight from each segment (seen from tau_j), -s_{m-1} w - s_m w; the end
+ * terms 1/2 S_m E_1(|tau_m - tau_j|) of the two segments cancel except at the bottom layer,
+ * where the slab ends with it.  The top segment's extrapolation adds its own dependence on
+ * tau_0 and tau_1.  The layer j itself follows from translation invariance: shifting every
+ * layer and the surface together leaves J_j unchanged, so sum_m dJ_j/dtau_m = 1/2 S(0) E_1(tau_j). */
+void pzo_lambda_dtau(int nd, const double *tau, const double *S, double *dJ) {
+    double D1 = tau[1] - tau[0];
+    double s0 = (S[1] - S[0]) / D1;
+    double Szero = S[0] - s0 * tau[0];
+    for (int j = 0; j < nd; ++j) {
+        double *row = dJ + (int64_t)j * nd;
+        double tj = tau[j];
+        for (int m = 0; m < nd; ++m) row[m] = 0.0;
+        /* top segment [0, tau_0]: weights of its values at 0 (lo) and tau_0 (hi) */
+        double wlo, whi;
+        lambda_interval(tj, 0.0, tau[0], &wlo, &whi);
+        row[0] += 0.5 * S[0] * pzo_expn(1, fabs(tau[0] - tj)) - (s0 / D1) * tau[0] * wlo - s0 * (wlo + whi);
+        row[1] += (s0 / D1) * tau[0] * wlo;
+        /* segments [tau_k, tau_k+1] */
+        for (int k = 0; k + 1 < nd; ++k) {
+            double wa, wb;
+            lambda_interval(tj, tau[k], tau[k + 1], &wa, &wb);
+            double sk = (S[k + 1] - S[k]) / (tau[k + 1] - tau[k]);
+            row[k] += -sk * wa;          /* its lower end moves */
+            row[k + 1] += -sk * wb;      /* its upper end moves */
+            /* end terms: +1/2 S E_1 at a moving upper end, -1/2 S E_1 at a moving lower end */
+            double e1b = (k + 1 == j) ? 0.0 : pzo_expn(1, fabs(tau[k + 1] - tj));
+            double e1a = (k == j) ? 0.0 : pzo_expn(1, fabs(tau[k] - tj));
+            row[k + 1] += 0.5 * S[k + 1] * e1b;
+            row[k] -= 0.5 * S[k] * e1a;
+        }
+        /* the layer itself */
+        double off = 0.0;
+        for (int m = 0; m < nd; ++m)
+            if (m != j) off += row[m];
+        row[j] = 0.5 * Szero * pzo_expn(1, tj) - off;
+    }
+}
+
+/* Reverse pass of one column's scattering flux: with S solving (I - diag(1 - eps) Lambda) S
+ * = eps B and F = flux_from(tau, S), returns dL/dtau (gtau) and dL/deps (geps) for
+ * dL/dF = Fbar.  The adjoint mu solves M^T mu = Fbar dF/dS; then
+ *   dL/deps_j = mu_j (B_j - J_j),
+ *   dL/dtau_m = Fbar dF/dtau_m (at fixed S) + sum_j mu_j (1 - eps_j) dJ_j/dtau_m. */
+void pzo_scatter_adjoint(int nd, const double *tau, const double *eps, const double *B, double Fbar, double *gtau,
+                         double *geps) {
+    size_t n2 = (size_t)nd * nd;
+    double *Lam = (double *)malloc(sizeof(double) * (n2 * 3 + (size_t)nd * (nd + 1) + 6 * nd));
+    double *dJ = Lam + n2, *A = dJ + n2, *Mt = A + (size_t)nd * (nd + 1);
+    double *S = Mt + n2, *J = S + nd, *a = J + nd, *mu = a + nd, *dF = mu + nd;
+    pzo_scatter_source(nd, tau, eps, B, S);
+    pzo_lambda_matrix(nd, tau, Lam);
+    for (int j = 0; j < nd; ++j) {
+        double v = 0.0;
+        for (int k = 0; k < nd; ++k) v += Lam[(int64_t)j * nd + k] * S[k];
+        J[j] = v;
+    }
+    flux_dS(nd, tau, a);
+    flux_dtau(nd, tau, S, dF);
+    /* M^T mu = Fbar a, M = I - diag(1 - eps) Lambda: Gaussian elimination with partial pivoting */
+    int W = nd + 1;
+    for (int r = 0; r < nd; ++r) {
+        for (int c = 0; c < nd; ++c)
+            A[(int64_t)r * W + c] = (r == c ? 1.0 : 0.0) - (1.0 - eps[c]) * Lam[(int64_t)c * nd + r];
+        A[(int64_t)r * W + nd] = Fbar * a[r];
+    }
+    for (int p = 0; p < nd; ++p) {
+        int piv = p;
+        for (int r = p + 1; r < nd; ++r)
+            if (fabs(A[(int64_t)r * W + p]) > fabs(A[(int64_t)piv * W + p])) piv = r;
+        if (piv != p)
+            for (int k = 0; k < W; ++k) {
+                double t = A[(int64_t)p * W + k];
+                A[(int64_t)p * W + k] = A[(int64_t)piv * W + k];
+                A[(int64_t)piv * W + k] = t;
+            }
+        for (int r = p + 1; r < nd; ++r) {
+            double f = A[(int64_t)r * W + p] / A[(int64_t)p * W + p];
+            for (int k = p; k < W; ++k) A[(int64_t)r * W + k] -= f * A[(int64_t)p * W + k];
+        }
+    }
+    for (int p = nd - 1; p >= 0; --p) {
+        double v = A[(int64_t)p * W + nd];
+        for (int k = p + 1; k < nd; ++k) v -= A[(int64_t)p * W + k] * mu[k];
+        mu[p] = v / A[(int64_t)p * W + p];
+    }
+    pzo_lambda_dtau(nd, tau, S, dJ);
+    for (int j = 0; j < nd; ++j) geps[j] = mu[j] * (B[j] - J[j]);
+    for (int m = 0; m < nd; ++m) {
+        double g = Fbar * dF[m];
+        for (int j = 0; j < nd; ++j) g += mu[j] * (1.0 - eps[j]) * dJ[(int64_t)j * nd + m];
+        gtau[m] = g;
+    }
+    (void)Mt;
+    free(Lam);
+}
+
+/* emergent flux of the scattering source on explicit tau, eps, B (for the adjoint pins) */
+double pzo_scatter_flux(int nd, const double *tau, const double *eps, const double *B) {
+    double *S = (double *)malloc(sizeof(double) * nd);
+    pzo_scatter_source(nd, tau, eps, B, S);
+    double F = flux_from(nd, tau, S);
+    free(S);
+    return F;
+}
+
 void pzo_rt_adjoint(const pzo_problem *P, const double *kline_full, const double *dLdF, double *G) {
     int nd = P->n_depth;
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < P->n_lambda; ++i) {
-        double *chi = (double *)malloc(sizeof(double) * nd * 4);
-        double *tau = chi + nd, *S = chi + 2 * nd, *dF = chi + 3 * nd;
+        double *chi = (double *)malloc(sizeof(double) * nd * 6);
+        double *tau = chi + nd, *S = chi + 2 * nd, *dF = chi + 3 * nd, *eps = chi + 4 * nd, *geps = chi + 5 * nd;
         double lam = grid_lambda_cm(P, i);
         for (int d = 0; d < nd; ++d) {
-            chi[d] = P->kappa_c[(int64_t)d * P->n_lambda + i] + kline_full[(int64_t)d * P->n_lambda + i];
+            int64_t o = (int64_t)d * P->n_lambda + i;
+            double sig = P->sigma_c ? P->sigma_c[o] : 0.0;
+            chi[d] = P->kappa_c[o] + kline_full[o] + sig;
+            eps[d] = (P->kappa_c[o] + kline_full[o]) / chi[d];
             S[d] = planck_nm(lam, P->T[d]);
         }
         optical_depth(nd, P->m, chi, tau);
-        flux_dtau(nd, tau, S, dF);
+        if (P->sigma_c) {
+            /* dF/dtau here is dL/dtau for dL/dF = 1 (S follows tau and eps); the eps part is
+             * added per layer below: eps = 1 - sigma/chi, so d eps / d kappa_line = sigma/chi^2 */
+            pzo_scatter_adjoint(nd, tau, eps, S, 1.0, dF, geps);
+        } else {
+            flux_dtau(nd, tau, S, dF);
+            for (int d = 0; d < nd; ++d) geps[d] = 0.0;
+        }
         for (int d = 0; d < nd; ++d) {
             double g = 0.0;
             for (int j = 0; j < nd; ++j) {
@@ -574,6 +713,10 @@ void pzo_rt_adjoint(const pzo_problem *P, const double *kline_full, const double
                     if (d == k + 1) J += hm;
                 }
                 g += dF[j] * J;
+            }
+            if (P->sigma_c) {
+                double sig = P->sigma_c[(int64_t)d * P->n_lambda + i];
+                g += geps[d] * sig / (chi[d] * chi[d]);
             }
             G[(int64_t)d * P->n_lambda + i] = dLdF[i] * g;
         }
