@@ -268,8 +268,11 @@ pz_status pz_calib_step(pz_ctx *ctx, const float *y, const float *w, int64_t n, 
  * (one CTA per wavelength and star).  The continuum branch uses
  * eps_c = kappa_c / (kappa_c + sigma_c).  sigma_c: host FP64 [S][n_depth][n_lambda],
  * cm^2/g, finite and >= 0, copied; NULL turns scattering off (S = B).  Synchronous.
- * The forward must run again.  The reverse pass does not cover scattering: while it is
- * on, pz_backward, pz_backward4, pz_calib_step and pz_group_eval return PZ_ESTATE.
+ * The forward must run again.  The reverse pass (pz_backward, pz_backward4,
+ * pz_calib_step, pz_group_eval) follows the scattering source too: the adjoint of the
+ * linear system, M^T mu = dL/dF dF/dS, gives dL/deps = mu (B - J) and the dependence of
+ * J = Lambda S on the optical depths, and kappa_line reaches eps through
+ * eps = 1 - sigma_c/chi.
  * Errors: PZ_EINVAL (negative or non-finite sigma_c, fewer than two layers), PZ_ENOMEM,
  * PZ_ECUDA. */
 pz_status pz_set_scattering(pz_ctx *ctx, const double *sigma_c, void *stream);

@@ -1009,7 +1009,6 @@ pz_status pz_backward(pz_ctx *c, const float *dLdf, float *g_gf, float *g_g6, fl
     if (!c) return fail(PZ_EINVAL, "pz_backward: ctx is NULL");
     if (!c->have_inst) return fail(PZ_ESTATE, "pz_backward: call pz_instrument first");
     if (!dLdf) return fail(PZ_EINVAL, "pz_backward: dL_df is NULL");
-    if (c->d_sigma) return fail(PZ_ESTATE, "pz_backward: no reverse pass through continuum scattering");
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
     PZ_TRY(ensure_backward_buffers(c));
@@ -1021,7 +1020,6 @@ pz_status pz_backward4(pz_ctx *c, const float *dLdf, float *g_gf, float *g_rad, 
     if (!c) return fail(PZ_EINVAL, "pz_backward4: ctx is NULL");
     if (!c->have_inst) return fail(PZ_ESTATE, "pz_backward4: call pz_instrument first");
     if (!dLdf) return fail(PZ_EINVAL, "pz_backward4: dL_df is NULL");
-    if (c->d_sigma) return fail(PZ_ESTATE, "pz_backward4: no reverse pass through continuum scattering");
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
     PZ_TRY(ensure_backward_buffers(c));
@@ -1048,7 +1046,6 @@ pz_status pz_calib_step(pz_ctx *c, const float *y, const float *w, int64_t n, fl
     if (!c) return fail(PZ_EINVAL, "pz_calib_step: ctx is NULL");
     if (c->n_out <= 0) return fail(PZ_ESTATE, "pz_calib_step: call pz_instrument once first");
     if (!y) return fail(PZ_EINVAL, "pz_calib_step: y is NULL");
-    if (c->d_sigma) return fail(PZ_ESTATE, "pz_calib_step: no reverse pass through continuum scattering");
     if (n != c->n_out) return fail(PZ_EINVAL, "pz_calib_step: n differs from the instrument output size");
     if (!std::isfinite(lr_gf) || !std::isfinite(lr_g6) || !std::isfinite(lr_ab))
         return fail(PZ_EINVAL, "pz_calib_step: learning rates must be finite");
@@ -1188,7 +1185,6 @@ pz_status pz_group_eval(pz_ctx *c, const float *y, const float *w, int64_t n, co
     if (c->n_groups <= 0) return fail(PZ_ESTATE, "pz_group_eval: call pz_set_line_groups first");
     if (c->n_out <= 0) return fail(PZ_ESTATE, "pz_group_eval: call pz_instrument once first");
     if (!y || !x) return fail(PZ_EINVAL, "pz_group_eval: y and x are required");
-    if (c->d_sigma) return fail(PZ_ESTATE, "pz_group_eval: no reverse pass through continuum scattering");
     if (n != c->n_out) return fail(PZ_EINVAL, "pz_group_eval: n differs from the instrument output size");
     cudaStream_t s = (cudaStream_t)stream;
     PZ_TRY(ensure_backward_buffers(c));

@@ -296,6 +296,12 @@ cudaError_t launch_flux(pz_ctx *c, cudaStream_t s) {
 // The matrix is diagonally dominant (row sums of Lambda <= 1, 1 - eps < 1), so Gaussian
 // elimination runs without pivoting.
 // ---------------------------------------------------------------------------
+// d/dtau_a and d/dtau_b of one interval integral at fixed endpoint values (defined with the
+// LTE transfer adjoint below)
+__device__ __forceinline__ void interval_grad(double ta, double tb, double Sa, double Sb, double e2a, double e3a,
+                                              double e4a, double e2b, double e3b, double e4b, double &da,
+                                              double &db);
+
 struct ScatArgs {
     int64_t nlam, ld;
     int nd;
@@ -303,42 +309,67 @@ struct ScatArgs {
     const double *m, *T, *kc, *sig;
     const void *kline;
     double *F, *Fc;
+    const double *dFbar;   // adjoint: dL/dF [S][nlam]
+    void *Gt;              // adjoint: G stim [S][nd][ld]
 };
 
 constexpr int kScatThreads = 256;
 constexpr int kScatTableMaxDepth = 96;    // the E2/E3 pair table fits shared memory up to here
 constexpr int kScatMaxRefine = 12;        // iterative-refinement rounds at most
+constexpr int kScatVec = 16;              // FP64 vectors of nd
 
-// shared memory: the FP64 system [nd][nd + 1], ten FP64 vectors, the FP32 LU factors
-// [nd][nd], and with the table the packed upper triangle of (E2, E3) pairs plus (E2, E3)
-// at tau_j itself
+// shared memory: Lambda [nd][nd + 1] (FP64; the adjoint reuses it for dJ/dtau), kScatVec
+// FP64 vectors, the FP32 LU factors [nd][nd], and with the table the packed upper triangle
+// of (E2, E3) pairs plus (E2, E3) at tau_j itself
 static size_t scatter_smem(int nd, bool table) {
-    size_t n = (size_t)nd * (nd + 1) + 10 * (size_t)nd;
+    size_t n = (size_t)nd * (nd + 1) + kScatVec * (size_t)nd;
     if (table) n += (size_t)nd * (nd + 1) + 2 * (size_t)nd;
     return sizeof(double) * n + sizeof(float) * (size_t)nd * nd;
 }
 
-// One warp solves L U x = r with the FP32 factors (unit lower L and U in place in LU,
-// row stride nd); lane l holds rows l, l + 32, l + 64, l + 96.  r and the result in y.
+// One warp solves L U x = r (TRANS false) or (L U)^T x = r (TRANS true) with the FP32
+// factors (unit lower L and U in place in LU, row stride nd); lane l holds rows l, l + 32,
+// l + 64, l + 96.  r and the result in y.
 __device__ __forceinline__ float pick4(const float (&y)[4], int q) {
     return q == 0 ? y[0] : (q == 1 ? y[1] : (q == 2 ? y[2] : y[3]));
 }
+template <bool TRANS>
 __device__ __forceinline__ void lu_solve_warp(const float *LU, int nd, int lane, float (&y)[4]) {
-    for (int p = 0; p < nd; ++p) {
-        const float yp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31);
+    if (!TRANS) {
+        for (int p = 0; p < nd; ++p) {       // L z = r
+            const float yp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int row = lane + 32 * q;
-            if (row > p && row < nd) y[q] = fmaf(-LU[row * nd + p], yp, y[q]);
+            for (int q = 0; q < 4; ++q) {
+                const int row = lane + 32 * q;
+                if (row > p && row < nd) y[q] = fmaf(-LU[row * nd + p], yp, y[q]);
+            }
         }
-    }
-    for (int p = nd - 1; p >= 0; --p) {
-        const float xp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31) / LU[p * nd + p];
+        for (int p = nd - 1; p >= 0; --p) {  // U x = z
+            const float xp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31) / LU[p * nd + p];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int row = lane + 32 * q;
-            if (row < p) y[q] = fmaf(-LU[row * nd + p], xp, y[q]);
-            if (row == p) y[q] = xp;
+            for (int q = 0; q < 4; ++q) {
+                const int row = lane + 32 * q;
+                if (row < p) y[q] = fmaf(-LU[row * nd + p], xp, y[q]);
+                if (row == p) y[q] = xp;
+            }
+        }
+    } else {
+        for (int p = 0; p < nd; ++p) {       // U^T z = r
+            const float zp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31) / LU[p * nd + p];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = lane + 32 * q;
+                if (row > p && row < nd) y[q] = fmaf(-LU[p * nd + row], zp, y[q]);
+                if (row == p) y[q] = zp;
+            }
+        }
+        for (int p = nd - 1; p >= 0; --p) {  // L^T x = z (unit diagonal)
+            const float xp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = lane + 32 * q;
+                if (row < p) y[q] = fmaf(-LU[p * nd + row], xp, y[q]);
+            }
         }
     }
 }
@@ -354,6 +385,24 @@ __device__ __forceinline__ void e23(double x, double &e2, double &e3) {
     expn234(x, e2, e3, e4);
 }
 
+// E_1(x), x > 0: the power series -gamma - ln x - sum_k (-x)^k / (k k!) below 1, else
+// (e^-x - E_2(x)) / x from the recurrence E_2 = e^-x - x E_1
+__device__ __forceinline__ double e1(double x) {
+    if (x < 1.0) {
+        double term = 1.0, sum = 0.0;
+#pragma unroll 1
+        for (int k = 1; k <= 20; ++k) {
+            term *= -x / k;
+            sum += term / k;
+        }
+        return -kEuler - log(x) - sum;
+    }
+    if (x > 700.0) return 0.0;
+    double e2, e3, e4;
+    expn234(x, e2, e3, e4);
+    return (exp(-x) - e2) / x;
+}
+
 // weights of the near and far ends of a segment (inverse length invD) seen from depth
 // tau_j, from E2, E3 at the distances of its near (n) and far (f) ends
 __device__ __forceinline__ void seg_weights(double D, double invD, double e2n, double e3n, double e2f, double e3f,
@@ -364,219 +413,405 @@ __device__ __forceinline__ void seg_weights(double D, double invD, double e2n, d
     wf = 0.25 * (P + Q);
 }
 
+// Shared-memory layout of one (wavelength, star) column.
+struct ScatCol {
+    int nd, W;
+    double *Lam, *tau, *chi, *eps, *B, *S, *e2, *e3, *e4, *invD, *res, *a, *mu, *J, *dF, *ge;
+    double *ET, *Etop;
+    float *LU;
+};
+
+template <bool TABLE>
+__device__ __forceinline__ ScatCol scat_carve(double *sm, int nd) {
+    ScatCol c;
+    c.nd = nd;
+    c.W = nd + 1;
+    c.Lam = sm;
+    double *v = sm + (size_t)nd * c.W;
+    double **vec[kScatVec] = {&c.tau, &c.chi, &c.eps, &c.B, &c.S, &c.e2, &c.e3, &c.e4,
+                              &c.invD, &c.res, &c.a, &c.mu, &c.J, &c.dF, &c.ge, nullptr};
+    for (int k = 0; k < kScatVec; ++k)
+        if (vec[k]) *vec[k] = v + (size_t)k * nd;
+    c.ET = v + (size_t)kScatVec * nd;
+    c.Etop = c.ET + (TABLE ? (size_t)nd * c.W : 0);
+    c.LU = reinterpret_cast<float *>(c.Etop + (TABLE ? 2 * (size_t)nd : 0));
+    return c;
+}
+
+__device__ __forceinline__ size_t pair_idx(int nd, int a, int b) {   // a <= b
+    return (size_t)a * nd - (size_t)a * (a - 1) / 2 + (b - a);
+}
+
+// chi, eps and tau of one branch (0: total, 1: continuum), the segment reciprocals and,
+// with the table, E2/E3 at every layer pair and at tau_j.  Ends with a barrier.
+template <typename KT, bool TABLE>
+__device__ void scat_columns(const ScatArgs &g, const ScatCol &c, int64_t base, const double *m, int branch) {
+    const int nd = c.nd, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const KT *kl = reinterpret_cast<const KT *>(g.kline);
+    for (int d = tid; d < nd; d += blockDim.x) {
+        const int64_t o = base + (int64_t)d * g.ld;
+        const double ka = g.kc[o] + (branch == 0 ? (double)kl[o] : 0.0);   // absorption
+        c.chi[d] = ka + g.sig[o];
+        c.eps[d] = ka / c.chi[d];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t = c.chi[0] * m[0];
+        c.tau[0] = t;
+        for (int d = 1; d < nd; ++d) {
+            t += 0.5 * (c.chi[d - 1] + c.chi[d]) * (m[d] - m[d - 1]);
+            c.tau[d] = t;
+        }
+    }
+    __syncthreads();
+    for (int k = tid; k + 1 < nd; k += blockDim.x) c.invD[k] = 1.0 / (c.tau[k + 1] - c.tau[k]);
+    if (TABLE) {
+        // warps over j, lanes over k >= j
+        for (int j = warp; j < nd; j += nwarp)
+            for (int k = j + lane; k < nd; k += 32) {
+                const size_t idx = pair_idx(nd, j, k);
+                e23(c.tau[k] - c.tau[j], c.ET[2 * idx], c.ET[2 * idx + 1]);
+            }
+        for (int j = tid; j < nd; j += blockDim.x) e23(c.tau[j], c.Etop[2 * j], c.Etop[2 * j + 1]);
+    }
+    __syncthreads();
+}
+
+// E2, E3 at |tau_k - tau_j| (table or direct)
+template <bool TABLE>
+__device__ __forceinline__ void scat_E(const ScatCol &c, int j, int k, double &e2, double &e3) {
+    if (TABLE) {
+        const size_t idx = pair_idx(c.nd, min(j, k), max(j, k));
+        e2 = c.ET[2 * idx];
+        e3 = c.ET[2 * idx + 1];
+    } else {
+        e23(fabs(c.tau[k] - c.tau[j]), e2, e3);
+    }
+}
+
+// Segment weights of row j: for every segment k (between layers k and k + 1) the weights
+// (wa, wb) of its lower and upper layer values, and of the top segment [0, tau_0] the
+// weights (wlo, whi) of S(0) and S(tau_0).  f(k, wa, wb) per segment, then top(wlo, whi).
+template <bool TABLE, class Seg, class Top>
+__device__ __forceinline__ void scat_row_weights(const ScatCol &c, int j, Seg &&seg, Top &&top) {
+    const int nd = c.nd;
+    double e2p, e3p;
+    scat_E<TABLE>(c, j, 0, e2p, e3p);
+    {
+        double e2z, e3z, wn, wf;
+        if (TABLE) {
+            e2z = c.Etop[2 * j];
+            e3z = c.Etop[2 * j + 1];
+        } else {
+            e23(c.tau[j], e2z, e3z);
+        }
+        seg_weights(c.tau[0], 1.0 / c.tau[0], e2p, e3p, e2z, e3z, wn, wf);   // near: tau_0, far: 0
+        top(wf, wn);
+    }
+    for (int k = 0; k + 1 < nd; ++k) {
+        double e2k, e3k, wn, wf;
+        scat_E<TABLE>(c, j, k + 1, e2k, e3k);
+        const double D = c.tau[k + 1] - c.tau[k];
+        if (k >= j) {          // below tau_j: near end k, far end k + 1
+            seg_weights(D, c.invD[k], e2p, e3p, e2k, e3k, wn, wf);
+            seg(k, wn, wf);
+        } else {               // above: near end k + 1, far end k
+            seg_weights(D, c.invD[k], e2k, e3k, e2p, e3p, wn, wf);
+            seg(k, wf, wn);
+        }
+        e2p = e2k;
+        e3p = e3k;
+    }
+}
+
+// rows of Lambda (J = Lambda S) and the right-hand side eps B in column nd.  Ends with a barrier.
+template <bool TABLE>
+__device__ void scat_lambda(const ScatCol &c) {
+    const int nd = c.nd, W = c.W;
+    const double D1 = c.tau[1] - c.tau[0];
+    for (int j = threadIdx.x; j < nd; j += blockDim.x) {
+        double *row = c.Lam + (size_t)j * W;
+        for (int k = 0; k < nd; ++k) row[k] = 0.0;
+        scat_row_weights<TABLE>(
+            c, j,
+            [&](int k, double wa, double wb) {
+                row[k] += wa;
+                row[k + 1] += wb;
+            },
+            [&](double wlo, double whi) {   // S(0) = S0 (1 + tau_0/D1) - S1 tau_0/D1
+                row[0] += wlo * (1.0 + c.tau[0] / D1) + whi;
+                row[1] -= wlo * (c.tau[0] / D1);
+            });
+        row[nd] = c.eps[j] * c.B[j];
+    }
+    __syncthreads();
+}
+
+// FP32 LU factors of M = I - diag(1 - eps) Lambda (no pivoting: diagonally dominant).
+__device__ void scat_lu(const ScatCol &c) {
+    const int nd = c.nd, W = c.W, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    float *LU = c.LU;
+    for (int r = warp; r < nd; r += nwarp) {
+        const double w = 1.0 - c.eps[r];
+        for (int k = lane; k < nd; k += 32) LU[r * nd + k] = (float)((r == k ? 1.0 : 0.0) - w * c.Lam[(size_t)r * W + k]);
+    }
+    __syncthreads();
+    for (int p = 0; p + 1 < nd; ++p) {
+        // warps over the rows below the pivot, lanes over the columns p+1 .. nd-1
+        const float inv = 1.0f / LU[p * nd + p];
+        for (int r = p + 1 + warp; r < nd; r += nwarp) {
+            const float f = LU[r * nd + p] * inv;
+            for (int k = p + 1 + lane; k < nd; k += 32) LU[r * nd + k] = fmaf(-f, LU[p * nd + k], LU[r * nd + k]);
+            __syncwarp();
+            if (lane == 0) LU[r * nd + p] = f;
+        }
+        __syncthreads();
+    }
+}
+
+// Iterative refinement with FP64 residuals of M x = rhs (TRANS false) or M^T x = rhs:
+// x += (LU)^-1 (rhs - M x) until the correction is below 1e-14 of x.  rhs and x of nd.
+template <bool TRANS>
+__device__ void scat_refine(const ScatCol &c, const double *rhs, double *x, int *s_done) {
+    const int nd = c.nd, W = c.W, tid = threadIdx.x;
+    for (int d = tid; d < nd; d += blockDim.x) {
+        x[d] = 0.0;
+        c.res[d] = rhs[d];
+    }
+    __syncthreads();
+    for (int it = 0; it < kScatMaxRefine; ++it) {
+        if (tid < 32) {
+            float y[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = tid + 32 * q;
+                y[q] = row < nd ? (float)c.res[row] : 0.0f;
+            }
+            lu_solve_warp<TRANS>(c.LU, nd, tid, y);
+            double dmax = 0.0, smax = 0.0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int row = tid + 32 * q;
+                if (row < nd) {
+                    const double v = x[row] + (double)y[q];
+                    x[row] = v;
+                    dmax = fmax(dmax, fabs((double)y[q]));
+                    smax = fmax(smax, fabs(v));
+                }
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+                smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
+            }
+            if (tid == 0) *s_done = dmax <= 1e-14 * smax;
+        }
+        __syncthreads();
+        if (*s_done) break;
+        for (int j = tid; j < nd; j += blockDim.x) {
+            double r = rhs[j] - x[j];
+            if (!TRANS) {
+                const double *row = c.Lam + (size_t)j * W;
+                double lx = 0.0;
+                for (int k = 0; k < nd; ++k) lx = fma(row[k], x[k], lx);
+                r = fma(1.0 - c.eps[j], lx, r);
+            } else {
+                double lx = 0.0;   // (Lambda^T diag(1 - eps) x)_j
+                for (int k = 0; k < nd; ++k) lx = fma(c.Lam[(size_t)k * W + j], (1.0 - c.eps[k]) * x[k], lx);
+                r += lx;
+            }
+            c.res[j] = r;
+        }
+        __syncthreads();
+    }
+}
+
 template <typename KT, bool TABLE>
 __global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
     extern __shared__ double sm[];
-    const int nd = g.nd, W = nd + 1;
-    double *M = sm;                        // [nd][nd + 1], right-hand side in column nd
-    double *tau = M + (size_t)nd * W;
-    double *chi = tau + nd;
-    double *eps = chi + nd;
-    double *B = eps + nd;
-    double *S = B + nd;
-    double *fac = S + nd;
-    double *e3 = fac + nd;
-    double *e4 = e3 + nd;
-    double *invD = e4 + nd;                // 1 / (tau_{k+1} - tau_k)
-    double *res = invD + nd;               // residual of the refinement
-    double *ET = res + nd;                 // TABLE: (E2, E3) of pair (j <= k) at 2 idx(j, k)
-    double *Etop = ET + (TABLE ? (size_t)nd * W : 0);   // TABLE: (E2, E3) at tau_j
-    float *LU = reinterpret_cast<float *>(Etop + (TABLE ? 2 * (size_t)nd : 0));   // [nd][nd] FP32
     __shared__ int s_done;
+    const int nd = g.nd;
+    const ScatCol c = scat_carve<TABLE>(sm, nd);
     const int64_t i = blockIdx.x;
     const int st = blockIdx.y;
     const int tid = threadIdx.x;
     const double *m = g.m + (int64_t)st * nd;
     const double *T = g.T + (int64_t)st * nd;
     const int64_t base = (int64_t)st * nd * g.ld + i;
-    const KT *kl = reinterpret_cast<const KT *>(g.kline);
     const double lam = g.lam0cm * exp((double)i * g.lnr);
-    for (int d = tid; d < nd; d += blockDim.x) B[d] = planck_nm(lam, T[d]);
+    for (int d = tid; d < nd; d += blockDim.x) c.B[d] = planck_nm(lam, T[d]);
     for (int branch = 0; branch < 2; ++branch) {
-        for (int d = tid; d < nd; d += blockDim.x) {
-            const int64_t o = base + (int64_t)d * g.ld;
-            const double ka = g.kc[o] + (branch == 0 ? (double)kl[o] : 0.0);   // absorption
-            chi[d] = ka + g.sig[o];
-            eps[d] = ka / chi[d];
-        }
+        scat_columns<KT, TABLE>(g, c, base, m, branch);
+        scat_lambda<TABLE>(c);
+        scat_lu(c);
+        for (int d = tid; d < nd; d += blockDim.x) c.a[d] = c.Lam[(size_t)d * c.W + nd];
         __syncthreads();
-        if (tid == 0) {
-            double t = chi[0] * m[0];
-            tau[0] = t;
-            for (int d = 1; d < nd; ++d) {
-                t += 0.5 * (chi[d - 1] + chi[d]) * (m[d] - m[d - 1]);
-                tau[d] = t;
-            }
-        }
-        __syncthreads();
-        for (int k = tid; k + 1 < nd; k += blockDim.x) invD[k] = 1.0 / (tau[k + 1] - tau[k]);
-        const int lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-        if (TABLE) {
-            // E2, E3 at |tau_j - tau_k| for every pair once (the distance is symmetric):
-            // warps over j, lanes over k >= j
-            for (int j = warp; j < nd; j += nwarp) {
-                const size_t r0 = (size_t)j * nd - (size_t)j * (j - 1) / 2 - j;
-                for (int k = j + lane; k < nd; k += 32) {
-                    const size_t idx = r0 + k;
-                    e23(tau[k] - tau[j], ET[2 * idx], ET[2 * idx + 1]);
-                }
-            }
-            for (int j = tid; j < nd; j += blockDim.x) e23(tau[j], Etop[2 * j], Etop[2 * j + 1]);
-        }
-        __syncthreads();
-        // rows of I - diag(1 - eps) Lambda and the right-hand side eps B
-        const double D1 = tau[1] - tau[0];
-        for (int j = tid; j < nd; j += blockDim.x) {
-            double *row = M + (size_t)j * W;
-            for (int k = 0; k < nd; ++k) row[k] = 0.0;
-            const double tj = tau[j];
-            auto E = [&](int k, double &e2, double &e3) {
-                if (TABLE) {
-                    const int a = min(j, k), b = max(j, k);
-                    const size_t idx = (size_t)a * nd - (size_t)a * (a - 1) / 2 + (b - a);
-                    e2 = ET[2 * idx];
-                    e3 = ET[2 * idx + 1];
-                } else {
-                    e23(fabs(tau[k] - tj), e2, e3);
-                }
-            };
-            // E2, E3 at each layer's distance from tau_j, shared by the two segments that meet there
-            double e2p, e3p;
-            E(0, e2p, e3p);
-            {
-                // top segment [0, tau_0] (above every layer): S(0) = S0 - tau_0 (S1 - S0)/D1
-                double e2z, e3z, wn, wf;
-                if (TABLE) {
-                    e2z = Etop[2 * j];
-                    e3z = Etop[2 * j + 1];
-                } else {
-                    e23(tj, e2z, e3z);
-                }
-                seg_weights(tau[0], 1.0 / tau[0], e2p, e3p, e2z, e3z, wn, wf);   // near: tau_0, far: 0
-                row[0] += wf * (1.0 + tau[0] / D1) + wn;
-                row[1] -= wf * (tau[0] / D1);
-            }
-            for (int k = 0; k + 1 < nd; ++k) {
-                double e2k, e3k, wn, wf;
-                E(k + 1, e2k, e3k);
-                const double D = tau[k + 1] - tau[k];
-                if (k >= j) {          // below tau_j: near end k, far end k + 1
-                    seg_weights(D, invD[k], e2p, e3p, e2k, e3k, wn, wf);
-                    row[k] += wn;
-                    row[k + 1] += wf;
-                } else {               // above: near end k + 1, far end k
-                    seg_weights(D, invD[k], e2k, e3k, e2p, e3p, wn, wf);
-                    row[k + 1] += wn;
-                    row[k] += wf;
-                }
-                e2p = e2k;
-                e3p = e3k;
-            }
-            const double w = 1.0 - eps[j];
-            for (int k = 0; k < nd; ++k) row[k] = (k == j ? 1.0 : 0.0) - w * row[k];
-            row[nd] = eps[j] * B[j];
-        }
-        __syncthreads();
-        // LU factors in FP32 (no pivoting: the system is diagonally dominant), then iterative
-        // refinement with FP64 residuals: S += (LU)^-1 (eps B - M S) until the correction is
-        // below 1e-14 of S
-        for (int r = warp; r < nd; r += nwarp)
-            for (int k = lane; k < nd; k += 32) LU[r * nd + k] = (float)M[(size_t)r * W + k];
-        __syncthreads();
-        for (int p = 0; p + 1 < nd; ++p) {
-            // rows below the pivot: warps over rows, lanes over columns p+1 .. nd-1; each
-            // warp scales its row's multiplier itself (lane-uniform value)
-            const float inv = 1.0f / LU[p * nd + p];
-            for (int r = p + 1 + warp; r < nd; r += nwarp) {
-                const float f = LU[r * nd + p] * inv;
-                for (int k = p + 1 + lane; k < nd; k += 32) LU[r * nd + k] = fmaf(-f, LU[p * nd + k], LU[r * nd + k]);
-                __syncwarp();
-                if (lane == 0) LU[r * nd + p] = f;
-            }
-            __syncthreads();
-        }
-        for (int d = tid; d < nd; d += blockDim.x) {
-            S[d] = 0.0;
-            res[d] = M[(size_t)d * W + nd];
-        }
-        __syncthreads();
-        for (int it = 0; it < kScatMaxRefine; ++it) {
-            if (tid < 32) {
-                float y[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int row = tid + 32 * q;
-                    y[q] = row < nd ? (float)res[row] : 0.0f;
-                }
-                lu_solve_warp(LU, nd, tid, y);
-                double dmax = 0.0, smax = 0.0;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int row = tid + 32 * q;
-                    if (row < nd) {
-                        const double v = S[row] + (double)y[q];
-                        S[row] = v;
-                        dmax = fmax(dmax, fabs((double)y[q]));
-                        smax = fmax(smax, fabs(v));
-                    }
-                }
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-                    smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
-                }
-                if (tid == 0) s_done = dmax <= 1e-14 * smax;
-            }
-            __syncthreads();
-            if (s_done) break;
-            for (int j = tid; j < nd; j += blockDim.x) {
-                const double *row = M + (size_t)j * W;
-                double r = row[nd];
-                for (int k = 0; k < nd; ++k) r = fma(-row[k], S[k], r);
-                res[j] = r;
-            }
-            __syncthreads();
-        }
+        scat_refine<false>(c, c.a, c.S, &s_done);
         // emergent flux of the solved source, the closed form of the LTE kernel
-        for (int d = tid; d < nd; d += blockDim.x) {
-            double e2;
-            expn234(tau[d], e2, e3[d], e4[d]);
-        }
+        for (int d = tid; d < nd; d += blockDim.x) expn234(c.tau[d], c.e2[d], c.e3[d], c.e4[d]);
         __syncthreads();
         if (tid == 0) {
-            const double s0 = (S[1] - S[0]) / D1;
-            double F = interval(0.0, tau[0], S[0] - s0 * tau[0], S[0], 0.5, 1.0 / 3.0, e3[0], e4[0]);
-            for (int d = 0; d + 1 < nd; ++d) F += interval(tau[d], tau[d + 1], S[d], S[d + 1], e3[d], e4[d], e3[d + 1], e4[d + 1]);
+            const double D1 = c.tau[1] - c.tau[0];
+            const double s0 = (c.S[1] - c.S[0]) / D1;
+            double F = interval(0.0, c.tau[0], c.S[0] - s0 * c.tau[0], c.S[0], 0.5, 1.0 / 3.0, c.e3[0], c.e4[0]);
+            for (int d = 0; d + 1 < nd; ++d)
+                F += interval(c.tau[d], c.tau[d + 1], c.S[d], c.S[d + 1], c.e3[d], c.e4[d], c.e3[d + 1], c.e4[d + 1]);
             (branch == 0 ? g.F : g.Fc)[(int64_t)st * g.nlam + i] = 2.0 * kPI * F;
         }
         __syncthreads();
     }
 }
 
-template <bool TABLE>
-static cudaError_t launch_scatter_t(pz_ctx *c, const ScatArgs &g, cudaStream_t s) {
-    const size_t smem = scatter_smem(c->nd, TABLE);
-    static size_t attr_set[64] = {0};   // dynamic shared memory granted so far, per device
-    if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
-    if (smem > attr_set[c->device]) {
-        cudaError_t e = cudaFuncSetAttribute(k_flux_scatter<float, TABLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_flux_scatter<double, TABLE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem);
-        if (e != cudaSuccess) return e;
-        attr_set[c->device] = smem;
+// Reverse pass of the total branch through the scattering source (Eq. 6), one CTA per
+// (wavelength, star).  With M S = eps B solved again, dF/dS = a and the explicit dF/dtau
+// at fixed S, the adjoint mu solves M^T mu = dL/dF a; then
+//   dL/deps_j = mu_j (B_j - J_j),  J = Lambda S,
+//   dL/dtau_m = dL/dF dF/dtau_m + sum_j mu_j (1 - eps_j) dJ_j/dtau_m,
+// with dJ_j/dtau_m (S fixed) from moving layer m: minus the slope times the layer's
+// weight in each adjacent segment, the slab-end term 1/2 S_{N-1} E_1(tau_{N-1} - tau_j) at
+// the bottom layer, the top segment's extrapolation terms, and the diagonal from
+// translation invariance (the row sums to 1/2 S(0) E_1(tau_j)).  Through the trapezoid and
+// eps = 1 - sigma/chi: G_d = dL/dchi_d + dL/deps_d sigma_d / chi_d^2, stored as G stim.
+template <typename KT, typename GT, bool TABLE>
+__global__ void __launch_bounds__(kScatThreads) k_rt_adjoint_scatter(ScatArgs g) {
+    extern __shared__ double sm[];
+    __shared__ int s_done;
+    const int nd = g.nd, W = nd + 1;
+    const ScatCol c = scat_carve<TABLE>(sm, nd);
+    const int64_t i = blockIdx.x;
+    const int st = blockIdx.y;
+    const int tid = threadIdx.x;
+    const double *m = g.m + (int64_t)st * nd;
+    const double *T = g.T + (int64_t)st * nd;
+    const int64_t base = (int64_t)st * nd * g.ld + i;
+    const double lam = g.lam0cm * exp((double)i * g.lnr);
+    const double Fb = g.dFbar[(int64_t)st * g.nlam + i];
+    for (int d = tid; d < nd; d += blockDim.x) c.B[d] = planck_nm(lam, T[d]);
+    scat_columns<KT, TABLE>(g, c, base, m, 0);
+    scat_lambda<TABLE>(c);
+    scat_lu(c);
+    for (int d = tid; d < nd; d += blockDim.x) c.a[d] = c.Lam[(size_t)d * W + nd];
+    __syncthreads();
+    scat_refine<false>(c, c.a, c.S, &s_done);
+    // J = Lambda S, E_n at the layers
+    for (int j = tid; j < nd; j += blockDim.x) {
+        const double *row = c.Lam + (size_t)j * W;
+        double v = 0.0;
+        for (int k = 0; k < nd; ++k) v = fma(row[k], c.S[k], v);
+        c.J[j] = v;
+        expn234(c.tau[j], c.e2[j], c.e3[j], c.e4[j]);
     }
-    dim3 nb((unsigned)c->nlam, c->S);
-    if (c->prec == PZ_MIXED)
-        k_flux_scatter<float, TABLE><<<nb, kScatThreads, smem, s>>>(g);
-    else
-        k_flux_scatter<double, TABLE><<<nb, kScatThreads, smem, s>>>(g);
-    c->launches++;
-    return cudaGetLastError();
+    __syncthreads();
+    // dF/dS (a, times dL/dF) and dF/dtau at fixed S (dF), both with the 2 pi of the flux
+    const double D1 = c.tau[1] - c.tau[0];
+    const double t0 = c.tau[0];
+    const double s0 = (c.S[1] - c.S[0]) / D1;
+    for (int d = tid; d < nd; d += blockDim.x) {
+        double a = 0.0, df = 0.0;
+        if (d + 1 < nd) {   // interval (d, d + 1), d its lower end
+            const double D = c.tau[d + 1] - c.tau[d];
+            const double q = (c.e4[d] - c.e4[d + 1] - D * c.e3[d + 1]) / D;
+            a += (c.e3[d] - c.e3[d + 1]) - q;
+            double da, db;
+            interval_grad(c.tau[d], c.tau[d + 1], c.S[d], c.S[d + 1], c.e2[d], c.e3[d], c.e4[d], c.e2[d + 1],
+                          c.e3[d + 1], c.e4[d + 1], da, db);
+            df += da;
+        }
+        if (d >= 1) {       // interval (d - 1, d), d its upper end
+            const double D = c.tau[d] - c.tau[d - 1];
+            a += (c.e4[d - 1] - c.e4[d] - D * c.e3[d]) / D;
+            double da, db;
+            interval_grad(c.tau[d - 1], c.tau[d], c.S[d - 1], c.S[d], c.e2[d - 1], c.e3[d - 1], c.e4[d - 1], c.e2[d],
+                          c.e3[d], c.e4[d], da, db);
+            df += db;
+        }
+        if (d <= 1) {       // top interval [0, tau_0] with S(0) = S0 - s0 tau_0
+            const double qt = (1.0 / 3.0 - c.e4[0] - t0 * c.e3[0]) / t0;
+            const double az = (0.5 - c.e3[0]) - qt;      // coefficient of S(0)
+            const double sp = s0 / D1;
+            const double Pt = 0.5 - c.e3[0];
+            const double Bt = 1.0 / 3.0 - c.e4[0] - t0 * c.e3[0];
+            if (d == 0) {
+                a += qt + az * (1.0 + t0 / D1);
+                df += -s0 * Pt + sp * (Bt - t0 * Pt) + c.S[0] * c.e2[0];
+            } else {
+                a += -az * t0 / D1;
+                df += -sp * (Bt - t0 * Pt);
+            }
+        }
+        c.a[d] = 2.0 * kPI * Fb * a;
+        c.dF[d] = 2.0 * kPI * Fb * df;
+    }
+    __syncthreads();
+    scat_refine<true>(c, c.a, c.mu, &s_done);
+    // dJ_j/dtau_m into the Lambda area (Lambda is no longer needed), one row per thread
+    const double Szero = c.S[0] - s0 * t0;
+    for (int j = tid; j < nd; j += blockDim.x) {
+        double *row = c.Lam + (size_t)j * W;
+        for (int k = 0; k < nd; ++k) row[k] = 0.0;
+        scat_row_weights<TABLE>(
+            c, j,
+            [&](int k, double wa, double wb) {
+                const double sk = (c.S[k + 1] - c.S[k]) * c.invD[k];
+                row[k] -= sk * wa;
+                row[k + 1] -= sk * wb;
+            },
+            [&](double wlo, double whi) {
+                row[0] += -(s0 / D1) * t0 * wlo - s0 * (wlo + whi);
+                row[1] += (s0 / D1) * t0 * wlo;
+            });
+        // the slab ends with the bottom layer
+        if (j != nd - 1) row[nd - 1] += 0.5 * c.S[nd - 1] * e1(c.tau[nd - 1] - c.tau[j]);
+        double off = 0.0;
+        for (int k = 0; k < nd; ++k)
+            if (k != j) off += row[k];
+        row[j] = 0.5 * Szero * e1(c.tau[j]) - off;
+    }
+    __syncthreads();
+    // dL/dtau_m and dL/deps_j
+    for (int mm = tid; mm < nd; mm += blockDim.x) {
+        double gtm = c.dF[mm];
+        for (int j = 0; j < nd; ++j) gtm = fma(c.mu[j] * (1.0 - c.eps[j]), c.Lam[(size_t)j * W + mm], gtm);
+        c.res[mm] = gtm;
+        c.ge[mm] = c.mu[mm] * (c.B[mm] - c.J[mm]);
+    }
+    __syncthreads();
+    // through the trapezoid (reverse cumulative sum) and eps = 1 - sigma/chi
+    if (tid == 0) {
+        GT *Gt = reinterpret_cast<GT *>(g.Gt) + (int64_t)st * nd * g.ld + i;
+        double Tn = 0.0;   // sum_{k > d} dL/dtau_k
+        for (int d = nd - 1; d >= 0; --d) {
+            const double Td = Tn + c.res[d];
+            double gch = 0.0;
+            if (d + 1 < nd) gch += 0.5 * (m[d + 1] - m[d]) * Tn;
+            if (d >= 1) gch += 0.5 * (m[d] - m[d - 1]) * Td;
+            else gch += m[0] * Td;
+            const double sig = g.sig[base + (int64_t)d * g.ld];
+            gch += c.ge[d] * sig / (c.chi[d] * c.chi[d]);
+            const double stim = -expm1(-kC2 / (lam * T[d]));
+            Gt[(int64_t)d * g.ld] = (GT)(gch * stim);
+            Tn = Td;
+        }
+    }
 }
 
-cudaError_t launch_flux_scatter(pz_ctx *c, cudaStream_t s) {
+template <bool TABLE>
+static cudaError_t scatter_attr(pz_ctx *c, size_t smem) {
+    static size_t attr_set[64] = {0};   // dynamic shared memory granted so far, per device
+    if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
+    if (smem <= attr_set[c->device]) return cudaSuccess;
+    const void *fns[4] = {(const void *)k_flux_scatter<float, TABLE>, (const void *)k_flux_scatter<double, TABLE>,
+                          (const void *)k_rt_adjoint_scatter<float, float, TABLE>,
+                          (const void *)k_rt_adjoint_scatter<double, double, TABLE>};
+    for (const void *f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    attr_set[c->device] = smem;
+    return cudaSuccess;
+}
+
+static ScatArgs scatter_args(pz_ctx *c) {
     ScatArgs g;
     g.nlam = c->nlam;
     g.ld = c->ld;
@@ -590,7 +825,39 @@ cudaError_t launch_flux_scatter(pz_ctx *c, cudaStream_t s) {
     g.kline = c->d_kline;
     g.F = c->d_F;
     g.Fc = c->d_Fc;
-    return c->nd <= kScatTableMaxDepth ? launch_scatter_t<true>(c, g, s) : launch_scatter_t<false>(c, g, s);
+    g.dFbar = c->d_dFbar;
+    g.Gt = c->prec == PZ_MIXED ? (void *)c->d_Gt : (void *)c->d_Gt64;
+    return g;
+}
+
+template <bool TABLE>
+static cudaError_t launch_scatter_t(pz_ctx *c, bool adjoint, cudaStream_t s) {
+    const size_t smem = scatter_smem(c->nd, TABLE);
+    cudaError_t e = scatter_attr<TABLE>(c, smem);
+    if (e != cudaSuccess) return e;
+    const ScatArgs g = scatter_args(c);
+    dim3 nb((unsigned)c->nlam, c->S);
+    if (!adjoint) {
+        if (c->prec == PZ_MIXED)
+            k_flux_scatter<float, TABLE><<<nb, kScatThreads, smem, s>>>(g);
+        else
+            k_flux_scatter<double, TABLE><<<nb, kScatThreads, smem, s>>>(g);
+    } else {
+        if (c->prec == PZ_MIXED)
+            k_rt_adjoint_scatter<float, float, TABLE><<<nb, kScatThreads, smem, s>>>(g);
+        else
+            k_rt_adjoint_scatter<double, double, TABLE><<<nb, kScatThreads, smem, s>>>(g);
+    }
+    c->launches++;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux_scatter(pz_ctx *c, cudaStream_t s) {
+    return c->nd <= kScatTableMaxDepth ? launch_scatter_t<true>(c, false, s) : launch_scatter_t<false>(c, false, s);
+}
+
+cudaError_t launch_rt_adjoint_scatter(pz_ctx *c, cudaStream_t s) {
+    return c->nd <= kScatTableMaxDepth ? launch_scatter_t<true>(c, true, s) : launch_scatter_t<false>(c, true, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -872,6 +1139,7 @@ __global__ void k_rt_adjoint(RtAdjArgs g) {
 }
 
 cudaError_t launch_rt_adjoint(pz_ctx *c, cudaStream_t s) {
+    if (c->d_sigma) return launch_rt_adjoint_scatter(c, s);
     RtAdjArgs g;
     g.nlam = c->nlam;
     g.ld = c->ld;

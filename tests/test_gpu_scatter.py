@@ -8,7 +8,7 @@ import pytest
 
 import paper_2607_24141_gb300 as pz
 from paper_2607_24141_gb300 import inputs as I
-from gpu_util import run_forward
+from gpu_util import rel_metric, run_forward, run_gradient
 from tiny import tiny_problem
 
 pytestmark = pytest.mark.gpu
@@ -71,10 +71,6 @@ def test_scattering_state_rules():
         pz.pz_instrument(s.ctx, 0.0, 0.0, 0.0, None)
     assert e.value.status == pz.PZ_ESTATE
     f_sc = s.forward()
-    dLdf = torch.ones_like(f_sc)
-    with pytest.raises(pz.PzError) as e:
-        s.backward(dLdf)
-    assert e.value.status == pz.PZ_ESTATE
     assert np.max(np.abs(f_sc.cpu().numpy() - f_lte)) > 1e-6
     pz.pz_set_scattering(s.ctx, None)
     # the LTE spectrum again (up to the order of the near-core shared-memory atomics)
@@ -90,3 +86,29 @@ def test_scattering_batch_matches_the_oracle_per_star(oracle):
         ref = oracle.forward(b.star(k))
         assert np.max(np.abs(f[k] - ref["f"])) < 1e-6
     s.close()
+
+
+@pytest.mark.parametrize("n_depth,instrument", [(30, False), (72, True)])
+def test_scattering_gradients(oracle, n_depth, instrument):
+    """The reverse pass through the scattering source (adjoint of the linear system, the
+    dependence of J on the optical depths, eps = 1 - sigma/chi) against the oracle's."""
+    prob = I.with_scattering(tiny_problem(n_lambda=600, n_depth=n_depth, n_lines=40, W=200, seed=n_depth + 3,
+                                          lam0=360.0, instrument=instrument), r0=3.0)
+    prob.lines.log_gf[:] -= 3.0
+    rng = np.random.default_rng(11)
+    nl = prob.lines.n_lines
+    corr = {"dlog_gf": rng.normal(0, 0.1, nl), "dlog_gamma6": rng.normal(0, 0.2, nl),
+            "dabund": rng.normal(0, 0.1, prob.n_elem)}
+    corr = {k: v.astype(np.float32).astype(np.float64) for k, v in corr.items()}
+    f0 = oracle.forward(prob, corr)
+    n_out = f0["f"].size
+    y = (f0["f"] + rng.normal(0, 1 / 200, n_out)).astype(np.float32).astype(np.float64)
+    w = 200.0 ** 2
+    L, ggf, gg6, gab, _ = oracle.gradient(prob, y, np.full(n_out, w), corr, fwd=f0)
+    c32 = {k: v.astype(np.float32) for k, v in corr.items()}
+    for prec, tol in ((pz.PZ_MIXED, 1e-3), (pz.PZ_FP64, 1e-5)):
+        got = run_gradient(prob, y.astype(np.float32), np.float32(w), prec, c32)
+        errs = (rel_metric(got["g_gf"], ggf).max(), rel_metric(got["g_g6"], gg6).max(),
+                rel_metric(got["g_ab"][:prob.n_elem], gab).max())
+        print("scattering gradients nd=%d prec=%d:" % (n_depth, prec), errs)
+        assert max(errs) < tol, (prec, errs)
