@@ -45,13 +45,19 @@ FMA_PER_EN = 39      # FP64 FMAs of one E_2/E_3/E_4 Taylor step (13 rounds of va
 
 # Per-evaluation pipe work of the far-wing kernels, which evaluate every in-window cell.
 # Reduced form (lines >= 100 Doppler widths from the whole tile, most cells of this
-# workload), written in p = (1/u^2)(1/k^2): forward 3 FP32-pipe lane operations
-# (p, B1 + B2' p, accumulate), backward 6 (p, G p, two polynomials, two accumulations),
-# and one MUFU reciprocal per line and point shared by the DS = 6 depths of a warp.
-# Full far form: 7 / 13 FP32-pipe operations and 1 MUFU reciprocal.  With 128 FP32
-# lanes and 16 MUFU lanes per SM the FP32 pipe binds.
-OPS = {"line_fwd": {"fp32_reduced": 3, "fp32_full": 7, "mufu_reduced": 1.0 / 6, "mufu_full": 1},
-       "line_bwd": {"fp32_reduced": 6, "fp32_full": 13, "mufu_reduced": 1.0 / 6, "mufu_full": 1}}
+# workload), with s = 1/U shared by the depths of a warp and the table's coefficients
+# (B1 K, B2' K^2, C1 K, C2' K^2): forward 2 FP32-pipe lane operations per cell (two
+# products accumulated); backward, per depth and thread, X1 = sum_j G s_j and
+# X2 = sum_j G s_j^2 over the thread's J points (2 per cell) and four products into
+# the two sums, 2 + 4/J per cell; one MUFU reciprocal per line and point shared by the
+# DS = 6 depths of a warp.  Full far form: 7 / 13 FP32-pipe operations and 1 MUFU
+# reciprocal.  With 128 FP32 lanes and 16 MUFU lanes per SM the FP32 pipe binds.
+def far_ops(J):
+    return {"line_fwd": {"fp32_reduced": 2, "fp32_full": 7, "mufu_reduced": 1.0 / 6, "mufu_full": 1},
+            "line_bwd": {"fp32_reduced": 2 + 4.0 / J, "fp32_full": 13, "mufu_reduced": 1.0 / 6, "mufu_full": 1}}
+
+
+OPS = far_ops(4)
 
 
 def parse():
@@ -967,7 +973,7 @@ def main():
            "line_bwd": ktimes["line_bwd"][0] - ktimes["near_bwd"][0]}
     dom = max(far, key=far.get)
     t_dom = far[dom] * 1e-3 / max(ktimes[dom][1], 1)            # s per launch of the far-wing kernel
-    ops = OPS[dom]
+    ops = far_ops(tune["tiling"][0] if tune else 4)[dom]
     # pipe peaks measured on this GPU by the library's probe kernels (independent
     # reciprocal / packed-FMA chains on every SM), next to the lane-count derivation
     peak_mufu_lanes = n_sm * 16 * clk_max * 1e6

@@ -117,11 +117,22 @@ static void dfree(void *p) {
 // longest first, so that the queue balances uneven stars and tiles.
 //   far:  lines whose window |i - i_l| <= W touches the tile; one item per depth
 //         group of DS x GW layers, every (star, tile, group) present (the far
-//         forward writes every cell of kappa_line);
+//         forward writes every cell of kappa_line).  An item that costs much more
+//         than 1/kPiecesPerCta of a resident CTA's share is cut into P pieces of
+//         its line range (a single spectrum has fewer (tile, group) items than
+//         twice the resident CTAs, and whole items left a long tail of idle SMs).
+//         Backward pieces add their per-line sums atomically like whole items;
+//         forward pieces store compensated partial sums, and the piece that
+//         finishes an item last combines them in piece order (deterministic);
 //   near: lines whose centre lies within 20 Doppler widths (the widest of the star)
 //         of the tile plus a margin; forward items for every (star, tile, group of
 //         8 layers) (they write the near-core buffer), backward items of 24 layers
 //         only where the range is not empty.
+constexpr double kPiecesPerCta = 8.0;       // target far pieces per resident CTA
+constexpr int kMaxPieces = 32;              // pieces of one far item at most
+constexpr int kMinPieceLines = 256;         // lines of a far piece at least
+constexpr size_t kMaxPartBytes = (size_t)512 << 20;   // partial-sum buffer of the split forward items
+
 static pz_status build_items(pz_ctx *c) {
     const int T = c->tiling.lambda_per_tile();
     const int nt = (int)((c->nlam + T - 1) / T);
@@ -165,18 +176,71 @@ static pz_status build_items(pz_ctx *c) {
         for (size_t k = 0; k < v.size(); ++k) out[k] = v[k].v;
         return out;
     };
-    int nbusy = 0;
-    for (const Item &it : fi) nbusy += it.v.w > it.v.z;
-    std::vector<int4> hf = order(fi), hn = order(nf), hb = order(nb);
+    // far pieces: P = round(cost / piece cost), the piece cost a 1/kPiecesPerCta share of
+    // what each resident CTA (n_sm x minb of them) would take
+    double tot = 0.0;
+    for (const Item &it : fi) tot += it.cost;
+    const double workers = (double)std::max(c->n_sm, 1) * std::max(c->tiling.minb, 1);
+    const double piece = std::max(tot / (workers * kPiecesPerCta), 1.0);
+    const size_t slot_bytes = (size_t)DC * 32 * 2 * sizeof(float4);   // DS x threads x (hi, lo) quads
+    struct FItem {
+        int4 v, ext;
+        double cost;
+    };
+    std::vector<FItem> fp;
+    std::vector<Item> bp;
+    fp.reserve(fi.size());
+    int nslot = 0, nsplit = 0;
+    for (const Item &it : fi) {
+        const int n = it.v.w - it.v.z;
+        int P = (int)std::lround(it.cost / piece);
+        P = std::max(1, std::min({P, kMaxPieces, n / kMinPieceLines}));
+        if ((size_t)(nslot + P) * slot_bytes > kMaxPartBytes) P = 1;
+        for (int q = 0; q < P; ++q) {
+            const int lo = it.v.z + (int)((int64_t)n * q / P), hi = it.v.z + (int)((int64_t)n * (q + 1) / P);
+            const int4 v = make_int4(it.v.x, it.v.y, lo, hi);
+            const int4 ext = P > 1 ? make_int4(nslot, P, nsplit, q) : make_int4(-1, 1, -1, 0);
+            fp.push_back({v, ext, it.cost / P});
+            if (hi > lo) bp.push_back({v, it.cost / P});
+        }
+        if (P > 1) {
+            nslot += P;
+            ++nsplit;
+        }
+    }
+    std::stable_sort(fp.begin(), fp.end(), [](const FItem &x, const FItem &y) { return x.cost > y.cost; });
+    std::vector<int4> hf(fp.size()), hx(fp.size());
+    for (size_t k = 0; k < fp.size(); ++k) {
+        hf[k] = fp[k].v;
+        hx[k] = fp[k].ext;
+    }
+    std::vector<int4> hbf = order(bp), hn = order(nf), hb = order(nb);
     dfree(c->d_fitems);
+    dfree(c->d_fext);
+    dfree(c->d_bitems);
     dfree(c->d_nitems_f);
     dfree(c->d_nitems_b);
-    c->d_fitems = c->d_nitems_f = c->d_nitems_b = nullptr;
+    dfree(c->d_fcnt);
+    c->d_fitems = c->d_fext = c->d_bitems = c->d_nitems_f = c->d_nitems_b = nullptr;
+    c->d_fcnt = nullptr;
     PZ_TRY(upload(&c->d_fitems, hf, "work items"));
+    PZ_TRY(upload(&c->d_fext, hx, "work items"));
+    PZ_TRY(upload(&c->d_bitems, hbf, "work items"));
     PZ_TRY(upload(&c->d_nitems_f, hn, "work items"));
     PZ_TRY(upload(&c->d_nitems_b, hb, "work items"));
+    PZ_TRY(dalloc(&c->d_fcnt, (size_t)nsplit, "work items"));
+    PZ_CUDA(cudaMemset(c->d_fcnt, 0, sizeof(int) * std::max(nsplit, 1)), "work items");
+    const size_t part = (size_t)nslot * slot_bytes;
+    if (c->fpart_cap < part) {
+        dfree(c->d_fpart);
+        c->d_fpart = nullptr;
+        c->fpart_cap = 0;
+        PZ_TRY(dalloc(&c->d_fpart, part / sizeof(float4), "far-wing partial sums"));
+        c->fpart_cap = part;
+    }
     c->n_fitems = (int)hf.size();
-    c->n_bitems = nbusy;
+    c->n_bitems = (int)hbf.size();
+    c->n_fsplit = nsplit;
     c->n_nitems_f = (int)hn.size();
     c->n_nitems_b = (int)hb.size();
     c->ntiles = nt;
@@ -226,7 +290,8 @@ static void destroy_ctx(pz_ctx *c) {
                     c->d_thr, c->d_kc, c->d_dab, c->d_mdgf, c->d_mdg6, c->d_eos, c->L.orig, c->L.star, c->L.ilf,
                     c->L.il32, c->L.frac, c->L.sp, c->L.E, c->L.lamcm, c->L.grad, c->L.g4, c->L.g6base, c->L.g6,
                     c->L.Q, c->L.Qbase, c->L.x64, c->L.lg_gf, c->L.lg_rad, c->L.lg_4, c->L.lg_6, c->L.dgf, c->L.dg6,
-                    c->d_line_off, c->d_fitems, c->d_nitems_f, c->d_nitems_b, c->d_ctr, c->d_knear, c->d_kline,
+                    c->d_line_off, c->d_fitems, c->d_fext, c->d_bitems, c->d_fpart, c->d_fcnt, c->d_nitems_f,
+                    c->d_nitems_b, c->d_ctr, c->d_knear, c->d_kline,
                     c->d_F, c->d_Fc, c->d_g, c->d_gc, c->d_tap0, c->d_ntap, c->d_tapw, c->d_dFbar, c->d_Gt,
                     c->d_Gt64, c->d_gacc, c->d_gline, c->d_gab, c->d_dLdf, c->d_ftab, c->d_finfo, c->d_status,
                     c->d_keep, c->L.gradbase, c->L.g4base, c->L.dgrad, c->L.dg4, c->d_mdgrad, c->d_mdg4,

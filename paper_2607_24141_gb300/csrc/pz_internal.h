@@ -141,10 +141,18 @@ struct pz_ctx {
     pz::LineTable L;
     int64_t *d_line_off = nullptr;  // [S+1]
     // work items (star, tile * groups + group, lo, hi), longest first
-    int4 *d_fitems = nullptr;       // far-wing kernels
+    // (far-wing items with many lines are split into pieces of their line range, so that
+    // the queue holds several items per resident CTA; see build_items)
+    int4 *d_fitems = nullptr;       // far-wing forward pieces
+    int4 *d_fext = nullptr;         // per forward piece: (first slot, pieces, item counter, piece)
+    int4 *d_bitems = nullptr;       // far-wing backward pieces (those holding lines)
     int4 *d_nitems_f = nullptr;     // near-core forward
     int4 *d_nitems_b = nullptr;     // near-core backward
-    int n_fitems = 0, n_bitems = 0, n_nitems_f = 0, n_nitems_b = 0;  // n_bitems: far items holding lines
+    int n_fitems = 0, n_bitems = 0, n_nitems_f = 0, n_nitems_b = 0;
+    float4 *d_fpart = nullptr;      // compensated partial sums of the split forward items
+    size_t fpart_cap = 0;           // bytes allocated at d_fpart
+    int *d_fcnt = nullptr;          // [n_fsplit] pieces finished per split forward item
+    int n_fsplit = 0;
     int *d_ctr = nullptr;           // [4] work-queue counters
     int ntiles = 0, tileT = 0;
     float *d_knear = nullptr;       // [S][nd][ld] near-core sums of the forward

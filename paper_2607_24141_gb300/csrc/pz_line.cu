@@ -148,6 +148,9 @@ struct LineArgs {
     int64_t nl;
     // work queue: items (star, tile * ngroups + group, lo, hi), longest first
     const int4 *items;
+    const int4 *fext;                               // forward pieces: (first slot, pieces, counter, piece)
+    float4 *fpart;                                  // partial sums of split forward items [slot][DS][threads][2]
+    int *fcnt;                                      // pieces finished per split forward item
     int n_items, ngroups;
     int *ctr;
     int64_t sstride, dstride, bstride, tstride;     // per-star strides of the tables above
@@ -194,11 +197,11 @@ __device__ __forceinline__ void for_each_item(const LineArgs &g, F &&f) {
         __syncthreads();
         if (it >= g.n_items) break;
         const int4 item = g.items[it];
-        using R = decltype(f(star_view(g, item.x), 0, 0, 0, 0));
+        using R = decltype(f(star_view(g, item.x), 0, 0, 0, 0, 0));
         if constexpr (std::is_same<R, bool>::value) {
-            if (!f(star_view(g, item.x), item.y / g.ngroups, item.y % g.ngroups, item.z, item.w)) break;
+            if (!f(star_view(g, item.x), item.y / g.ngroups, item.y % g.ngroups, item.z, item.w, it)) break;
         } else {
-            f(star_view(g, item.x), item.y / g.ngroups, item.y % g.ngroups, item.z, item.w);
+            f(star_view(g, item.x), item.y / g.ngroups, item.y % g.ngroups, item.z, item.w, it);
         }
     }
 }
@@ -336,29 +339,41 @@ __device__ __forceinline__ float f2_lo(f2_t v) {
 // layers and every line l, the (DC/2) depth pairs of NQ quads, quad q holding
 // {p_2q(d), p_2q(d + 1), p_2q+1(d), p_2q+1(d + 1)} (one 16-byte load returns the
 // packed depth pairs of two parameters):
-//   forward  (NQ = 2): (1/k^2, a^2) (B1, B2')
-//   backward (NQ = 3): (1/k^2, a^2) (B1, B2') (C1, C2')
-// with k = c/dv_D, B2' = B2 - B1 a^2 = B1 (1.5 - a^2) and C2' = C2 - C1 a^2 = C1 (1.5 - 3a^2).
-// Away from the masked lines |z|^2 = (u^2 + a^2/k^2) k^2, u^2 formed once per point and
-// shared by all depths; B2 = 1.5 B1 and C2 = (1.5 - 2a^2) C1 are restored in registers.
-// at tab[(g n_lines + l) (DC/2) NQ + pair NQ + q], and the line record at
+//   forward  (NQ = 2): (K, a^2) (B1 K, B2' K^2)
+//   backward (NQ = 3): (K, a^2) (B1 K, B2' K^2) (C1 K, C2' K^2)
+// with k = c/dv_D, K = 2^36/k^2 (the power of two keeps every product of the table
+// and of the offsets far from the FP32 exponent limits), B2' = B2 - B1 a^2 =
+// B1 (1.5 - a^2) and C2' = C2 - C1 a^2 = C1 (1.5 - 3a^2).  The far kernels take the
+// squared offsets scaled alike, U = 2^36 u^2, so that with s = 1/U
+//   reduced form:  H sqrt(pi)/A = (B1 K) s + (B2' K^2) s^2   (p = K s exactly, see below)
+//   full form:     r = 1/(U + a^2 K) and t = 1/|z|^2 = K r, so B1 t (...) = (B1 K) r (...)
+// and the masked lines recover B1 = (B1 K) k^2 2^-36 (and C1 alike) per depth pair.
+// The table sits at tab[(g n_lines + l) (DC/2) NQ + pair NQ + q], the line record at
 // info[g n_lines + l].  The rest of the far polynomial (B3..B5, C3..C6) follows
-// from a^2, B1 and C1 in registers.  The chunk of LC lines a CTA needs is then
+// from a^2 and B1 K (C1 K) in registers.  The chunk of LC lines a CTA needs is then
 // one contiguous block, which the kernels move into shared memory with bulk
 // copies (cp.async.bulk, completion on an mbarrier), double-buffered.
 constexpr int kNQF = 2, kNQB = 3;
+constexpr float kKScale = 68719476736.0f;         // 2^36: K = 2^36/k^2, U = 2^36 u^2
+constexpr float kUScale = 262144.0f;              // 2^18: scaled offset u 2^18
+constexpr float kKUnscale = 1.4551915228366852e-11f;   // 2^-36
 
 // Reduced far-wing form.  Far from the core the polynomial in t = 1/|z|^2 is cut
 // after its t^2 term: H sqrt(pi)/(A a) = t (1 + 1.5 t) and, for dH/da, C1 t (1 +
 // (1.5 - 2a^2) t).  With |v| >= 100 (t <= 1e-4) and a^2 <= 1.5 (s = a^2 t <= 1.5e-4)
 // the dropped terms, (3.75 t^2 + 2 s t + 15 s t^2 + 12 s^2 t^2) relative for H, stay
 // below 7e-8 (about one FP32 rounding) and below 2.2e-7 for dH/da.
-// In the same region t is expanded about p = 1/(u k)^2 = (1/u^2)(1/k^2):
+// In the same region t is expanded about p = 1/(u k)^2 = (1/U) K:
 // t = p/(1 + a^2 p) = p - a^2 p^2 + O((a^2 p)^2 p), so that
-//   H sqrt(pi)/A = B1 p + B2' p^2,   dH/da sqrt(pi)/(A a6) = C1 p + C2' p^2
-// with B2' = B1 (1.5 - a^2), C2' = C1 (1.5 - 3a^2); the further dropped terms,
-// (a^2 p)^2 and 3 a^2 p^2 relative, stay below 5e-8.  1/u^2 depends on the line and the
-// point only, so one MUFU reciprocal serves all the depths of a warp.
+//   H sqrt(pi)/A = B1 p + B2' p^2 = (B1 K) s + (B2' K^2) s^2,   s = 1/U,
+// and dH/da sqrt(pi)/(A a6) = (C1 K) s + (C2' K^2) s^2, with B2' = B1 (1.5 - a^2),
+// C2' = C1 (1.5 - 3a^2); the further dropped terms, (a^2 p)^2 and 3 a^2 p^2 relative,
+// stay below 5e-8.  s and s^2 depend on the line and the point only, so one MUFU
+// reciprocal serves all the depths of a warp, and the forward adds two products per
+// cell.  In the backward the sums over the cells of one depth factor:
+//   sum_i G_i [(B1 K) s_i + (B2' K^2) s_i^2] = (B1 K) X1 + (B2' K^2) X2,
+//   X1 = sum_i G_i s_i,  X2 = sum_i G_i s_i^2,
+// and X1, X2 serve both gradients (the C coefficients multiply the same sums).
 constexpr float kFast2V = 5.0f;      // distance threshold factor: |v| >= 5 x 20
 constexpr float kFast2A2 = 1.5f;     // a^2 bound
 
@@ -385,14 +400,16 @@ __global__ void k_far_table(LineArgs gq, int DC, int DS, int ngroups, float4 *ta
         if (!pair_kept(g.keep, l, d)) p0[2] = p0[3] = p0[8] = p0[9] = 0.0f;
         if (!pair_kept(g.keep, l, d + 1)) p1[2] = p1[3] = p1[8] = p1[9] = 0.0f;
         float4 *dst = tab + gl * (P * NQ) + pr * NQ;
-        // 1/k^2 (0 on the padding layers past the last one, whose coefficients are 0)
-        const float ik0 = p0[0] > 0.0f ? 1.0f / (p0[0] * p0[0]) : 0.0f;
-        const float ik1 = p1[0] > 0.0f ? 1.0f / (p1[0] * p1[0]) : 0.0f;
-        dst[0] = make_float4(ik0, ik1, p0[1], p1[1]);
-        // B2' = B2 - B1 a^2 and C2' = C2 - C1 a^2 (the reduced forms in p, see far_reduced)
-        dst[1] = make_float4(p0[2], p1[2], fmaf(-p0[2], p0[1], p0[3]), fmaf(-p1[2], p1[1], p1[3]));
+        // K = 2^36/k^2 (0 on the padding layers past the last one, whose coefficients are 0)
+        const float K0 = p0[0] > 0.0f ? kKScale / (p0[0] * p0[0]) : 0.0f;
+        const float K1 = p1[0] > 0.0f ? kKScale / (p1[0] * p1[0]) : 0.0f;
+        const float KK0 = K0 * K0, KK1 = K1 * K1;
+        dst[0] = make_float4(K0, K1, p0[1], p1[1]);
+        // (B1 K, B2' K^2) with B2' = B2 - B1 a^2, and (C1 K, C2' K^2) with C2' = C2 - C1 a^2
+        dst[1] = make_float4(p0[2] * K0, p1[2] * K1, fmaf(-p0[2], p0[1], p0[3]) * KK0, fmaf(-p1[2], p1[1], p1[3]) * KK1);
         if (NQ == kNQB)
-            dst[2] = make_float4(p0[8], p1[8], fmaf(-p0[8], p0[1], p0[9]), fmaf(-p1[8], p1[1], p1[9]));
+            dst[2] = make_float4(p0[8] * K0, p1[8] * K1, fmaf(-p0[8], p0[1], p0[9]) * KK0,
+                                 fmaf(-p1[8], p1[1], p1[9]) * KK1);
         if (pr == 0) {
             // bit w: a^2 <= kFast2A2 on every layer of slab w; bit 8 + w: the centre test
             // rejects every layer of slab w (its warp skips the line)
@@ -507,7 +524,7 @@ __device__ __forceinline__ void far_abort(const LineArgs &g, const ChunkPipe &cp
 // and every cell of the warp's slab is in the far wing (|v| >= 20); bit 1 if every
 // cell of the slab has |v| >= 100 and a^2 <= kFast2A2 at every layer (reduced form),
 // whether or not the window covers the tile: the reduced form masks the window per
-// point at no cost per cell (a zero reciprocal 1/u^2).
+// point at no cost per cell (a zero reciprocal s = 1/U).
 __device__ __forceinline__ int far_flags(const LineArgs &g, const LineInfo &info, float t0f, float tendf, int slab,
                                          int w) {
     const float dlo = info.ilf - t0f + info.frac;      // x_l - t0
@@ -562,7 +579,7 @@ __device__ __forceinline__ void far_c3456(f2_t a2, f2_t C1, f2_t &C3, f2_t &C4, 
 // Returns false if a chunk never arrived (the kernel stops).
 template <int J, int DS>
 __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, const int group, const int lo,
-                                             const int hi, const int GW, ChunkPipe &cp) {
+                                             const int hi, const int GW, ChunkPipe &cp, const int4 ext) {
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
     static_assert(DS % 2 == 0, "DS must be even (depth pairs)");
     constexpr int DP = DS / 2;          // depth pairs per warp
@@ -627,11 +644,12 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
             f2_t u2[J];
             if (fl != 0) {
                 // the whole tile is in the line's far wing: offsets from the first point's,
-                // u_j = u_0 r^-j + (r^-j - 1), and their squares
-                const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
+                // u_j = u_0 r^-j + (r^-j - 1), scaled by 2^18, and their squares U = 2^36 u^2
+                const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr) * kUScale;
                 u2[0] = f2_splat(u0);
 #pragma unroll
-                for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j]));
+                for (int j = 1; j < J; ++j)
+                    u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j] * kUScale));
 #pragma unroll
                 for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
             } else {
@@ -640,9 +658,9 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                 for (int j = 0; j < J; ++j) u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
             }
             if (fl & 2) {
-                // reduced form in p = (1/u^2)(1/k^2): B1 p + B2' p^2; points outside the
-                // window (lines whose window edge crosses the tile) get 1/u^2 = 0
-                f2_t sp[J];
+                // reduced form (B1 K) s + (B2' K^2) s^2 with s = 1/U; points outside the
+                // window (lines whose window edge crosses the tile) get s = 0
+                f2_t sp[J], sq[J];
                 if (fl & 1) {
 #pragma unroll
                     for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(u2[j])));
@@ -655,32 +673,34 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                     }
                 }
 #pragma unroll
-                for (int dp = 0; dp < DP; ++dp) {
-                    // q0 = (1/k^2, a^2), q1 = (B1, B2')
-                    const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
+                for (int j = 0; j < J; ++j) sq[j] = f2_mul(sp[j], sp[j]);
 #pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        const f2_t pp = f2_mul(sp[j], q0.x);
-                        acc[dp][j] = f2_fma(pp, f2_fma(pp, q1.y, q1.x), acc[dp][j]);
-                    }
+                for (int dp = 0; dp < DP; ++dp) {
+                    // q1 = (B1 K, B2' K^2)
+                    const ulonglong2 q1 = par[NQ * dp + 1];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) acc[dp][j] = f2_fma(sq[j], q1.y, f2_fma(sp[j], q1.x, acc[dp][j]));
                 }
             } else if (fl & 1) {
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
+                    // q0 = (K, a^2), q1 = (B1 K, B2' K^2): the polynomial in t with every
+                    // coefficient times K, applied to r = t/K
                     const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
                     f2_t B3, B4, B5;
                     far_b345(q0.y, q1.x, B3, B4, B5);
                     const f2_t B2 = f2_mul(q1.x, f2_splat(1.5f));
-                    const f2_t ak = f2_mul(q0.y, q0.x);          // a^2/k^2
+                    const f2_t ak = f2_mul(q0.y, q0.x);          // a^2 K
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        // t = 1/(u^2 k^2 + a^2) = (1/k^2)/(u^2 + a^2/k^2)
-                        const f2_t t = f2_mul(q0.x, f2_rcp(f2_fma(u2[j], f2_splat(1.0f), ak)));
+                        // r = 1/(U + a^2 K) = 2^-36/(u^2 + a^2/k^2), t = 1/(u^2 k^2 + a^2) = K r
+                        const f2_t r = f2_rcp(f2_fma(u2[j], f2_splat(1.0f), ak));
+                        const f2_t t = f2_mul(q0.x, r);
                         f2_t h = f2_fma(t, B5, B4);
                         h = f2_fma(t, h, B3);
                         h = f2_fma(t, h, B2);
                         h = f2_fma(t, h, q1.x);
-                        acc[dp][j] = f2_fma(t, h, acc[dp][j]);
+                        acc[dp][j] = f2_fma(r, h, acc[dp][j]);
                     }
                 }
             } else {
@@ -697,9 +717,11 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
                     const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
+                    // B1 = (B1 K) k^2 2^-36
+                    const f2_t B1 = f2_mul(q1.x, f2_mul(f2_mul(kp[dp], kp[dp]), f2_splat(kKUnscale)));
                     f2_t B3, B4, B5;
-                    far_b345(q0.y, q1.x, B3, B4, B5);
-                    const f2_t B2 = f2_mul(q1.x, f2_splat(1.5f));
+                    far_b345(q0.y, B1, B3, B4, B5);
+                    const f2_t B2 = f2_mul(B1, f2_splat(1.5f));
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const f2_t x = f2_mul(u2[j], kp[dp]);
@@ -708,7 +730,7 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                         f2_t h = f2_fma(t, B5, B4);
                         h = f2_fma(t, h, B3);
                         h = f2_fma(t, h, B2);
-                        h = f2_fma(t, h, q1.x);
+                        h = f2_fma(t, h, B1);
                         const f2_t r = f2_fma(t, h, acc[dp][j]);
                         float r2a, r2b, ra, rb, aa, ab;
                         f2_unpack(r2, r2a, r2b);
@@ -753,6 +775,48 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
         }
     }
     cp.cc += nch;
+
+    if (ext.y > 1) {
+        // one of ext.y pieces of a split item (slots ext.x.., counter ext.z, piece ext.w):
+        // store this piece's compensated sums; the piece that completes the item adds
+        // all pieces' sums in piece order and finishes the cells below
+        __shared__ int s_last;
+        const size_t slot = (size_t)DS * nthr * 2;
+        float4 *mine = g.fpart + (size_t)(ext.x + ext.w) * slot;
+#pragma unroll
+        for (int dd = 0; dd < DS; ++dd) {
+            const float4 *cs = reinterpret_cast<const float4 *>(s_comp + comp_slot(dd, tid, nthr));
+            mine[((size_t)dd * nthr + tid) * 2] = cs[0];
+            mine[((size_t)dd * nthr + tid) * 2 + 1] = cs[1];
+        }
+        __threadfence();
+        __syncthreads();
+        if (tid == 0) s_last = atomicAdd(g.fcnt + ext.z, 1) == ext.y - 1;
+        __syncthreads();
+        if (!s_last) return true;
+        __threadfence();
+#pragma unroll
+        for (int dd = 0; dd < DS; ++dd) {
+            float hj[4] = {0.f, 0.f, 0.f, 0.f}, lj[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int q = 0; q < ext.y; ++q) {
+                const float4 *src = g.fpart + (size_t)(ext.x + q) * slot + ((size_t)dd * nthr + tid) * 2;
+                const float4 h4 = __ldcg(src), l4 = __ldcg(src + 1);
+                const float hq[4] = {h4.x, h4.y, h4.z, h4.w}, lq[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const float h = hj[j], p = hq[j];
+                    const float sum = h + p;
+                    const float bp = sum - h;
+                    const float e = (h - (sum - bp)) + (p - bp);
+                    hj[j] = sum;
+                    lj[j] += lq[j] + e;
+                }
+            }
+            float4 *cs = reinterpret_cast<float4 *>(s_comp + comp_slot(dd, tid, nthr));
+            cs[0] = make_float4(hj[0], hj[1], hj[2], hj[3]);
+            cs[1] = make_float4(lj[0], lj[1], lj[2], lj[3]);
+        }
+    }
 
     // epilogue: near-core sums, stimulated-emission factor at the sample frequency, vector store
 #pragma unroll
@@ -801,21 +865,22 @@ __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int 
     __shared__ uint64_t bars[2];
     pipe_init(bars);
     ChunkPipe cp{bars, smem4, LC, GW * DS / 2 * kNQF, 0u};
-    for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi) {
-        return far_fwd_item<J, DS>(v, tile, group, lo, hi, GW, cp);
+    for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi, int it) {
+        return far_fwd_item<J, DS>(v, tile, group, lo, hi, GW, cp, g.fext ? g.fext[it] : make_int4(-1, 1, -1, 0));
     });
 }
 
 // Reduced far-wing backward form (lines flagged for it): H and dH/da polynomials cut
-// after their t^2 terms.  par: the warp's depth pairs, (1/k^2, a^2) (B1, B2') (C1, C2');
-// usq: the squared offsets u^2 of the thread's points.
+// after their t^2 terms.  par: the warp's depth pairs, (K, a^2) (B1 K, B2' K^2)
+// (C1 K, C2' K^2); usq: the scaled squared offsets U = 2^36 u^2 of the thread's points.
 template <int J, int DP>
 __device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, const f2_t (&usq)[J],
                                                      const f2_t (&gv)[DP][J], bool full, int di0, int W, f2_t &S1,
                                                      f2_t &S2) {
-    // reduced forms in p = (1/u^2)(1/k^2): G (B1 p + B2' p^2) and G (C1 p + C2' p^2);
-    // points outside the window (di0 + j = i - i_l) get 1/u^2 = 0 unless it covers the tile
-    f2_t sp[J];
+    // reduced forms with s = 1/U: per depth pair X1 = sum_j G s_j and X2 = sum_j G s_j^2,
+    // then S1 += (B1 K) X1 + (B2' K^2) X2 and S2 += (C1 K) X1 + (C2' K^2) X2; points
+    // outside the window (di0 + j = i - i_l) get s = 0 unless it covers the tile
+    f2_t sp[J], sq[J];
     if (full) {
 #pragma unroll
         for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(usq[j])));
@@ -825,55 +890,68 @@ __device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, cons
             sp[j] = f2_splat(di0 + j >= -W && di0 + j <= W ? rcp_approx(f2_lo(usq[j])) : 0.0f);
     }
 #pragma unroll
-    for (int dp = 0; dp < DP; ++dp) {
-        const ulonglong2 q0 = par[kNQB * dp], q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
+    for (int j = 0; j < J; ++j) sq[j] = f2_mul(sp[j], sp[j]);
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const f2_t pp = f2_mul(sp[j], q0.x);
-            const f2_t gp = f2_mul(gv[dp][j], pp);
-            S1 = f2_fma(gp, f2_fma(pp, q1.y, q1.x), S1);
-            S2 = f2_fma(gp, f2_fma(pp, q2.y, q2.x), S2);
+    for (int dp = 0; dp < DP; ++dp) {
+        const ulonglong2 q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
+        f2_t X1 = f2_mul(gv[dp][0], sp[0]), X2 = f2_mul(gv[dp][0], sq[0]);
+#pragma unroll
+        for (int j = 1; j < J; ++j) {
+            X1 = f2_fma(gv[dp][j], sp[j], X1);
+            X2 = f2_fma(gv[dp][j], sq[j], X2);
         }
+        S1 = f2_fma(q1.y, X2, f2_fma(q1.x, X1, S1));
+        S2 = f2_fma(q2.y, X2, f2_fma(q2.x, X1, S2));
     }
 }
 
 // One line's far-wing backward sums over a warp's J x DS cells (depth pairs):
-// S1 += G stim A H, S2 += G stim A a6 dH/da.  Without MASK, w holds the squared
-// offsets u^2; with MASK, w holds the offsets u and kp the depth pairs' k, and only
-// the far cells inside the window (inwin per lambda point) are kept.
+// S1 += G stim A H, S2 += G stim A a6 dH/da.  Without MASK, w holds the scaled squared
+// offsets U = 2^36 u^2; with MASK, w holds the offsets u and kp the depth pairs' k, and
+// only the far cells inside the window (inwin per lambda point) are kept.
 template <int J, int DP, bool MASK>
 __device__ __forceinline__ void far_bwd_line(const ulonglong2 *par, const f2_t (&w)[J], const f2_t (&gv)[DP][J],
                                              const bool *inwin, const f2_t *kp, f2_t &S1, f2_t &S2) {
 #pragma unroll
     for (int dp = 0; dp < DP; ++dp) {
-        // (1/k^2, a^2) (B1, B2') (C1, C2'); the other coefficients from a^2, B1 and C1
+        // (K, a^2) (B1 K, B2' K^2) (C1 K, C2' K^2); the other coefficients from a^2, B1 K and C1 K
         const ulonglong2 q0 = par[kNQB * dp], q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
+        f2_t B1 = q1.x, C1 = q2.x;
+        if (MASK) {
+            // the masked cells use t = 1/|z|^2 itself: B1 = (B1 K) k^2 2^-36, C1 alike
+            const f2_t kk = f2_mul(f2_mul(kp[dp], kp[dp]), f2_splat(kKUnscale));
+            B1 = f2_mul(B1, kk);
+            C1 = f2_mul(C1, kk);
+        }
         f2_t B3, B4, B5, C3, C4, C5, C6;
-        far_b345(q0.y, q1.x, B3, B4, B5);
-        far_c3456(q0.y, q2.x, C3, C4, C5, C6);
-        const f2_t B2 = f2_mul(q1.x, f2_splat(1.5f));
-        const f2_t C2 = f2_mul(f2_fma(q0.y, f2_splat(-2.0f), f2_splat(1.5f)), q2.x);
-        const f2_t ak = f2_mul(q0.y, q0.x);          // a^2/k^2
+        far_b345(q0.y, B1, B3, B4, B5);
+        far_c3456(q0.y, C1, C3, C4, C5, C6);
+        const f2_t B2 = f2_mul(B1, f2_splat(1.5f));
+        const f2_t C2 = f2_mul(f2_fma(q0.y, f2_splat(-2.0f), f2_splat(1.5f)), C1);
+        const f2_t ak = f2_mul(q0.y, q0.x);          // a^2 K
 #pragma unroll
         for (int j = 0; j < J; ++j) {
-            f2_t r2, t;
+            f2_t r2, t, m;
             if (MASK) {
                 const f2_t x = f2_mul(w[j], kp[dp]);
                 r2 = f2_fma(x, x, q0.y);
                 t = f2_rcp(r2);
+                m = t;
             } else {
-                t = f2_mul(q0.x, f2_rcp(f2_fma(w[j], f2_splat(1.0f), ak)));
+                // r = 1/(U + a^2 K), t = K r; the coefficients carry K, so the sums take r
+                m = f2_rcp(f2_fma(w[j], f2_splat(1.0f), ak));
+                t = f2_mul(q0.x, m);
             }
             f2_t h = f2_fma(t, B5, B4);
             h = f2_fma(t, h, B3);
             h = f2_fma(t, h, B2);
-            h = f2_fma(t, h, q1.x);
+            h = f2_fma(t, h, B1);
             f2_t q = f2_fma(t, C6, C5);
             q = f2_fma(t, q, C4);
             q = f2_fma(t, q, C3);
             q = f2_fma(t, q, C2);
-            q = f2_fma(t, q, q2.x);
-            f2_t gt = f2_mul(gv[dp][j], t);
+            q = f2_fma(t, q, C1);
+            f2_t gt = f2_mul(gv[dp][j], m);
             if (MASK) {
                 float r2a, r2b, ga, gb;
                 f2_unpack(r2, r2a, r2b);
@@ -962,10 +1040,11 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
             if (!((m_skip >> (li & 31)) & 1u)) {
                 f2_t u2[J];
                 if (fl != 0) {
-                    const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr);
+                    const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr) * kUScale;
                     u2[0] = f2_splat(u0);
 #pragma unroll
-                    for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j]));
+                    for (int j = 1; j < J; ++j)
+                        u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j] * kUScale));
 #pragma unroll
                     for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
                 } else {
@@ -1045,7 +1124,7 @@ __global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int 
     __shared__ uint64_t bars[2];
     pipe_init(bars);
     ChunkPipe cp{bars, smem4, LC, GW * DS / 2 * kNQB, 0u};
-    for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi) {
+    for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi, int) {
         return far_bwd_item<J, DS>(v, tile, group, lo, hi, GW, cp);
     });
 }
@@ -1232,7 +1311,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) k_line_near_fwd(LineArgs gq) 
     int *s_pref = reinterpret_cast<int *>(s_items + kNearWarps * 32);              // [warps][2][33]
     float *s_daw = reinterpret_cast<float *>(s_pref + kNearWarps * 66);            // Dawson table
     for (int k = threadIdx.x; k < kDawsonNodes * (kDawsonK + 1); k += blockDim.x) s_daw[k] = g_dawson[k];
-    for_each_item(gq, [&](const LineArgs &g, int tile, int group, int nlo, int nhi) {
+    for_each_item(gq, [&](const LineArgs &g, int tile, int group, int nlo, int nhi, int) {
     const int tid = threadIdx.x;
     const int t0 = tile * T;
     const int dbase = group * NDG, ndg = min(NDG, g.nd - dbase);
@@ -1265,7 +1344,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) k_line_near_bwd(LineArgs gq) 
     int *s_pref = reinterpret_cast<int *>(s_items + kNearWarps * 32);              // [warps][2][33]
     float *s_daw = reinterpret_cast<float *>(s_pref + kNearWarps * 66);            // Dawson table
     for (int k = threadIdx.x; k < kDawsonNodes * (kDawsonK + 1); k += blockDim.x) s_daw[k] = g_dawson[k];
-    for_each_item(gq, [&](const LineArgs &g, int tile, int group, int nlo, int nhi) {
+    for_each_item(gq, [&](const LineArgs &g, int tile, int group, int nlo, int nhi, int) {
     const int tid = threadIdx.x;
     const int t0 = tile * T;
     const int dbase = group * NDG, ndg = min(NDG, g.nd - dbase);
@@ -1320,6 +1399,9 @@ static LineArgs make_args(pz_ctx *c) {
         g.rm1j[j] = (float)std::expm1(-j * c->lnr);
     }
     g.star = c->L.star;
+    g.fext = nullptr;
+    g.fpart = c->d_fpart;
+    g.fcnt = c->d_fcnt;
     g.ftab = reinterpret_cast<const float4 *>(c->d_ftab);
     g.finfo = reinterpret_cast<const LineInfo *>(c->d_finfo);
     g.status = c->d_status;
@@ -1467,11 +1549,16 @@ static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
     e = launch_near<32 * J, false>(c, g, s);
     if (e != cudaSuccess || c->n_fitems == 0) return e;
     g.items = c->d_fitems;
+    g.fext = c->d_fext;
     g.n_items = c->n_fitems;
     g.ngroups = (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta();
     g.ctr = c->d_ctr + 1;
     if (c->L.n > 0) {
         e = launch_far_table<kNQF>(c, g, DS, s);
+        if (e != cudaSuccess) return e;
+    }
+    if (c->n_fsplit > 0) {
+        e = cudaMemsetAsync(c->d_fcnt, 0, sizeof(int) * c->n_fsplit, s);
         if (e != cudaSuccess) return e;
     }
     int grid = persistent_grid(c, k_line_fwd<J, DS, MINB>, 32 * t.GW, smem, g.n_items);
@@ -1494,8 +1581,8 @@ static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (c->n_bitems > 0) {
         LineArgs gb = g;
-        gb.items = c->d_fitems;
-        gb.n_items = c->n_bitems;   // the far items with lines come first
+        gb.items = c->d_bitems;
+        gb.n_items = c->n_bitems;
         gb.ngroups = (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta();
         gb.ctr = c->d_ctr + 2;
         e = launch_far_table<kNQB>(c, gb, DS, s);
