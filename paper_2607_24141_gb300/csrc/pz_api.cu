@@ -124,6 +124,7 @@ static void dfree(void *p) {
 //         Backward pieces add their per-line sums atomically like whole items;
 //         forward pieces store compensated partial sums, and the piece that
 //         finishes an item last combines them in piece order (deterministic);
+//         near-core backward items are cut the same way;
 //   near: lines whose centre lies within 20 Doppler widths (the widest of the star)
 //         of the tile plus a margin; forward items for every (star, tile, group of
 //         8 layers) (they write the near-core buffer), backward items of 24 layers
@@ -132,6 +133,8 @@ constexpr double kPiecesPerCta = 8.0;       // target far pieces per resident CT
 constexpr int kMaxPieces = 32;              // pieces of one far item at most
 constexpr int kMinPieceLines = 256;         // lines of a far piece at least
 constexpr size_t kMaxPartBytes = (size_t)512 << 20;   // partial-sum buffer of the split forward items
+constexpr double kNearCtasPerSm = 6.0;      // resident near-core CTAs per SM (estimate for the split)
+constexpr int kMinNearPieceLines = 64;      // lines of a near-core backward piece at least
 
 static pz_status build_items(pz_ctx *c) {
     const int T = c->tiling.lambda_per_tile();
@@ -214,7 +217,23 @@ static pz_status build_items(pz_ctx *c) {
         hf[k] = fp[k].v;
         hx[k] = fp[k].ext;
     }
-    std::vector<int4> hbf = order(bp), hn = order(nf), hb = order(nb);
+    // near-core backward pieces (per-line sums added atomically, as whole items do); the
+    // near kernels hold about kNearCtasPerSm CTAs per SM
+    double totn = 0.0;
+    for (const Item &it : nb) totn += it.cost;
+    const double npiece = std::max(totn / ((double)std::max(c->n_sm, 1) * kNearCtasPerSm * kPiecesPerCta), 1.0);
+    std::vector<Item> nbp;
+    nbp.reserve(nb.size());
+    for (const Item &it : nb) {
+        const int n = it.v.w - it.v.z;
+        int P = (int)std::lround(it.cost / npiece);
+        P = std::max(1, std::min({P, kMaxPieces, n / kMinNearPieceLines}));
+        for (int q = 0; q < P; ++q) {
+            const int lo = it.v.z + (int)((int64_t)n * q / P), hi = it.v.z + (int)((int64_t)n * (q + 1) / P);
+            if (hi > lo) nbp.push_back({make_int4(it.v.x, it.v.y, lo, hi), it.cost / P});
+        }
+    }
+    std::vector<int4> hbf = order(bp), hn = order(nf), hb = order(nbp);
     dfree(c->d_fitems);
     dfree(c->d_fext);
     dfree(c->d_bitems);
