@@ -375,6 +375,15 @@ constexpr float kKUnscale = 1.4551915228366852e-11f;   // 2^-36
 //   X1 = sum_i G_i s_i,  X2 = sum_i G_i s_i^2,
 // and X1, X2 serve both gradients (the C coefficients multiply the same sums).
 constexpr float kFast2V = 5.0f;      // distance threshold factor: |v| >= 5 x 20
+// Three-term reduced form, for the lines between 30 and 100 Doppler widths from the tile:
+// the same expansion one order further,
+//   H sqrt(pi)/A = (B1 K) s + (B2' K^2) s^2 + (B3' K^3) s^3,  B3' = B1 (3.75 - 5a^2 + a^4),
+//   dH/da sqrt(pi)/(A a6) = (C1 K) s + (C2' K^2) s^2 + (C3' K^3) s^3,  C3' = C1 (3.75 - 15a^2 + 5a^4),
+// (the t^3 terms of the far polynomial and the p^3 terms of t and t^2 in p).  Against the
+// five-term polynomial the dropped p^4 terms stay below 2.6e-8 relative for H and 4.6e-8 for
+// dH/da at |v| >= 30 and a^2 <= 1.5 (evaluated on a dense (a^2, v) lattice).  B3' K^3 and
+// C3' K^3 are formed per depth pair from K, a^2, B1 K and C1 K.
+constexpr float kFast3V = 1.5f;      // distance threshold factor: |v| >= 1.5 x 20
 constexpr float kFast2A2 = 1.5f;     // a^2 bound
 
 // One thread per (group, line, depth pair); the thread of pair 0 also writes the
@@ -524,7 +533,8 @@ __device__ __forceinline__ void far_abort(const LineArgs &g, const ChunkPipe &cp
 // and every cell of the warp's slab is in the far wing (|v| >= 20); bit 1 if every
 // cell of the slab has |v| >= 100 and a^2 <= kFast2A2 at every layer (reduced form),
 // whether or not the window covers the tile: the reduced form masks the window per
-// point at no cost per cell (a zero reciprocal s = 1/U).
+// point at no cost per cell (a zero reciprocal s = 1/U); bit 3 if instead every cell
+// has |v| >= 30 with the same a^2 bound (three-term reduced form).
 __device__ __forceinline__ int far_flags(const LineArgs &g, const LineInfo &info, float t0f, float tendf, int slab,
                                          int w) {
     const float dlo = info.ilf - t0f + info.frac;      // x_l - t0
@@ -534,8 +544,10 @@ __device__ __forceinline__ int far_flags(const LineArgs &g, const LineInfo &info
     if ((info.amask >> (8 + w)) & 1) return 4;        // the centre test rejects the whole slab
     const float thr = __ldg(g.thr + info.sp * g.nslab + slab);
     const bool fast = full && dmin >= thr;
-    const bool red = dmin >= kFast2V * thr && ((info.amask >> w) & 1);
-    return (fast ? 1 : 0) | (red ? 2 : 0);
+    const bool amask = (info.amask >> w) & 1;
+    const bool red = dmin >= kFast2V * thr && amask;
+    const bool red3 = !red && dmin >= kFast3V * thr && amask;
+    return (fast ? 1 : 0) | (red ? 2 : 0) | (red3 ? 8 : 0);
 }
 
 // k = c/dv_D of the warp's depth pairs, rounded exactly as depth_params forms it, for the
@@ -628,17 +640,19 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
         const int nl = min(cp.LC, hi - (lo + c * cp.LC));
         const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
         const LineInfo *s_line = cp.info(k);
-        unsigned m_fast = 0u, m_red = 0u, m_skip = 0u;   // this warp's flags of 32 lines, one line per lane
+        unsigned m_fast = 0u, m_red = 0u, m_red3 = 0u, m_skip = 0u;   // this warp's flags of 32 lines, one per lane
         for (int li = 0; li < nl; ++li) {
             if ((li & 31) == 0) {
                 const int lj = li + lane;
                 const int f = lj < nl ? far_flags(g, s_line[lj], t0f, tendf, slab, warp) : 0;
                 m_fast = __ballot_sync(0xffffffffu, f & 1);
                 m_red = __ballot_sync(0xffffffffu, (f & 2) != 0);
+                m_red3 = __ballot_sync(0xffffffffu, (f & 8) != 0);
                 m_skip = __ballot_sync(0xffffffffu, (f & 4) != 0);
             }
             const LineInfo info = s_line[li];
-            const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1);
+            const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1) |
+                           (int)(((m_red3 >> (li & 31)) & 1u) << 2);
             if ((m_skip >> (li & 31)) & 1u) continue;        // every layer rejected by the centre test
             const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
             f2_t u2[J];
@@ -657,9 +671,9 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
 #pragma unroll
                 for (int j = 0; j < J; ++j) u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
             }
-            if (fl & 2) {
-                // reduced form (B1 K) s + (B2' K^2) s^2 with s = 1/U; points outside the
-                // window (lines whose window edge crosses the tile) get s = 0
+            if (fl & 6) {
+                // reduced forms (B1 K) s + (B2' K^2) s^2 [+ (B3' K^3) s^3] with s = 1/U; points
+                // outside the window (lines whose window edge crosses the tile) get s = 0
                 f2_t sp[J], sq[J];
                 if (fl & 1) {
 #pragma unroll
@@ -674,12 +688,30 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                 }
 #pragma unroll
                 for (int j = 0; j < J; ++j) sq[j] = f2_mul(sp[j], sp[j]);
+                if (fl & 2) {
 #pragma unroll
-                for (int dp = 0; dp < DP; ++dp) {
-                    // q1 = (B1 K, B2' K^2)
-                    const ulonglong2 q1 = par[NQ * dp + 1];
+                    for (int dp = 0; dp < DP; ++dp) {
+                        // q1 = (B1 K, B2' K^2)
+                        const ulonglong2 q1 = par[NQ * dp + 1];
 #pragma unroll
-                    for (int j = 0; j < J; ++j) acc[dp][j] = f2_fma(sq[j], q1.y, f2_fma(sp[j], q1.x, acc[dp][j]));
+                        for (int j = 0; j < J; ++j)
+                            acc[dp][j] = f2_fma(sq[j], q1.y, f2_fma(sp[j], q1.x, acc[dp][j]));
+                    }
+                } else {
+                    f2_t sc[J];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) sc[j] = f2_mul(sq[j], sp[j]);
+#pragma unroll
+                    for (int dp = 0; dp < DP; ++dp) {
+                        // q0 = (K, a^2), q1 = (B1 K, B2' K^2); B3' K^3 = (B1 K) K^2 (3.75 - 5a^2 + a^4)
+                        const ulonglong2 q0 = par[NQ * dp], q1 = par[NQ * dp + 1];
+                        const f2_t b3 = f2_mul(f2_mul(q1.x, f2_mul(q0.x, q0.x)),
+                                               f2_fma(q0.y, f2_fma(q0.y, f2_splat(1.0f), f2_splat(-5.0f)),
+                                                      f2_splat(3.75f)));
+#pragma unroll
+                        for (int j = 0; j < J; ++j)
+                            acc[dp][j] = f2_fma(sc[j], b3, f2_fma(sq[j], q1.y, f2_fma(sp[j], q1.x, acc[dp][j])));
+                    }
                 }
             } else if (fl & 1) {
 #pragma unroll
@@ -870,16 +902,17 @@ __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int 
     });
 }
 
-// Reduced far-wing backward form (lines flagged for it): H and dH/da polynomials cut
-// after their t^2 terms.  par: the warp's depth pairs, (K, a^2) (B1 K, B2' K^2)
+// Reduced far-wing backward forms (lines flagged for them): H and dH/da polynomials cut
+// after their t^2 terms (THREE: t^3).  par: the warp's depth pairs, (K, a^2) (B1 K, B2' K^2)
 // (C1 K, C2' K^2); usq: the scaled squared offsets U = 2^36 u^2 of the thread's points.
-template <int J, int DP>
+template <int J, int DP, bool THREE>
 __device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, const f2_t (&usq)[J],
                                                      const f2_t (&gv)[DP][J], bool full, int di0, int W, f2_t &S1,
                                                      f2_t &S2) {
     // reduced forms with s = 1/U: per depth pair X1 = sum_j G s_j and X2 = sum_j G s_j^2,
-    // then S1 += (B1 K) X1 + (B2' K^2) X2 and S2 += (C1 K) X1 + (C2' K^2) X2; points
-    // outside the window (di0 + j = i - i_l) get s = 0 unless it covers the tile
+    // then S1 += (B1 K) X1 + (B2' K^2) X2 and S2 += (C1 K) X1 + (C2' K^2) X2 (THREE: also
+    // X3 = sum_j G s_j^3 with B3' K^3 and C3' K^3); points outside the window
+    // (di0 + j = i - i_l) get s = 0 unless it covers the tile
     f2_t sp[J], sq[J];
     if (full) {
 #pragma unroll
@@ -891,17 +924,42 @@ __device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, cons
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) sq[j] = f2_mul(sp[j], sp[j]);
+    if (THREE) {
+        f2_t sc[J];
 #pragma unroll
-    for (int dp = 0; dp < DP; ++dp) {
-        const ulonglong2 q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
-        f2_t X1 = f2_mul(gv[dp][0], sp[0]), X2 = f2_mul(gv[dp][0], sq[0]);
+        for (int j = 0; j < J; ++j) sc[j] = f2_mul(sq[j], sp[j]);
 #pragma unroll
-        for (int j = 1; j < J; ++j) {
-            X1 = f2_fma(gv[dp][j], sp[j], X1);
-            X2 = f2_fma(gv[dp][j], sq[j], X2);
+        for (int dp = 0; dp < DP; ++dp) {
+            const ulonglong2 q0 = par[kNQB * dp], q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
+            f2_t X1 = f2_mul(gv[dp][0], sp[0]), X2 = f2_mul(gv[dp][0], sq[0]), X3 = f2_mul(gv[dp][0], sc[0]);
+#pragma unroll
+            for (int j = 1; j < J; ++j) {
+                X1 = f2_fma(gv[dp][j], sp[j], X1);
+                X2 = f2_fma(gv[dp][j], sq[j], X2);
+                X3 = f2_fma(gv[dp][j], sc[j], X3);
+            }
+            // B3' K^3 = (B1 K) K^2 (3.75 - 5a^2 + a^4), C3' K^3 = (C1 K) K^2 (3.75 - 15a^2 + 5a^4)
+            const f2_t K2 = f2_mul(q0.x, q0.x);
+            const f2_t b3 = f2_mul(f2_mul(q1.x, K2),
+                                   f2_fma(q0.y, f2_fma(q0.y, f2_splat(1.0f), f2_splat(-5.0f)), f2_splat(3.75f)));
+            const f2_t c3 = f2_mul(f2_mul(q2.x, K2),
+                                   f2_fma(q0.y, f2_fma(q0.y, f2_splat(5.0f), f2_splat(-15.0f)), f2_splat(3.75f)));
+            S1 = f2_fma(b3, X3, f2_fma(q1.y, X2, f2_fma(q1.x, X1, S1)));
+            S2 = f2_fma(c3, X3, f2_fma(q2.y, X2, f2_fma(q2.x, X1, S2)));
         }
-        S1 = f2_fma(q1.y, X2, f2_fma(q1.x, X1, S1));
-        S2 = f2_fma(q2.y, X2, f2_fma(q2.x, X1, S2));
+    } else {
+#pragma unroll
+        for (int dp = 0; dp < DP; ++dp) {
+            const ulonglong2 q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
+            f2_t X1 = f2_mul(gv[dp][0], sp[0]), X2 = f2_mul(gv[dp][0], sq[0]);
+#pragma unroll
+            for (int j = 1; j < J; ++j) {
+                X1 = f2_fma(gv[dp][j], sp[j], X1);
+                X2 = f2_fma(gv[dp][j], sq[j], X2);
+            }
+            S1 = f2_fma(q1.y, X2, f2_fma(q1.x, X1, S1));
+            S2 = f2_fma(q2.y, X2, f2_fma(q2.x, X1, S2));
+        }
     }
 }
 
@@ -1022,17 +1080,19 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
         const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
         const LineInfo *s_line = cp.info(k);
         float h1 = 0.0f, h2 = 0.0f;   // lane sums of the held even line
-        unsigned m_fast = 0u, m_red = 0u, m_skip = 0u;   // this warp's flags of 32 lines, one line per lane
+        unsigned m_fast = 0u, m_red = 0u, m_red3 = 0u, m_skip = 0u;   // this warp's flags of 32 lines, one per lane
         for (int li = 0; li < nl; ++li) {
             if ((li & 31) == 0) {
                 const int lj = li + lane;
                 const int f = lj < nl ? far_flags(g, s_line[lj], t0f, tendf, slab, warp) : 0;
                 m_fast = __ballot_sync(0xffffffffu, f & 1);
                 m_red = __ballot_sync(0xffffffffu, (f & 2) != 0);
+                m_red3 = __ballot_sync(0xffffffffu, (f & 8) != 0);
                 m_skip = __ballot_sync(0xffffffffu, (f & 4) != 0);
             }
             const LineInfo info = s_line[li];
-            const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1);
+            const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1) |
+                           (int)(((m_red3 >> (li & 31)) & 1u) << 2);
             const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
             f2_t S1 = 0ull, S2 = 0ull;
             // (a slab whose every layer the centre test rejects keeps zero sums; it still takes
@@ -1053,7 +1113,11 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
                         u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
                 }
                 if (fl & 2) {
-                    far_bwd_line_reduced<J, DP>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W, S1, S2);
+                    far_bwd_line_reduced<J, DP, false>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W, S1,
+                                                       S2);
+                } else if (fl & 4) {
+                    far_bwd_line_reduced<J, DP, true>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W, S1,
+                                                      S2);
                 } else if (fl & 1) {
                     far_bwd_line<J, DP, false>(par, u2, gv, nullptr, nullptr, S1, S2);
                 } else {
