@@ -37,9 +37,9 @@ WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts
             "chi^2 vs synthetic target, gradients for 2e5 dlog_gf + 2e5 dlog_gamma6 + 20 abundances")
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# kernel on this workload (profiles/k_line_bwd_apogee.md: 6.479 GB read + 86.0 MB written, default
+# kernel on this workload (profiles/k_line_bwd_apogee.md: 5.012 GB read + 46.1 MB written, default
 # tiling), valid only while the kernel sources hash to the recorded value; otherwise null.
-TRAFFIC = {"k_line_bwd": (6.5242e+09, "cdbac6aea8dcfe66")}
+TRAFFIC = {"k_line_bwd": (5.0582e+09, "46f6e4e57593924c")}
 KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h")
 FMA_PER_EN = 39      # FP64 FMAs of one E_2/E_3/E_4 Taylor step (13 rounds of value + two derivatives)
 
