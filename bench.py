@@ -40,6 +40,12 @@ WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts
 # kernel on this workload (profiles/k_line_bwd_apogee.md: 5.012 GB read + 46.1 MB written, default
 # tiling), valid only while the kernel sources hash to the recorded value; otherwise null.
 TRAFFIC = {"k_line_bwd": (5.0582e+09, "46f6e4e57593924c")}
+# Pipe counters of the same capture (fractions of peak over the kernel's active cycles), beside
+# the algorithmic fraction, which counts only the two-term reduced form's operations and so is
+# a lower bound; same validity rule.
+NCU_PIPES = {"k_line_bwd": ({"fma_pipe_cycles_active": 0.5007, "issue_slots_busy": 0.6192,
+                             "warps_active": 0.2435, "thread_instructions_per_eval": 8.52},
+                            "46f6e4e57593924c")}
 KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h")
 FMA_PER_EN = 39      # FP64 FMAs of one E_2/E_3/E_4 Taylor step (13 rounds of value + two derivatives)
 
@@ -988,12 +994,15 @@ def main():
         h.update(open(os.path.join(ROOT, "paper_2607_24141_gb300", "csrc", name), "rb").read())
     kname = "k_line_bwd" if dom == "line_bwd" else "k_line_fwd"
     traffic = None
+    ncu_pipes = None
     if kname in TRAFFIC and TRAFFIC[kname][1] == h.hexdigest()[:16]:
         traffic = TRAFFIC[kname][0]
+    if kname in NCU_PIPES and NCU_PIPES[kname][1] == h.hexdigest()[:16]:
+        ncu_pipes = NCU_PIPES[kname][0]
     roofline = {
         "bound": "alu", "kernel": kname + " (far wing)", "pipe": "fp32",
         "achieved": achieved * 1e-9, "peak": peak_fp32 * 1e-9, "unit": "Gop/s",
-        "frac": achieved / peak_fp32, "traffic": traffic,
+        "frac": achieved / peak_fp32, "traffic": traffic, "ncu_pipes": ncu_pipes,
         "peak_source": ("measured: pz_probe_pipe packed-FMA throughput (%d SMs); 128-lane derivation %.0f Gop/s"
                         % (n_sm, peak_fp32_lanes * 1e-9)) if pipe_peaks.get("fp32") else
                        "derived: %d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (n_sm, clk_max),
