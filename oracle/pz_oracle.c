@@ -23,15 +23,16 @@
  *   adjoint         Sec. 6: reverse pass from the pixel loss to per-line
  *                   Delta log gf, Delta log gamma_6 and abundances (Eq. 10)
  *
- * Readings where the paper is silent (units, window rule, boundary treatment)
- * are the ones listed in the project's design notes; each is restated where
- * it is used below.
+ * Where the paper is silent (units, window rule, boundary treatment) the
+ * reading taken is stated where it is used below.
  *
  * Voigt function: H(a,v) = Re w(v + i a), w the Faddeeva function.
  *   |z| <  7 : H, L = Im w and dH/da from the Fourier representation
  *              H + iL = pi^-1/2 Int_0^inf exp(-a t - t^2/4) exp(i v t) dt,
  *              by composite Gauss-Legendre quadrature (12 panels x 16 nodes
- *              on [0, 12.5]; the integrand there is below 1e-16 of its peak).
+ *              on [0, 12.5]; the integrand there is below 1e-16 of its peak);
+ *              for H the a = 0 term, pi^-1/2 Int exp(-t^2/4) cos(v t) dt =
+ *              exp(-v^2), is taken in closed form and only the rest is summed.
  *   |z| >= 7 : the Laplace continued fraction
  *              w(z) = (i/sqrt(pi)) / (z - (1/2)/(z - (2/2)/(z - (3/2)/(z - ...)))),
  *              evaluated bottom-up, and dH/da = 2 (v L + a H) - 2/sqrt(pi)
@@ -111,17 +112,22 @@ void pzo_voigt(double a, double v, double *H, double *L, double *dHda) {
     double x = fabs(v);
     double sgn = v < 0.0 ? -1.0 : 1.0;
     if (x * x + a * a < 49.0) {
+        /* The a = 0 part of the real integral is exp(-v^2) in closed form; only
+         * the remainder, with (exp(-a t) - 1) in place of exp(-a t), goes through
+         * the quadrature.  Its terms are O(a), so a small H near |z| = 7 is no
+         * longer the difference of O(1) terms. */
         double sh = 0.0, sl = 0.0, sd = 0.0;
         for (int k = 0; k < GL_N * GL_PANELS; ++k) {
             double t = fq_t[k];
-            double e = fq_w[k] * fq_g[k] * exp(-a * t);
+            double g = fq_w[k] * fq_g[k];
+            double e = g * exp(-a * t);
             double s, c;
             sincos(x * t, &s, &c);
-            sh += e * c;
+            sh += g * expm1(-a * t) * c;
             sl += e * s;
             sd -= t * e * c;
         }
-        *H = sh / O_SQRTPI;
+        *H = exp(-x * x) + sh / O_SQRTPI;
         if (L) *L = sgn * sl / O_SQRTPI;
         if (dHda) *dHda = sd / O_SQRTPI;
         return;

@@ -19,10 +19,34 @@ def test_voigt_matches_faddeeva_lattice(oracle):
     H, L, dH = oracle.voigt(a, v)
     w = wofz(v + 1j * a)
     core = v * v + a * a < 49
-    # Fourier quadrature region: relative error limited by FP64 rounding of O(1) integrands
-    assert np.max(np.abs(H[core] / w.real[core] - 1)) < 2e-8
+    # both regions (Fourier quadrature inside |z| = 7, continued fraction outside)
+    assert np.max(np.abs(H[core] / w.real[core] - 1)) < 1e-12
     assert np.max(np.abs(H[~core] / w.real[~core] - 1)) < 1e-12
     assert np.max(np.abs(L - w.imag) / np.abs(w.imag).clip(1e-300)) < 1e-10
+
+
+def test_voigt_matches_high_precision_faddeeva():
+    """Against w(z) = exp(-z^2) erfc(-iz) in 40-digit arithmetic (mpmath), on the
+    lattice points nearest the |z| = 7 seam and the smallest damping, where a small
+    H is the sum of an O(1) Gaussian and an O(a) damping term."""
+    mpmath = pytest.importorskip("mpmath")
+    from oracle import oracle as o
+    o.build()
+    a = np.array([1e-5, 1e-4, 1e-3, 1e-2, 0.1, 1.0, 3.0])
+    v = np.array([0.0, 0.5, 2.0, 4.0, 5.5, 6.5, 6.9, 6.999, 7.001, 7.5, 12.0, 60.0])
+    A, V = (x.ravel() for x in np.meshgrid(a, v, indexing="ij"))
+    H, L, dH = o.voigt(A, V)
+    mpmath.mp.dps = 40
+    ref_w = [mpmath.exp(-z * z) * mpmath.erfc(-1j * z) for z in (mpmath.mpc(x, y) for x, y in zip(V, A))]
+    ref_H = np.array([float(mpmath.re(w)) for w in ref_w])
+    ref_L = np.array([float(mpmath.im(w)) for w in ref_w])
+    # dH/da = Re(i w'(z)) with w' = -2 z w + 2i/sqrt(pi)
+    ref_dH = np.array([float(mpmath.re(1j * (-2 * mpmath.mpc(x, y) * w + 2j / mpmath.sqrt(mpmath.pi))))
+                       for x, y, w in zip(V, A, ref_w)])
+    assert np.max(np.abs(H / ref_H - 1)) < 1e-13
+    nz = np.abs(ref_L) > 0
+    assert np.max(np.abs(L[nz] / ref_L[nz] - 1)) < 1e-12
+    assert np.max(np.abs(dH - ref_dH) / np.abs(ref_dH)) < 1e-11
 
 
 def test_voigt_negative_v_symmetry(oracle):
