@@ -1,23 +1,29 @@
 #!/usr/bin/env python
-"""Benchmark of the synthesis hot path on the APOGEE-like workload.
+"""Benchmark of the synthesis hot path; the headline is the 64-star batched fwd+bwd.
 
-Workload: 1500-1700 nm at R_grid = 300,000 (37,550 points), 2e5 Voigt lines
-over 40 species (one third in molecule-like bands), 72 depths, W = 1,500,
-Doppler shift 12.3 km/s, Gaussian LSF R = 22,500 onto 8,575 pixels.
+Headline workload: 64 stars (Teff ~ U[3500, 7000] K, log g ~ U[1, 5], [M/H] ~
+U[-2, 0.5]), each with its own 72-layer atmosphere and its strongest N_k (2e4-3e5)
+lines of a 3e5-line master list, on 1500-1700 nm at R_grid = 300,000 (37,550
+points), W = 1,500, Doppler shift 12.3 km/s, Gaussian LSF R = 22,500 onto 8,575
+pixels per star.  One step = one pz_calib_step CUDA-graph launch over all stars:
+corrections -> line opacity -> tau + flux (total and continuum) -> instrument +
+normalisation -> chi^2 against synthetic targets -> reverse pass to per-line
+Delta log gf, Delta log gamma6 and 20 abundances -> gradient update.
+The metric counts (line, lambda, depth) Voigt evaluations of the forward window
+sum per step; value = evaluations of all ranks / max rank time.
 
-One step = one pass of the whole hot path for one spectrum:
-  corrections -> line opacity -> tau + flux (total and continuum) ->
-  instrument + normalisation -> chi^2 against a synthetic target ->
-  reverse pass to per-line Delta log gf, Delta log gamma6 and 20 abundances.
-The metric counts (line, lambda, depth) Voigt evaluations of the forward
-window sum per spectrum; value = evaluations of all ranks / max rank time.
+Beside it, near the front of the JSON line: the single-star APOGEE-like step
+("config1"), the 300-1000 nm forward ("config2"), the calibration workload against
+the oracle's stored full-size adjoint ("config3"), and the parity of the batch
+against the oracle's stored star results ("parity").
 
-``--impl reference`` times the FP64 CPU oracle (forward + adjoint) on a
-bounded slice of the same recipe on the host cores instead.
+``--impl reference`` times the FP64 CPU oracle (forward + adjoint) on a bounded
+slice of the same recipe on the host cores instead.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -32,26 +38,26 @@ sys.path.insert(0, ROOT)
 
 METRIC = "s per spectrum & line-pt-depth evals/s (fwd, fwd+bwd) vs FP64 GPU form, % roofline"
 UNIT = "line-pt-depth evals/s"
-WORKLOAD = ("APOGEE-like window, fwd+bwd: 1500-1700 nm at R_grid=3e5 (37,550 pts) x 2e5 Voigt lines "
-            "(40 species, 1/3 in bands) x 72 depths, W=1,500, v_r=12.3 km/s, LSF R=22,500 -> 8,575 px, "
-            "chi^2 vs synthetic target, gradients for 2e5 dlog_gf + 2e5 dlog_gamma6 + 20 abundances")
+WORKLOAD = ("64-star batched fwd+bwd: 64 stars (Teff U[3500,7000] K, log g U[1,5], [M/H] U[-2,0.5]), each its "
+            "own 72-layer atmosphere and top-N_k (2e4-3e5) lines of a 3e5-line master list, 1500-1700 nm at "
+            "R_grid=3e5 (37,550 pts), W=1,500, v_r=12.3 km/s, LSF R=22,500 -> 8,575 px per star; one step = one "
+            "pz_calib_step graph launch (corrections, fwd, chi^2, bwd to 3e5 dlog_gf + 3e5 dlog_gamma6 + 20 "
+            "abundances, update)")
+GOLDEN = os.path.join(ROOT, "tests", "golden")
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the
-# kernel on this workload (profiles/k_line_bwd_apogee.md: 5.012 GB read + 46.1 MB written, default
-# tiling), valid only while the kernel sources hash to the recorded value; otherwise null.
-TRAFFIC = {"k_line_bwd": (5.0582e+09, "46f6e4e57593924c")}
-# Pipe counters of the same capture (fractions of peak over the kernel's active cycles), beside
-# the algorithmic fraction, which counts only the two-term reduced form's operations and so is
-# a lower bound; same validity rule.
-NCU_PIPES = {"k_line_bwd": ({"fma_pipe_cycles_active": 0.5007, "issue_slots_busy": 0.6192,
-                             "warps_active": 0.2435, "thread_instructions_per_eval": 8.52},
-                            "46f6e4e57593924c")}
-KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h")
+# Per-launch DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and pipe counters of
+# the dominant kernel, from one ncu capture per (kernel, workload) written up under profiles/;
+# each entry is valid only while the library sources hash to the recorded value, and is
+# reported as null otherwise.
+TRAFFIC = {}
+NCU_PIPES = {}
+KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h", "pz_api.cu")
 FMA_PER_EN = 39      # FP64 FMAs of one E_2/E_3/E_4 Taylor step (13 rounds of value + two derivatives)
 
+
 # Per-evaluation pipe work of the far-wing kernels, which evaluate every in-window cell.
-# Reduced form (lines >= 100 Doppler widths from the whole tile, most cells of this
-# workload), with s = 1/U shared by the depths of a warp and the table's coefficients
+# Reduced form (lines >= 100 Doppler widths from the whole tile, most cells of these
+# workloads), with s = 1/U shared by the depths of a warp and the table's coefficients
 # (B1 K, B2' K^2, C1 K, C2' K^2): forward 2 FP32-pipe lane operations per cell (two
 # products accumulated); backward, per depth and thread, X1 = sum_j G s_j and
 # X2 = sum_j G s_j^2 over the thread's J points (2 per cell) and four products into
@@ -63,29 +69,28 @@ def far_ops(J):
             "line_bwd": {"fp32_reduced": 2 + 4.0 / J, "fp32_full": 13, "mufu_reduced": 1.0 / 6, "mufu_full": 1}}
 
 
-OPS = far_ops(4)
-
-
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--fp64-steps", type=int, default=1)
+    ap.add_argument("--batch-stars", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=4)
+    ap.add_argument("--config1-steps", type=int, default=20)
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-batch", action="store_true", help="skip the batched many-star measurement")
-    ap.add_argument("--batch-stars", type=int, default=64)
-    ap.add_argument("--batch-steps", type=int, default=3)
+    ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default line-kernel tiling")
     ap.add_argument("--no-broad", action="store_true", help="skip the 300-1000 nm forward measurement")
     ap.add_argument("--broad-steps", type=int, default=3)
+    ap.add_argument("--no-config3", action="store_true", help="skip the calibration workload's oracle parity")
     ap.add_argument("--no-scatter", action="store_true",
                     help="skip the scattering measurements (300-1000 nm forward, APOGEE-like fwd+bwd)")
     ap.add_argument("--no-centre", action="store_true", help="skip the centre-test measurement")
     ap.add_argument("--no-lbfgs", action="store_true", help="skip the L-BFGS calibration measurement")
+    ap.add_argument("--lbfgs-runs", type=int, default=3)
     ap.add_argument("--scaling", action="store_true", help="run the R_grid and span scaling sweeps (about a minute)")
     ap.add_argument("--scaling-reps", type=int, default=3)
     ap.add_argument("--lbfgs-updates", type=int, default=40)
@@ -123,6 +128,107 @@ def make_collectives(ws, device):
 def aggregate_value(units_per_rank, ws, steps, ms_max):
     """Whole-job throughput: the units every rank processed / the slowest rank's time."""
     return ws * units_per_rank * steps / (ms_max * 1e-3)
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2607_24141_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def golden(name):
+    """Stored oracle results under tests/golden/ (written by the scripts there), or None."""
+    path = os.path.join(GOLDEN, name + "_oracle.npz")
+    if not os.path.exists(path):
+        return None
+    import numpy as np
+    return dict(np.load(path))
+
+
+def diff_stats(d):
+    """max, p99 and rms of |d|."""
+    import numpy as np
+    a = np.abs(np.asarray(d, np.float64)).ravel()
+    if a.size == 0:
+        return {"max": None, "p99": None, "rms": None, "n": 0}
+    return {"max": float(a.max()), "p99": float(np.quantile(a, 0.99)), "rms": float(np.sqrt(np.mean(a * a))),
+            "n": int(a.size)}
+
+
+def grad_rel(g, ref):
+    """Gradient error metric |g - ref| / max(|ref|, 1e-3 max|ref|), elementwise."""
+    import numpy as np
+    g, ref = np.asarray(g, np.float64), np.asarray(ref, np.float64)
+    if ref.size == 0:
+        return np.zeros(0)
+    floor = 1e-3 * np.max(np.abs(ref))
+    return np.abs(g - ref) / np.maximum(np.abs(ref), floor)
+
+
+def line_roofline(kt, evals, J, pipe_peaks, n_sm, clk_max, workload_key):
+    """Roofline of the dominant far-wing line kernel from the profiler's kernel times
+    {family: (ms, launches)}: achieved FP32-pipe lane operations per second at the
+    two-term reduced form's count (a lower bound of the work) against the measured
+    FP32 pipe peak."""
+    far = {"line_fwd": kt["line_fwd"][0] - kt["near_fwd"][0], "line_bwd": kt["line_bwd"][0] - kt["near_bwd"][0]}
+    dom = max(far, key=far.get)
+    t_dom = far[dom] * 1e-3 / max(kt[dom][1], 1)
+    ops = far_ops(J)[dom]
+    peak_fp32_lanes = n_sm * 128 * clk_max * 1e6
+    peak_mufu = pipe_peaks.get("mufu") or n_sm * 16 * clk_max * 1e6
+    peak_fp32 = pipe_peaks.get("fp32") or peak_fp32_lanes
+    achieved = evals * ops["fp32_reduced"] / t_dom
+    kname = "k_line_bwd" if dom == "line_bwd" else "k_line_fwd"
+    hsh = source_hash()
+    tr = TRAFFIC.get((kname, workload_key))
+    np_ = NCU_PIPES.get((kname, workload_key))
+    share = {k: v[0] for k, v in kt.items() if k not in ("near_fwd", "near_bwd", "step")}
+    tot = sum(share.values())
+    return {
+        "bound": "alu", "kernel": kname + " (far wing)", "pipe": "fp32",
+        "achieved": achieved * 1e-9, "peak": peak_fp32 * 1e-9, "unit": "Gop/s", "frac": achieved / peak_fp32,
+        "traffic": tr[0] if tr and tr[1] == hsh else None,
+        "ncu_pipes": np_[0] if np_ and np_[1] == hsh else None,
+        "peak_source": ("measured: pz_probe_pipe packed-FMA throughput (%d SMs); 128-lane derivation %.0f Gop/s"
+                        % (n_sm, peak_fp32_lanes * 1e-9)) if pipe_peaks.get("fp32") else
+                       "derived: %d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (n_sm, clk_max),
+        "evals_per_launch": evals, "ms_per_launch": t_dom * 1e3, "evals_per_s": evals / t_dom,
+        "ops_per_eval": ops,
+        "fp32_pipe_frac_full_form": evals * ops["fp32_full"] / t_dom / peak_fp32,
+        "mufu_pipe_frac_reduced_form": evals * ops["mufu_reduced"] / t_dom / peak_mufu,
+        "kernel_share": {k: round(v / tot, 4) for k, v in share.items() if tot > 0},
+        "far_ms_per_launch": {k: v / max(kt[k][1], 1) for k, v in far.items()},
+        "near_ms_per_launch": {k: kt[k][0] / max(kt[k][1], 1) for k in ("near_fwd", "near_bwd")},
+        "source_hash": hsh,
+    }
+
+
+# ---------------------------------------------------------------------------
+# helpers shared by the workloads
+# ---------------------------------------------------------------------------
+_CACHE = {}
+
+
+def cached(name, make):
+    """Seeded inputs generated once per process (several measurements share them)."""
+    if name not in _CACHE:
+        _CACHE[name] = make()
+    return _CACHE[name]
+
+
+def run_summary(runs):
+    """Wall time of repeated optimiser loops: every run, the median and the spread
+    (max - min) / median, with the time the loop spent waiting on its evaluations
+    (graph launch to loss readback) and the rest (the optimiser's host-side work)."""
+    secs = [r["seconds"] for r in runs]
+    med = statistics.median(secs)
+    last = runs[-1]
+    return {"updates": last["updates"], "evaluations": last["evals"], "seconds_runs": secs, "seconds": med,
+            "spread": (max(secs) - min(secs)) / med if med > 0 else None,
+            "s_per_update": med / max(last["updates"], 1),
+            "eval_seconds_runs": [r.get("eval_seconds") for r in runs],
+            "optimizer_seconds_runs": [r["seconds"] - r["eval_seconds"] for r in runs if "eval_seconds" in r]}
 
 
 # ---------------------------------------------------------------------------
@@ -244,89 +350,6 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
-# batched many-star workload: one CUDA-graph launch per calibration step
-# ---------------------------------------------------------------------------
-def run_batched(args, dev, barrier, max_over_ranks, ws, tiling=None):
-    """64 stars (seeded Teff, log g, [M/H]) on the APOGEE-like grid and instrument, each
-    with its own top-N_k subset (2e4-3e5) of a 3e5-line master list; one step =
-    pz_calib_step (corrections, fwd, chi^2, bwd, update) replayed as one graph launch.
-    Plus the joint two-star (solar-like + giant-like) step on 1e5 shared lines.
-    tiling: the line-kernel tiling tuned on the single-star workload (same grid and
-    line density), applied to both contexts."""
-    import numpy as np
-    import torch
-
-    import paper_2607_24141_gb300 as pz
-    from paper_2607_24141_gb300 import inputs as I
-    stream = torch.cuda.current_stream()
-
-    def measure(batch, truth_gf, truth_g6, noise, steps, warmup):
-        t0 = time.perf_counter()
-        s = pz.Synthesizer(batch, pz.PZ_MIXED, device=dev.index)
-        t_create = time.perf_counter() - t0
-        if tiling is not None:
-            pz.pz_set_tiling(s.ctx, *tiling)
-        S, n_out, nl = batch.n_stars, s.n_out, batch.lines.n_lines
-        s.set_corrections(truth_gf, truth_g6, None)
-        f_true = s.forward()
-        y = (f_true + torch.tensor(noise, dtype=torch.float32, device=dev)).contiguous()
-        w = torch.full_like(y, 200.0 ** 2)
-        s.set_corrections(None, None, np.zeros(batch.n_elem, np.float32))
-        s.forward()
-        loss = torch.zeros(1, dtype=torch.float64, device=dev)
-        g_gf = torch.empty(nl, dtype=torch.float32, device=dev)
-        g_g6 = torch.empty(nl, dtype=torch.float32, device=dev)
-        g_ab = torch.empty(batch.n_elem, dtype=torch.float32, device=dev)
-        s.calib_step(y, w, 0.0, 0.0, 0.0, loss, g_gf, g_g6, g_ab)
-        torch.cuda.synchronize()
-        L0 = loss.item()
-        gn, gmax = float(g_gf.double().norm().item()), float(g_gf.abs().max().item())
-        # plain gradient step: linear model lowers L by 5%, at most 0.01 dex per correction
-        lr = float(min(0.05 * L0 / max(gn * gn, 1e-300), 0.01 / max(gmax, 1e-300)))
-        for _ in range(warmup):
-            s.calib_step(y, w, lr, 0.0, 0.0, loss, g_gf, g_g6, g_ab)
-        barrier()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(steps):
-            s.calib_step(y, w, lr, 0.0, 0.0, loss, g_gf, g_g6, g_ab)
-        b.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-        ms = max_over_ranks(a.elapsed_time(b)) / steps
-        L1 = loss.item()
-        kernels = pz.pz_last_launch_count(s.ctx)
-        evals = s.n_evals
-        lines = [pz.pz_star_lines(s.ctx, k) for k in range(S)]
-        s.close()
-        return {"ms_per_step": ms, "evals_per_step": evals, "evals_per_s": ws * evals / (ms * 1e-3),
-                "stars": S, "lines_per_star_min_mean_max": [min(lines), float(np.mean(lines)), max(lines)],
-                "graph_launches_per_step": 1, "kernels_per_step": kernels, "create_s": t_create,
-                "loss_first_last": [L0, L1], "lr_gf": lr}
-
-    b = I.config4(n_stars=args.batch_stars)
-    rng = np.random.default_rng(7)
-    nl = b.lines.n_lines
-    n_out = b.instrument.pix_lambda_nm.size
-    tg, t6 = rng.normal(0, 0.1, nl).astype(np.float32), rng.normal(0, 0.2, nl).astype(np.float32)
-    big = measure(b, tg, t6, rng.normal(0, 1 / 200, (b.n_stars, n_out)), args.batch_steps, 3)
-    big["workload"] = ("%d stars (Teff U[3500,7000], log g U[1,5], [M/H] U[-2,0.5]) on the APOGEE-like grid and "
-                       "instrument, per-star top-N_k (N_k = exp U[ln 2e4, ln 3e5]) of a 3e5-line master list; "
-                       "one step = pz_calib_step (corrections, fwd, chi^2, bwd, update) as one CUDA-graph launch"
-                       % b.n_stars)
-    big["l2"] = "inputs larger than L2 (line tables and [star][depth][lambda] buffers, > 1 GB)"
-    del b
-    jb, tr = I.config4_joint()
-    joint = measure(jb, tr["dlog_gf"], tr["dlog_gamma6"], tr["noise"], max(args.batch_steps, 5), 3)
-    joint["workload"] = ("joint two-star calibration step: solar-like (5777, 4.44) + giant-like (4286, 1.66), "
-                         "1e5 shared lines, shared dlog_gf/dlog_gamma6 corrections, gradients summed, one update")
-    big["joint_two_star"] = joint
-    return big
-
-
-# ---------------------------------------------------------------------------
 # broad optical forward: 300-1000 nm at R_grid = 3e5, 3e6 lines
 # ---------------------------------------------------------------------------
 def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None, pipe_peaks=None):
@@ -339,7 +362,7 @@ def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None, pipe_peaks=No
     import paper_2607_24141_gb300 as pz
     from paper_2607_24141_gb300 import inputs as I
     stream = torch.cuda.current_stream()
-    prob = I.config2()
+    prob = cached("config2", I.config2)
     t0 = time.perf_counter()
     s = pz.Synthesizer(prob, pz.PZ_MIXED, device=dev.index)
     t_create = time.perf_counter() - t0
@@ -409,7 +432,7 @@ def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None, pipe_peaks=No
            "create_s": t_create,
            "kernel_ms_per_step": {k: v[0] / args.broad_steps for k, v in kt.items() if v[1] > 0},
            "far_fwd_ms": far_ms,
-           "far_fwd_fp32_ops_per_s": evals * OPS["line_fwd"]["fp32_reduced"] / (far_ms * 1e-3),
+           "far_fwd_fp32_ops_per_s": evals * far_ops(4)["line_fwd"]["fp32_reduced"] / (far_ms * 1e-3),
            "scattering": scat}
     # plain FP64 GPU form on a slice of the same line list
     if not args.no_fp64:
@@ -450,7 +473,7 @@ def run_scatter_step(args, dev, tiling=None):
     import paper_2607_24141_gb300 as pz
     from paper_2607_24141_gb300 import inputs as I
     stream = torch.cuda.current_stream()
-    prob = I.with_scattering(I.config1(seed=1), r0=50.0)
+    prob = I.with_scattering(cached("config1", lambda: I.config1(seed=1)), r0=50.0)
     s = pz.Synthesizer(prob, pz.PZ_MIXED, device=dev.index)
     if tiling is not None:
         pz.pz_set_tiling(s.ctx, *tiling)
@@ -521,8 +544,8 @@ def run_centre(args, dev, barrier, max_over_ranks, ws, tiling=None):
         barrier()
         return max_over_ranks(a.elapsed_time(b)) / k
 
-    for name, prob, steps, grad in (("apogee_fwdbwd", I.config1(seed=1), 10, True),
-                                    ("broad_fwd", I.config2(), 2, False)):
+    for name, prob, steps, grad in (("apogee_fwdbwd", cached("config1", lambda: I.config1(seed=1)), 10, True),
+                                    ("broad_fwd", cached("config2", I.config2), 2, False)):
         s = pz.Synthesizer(prob, pz.PZ_MIXED, device=dev.index)
         if tiling is not None:
             pz.pz_set_tiling(s.ctx, *tiling)
@@ -595,7 +618,12 @@ def run_lbfgs(args, dev, tiling=None):
     g0 = torch.empty(nl, dtype=torch.float32, device=dev)
     s.calib_step(y, w, 0.0, 0.0, 0.0, loss, g0, None, None)
     g0 = g0.abs().cpu().numpy()
-    res = calibrate.lbfgs(s, y, w, n_updates=args.lbfgs_updates)
+    runs = []
+    for _ in range(max(1, args.lbfgs_runs)):
+        s.set_corrections(np.zeros(nl, np.float32), np.zeros(nl, np.float32), None)
+        s.forward()
+        runs.append(calibrate.lbfgs(s, y, w, n_updates=args.lbfgs_updates))
+    res = runs[-1]
     est = res["dlog_gf"].cpu().numpy()
     used = g0 > 0
     top = used & (g0 >= np.quantile(g0[used], 0.99))
@@ -604,9 +632,7 @@ def run_lbfgs(args, dev, tiling=None):
     n_data = int(y.numel())
     return {"workload": "joint two-star calibration: solar-like (5777, 4.44) + giant-like (4286, 1.66), 1e5 shared "
                         "lines, true Delta log gf ~ N(0, 0.1), Delta log gamma6 ~ N(0, 0.2), S/N 200 noise",
-            "updates": res["updates"], "evaluations": res["evals"], "seconds": res["seconds"],
-            "s_per_update": res["seconds"] / max(res["updates"], 1),
-            "chi2_start": res["loss_start"], "chi2_final": res["loss_final"], "n_data": n_data,
+            **run_summary(runs), "chi2_start": res["loss_start"], "chi2_final": res["loss_final"], "n_data": n_data,
             "corr_dlog_gf_top1pct_lines": corr}
 
 
@@ -647,7 +673,10 @@ def run_lbfgs_groups(args, dev, tiling=None):
     g0 = torch.empty((4, G), dtype=torch.float32, device=dev)
     pz.pz_group_eval(s.ctx, y, w, torch.zeros((4, G), dtype=torch.float32, device=dev), loss, g0)
     g0 = g0[0].abs().cpu().numpy()
-    res = calibrate.lbfgs_groups(s, y, w, q, G, n_updates=args.lbfgs_updates)
+    runs = []
+    for _ in range(max(1, args.lbfgs_runs)):
+        runs.append(calibrate.lbfgs_groups(s, y, w, q, G, n_updates=args.lbfgs_updates))
+    res = runs[-1]
     xf = res["x"].cpu().numpy()
     top = g0 >= np.quantile(g0, 0.99)
     lines = top[q]
@@ -656,9 +685,7 @@ def run_lbfgs_groups(args, dev, tiling=None):
     return {"workload": "joint two-star four-parameter grouped calibration: solar-like (5777, 4.44) + giant-like "
                         "(4286, 1.66), %d records in %d component complexes, groups from the greedy pass "
                         "(2.0 cm^-1, 0.035 nm), true corrections per complex, S/N 200 noise" % (nl, tr["x"].shape[1]),
-            "records": nl, "groups": G, "scalars": 4 * G, "grouping_s": t_group,
-            "updates": res["updates"], "evaluations": res["evals"], "seconds": res["seconds"],
-            "s_per_update": res["seconds"] / max(res["updates"], 1),
+            "records": nl, "groups": G, "scalars": 4 * G, "grouping_s": t_group, **run_summary(runs),
             "chi2_start": res["loss_start"], "chi2_final": res["loss_final"], "n_data": int(y.numel()),
             "corr_dlog_gf_top1pct_groups": corr,
             "paper_context": "40 shared Sun-Arcturus updates, 101,124 scalars: 64 s on one H100 (Sec. 6)"}
@@ -766,59 +793,212 @@ def fp64_batch_rate(dev):
 
 
 # ---------------------------------------------------------------------------
-# native arm
+# headline: the 64-star batched fwd+bwd, one CUDA-graph launch per step
 # ---------------------------------------------------------------------------
-def main():
-    args = parse()
-    if args.impl == "reference":
-        return run_reference(args)
+def run_headline(args, dev, barrier, max_over_ranks, ws, rank, tiling, pipe_peaks, clk_max):
+    """64 stars (seeded Teff, log g, [M/H]) on the APOGEE-like grid and instrument, each
+    with its own top-N_k subset (2e4-3e5) of a 3e5-line master list; one step =
+    pz_calib_step (corrections, fwd, chi^2, bwd, update) replayed as one graph launch.
+    Returns the timed result with the per-kernel times of the graph's own event pairs,
+    the end-to-end form through host buffers, and the parity of the batch against the
+    oracle's stored results for four of its stars.
+    tiling: the line-kernel tiling tuned on the single-star workload (same grid and
+    line density)."""
     import numpy as np
     import torch
 
     import paper_2607_24141_gb300 as pz
     from paper_2607_24141_gb300 import inputs as I
+    stream = torch.cuda.current_stream()
+    b = I.config4(n_stars=args.batch_stars)
+    t0 = time.perf_counter()
+    s = pz.Synthesizer(b, pz.PZ_MIXED, device=dev.index)
+    t_create = time.perf_counter() - t0
+    if tiling is not None:
+        pz.pz_set_tiling(s.ctx, *tiling)
+    S, n_out, nl, n_elem = b.n_stars, s.n_out, b.lines.n_lines, b.n_elem
+    evals = s.n_evals
+    # synthetic targets: the model at seeded true corrections plus S/N-200 noise
+    rng = np.random.default_rng(7)
+    tg = rng.normal(0, 0.1, nl).astype(np.float32)
+    t6 = rng.normal(0, 0.2, nl).astype(np.float32)
+    noise = rng.normal(0, 1 / 200, (S, n_out))
+    s.set_corrections(tg, t6, None)
+    y = (s.forward() + torch.tensor(noise, dtype=torch.float32, device=dev)).contiguous()
+    w = torch.full_like(y, 200.0 ** 2)
+    zero_gf = torch.zeros(nl, dtype=torch.float32, device=dev)
+    zero_ab = torch.zeros(n_elem, dtype=torch.float32, device=dev)
+    s.set_corrections(zero_gf, zero_gf, zero_ab)
+    s.forward()
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    g_gf = torch.empty(nl, dtype=torch.float32, device=dev)
+    g_g6 = torch.empty(nl, dtype=torch.float32, device=dev)
+    g_ab = torch.empty(n_elem, dtype=torch.float32, device=dev)
+    s.calib_step(y, w, 0.0, 0.0, 0.0, loss, g_gf, g_g6, g_ab)
+    torch.cuda.synchronize()
+    L0 = loss.item()
+    gn, gmax = float(g_gf.double().norm().item()), float(g_gf.abs().max().item())
+    # plain gradient step: its linear model lowers L by 5 %, at most 0.01 dex per correction
+    lr = float(min(0.05 * L0 / max(gn * gn, 1e-300), 0.01 / max(gmax, 1e-300)))
 
-    ws, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+    def step():
+        s.calib_step(y, w, lr, 0.0, 0.0, loss, g_gf, g_g6, g_ab)
 
-    barrier, max_over_ranks = make_collectives(ws, dev)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    pz.pz_set_profiling(s.ctx, True)
+    step()                        # re-capture with the graph's event pairs, untimed
+    torch.cuda.synchronize()
+    pz.pz_set_profiling(s.ctx, False)
+    pz.pz_set_profiling(s.ctx, True)
+    kernels = pz.pz_last_launch_count(s.ctx)
+    clk = ClockSampler(getattr(torch.cuda.get_device_properties(dev.index), "pci_bus_id", None))
+    barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(args.steps):
+        step()
+    e.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    barrier()
+    ms_total = max_over_ranks(a.elapsed_time(e))
+    kt = pz.pz_kernel_times(s.ctx)
+    pz.pz_set_profiling(s.ctx, False)
+    pz.pz_sync_status(s.ctx, stream)            # raises if a bounded device wait gave up
+    L1 = loss.item()
+    lines = [pz.pz_star_lines(s.ctx, k) for k in range(S)]
+    out = {"ms_total": ms_total, "ms_per_step": ms_total / args.steps, "evals_per_step": evals,
+           "value": aggregate_value(evals, ws, args.steps, ms_total), "kernels_per_step": kernels,
+           "gpu_launches": kernels * args.steps, "clocks": clocks, "kernel_times": kt, "create_s": t_create,
+           "stars": S, "lines_per_star_min_mean_max": [min(lines), float(np.mean(lines)), max(lines)],
+           "loss_first_last": [L0, L1], "lr_gf": lr}
 
-    # CPU baseline first (rank 0, before the GPU work of this process starts)
-    cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        ev, dt, desc = oracle_sample()
-        cpu = {"value": ev / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc}
+    # ---- parity against the oracle's stored star results (zero corrections) ----
+    gd = golden("config4") if not args.no_parity else None
+    if gd is not None and S == 64:
+        s.set_corrections(zero_gf, zero_gf, zero_ab)
+        f = s.forward().cpu().numpy().astype(np.float64)
+        df = []
+        par = {"stars_full": [int(k) for k in gd["full_stars"]],
+               "stars_sampled": [int(k) for k in gd["sampled_stars"]]}
+        for k in gd["full_stars"]:
+            df.append(f[k] - gd["star%d_f" % k])
+        pix = gd["sampled_pixels"]
+        for k in gd["sampled_stars"]:
+            df.append(f[k][pix] - gd["star%d_f_sampled" % k])
+        par["df_norm"] = diff_stats(np.concatenate(df))
+        ge = {"gf": 0.0, "g6": 0.0, "abund": 0.0, "loss_rel": 0.0}
+        for k in gd["full_stars"]:
+            yk = torch.zeros_like(y)
+            wk = torch.zeros_like(w)
+            yk[k] = torch.tensor(gd["star%d_y" % k], device=dev)
+            wk[k] = 200.0 ** 2
+            s.calib_step(yk, wk, 0.0, 0.0, 0.0, loss, g_gf, g_g6, g_ab)
+            torch.cuda.synchronize()
+            sub = b.subsets[k]
+            ge["gf"] = max(ge["gf"], float(grad_rel(g_gf.cpu().numpy()[sub], gd["star%d_g_gf" % k]).max()))
+            ge["g6"] = max(ge["g6"], float(grad_rel(g_g6.cpu().numpy()[sub], gd["star%d_g_g6" % k]).max()))
+            ge["abund"] = max(ge["abund"], float(grad_rel(g_ab.cpu().numpy(), gd["star%d_g_ab" % k]).max()))
+            ge["loss_rel"] = max(ge["loss_rel"], abs(loss.item() / float(gd["star%d_loss" % k]) - 1))
+        par["grad_rel_max"] = ge
+        par["reference"] = ("FP64 oracle, stored by tests/golden/make_config4_golden.py: every pixel and every "
+                            "line gradient of the two stars with the fewest lines, 12 pixels of the star with "
+                            "the most lines and of star 17; the batch context at zero corrections, gradients "
+                            "with the chi^2 weights of one star at a time")
+        par["pass"] = bool(par["df_norm"]["max"] <= 1e-4 and max(ge["gf"], ge["g6"], ge["abund"]) <= 1e-3)
+        out["parity"] = par
+    else:
+        out["parity"] = None
 
+    # ---- end to end through the C ABI with host buffers ----
+    if not args.no_e2e and args.e2e_steps > 0:
+        h_gf = torch.zeros(nl, dtype=torch.float32).pin_memory()
+        h_g6 = torch.zeros(nl, dtype=torch.float32).pin_memory()
+        h_ab = torch.zeros(n_elem, dtype=torch.float32).pin_memory()
+        h_y = y.cpu().pin_memory()
+        o_gf = torch.empty(nl, dtype=torch.float32).pin_memory()
+        o_g6 = torch.empty(nl, dtype=torch.float32).pin_memory()
+        o_ab = torch.empty(n_elem, dtype=torch.float32).pin_memory()
+        o_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+        y_dev = torch.empty_like(y)
+        eos = b.elem_of_species
+
+        def e2e_step():
+            # host corrections go straight into the C ABI (it copies them); the targets go up,
+            # the step runs, the loss and the gradients come back for a host-side optimiser
+            pz.pz_set_corrections(s.ctx, h_gf.numpy(), h_g6.numpy(), h_ab.numpy(), eos, n_elem, stream)
+            y_dev.copy_(h_y, non_blocking=True)
+            s.calib_step(y_dev, w, 0.0, 0.0, 0.0, loss, g_gf, g_g6, g_ab)
+            o_gf.copy_(g_gf, non_blocking=True)
+            o_g6.copy_(g_g6, non_blocking=True)
+            o_ab.copy_(g_ab, non_blocking=True)
+            o_loss.copy_(loss, non_blocking=True)
+            stream.synchronize()
+
+        e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        e.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms_e2e = max_over_ranks(a.elapsed_time(e))
+        out["e2e"] = {"value": aggregate_value(evals, ws, args.e2e_steps, ms_e2e), "unit": UNIT,
+                      "h2d_bytes_per_step": 4 * (2 * nl + n_elem + S * n_out),
+                      "d2h_bytes_per_step": 4 * (2 * nl + n_elem) + 8,
+                      "ms_per_step": ms_e2e / args.e2e_steps, "steps": args.e2e_steps}
+    else:
+        out["e2e"] = None
+    pz.pz_sync_status(s.ctx, stream)
+    s.close()
+    del s, b
+    torch.cuda.empty_cache()
+
+    # ---- the plain FP64 GPU form and the mixed path on the same 3-star slice ----
+    if not args.no_fp64:
+        r64 = fp64_batch_rate(dev)
+        out["fp64_form"] = r64
+        out["speedup_vs_fp64_form"] = out["value"] / ws / r64["evals_per_s"]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# single-star APOGEE-like fwd+bwd (config 1): autotune, timing, roofline
+# ---------------------------------------------------------------------------
+def run_config1(args, dev, pipe_peaks, clk_max):
+    """The APOGEE-like fwd+bwd step of one spectrum (37,550 points x 2e5 lines x 72
+    depths, instrument onto 8,575 pixels, chi^2, reverse pass), eager calls through the
+    C ABI; tunes the line-kernel tiling first (reused by every other workload).  The
+    plain FP64 GPU form is timed on a 4,000-point slice of the same spectrum."""
+    import numpy as np
+    import torch
+
+    import paper_2607_24141_gb300 as pz
+    from paper_2607_24141_gb300 import inputs as I
+    stream = torch.cuda.current_stream()
     prob = I.config1(seed=1)
     inst = prob.instrument
     nl, n_pix, n_elem = prob.lines.n_lines, inst.pix_lambda_nm.size, prob.n_elem
-    s = pz.Synthesizer(prob, pz.PZ_MIXED, device=local)
+    s = pz.Synthesizer(prob, pz.PZ_MIXED, device=dev.index)
     evals = s.n_evals
-    stream = torch.cuda.current_stream()
-    # tiling of the line kernels: measured on this workload before any timing
     tune = None
     if not args.no_autotune:
         t0 = time.perf_counter()
         tune = pz.pz_autotune(s.ctx, with_backward=True, reps=2, stream=stream)
         tune["seconds"] = time.perf_counter() - t0
-
-    # synthetic target: the model at seeded "true" corrections plus S/N-200 noise
     rng = np.random.default_rng(7)
-    truth_gf = rng.normal(0, 0.1, nl).astype(np.float32)
-    truth_g6 = rng.normal(0, 0.2, nl).astype(np.float32)
-    s.set_corrections(truth_gf, truth_g6, None)
-    f_true = s.forward().cpu().numpy()
-    y_host = (f_true + rng.normal(0, 1 / 200, n_pix)).astype(np.float32)
+    s.set_corrections(rng.normal(0, 0.1, nl).astype(np.float32), rng.normal(0, 0.2, nl).astype(np.float32), None)
+    y = (s.forward() + torch.tensor(rng.normal(0, 1 / 200, n_pix), dtype=torch.float32, device=dev)).contiguous()
     eos = prob.elem_of_species
-
     dgf = torch.zeros(nl, dtype=torch.float32, device=dev)
-    dg6 = torch.zeros(nl, dtype=torch.float32, device=dev)
     dab = torch.zeros(n_elem, dtype=torch.float32, device=dev)
-    y = torch.tensor(y_host, device=dev)
     w = torch.full((n_pix,), 200.0 ** 2, dtype=torch.float32, device=dev)
     loss = torch.zeros(1, dtype=torch.float64, device=dev)
     dLdf = torch.empty(n_pix, dtype=torch.float32, device=dev)
@@ -827,28 +1007,20 @@ def main():
     g_g6 = torch.empty(nl, dtype=torch.float32, device=dev)
     g_ab = torch.empty(n_elem, dtype=torch.float32, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MiB > L2
-    launches = [0]
 
-    def fwd_only():
-        pz.pz_line_opacity(s.ctx, None, stream)
-        launches[0] += pz.pz_last_launch_count(s.ctx)
-        pz.pz_flux(s.ctx, None, None, stream)
-        launches[0] += pz.pz_last_launch_count(s.ctx)
-        pz.pz_instrument(s.ctx, inst.v_r_kms, inst.v_b_kms, inst.R_lsf, inst.pix_lambda_nm, f, stream)
-        launches[0] += pz.pz_last_launch_count(s.ctx)
+    def fwd_only(ctx):
+        pz.pz_line_opacity(ctx, None, stream)
+        pz.pz_flux(ctx, None, None, stream)
+        pz.pz_instrument(ctx, inst.v_r_kms, inst.v_b_kms, inst.R_lsf, inst.pix_lambda_nm, f, stream)
 
-    def step():
-        pz.pz_set_corrections(s.ctx, dgf, dg6, dab, eos, n_elem, stream)
-        launches[0] += pz.pz_last_launch_count(s.ctx)
-        fwd_only()
-        pz.pz_loss_chi2(s.ctx, y, w, loss, dLdf, stream)
-        launches[0] += pz.pz_last_launch_count(s.ctx)
-        pz.pz_backward(s.ctx, dLdf, g_gf, g_g6, g_ab, stream)
-        launches[0] += pz.pz_last_launch_count(s.ctx)
+    def step(ctx, yy):
+        pz.pz_set_corrections(ctx, dgf, dgf, dab, eos, n_elem, stream)
+        fwd_only(ctx)
+        pz.pz_loss_chi2(ctx, yy, w, loss, dLdf, stream)
+        pz.pz_backward(ctx, dLdf, g_gf, g_g6, g_ab, stream)
         flush.zero_()
 
     def timed(fn, k):
-        barrier()
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
@@ -857,10 +1029,174 @@ def main():
             fn()
         b.record(stream)
         torch.cuda.synchronize()
-        barrier()
-        return a.elapsed_time(b)
+        return a.elapsed_time(b) / k
 
-    # ---- pipe peaks (roofline denominators of the ALU-bound line kernels) ----
+    for _ in range(3):
+        step(s.ctx, y)
+    pz.pz_set_profiling(s.ctx, True)
+    ms = timed(lambda: step(s.ctx, y), args.config1_steps)
+    kt = pz.pz_kernel_times(s.ctx)
+    pz.pz_set_profiling(s.ctx, False)
+    ms_fwd = timed(lambda: (fwd_only(s.ctx), flush.zero_()), args.config1_steps)
+    pz.pz_sync_status(s.ctx, stream)
+    s.close()
+    J = tune["tiling"][0] if tune else 4
+    n_sm = torch.cuda.get_device_properties(dev.index).multi_processor_count
+    roof = line_roofline(kt, evals, J, pipe_peaks, n_sm, clk_max, "apogee")
+    out = {"workload": "APOGEE-like fwd+bwd, one spectrum: 37,550 pts x 2e5 lines (40 species, 1/3 in bands) x "
+                       "72 depths, W=1,500, instrument onto 8,575 px, chi^2, reverse pass; eager C-ABI calls, "
+                       "256 MiB L2 flush between steps",
+           "s_per_spectrum_fwdbwd": ms * 1e-3, "s_per_spectrum_fwd": ms_fwd * 1e-3,
+           "evals_per_spectrum": evals, "evals_per_s_fwdbwd": evals / (ms * 1e-3),
+           "evals_per_s_fwd": evals / (ms_fwd * 1e-3),
+           "roofline_frac": roof["frac"], "roofline_kernel": roof["kernel"],
+           "kernel_ms_per_step": {k: v[0] / args.config1_steps for k, v in kt.items() if v[1] > 0},
+           "roofline": roof}
+    # transfer stage against the measured FP64 FMA peak: E_n evaluations, two per
+    # (lambda, depth) in the flux (both branches), one in its adjoint, each a Taylor step
+    # of FMA_PER_EN FMAs (tau, Planck and the interval weights are not counted)
+    if pipe_peaks.get("fp64") and kt["flux"][1] > 0:
+        cells = prob.grid.n_lambda * prob.atmos.n_depth
+        rt = {"bound": "fp64", "unit": "GFMA/s", "peak": pipe_peaks["fp64"] * 1e-9, "fma_per_En": FMA_PER_EN}
+        for name, per_cell in (("flux", 2), ("rt_adjoint", 1)):
+            t = kt[name][0] * 1e-3 / max(kt[name][1], 1)
+            ach = per_cell * cells * FMA_PER_EN / t
+            rt[name] = {"ms_per_launch": t * 1e3, "achieved": ach * 1e-9, "frac": ach / pipe_peaks["fp64"]}
+        out["rt_roofline"] = rt
+    if not args.no_fp64:
+        sl = I.wavelength_slice(prob, 1600.0, 4000)
+        s64 = pz.Synthesizer(sl, pz.PZ_FP64, device=dev.index)
+        s32 = pz.Synthesizer(sl, pz.PZ_MIXED, device=dev.index)
+        n_sl = sl.grid.n_lambda
+        ys = torch.ones(n_sl, dtype=torch.float32, device=dev)
+        ws_ = torch.full((n_sl,), 200.0 ** 2, dtype=torch.float32, device=dev)
+        d_sl = torch.empty(n_sl, dtype=torch.float32, device=dev)
+        f_sl = torch.empty(n_sl, dtype=torch.float32, device=dev)
+        nls = sl.lines.n_lines
+        gs = [torch.empty(nls, dtype=torch.float32, device=dev) for _ in range(2)]
+
+        def step_sl(ctx):
+            pz.pz_line_opacity(ctx, None, stream)
+            pz.pz_flux(ctx, None, None, stream)
+            pz.pz_instrument(ctx, 0.0, 0.0, 0.0, None, f_sl, stream)
+            pz.pz_loss_chi2(ctx, ys, ws_, loss, d_sl, stream)
+            pz.pz_backward(ctx, d_sl, gs[0], gs[1], None, stream)
+
+        step_sl(s64.ctx)
+        ms64 = timed(lambda: step_sl(s64.ctx), 1)
+        step_sl(s32.ctx)
+        ms32 = timed(lambda: step_sl(s32.ctx), 3)
+        ev_sl = s64.n_evals
+        s64.close()
+        s32.close()
+        out["fp64_form"] = {"sample": "plain FP64 GPU form, fwd+bwd of a 4,000-point slice from 1600 nm of the same "
+                                      "spectrum (%d lines, %.3g evals); mixed path on the same slice" % (nls, ev_sl),
+                            "s_fp64": ms64 * 1e-3, "s_mixed": ms32 * 1e-3, "speedup_same_slice": ms64 / ms32,
+                            "s_per_spectrum_fwdbwd_extrapolated": evals * ms64 * 1e-3 / ev_sl}
+        out["speedup_vs_fp64_form"] = out["fp64_form"]["s_per_spectrum_fwdbwd_extrapolated"] / (ms * 1e-3)
+    return out, tune
+
+
+# ---------------------------------------------------------------------------
+# calibration workload (config 3) against the oracle's stored full-size results
+# ---------------------------------------------------------------------------
+def run_config3(args, dev, tiling):
+    """The differentiable-calibration workload at full size (37,550 points, 1.2e5 lines,
+    8,575 pixels): normalised flux on every pixel, chi^2 and the gradients of every line
+    and element at zero corrections against the FP64 oracle's stored results
+    (tests/golden/make_config3_golden.py), plus the time of the step."""
+    import numpy as np
+    import torch
+
+    import paper_2607_24141_gb300 as pz
+    from paper_2607_24141_gb300 import inputs as I
+    gd = golden("config3")
+    if gd is None:
+        return None
+    stream = torch.cuda.current_stream()
+    prob, _ = I.config3()
+    nl, n_elem = prob.lines.n_lines, prob.n_elem
+    s = pz.Synthesizer(prob, pz.PZ_MIXED, device=dev.index)
+    if tiling is not None:
+        pz.pz_set_tiling(s.ctx, *tiling)
+    z = torch.zeros(nl, dtype=torch.float32, device=dev)
+    s.set_corrections(z, z, torch.zeros(n_elem, dtype=torch.float32, device=dev))
+    y = torch.tensor(gd["y"], dtype=torch.float32, device=dev)
+    w = torch.full_like(y, 200.0 ** 2)
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    dLdf = torch.empty_like(y)
+    g = [torch.empty(nl, dtype=torch.float32, device=dev) for _ in range(2)]
+    gab = torch.empty(n_elem, dtype=torch.float32, device=dev)
+    f = torch.empty_like(y)
+
+    def step():
+        s.forward(f=f)
+        s.loss(y, w, loss, dLdf)
+        s.backward(dLdf, g[0], g[1], gab)
+
+    step()
+    torch.cuda.synchronize()
+    out = {"workload": "calibration: 37,550 pts x 1.2e5 lines x 72 depths -> 8,575 px, target = oracle f at seeded "
+                       "true corrections + S/N 200 noise; gradients at zero corrections",
+           "df_norm": diff_stats(f.cpu().numpy().astype(np.float64) - gd["f"]),
+           "loss_rel": abs(loss.item() / float(gd["loss"]) - 1),
+           "grad_rel_max": {"gf": float(grad_rel(g[0].cpu().numpy(), gd["g_gf"]).max()),
+                            "g6": float(grad_rel(g[1].cpu().numpy(), gd["g_g6"]).max()),
+                            "abund": float(grad_rel(gab.cpu().numpy(), gd["g_ab"]).max())},
+           "oracle_fd_check_rel_max": {
+               "gf": float(np.max(np.abs(gd["adj_g_gf"] - gd["fd_g_gf"])
+                                  / np.maximum(np.abs(gd["fd_g_gf"]), 1e-3 * gd["g_gf_max"]))),
+               "g6": float(np.max(np.abs(gd["adj_g_g6"] - gd["fd_g_g6"])
+                                  / np.maximum(np.abs(gd["fd_g_g6"]), 1e-3 * gd["g_g6_max"])))}}
+    a = torch.cuda.Event(enable_timing=True)
+    e = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(3):
+        step()
+    e.record(stream)
+    torch.cuda.synchronize()
+    out["s_per_spectrum_fwdbwd"] = a.elapsed_time(e) / 3 * 1e-3
+    out["evals_per_spectrum"] = s.n_evals
+    gmax = max(out["grad_rel_max"].values())
+    out["pass"] = bool(out["df_norm"]["max"] <= 1e-4 and gmax <= 1e-3)
+    pz.pz_sync_status(s.ctx, stream)
+    s.close()
+    return out
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+
+    import paper_2607_24141_gb300 as pz
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    barrier, max_over_ranks = make_collectives(ws, dev)
+
+    # CPU baseline first (rank 0, before the GPU work of this process starts)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        ev, dt, desc = oracle_sample()
+        cpu = {"value": ev / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle", "sample": desc}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    clk_max = float(peaks.get("sm_max_mhz") or 2070.0)
+    stream = torch.cuda.current_stream()
+    # pipe peaks (roofline denominators of the ALU-bound line kernels), measured here
     pipe_peaks = {}
     try:
         pipe_peaks = {"fp32": pz.pz_probe_pipe(0, 4096, stream), "mufu": pz.pz_probe_pipe(1, 4096, stream),
@@ -868,206 +1204,67 @@ def main():
     except Exception:
         pipe_peaks = {}
 
-    # ---- fwd+bwd (headline) ----
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    clk = ClockSampler(getattr(torch.cuda.get_device_properties(local), "pci_bus_id", None))
-    clk.start()
-    pz.pz_set_profiling(s.ctx, True)
-    launches[0] = 0
-    ms = timed(step, args.steps)
-    ktimes = pz.pz_kernel_times(s.ctx)
-    pz.pz_set_profiling(s.ctx, False)
-    pz.pz_sync_status(s.ctx, stream)            # raises if a bounded device wait gave up
-    n_launch = launches[0] + 0
-    clocks = clk.stop()
-    ms_max = max_over_ranks(ms)
-    ms_step = ms_max / args.steps
-    value = aggregate_value(evals, ws, args.steps, ms_max)
+    # single-star APOGEE-like step; tunes the tiling every other workload reuses
+    c1, tune = run_config1(args, dev, pipe_peaks, clk_max)
+    tiling = tune["tiling"] if tune else None
 
-    # ---- fwd only ----
-    for _ in range(2):
-        fwd_only()
-    ms_fwd = max_over_ranks(timed(lambda: (fwd_only(), flush.zero_()), args.steps)) / args.steps
+    # headline: the 64-star batch
+    hl = run_headline(args, dev, barrier, max_over_ranks, ws, rank, tiling, pipe_peaks, clk_max)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = line_roofline(hl["kernel_times"], hl["evals_per_step"], tiling[0] if tiling else 4, pipe_peaks, n_sm,
+                         clk_max, "batch64")
+    roof["hbm_gbs_peak"] = peaks.get("hbm_gbs")
+    roof["timing"] = "CUDA events recorded inside the step graph around each kernel family, over the timed steps"
+    roof["pipe_peaks_measured"] = {k: v * 1e-9 for k, v in pipe_peaks.items()}
 
-    # ---- end to end through the C ABI with host buffers ----
-    e2e = None
-    if not args.no_e2e:
-        h_gf = torch.zeros(nl, dtype=torch.float32).pin_memory()
-        h_g6 = torch.zeros(nl, dtype=torch.float32).pin_memory()
-        h_ab = torch.zeros(n_elem, dtype=torch.float32).pin_memory()
-        h_y = torch.tensor(y_host).pin_memory()
-        o_gf = torch.empty(nl, dtype=torch.float32).pin_memory()
-        o_g6 = torch.empty(nl, dtype=torch.float32).pin_memory()
-        o_ab = torch.empty(n_elem, dtype=torch.float32).pin_memory()
-        o_loss = torch.empty(1, dtype=torch.float64).pin_memory()
-
-        def e2e_step():
-            # host corrections go straight into the C ABI (it copies them); the target goes up too
-            pz.pz_set_corrections(s.ctx, h_gf.numpy(), h_g6.numpy(), h_ab.numpy(), eos, n_elem, stream)
-            y.copy_(h_y, non_blocking=True)
-            fwd_only()
-            pz.pz_loss_chi2(s.ctx, y, w, loss, dLdf, stream)
-            pz.pz_backward(s.ctx, dLdf, g_gf, g_g6, g_ab, stream)
-            o_gf.copy_(g_gf, non_blocking=True)
-            o_g6.copy_(g_g6, non_blocking=True)
-            o_ab.copy_(g_ab, non_blocking=True)
-            o_loss.copy_(loss, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
-            flush.zero_()
-
-        for _ in range(2):
-            e2e_step()
-        ms_e2e = max_over_ranks(timed(e2e_step, args.steps))
-        e2e = {"value": ws * evals * args.steps / (ms_e2e * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": 4 * (2 * nl + n_elem + n_pix),
-               "d2h_bytes_per_step": 4 * (2 * nl + n_elem) + 8,
-               "ms_per_step": ms_e2e / args.steps}
-
-    # ---- plain FP64 GPU form ----
-    fp64 = None
-    if not args.no_fp64 and args.fp64_steps > 0:
-        s.close()
-        s64 = pz.Synthesizer(prob, pz.PZ_FP64, device=local)
-
-        def step64():
-            pz.pz_set_corrections(s64.ctx, dgf, dg6, dab, eos, n_elem, stream)
-            pz.pz_line_opacity(s64.ctx, None, stream)
-            pz.pz_flux(s64.ctx, None, None, stream)
-            pz.pz_instrument(s64.ctx, inst.v_r_kms, inst.v_b_kms, inst.R_lsf, inst.pix_lambda_nm, f, stream)
-            pz.pz_loss_chi2(s64.ctx, y, w, loss, dLdf, stream)
-            pz.pz_backward(s64.ctx, dLdf, g_gf, g_g6, g_ab, stream)
-        step64()
-        torch.cuda.synchronize()
-        pz.pz_set_profiling(s64.ctx, True)
-        ms64 = max_over_ranks(timed(step64, args.fp64_steps)) / args.fp64_steps
-        k64 = pz.pz_kernel_times(s64.ctx)
-        s64.close()
-        fwd64 = sum(k64[k][0] for k in ("line_fwd", "flux", "instrument")) / args.fp64_steps
-        fp64 = {"s_per_spectrum_fwdbwd": ms64 * 1e-3, "s_per_spectrum_fwd": fwd64 * 1e-3,
-                "evals_per_s_fwdbwd": evals / (ms64 * 1e-3), "steps": args.fp64_steps}
-
-    # ---- batched many-star workload ----
-    batched = None
-    if fp64 is None:
-        s.close()
-    if not args.no_batch and args.batch_stars > 0:
-        batched = run_batched(args, dev, barrier, max_over_ranks, ws, tune["tiling"] if tune else None)
-        if not args.no_fp64:
-            r64 = fp64_batch_rate(dev)
-            batched["fp64_form"] = r64
-            batched["speedup_vs_fp64_form"] = batched["evals_per_s"] / ws / r64["evals_per_s"]
-
-    # ---- broad optical forward ----
     broad = None
     if not args.no_broad:
-        broad = run_broad(args, dev, barrier, max_over_ranks, ws, tune["tiling"] if tune else None, pipe_peaks)
+        broad = run_broad(args, dev, barrier, max_over_ranks, ws, tiling, pipe_peaks)
+    c3 = None
+    if not args.no_config3:
+        c3 = run_config3(args, dev, tiling)
 
-    # ---- roofline of the dominant kernel ----
-    props = torch.cuda.get_device_properties(local)
-    n_sm = props.multi_processor_count
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    clk_max = float(peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2070.0)
-    # near_* are the near-core parts already inside line_fwd / line_bwd; step is unused here
-    share = {k: v[0] for k, v in ktimes.items() if k not in ("near_fwd", "near_bwd", "step")}
-    far = {"line_fwd": ktimes["line_fwd"][0] - ktimes["near_fwd"][0],
-           "line_bwd": ktimes["line_bwd"][0] - ktimes["near_bwd"][0]}
-    dom = max(far, key=far.get)
-    t_dom = far[dom] * 1e-3 / max(ktimes[dom][1], 1)            # s per launch of the far-wing kernel
-    ops = far_ops(tune["tiling"][0] if tune else 4)[dom]
-    # pipe peaks measured on this GPU by the library's probe kernels (independent
-    # reciprocal / packed-FMA chains on every SM), next to the lane-count derivation
-    peak_mufu_lanes = n_sm * 16 * clk_max * 1e6
-    peak_fp32_lanes = n_sm * 128 * clk_max * 1e6
-    peak_mufu = pipe_peaks.get("mufu") or peak_mufu_lanes
-    peak_fp32 = pipe_peaks.get("fp32") or peak_fp32_lanes
-    achieved = evals * ops["fp32_reduced"] / t_dom
-    total_k = sum(share.values())
-    import hashlib
-    h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
-        h.update(open(os.path.join(ROOT, "paper_2607_24141_gb300", "csrc", name), "rb").read())
-    kname = "k_line_bwd" if dom == "line_bwd" else "k_line_fwd"
-    traffic = None
-    ncu_pipes = None
-    if kname in TRAFFIC and TRAFFIC[kname][1] == h.hexdigest()[:16]:
-        traffic = TRAFFIC[kname][0]
-    if kname in NCU_PIPES and NCU_PIPES[kname][1] == h.hexdigest()[:16]:
-        ncu_pipes = NCU_PIPES[kname][0]
-    roofline = {
-        "bound": "alu", "kernel": kname + " (far wing)", "pipe": "fp32",
-        "achieved": achieved * 1e-9, "peak": peak_fp32 * 1e-9, "unit": "Gop/s",
-        "frac": achieved / peak_fp32, "traffic": traffic, "ncu_pipes": ncu_pipes,
-        "peak_source": ("measured: pz_probe_pipe packed-FMA throughput (%d SMs); 128-lane derivation %.0f Gop/s"
-                        % (n_sm, peak_fp32_lanes * 1e-9)) if pipe_peaks.get("fp32") else
-                       "derived: %d SMs x 128 FP32 lanes x %.0f MHz (max SM clock)" % (n_sm, clk_max),
-        "pipe_peaks_measured": {k: v * 1e-9 for k, v in pipe_peaks.items()},
-        "ops_per_eval": ops, "evals_per_s": evals / t_dom, "ms_per_launch": t_dom * 1e3,
-        "fp32_pipe_frac_full_form": evals * ops["fp32_full"] / t_dom / peak_fp32,
-        "mufu_pipe_frac_reduced_form": evals * ops["mufu_reduced"] / t_dom / peak_mufu,
-        "kernel_share": {k: round(v / total_k, 4) for k, v in share.items() if total_k > 0},
-        "far_ms_per_launch": {k: v / max(ktimes[k][1], 1) for k, v in far.items()},
-        "near_ms_per_launch": {k: ktimes[k][0] / max(ktimes[k][1], 1) for k in ("near_fwd", "near_bwd")},
-        "hbm_gbs_peak": peaks.get("hbm_gbs"),
-    }
-
-    # ---- the FP64 transfer stage against the measured FP64 FMA peak ----
-    # E_n evaluations: two per (lambda, depth) in the flux (both branches), one in its
-    # adjoint; each is a Taylor step of FMA_PER_EN FP64 FMAs (the other FP64 work of the
-    # stage -- tau, Planck, the interval weights -- is not counted)
-    rt = None
-    if pipe_peaks.get("fp64") and ktimes["flux"][1] > 0:
-        cells = prob.grid.n_lambda * prob.atmos.n_depth
-        rt = {"bound": "fp64", "unit": "GFMA/s", "peak": pipe_peaks["fp64"] * 1e-9, "fma_per_En": FMA_PER_EN,
-              "peak_source": "measured: pz_probe_pipe FP64 FMA throughput (%d SMs)" % n_sm}
-        for name, per_cell in (("flux", 2), ("rt_adjoint", 1)):
-            t = ktimes[name][0] * 1e-3 / max(ktimes[name][1], 1)
-            ach = per_cell * cells * FMA_PER_EN / t
-            rt[name] = {"ms_per_launch": t * 1e3, "En_per_launch": per_cell * cells, "achieved": ach * 1e-9,
-                        "frac": ach / pipe_peaks["fp64"]}
-
-    # ---- continuum-referenced centre test (the paper's line rejection) ----
-    centre = None
-    if not args.no_centre:
-        centre = run_centre(args, dev, barrier, max_over_ranks, ws, tune["tiling"] if tune else None)
-
-    # ---- fwd+bwd with continuum scattering ----
-    scatter_step = None
-    if not args.no_scatter:
-        scatter_step = run_scatter_step(args, dev, tune["tiling"] if tune else None)
-
-    # ---- multi-update L-BFGS calibration of the joint two-star workload ----
+    centre = run_centre(args, dev, barrier, max_over_ranks, ws, tiling) if not args.no_centre else None
+    scatter_step = run_scatter_step(args, dev, tiling) if not args.no_scatter else None
     lbfgs = None
     if not args.no_lbfgs and args.lbfgs_updates > 0:
-        lbfgs = run_lbfgs(args, dev, tune["tiling"] if tune else None)
-        lbfgs["grouped_four_parameter"] = run_lbfgs_groups(args, dev, tune["tiling"] if tune else None)
+        lbfgs = run_lbfgs(args, dev, tiling)
+        lbfgs["grouped_four_parameter"] = run_lbfgs_groups(args, dev, tiling)
+    scaling = run_scaling(args, dev, tiling) if args.scaling else None
 
-    # ---- scaling sweeps (opt-in) ----
-    scaling = run_scaling(args, dev, tune["tiling"] if tune else None) if args.scaling else None
-
-    if broad is not None and pipe_peaks.get("fp32"):
-        broad["far_fwd_fp32_frac"] = broad["far_fwd_fp32_ops_per_s"] / pipe_peaks["fp32"]
-
+    c2 = None
+    if broad is not None:
+        if pipe_peaks.get("fp32"):
+            broad["far_fwd_fp32_frac"] = broad["far_fwd_fp32_ops_per_s"] / pipe_peaks["fp32"]
+        c2 = {k: broad.get(k) for k in ("s_per_spectrum_fwd", "evals_per_s", "far_fwd_fp32_frac",
+                                        "speedup_vs_fp64_form")}
+    ms_step = hl["ms_per_step"]
+    S = hl["stars"]
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "spectra_per_step": ws, "evals_per_spectrum": evals,
-                   "l2": "256 MiB buffer written between steps (inside the timed region)",
+        "metric": METRIC, "value": hl["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "stars_per_step": S * ws, "evals_per_step": hl["evals_per_step"],
+                   "l2": "inputs larger than L2 (line tables and [star][depth][lambda] buffers, > 1 GB)",
                    "precision": "FP32 Voigt + compensated FP32 sums; FP64 tau, E_n and flux"},
-        "s_per_spectrum_fwdbwd": ms_step * 1e-3, "s_per_spectrum_fwd": ms_fwd * 1e-3,
-        "evals_per_s_fwd": ws * evals / (ms_fwd * 1e-3),
-        "fp64_form": fp64,
-        "speedup_vs_fp64_form": (fp64["s_per_spectrum_fwdbwd"] / (ms_step * 1e-3)) if fp64 else None,
-        "roofline": roofline, "rt_roofline": rt, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch,
-        "clocks": clocks,
-        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in ktimes.items()},
-        "batched": batched,
+        "gpu_launches": hl["gpu_launches"],
+        "s_per_spectrum_fwdbwd": ms_step * 1e-3 / S,
+        "speedup_vs_fp64_form": hl.get("speedup_vs_fp64_form"),
+        "parity": hl["parity"],
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": hl["e2e"],
+        "clocks": hl["clocks"],
+        "config1": {k: c1.get(k) for k in ("s_per_spectrum_fwdbwd", "s_per_spectrum_fwd", "evals_per_s_fwdbwd",
+                                           "roofline_frac", "speedup_vs_fp64_form")},
+        "config2": c2,
+        "config3": None if c3 is None else {k: c3[k] for k in ("df_norm", "loss_rel", "grad_rel_max",
+                                                               "oracle_fd_check_rel_max", "pass",
+                                                               "s_per_spectrum_fwdbwd")},
+        "batch": {k: hl.get(k) for k in ("kernels_per_step", "create_s", "lines_per_star_min_mean_max",
+                                         "loss_first_last", "lr_gf", "fp64_form")},
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in hl["kernel_times"].items() if v[1] > 0},
+        "config1_detail": c1,
         "broad_optical_fwd": broad,
         "centre_test": centre,
         "lbfgs_calibration": lbfgs,

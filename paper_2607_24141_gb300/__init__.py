@@ -355,10 +355,42 @@ def pz_kernel_times(ctx):
     return {KERNEL_NAMES[k]: (ms[k], cnt[k]) for k in range(n)}
 
 
+def _check_tensor(name, t, dtype, min_numel):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise PzError(PZ_EINVAL, "%s must be a torch tensor" % name)
+    if t.dtype != dtype:
+        raise PzError(PZ_EINVAL, "%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise PzError(PZ_EINVAL, "%s must be contiguous" % name)
+    if t.numel() < min_numel:
+        raise PzError(PZ_EINVAL, "%s holds %d entries, needs %d" % (name, t.numel(), min_numel))
+
+
 def pz_abundance_grad_noalloc(g_dlog_gf, species, elem_of_species, n_elem, g_dabund, stream=None):
-    """Per-element sums of per-line gradients with no device allocation (device tensors)."""
+    """Per-element sums of per-line gradients with no device allocation.
+
+    g_dlog_gf: float32 [n_lines], species: int32 [n_lines], elem_of_species: int32
+    [n_species], g_dabund: float32 [>= n_elem], all contiguous CUDA tensors on one
+    device.  The C entry point takes bare pointers, so the sizes, types and device
+    are checked here before the call (PZ_EINVAL)."""
+    import torch
+    if int(n_elem) < 0:
+        raise PzError(PZ_EINVAL, "n_elem must be >= 0")
+    _check_tensor("g_dlog_gf", g_dlog_gf, torch.float32, 0)
+    n_lines = g_dlog_gf.numel()
+    _check_tensor("species", species, torch.int32, 0)
+    if species.numel() != n_lines:
+        raise PzError(PZ_EINVAL, "species holds %d entries, g_dlog_gf %d" % (species.numel(), n_lines))
+    _check_tensor("elem_of_species", elem_of_species, torch.int32, 0)
+    _check_tensor("g_dabund", g_dabund, torch.float32, int(n_elem))
+    dev = g_dlog_gf.device
+    for name, t in (("g_dlog_gf", g_dlog_gf), ("species", species), ("elem_of_species", elem_of_species),
+                    ("g_dabund", g_dabund)):
+        if not t.is_cuda or t.device != dev:
+            raise PzError(PZ_EINVAL, "%s must be a CUDA tensor on the device of g_dlog_gf (%s)" % (name, dev))
     _check(load().pz_abundance_grad_noalloc(_ptr(g_dlog_gf), _ptr(species), _ptr(elem_of_species),
-                                            g_dlog_gf.numel(), elem_of_species.numel(), int(n_elem),
+                                            n_lines, elem_of_species.numel(), int(n_elem),
                                             _ptr(g_dabund), _stream(stream)))
 
 

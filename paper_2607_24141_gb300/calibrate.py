@@ -22,28 +22,34 @@ def _minimise(set_and_eval, n_params, dev, n_updates, history):
 
     x = torch.zeros(n_params, dtype=torch.float64, device=dev, requires_grad=True)
     evals = [0]
+    t_eval = [0.0]
 
     def objective():
+        t = time.perf_counter()
         loss, grad = set_and_eval(x.detach())
         evals[0] += 1
         x.grad = grad.to(torch.float64)
-        return float(loss)                      # a copy: the buffer is rewritten by the next evaluation
+        out = float(loss)                       # a copy: the buffer is rewritten by the next evaluation
+        t_eval[0] += time.perf_counter() - t
+        return out
 
     opt = torch.optim.LBFGS([x], lr=1.0, max_iter=n_updates, max_eval=4 * n_updates, history_size=history,
                             line_search_fn="strong_wolfe", tolerance_grad=0.0, tolerance_change=0.0)
     sync = torch.cuda.synchronize if x.is_cuda else (lambda: None)
     objective()                                 # untimed: captures the step's graph for these buffers
     evals[0] = 0
+    t_eval[0] = 0.0
     sync()
     t0 = time.perf_counter()
     loss0 = opt.step(objective)                 # runs the n_updates iterations; returns the first loss
     sync()
     seconds = time.perf_counter() - t0
     n_evals = evals[0]
+    eval_seconds = t_eval[0]
     updates = int(opt.state[x]["n_iter"])
     final = objective()                         # the objective at the accepted corrections
     return x.detach(), {"loss_start": loss0, "loss_final": final, "evals": n_evals, "updates": updates,
-                        "seconds": seconds}
+                        "seconds": seconds, "eval_seconds": eval_seconds}
 
 
 def lbfgs(synth, y, w=None, n_updates=40, history=10, fit_gamma6=True, stream=None):
@@ -55,7 +61,9 @@ def lbfgs(synth, y, w=None, n_updates=40, history=10, fit_gamma6=True, stream=No
     Returns {"dlog_gf", "dlog_gamma6": device FP32 [n_lines], "loss_start",
     "loss_final": the objective at zero and at the final corrections, "evals":
     objective evaluations of the loop, "updates": L-BFGS iterations, "seconds": wall
-    time of the loop, after one untimed evaluation that captures the step}.
+    time of the loop, after one untimed evaluation that captures the step,
+    "eval_seconds": the part of it spent from each evaluation's launch to its loss
+    readback}.
     """
     import torch
 

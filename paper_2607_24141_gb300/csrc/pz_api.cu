@@ -52,19 +52,50 @@ static void prof_fold(pz_ctx *c) {
     c->marks.clear();
 }
 
+// During a capture the events become event-record nodes of the graph (external
+// records), so that every replay times its kernels where they run.
 cudaEvent_t prof_begin(pz_ctx *c, cudaStream_t s) {
-    if (!c->profiling || c->capturing) return nullptr;
+    if (!c->profiling) return nullptr;
     cudaEvent_t a = prof_event(c);
-    cudaEventRecord(a, s);
+    if (c->capturing)
+        cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(a, s);
     return a;
 }
 
 void prof_end(pz_ctx *c, cudaStream_t s, int kid, cudaEvent_t a) {
     if (!a) return;
     cudaEvent_t b = prof_event(c);
+    if (c->capturing) {
+        cudaEventRecordWithFlags(b, s, cudaEventRecordExternal);
+        c->cap_marks.push_back({a, b, kid});
+        return;
+    }
     cudaEventRecord(b, s);
     c->marks.push_back({a, b, kid});
     if (c->marks.size() > 8192) prof_fold(c);
+}
+
+// Events recorded by a graph are read after each replay (the host waits for the
+// replay's last event) and are destroyed with the graph.
+static void fold_graph_marks(pz_ctx *c, const StepGraph &G) {
+    if (G.marks.empty() || cudaEventSynchronize(G.marks.back().b) != cudaSuccess) return;
+    for (const auto &m : G.marks) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, m.a, m.b) == cudaSuccess) {
+            c->k_ms[m.kid] += ms;
+            c->k_count[m.kid] += 1;
+        }
+    }
+}
+
+static void destroy_marks(std::vector<ProfMark> &marks) {
+    for (auto &m : marks) {
+        cudaEventDestroy(m.a);
+        cudaEventDestroy(m.b);
+    }
+    marks.clear();
 }
 
 template <class Fn>
@@ -296,8 +327,10 @@ static pz_status build_thresholds(pz_ctx *c) {
 
 static void drop_graph(pz_ctx *c) {
     if (c->graph.exec) cudaGraphExecDestroy(c->graph.exec);
+    destroy_marks(c->graph.marks);
     c->graph = StepGraph();
     if (c->ggraph.exec) cudaGraphExecDestroy(c->ggraph.exec);
+    destroy_marks(c->ggraph.marks);
     c->ggraph = StepGraph();
 }
 
@@ -316,10 +349,8 @@ static void destroy_ctx(pz_ctx *c) {
                     c->d_keep, c->L.gradbase, c->L.g4base, c->L.dgrad, c->L.dg4, c->d_mdgrad, c->d_mdg4,
                     c->d_grp_of, c->d_grp_off, c->d_grp_mem, c->d_sigma};
     for (void *p : ptrs) dfree(p);
-    for (auto &m : c->marks) {
-        cudaEventDestroy(m.a);
-        cudaEventDestroy(m.b);
-    }
+    destroy_marks(c->marks);
+    destroy_marks(c->cap_marks);
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
@@ -398,9 +429,10 @@ static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, 
         return fail(PZ_EINVAL, w + ": n_stars x n_lines too large");
     }
 
-    pz_ctx *c = new pz_ctx();
     int dev = 0;
-    cudaGetDevice(&dev);
+    PZ_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(PZ_EINVAL, w + ": device ordinal beyond the supported 64");
+    pz_ctx *c = new pz_ctx();
     c->device = dev;
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
     c->prec = prec;
@@ -1114,14 +1146,17 @@ pz_status pz_backward4(pz_ctx *c, const float *dLdf, float *g_gf, float *g_rad, 
 // adjoint -> gradients -> delta -= lr * gradient, enqueued on the capture stream.
 static pz_status enqueue_step(pz_ctx *c, const float *y, const float *w, double *loss, float *g_gf, float *g_g6,
                               float *g_ab, float lr_gf, float lr_g6, float lr_ab, cudaStream_t s) {
-    PZ_CUDA(launch_apply_corrections(c, s), "apply corrections");
-    PZ_CUDA(c->prec == PZ_MIXED ? launch_line_fwd_mixed(c, s) : launch_line_fwd_fp64(c, s), "line opacity kernel");
-    PZ_CUDA(launch_flux(c, s), "flux kernel");
-    PZ_CUDA(launch_inst_apply(c, nullptr, s), "instrument apply");
+    PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_apply_corrections(c, s); }), "apply corrections");
+    PZ_CUDA(timed(c, s, PZ_K_LINE_FWD,
+                  [&] { return c->prec == PZ_MIXED ? launch_line_fwd_mixed(c, s) : launch_line_fwd_fp64(c, s); }),
+            "line opacity kernel");
+    PZ_CUDA(timed(c, s, PZ_K_FLUX, [&] { return launch_flux(c, s); }), "flux kernel");
+    PZ_CUDA(timed(c, s, PZ_K_INSTRUMENT, [&] { return launch_inst_apply(c, nullptr, s); }), "instrument apply");
     if (loss) PZ_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s), "loss");
-    PZ_CUDA(launch_loss(c, y, w, (int64_t)c->S * c->n_out, loss, c->d_dLdf, s), "loss kernel");
+    PZ_CUDA(timed(c, s, PZ_K_LOSS, [&] { return launch_loss(c, y, w, (int64_t)c->S * c->n_out, loss, c->d_dLdf, s); }),
+            "loss kernel");
     PZ_TRY(enqueue_backward(c, c->d_dLdf, g_gf, g_g6, g_ab, s));
-    PZ_CUDA(launch_update(c, lr_gf, lr_g6, lr_ab, s), "update");
+    PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_update(c, lr_gf, lr_g6, lr_ab, s); }), "update");
     return PZ_OK;
 }
 
@@ -1138,26 +1173,29 @@ pz_status pz_calib_step(pz_ctx *c, const float *y, const float *w, int64_t n, fl
     if (!c->d_dLdf) PZ_TRY(dalloc(&c->d_dLdf, (size_t)c->S * c->pix_cap, "step seed"));
     StepGraph &G = c->graph;
     const void *key[6] = {y, w, loss, g_gf, g_g6, g_ab};
-    bool same = G.exec && G.n == n && G.lr[0] == lr_gf && G.lr[1] == lr_g6 && G.lr[2] == lr_ab;
+    bool same = G.exec && G.n == n && G.lr[0] == lr_gf && G.lr[1] == lr_g6 && G.lr[2] == lr_ab &&
+                G.prof == c->profiling;
     for (int k = 0; k < 6 && same; ++k) same = G.key[k] == key[k];
     if (!same) {
         drop_graph(c);
         PZ_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "pz_calib_step: capture");
         c->capturing = true;
         c->launches = 0;
+        c->cap_marks.clear();
         pz_status st = enqueue_step(c, y, w, loss, g_gf, g_g6, g_ab, lr_gf, lr_g6, lr_ab, c->cap_stream);
         c->capturing = false;
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
-        if (st != PZ_OK) {
+        if (st != PZ_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            return st;
+            destroy_marks(c->cap_marks);
+            return st != PZ_OK ? st : cuda_check(e, "pz_calib_step: end capture");
         }
-        if (e != cudaSuccess) return cuda_check(e, "pz_calib_step: end capture");
         e = cudaGraphInstantiate(&G.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             G.exec = nullptr;
+            destroy_marks(c->cap_marks);
             return cuda_check(e, "pz_calib_step: instantiate");
         }
         for (int k = 0; k < 6; ++k) G.key[k] = key[k];
@@ -1166,11 +1204,14 @@ pz_status pz_calib_step(pz_ctx *c, const float *y, const float *w, int64_t n, fl
         G.lr[2] = lr_ab;
         G.n = n;
         G.launches = c->launches;
+        G.prof = c->profiling;
+        G.marks.swap(c->cap_marks);
     }
     cudaEvent_t ev = prof_begin(c, s);
     cudaError_t e = cudaGraphLaunch(G.exec, s);
     prof_end(c, s, PZ_K_STEP, ev);
     PZ_CUDA(e, "pz_calib_step: graph launch");
+    if (c->profiling) fold_graph_marks(c, G);
     c->launches = G.launches;
     c->have_kline = c->have_flux = c->have_inst = true;
     return PZ_OK;
@@ -1251,15 +1292,18 @@ pz_status pz_set_line_groups(pz_ctx *c, const int32_t *group_of_line, int64_t n_
 // four-family reverse pass -> group sums, enqueued on the capture stream.
 static pz_status enqueue_group_eval(pz_ctx *c, const float *y, const float *w, const float *x, double *loss, float *g,
                                     cudaStream_t s) {
-    PZ_CUDA(launch_group_gather(c, x, s), "group corrections");
-    PZ_CUDA(launch_apply_corrections(c, s), "apply corrections");
-    PZ_CUDA(c->prec == PZ_MIXED ? launch_line_fwd_mixed(c, s) : launch_line_fwd_fp64(c, s), "line opacity kernel");
-    PZ_CUDA(launch_flux(c, s), "flux kernel");
-    PZ_CUDA(launch_inst_apply(c, nullptr, s), "instrument apply");
+    PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_group_gather(c, x, s); }), "group corrections");
+    PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_apply_corrections(c, s); }), "apply corrections");
+    PZ_CUDA(timed(c, s, PZ_K_LINE_FWD,
+                  [&] { return c->prec == PZ_MIXED ? launch_line_fwd_mixed(c, s) : launch_line_fwd_fp64(c, s); }),
+            "line opacity kernel");
+    PZ_CUDA(timed(c, s, PZ_K_FLUX, [&] { return launch_flux(c, s); }), "flux kernel");
+    PZ_CUDA(timed(c, s, PZ_K_INSTRUMENT, [&] { return launch_inst_apply(c, nullptr, s); }), "instrument apply");
     if (loss) PZ_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s), "loss");
-    PZ_CUDA(launch_loss(c, y, w, (int64_t)c->S * c->n_out, loss, c->d_dLdf, s), "loss kernel");
+    PZ_CUDA(timed(c, s, PZ_K_LOSS, [&] { return launch_loss(c, y, w, (int64_t)c->S * c->n_out, loss, c->d_dLdf, s); }),
+            "loss kernel");
     PZ_TRY(enqueue_backward(c, c->d_dLdf, nullptr, nullptr, nullptr, s, true, nullptr, nullptr));
-    if (g) PZ_CUDA(launch_group_reduce(c, g, s), "group gradients");
+    if (g) PZ_CUDA(timed(c, s, PZ_K_OTHER, [&] { return launch_group_reduce(c, g, s); }), "group gradients");
     return PZ_OK;
 }
 
@@ -1275,37 +1319,43 @@ pz_status pz_group_eval(pz_ctx *c, const float *y, const float *w, int64_t n, co
     if (!c->d_dLdf) PZ_TRY(dalloc(&c->d_dLdf, (size_t)c->S * c->pix_cap, "step seed"));
     StepGraph &G = c->ggraph;
     const void *key[6] = {y, w, x, loss, g, nullptr};
-    bool same = G.exec && G.n == n;
+    bool same = G.exec && G.n == n && G.prof == c->profiling;
     for (int k = 0; k < 6 && same; ++k) same = G.key[k] == key[k];
     if (!same) {
         if (G.exec) cudaGraphExecDestroy(G.exec);
+        destroy_marks(G.marks);
         G = StepGraph();
         PZ_CUDA(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "pz_group_eval: capture");
         c->capturing = true;
         c->launches = 0;
+        c->cap_marks.clear();
         pz_status st = enqueue_group_eval(c, y, w, x, loss, g, c->cap_stream);
         c->capturing = false;
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamEndCapture(c->cap_stream, &graph);
-        if (st != PZ_OK) {
+        if (st != PZ_OK || e != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
-            return st;
+            destroy_marks(c->cap_marks);
+            return st != PZ_OK ? st : cuda_check(e, "pz_group_eval: end capture");
         }
-        if (e != cudaSuccess) return cuda_check(e, "pz_group_eval: end capture");
         e = cudaGraphInstantiate(&G.exec, graph, 0);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) {
             G.exec = nullptr;
+            destroy_marks(c->cap_marks);
             return cuda_check(e, "pz_group_eval: instantiate");
         }
         for (int k = 0; k < 6; ++k) G.key[k] = key[k];
         G.n = n;
         G.launches = c->launches;
+        G.prof = c->profiling;
+        G.marks.swap(c->cap_marks);
     }
     cudaEvent_t ev = prof_begin(c, s);
     cudaError_t e = cudaGraphLaunch(G.exec, s);
     prof_end(c, s, PZ_K_STEP, ev);
     PZ_CUDA(e, "pz_group_eval: graph launch");
+    if (c->profiling) fold_graph_marks(c, G);
     c->launches = G.launches;
     c->have_kline = c->have_flux = c->have_inst = true;
     return PZ_OK;

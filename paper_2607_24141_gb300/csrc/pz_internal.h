@@ -29,6 +29,8 @@ constexpr double kC2 = kH * kC / kKB;       // second radiation constant, cm K
 constexpr int kMaxDepth = 128;
 // Largest number of instrument taps per pixel.
 constexpr int kMaxTaps = 4096;
+// Device ordinals a context may live on (per-device launch-attribute bookkeeping).
+constexpr int kMaxDevices = 64;
 
 // Far-wing / mid / core boundaries of the FP32 Voigt (|z|^2 thresholds).
 constexpr float kFar2 = 400.0f;   // |z| >= 20: asymptotic series, 2 corrections
@@ -80,14 +82,24 @@ struct LineTable {
     float *dgrad = nullptr, *dg4 = nullptr;
 };
 
+// A pair of profiler events around one launch and the kernel family it times.
+struct ProfMark {
+    cudaEvent_t a, b;
+    int kid;
+};
+
 // Captured corrections + fwd + loss + bwd + update step (pz_calib_step), re-captured
-// when any of its arguments changes.
+// when any of its arguments changes or profiling is switched.  With profiling on at
+// capture, the graph records its own event pairs around each kernel family (marks),
+// read after every launch.
 struct StepGraph {
     cudaGraphExec_t exec = nullptr;
     const void *key[6] = {nullptr};
     float lr[3] = {0.0f, 0.0f, 0.0f};
     int64_t n = -1;
     int32_t launches = 0;
+    bool prof = false;
+    std::vector<ProfMark> marks;
 };
 
 }  // namespace pz
@@ -196,15 +208,12 @@ struct pz_ctx {
     pz::StepGraph graph;
     pz::StepGraph ggraph;                // captured group evaluation (pz_group_eval)
     cudaStream_t cap_stream = nullptr;   // private stream the step graph is captured on
-    bool capturing = false;              // profiler off while capturing
+    bool capturing = false;              // a step graph is being captured
 
     // CUDA-event profiler (pz_set_profiling)
     bool profiling = false;
-    struct Mark {
-        cudaEvent_t a, b;
-        int kid;
-    };
-    std::vector<Mark> marks;          // recorded, not yet folded
+    std::vector<pz::ProfMark> marks;      // recorded, not yet folded
+    std::vector<pz::ProfMark> cap_marks;  // recorded into the graph being captured
     std::vector<cudaEvent_t> ev_pool; // free events
     double k_ms[PZ_NK] = {0};
     int64_t k_count[PZ_NK] = {0};

@@ -23,6 +23,8 @@
 // cancellation of lambda_l/lambda_i - 1.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include <algorithm>
 #include <cmath>
 #include <mutex>
@@ -1527,11 +1529,11 @@ static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
         g.ngroups = (c->nd + kNearDepthsBwd - 1) / kNearDepthsBwd;
         g.ctr = c->d_ctr + 3;
         constexpr size_t smem = near_smem<T, kNearDepthsBwd, true>();
-        static bool attr_set[64] = {false};
-        if (!attr_set[c->device]) {
+        static std::atomic<bool> attr_set[kMaxDevices];
+        if (!attr_set[c->device].load(std::memory_order_acquire)) {
             cudaFuncSetAttribute(k_line_near_bwd<T, kNearDepthsBwd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
-            attr_set[c->device] = true;
+            attr_set[c->device].store(true, std::memory_order_release);
         }
         int grid = persistent_grid(c, k_line_near_bwd<T, kNearDepthsBwd>, 32 * kNearWarps, smem, g.n_items);
         cudaEvent_t ev = prof_begin(c, s);
@@ -1544,11 +1546,11 @@ static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
         g.ngroups = (c->nd + kNearDepthsFwd - 1) / kNearDepthsFwd;
         g.ctr = c->d_ctr + 0;
         constexpr size_t smem = near_smem<T, kNearDepthsFwd, false>();
-        static bool attr_set[64] = {false};
-        if (!attr_set[c->device]) {
+        static std::atomic<bool> attr_set[kMaxDevices];
+        if (!attr_set[c->device].load(std::memory_order_acquire)) {
             cudaFuncSetAttribute(k_line_near_fwd<T, kNearDepthsFwd>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
-            attr_set[c->device] = true;
+            attr_set[c->device].store(true, std::memory_order_release);
         }
         int grid = persistent_grid(c, k_line_near_fwd<T, kNearDepthsFwd>, 32 * kNearWarps, smem, g.n_items);
         cudaEvent_t ev = prof_begin(c, s);
@@ -1603,10 +1605,10 @@ static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
     const Tiling &t = c->tiling;
     LineArgs g = make_args(c);
     const size_t smem = far_fwd_smem(t);
-    static bool attr_set[64] = {false};
-    if (!attr_set[c->device]) {
+    static std::atomic<bool> attr_set[kMaxDevices];
+    if (!attr_set[c->device].load(std::memory_order_acquire)) {
         cudaFuncSetAttribute(k_line_fwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFarSmemMax);
-        attr_set[c->device] = true;
+        attr_set[c->device].store(true, std::memory_order_release);
     }
     cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -1636,10 +1638,10 @@ static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
     const Tiling &t = c->tiling;
     LineArgs g = make_args(c);
     const size_t smem = far_bwd_smem(t);
-    static bool attr_set[64] = {false};
-    if (!attr_set[c->device]) {
+    static std::atomic<bool> attr_set[kMaxDevices];
+    if (!attr_set[c->device].load(std::memory_order_acquire)) {
         cudaFuncSetAttribute(k_line_bwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFarSmemMax);
-        attr_set[c->device] = true;
+        attr_set[c->device].store(true, std::memory_order_release);
     }
     cudaError_t e = cudaMemsetAsync(c->d_ctr + 2, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;

@@ -173,5 +173,7 @@ def test_gradients_with_scattering_against_differences(oracle):
                 c = {k: vv.copy() for k, vv in corr.items()}
                 c[key] = v
                 return oracle.chi2(y, w, oracle.forward(prob, c)["f"])[0]
-            fd = _cd(L_at, corr[key], j, 1e-4)
+            # steps 5e-4 and 1e-3: the chi^2 of the solved scattering source carries FP64
+            # rounding noise near 1e-13 of its value, which swamps a quotient at 1e-4
+            fd = _cd(L_at, corr[key], j, 5e-4)
             assert abs(g[j] - fd) <= 1e-6 * max(abs(fd), 1e-3 * np.max(np.abs(g))), (key, j, g[j], fd)
