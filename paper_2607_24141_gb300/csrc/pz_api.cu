@@ -338,14 +338,14 @@ static void destroy_ctx(pz_ctx *c) {
     if (!c) return;
     drop_graph(c);
     void *ptrs[] = {c->d_m, c->d_T, c->d_beta_hi, c->d_beta_lo, c->d_ne, c->d_npert, c->d_c2T, c->d_ne64,
-                    c->d_npert64, c->d_rho64, c->d_R, c->d_Rbase, c->d_invdv, c->d_pop64, c->d_mass64, c->d_xi64,
+                    c->d_npert64, c->d_rho64, c->d_R, c->d_Rbase, c->d_invdv, c->d_Ksd, c->d_pop64, c->d_mass64, c->d_xi64,
                     c->d_thr, c->d_kc, c->d_dab, c->d_mdgf, c->d_mdg6, c->d_eos, c->L.orig, c->L.star, c->L.ilf,
                     c->L.il32, c->L.frac, c->L.sp, c->L.E, c->L.lamcm, c->L.grad, c->L.g4, c->L.g6base, c->L.g6,
                     c->L.Q, c->L.Qbase, c->L.x64, c->L.lg_gf, c->L.lg_rad, c->L.lg_4, c->L.lg_6, c->L.dgf, c->L.dg6,
                     c->d_line_off, c->d_fitems, c->d_fext, c->d_bitems, c->d_fpart, c->d_fcnt, c->d_nitems_f,
                     c->d_nitems_b, c->d_ctr, c->d_knear, c->d_kline,
                     c->d_F, c->d_Fc, c->d_g, c->d_gc, c->d_tap0, c->d_ntap, c->d_tapw, c->d_dFbar, c->d_Gt,
-                    c->d_Gt64, c->d_gacc, c->d_gline, c->d_gab, c->d_dLdf, c->d_ftab, c->d_finfo, c->d_status,
+                    c->d_Gt64, c->d_gacc, c->d_gline, c->d_gab, c->d_dLdf, c->d_finfo, c->d_status,
                     c->d_keep, c->L.gradbase, c->L.g4base, c->L.dgrad, c->L.dg4, c->d_mdgrad, c->d_mdg4,
                     c->d_grp_of, c->d_grp_off, c->d_grp_mem, c->d_sigma};
     for (void *p : ptrs) dfree(p);
@@ -530,7 +530,7 @@ static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, 
     const size_t SD = (size_t)S * nd, SSD = (size_t)S * ns * nd;
     c->h_m.resize(SD);
     c->h_T.resize(SD);
-    std::vector<float> bh(SD), bl(SD), ne(SD), npert(SD), c2T(SD), invdv(SSD), Rf(SSD);
+    std::vector<float> bh(SD), bl(SD), ne(SD), npert(SD), c2T(SD), invdv(SSD), Ksd(SSD), Rf(SSD);
     std::vector<double> ne64(SD), np64(SD), rho64(SD), Rb(SSD), pop64(SSD), mass64((size_t)S * ns), xi64(S);
     for (int st = 0; st < S; ++st) {
         const pz_atmos *at = atv + st;
@@ -555,6 +555,9 @@ static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, 
                 double dv = std::sqrt(2.0 * kKB * at->T[d] / (at->mass_amu[s] * kAMU) + at->xi_cms * at->xi_cms);
                 const size_t id = (size_t)s * nd + d, o = (size_t)st * ns * nd + id;
                 invdv[o] = (float)(1.0 / dv);
+                // K = 2^36/k^2 of the far-wing prefactors, k = c/dv_D rounded as the kernels form it
+                const float kf = (float)kC * invdv[o];
+                Ksd[o] = kKScale / (kf * kf);
                 pop64[o] = at->pop[id];
                 Rb[o] = (1.0 / dv) * at->pop[id] / at->rho[d];
                 Rf[o] = (float)Rb[o];
@@ -567,7 +570,8 @@ static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, 
     if (upload(&c->d_m, c->h_m, "depth") || upload(&c->d_T, c->h_T, "depth") || upload(&c->d_beta_hi, bh, "depth") ||
         upload(&c->d_beta_lo, bl, "depth") || upload(&c->d_ne, ne, "depth") || upload(&c->d_npert, npert, "depth") ||
         upload(&c->d_c2T, c2T, "depth") || upload(&c->d_ne64, ne64, "depth") || upload(&c->d_npert64, np64, "depth") ||
-        upload(&c->d_rho64, rho64, "depth") || upload(&c->d_invdv, invdv, "species") || upload(&c->d_R, Rf, "species") ||
+        upload(&c->d_rho64, rho64, "depth") || upload(&c->d_invdv, invdv, "species") || upload(&c->d_Ksd, Ksd, "species") ||
+        upload(&c->d_R, Rf, "species") ||
         upload(&c->d_Rbase, Rb, "species") || upload(&c->d_pop64, pop64, "species") ||
         upload(&c->d_mass64, mass64, "species") || upload(&c->d_xi64, xi64, "species") || build_thresholds(c) ||
         upload(&c->d_dab, dab, "abund") || upload(&c->d_eos, eos, "abund"))
@@ -626,20 +630,10 @@ static pz_status ensure_backward_buffers(pz_ctx *c) {
     return PZ_OK;
 }
 
-// Far-wing prefactor table and line records for the current tiling (mixed form).
+// Far-wing line records for the current tiling (mixed form), one per depth group and line.
 // Allocated here, outside any stream capture, and grown only when a tiling needs more.
 static pz_status ensure_far_tables(pz_ctx *c) {
-    const size_t tb = far_table_bytes(c), ib = far_info_bytes(c);
-    if (c->ftab_cap < tb) {
-        dfree(c->d_ftab);
-        c->d_ftab = nullptr;
-        c->ftab_cap = 0;
-        if (cudaMalloc(&c->d_ftab, tb) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(PZ_ENOMEM, "far-wing table: cudaMalloc failed");
-        }
-        c->ftab_cap = tb;
-    }
+    const size_t ib = far_info_bytes(c);
     if (c->finfo_cap < ib) {
         dfree(c->d_finfo);
         c->d_finfo = nullptr;

@@ -43,6 +43,9 @@ constexpr int kDawsonNodes = 6 * kDawsonPerUnit + 1;
 constexpr int kWeidN = 16;        // Weideman rational order (FP32 core)
 constexpr int kWeidN64 = 32;      // Weideman rational order (FP64 plain form)
 
+// Scale of the far-wing prefactors and offsets: K = 2^36/k^2 with k = c/dv_D, U = 2^36 u^2.
+constexpr float kKScale = 68719476736.0f;
+
 // Mixed-precision line-kernel tiling.
 struct Tiling {
     int J = 4;       // lambda points per thread (contiguous)
@@ -131,6 +134,7 @@ struct pz_ctx {
     float *d_R = nullptr;           // [S][ns][nd] (1/dv_D) (pop/rho) 10^dabund
     double *d_Rbase = nullptr;      // [S][ns][nd] (1/dv_D)(pop/rho), FP64
     float *d_invdv = nullptr;       // [S][ns][nd] 1/dv_D (s/cm)
+    float *d_Ksd = nullptr;         // [S][ns][nd] K = 2^36/k^2, k = c/dv_D (far-wing prefactors)
     double *d_pop64 = nullptr;      // [S][ns][nd]
     double *d_mass64 = nullptr;     // [S][ns]
     double *d_xi64 = nullptr;       // [S]
@@ -198,9 +202,8 @@ struct pz_ctx {
     // state
     bool have_kline = false, have_flux = false, have_inst = false;
     bool have_gt = false;                // G (dL/dkappa_line) holds a reverse pass
-    void *d_ftab = nullptr;              // far-wing prefactor table (sized for the backward's layout)
-    void *d_finfo = nullptr;             // far-wing line records
-    size_t ftab_cap = 0, finfo_cap = 0;  // their sizes in bytes
+    void *d_finfo = nullptr;             // far-wing line records [depth groups][lines]
+    size_t finfo_cap = 0;                // its size in bytes
     int32_t *d_status = nullptr;         // device status word (bounded-wait failures), read by pz_sync_status
     uint32_t *d_keep = nullptr;          // centre test: bit d of word [l][d / 32] set if (l, d) is kept; NULL = off
     double centre_eta = 0.0;             // its selection fraction (0 = off)
@@ -263,7 +266,6 @@ constexpr int kKeepWords = kMaxDepth / 32;   // centre-test mask words per line
 cudaError_t launch_centre_mask(pz_ctx *c, double eta, unsigned long long *d_count, cudaStream_t s);
 bool tiling_supported(int J, int DS, int minb);
 bool tiling_fits(const Tiling &t);   // both far-wing chunks fit in shared memory
-size_t far_table_bytes(const pz_ctx *c);   // far-wing table bytes for the current tiling
 size_t far_info_bytes(const pz_ctx *c);
 
 }  // namespace pz

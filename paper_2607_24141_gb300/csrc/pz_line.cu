@@ -141,6 +141,7 @@ struct LineArgs {
     const float *ilf, *frac, *E, *lamcm, *grad, *g4, *g6, *Q;
     const int32_t *sp;
     const float *R, *invdv, *thr;                   // [ns][nd], [ns][nd], [ns][nslab] of the star
+    const float *Ksd;                               // [ns][nd] K = 2^36/k^2 of the star
     int nslab;
     const float *beta_hi, *beta_lo, *ne, *npert, *c2T;   // [nd] of the star
     float *kline;                                   // forward output [nd][ld] of the star
@@ -158,8 +159,7 @@ struct LineArgs {
     int64_t sstride, dstride, bstride, tstride;     // per-star strides of the tables above
     float rj[4], rm1j[4];                           // r^-j and r^-j - 1, j = 0..3 (r = 1 + 1/R)
     const int32_t *star;                            // [nl] star of each line
-    const float4 *ftab;                             // far-wing prefactor table (k_far_table)
-    const LineInfo *finfo;                          // far-wing line records
+    const LineInfo *finfo;                          // far-wing line records [ngroups][nl] (k_far_info)
     int *status;                                    // device status word (bounded-wait failures)
     const uint32_t *keep;                           // centre-test mask [nl][kKeepWords] or NULL (all kept)
     int dsel;                                       // backward: damping family of the second sum
@@ -175,6 +175,7 @@ __device__ __forceinline__ LineArgs star_view(const LineArgs &g, int s) {
     LineArgs v = g;
     v.R += s * g.sstride;
     v.invdv += s * g.sstride;
+    v.Ksd += s * g.sstride;
     v.thr += s * g.tstride;
     v.beta_hi += s * g.dstride;
     v.beta_lo += s * g.dstride;
@@ -336,27 +337,28 @@ __device__ __forceinline__ float f2_lo(f2_t v) {
     return lo;
 }
 
-// ---- far-wing prefactor tables ----------------------------------------------
-// Before each far-wing launch k_far_table writes, for every depth group g of DC
-// layers and every line l, the (DC/2) depth pairs of NQ quads, quad q holding
-// {p_2q(d), p_2q(d + 1), p_2q+1(d), p_2q+1(d + 1)} (one 16-byte load returns the
-// packed depth pairs of two parameters):
+// ---- far-wing prefactors ------------------------------------------------------
+// A far-wing CTA stages LC lines at a time.  For each line of the chunk and each of
+// the (DC/2) depth pairs of its group it forms NQ quads, quad q holding
+// {p_2q(d), p_2q(d + 1), p_2q+1(d), p_2q+1(d + 1)} (one 16-byte shared-memory load
+// returns the packed depth pairs of two parameters):
 //   forward  (NQ = 2): (K, a^2) (B1 K, B2' K^2)
 //   backward (NQ = 3): (K, a^2) (B1 K, B2' K^2) (C1 K, C2' K^2)
-// with k = c/dv_D, K = 2^36/k^2 (the power of two keeps every product of the table
-// and of the offsets far from the FP32 exponent limits), B2' = B2 - B1 a^2 =
-// B1 (1.5 - a^2) and C2' = C2 - C1 a^2 = C1 (1.5 - 3a^2).  The far kernels take the
+// with k = c/dv_D, K = 2^36/k^2 (the power of two keeps every product of the
+// prefactors and of the offsets far from the FP32 exponent limits), B2' = B2 - B1 a^2
+// = B1 (1.5 - a^2) and C2' = C2 - C1 a^2 = C1 (1.5 - 3a^2).  The far kernels take the
 // squared offsets scaled alike, U = 2^36 u^2, so that with s = 1/U
 //   reduced form:  H sqrt(pi)/A = (B1 K) s + (B2' K^2) s^2   (p = K s exactly, see below)
 //   full form:     r = 1/(U + a^2 K) and t = 1/|z|^2 = K r, so B1 t (...) = (B1 K) r (...)
 // and the masked lines recover B1 = (B1 K) k^2 2^-36 (and C1 alike) per depth pair.
-// The table sits at tab[(g n_lines + l) (DC/2) NQ + pair NQ + q], the line record at
-// info[g n_lines + l].  The rest of the far polynomial (B3..B5, C3..C6) follows
-// from a^2 and B1 K (C1 K) in registers.  The chunk of LC lines a CTA needs is then
-// one contiguous block, which the kernels move into shared memory with bulk
-// copies (cp.async.bulk, completion on an mbarrier), double-buffered.
+// Each warp stages the quads of its own slab, par[li][pair][q] in its part of shared
+// memory; the rest of the far polynomial (B3..B5, C3..C6) follows from a^2 and B1 K
+// (C1 K) in registers.  Lane li computes line li's quads from the line data and the
+// star's per-(species, depth) tables (Eqs. 4-5, with the roundings of depth_params), so
+// no per-(line, depth) array exists in device memory: the quads are recomputed for each
+// tile the line's window reaches.  The only per-line device array of the far kernels is
+// the 16-byte line record of each depth group (k_far_info).
 constexpr int kNQF = 2, kNQB = 3;
-constexpr float kKScale = 68719476736.0f;         // 2^36: K = 2^36/k^2, U = 2^36 u^2
 constexpr float kUScale = 262144.0f;              // 2^18: scaled offset u 2^18
 constexpr float kKUnscale = 1.4551915228366852e-11f;   // 2^-36
 
@@ -388,64 +390,129 @@ constexpr float kFast2V = 5.0f;      // distance threshold factor: |v| >= 5 x 20
 constexpr float kFast3V = 1.5f;      // distance threshold factor: |v| >= 1.5 x 20
 constexpr float kFast2A2 = 1.5f;     // a^2 bound
 
-// One thread per (group, line, depth pair); the thread of pair 0 also writes the
-// line record, whose amask has bit w set when a^2 <= kFast2A2 at every layer of
-// slab w (DS layers) of the group.
-template <int NQ>
-__global__ void k_far_table(LineArgs gq, int DC, int DS, int ngroups, float4 *tab, LineInfo *info) {
-    const int P = DC / 2;
-    const int64_t n = (int64_t)ngroups * gq.nl * P;
-    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
-         idx += (int64_t)gridDim.x * blockDim.x) {
-        const int pr = (int)(idx % P);
-        const int64_t gl = idx / P;
+// One thread per (group, line): the line record, whose amask has bit w set when
+// a^2 <= kFast2A2 at every layer of slab w (DS layers) of the group, and bit 8 + w when
+// the centre test rejects every layer of slab w (its warp skips the line).
+__global__ void k_far_info(LineArgs gq, int DC, int DS, int ngroups, LineInfo *info) {
+    const int64_t n = (int64_t)ngroups * gq.nl;
+    for (int64_t gl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gl < n; gl += (int64_t)gridDim.x * blockDim.x) {
         const int64_t l = gl % gq.nl;
         const int grp = (int)(gl / gq.nl);
         const LineArgs g = star_view(gq, gq.star[l]);
         const LineScalars L = load_line(g, l);
-        const int d = grp * DC + 2 * pr;
-        float p0[16], p1[16];
-        depth_params<NQ == kNQB ? 16 : 8>(g, L, d, p0);
-        depth_params<NQ == kNQB ? 16 : 8>(g, L, d + 1, p1);
-        // pairs rejected by the centre test contribute nothing: zero strength coefficients
-        if (!pair_kept(g.keep, l, d)) p0[2] = p0[3] = p0[8] = p0[9] = 0.0f;
-        if (!pair_kept(g.keep, l, d + 1)) p1[2] = p1[3] = p1[8] = p1[9] = 0.0f;
-        float4 *dst = tab + gl * (P * NQ) + pr * NQ;
-        // K = 2^36/k^2 (0 on the padding layers past the last one, whose coefficients are 0)
-        const float K0 = p0[0] > 0.0f ? kKScale / (p0[0] * p0[0]) : 0.0f;
-        const float K1 = p1[0] > 0.0f ? kKScale / (p1[0] * p1[0]) : 0.0f;
-        const float KK0 = K0 * K0, KK1 = K1 * K1;
-        dst[0] = make_float4(K0, K1, p0[1], p1[1]);
-        // (B1 K, B2' K^2) with B2' = B2 - B1 a^2, and (C1 K, C2' K^2) with C2' = C2 - C1 a^2
-        dst[1] = make_float4(p0[2] * K0, p1[2] * K1, fmaf(-p0[2], p0[1], p0[3]) * KK0, fmaf(-p1[2], p1[1], p1[3]) * KK1);
-        if (NQ == kNQB)
-            dst[2] = make_float4(p0[8] * K0, p1[8] * K1, fmaf(-p0[8], p0[1], p0[9]) * KK0,
-                                 fmaf(-p1[8], p1[1], p1[9]) * KK1);
-        if (pr == 0) {
-            // bit w: a^2 <= kFast2A2 on every layer of slab w; bit 8 + w: the centre test
-            // rejects every layer of slab w (its warp skips the line)
-            int amask = 0;
-            for (int w = 0; w < DC / DS; ++w) {
-                bool ok = true, none = true;
-                for (int dd = grp * DC + w * DS; dd < min(grp * DC + (w + 1) * DS, g.nd); ++dd) {
-                    float q[16];
-                    depth_params<8>(g, L, dd, q);
-                    ok = ok && q[1] <= kFast2A2;
-                    none = none && !pair_kept(g.keep, l, dd);
-                }
-                amask |= (ok ? 1 << w : 0) | (none ? 1 << (8 + w) : 0);
+        int amask = 0;
+        for (int w = 0; w < DC / DS; ++w) {
+            bool ok = true, none = true;
+            for (int dd = grp * DC + w * DS; dd < min(grp * DC + (w + 1) * DS, g.nd); ++dd) {
+                float q[16];
+                depth_params<8>(g, L, dd, q);
+                ok = ok && q[1] <= kFast2A2;
+                none = none && !pair_kept(g.keep, l, dd);
             }
-            LineInfo r;
-            r.ilf = g.ilf[l];
-            r.frac = g.frac[l];
-            r.sp = L.sp;
-            r.amask = amask;
-            info[gl] = r;
+            amask |= (ok ? 1 << w : 0) | (none ? 1 << (8 + w) : 0);
         }
+        LineInfo r;
+        r.ilf = g.ilf[l];
+        r.frac = g.frac[l];
+        r.sp = L.sp;
+        r.amask = amask;
+        info[gl] = r;
     }
 }
 
-// ---- bulk-copy staging ------------------------------------------------------
+// Prefactors of line l at layer d (one half of a depth pair), with the roundings of
+// depth_params for k and a^2 (the cells' near / far classification depends on them):
+// K = 2^36/k^2, a^2, B1 K, B2' K^2 and (NQ = kNQB) C1 K, C2' K^2.  dc holds the layer's
+// {beta_hi, beta_lo, n_e, n_pert}.  Layers past the last one get K = 0, a^2 = 1 and zero
+// coefficients, pairs rejected by the centre test zero coefficients.
+template <int NQ>
+__device__ __forceinline__ void far_depth_prefactors(const LineArgs &g, const LineScalars &L, int64_t l, int d,
+                                                     const float4 dc, float &K, float &a2, float &b1, float &b2,
+                                                     float &c1, float &c2) {
+    if (d >= g.nd) {
+        K = 0.0f;
+        a2 = 1.0f;
+        b1 = b2 = c1 = c2 = 0.0f;
+        return;
+    }
+    const int id = L.sp * g.nd + d;
+    const float invdv = __ldg(g.invdv + id);
+    const float p = L.E * dc.x;
+    const float r = fmaf(L.E, dc.x, -p) + L.E * dc.y;      // E beta = p + r
+    const float boltz = expf(-p) * (1.0f - r);
+    const float A = L.Q * __ldg(g.R + id) * boltz;
+    const float lw = __fmul_rn(__fmul_rn(L.lamcm, invdv), (float)(1.0 / (4.0 * kPI)));
+    const float g6n = __fmul_rn(L.g6, dc.w);
+    const float a = __fmul_rn(fmaf(L.g4, dc.z, __fadd_rn(L.grad, g6n)), lw);
+    a2 = __fmul_rn(a, a);
+    K = __ldg(g.Ksd + id);
+    const float KK = K * K;
+    const bool kept = pair_kept(g.keep, l, d);
+    const float B1 = kept ? A * a * kInvSqrtPiF : 0.0f;
+    b1 = B1 * K;
+    b2 = fmaf(-B1, a2, 1.5f * B1) * KK;
+    if (NQ == kNQB) {
+        const float gb = g.dsel == 0 ? g6n : (g.dsel == 1 ? L.grad : __fmul_rn(L.g4, dc.z));
+        const float C1 = kept ? A * gb * lw * kInvSqrtPiF : 0.0f;
+        c1 = C1 * K;
+        c2 = fmaf(-C1, a2, fmaf(-2.0f, a2, 1.5f) * C1) * KK;
+    } else {
+        c1 = c2 = 0.0f;
+    }
+}
+
+// Per-warp staging of a chunk of lines.  Each warp keeps, in its own part of shared
+// memory, the layer constants of its slab (dc: DS x {beta_hi, beta_lo, n_e, n_pert}),
+// and for the chunk's lines their records and the prefactor quads of its DP depth pairs
+// (par: [LC][DP][NQ]).  Lane li fills line li (li + 32, ... for chunks over 32 lines); a
+// warp barrier publishes the chunk, and the next fill waits on a warp barrier so that
+// no lane still reads the previous chunk.  No CTA-wide barrier is involved.
+struct WarpStage {
+    float4 *dc;          // [DS]
+    float4 *par;         // [LC][DP * NQ]
+    LineInfo *info;      // [LC]
+};
+
+__host__ __device__ constexpr size_t warp_stage_quads(int LC, int DS, int NQ) {
+    return (size_t)DS + (size_t)LC * (DS / 2) * NQ + (size_t)LC;
+}
+
+template <int DS>
+__device__ __forceinline__ void warp_stage_depths(const LineArgs &g, const WarpStage &ws, int dfirst, int lane) {
+    __syncwarp();
+    if (lane < DS) {
+        const int d = dfirst + lane;
+        ws.dc[lane] = d < g.nd ? make_float4(__ldg(g.beta_hi + d), __ldg(g.beta_lo + d), __ldg(g.ne + d),
+                                              __ldg(g.npert + d))
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    __syncwarp();
+}
+
+template <int NQ, int DS>
+__device__ __forceinline__ void warp_fill(const LineArgs &g, const WarpStage &ws, const LineInfo *ginfo,
+                                          int64_t first, int nl, int dfirst, int lane) {
+    constexpr int DP = DS / 2;
+    __syncwarp();
+    for (int li = lane; li < nl; li += 32) {
+        const int64_t l = first + li;
+        ws.info[li] = ginfo[l];
+        const LineScalars L = load_line(g, l);
+        float4 *dst = ws.par + (size_t)li * DP * NQ;
+#pragma unroll
+        for (int dp = 0; dp < DP; ++dp) {
+            float K0, K1, a0, a1, b10, b11, b20, b21, c10, c11, c20, c21;
+            far_depth_prefactors<NQ>(g, L, l, dfirst + 2 * dp, ws.dc[2 * dp], K0, a0, b10, b20, c10, c20);
+            far_depth_prefactors<NQ>(g, L, l, dfirst + 2 * dp + 1, ws.dc[2 * dp + 1], K1, a1, b11, b21, c11, c21);
+            dst[NQ * dp] = make_float4(K0, K1, a0, a1);
+            dst[NQ * dp + 1] = make_float4(b10, b11, b20, b21);
+            if (NQ == kNQB) dst[NQ * dp + 2] = make_float4(c10, c11, c20, c21);
+        }
+    }
+    __syncwarp();
+}
+
+// ---- mbarrier waits (the bounded-wait probe) ---------------------------------
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar) {
@@ -478,57 +545,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
     }
 }
 
-// One thread: copy a chunk (its quads, then its line records) into shared memory,
-// completing on `bar`.  The proxy fence orders the generic-proxy reads of the previous
-// use of the buffer (made visible by the CTA barrier the caller passed) before the
-// asynchronous writes.
-__device__ __forceinline__ void issue_chunk(uint64_t *bar, float4 *dst_par, const float4 *src_par, uint32_t par_bytes,
-                                            float4 *dst_info, const void *src_info, uint32_t info_bytes) {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(par_bytes + info_bytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst_par)),
-                 "l"(src_par), "r"(par_bytes), "r"(smem_addr(bar))
-                 : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     smem_addr(dst_info)),
-                 "l"(src_info), "r"(info_bytes), "r"(smem_addr(bar))
-                 : "memory");
-}
-
-// Double-buffered chunk pipeline of one CTA.  Buffer b holds [LC][PQ] quads followed
-// by [LC] line records.  cc counts the chunks the CTA has consumed (every thread keeps
-// the same count): chunk number cc uses buffer cc & 1 and phase (cc >> 1) & 1 of that
-// buffer's barrier.
-struct ChunkPipe {
-    uint64_t *bar;       // [2]
-    float4 *buf;         // 2 x LC x (PQ + 1) quads
-    int LC, PQ;
-    unsigned cc;
-    __device__ float4 *par(unsigned k) const { return buf + (size_t)(k & 1) * LC * (PQ + 1); }
-    __device__ const LineInfo *info(unsigned k) const {
-        return reinterpret_cast<const LineInfo *>(par(k) + (size_t)LC * PQ);
-    }
-    __device__ void issue(unsigned k, const float4 *tab, const LineInfo *linfo, int64_t first, int n) const {
-        issue_chunk(bar + (k & 1), par(k), tab + first * PQ, (uint32_t)(n * PQ * 16), par(k) + (size_t)LC * PQ,
-                    linfo + first, (uint32_t)(n * 16));
-    }
-};
-
-constexpr uint64_t kWaitLimitNs = 1000000000ull;   // bounded waits give up after 1 s
-constexpr int kStatusFarWait = 1;                   // status bit: a far-wing chunk never arrived
-
-// Give up after a timed-out wait: record it, let the CTA's copies in flight land
-// (bounded again) and tell the caller to stop.
-__device__ __forceinline__ void far_abort(const LineArgs &g, const ChunkPipe &cp, unsigned k) {
-    if (threadIdx.x == 0) {
-        atomicOr(g.status, kStatusFarWait);
-        mbar_wait(cp.bar + (k & 1), (k >> 1) & 1, kWaitLimitNs);
-    }
-    __syncthreads();
-}
+constexpr int kStatusFarWait = 1;                   // status bit: a bounded wait gave up
 
 // Per-warp flags of a line over the tile (4: every layer of the slab rejected by the
 // centre test, nothing to evaluate): bit 0 if the line's window covers the tile
@@ -593,7 +610,8 @@ __device__ __forceinline__ void far_c3456(f2_t a2, f2_t C1, f2_t &C3, f2_t &C4, 
 // Returns false if a chunk never arrived (the kernel stops).
 template <int J, int DS>
 __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, const int group, const int lo,
-                                             const int hi, const int GW, ChunkPipe &cp, const int4 ext) {
+                                             const int hi, const int GW, const int LC, const WarpStage &ws,
+                                             float *s_comp, const int4 ext) {
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
     static_assert(DS % 2 == 0, "DS must be even (depth pairs)");
     constexpr int DP = DS / 2;          // depth pairs per warp
@@ -601,8 +619,6 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
     const int T = 32 * J;
     const int DC = GW * DS;
     const int nthr = blockDim.x;
-    float *s_comp = reinterpret_cast<float *>(cp.buf + (size_t)2 * cp.LC * (cp.PQ + 1));   // [DS][nthr][8]
-    const float4 *gtab = g.ftab + (int64_t)group * g.nl * cp.PQ;
     const LineInfo *ginfo = g.finfo + (int64_t)group * g.nl;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -625,23 +641,13 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
         cs[1] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
-    const int nch = (hi - lo + cp.LC - 1) / cp.LC;
-    if (tid == 0 && nch > 0) cp.issue(cp.cc, gtab, ginfo, lo, min(cp.LC, hi - lo));
+    warp_stage_depths<DS>(g, ws, d0 + warp * DS, lane);
+    const int nch = (hi - lo + LC - 1) / LC;
     for (int c = 0; c < nch; ++c) {
-        const unsigned k = cp.cc + c;
-        const bool ok = mbar_wait(cp.bar + (k & 1), (k >> 1) & 1, kWaitLimitNs);
-        if (__syncthreads_or(!ok)) {
-            far_abort(g, cp, k);
-            return false;
-        }
-        // the other buffer is free (every thread is past its chunk): prefetch the next chunk
-        if (tid == 0 && c + 1 < nch) {
-            const int n1 = lo + (c + 1) * cp.LC;
-            cp.issue(k + 1, gtab, ginfo, n1, min(cp.LC, hi - n1));
-        }
-        const int nl = min(cp.LC, hi - (lo + c * cp.LC));
-        const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
-        const LineInfo *s_line = cp.info(k);
+        const int nl = min(LC, hi - (lo + c * LC));
+        warp_fill<NQ, DS>(g, ws, ginfo, lo + c * LC, nl, d0 + warp * DS, lane);
+        const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(ws.par);
+        const LineInfo *s_line = ws.info;
         unsigned m_fast = 0u, m_red = 0u, m_red3 = 0u, m_skip = 0u;   // this warp's flags of 32 lines, one per lane
         for (int li = 0; li < nl; ++li) {
             if ((li & 31) == 0) {
@@ -656,7 +662,7 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
             const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1) |
                            (int)(((m_red3 >> (li & 31)) & 1u) << 2);
             if ((m_skip >> (li & 31)) & 1u) continue;        // every layer rejected by the centre test
-            const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
+            const ulonglong2 *par = s_par + (size_t)li * DP * NQ;
             f2_t u2[J];
             if (fl != 0) {
                 // the whole tile is in the line's far wing: offsets from the first point's,
@@ -808,7 +814,6 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
             }
         }
     }
-    cp.cc += nch;
 
     if (ext.y > 1) {
         // one of ext.y pieces of a split item (slots ext.x.., counter ext.z, piece ext.w):
@@ -883,24 +888,20 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
     return true;
 }
 
-// Barriers of the chunk pipeline: initialised once per CTA, visible to the async proxy.
-__device__ __forceinline__ void pipe_init(uint64_t *bars) {
-    if (threadIdx.x == 0) {
-        mbar_init(bars);
-        mbar_init(bars + 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-}
-
+// Shared memory of the far-wing kernels: each warp's stage (warp_stage_quads), then
+// (forward) the compensated sums of every thread [DS][threads][8] or (backward) the
+// per-line sums of the warps, double-buffered by chunk [2][LC][GW].
 template <int J, int DS, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int LC) {
     extern __shared__ float4 smem4[];
-    __shared__ uint64_t bars[2];
-    pipe_init(bars);
-    ChunkPipe cp{bars, smem4, LC, GW * DS / 2 * kNQF, 0u};
+    const int warp = threadIdx.x >> 5;
+    const size_t wq = warp_stage_quads(LC, DS, kNQF);
+    float4 *mine = smem4 + (size_t)warp * wq;
+    const WarpStage ws{mine, mine + DS, reinterpret_cast<LineInfo *>(mine + DS + (size_t)LC * (DS / 2) * kNQF)};
+    float *s_comp = reinterpret_cast<float *>(smem4 + (size_t)GW * wq);
     for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi, int it) {
-        return far_fwd_item<J, DS>(v, tile, group, lo, hi, GW, cp, g.fext ? g.fext[it] : make_int4(-1, 1, -1, 0));
+        return far_fwd_item<J, DS>(v, tile, group, lo, hi, GW, LC, ws, s_comp,
+                                   g.fext ? g.fext[it] : make_int4(-1, 1, -1, 0));
     });
 }
 
@@ -1030,7 +1031,8 @@ __device__ __forceinline__ void far_bwd_line(const ulonglong2 *par, const f2_t (
 // G stim A H and G stim A a6 dH/da, reduced over the CTA and added to gacc.
 template <int J, int DS>
 __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, const int group, const int lo,
-                                             const int hi, const int GW, ChunkPipe &cp) {
+                                             const int hi, const int GW, const int LC, const WarpStage &ws,
+                                             float2 *s_red2, unsigned &cc) {
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
     static_assert(DS % 2 == 0, "DS must be even (depth pairs)");
     constexpr int DP = DS / 2;
@@ -1038,8 +1040,6 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
     const int T = 32 * J;
     const int DC = GW * DS;
     const int nthr = blockDim.x;
-    float2 *s_red = reinterpret_cast<float2 *>(cp.buf + (size_t)2 * cp.LC * (cp.PQ + 1));   // [LC][GW]
-    const float4 *gtab = g.ftab + (int64_t)group * g.nl * cp.PQ;
     const LineInfo *ginfo = g.finfo + (int64_t)group * g.nl;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1064,23 +1064,17 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
         }
     }
 
-    const int nch = (hi - lo + cp.LC - 1) / cp.LC;
-    if (tid == 0 && nch > 0) cp.issue(cp.cc, gtab, ginfo, lo, min(cp.LC, hi - lo));
+    warp_stage_depths<DS>(g, ws, d0 + warp * DS, lane);
+    const int nch = (hi - lo + LC - 1) / LC;
     for (int c = 0; c < nch; ++c) {
-        const unsigned k = cp.cc + c;
-        const int c0 = lo + c * cp.LC;
-        const int nl = min(cp.LC, hi - c0);
-        const bool ok = mbar_wait(cp.bar + (k & 1), (k >> 1) & 1, kWaitLimitNs);
-        if (__syncthreads_or(!ok)) {
-            far_abort(g, cp, k);
-            return false;
-        }
-        if (tid == 0 && c + 1 < nch) {
-            const int n1 = c0 + cp.LC;
-            cp.issue(k + 1, gtab, ginfo, n1, min(cp.LC, hi - n1));
-        }
-        const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(cp.par(k));
-        const LineInfo *s_line = cp.info(k);
+        const int c0 = lo + c * LC;
+        const int nl = min(LC, hi - c0);
+        // per-line sums of this chunk go to buffer cc & 1: its previous readers (the
+        // reduction two chunks back) are past the CTA barrier of the previous chunk
+        float2 *s_red = s_red2 + (size_t)((cc + c) & 1) * LC * GW;
+        warp_fill<NQ, DS>(g, ws, ginfo, c0, nl, d0 + warp * DS, lane);
+        const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(ws.par);
+        const LineInfo *s_line = ws.info;
         float h1 = 0.0f, h2 = 0.0f;   // lane sums of the held even line
         unsigned m_fast = 0u, m_red = 0u, m_red3 = 0u, m_skip = 0u;   // this warp's flags of 32 lines, one per lane
         for (int li = 0; li < nl; ++li) {
@@ -1095,7 +1089,7 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
             const LineInfo info = s_line[li];
             const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1) |
                            (int)(((m_red3 >> (li & 31)) & 1u) << 2);
-            const ulonglong2 *par = s_par + (size_t)li * cp.PQ + warp * DP * NQ;
+            const ulonglong2 *par = s_par + (size_t)li * DP * NQ;
             f2_t S1 = 0ull, S2 = 0ull;
             // (a slab whose every layer the centre test rejects keeps zero sums; it still takes
             // part in the pairwise reduction below)
@@ -1180,18 +1174,21 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
             atomicAdd(g.gacc + g.nl + c0 + li, a2);
         }
     }
-    cp.cc += nch;
+    cc += nch;
     return true;
 }
 
 template <int J, int DS, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int LC) {
     extern __shared__ float4 smem4[];
-    __shared__ uint64_t bars[2];
-    pipe_init(bars);
-    ChunkPipe cp{bars, smem4, LC, GW * DS / 2 * kNQB, 0u};
+    const int warp = threadIdx.x >> 5;
+    const size_t wq = warp_stage_quads(LC, DS, kNQB);
+    float4 *mine = smem4 + (size_t)warp * wq;
+    const WarpStage ws{mine, mine + DS, reinterpret_cast<LineInfo *>(mine + DS + (size_t)LC * (DS / 2) * kNQB)};
+    float2 *s_red2 = reinterpret_cast<float2 *>(smem4 + (size_t)GW * wq);
+    unsigned cc = 0;
     for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi, int) {
-        return far_bwd_item<J, DS>(v, tile, group, lo, hi, GW, cp);
+        return far_bwd_item<J, DS>(v, tile, group, lo, hi, GW, LC, ws, s_red2, cc);
     });
 }
 
@@ -1468,7 +1465,6 @@ static LineArgs make_args(pz_ctx *c) {
     g.fext = nullptr;
     g.fpart = c->d_fpart;
     g.fcnt = c->d_fcnt;
-    g.ftab = reinterpret_cast<const float4 *>(c->d_ftab);
     g.finfo = reinterpret_cast<const LineInfo *>(c->d_finfo);
     g.status = c->d_status;
     g.keep = c->d_keep;
@@ -1485,6 +1481,7 @@ static LineArgs make_args(pz_ctx *c) {
     g.sp = c->L.sp;
     g.R = c->d_R;
     g.invdv = c->d_invdv;
+    g.Ksd = c->d_Ksd;
     g.thr = c->d_thr;
     g.nslab = c->nslab;
     g.beta_hi = c->d_beta_hi;
@@ -1561,39 +1558,33 @@ static cudaError_t launch_near(pz_ctx *c, LineArgs g, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Dynamic shared memory of the far-wing kernels: staged prefactors, line records and
-// (forward) the compensated sums of every thread, or (backward) the per-line sums.
+// Dynamic shared memory of the far-wing kernels: the warps' stages (layer constants,
+// line records, prefactors) and (forward) the compensated sums of every thread, or
+// (backward) the per-line sums.
 static size_t far_fwd_smem(const Tiling &t) {
-    return (size_t)2 * t.LC * (t.depth_per_cta() / 2 * kNQF + 1) * sizeof(float4) +
+    return (size_t)t.GW * warp_stage_quads(t.LC, t.DS, kNQF) * sizeof(float4) +
            (size_t)t.DS * 32 * t.GW * 2 * sizeof(float4);
 }
 static size_t far_bwd_smem(const Tiling &t) {
-    return (size_t)2 * t.LCB * (t.depth_per_cta() / 2 * kNQB + 1) * sizeof(float4) + (size_t)t.LCB * t.GW * sizeof(float2);
+    return (size_t)t.GW * warp_stage_quads(t.LCB, t.DS, kNQB) * sizeof(float4) +
+           (size_t)2 * t.LCB * t.GW * sizeof(float2);
 }
 constexpr size_t kFarSmemMax = 200 * 1024;   // the opt-in size the far-wing kernels are given
 
 bool tiling_fits(const Tiling &t) { return far_fwd_smem(t) <= kFarSmemMax && far_bwd_smem(t) <= kFarSmemMax; }
 
-// Prefactor table of the far-wing kernels for the current tiling (forward NQ = kNQF,
-// backward kNQB), into the context's table buffers (sized by ensure_far_tables).
-template <int NQ>
-static cudaError_t launch_far_table(pz_ctx *c, LineArgs &g, int DS, cudaStream_t s) {
+// Line records of the far-wing kernels for the current tiling, into the context's
+// buffer (sized by ensure_far_tables).
+static cudaError_t launch_far_info(pz_ctx *c, LineArgs &g, int DS, cudaStream_t s) {
     const int DC = c->tiling.depth_per_cta();
-    const int64_t n = (int64_t)g.ngroups * c->L.n * (DC / 2);
+    const int64_t n = (int64_t)g.ngroups * c->L.n;
     const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->n_sm * 16);
-    g.ftab = reinterpret_cast<const float4 *>(c->d_ftab);
     g.finfo = reinterpret_cast<const LineInfo *>(c->d_finfo);
-    k_far_table<NQ><<<grid, 256, 0, s>>>(g, DC, DS, g.ngroups, reinterpret_cast<float4 *>(c->d_ftab),
-                                         reinterpret_cast<LineInfo *>(c->d_finfo));
+    k_far_info<<<grid, 256, 0, s>>>(g, DC, DS, g.ngroups, reinterpret_cast<LineInfo *>(c->d_finfo));
     c->launches++;
     return cudaGetLastError();
 }
 
-size_t far_table_bytes(const pz_ctx *c) {
-    const int DC = c->tiling.depth_per_cta();
-    const int ng = (c->nd + DC - 1) / DC;
-    return (size_t)ng * std::max<int64_t>(c->L.n, 1) * (DC / 2) * kNQB * sizeof(float4);
-}
 size_t far_info_bytes(const pz_ctx *c) {
     const int DC = c->tiling.depth_per_cta();
     const int ng = (c->nd + DC - 1) / DC;
@@ -1620,7 +1611,7 @@ static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
     g.ngroups = (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta();
     g.ctr = c->d_ctr + 1;
     if (c->L.n > 0) {
-        e = launch_far_table<kNQF>(c, g, DS, s);
+        e = launch_far_info(c, g, DS, s);
         if (e != cudaSuccess) return e;
     }
     if (c->n_fsplit > 0) {
@@ -1651,7 +1642,7 @@ static cudaError_t launch_bwd_t(pz_ctx *c, cudaStream_t s) {
         gb.n_items = c->n_bitems;
         gb.ngroups = (c->nd + t.depth_per_cta() - 1) / t.depth_per_cta();
         gb.ctr = c->d_ctr + 2;
-        e = launch_far_table<kNQB>(c, gb, DS, s);
+        e = launch_far_info(c, gb, DS, s);
         if (e != cudaSuccess) return e;
         int grid = persistent_grid(c, k_line_bwd<J, DS, MINB>, 32 * t.GW, smem, gb.n_items);
         k_line_bwd<J, DS, MINB><<<grid, 32 * t.GW, smem, s>>>(gb, t.GW, t.LCB);

@@ -137,6 +137,8 @@ def test_batch_gradients_are_star_sums(oracle):
         gab_t = torch.empty(b.n_elem, dtype=torch.float32, device=dev)
         s.backward(dLdf, g[0], g[1], gab_t)
         torch.cuda.synchronize()
+        print("batch loss rel err vs oracle (%s): %.3g" % ("mixed" if prec == pz.PZ_MIXED else "fp64",
+                                                          abs(loss.item() / L - 1)))
         assert abs(loss.item() / L - 1) < (1e-4 if prec == pz.PZ_MIXED else 1e-7)
         e1 = rel_metric(g[0].cpu().numpy().astype(np.float64), ggf).max()
         e2 = rel_metric(g[1].cpu().numpy().astype(np.float64), gg6).max()
@@ -145,14 +147,18 @@ def test_batch_gradients_are_star_sums(oracle):
         s.close()
 
 
-def test_calib_step_graph_matches_eager_calls():
+@pytest.mark.parametrize("prec", [pz.PZ_MIXED, pz.PZ_FP64])
+def test_calib_step_graph_matches_eager_calls(prec):
     """pz_calib_step = corrections + forward + chi2 + backward + update in one graph
     launch; its loss and gradients equal the eager calls, its update is delta - lr g,
-    and a replay sees the updated corrections."""
+    and a replay sees the updated corrections.  The plain FP64 form matches to 1e-12;
+    the mixed path's near-core forward adds FP32 partial sums through shared-memory
+    atomics whose order changes from launch to launch, so two eager runs already
+    differ at FP32 rounding and the graph is held to the same bar."""
     import torch
     b = I.small_batch(n_stars=2, span_nm=3.0, seed=37)
     nl = b.lines.n_lines
-    s = pz.Synthesizer(b)
+    s = pz.Synthesizer(b, prec)
     rng = np.random.default_rng(2)
     d0 = rng.normal(0, 0.05, nl).astype(np.float32)
     s.set_corrections(d0, None, np.zeros(b.n_elem, np.float32))
@@ -167,6 +173,13 @@ def test_calib_step_graph_matches_eager_calls():
     s.backward(dLdf, g_e[0], g_e[1], gab_e)
     torch.cuda.synchronize()
     L_e = loss.item()
+    # a second eager pass at the same corrections: the launch-to-launch spread
+    s.forward()
+    s.loss(y, None, loss, dLdf)
+    g_e2 = [torch.empty(nl, dtype=torch.float32, device=dev) for _ in range(2)]
+    s.backward(dLdf, g_e2[0], g_e2[1], None)
+    torch.cuda.synchronize()
+    L_e2 = loss.item()
 
     lr = (1e-3, 2e-3, 5e-4)
     loss_s = torch.zeros(1, dtype=torch.float64, device=dev)
@@ -174,7 +187,19 @@ def test_calib_step_graph_matches_eager_calls():
     gab_s = torch.empty(b.n_elem, dtype=torch.float32, device=dev)
     s.calib_step(y, None, *lr, loss_s, g_s[0], g_s[1], gab_s)
     torch.cuda.synchronize()
-    assert abs(loss_s.item() / L_e - 1) < 1e-7      # near-core sums: last-bit order effects only
+    d_ee = abs(L_e2 / L_e - 1)
+    d_ge = abs(loss_s.item() / L_e - 1)
+    g_ee = max(float(np.max(np.abs(a.cpu().numpy().astype(np.float64) - c.cpu().numpy()))
+                     / np.max(np.abs(c.cpu().numpy()))) for a, c in zip(g_e2, g_e))
+    g_ge = max(float(np.max(np.abs(a.cpu().numpy().astype(np.float64) - c.cpu().numpy()))
+                     / np.max(np.abs(c.cpu().numpy()))) for a, c in zip(g_s, g_e))
+    print("%s: loss eager-eager %.3g graph-eager %.3g; gradients eager-eager %.3g graph-eager %.3g"
+          % ("mixed" if prec == pz.PZ_MIXED else "fp64", d_ee, d_ge, g_ee, g_ge))
+    if prec == pz.PZ_FP64:
+        # FP64 throughout: only the order of FP64 atomic additions differs
+        assert d_ge < 1e-12 and g_ge < 1e-6     # gradients are returned in FP32
+    else:
+        assert d_ge < 1e-7 and d_ee < 1e-7
     for a, c in zip(g_s + [gab_s], g_e + [gab_e]):
         a, c = a.cpu().numpy().astype(np.float64), c.cpu().numpy().astype(np.float64)
         assert np.max(np.abs(a - c)) <= 1e-5 * np.max(np.abs(c)) + 1e-30
@@ -190,12 +215,12 @@ def test_calib_step_graph_matches_eager_calls():
     s.calib_step(y, None, *lr, loss_s, g_s[0], g_s[1], gab_s)
     torch.cuda.synchronize()
     L2 = loss_s.item()
-    s2 = pz.Synthesizer(b)
+    s2 = pz.Synthesizer(b, prec)
     s2.set_corrections(gf, g6, ab)
-    f2 = s2.forward()
+    s2.forward()
     s2.loss(y, None, loss)
     torch.cuda.synchronize()
-    assert abs(L2 / loss.item() - 1) < 1e-7
+    assert abs(L2 / loss.item() - 1) < (1e-7 if prec == pz.PZ_MIXED else 1e-12)
     s.close()
     s2.close()
 
