@@ -336,6 +336,11 @@ __device__ __forceinline__ float f2_lo(f2_t v) {
     f2_unpack(v, lo, hi);
     return lo;
 }
+__device__ __forceinline__ float f2_hi(f2_t v) {
+    float lo, hi;
+    f2_unpack(v, lo, hi);
+    return hi;
+}
 
 // ---- far-wing prefactors ------------------------------------------------------
 // A far-wing CTA stages LC lines at a time.  For each line of the chunk and each of
@@ -604,6 +609,34 @@ __device__ __forceinline__ void far_c3456(f2_t a2, f2_t C1, f2_t &C3, f2_t &C4, 
     C6 = f2_mul(f2_mul(f2_mul(a4, f2_splat(-120.0f)), a2), C1);
 }
 
+// Reciprocals s_j = 1/U_j of the squared scaled offsets of one line at the thread's J
+// points (and their squares), for the reduced forms: offsets from the first point's,
+// u_j = u_0 r^-j + (r^-j - 1) scaled by 2^18; points outside the line's window get
+// s = 0 unless the window covers the tile (full).
+template <int J>
+__device__ __forceinline__ void far_reduced_s(const LineArgs &g, const LineInfo &info, bool full, float lamf,
+                                              int lam_thr, f2_t (&sp)[J], f2_t (&sq)[J]) {
+    f2_t u2[J];
+    u2[0] = f2_splat(offset_u((info.ilf - lamf) + info.frac, g.lnr) * kUScale);
+#pragma unroll
+    for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j] * kUScale));
+#pragma unroll
+    for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
+    if (full) {
+#pragma unroll
+        for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(u2[j])));
+    } else {
+        const int il = (int)info.ilf;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const int di = lam_thr + j - il;
+            sp[j] = f2_splat(di >= -g.W && di <= g.W ? rcp_approx(f2_lo(u2[j])) : 0.0f);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) sq[j] = f2_mul(sp[j], sp[j]);
+}
+
 // Far-wing kernel (forward).  Every cell with |v|^2 + a^2 >= 400 inside its window is
 // evaluated here with the far polynomial; the near-core cells are summed by
 // k_line_near_fwd into knear, which this kernel adds before applying stim.
@@ -658,10 +691,29 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                 m_red3 = __ballot_sync(0xffffffffu, (f & 8) != 0);
                 m_skip = __ballot_sync(0xffffffffu, (f & 4) != 0);
             }
+            const unsigned b = li & 31;
+            if (b < 31 && li + 1 < nl && ((m_red >> b) & 3u) == 3u && ((m_skip >> b) & 3u) == 0u) {
+                // two consecutive two-term lines: their offsets and reciprocals are independent
+                // chains, formed together; the sums take line li's terms, then line li + 1's
+                f2_t spa[J], sqa[J], spb[J], sqb[J];
+                far_reduced_s<J>(g, s_line[li], (m_fast >> b) & 1u, lamf, lam_thr, spa, sqa);
+                far_reduced_s<J>(g, s_line[li + 1], (m_fast >> (b + 1)) & 1u, lamf, lam_thr, spb, sqb);
+                const ulonglong2 *pa = s_par + (size_t)li * DP * NQ, *pb = pa + DP * NQ;
+#pragma unroll
+                for (int dp = 0; dp < DP; ++dp) {
+                    const ulonglong2 qa = pa[NQ * dp + 1], qb = pb[NQ * dp + 1];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        acc[dp][j] = f2_fma(sqa[j], qa.y, f2_fma(spa[j], qa.x, acc[dp][j]));
+                        acc[dp][j] = f2_fma(sqb[j], qb.y, f2_fma(spb[j], qb.x, acc[dp][j]));
+                    }
+                }
+                ++li;
+                continue;
+            }
             const LineInfo info = s_line[li];
-            const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1) |
-                           (int)(((m_red3 >> (li & 31)) & 1u) << 2);
-            if ((m_skip >> (li & 31)) & 1u) continue;        // every layer rejected by the centre test
+            const int fl = (int)((m_fast >> b) & 1u) | (int)(((m_red >> b) & 1u) << 1) | (int)(((m_red3 >> b) & 1u) << 2);
+            if ((m_skip >> b) & 1u) continue;        // every layer rejected by the centre test
             const ulonglong2 *par = s_par + (size_t)li * DP * NQ;
             f2_t u2[J];
             if (fl != 0) {
@@ -890,7 +942,9 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
 
 // Shared memory of the far-wing kernels: each warp's stage (warp_stage_quads), then
 // (forward) the compensated sums of every thread [DS][threads][8] or (backward) the
-// per-line sums of the warps, double-buffered by chunk [2][LC][GW].
+// per-line sums of the warps, double-buffered by chunk [2][LC][GW], and each warp's
+// per-lane partial sums of a batch of 32 lines [32][32] (lane l of line k at column
+// l ^ k, so that both the row writes and the column reads avoid bank conflicts).
 template <int J, int DS, int MINB>
 __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int LC) {
     extern __shared__ float4 smem4[];
@@ -966,6 +1020,26 @@ __device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, cons
     }
 }
 
+// Two-term reduced backward sums of one line from the reciprocals s_j of its points
+// (far_reduced_s): per depth pair X1 = sum_j G s_j and X2 = sum_j G s_j^2, then
+// S1 += (B1 K) X1 + (B2' K^2) X2 and S2 += (C1 K) X1 + (C2' K^2) X2.
+template <int J, int DP>
+__device__ __forceinline__ void far_bwd_two_term(const ulonglong2 *par, const f2_t (&sp)[J], const f2_t (&sq)[J],
+                                                 const f2_t (&gv)[DP][J], f2_t &S1, f2_t &S2) {
+#pragma unroll
+    for (int dp = 0; dp < DP; ++dp) {
+        const ulonglong2 q1 = par[kNQB * dp + 1], q2 = par[kNQB * dp + 2];
+        f2_t X1 = f2_mul(gv[dp][0], sp[0]), X2 = f2_mul(gv[dp][0], sq[0]);
+#pragma unroll
+        for (int j = 1; j < J; ++j) {
+            X1 = f2_fma(gv[dp][j], sp[j], X1);
+            X2 = f2_fma(gv[dp][j], sq[j], X2);
+        }
+        S1 = f2_fma(q1.y, X2, f2_fma(q1.x, X1, S1));
+        S2 = f2_fma(q2.y, X2, f2_fma(q2.x, X1, S2));
+    }
+}
+
 // One line's far-wing backward sums over a warp's J x DS cells (depth pairs):
 // S1 += G stim A H, S2 += G stim A a6 dH/da.  Without MASK, w holds the scaled squared
 // offsets U = 2^36 u^2; with MASK, w holds the offsets u and kp the depth pairs' k, and
@@ -1032,7 +1106,7 @@ __device__ __forceinline__ void far_bwd_line(const ulonglong2 *par, const f2_t (
 template <int J, int DS>
 __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, const int group, const int lo,
                                              const int hi, const int GW, const int LC, const WarpStage &ws,
-                                             float2 *s_red2, unsigned &cc) {
+                                             float2 *s_part, float2 *s_red2, unsigned &cc) {
     static_assert(J == 2 || J == 4, "J must be 2 or 4");
     static_assert(DS % 2 == 0, "DS must be even (depth pairs)");
     constexpr int DP = DS / 2;
@@ -1075,10 +1149,10 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
         warp_fill<NQ, DS>(g, ws, ginfo, c0, nl, d0 + warp * DS, lane);
         const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(ws.par);
         const LineInfo *s_line = ws.info;
-        float h1 = 0.0f, h2 = 0.0f;   // lane sums of the held even line
         unsigned m_fast = 0u, m_red = 0u, m_red3 = 0u, m_skip = 0u;   // this warp's flags of 32 lines, one per lane
-        for (int li = 0; li < nl; ++li) {
-            if ((li & 31) == 0) {
+        for (int li = 0; li < nl;) {
+            const unsigned b = li & 31;
+            if (b == 0) {
                 const int lj = li + lane;
                 const int f = lj < nl ? far_flags(g, s_line[lj], t0f, tendf, slab, warp) : 0;
                 m_fast = __ballot_sync(0xffffffffu, f & 1);
@@ -1086,80 +1160,82 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
                 m_red3 = __ballot_sync(0xffffffffu, (f & 8) != 0);
                 m_skip = __ballot_sync(0xffffffffu, (f & 4) != 0);
             }
-            const LineInfo info = s_line[li];
-            const int fl = (int)((m_fast >> (li & 31)) & 1u) | (int)(((m_red >> (li & 31)) & 1u) << 1) |
-                           (int)(((m_red3 >> (li & 31)) & 1u) << 2);
-            const ulonglong2 *par = s_par + (size_t)li * DP * NQ;
-            f2_t S1 = 0ull, S2 = 0ull;
-            // (a slab whose every layer the centre test rejects keeps zero sums; it still takes
-            // part in the pairwise reduction below)
-            if (!((m_skip >> (li & 31)) & 1u)) {
-                f2_t u2[J];
-                if (fl != 0) {
-                    const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr) * kUScale;
-                    u2[0] = f2_splat(u0);
-#pragma unroll
-                    for (int j = 1; j < J; ++j)
-                        u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j] * kUScale));
-#pragma unroll
-                    for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < J; ++j)
-                        u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
-                }
-                if (fl & 2) {
-                    far_bwd_line_reduced<J, DP, false>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W, S1,
-                                                       S2);
-                } else if (fl & 4) {
-                    far_bwd_line_reduced<J, DP, true>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W, S1,
-                                                      S2);
-                } else if (fl & 1) {
-                    far_bwd_line<J, DP, false>(par, u2, gv, nullptr, nullptr, S1, S2);
-                } else {
-                    // line near the tile or partly outside its window: far cells inside the window only
-                    bool inwin[J];
-                    const int il = (int)info.ilf;
-#pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        const int di = lam_thr + j - il;
-                        inwin[j] = di >= -g.W && di <= g.W;
-                    }
-                    f2_t kp[DP];
-                    far_kpairs<DP>(g, info.sp, d0 + warp * DS, kp);
-                    far_bwd_line<J, DP, true>(par, u2, gv, inwin, kp, S1, S2);
-                }
-            }
-            float s1a, s1b, s2a, s2b;
-            f2_unpack(S1, s1a, s1b);
-            f2_unpack(S2, s2a, s2b);
-            float s1 = s1a + s1b, s2 = s2a + s2b;
-            if ((li & 1) == 0 && li + 1 < nl) {
-                // hold an even line's lane sums; they are reduced together with the next line's
-                h1 = s1;
-                h2 = s2;
-                continue;
-            }
-            if (li & 1) {
-                // two lines at once: the first exchange leaves lanes 0-15 with partial sums of
-                // line li - 1 and lanes 16-31 with those of line li
-                const bool up = (lane & 16) != 0;
-                float k1 = up ? s1 : h1, k2 = up ? s2 : h2;
-                k1 += __shfl_xor_sync(0xffffffffu, up ? h1 : s1, 16);
-                k2 += __shfl_xor_sync(0xffffffffu, up ? h2 : s2, 16);
-#pragma unroll
-                for (int o = 8; o > 0; o >>= 1) {
-                    k1 += __shfl_xor_sync(0xffffffffu, k1, o);
-                    k2 += __shfl_xor_sync(0xffffffffu, k2, o);
-                }
-                if ((lane & 15) == 0) s_red[(li - (up ? 0 : 1)) * GW + warp] = make_float2(k1, k2);
+            if (b < 31 && li + 1 < nl && ((m_red >> b) & 3u) == 3u && ((m_skip >> b) & 3u) == 0u) {
+                // two consecutive two-term lines: independent offset and reciprocal chains,
+                // formed together
+                f2_t spa[J], sqa[J], spb[J], sqb[J];
+                far_reduced_s<J>(g, s_line[li], (m_fast >> b) & 1u, lamf, lam_thr, spa, sqa);
+                far_reduced_s<J>(g, s_line[li + 1], (m_fast >> (b + 1)) & 1u, lamf, lam_thr, spb, sqb);
+                const ulonglong2 *pa = s_par + (size_t)li * DP * NQ;
+                f2_t S1a = 0ull, S2a = 0ull, S1b = 0ull, S2b = 0ull;
+                far_bwd_two_term<J, DP>(pa, spa, sqa, gv, S1a, S2a);
+                far_bwd_two_term<J, DP>(pa + DP * NQ, spb, sqb, gv, S1b, S2b);
+                s_part[b * 32 + (lane ^ b)] = make_float2(f2_lo(S1a) + f2_hi(S1a), f2_lo(S2a) + f2_hi(S2a));
+                s_part[(b + 1) * 32 + (lane ^ (b + 1))] = make_float2(f2_lo(S1b) + f2_hi(S1b), f2_lo(S2b) + f2_hi(S2b));
+                li += 2;
             } else {
+                const LineInfo info = s_line[li];
+                const int fl = (int)((m_fast >> b) & 1u) | (int)(((m_red >> b) & 1u) << 1) | (int)(((m_red3 >> b) & 1u) << 2);
+                const ulonglong2 *par = s_par + (size_t)li * DP * NQ;
+                f2_t S1 = 0ull, S2 = 0ull;
+                // (a slab whose every layer the centre test rejects keeps zero sums)
+                if (!((m_skip >> b) & 1u)) {
+                    f2_t u2[J];
+                    if (fl != 0) {
+                        const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr) * kUScale;
+                        u2[0] = f2_splat(u0);
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-                    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                        for (int j = 1; j < J; ++j)
+                            u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j] * kUScale));
+#pragma unroll
+                        for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < J; ++j)
+                            u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
+                    }
+                    if (fl & 2) {
+                        far_bwd_line_reduced<J, DP, false>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W,
+                                                           S1, S2);
+                    } else if (fl & 4) {
+                        far_bwd_line_reduced<J, DP, true>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W,
+                                                          S1, S2);
+                    } else if (fl & 1) {
+                        far_bwd_line<J, DP, false>(par, u2, gv, nullptr, nullptr, S1, S2);
+                    } else {
+                        // line near the tile or partly outside its window: far cells inside the window only
+                        bool inwin[J];
+                        const int il = (int)info.ilf;
+#pragma unroll
+                        for (int j = 0; j < J; ++j) {
+                            const int di = lam_thr + j - il;
+                            inwin[j] = di >= -g.W && di <= g.W;
+                        }
+                        f2_t kp[DP];
+                        far_kpairs<DP>(g, info.sp, d0 + warp * DS, kp);
+                        far_bwd_line<J, DP, true>(par, u2, gv, inwin, kp, S1, S2);
+                    }
                 }
-                if (lane == 0) s_red[li * GW + warp] = make_float2(s1, s2);
+                s_part[b * 32 + (lane ^ b)] = make_float2(f2_lo(S1) + f2_hi(S1), f2_lo(S2) + f2_hi(S2));
+                ++li;
+            }
+            if ((li & 31) == 0 || li >= nl) {
+                // end of a batch of 32 lines: lane k adds line k's partial sums over the warp's
+                // lanes in lane order and leaves the warp's total for the CTA reduction
+                __syncwarp();
+                const int base = (li - 1) & ~31;
+                if (base + lane < nl) {
+                    const float2 *row = s_part + lane * 32;
+                    float a1 = 0.0f, a2 = 0.0f;
+#pragma unroll 8
+                    for (int k = 0; k < 32; ++k) {
+                        const float2 r = row[k ^ lane];
+                        a1 += r.x;
+                        a2 += r.y;
+                    }
+                    s_red[(base + lane) * GW + warp] = make_float2(a1, a2);
+                }
+                __syncwarp();
             }
         }
         __syncthreads();
@@ -1186,9 +1262,10 @@ __global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int 
     float4 *mine = smem4 + (size_t)warp * wq;
     const WarpStage ws{mine, mine + DS, reinterpret_cast<LineInfo *>(mine + DS + (size_t)LC * (DS / 2) * kNQB)};
     float2 *s_red2 = reinterpret_cast<float2 *>(smem4 + (size_t)GW * wq);
+    float2 *s_part = s_red2 + (size_t)2 * LC * GW + (size_t)warp * 32 * 32;
     unsigned cc = 0;
     for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi, int) {
-        return far_bwd_item<J, DS>(v, tile, group, lo, hi, GW, LC, ws, s_red2, cc);
+        return far_bwd_item<J, DS>(v, tile, group, lo, hi, GW, LC, ws, s_part, s_red2, cc);
     });
 }
 
@@ -1567,7 +1644,7 @@ static size_t far_fwd_smem(const Tiling &t) {
 }
 static size_t far_bwd_smem(const Tiling &t) {
     return (size_t)t.GW * warp_stage_quads(t.LCB, t.DS, kNQB) * sizeof(float4) +
-           (size_t)2 * t.LCB * t.GW * sizeof(float2);
+           (size_t)2 * t.LCB * t.GW * sizeof(float2) + (size_t)t.GW * 32 * 32 * sizeof(float2);
 }
 constexpr size_t kFarSmemMax = 200 * 1024;   // the opt-in size the far-wing kernels are given
 
