@@ -95,6 +95,9 @@ def parse():
     ap.add_argument("--scaling-reps", type=int, default=3)
     ap.add_argument("--lbfgs-updates", type=int, default=40)
     ap.add_argument("--centre-eta", type=float, default=1e-3)
+    ap.add_argument("--only", choices=["config1", "headline"], default=None,
+                    help="run only the single-star APOGEE-like step, or only the batched headline step (default "
+                         "tiling, no autotune), and print its result (profiling runs)")
     return ap.parse_args()
 
 
@@ -1205,8 +1208,19 @@ def main():
         pipe_peaks = {}
 
     # single-star APOGEE-like step; tunes the tiling every other workload reuses
+    if args.only == "headline":
+        hl = run_headline(args, dev, barrier, max_over_ranks, ws, rank, None, pipe_peaks, clk_max)
+        if rank == 0:
+            print(json.dumps({"ms_per_step": hl["ms_per_step"], "value": hl["value"], "parity": hl["parity"],
+                              "kernel_ms_per_step": {k: v[0] / args.steps for k, v in hl["kernel_times"].items()}}),
+                  flush=True)
+        return 0
     c1, tune = run_config1(args, dev, pipe_peaks, clk_max)
     tiling = tune["tiling"] if tune else None
+    if args.only == "config1":
+        if rank == 0:
+            print(json.dumps({"config1": c1, "autotune": tune}), flush=True)
+        return 0
 
     # headline: the 64-star batch
     hl = run_headline(args, dev, barrier, max_over_ranks, ws, rank, tiling, pipe_peaks, clk_max)

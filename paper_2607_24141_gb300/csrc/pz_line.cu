@@ -1363,6 +1363,50 @@ __device__ __forceinline__ void near_pass(const LineArgs &g, const NearItem *min
     }
 }
 
+// Backward mid-wing pass with a blocked assignment: lane l takes the concatenated cells
+// [l P, (l + 1) P), P = ceil(total / 32), so that each lane's cells belong to a few
+// consecutive items; the lane sums an item's cells in registers and hands the sum to
+// done when it moves to the next item (no cross-lane reduction).  voigt_mid has no
+// branch on the item's parameters, so lanes holding different items do not diverge.
+template <class Val, class Done>
+__device__ __forceinline__ void near_pass_mid_blocked(const LineArgs &g, const NearItem *mine, const int *pref,
+                                                      Val &val, Done &done) {
+    const int lane = threadIdx.x & 31;
+    const int total = pref[32];
+    const int per = (total + 31) >> 5;
+    const int nb = min(lane * per, total), ne = min(nb + per, total);
+    if (nb >= ne) return;
+    int src = 0;
+    while (pref[src + 1] <= nb) ++src;
+    NearItem it = mine[src];
+    int start = pref[src], end = pref[src + 1];
+    float2 acc = make_float2(0.0f, 0.0f);
+    for (int n = nb; n < ne; ++n) {
+        if (n >= end) {
+            done(it, acc);
+            acc = make_float2(0.0f, 0.0f);
+            do {
+                ++src;
+            } while (pref[src + 1] <= n);
+            it = mine[src];
+            start = pref[src];
+            end = pref[src + 1];
+        }
+        const int off = n - start;
+        const int i = off < it.nl ? it.lo + off : it.r0 + (off - it.nl);
+        const float x = fabsf(offset_u((it.ilf - (float)i) + it.frac, g.lnr) * it.k);
+        // a mid-wing cell at |z| >= 20 belongs to the far-wing kernels (same test)
+        if (fmaf(x, x, it.a2) < kFar2) {
+            float H, dH;
+            voigt_mid<true>(x, it.a, H, dH);
+            const float2 v = val(it, i, H, dH);
+            acc.x += v.x;
+            acc.y += v.y;
+        }
+    }
+    done(it, acc);
+}
+
 // Near-core sweep shared by the forward (D = false) and the backward (D = true).
 // Each warp takes rounds of 32 (line, depth) items: every lane sets up one item
 // (coarse span from c/dv_D alone, then the exact prefactors, the clipped span and
@@ -1437,7 +1481,11 @@ __device__ __forceinline__ void near_sweep(const LineArgs &g, int t0, int64_t nl
         }
         if (own != 0) mine[lane] = item;
         __syncwarp();
-        near_pass<T, D, false>(g, mine, pm, s_daw, cell, val, done);
+        if (D)
+            near_pass_mid_blocked(g, mine, pm, val, done);
+        else
+            near_pass<T, D, false>(g, mine, pm, s_daw, cell, val, done);
+        __syncwarp();
         near_pass<T, D, true>(g, mine, pc, s_daw, cell, val, done);
     }
 }
@@ -1476,7 +1524,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) k_line_near_fwd(LineArgs gq) 
 // Lines are processed in batches whose per-line sums live in shared memory; one
 // global atomic per (line, tile, depth group) at the end of each batch.
 template <int T, int NDG>
-__global__ void __launch_bounds__(32 * kNearWarps) k_line_near_bwd(LineArgs gq) {
+__global__ void __launch_bounds__(32 * kNearWarps, 5) k_line_near_bwd(LineArgs gq) {
     extern __shared__ float4 smem4[];
     float *s_g = reinterpret_cast<float *>(smem4);                                 // [NDG][T] G * stim
     float2 *s_sum = reinterpret_cast<float2 *>(s_g + NDG * T);                     // [kNearBatch]
