@@ -67,7 +67,8 @@ typedef enum {
     PZ_ENOMEM = 2,    /* device or host allocation failed */
     PZ_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
     PZ_ETIMEOUT = 4,  /* a bounded device-side wait gave up (batched scheduler) */
-    PZ_ESTATE = 5     /* call order violated (e.g. pz_flux before pz_line_opacity) */
+    PZ_ESTATE = 5,    /* call order violated (e.g. pz_flux before pz_line_opacity) */
+    PZ_ENUMERIC = 6   /* a device-side iterative solve did not converge (results unreliable) */
 } pz_status;
 
 typedef enum {
@@ -393,13 +394,16 @@ pz_status pz_set_tiling(pz_ctx *ctx, int32_t lambda_per_thread, int32_t depth_pe
 pz_status pz_autotune(pz_ctx *ctx, int32_t with_backward, int32_t reps, int32_t *best, double *best_ms,
                       void *stream);
 
-/* Device status of the context's bounded waits.  The far-wing line kernels stage
- * each chunk of line prefactors into shared memory with bulk copies that complete
- * on an mbarrier; a CTA that waits longer than 1 s for a chunk gives up, records the
- * failure in the context's device status word and stops (its outputs are then
- * incomplete) instead of hanging the GPU.  This call synchronises `stream`, stores
- * the status word in *flags (host, may be NULL; bit 0 = a far-wing chunk never
- * arrived), clears it, and returns PZ_ETIMEOUT if it was non-zero, else PZ_OK. */
+/* Device status word of the context, set by kernels that cannot finish normally
+ * without a host round trip:
+ *   bit 0: a bounded device-side wait gave up (outputs incomplete);
+ *   bit 1: the iterative refinement of the scattering source (Eq. 6, pz_set_scattering)
+ *          reached its round limit without the correction falling below 1e-14 of the
+ *          solution, in the forward or the reverse pass (the flux or the gradients of
+ *          that wavelength rest on an unconverged solve).
+ * This call synchronises `stream`, stores the status word in *flags (host, may be
+ * NULL), clears it, and returns PZ_ETIMEOUT if bit 0 was set, PZ_ENUMERIC if bit 1
+ * was set, else PZ_OK. */
 pz_status pz_sync_status(pz_ctx *ctx, void *stream, int32_t *flags);
 
 /* ---- profiling ------------------------------------------------------------- */

@@ -28,9 +28,9 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "libpz.so")
 _lib = None
 
-PZ_OK, PZ_EINVAL, PZ_ENOMEM, PZ_ECUDA, PZ_ETIMEOUT, PZ_ESTATE = range(6)
+PZ_OK, PZ_EINVAL, PZ_ENOMEM, PZ_ECUDA, PZ_ETIMEOUT, PZ_ESTATE, PZ_ENUMERIC = range(7)
 PZ_FP64, PZ_MIXED = 0, 1
-_STATUS = {1: "PZ_EINVAL", 2: "PZ_ENOMEM", 3: "PZ_ECUDA", 4: "PZ_ETIMEOUT", 5: "PZ_ESTATE"}
+_STATUS = {1: "PZ_EINVAL", 2: "PZ_ENOMEM", 3: "PZ_ECUDA", 4: "PZ_ETIMEOUT", 5: "PZ_ESTATE", 6: "PZ_ENUMERIC"}
 
 _dp = C.POINTER(C.c_double)
 _fp = C.POINTER(C.c_float)
@@ -410,7 +410,8 @@ def pz_probe_wait(limit_ns, stream=None) -> int:
 
 
 def pz_sync_status(ctx, stream=None) -> int:
-    """Synchronise, read and clear the context's device status word (raises PZ_ETIMEOUT if set)."""
+    """Synchronise, read and clear the context's device status word (raises PZ_ETIMEOUT if a bounded
+    wait gave up, PZ_ENUMERIC if a scattering-source refinement did not converge)."""
     f = C.c_int32(0)
     _check(load().pz_sync_status(ctx, _stream(stream), C.byref(f)))
     return f.value

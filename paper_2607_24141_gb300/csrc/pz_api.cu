@@ -1480,8 +1480,10 @@ pz_status pz_sync_status(pz_ctx *c, void *stream, int32_t *flags) {
     if (h != 0) {
         PZ_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int32_t), s), "pz_sync_status");
         PZ_CUDA(cudaStreamSynchronize(s), "pz_sync_status");
-        return fail(PZ_ETIMEOUT, "pz_sync_status: a far-wing line kernel gave up waiting for a staged chunk "
-                                 "(its outputs are incomplete)");
+        if (h & kStatusWaitGaveUp)
+            return fail(PZ_ETIMEOUT, "pz_sync_status: a bounded device-side wait gave up (outputs incomplete)");
+        return fail(PZ_ENUMERIC, "pz_sync_status: the scattering-source refinement did not converge for some "
+                                 "wavelength (flux or gradients unreliable there)");
     }
     return PZ_OK;
 }

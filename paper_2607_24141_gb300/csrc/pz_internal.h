@@ -43,6 +43,10 @@ constexpr int kDawsonNodes = 6 * kDawsonPerUnit + 1;
 constexpr int kWeidN = 16;        // Weideman rational order (FP32 core)
 constexpr int kWeidN64 = 32;      // Weideman rational order (FP64 plain form)
 
+// Bits of the context's device status word (pz_sync_status).
+constexpr int kStatusWaitGaveUp = 1;      // a bounded device-side wait gave up
+constexpr int kStatusScatNoConverge = 2;  // the scattering-source refinement hit its round limit
+
 // Scale of the far-wing prefactors and offsets: K = 2^36/k^2 with k = c/dv_D, U = 2^36 u^2.
 constexpr float kKScale = 68719476736.0f;
 

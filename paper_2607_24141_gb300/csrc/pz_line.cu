@@ -550,7 +550,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint64
     }
 }
 
-constexpr int kStatusFarWait = 1;                   // status bit: a bounded wait gave up
 
 // Per-warp flags of a line over the tile (4: every layer of the slab rejected by the
 // centre test, nothing to evaluate): bit 0 if the line's window covers the tile
@@ -2239,7 +2238,7 @@ __global__ void k_probe_wait(uint64_t limit_ns, int32_t *status) {
     }
     __syncthreads();
     const bool ok = mbar_wait(&bar, 0, limit_ns);
-    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, kStatusFarWait);
+    if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, kStatusWaitGaveUp);
 }
 
 cudaError_t launch_probe_wait(uint64_t limit_ns, int32_t *status, cudaStream_t s) {

@@ -311,6 +311,7 @@ struct ScatArgs {
     double *F, *Fc;
     const double *dFbar;   // adjoint: dL/dF [S][nlam]
     void *Gt;              // adjoint: G stim [S][nd][ld]
+    int *status;           // context status word: kStatusScatNoConverge if a refinement hit its limit
 };
 
 constexpr int kScatThreads = 256;
@@ -571,8 +572,10 @@ __device__ void scat_lu(const ScatCol &c) {
 
 // Iterative refinement with FP64 residuals of M x = rhs (TRANS false) or M^T x = rhs:
 // x += (LU)^-1 (rhs - M x) until the correction is below 1e-14 of x.  rhs and x of nd.
+// A solve that reaches kScatMaxRefine rounds without converging sets
+// kStatusScatNoConverge in the context's status word (read by pz_sync_status).
 template <bool TRANS>
-__device__ void scat_refine(const ScatCol &c, const double *rhs, double *x, int *s_done) {
+__device__ void scat_refine(const ScatCol &c, const double *rhs, double *x, int *s_done, int *status) {
     const int nd = c.nd, W = c.W, tid = threadIdx.x;
     for (int d = tid; d < nd; d += blockDim.x) {
         x[d] = 0.0;
@@ -608,6 +611,10 @@ __device__ void scat_refine(const ScatCol &c, const double *rhs, double *x, int 
         }
         __syncthreads();
         if (*s_done) break;
+        if (it + 1 == kScatMaxRefine) {
+            if (tid == 0 && status) atomicOr(status, kStatusScatNoConverge);
+            break;
+        }
         for (int j = tid; j < nd; j += blockDim.x) {
             double r = rhs[j] - x[j];
             if (!TRANS) {
@@ -646,7 +653,7 @@ __global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
         scat_lu(c);
         for (int d = tid; d < nd; d += blockDim.x) c.a[d] = c.Lam[(size_t)d * c.W + nd];
         __syncthreads();
-        scat_refine<false>(c, c.a, c.S, &s_done);
+        scat_refine<false>(c, c.a, c.S, &s_done, g.status);
         // emergent flux of the solved source, the closed form of the LTE kernel
         for (int d = tid; d < nd; d += blockDim.x) expn234(c.tau[d], c.e2[d], c.e3[d], c.e4[d]);
         __syncthreads();
@@ -692,7 +699,7 @@ __global__ void __launch_bounds__(kScatThreads) k_rt_adjoint_scatter(ScatArgs g)
     scat_lu(c);
     for (int d = tid; d < nd; d += blockDim.x) c.a[d] = c.Lam[(size_t)d * W + nd];
     __syncthreads();
-    scat_refine<false>(c, c.a, c.S, &s_done);
+    scat_refine<false>(c, c.a, c.S, &s_done, g.status);
     // J = Lambda S, E_n at the layers
     for (int j = tid; j < nd; j += blockDim.x) {
         const double *row = c.Lam + (size_t)j * W;
@@ -743,7 +750,7 @@ __global__ void __launch_bounds__(kScatThreads) k_rt_adjoint_scatter(ScatArgs g)
         c.dF[d] = 2.0 * kPI * Fb * df;
     }
     __syncthreads();
-    scat_refine<true>(c, c.a, c.mu, &s_done);
+    scat_refine<true>(c, c.a, c.mu, &s_done, g.status);
     // dJ_j/dtau_m into the Lambda area (Lambda is no longer needed), one row per thread
     const double Szero = c.S[0] - s0 * t0;
     for (int j = tid; j < nd; j += blockDim.x) {
@@ -827,6 +834,7 @@ static ScatArgs scatter_args(pz_ctx *c) {
     g.Fc = c->d_Fc;
     g.dFbar = c->d_dFbar;
     g.Gt = c->prec == PZ_MIXED ? (void *)c->d_Gt : (void *)c->d_Gt64;
+    g.status = c->d_status;
     return g;
 }
 

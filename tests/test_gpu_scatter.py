@@ -112,3 +112,29 @@ def test_scattering_gradients(oracle, n_depth, instrument):
                 rel_metric(got["g_ab"][:prob.n_elem], gab).max())
         print("scattering gradients nd=%d prec=%d:" % (n_depth, prec), errs)
         assert max(errs) < tol, (prec, errs)
+
+
+@pytest.mark.parametrize("r0", [1e4, 1e8])
+def test_scattering_dominated_solve_converges_or_reports(oracle, r0):
+    """eps near 0 in the upper layers (sigma_c up to r0 kappa_c): the FP64-refined solve
+    either converges, and then F and f match the oracle's at the parity bars, or it
+    reports PZ_ENUMERIC through pz_sync_status; an unconverged result is never returned
+    silently."""
+    prob = tiny_problem(n_lambda=160, n_depth=40, n_lines=20, W=60, seed=41, lam0=340.0)
+    prob.lines.log_gf[:] -= 3.0
+    sc = I.with_scattering(prob, r0=r0)
+    ref = oracle.forward(sc)
+    for prec, ftol in ((pz.PZ_MIXED, 1e-5), (pz.PZ_FP64, 1e-9)):
+        got = run_forward(sc, prec, want_kline=False)
+        s = got["synth"]
+        try:
+            pz.pz_sync_status(s.ctx)
+            converged = True
+        except pz.PzError as e:
+            assert e.status == pz.PZ_ENUMERIC, e
+            converged = False
+        eF = float(np.max(np.abs(got["F"] / ref["F"] - 1)))
+        print("r0 %.0e prec %d: converged %s, F rel err %.3g" % (r0, prec, converged, eF))
+        if converged:
+            assert eF < ftol, eF
+        s.close()
