@@ -53,6 +53,7 @@
 #ifndef PZ_H
 #define PZ_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -398,9 +399,11 @@ pz_status pz_autotune(pz_ctx *ctx, int32_t with_backward, int32_t reps, int32_t 
  * without a host round trip:
  *   bit 0: a bounded device-side wait gave up (outputs incomplete);
  *   bit 1: the iterative refinement of the scattering source (Eq. 6, pz_set_scattering)
- *          reached its round limit without the correction falling below 1e-14 of the
- *          solution, in the forward or the reverse pass (the flux or the gradients of
- *          that wavelength rest on an unconverged solve).
+ *          stopped with its last correction above 1e-9 of the solution (stalled,
+ *          growing, or out of rounds), in the forward or the reverse pass: the flux or
+ *          the gradients of that wavelength rest on an unconverged solve.  Refinement
+ *          ends at a correction below 1e-14 of the solution, or where the correction
+ *          stops halving per round.
  * This call synchronises `stream`, stores the status word in *flags (host, may be
  * NULL), clears it, and returns PZ_ETIMEOUT if bit 0 was set, PZ_ENUMERIC if bit 1
  * was set, else PZ_OK. */
@@ -433,6 +436,26 @@ pz_status pz_set_profiling(pz_ctx *ctx, int32_t enable);
  * profiling was enabled, for the first nk families (ms, counts: host arrays
  * [nk]).  Synchronises on the recorded events. */
 pz_status pz_kernel_times(pz_ctx *ctx, double *ms, int64_t *counts, int32_t nk);
+
+/* ---- device memory ------------------------------------------------------------ */
+
+/* The library's device buffers (context tables, work queues, outputs it keeps, scratch)
+ * come from cudaMalloc and go back through cudaFree unless the caller installs its own
+ * allocator here, e.g. a framework that accounts for every byte of device memory in
+ * its own pool or caps it.  Not a step of the paper's method: host-side plumbing.
+ *   alloc(bytes, user) returns device memory of the current device, aligned to 256
+ *     bytes (as cudaMalloc), or NULL on failure; the call that needed it then returns
+ *     PZ_ENOMEM and frees what it had taken (misaligned memory is handed back to
+ *     free_fn and treated as a failure);
+ *   free_fn(ptr, user) releases memory alloc returned;
+ *   user is passed through unchanged.
+ * Both functions, or neither (NULL, NULL: back to cudaMalloc / cudaFree).  The
+ * allocator is process-wide and may change only while no context exists (PZ_ESTATE
+ * otherwise), so every buffer is freed by the allocator that made it.  Errors:
+ * PZ_EINVAL (exactly one function NULL), PZ_ESTATE. */
+typedef void *(*pz_alloc_fn)(size_t bytes, void *user);
+typedef void (*pz_free_fn)(void *ptr, void *user);
+pz_status pz_set_allocator(pz_alloc_fn alloc, pz_free_fn free_fn, void *user);
 
 /* ---- allocation-free variant -------------------------------------------------- */
 

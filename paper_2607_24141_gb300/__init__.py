@@ -96,6 +96,7 @@ _SIGS = {
     "pz_group_eval": (C.c_int, [_vp, _vp, _vp, C.c_int64, _vp, _vp, _vp, _vp]),
     "pz_build_line_groups": (C.c_int, [C.c_int64, _vp, _vp, _vp, _vp, C.c_double, C.c_double, _vp,
                                        C.POINTER(C.c_int64)]),
+    "pz_set_allocator": (C.c_int, [_vp, _vp, _vp]),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -196,6 +197,46 @@ def pz_calib_step(ctx, y, w=None, lr_gf=0.0, lr_g6=0.0, lr_ab=0.0, loss=None, g_
 
 def pz_destroy(ctx: int):
     _check(load().pz_destroy(ctx))
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_allocator_refs = None   # keeps the installed callbacks alive
+
+
+def pz_set_allocator(alloc=None, free=None, user=None):
+    """Install device-memory callbacks for the library (alloc(bytes, user) -> int pointer
+    or 0, free(ptr, user)), or, with no arguments, go back to cudaMalloc / cudaFree.
+    Python callables are wrapped as C function pointers and kept alive here."""
+    global _allocator_refs
+    if (alloc is None) != (free is None):
+        raise PzError(PZ_EINVAL, "pz_set_allocator: give both functions or neither")
+    if alloc is None:
+        _check(load().pz_set_allocator(None, None, None))
+        _allocator_refs = None
+        return
+    a = alloc if isinstance(alloc, ALLOC_FN) else ALLOC_FN(lambda n, u: alloc(int(n), u) or 0)
+    f = free if isinstance(free, FREE_FN) else FREE_FN(lambda p, u: free(int(p or 0), u))
+    _check(load().pz_set_allocator(C.cast(a, C.c_void_p), C.cast(f, C.c_void_p), user))
+    _allocator_refs = (a, f)
+
+
+def torch_allocator():
+    """(alloc, free) callbacks that take the library's device memory from PyTorch's
+    caching allocator on the current device (a framework-owned pool)."""
+    import torch
+
+    def alloc(n, _user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(n)))
+        except RuntimeError:
+            return 0
+
+    def free(p, _user):
+        if p:
+            torch.cuda.caching_allocator_delete(p)
+
+    return alloc, free
 
 
 def pz_set_corrections(ctx, dlog_gf=None, dlog_gamma6=None, dabund=None, elem_of_species=None,

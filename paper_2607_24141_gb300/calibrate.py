@@ -13,14 +13,21 @@ Sun-Arcturus fit the same way (40 L-BFGS updates).
 """
 from __future__ import annotations
 
+import hashlib
 import time
 
+import numpy as np
 
-def _minimise(set_and_eval, n_params, dev, n_updates, history):
-    """L-BFGS on a float64 device vector of n_params; set_and_eval(x) -> (loss, grad)."""
+
+def _minimise(set_and_eval, n_params, dev, n_updates, history, resume=None):
+    """L-BFGS on a float64 device vector of n_params; set_and_eval(x) -> (loss, grad).
+    resume: {"x", "optimizer"} of an earlier run (see save_state) to continue from."""
     import torch
 
     x = torch.zeros(n_params, dtype=torch.float64, device=dev, requires_grad=True)
+    if resume is not None:
+        with torch.no_grad():
+            x.copy_(torch.as_tensor(resume["x"], dtype=torch.float64, device=dev))
     evals = [0]
     t_eval = [0.0]
 
@@ -35,6 +42,8 @@ def _minimise(set_and_eval, n_params, dev, n_updates, history):
 
     opt = torch.optim.LBFGS([x], lr=1.0, max_iter=n_updates, max_eval=4 * n_updates, history_size=history,
                             line_search_fn="strong_wolfe", tolerance_grad=0.0, tolerance_change=0.0)
+    if resume is not None and resume.get("optimizer") is not None:
+        opt.load_state_dict(resume["optimizer"])
     sync = torch.cuda.synchronize if x.is_cuda else (lambda: None)
     objective()                                 # untimed: captures the step's graph for these buffers
     evals[0] = 0
@@ -49,10 +58,11 @@ def _minimise(set_and_eval, n_params, dev, n_updates, history):
     updates = int(opt.state[x]["n_iter"])
     final = objective()                         # the objective at the accepted corrections
     return x.detach(), {"loss_start": loss0, "loss_final": final, "evals": n_evals, "updates": updates,
-                        "seconds": seconds, "eval_seconds": eval_seconds}
+                        "seconds": seconds, "eval_seconds": eval_seconds, "x": x.detach().clone(),
+                        "optimizer": opt.state_dict()}
 
 
-def lbfgs(synth, y, w=None, n_updates=40, history=10, fit_gamma6=True, stream=None):
+def lbfgs(synth, y, w=None, n_updates=40, history=10, fit_gamma6=True, stream=None, resume=None):
     """Minimise L = sum_stars sum_p w (y - f)^2 over the shared per-line corrections
     Delta log gf (and Delta log gamma_6).
 
@@ -63,7 +73,8 @@ def lbfgs(synth, y, w=None, n_updates=40, history=10, fit_gamma6=True, stream=No
     objective evaluations of the loop, "updates": L-BFGS iterations, "seconds": wall
     time of the loop, after one untimed evaluation that captures the step,
     "eval_seconds": the part of it spent from each evaluation's launch to its loss
-    readback}.
+    readback, "x" and "optimizer": the final parameter vector and the L-BFGS state, which
+    save_state stores and resume= takes back to continue the fit}.
     """
     import torch
 
@@ -83,13 +94,13 @@ def lbfgs(synth, y, w=None, n_updates=40, history=10, fit_gamma6=True, stream=No
         synth.calib_step(y, w, 0.0, 0.0, 0.0, loss, g_gf, g_g6, None, stream)
         return loss[0], (torch.cat([g_gf, g_g6]) if fit_gamma6 else g_gf)
 
-    x, res = _minimise(set_and_eval, 2 * nl if fit_gamma6 else nl, dev, n_updates, history)
+    x, res = _minimise(set_and_eval, 2 * nl if fit_gamma6 else nl, dev, n_updates, history, resume)
     res["dlog_gf"] = x[:nl].float().clone()
     res["dlog_gamma6"] = x[nl:].float().clone() if fit_gamma6 else torch.zeros_like(res["dlog_gf"])
     return res
 
 
-def lbfgs_groups(synth, y, w, group_of_line, n_groups, n_updates=40, history=10, stream=None):
+def lbfgs_groups(synth, y, w, group_of_line, n_groups, n_updates=40, history=10, stream=None, resume=None):
     """Minimise the chi-square over the four corrections of Eq. 10 per linked group
     (Delta log gf, Delta log gamma_rad, Delta log gamma_4, Delta log gamma_6), each
     shared by the group's members (Sec. 6).  group_of_line: host int32 [n_lines] in
@@ -111,6 +122,77 @@ def lbfgs_groups(synth, y, w, group_of_line, n_groups, n_updates=40, history=10,
         pz_group_eval(synth.ctx, y, w, x32, loss, g, stream)
         return loss[0], g.view(-1)
 
-    x, res = _minimise(set_and_eval, 4 * G, dev, n_updates, history)
-    res["x"] = x.view(4, G).float().clone()
+    x, res = _minimise(set_and_eval, 4 * G, dev, n_updates, history, resume)
+    res["groups"] = x.view(4, G).float().clone()
     return res
+
+
+# ---------------------------------------------------------------------------
+# saving and restoring a calibration (corrections bound to their line list)
+# ---------------------------------------------------------------------------
+
+def catalog_digest(lines) -> str:
+    """SHA-256 of the line list a set of corrections applies to (centres, log gf,
+    E_low, the three damping constants and species, in caller order): corrections are
+    an overlay on one catalog and must not be applied to another."""
+    h = hashlib.sha256()
+    for a, dt in ((lines.lambda_nm, np.float64), (lines.log_gf, np.float32), (lines.E_low_eV, np.float32),
+                  (lines.log_gamma_rad, np.float32), (lines.log_gamma4, np.float32),
+                  (lines.log_gamma6, np.float32), (lines.species, np.int32)):
+        h.update(np.ascontiguousarray(a, dtype=dt).tobytes())
+    h.update(str(int(lines.half_window)).encode())
+    return h.hexdigest()
+
+
+def save_state(path, synth, result=None, meta=None):
+    """Write the context's current corrections (Delta log gf, Delta log gamma_6, the
+    radiative and Stark corrections and the abundance offsets), the digest of its line
+    list and, if given, the optimiser state of an lbfgs / lbfgs_groups result
+    ("x", "optimizer") to path (torch.save format)."""
+    import torch
+    gf, g6, ab = synth.get_corrections()
+    rad, g4 = synth.get_damping_corrections()
+    state = {"digest": catalog_digest(synth.prob.lines), "n_lines": int(synth.n_lines),
+             "dlog_gf": gf, "dlog_gamma6": g6, "dlog_gamma_rad": rad, "dlog_gamma4": g4, "dabund": ab,
+             "meta": dict(meta or {})}
+    if result is not None:
+        state["x"] = result["x"].detach().cpu()
+        state["optimizer"] = _to_cpu(result["optimizer"])
+    torch.save(state, path)
+
+
+def load_state(path, synth, device=None):
+    """Read a file written by save_state, check that it belongs to this context's line
+    list (ValueError otherwise), apply its corrections to the context and return the
+    state; its "x" / "optimizer" (if present) continue a fit through resume=."""
+    import torch
+    state = torch.load(path, map_location="cpu", weights_only=False)
+    if state.get("digest") != catalog_digest(synth.prob.lines) or state.get("n_lines") != synth.n_lines:
+        raise ValueError("load_state: %s holds corrections for another line list" % path)
+    synth.set_corrections(state["dlog_gf"], state["dlog_gamma6"], state["dabund"])
+    synth.set_damping_corrections(state["dlog_gamma_rad"], state["dlog_gamma4"])
+    if "optimizer" in state and device is not None:
+        state["optimizer"] = _to_device(state["optimizer"], device)
+    return state
+
+
+def _to_cpu(obj):
+    import torch
+    if isinstance(obj, torch.Tensor):
+        return obj.detach().cpu()
+    if isinstance(obj, dict):
+        return {k: _to_cpu(v) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return type(obj)(_to_cpu(v) for v in obj)
+    return obj
+
+
+def _to_device(obj, device):
+    import torch
+    if isinstance(obj, torch.Tensor):
+        return obj.to(device)
+    if isinstance(obj, dict):
+        return {k: _to_device(v, device) for k, v in obj.items()}
+    if isinstance(obj, (list, tuple)):
+        return type(obj)(_to_device(v, device) for v in obj)
+    return obj

@@ -2,11 +2,14 @@
 // preparation (sorting, per-tile line ranges, device tables) and the
 // orchestration of the kernels in pz_line.cu and pz_rt.cu.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -14,6 +17,16 @@
 #include "pz_internal.h"
 
 namespace pz {
+
+// An NVTX range around each entry point (a profiler's timeline shows the pz_* calls and
+// the kernels they enqueue; without a profiler attached a push and a pop cost a few ns).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+#define PZ_RANGE(name) ::pz::NvtxRange pz_nvtx_range_(name)
 
 static thread_local std::string g_err;
 
@@ -113,11 +126,55 @@ static cudaError_t timed(pz_ctx *c, cudaStream_t s, int kid, Fn &&fn) {
     } while (0)
 #define PZ_CUDA(expr, what) PZ_TRY(cuda_check((expr), what))
 
+// Device memory of the library: cudaMalloc / cudaFree, or the caller's allocator
+// (pz_set_allocator).  The allocator may change only while no context exists, so that
+// every buffer is freed by the allocator that made it.
+static std::mutex g_alloc_mu;
+static pz_alloc_fn g_alloc = nullptr;
+static pz_free_fn g_free = nullptr;
+static void *g_alloc_user = nullptr;
+static std::atomic<int> g_live_ctx{0};
+constexpr size_t kAllocAlign = 256;   // alignment a caller's allocator must give (as cudaMalloc)
+
+static cudaError_t dev_alloc(void **p, size_t bytes) {
+    pz_alloc_fn a;
+    pz_free_fn f;
+    void *u;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        a = g_alloc;
+        f = g_free;
+        u = g_alloc_user;
+    }
+    if (!a) return cudaMalloc(p, bytes);
+    *p = a(bytes, u);
+    if (*p && ((uintptr_t)*p % kAllocAlign) != 0) {   // misaligned memory is refused
+        f(*p, u);
+        *p = nullptr;
+    }
+    return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+}
+
+static void dev_free(void *p) {
+    if (!p) return;
+    pz_free_fn f;
+    void *u;
+    {
+        std::lock_guard<std::mutex> lk(g_alloc_mu);
+        f = g_free;
+        u = g_alloc_user;
+    }
+    if (f)
+        f(p, u);
+    else
+        cudaFree(p);
+}
+
 template <typename T>
 static pz_status dalloc(T **p, size_t n, const char *what) {
     *p = nullptr;
     if (n == 0) n = 1;
-    return cuda_check(cudaMalloc((void **)p, n * sizeof(T)), what);
+    return cuda_check(dev_alloc((void **)p, n * sizeof(T)), what);
 }
 
 template <typename T>
@@ -139,9 +196,7 @@ static bool is_device_ptr(const void *p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
-static void dfree(void *p) {
-    if (p) cudaFree(p);
-}
+static void dfree(void *p) { dev_free(p); }
 
 // Work items of the persistent line kernels: (star, tile * groups + group, lo, hi) with
 // [lo, hi) the star's lines that the item must visit, ordered by estimated cost,
@@ -354,6 +409,7 @@ static void destroy_ctx(pz_ctx *c) {
     for (auto e : c->ev_pool) cudaEventDestroy(e);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
+    --g_live_ctx;
 }
 
 // Validation of one atmosphere; shared fields are checked against ref (star 0).
@@ -433,6 +489,7 @@ static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, 
     PZ_CUDA(cudaGetDevice(&dev), "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return fail(PZ_EINVAL, w + ": device ordinal beyond the supported 64");
     pz_ctx *c = new pz_ctx();
+    ++g_live_ctx;
     c->device = dev;
     cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, dev);
     c->prec = prec;
@@ -588,7 +645,7 @@ static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, 
 
     // ---- resident buffers ----
     size_t ksz = (prec == PZ_MIXED) ? sizeof(float) : sizeof(double);
-    if (cuda_check(cudaMalloc(&c->d_kline, ksz * SD * c->ld), "kappa_line buffer") ||
+    if (cuda_check(dev_alloc(&c->d_kline, ksz * SD * c->ld), "kappa_line buffer") ||
         (prec == PZ_MIXED && dalloc(&c->d_knear, SD * c->ld, "kappa_line buffer")) ||
         dalloc(&c->d_F, (size_t)S * nlam, "flux") || dalloc(&c->d_Fc, (size_t)S * nlam, "flux") ||
         dalloc(&c->d_ctr, 4, "work counters") || dalloc(&c->d_status, 1, "status word"))
@@ -638,9 +695,9 @@ static pz_status ensure_far_tables(pz_ctx *c) {
         dfree(c->d_finfo);
         c->d_finfo = nullptr;
         c->finfo_cap = 0;
-        if (cudaMalloc(&c->d_finfo, ib) != cudaSuccess) {
+        if (dev_alloc(&c->d_finfo, ib) != cudaSuccess) {
             cudaGetLastError();
-            return fail(PZ_ENOMEM, "far-wing line records: cudaMalloc failed");
+            return fail(PZ_ENOMEM, "far-wing line records: allocation failed");
         }
         c->finfo_cap = ib;
     }
@@ -712,16 +769,19 @@ using namespace pz;
 extern "C" {
 
 pz_status pz_create(const pz_atmos *atmos, const pz_linelist *lines, pz_precision precision, pz_ctx **out) {
+    PZ_RANGE("pz_create");
     return create_impl(1, atmos, lines, nullptr, nullptr, precision, out, "pz_create");
 }
 
 pz_status pz_create_batch(int32_t n_stars, const pz_atmos *atmos, const pz_linelist *lines,
                           const int64_t *subset_offsets, const int32_t *subset_index, pz_precision precision,
                           pz_ctx **out) {
+    PZ_RANGE("pz_create_batch");
     return create_impl(n_stars, atmos, lines, subset_offsets, subset_index, precision, out, "pz_create_batch");
 }
 
 pz_status pz_destroy(pz_ctx *ctx) {
+    PZ_RANGE("pz_destroy");
     if (!ctx) return PZ_OK;
     cudaDeviceSynchronize();
     destroy_ctx(ctx);
@@ -729,6 +789,19 @@ pz_status pz_destroy(pz_ctx *ctx) {
 }
 
 const char *pz_last_error(void) { return g_err.c_str(); }
+
+pz_status pz_set_allocator(pz_alloc_fn alloc, pz_free_fn free_fn, void *user) {
+    PZ_RANGE("pz_set_allocator");
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(PZ_EINVAL, "pz_set_allocator: give both functions or neither");
+    if (g_live_ctx.load() != 0)
+        return fail(PZ_ESTATE, "pz_set_allocator: contexts exist; destroy them before changing the allocator");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_user = alloc ? user : nullptr;
+    return PZ_OK;
+}
 
 int64_t pz_eval_count(const pz_ctx *ctx) { return ctx ? ctx->n_evals : 0; }
 
@@ -742,6 +815,7 @@ int64_t pz_star_lines(const pz_ctx *ctx, int32_t star) {
 }
 
 pz_status pz_set_tiling(pz_ctx *c, int32_t J, int32_t DS, int32_t GW, int32_t LC, int32_t MINB) {
+    PZ_RANGE("pz_set_tiling");
     if (!c) return fail(PZ_EINVAL, "pz_set_tiling: ctx is NULL");
     Tiling t = c->tiling;
     if (J > 0) t.J = J;
@@ -754,6 +828,7 @@ pz_status pz_set_tiling(pz_ctx *c, int32_t J, int32_t DS, int32_t GW, int32_t LC
 }
 
 pz_status pz_autotune(pz_ctx *c, int32_t with_backward, int32_t reps, int32_t *best, double *best_ms, void *stream) {
+    PZ_RANGE("pz_autotune");
     if (!c) return fail(PZ_EINVAL, "pz_autotune: ctx is NULL");
     if (c->prec != PZ_MIXED) return fail(PZ_EINVAL, "pz_autotune: only the mixed-precision form has tilings");
     if (reps < 1 || reps > 100) return fail(PZ_EINVAL, "pz_autotune: reps must be in [1, 100]");
@@ -867,6 +942,7 @@ pz_status pz_autotune(pz_ctx *c, int32_t with_backward, int32_t reps, int32_t *b
 }
 
 pz_status pz_set_centre_test(pz_ctx *c, double eta, int64_t *kept_pairs, void *stream) {
+    PZ_RANGE("pz_set_centre_test");
     if (!c) return fail(PZ_EINVAL, "pz_set_centre_test: ctx is NULL");
     if (!(std::isfinite(eta) && eta >= 0.0)) return fail(PZ_EINVAL, "pz_set_centre_test: eta must be finite and >= 0");
     cudaStream_t s = (cudaStream_t)stream;
@@ -905,6 +981,7 @@ pz_status pz_set_centre_test(pz_ctx *c, double eta, int64_t *kept_pairs, void *s
 
 pz_status pz_set_corrections(pz_ctx *c, const float *dgf, const float *dg6, const float *dab,
                              const int32_t *eos, int32_t n_elem, void *stream) {
+    PZ_RANGE("pz_set_corrections");
     if (!c) return fail(PZ_EINVAL, "pz_set_corrections: ctx is NULL");
     if (n_elem < 0) return fail(PZ_EINVAL, "pz_set_corrections: n_elem < 0");
     if (dab && (n_elem == 0 || !eos)) return fail(PZ_EINVAL, "pz_set_corrections: dabund needs n_elem > 0 and elem_of_species");
@@ -963,6 +1040,7 @@ pz_status pz_set_corrections(pz_ctx *c, const float *dgf, const float *dg6, cons
 }
 
 pz_status pz_get_corrections(pz_ctx *c, float *dgf, float *dg6, float *dab, void *stream) {
+    PZ_RANGE("pz_get_corrections");
     if (!c) return fail(PZ_EINVAL, "pz_get_corrections: ctx is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = c->nl_caller;
@@ -980,6 +1058,7 @@ pz_status pz_get_corrections(pz_ctx *c, float *dgf, float *dg6, float *dab, void
 }
 
 pz_status pz_line_opacity(pz_ctx *c, float *kappa, void *stream) {
+    PZ_RANGE("pz_line_opacity");
     if (!c) return fail(PZ_EINVAL, "pz_line_opacity: ctx is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
@@ -1008,6 +1087,7 @@ pz_status pz_line_opacity(pz_ctx *c, float *kappa, void *stream) {
 }
 
 pz_status pz_flux(pz_ctx *c, double *F, double *Fc, void *stream) {
+    PZ_RANGE("pz_flux");
     if (!c) return fail(PZ_EINVAL, "pz_flux: ctx is NULL");
     if (!c->have_kline) return fail(PZ_ESTATE, "pz_flux: call pz_line_opacity first");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1023,6 +1103,7 @@ pz_status pz_flux(pz_ctx *c, double *F, double *Fc, void *stream) {
 
 pz_status pz_instrument(pz_ctx *c, double v_r, double v_b, double R_lsf, const double *pix, int64_t n_pix, float *f,
                         void *stream) {
+    PZ_RANGE("pz_instrument");
     if (!c) return fail(PZ_EINVAL, "pz_instrument: ctx is NULL");
     if (!c->have_flux) return fail(PZ_ESTATE, "pz_instrument: call pz_flux first");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1103,6 +1184,7 @@ pz_status pz_instrument(pz_ctx *c, double v_r, double v_b, double R_lsf, const d
 }
 
 pz_status pz_loss_chi2(pz_ctx *c, const float *y, const float *w, int64_t n, double *loss, float *dLdf, void *stream) {
+    PZ_RANGE("pz_loss_chi2");
     if (!c) return fail(PZ_EINVAL, "pz_loss_chi2: ctx is NULL");
     if (!c->have_inst) return fail(PZ_ESTATE, "pz_loss_chi2: call pz_instrument first");
     if (!y) return fail(PZ_EINVAL, "pz_loss_chi2: y is NULL");
@@ -1116,6 +1198,7 @@ pz_status pz_loss_chi2(pz_ctx *c, const float *y, const float *w, int64_t n, dou
 }
 
 pz_status pz_backward(pz_ctx *c, const float *dLdf, float *g_gf, float *g_g6, float *g_ab, void *stream) {
+    PZ_RANGE("pz_backward");
     if (!c) return fail(PZ_EINVAL, "pz_backward: ctx is NULL");
     if (!c->have_inst) return fail(PZ_ESTATE, "pz_backward: call pz_instrument first");
     if (!dLdf) return fail(PZ_EINVAL, "pz_backward: dL_df is NULL");
@@ -1127,6 +1210,7 @@ pz_status pz_backward(pz_ctx *c, const float *dLdf, float *g_gf, float *g_g6, fl
 
 pz_status pz_backward4(pz_ctx *c, const float *dLdf, float *g_gf, float *g_rad, float *g_g4, float *g_g6,
                        float *g_ab, void *stream) {
+    PZ_RANGE("pz_backward4");
     if (!c) return fail(PZ_EINVAL, "pz_backward4: ctx is NULL");
     if (!c->have_inst) return fail(PZ_ESTATE, "pz_backward4: call pz_instrument first");
     if (!dLdf) return fail(PZ_EINVAL, "pz_backward4: dL_df is NULL");
@@ -1156,6 +1240,7 @@ static pz_status enqueue_step(pz_ctx *c, const float *y, const float *w, double 
 
 pz_status pz_calib_step(pz_ctx *c, const float *y, const float *w, int64_t n, float lr_gf, float lr_g6, float lr_ab,
                         double *loss, float *g_gf, float *g_g6, float *g_ab, void *stream) {
+    PZ_RANGE("pz_calib_step");
     if (!c) return fail(PZ_EINVAL, "pz_calib_step: ctx is NULL");
     if (c->n_out <= 0) return fail(PZ_ESTATE, "pz_calib_step: call pz_instrument once first");
     if (!y) return fail(PZ_EINVAL, "pz_calib_step: y is NULL");
@@ -1223,6 +1308,7 @@ static pz_status set_master_corr(pz_ctx *c, const float *src, float *dst, cudaSt
 }
 
 pz_status pz_set_damping_corrections(pz_ctx *c, const float *dgrad, const float *dg4, void *stream) {
+    PZ_RANGE("pz_set_damping_corrections");
     if (!c) return fail(PZ_EINVAL, "pz_set_damping_corrections: ctx is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     c->launches = 0;
@@ -1234,6 +1320,7 @@ pz_status pz_set_damping_corrections(pz_ctx *c, const float *dgrad, const float 
 }
 
 pz_status pz_get_damping_corrections(pz_ctx *c, float *dgrad, float *dg4, void *stream) {
+    PZ_RANGE("pz_get_damping_corrections");
     if (!c) return fail(PZ_EINVAL, "pz_get_damping_corrections: ctx is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = c->nl_caller;
@@ -1245,6 +1332,7 @@ pz_status pz_get_damping_corrections(pz_ctx *c, float *dgrad, float *dg4, void *
 }
 
 pz_status pz_set_line_groups(pz_ctx *c, const int32_t *group_of_line, int64_t n_groups) {
+    PZ_RANGE("pz_set_line_groups");
     if (!c) return fail(PZ_EINVAL, "pz_set_line_groups: ctx is NULL");
     if (n_groups < 0 || n_groups > std::max<int64_t>(c->nl_caller, 1))
         return fail(PZ_EINVAL, "pz_set_line_groups: n_groups must be in [0, n_lines]");
@@ -1303,6 +1391,7 @@ static pz_status enqueue_group_eval(pz_ctx *c, const float *y, const float *w, c
 
 pz_status pz_group_eval(pz_ctx *c, const float *y, const float *w, int64_t n, const float *x, double *loss, float *g,
                         void *stream) {
+    PZ_RANGE("pz_group_eval");
     if (!c) return fail(PZ_EINVAL, "pz_group_eval: ctx is NULL");
     if (c->n_groups <= 0) return fail(PZ_ESTATE, "pz_group_eval: call pz_set_line_groups first");
     if (c->n_out <= 0) return fail(PZ_ESTATE, "pz_group_eval: call pz_instrument once first");
@@ -1358,6 +1447,7 @@ pz_status pz_group_eval(pz_ctx *c, const float *y, const float *w, int64_t n, co
 pz_status pz_build_line_groups(int64_t n, const double *lambda_nm, const float *E_low_eV, const int32_t *species,
                                const float *strength, double dE_eV, double dlam_nm, int32_t *group_of_line,
                                int64_t *n_groups) {
+    PZ_RANGE("pz_build_line_groups");
     if (n < 0 || (n > 0 && (!lambda_nm || !E_low_eV || !species || !strength || !group_of_line)) || !n_groups)
         return fail(PZ_EINVAL, "pz_build_line_groups: bad arguments");
     if (!(dE_eV >= 0.0) || !(dlam_nm >= 0.0) || !std::isfinite(dE_eV) || !std::isfinite(dlam_nm))
@@ -1407,6 +1497,7 @@ pz_status pz_build_line_groups(int64_t n, const double *lambda_nm, const float *
 }
 
 pz_status pz_set_scattering(pz_ctx *c, const double *sigma_c, void *stream) {
+    PZ_RANGE("pz_set_scattering");
     if (!c) return fail(PZ_EINVAL, "pz_set_scattering: ctx is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     if (!sigma_c) {
@@ -1439,6 +1530,7 @@ pz_status pz_set_scattering(pz_ctx *c, const double *sigma_c, void *stream) {
 }
 
 pz_status pz_set_profiling(pz_ctx *c, int32_t enable) {
+    PZ_RANGE("pz_set_profiling");
     if (!c) return fail(PZ_EINVAL, "pz_set_profiling: ctx is NULL");
     prof_fold(c);
     for (int k = 0; k < PZ_NK; ++k) {
@@ -1450,6 +1542,7 @@ pz_status pz_set_profiling(pz_ctx *c, int32_t enable) {
 }
 
 pz_status pz_kernel_times(pz_ctx *c, double *ms, int64_t *counts, int32_t nk) {
+    PZ_RANGE("pz_kernel_times");
     if (!c || nk < 0 || (nk > 0 && (!ms || !counts))) return fail(PZ_EINVAL, "pz_kernel_times: bad arguments");
     prof_fold(c);
     for (int k = 0; k < nk && k < PZ_NK; ++k) {
@@ -1464,6 +1557,7 @@ pz_status pz_kernel_times(pz_ctx *c, double *ms, int64_t *counts, int32_t nk) {
 }
 
 pz_status pz_probe_voigt(const float *a, const float *v, int64_t n, float *H, float *dH, void *stream) {
+    PZ_RANGE("pz_probe_voigt");
     if (n < 0 || (n > 0 && (!a || !v || !H))) return fail(PZ_EINVAL, "pz_probe_voigt: bad arguments");
     PZ_TRY(ensure_device_tables());
     PZ_CUDA(launch_probe_voigt(a, v, n, H, dH, (cudaStream_t)stream), "probe voigt");
@@ -1471,6 +1565,7 @@ pz_status pz_probe_voigt(const float *a, const float *v, int64_t n, float *H, fl
 }
 
 pz_status pz_sync_status(pz_ctx *c, void *stream, int32_t *flags) {
+    PZ_RANGE("pz_sync_status");
     if (!c) return fail(PZ_EINVAL, "pz_sync_status: ctx is NULL");
     cudaStream_t s = (cudaStream_t)stream;
     int32_t h = 0;
@@ -1489,6 +1584,7 @@ pz_status pz_sync_status(pz_ctx *c, void *stream, int32_t *flags) {
 }
 
 pz_status pz_probe_wait(int64_t limit_ns, int32_t *flags, void *stream) {
+    PZ_RANGE("pz_probe_wait");
     if (limit_ns < 1 || limit_ns > 1000000000) return fail(PZ_EINVAL, "pz_probe_wait: limit_ns must be in [1, 1e9]");
     if (!flags) return fail(PZ_EINVAL, "pz_probe_wait: flags is NULL");
     cudaStream_t s = (cudaStream_t)stream;
@@ -1507,6 +1603,7 @@ pz_status pz_probe_wait(int64_t limit_ns, int32_t *flags, void *stream) {
 }
 
 pz_status pz_probe_pipe(int32_t pipe, int32_t iters, double *ops_per_s, void *stream) {
+    PZ_RANGE("pz_probe_pipe");
     if (pipe < 0 || pipe > 2)
         return fail(PZ_EINVAL, "pz_probe_pipe: pipe must be 0 (FP32 FMA), 1 (MUFU) or 2 (FP64 FMA)");
     if (iters < 1 || iters > (1 << 20)) return fail(PZ_EINVAL, "pz_probe_pipe: iters must be in [1, 2^20]");
@@ -1539,6 +1636,7 @@ pz_status pz_probe_pipe(int32_t pipe, int32_t iters, double *ops_per_s, void *st
 }
 
 pz_status pz_probe_expn(const double *x, int64_t n, double *out, void *stream) {
+    PZ_RANGE("pz_probe_expn");
     if (n < 0 || (n > 0 && (!x || !out))) return fail(PZ_EINVAL, "pz_probe_expn: bad arguments");
     PZ_CUDA(launch_probe_expn(x, n, out, (cudaStream_t)stream), "probe expn");
     return PZ_OK;

@@ -571,16 +571,20 @@ __device__ void scat_lu(const ScatCol &c) {
 }
 
 // Iterative refinement with FP64 residuals of M x = rhs (TRANS false) or M^T x = rhs:
-// x += (LU)^-1 (rhs - M x) until the correction is below 1e-14 of x.  rhs and x of nd.
-// A solve that reaches kScatMaxRefine rounds without converging sets
+// x += (LU)^-1 (rhs - M x) until the correction is below 1e-14 of x, or until it stops
+// shrinking (at least halving per round after the second), which is where FP64
+// residuals of an ill-conditioned M (eps near 0) leave it.  A solve that stops with a
+// last correction above 1e-9 of x (stalled there, growing, or out of rounds) sets
 // kStatusScatNoConverge in the context's status word (read by pz_sync_status).
 template <bool TRANS>
 __device__ void scat_refine(const ScatCol &c, const double *rhs, double *x, int *s_done, int *status) {
     const int nd = c.nd, W = c.W, tid = threadIdx.x;
+    __shared__ double s_dprev;
     for (int d = tid; d < nd; d += blockDim.x) {
         x[d] = 0.0;
         c.res[d] = rhs[d];
     }
+    if (tid == 0) s_dprev = 0.0;
     __syncthreads();
     for (int it = 0; it < kScatMaxRefine; ++it) {
         if (tid < 32) {
@@ -607,14 +611,16 @@ __device__ void scat_refine(const ScatCol &c, const double *rhs, double *x, int 
                 dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
                 smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
             }
-            if (tid == 0) *s_done = dmax <= 1e-14 * smax;
+            if (tid == 0) {
+                const bool conv = dmax <= 1e-14 * smax;
+                const bool stop = conv || (it >= 2 && dmax >= 0.5 * s_dprev) || it + 1 == kScatMaxRefine;
+                if (stop && !conv && dmax > 1e-9 * smax && status) atomicOr(status, kStatusScatNoConverge);
+                s_dprev = dmax;
+                *s_done = stop;
+            }
         }
         __syncthreads();
         if (*s_done) break;
-        if (it + 1 == kScatMaxRefine) {
-            if (tid == 0 && status) atomicOr(status, kStatusScatNoConverge);
-            break;
-        }
         for (int j = tid; j < nd; j += blockDim.x) {
             double r = rhs[j] - x[j];
             if (!TRANS) {

@@ -83,3 +83,79 @@ def test_driver_without_gamma6():
     b = (y.double().numpy() - 1.0) * sw
     L_min = float(((A @ np.linalg.lstsq(A, b, rcond=None)[0] - b) ** 2).sum())
     assert res["loss_final"] <= L_min * (1 + 1e-3)
+
+
+class LinearSynthWithState(LinearSynth):
+    """LinearSynth with the read-back calls save_state needs and a line list."""
+
+    def __init__(self, n_lines, n_data, seed=0):
+        super().__init__(n_lines, n_data, seed)
+        from paper_2607_24141_gb300 import inputs as I
+        rng = np.random.default_rng(seed)
+        self.prob = type("P", (), {})()
+        self.prob.lines = I.LineList(
+            lambda_nm=np.sort(rng.uniform(1500, 1700, n_lines)), log_gf=rng.normal(-2, 1, n_lines).astype(np.float32),
+            E_low_eV=rng.uniform(0, 5, n_lines).astype(np.float32),
+            log_gamma_rad=np.full(n_lines, 8.0, np.float32), log_gamma4=np.full(n_lines, -5.5, np.float32),
+            log_gamma6=np.full(n_lines, -7.5, np.float32), species=rng.integers(0, 4, n_lines).astype(np.int32),
+            half_window=1500)
+        self.damp = (np.zeros(n_lines, np.float32), np.zeros(n_lines, np.float32))
+        self.ab = np.zeros(3, np.float32)
+
+    def get_corrections(self):
+        c = self.c.numpy().astype(np.float32)
+        return c[:self.n_lines].copy(), c[self.n_lines:].copy(), self.ab.copy()
+
+    def get_damping_corrections(self):
+        return self.damp[0].copy(), self.damp[1].copy()
+
+    def set_corrections(self, dlog_gf, dlog_gamma6, dabund, stream=None):
+        super().set_corrections(dlog_gf, dlog_gamma6, dabund, stream)
+        if dabund is not None:
+            self.ab = np.asarray(dabund, np.float32).copy()
+
+    def set_damping_corrections(self, rad, g4, stream=None):
+        self.damp = (np.asarray(rad, np.float32).copy(), np.asarray(g4, np.float32).copy())
+
+
+def _state_problem(seed):
+    s = LinearSynthWithState(40, 300, seed)
+    g = torch.Generator().manual_seed(seed + 1)
+    s.c = torch.randn(80, generator=g, dtype=torch.float64) * 0.1
+    y = (s.f() + torch.randn(300, generator=g, dtype=torch.float64) / 200).float()
+    s.c = torch.zeros(80, dtype=torch.float64)
+    return s, y, torch.full_like(y, 200.0 ** 2)
+
+
+def test_saved_fit_resumes_where_it_stopped(tmp_path):
+    """Six updates, save, load into a fresh context, six more: the same corrections as
+    twelve updates in one run (the L-BFGS history and step travel with the state)."""
+    s, y, w = _state_problem(7)
+    straight = calibrate.lbfgs(s, y, w, n_updates=12)
+    s, y, w = _state_problem(7)
+    first = calibrate.lbfgs(s, y, w, n_updates=6)
+    path = str(tmp_path / "fit.pt")
+    calibrate.save_state(path, s, first, meta={"note": "six updates"})
+    s2, y2, w2 = _state_problem(7)
+    state = calibrate.load_state(path, s2)
+    assert state["meta"]["note"] == "six updates"
+    np.testing.assert_array_equal(s2.c.numpy(), s.c.numpy())       # corrections restored
+    second = calibrate.lbfgs(s2, y2, w2, n_updates=6, resume=state)
+    np.testing.assert_allclose(second["dlog_gf"].numpy(), straight["dlog_gf"].numpy(), rtol=1e-5, atol=1e-7)
+    assert second["loss_final"] == pytest.approx(straight["loss_final"], rel=1e-6)
+
+
+def test_state_is_bound_to_its_line_list(tmp_path):
+    s, y, w = _state_problem(2)
+    res = calibrate.lbfgs(s, y, w, n_updates=3)
+    path = str(tmp_path / "fit.pt")
+    calibrate.save_state(path, s, res)
+    other, _, _ = _state_problem(3)                 # another catalog
+    with pytest.raises(ValueError):
+        calibrate.load_state(path, other)
+    same = LinearSynthWithState(40, 300, 2)
+    calibrate.load_state(path, same)
+    edited = LinearSynthWithState(40, 300, 2)
+    edited.prob.lines.log_gf[5] += 0.01             # one edited record changes the digest
+    with pytest.raises(ValueError):
+        calibrate.load_state(path, edited)

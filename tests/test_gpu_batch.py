@@ -139,7 +139,10 @@ def test_batch_gradients_are_star_sums(oracle):
         torch.cuda.synchronize()
         print("batch loss rel err vs oracle (%s): %.3g" % ("mixed" if prec == pz.PZ_MIXED else "fp64",
                                                           abs(loss.item() / L - 1)))
-        assert abs(loss.item() / L - 1) < (1e-4 if prec == pz.PZ_MIXED else 1e-7)
+        # the plain FP64 form's F carries ~1e-11 relative from its FP64 Voigt (its continuum
+        # flux, from the same E_n, matches to 1e-15); chi^2 scales a relative flux error by
+        # 2 f / (y - f) ~ 400 at S/N 200, hence 3e-8
+        assert abs(loss.item() / L - 1) < (1e-4 if prec == pz.PZ_MIXED else 3e-8)
         e1 = rel_metric(g[0].cpu().numpy().astype(np.float64), ggf).max()
         e2 = rel_metric(g[1].cpu().numpy().astype(np.float64), gg6).max()
         e3 = rel_metric(gab_t.cpu().numpy().astype(np.float64), gab).max()
@@ -196,10 +199,11 @@ def test_calib_step_graph_matches_eager_calls(prec):
     print("%s: loss eager-eager %.3g graph-eager %.3g; gradients eager-eager %.3g graph-eager %.3g"
           % ("mixed" if prec == pz.PZ_MIXED else "fp64", d_ee, d_ge, g_ee, g_ge))
     if prec == pz.PZ_FP64:
-        # FP64 throughout: only the order of FP64 atomic additions differs
+        # FP64 throughout: only the order of FP64 atomic additions may differ
         assert d_ge < 1e-12 and g_ge < 1e-6     # gradients are returned in FP32
     else:
-        assert d_ge < 1e-7 and d_ee < 1e-7
+        # FP32 near-core sums through shared-memory atomics: the launch-to-launch spread
+        assert d_ge < 1e-8 and d_ee < 1e-8 and g_ge < 1e-6
     for a, c in zip(g_s + [gab_s], g_e + [gab_e]):
         a, c = a.cpu().numpy().astype(np.float64), c.cpu().numpy().astype(np.float64)
         assert np.max(np.abs(a - c)) <= 1e-5 * np.max(np.abs(c)) + 1e-30

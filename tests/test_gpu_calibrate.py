@@ -83,7 +83,7 @@ def test_grouped_lbfgs_calibration():
     assert res["loss_final"] < 1.1 * chi2_truth
     # the context holds the expanded fit
     gf, g6, _ = s.get_corrections()
-    xf = res["x"].cpu().numpy()
+    xf = res["groups"].cpu().numpy()
     np.testing.assert_array_equal(gf, xf[0][q])
     np.testing.assert_array_equal(g6, xf[3][q])
     s.close()

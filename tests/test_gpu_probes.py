@@ -53,7 +53,10 @@ def test_fp64_expn(oracle):
     for k, n in enumerate((2, 3, 4)):
         ref = oracle.expn(n, x)
         m = ref > 1e-290
-        assert np.max(np.abs(got[k][m] / ref[m] - 1)) < 5e-14, n
+        err = np.abs(got[k][m] / ref[m] - 1)
+        small = m & (x < 2.0)
+        print("E_%d: max rel err %.3g (x < 2: %.3g)" % (n, err.max(), np.max(np.abs(got[k][small] / ref[small] - 1))))
+        assert err.max() < 5e-14, n
 
 
 def test_pipe_probes_are_plausible():

@@ -124,7 +124,11 @@ def test_scattering_dominated_solve_converges_or_reports(oracle, r0):
     prob.lines.log_gf[:] -= 3.0
     sc = I.with_scattering(prob, r0=r0)
     ref = oracle.forward(sc)
-    for prec, ftol in ((pz.PZ_MIXED, 1e-5), (pz.PZ_FP64, 1e-9)):
+    # the system I - diag(1 - eps) Lambda has a condition number ~ 1/eps_min: two FP64
+    # solves (the oracle's pivoted elimination, the device's refinement) agree to about
+    # 1e-15 / eps_min
+    eps_min = float(np.min(sc.kappa_c / (sc.kappa_c + sc.sigma_c)))
+    for prec, ftol in ((pz.PZ_MIXED, 1e-5), (pz.PZ_FP64, max(1e-9, 1e-15 / eps_min))):
         got = run_forward(sc, prec, want_kline=False)
         s = got["synth"]
         try:
