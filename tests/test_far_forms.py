@@ -87,3 +87,50 @@ def test_factored_backward_sum_equals_the_cell_sum():
     cell = sum(G[:, i] * (b[:, 0] * s[i] + b[:, 1] * s[i]**2 + b[:, 2] * s[i]**3) for i in range(4))
     X = np.stack([G @ s, G @ s**2, G @ s**3], axis=1)
     assert np.allclose(cell, (b * X).sum(axis=1), rtol=1e-13, atol=0)
+
+
+def _laplace_mid(x, a, nc):
+    """The mid-wing Laplace series of the FP32 kernels in FP64, nc corrections:
+    H sqrt(pi) = a sum_n c_n t^(n+1) U_2n and dH/da sqrt(pi) = sum_n c_n (2n+1) t^(n+1) T_2n+2
+    (t = 1/|z|^2, Chebyshev recurrences in w = 2 - 4 a^2 t, c_n+1 = c_n (2n+1)/2)."""
+    t = 1.0 / (x * x + a * a)
+    w = 2.0 - 4.0 * a * a * t
+    u0, um, g0, gm = 1.0, -1.0, 0.5 * w, 1.0
+    tp, c, sh, sd = t, 1.0, 0.0, 0.0
+    for n in range(nc + 1):
+        sh += c * tp * u0
+        sd += c * (2 * n + 1) * tp * g0
+        u0, um = w * u0 - um, u0
+        g0, gm = w * g0 - gm, g0
+        c *= (2 * n + 1) * 0.5
+        tp *= t
+    return a * sh / np.sqrt(np.pi), sd / np.sqrt(np.pi)
+
+
+@pytest.mark.parametrize("zmin,zmax,h_bound,d_bound", [(6, 8, 2.6e-7, 6e-5), (8, 12, 4.1e-9, 6.4e-7),
+                                                       (12, 20, 1e-9, 1e-8)])
+def test_mid_series_truncation(zmin, zmax, h_bound, d_bound):
+    """The six-correction Laplace series of the near-core kernels' mid wing (6 <= |z| <
+    20) against scipy's Faddeeva function: H within 2.6e-7 relative and dH/da within
+    6e-5 relative to itself (largest where it crosses zero) at |z| = 6, far less further
+    out; five corrections would miss the bound at |z| = 6."""
+    from scipy.special import wofz
+    a = np.concatenate([np.logspace(-4, 0, 25), np.linspace(1.0, zmin - 0.1, 30)])
+
+    def worst(nc):
+        eh = ed = 0.0
+        for r in np.linspace(zmin, zmax, 40):
+            for aa in a[a < r]:
+                x = np.sqrt(r * r - aa * aa)
+                H, dH = _laplace_mid(x, aa, nc)
+                w = wofz(x + 1j * aa)
+                dref = 2 * (x * w.imag + aa * w.real) - 2 / np.sqrt(np.pi)
+                eh = max(eh, abs(H / w.real - 1))
+                ed = max(ed, abs(dH - dref) / abs(dref))
+        return eh, ed
+
+    eh, ed = worst(6)
+    assert eh < h_bound and ed < d_bound, (eh, ed)
+    if zmin == 6:
+        eh5, ed5 = worst(5)
+        assert eh5 > h_bound or ed5 > d_bound
