@@ -55,7 +55,7 @@ def test_launch_count_and_eval_count():
     prob = tiny_problem(n_lambda=400, n_lines=12, W=30)
     s = pz.Synthesizer(prob)
     pz.pz_line_opacity(s.ctx)
-    assert pz.pz_last_launch_count(s.ctx) == 3      # near-core, far-wing prefactor table, far-wing kernels
+    assert pz.pz_last_launch_count(s.ctx) == 3      # near-core, far-wing line records, far-wing kernels
     assert s.n_evals == prob.n_evals
 
 
