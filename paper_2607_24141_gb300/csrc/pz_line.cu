@@ -1362,14 +1362,15 @@ __device__ __forceinline__ void near_pass(const LineArgs &g, const NearItem *min
     }
 }
 
-// Backward mid-wing pass with a blocked assignment: lane l takes the concatenated cells
-// [l P, (l + 1) P), P = ceil(total / 32), so that each lane's cells belong to a few
-// consecutive items; the lane sums an item's cells in registers and hands the sum to
-// done when it moves to the next item (no cross-lane reduction).  voigt_mid has no
-// branch on the item's parameters, so lanes holding different items do not diverge.
-template <class Val, class Done>
-__device__ __forceinline__ void near_pass_mid_blocked(const LineArgs &g, const NearItem *mine, const int *pref,
-                                                      Val &val, Done &done) {
+// Backward pass with a blocked assignment (mid wing or core): lane l takes the
+// concatenated cells [l P, (l + 1) P), P = ceil(total / 32), so that each lane's cells
+// belong to a few consecutive items; the lane sums an item's cells in registers and
+// hands the sum to done when it moves to the next item (no cross-lane reduction).
+// voigt_mid has no branch on the item's parameters; the core form branches on the
+// damping (Taylor order, table or rational), where lanes of different items diverge.
+template <bool CORE, class Val, class Done>
+__device__ __forceinline__ void near_pass_blocked(const LineArgs &g, const NearItem *mine, const int *pref,
+                                                  const float *s_daw, Val &val, Done &done) {
     const int lane = threadIdx.x & 31;
     const int total = pref[32];
     const int per = (total + 31) >> 5;
@@ -1392,12 +1393,15 @@ __device__ __forceinline__ void near_pass_mid_blocked(const LineArgs &g, const N
             end = pref[src + 1];
         }
         const int off = n - start;
-        const int i = off < it.nl ? it.lo + off : it.r0 + (off - it.nl);
+        const int i = CORE ? it.c0 + off : (off < it.nl ? it.lo + off : it.r0 + (off - it.nl));
         const float x = fabsf(offset_u((it.ilf - (float)i) + it.frac, g.lnr) * it.k);
         // a mid-wing cell at |z| >= 20 belongs to the far-wing kernels (same test)
-        if (fmaf(x, x, it.a2) < kFar2) {
+        if (CORE || fmaf(x, x, it.a2) < kFar2) {
             float H, dH;
-            voigt_mid<true>(x, it.a, H, dH);
+            if (CORE)
+                voigt_core<true>(x, it.a, H, dH, s_daw);
+            else
+                voigt_mid<true>(x, it.a, H, dH);
             const float2 v = val(it, i, H, dH);
             acc.x += v.x;
             acc.y += v.y;
@@ -1480,12 +1484,17 @@ __device__ __forceinline__ void near_sweep(const LineArgs &g, int t0, int64_t nl
         }
         if (own != 0) mine[lane] = item;
         __syncwarp();
-        if (D)
-            near_pass_mid_blocked(g, mine, pm, val, done);
-        else
+        if (D) {
+            // mid wing blocked; the core keeps interleaved cells (its damping branches would
+            // diverge across the items of a blocked warp: measured 238 -> 339 ms per batch step)
+            near_pass_blocked<false>(g, mine, pm, s_daw, val, done);
+            __syncwarp();
+            near_pass<T, D, true>(g, mine, pc, s_daw, cell, val, done);
+        } else {
             near_pass<T, D, false>(g, mine, pm, s_daw, cell, val, done);
-        __syncwarp();
-        near_pass<T, D, true>(g, mine, pc, s_daw, cell, val, done);
+            __syncwarp();
+            near_pass<T, D, true>(g, mine, pc, s_daw, cell, val, done);
+        }
     }
 }
 
