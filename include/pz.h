@@ -489,8 +489,10 @@ pz_status pz_abundance_grad_noalloc(const float *g_dlog_gf, const int32_t *speci
 pz_status pz_probe_voigt(const float *a, const float *v, int64_t n, float *H, float *dHda,
                          void *stream);
 
-/* FP64 E_2, E_3, E_4 exactly as the flux kernels evaluate them.  x: device
- * FP64 [n] (x >= 0); out: device FP64 [3][n]. */
+/* FP64 exponential integrals exactly as the transfer kernels evaluate them.
+ * x: device FP64 [n] (x >= 0); out: device FP64 [5][n]: rows 0-2 E_2, E_3, E_4
+ * of the flux kernels, rows 3-4 E_2, E_3 of the scattering kernels' layer-pair
+ * table (its own Taylor table of E_3; zero above x = 40). */
 pz_status pz_probe_expn(const double *x, int64_t n, double *out, void *stream);
 
 /* Measured throughput of the two arithmetic pipes the line kernels are bound by,

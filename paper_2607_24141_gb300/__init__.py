@@ -440,6 +440,9 @@ def pz_probe_voigt(a, v, H, dHda=None, stream=None):
 
 
 def pz_probe_expn(x, out, stream=None):
+    """out: device FP64 [5][n] (E_2, E_3, E_4 of the flux kernels; E_2, E_3 of the scattering table)."""
+    if out.numel() < 5 * x.numel():
+        raise ValueError("pz_probe_expn: out needs 5 * x.numel() elements")
     _check(load().pz_probe_expn(_ptr(x), x.numel(), _ptr(out), _stream(stream)))
 
 

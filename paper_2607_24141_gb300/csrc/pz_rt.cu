@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <mutex>
 #include <vector>
@@ -49,6 +50,9 @@ constexpr int kExpnUni = (int)((kExpnUni1 - kExpnUni0) * 8);   // nodes on [2, 4
 constexpr int kExpnNodes = kExpnGeo + kExpnUni;
 
 __device__ double g_expn_tab[kExpnNodes * kExpnK];
+// The same nodes for E_3 (E_3 = p, E_2 = -p'): the scattering kernels need E_2 and E_3 at
+// every layer pair, and two Horner chains cost 2/3 of the three E_4 takes.
+__device__ double g_expn3_tab[kExpnNodes * kExpnK];
 
 // host: E_1..E_4 at x > 0 in extended precision (series below 2, continued fraction above)
 static void expn_host(long double x, long double E[5]) {
@@ -72,23 +76,25 @@ static void expn_host(long double x, long double E[5]) {
     E[0] = ex / x;
 }
 
-static void expn_node_coeffs(long double x0, double *c) {
+// Taylor coefficients E_n^(k)(x0)/k! of E_n (n = 3 or 4) about x0:
+//   E_n^(k) = (-1)^k E_{n-k} (k <= n),  E_n^(k) = (-1)^n E_0^(k-n) (k > n).
+static void expn_node_coeffs(long double x0, double *c, int n = 4) {
     long double E[5];
     expn_host(x0, E);
     long double fact = 1.0L;   // k!
     for (int k = 0; k < kExpnK; ++k) {
         if (k > 0) fact *= k;
         long double d;
-        if (k <= 4) {
-            d = ((k & 1) ? -1.0L : 1.0L) * E[4 - k];
+        if (k <= n) {
+            d = ((k & 1) ? -1.0L : 1.0L) * E[n - k];
         } else {
-            const int m = k - 4;
+            const int m = k - n;
             long double sum = 0.0L, mf = 1.0L;   // m! / (m - i)! built as a running product
             for (int i = 0; i <= m; ++i) {
                 if (i > 0) mf *= (m - i + 1);
                 sum += mf * powl(x0, -(long double)(i + 1));
             }
-            d = ((m & 1) ? -1.0L : 1.0L) * expl(-x0) * sum;
+            d = ((n & 1) ? -1.0L : 1.0L) * ((m & 1) ? -1.0L : 1.0L) * expl(-x0) * sum;
         }
         c[k] = (double)(d / fact);
     }
@@ -112,12 +118,19 @@ pz_status ensure_expn_table() {
     if (dev < 0 || dev >= 64) return fail(PZ_EINVAL, "device ordinal out of range");
     std::lock_guard<std::mutex> lk(mu);
     if (done[dev]) return PZ_OK;
+    static std::vector<double> tab3;
     if (tab.empty()) {
         tab.resize((size_t)kExpnNodes * kExpnK);
-        for (int j = 0; j < kExpnNodes; ++j) expn_node_coeffs((long double)expn_node_x0(j), &tab[(size_t)j * kExpnK]);
+        tab3.resize((size_t)kExpnNodes * kExpnK);
+        for (int j = 0; j < kExpnNodes; ++j) {
+            expn_node_coeffs((long double)expn_node_x0(j), &tab[(size_t)j * kExpnK], 4);
+            expn_node_coeffs((long double)expn_node_x0(j), &tab3[(size_t)j * kExpnK], 3);
+        }
     }
     e = cudaMemcpyToSymbol(g_expn_tab, tab.data(), sizeof(double) * tab.size());
     if (e != cudaSuccess) return cuda_check(e, "upload E_n table");
+    e = cudaMemcpyToSymbol(g_expn3_tab, tab3.data(), sizeof(double) * tab3.size());
+    if (e != cudaSuccess) return cuda_check(e, "upload E_3 table");
     done[dev] = true;
     return PZ_OK;
 }
@@ -314,76 +327,104 @@ struct ScatArgs {
     int *status;           // context status word: kStatusScatNoConverge if a refinement hit its limit
 };
 
-constexpr int kScatThreads = 256;
-constexpr int kScatTableMaxDepth = 96;    // the E2/E3 pair table fits shared memory up to here
+constexpr int kScatThreadsFwd = 256;     // forward CTA: a 16 x 16 grid in the inverse
+constexpr int kScatThreadsAdj = 512;     // adjoint CTA: a 16 x 32 grid (one CTA per SM fits its shared memory)
+constexpr int kScatTableMaxDepth = 96;    // the adjoint's (E2, E3) pair table fits shared memory up to here
 constexpr int kScatMaxRefine = 12;        // iterative-refinement rounds at most
-constexpr int kScatVec = 16;              // FP64 vectors of nd
+constexpr int kScatVecFwd = 10;           // FP64 vectors of nd: forward kernel
+constexpr int kScatVecAdj = 20;           // FP64 vectors of nd: adjoint kernel
 
-// shared memory: Lambda [nd][nd + 1] (FP64; the adjoint reuses it for dJ/dtau), kScatVec
-// FP64 vectors, the FP32 LU factors [nd][nd], and with the table the packed upper triangle
-// of (E2, E3) pairs plus (E2, E3) at tau_j itself
-static size_t scatter_smem(int nd, bool table) {
-    size_t n = (size_t)nd * (nd + 1) + kScatVec * (size_t)nd;
-    if (table) n += (size_t)nd * (nd + 1) + 2 * (size_t)nd;
-    return sizeof(double) * n + sizeof(float) * (size_t)nd * nd;
+// Row stride of the FP32 inverse: odd, so that a warp walking a row or a column of it
+// touches 32 different banks.
+__host__ __device__ __forceinline__ int scat_ldm(int nd) { return nd | 1; }
+
+// Shared memory of one (wavelength, star) column, by table layout TS:
+//   1 (forward): E3 at every layer pair, one FP64 per pair of the packed triangle; the FP32
+//     inverse of M takes its space once Lambda is built;
+//   2 (adjoint): (E2, E3) at every pair;
+//   0 (adjoint above kScatTableMaxDepth layers): no table, E_n evaluated where needed.
+// Lambda [nd][nd + 1] (FP64, odd row stride; the adjoint reuses it for dJ/dtau), the FP64
+// vectors, the table, one FP64 partial sum per thread, then FP32: the inverse [nd][ldm]
+// (TS != 1), one partial sum per thread, the residual and the pivot row and column [4][nd].
+static size_t scatter_smem(int nd, int ts, int threads) {
+    const size_t W = (size_t)nd + 1;
+    size_t n = (size_t)nd * W + threads + (size_t)(ts == 1 ? kScatVecFwd : kScatVecAdj) * nd;
+    if (ts == 1) n += (size_t)nd * W / 2;
+    if (ts == 2) n += (size_t)nd * W;
+    size_t nf = threads + 5 * (size_t)nd;
+    if (ts != 1) nf += (size_t)nd * scat_ldm(nd);
+    return sizeof(double) * n + sizeof(float) * nf;
 }
 
-// One warp solves L U x = r (TRANS false) or (L U)^T x = r (TRANS true) with the FP32
-// factors (unit lower L and U in place in LU, row stride nd); lane l holds rows l, l + 32,
-// l + 64, l + 96.  r and the result in y.
-__device__ __forceinline__ float pick4(const float (&y)[4], int q) {
-    return q == 0 ? y[0] : (q == 1 ? y[1] : (q == 2 ? y[2] : y[3]));
-}
-template <bool TRANS>
-__device__ __forceinline__ void lu_solve_warp(const float *LU, int nd, int lane, float (&y)[4]) {
-    if (!TRANS) {
-        for (int p = 0; p < nd; ++p) {       // L z = r
-            const float yp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = lane + 32 * q;
-                if (row > p && row < nd) y[q] = fmaf(-LU[row * nd + p], yp, y[q]);
-            }
-        }
-        for (int p = nd - 1; p >= 0; --p) {  // U x = z
-            const float xp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31) / LU[p * nd + p];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = lane + 32 * q;
-                if (row < p) y[q] = fmaf(-LU[row * nd + p], xp, y[q]);
-                if (row == p) y[q] = xp;
-            }
-        }
+// Taylor node of x in [2^-40, 40) and the offset from it (the node layout of expn234)
+__device__ __forceinline__ const double *expn3_node(double x, double &t) {
+    int j;
+    double x0;
+    if (x < kExpnUni0) {
+        const long long bits = __double_as_longlong(x);
+        const int ex = (int)((bits >> 52) & 0x7ff) - 1023, mm = (int)((bits >> 49) & 7);
+        j = (ex - kExpnMinExp) * 8 + mm;
+        x0 = __longlong_as_double((bits & ~((1LL << 49) - 1)) | (1LL << 48));
     } else {
-        for (int p = 0; p < nd; ++p) {       // U^T z = r
-            const float zp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31) / LU[p * nd + p];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = lane + 32 * q;
-                if (row > p && row < nd) y[q] = fmaf(-LU[p * nd + row], zp, y[q]);
-                if (row == p) y[q] = zp;
-            }
-        }
-        for (int p = nd - 1; p >= 0; --p) {  // L^T x = z (unit diagonal)
-            const float xp = __shfl_sync(0xffffffffu, pick4(y, p >> 5), p & 31);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = lane + 32 * q;
-                if (row < p) y[q] = fmaf(-LU[p * nd + row], xp, y[q]);
-            }
-        }
+        j = kExpnGeo + (int)((x - kExpnUni0) * 8.0);
+        x0 = kExpnUni0 + ((j - kExpnGeo) + 0.5) * 0.125;
     }
+    t = x - x0;                                    // exact
+    return g_expn3_tab + j * kExpnK;
 }
 
-// E2, E3 at distance x; beyond x = 40 they are below e^-40 / 40 and are taken as zero
-// (a weight there is below 1e-19 of the local ones)
+// E2, E3 at distance x from the E_3 Taylor table (two Horner chains); beyond x = 40 they
+// are below e^-40 / 40 and are taken as zero (a weight there is below 1e-19 of the local
+// ones)
 __device__ __forceinline__ void e23(double x, double &e2, double &e3) {
-    if (x > 40.0) {
-        e2 = e3 = 0.0;
+    if (x >= kExpnUni1) {          // the table ends below x = 40
+        if (x > 40.0) {
+            e2 = e3 = 0.0;
+        } else {
+            double e4;
+            expn234(x, e2, e3, e4);
+        }
         return;
     }
-    double e4;
-    expn234(x, e2, e3, e4);
+    if (x <= 0.0) {
+        e2 = 1.0;
+        e3 = 0.5;
+        return;
+    }
+    if (x < 0x1p-40) {
+        // E_2 = 1 + x (ln x + gamma - 1) + O(x^2), E_3 = 1/2 - x + O(x^2 ln x)
+        e2 = 1.0 + x * (log(x) + (kEuler - 1.0));
+        e3 = 0.5 - x;
+        return;
+    }
+    double t;
+    const double *c = expn3_node(x, t);
+    double p = __ldg(c + kExpnK - 1), d1 = 0.0;
+#pragma unroll
+    for (int k = kExpnK - 2; k >= 0; --k) {
+        d1 = fma(d1, t, p);
+        p = fma(p, t, __ldg(c + k));
+    }
+    e3 = p;
+    e2 = -d1;
+}
+
+// E3 alone (one Horner chain), the same values as e23's
+__device__ __forceinline__ double e3only(double x) {
+    if (x >= kExpnUni1) {
+        if (x > 40.0) return 0.0;
+        double e2, e3, e4;
+        expn234(x, e2, e3, e4);
+        return e3;
+    }
+    if (x <= 0.0) return 0.5;
+    if (x < 0x1p-40) return 0.5 - x;
+    double t;
+    const double *c = expn3_node(x, t);
+    double p = __ldg(c + kExpnK - 1);
+#pragma unroll
+    for (int k = kExpnK - 2; k >= 0; --k) p = fma(p, t, __ldg(c + k));
+    return p;
 }
 
 // E_1(x), x > 0: the power series -gamma - ln x - sum_k (-x)^k / (k k!) below 1, else
@@ -416,38 +457,77 @@ __device__ __forceinline__ void seg_weights(double D, double invD, double e2n, d
 
 // Shared-memory layout of one (wavelength, star) column.
 struct ScatCol {
-    int nd, W;
-    double *Lam, *tau, *chi, *eps, *B, *S, *e2, *e3, *e4, *invD, *res, *a, *mu, *J, *dF, *ge;
-    double *ET, *Etop;
-    float *LU;
+    int nd, W, ldm;
+    double *Lam, *tau, *chi, *eps, *B, *S, *hD, *a, *e3, *e4, *res;   // both kernels
+    double *e2, *invD, *mu, *J, *dF, *ge, *wx;                        // adjoint only
+    double *e2top, *e3top, *e2bot;   // E2, E3 at tau_j; E2 at tau_{N-1} - tau_j
+    double *ET, *p64;
+    float *Mi, *p32, *r32, *piv;
 };
 
-template <bool TABLE>
+template <int TS>
 __device__ __forceinline__ ScatCol scat_carve(double *sm, int nd) {
-    ScatCol c;
+    ScatCol c = {};
     c.nd = nd;
     c.W = nd + 1;
+    c.ldm = scat_ldm(nd);
     c.Lam = sm;
     double *v = sm + (size_t)nd * c.W;
-    double **vec[kScatVec] = {&c.tau, &c.chi, &c.eps, &c.B, &c.S, &c.e2, &c.e3, &c.e4,
-                              &c.invD, &c.res, &c.a, &c.mu, &c.J, &c.dF, &c.ge, nullptr};
-    for (int k = 0; k < kScatVec; ++k)
-        if (vec[k]) *vec[k] = v + (size_t)k * nd;
-    c.ET = v + (size_t)kScatVec * nd;
-    c.Etop = c.ET + (TABLE ? (size_t)nd * c.W : 0);
-    c.LU = reinterpret_cast<float *>(c.Etop + (TABLE ? 2 * (size_t)nd : 0));
+    if (TS == 1) {
+        double **vec[kScatVecFwd] = {&c.tau, &c.chi, &c.eps, &c.B, &c.S, &c.hD, &c.a, &c.e3, &c.e4, &c.res};
+        for (int k = 0; k < kScatVecFwd; ++k) *vec[k] = v + (size_t)k * nd;
+        v += (size_t)kScatVecFwd * nd;
+        // the slab-end E_n are dead before the flux writes e3, e4 and its partial sums
+        c.e2top = c.e3;
+        c.e3top = c.e4;
+        c.e2bot = c.res;
+    } else {
+        double **vec[kScatVecAdj] = {&c.tau, &c.chi, &c.eps, &c.B, &c.S, &c.hD, &c.a, &c.e3, &c.e4, &c.res,
+                                     &c.e2, &c.invD, &c.mu, &c.J, &c.dF, &c.ge, &c.wx, &c.e2top, &c.e3top,
+                                     &c.e2bot};
+        for (int k = 0; k < kScatVecAdj; ++k) *vec[k] = v + (size_t)k * nd;
+        v += (size_t)kScatVecAdj * nd;
+    }
+    c.ET = v;
+    v += TS == 1 ? (size_t)nd * c.W / 2 : (TS == 2 ? (size_t)nd * c.W : 0);
+    c.p64 = v;
+    float *f = reinterpret_cast<float *>(v + blockDim.x);
+    if (TS == 1) {
+        c.Mi = reinterpret_cast<float *>(c.ET);
+    } else {
+        c.Mi = f;
+        f += (size_t)nd * c.ldm;
+    }
+    c.p32 = f;
+    c.r32 = f + blockDim.x;
+    c.piv = c.r32 + nd;
     return c;
 }
 
-__device__ __forceinline__ size_t pair_idx(int nd, int a, int b) {   // a <= b
+__host__ __device__ __forceinline__ size_t pair_idx(int nd, int a, int b) {   // a <= b
     return (size_t)a * nd - (size_t)a * (a - 1) / 2 + (b - a);
 }
 
-// chi, eps and tau of one branch (0: total, 1: continuum), the segment reciprocals and,
-// with the table, E2/E3 at every layer pair and at tau_j.  Ends with a barrier.
-template <typename KT, bool TABLE>
+// The split of an nd x nd product over the CTA: row j = tid % nd, part q = tid / nd of the
+// columns [k0, k1); threads with q >= P idle.
+struct ScatSplit {
+    int P, j, q, k0, k1;
+    __device__ __forceinline__ ScatSplit(int nd) {
+        P = (int)blockDim.x / nd;
+        const int L = (nd + P - 1) / P;
+        j = threadIdx.x % nd;
+        q = threadIdx.x / nd;
+        k0 = min(nd, q * L);
+        k1 = min(nd, k0 + L);
+    }
+};
+
+// chi, eps and tau of one branch (0: total, 1: continuum); hD = 0.5 / tau_0, then 0.5 / D
+// of each segment; invD (adjoint); E_n at the layer pairs by the table layout TS, and E2,
+// E3 at tau_j and E2 at tau_{N-1} - tau_j.  Ends with a barrier.
+template <typename KT, int TS>
 __device__ void scat_columns(const ScatArgs &g, const ScatCol &c, int64_t base, const double *m, int branch) {
-    const int nd = c.nd, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int nd = c.nd, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const KT *kl = reinterpret_cast<const KT *>(g.kline);
     for (int d = tid; d < nd; d += blockDim.x) {
         const int64_t o = base + (int64_t)d * g.ld;
@@ -456,32 +536,73 @@ __device__ void scat_columns(const ScatArgs &g, const ScatCol &c, int64_t base, 
         c.eps[d] = ka / c.chi[d];
     }
     __syncthreads();
-    if (tid == 0) {
-        double t = c.chi[0] * m[0];
-        c.tau[0] = t;
-        for (int d = 1; d < nd; ++d) {
-            t += 0.5 * (c.chi[d - 1] + c.chi[d]) * (m[d] - m[d - 1]);
-            c.tau[d] = t;
+    // trapezoid tau: the increments by lane, then an inclusive warp scan per 32 layers
+    if (warp == 0) {
+        double carry = 0.0;
+        for (int b = 0; b < nd; b += 32) {
+            const int d = b + lane;
+            double v = 0.0;
+            if (d < nd) v = d == 0 ? c.chi[0] * m[0] : 0.5 * (c.chi[d - 1] + c.chi[d]) * (m[d] - m[d - 1]);
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += u;
+            }
+            v += carry;
+            if (d < nd) c.tau[d] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
         }
     }
     __syncthreads();
-    for (int k = tid; k + 1 < nd; k += blockDim.x) c.invD[k] = 1.0 / (c.tau[k + 1] - c.tau[k]);
-    if (TABLE) {
-        // warps over j, lanes over k >= j
-        for (int j = warp; j < nd; j += nwarp)
-            for (int k = j + lane; k < nd; k += 32) {
-                const size_t idx = pair_idx(nd, j, k);
-                e23(c.tau[k] - c.tau[j], c.ET[2 * idx], c.ET[2 * idx + 1]);
-            }
-        for (int j = tid; j < nd; j += blockDim.x) e23(c.tau[j], c.Etop[2 * j], c.Etop[2 * j + 1]);
+    for (int k = tid; k < nd; k += blockDim.x) {
+        const double inv = 1.0 / (k == 0 ? c.tau[0] : c.tau[k] - c.tau[k - 1]);
+        c.hD[k] = 0.5 * inv;
+        if (TS != 1 && k > 0) c.invD[k - 1] = inv;
+    }
+    if (TS != 0) {
+        // one thread per pair a <= b of the packed triangle, p = pair_idx(nd, a, b); the row
+        // a is the root of the quadratic pair_idx(nd, a, a) = p, corrected to the integer
+        const int P = nd * (nd + 1) / 2;
+        const float b2 = 2.0f * (float)nd + 1.0f;
+        for (int p = tid; p < P; p += blockDim.x) {
+            int a = (int)((b2 - sqrtf(fmaxf(b2 * b2 - 8.0f * (float)p, 0.0f))) * 0.5f);
+            a = max(0, min(a, nd - 1));
+            while (a > 0 && (int)pair_idx(nd, a, a) > p) --a;
+            while (a + 1 < nd && (int)pair_idx(nd, a + 1, a + 1) <= p) ++a;
+            const int b = a + (p - (int)pair_idx(nd, a, a));
+            const double x = c.tau[b] - c.tau[a];
+            if (TS == 1)
+                c.ET[p] = e3only(x);
+            else
+                e23(x, c.ET[2 * p], c.ET[2 * p + 1]);
+        }
+    }
+    for (int t = tid; t < 2 * nd; t += blockDim.x) {
+        const bool top = t < nd;
+        double e2, e3;
+        e23(top ? c.tau[t] : c.tau[nd - 1] - c.tau[t - nd], e2, e3);
+        if (top) {
+            c.e2top[t] = e2;
+            c.e3top[t] = e3;
+        } else {
+            c.e2bot[t - nd] = e2;
+        }
     }
     __syncthreads();
 }
 
-// E2, E3 at |tau_k - tau_j| (table or direct)
-template <bool TABLE>
+// E3(|tau_k - tau_j|) (table or direct)
+template <int TS>
+__device__ __forceinline__ double scat_g3(const ScatCol &c, int j, int k) {
+    if (TS == 0) return e3only(fabs(c.tau[k] - c.tau[j]));
+    const size_t idx = pair_idx(c.nd, min(j, k), max(j, k));
+    return TS == 1 ? c.ET[idx] : c.ET[2 * idx + 1];
+}
+
+// E2, E3 at |tau_k - tau_j| (adjoint table or direct)
+template <int TS>
 __device__ __forceinline__ void scat_E(const ScatCol &c, int j, int k, double &e2, double &e3) {
-    if (TABLE) {
+    if (TS == 2) {
         const size_t idx = pair_idx(c.nd, min(j, k), max(j, k));
         e2 = c.ET[2 * idx];
         e3 = c.ET[2 * idx + 1];
@@ -490,28 +611,78 @@ __device__ __forceinline__ void scat_E(const ScatCol &c, int j, int k, double &e
     }
 }
 
+// Rows of Lambda (J = Lambda S) and the right-hand side a = eps B.
+//
+// With G(t) = E3(|t - tau_j|)/2 + |t - tau_j|/2, G'' = E1(|t - tau_j|)/2 and G' is
+// continuous, so the integral of a hat function against the kernel is the second divided
+// difference of G over its three nodes.  With qt_k = (E3(|tau_{k+1} - tau_j|) - E3(|tau_k -
+// tau_j|)) / (2 D_k) (the E3 part of G's difference quotient over segment k; qt_{-1} over
+// [0, tau_0]) the |t - tau_j| part contributes 1 to the diagonal and nothing else:
+//   Lambda_jk = qt_k - qt_{k-1} + [k = j]                          (k < N - 1),
+//   Lambda_j,N-1 = G'(tau_{N-1}^-) - qt_{N-2}, G' = -E2(tau_{N-1} - tau_j)/2 (j < N - 1), 1/2 (j = N - 1),
+// and the top segment's weight of S(0) is wz = qt_{-1} - E2(tau_j)/2, carried to layers 0
+// and 1 by the extrapolation S(0) = S_0 (1 + tau_0/D_0) - S_1 tau_0/D_0.  The same sums the
+// segment weights P, Q of the formulation above, three FP64 operations per element.
+// Threads over (row, part of the row).  Ends with a barrier.
+template <int TS>
+__device__ void scat_lambda(const ScatCol &c) {
+    const int nd = c.nd, W = c.W;
+    const ScatSplit sp(nd);
+    if (sp.q < sp.P && sp.k0 < sp.k1) {
+        const int j = sp.j;
+        double *row = c.Lam + (size_t)j * W;
+        double ecur, qprev;   // E3 at node k, qt_{k-1}
+        if (sp.k0 == 0) {
+            ecur = scat_g3<TS>(c, j, 0);
+            qprev = (ecur - c.e3top[j]) * c.hD[0];
+        } else {
+            const double em = scat_g3<TS>(c, j, sp.k0 - 1);
+            ecur = scat_g3<TS>(c, j, sp.k0);
+            qprev = (ecur - em) * c.hD[sp.k0];
+        }
+        for (int k = sp.k0; k < sp.k1; ++k) {
+            double v;
+            if (k + 1 < nd) {
+                const double en = scat_g3<TS>(c, j, k + 1);
+                const double qk = (en - ecur) * c.hD[k + 1];
+                v = qk - qprev;
+                if (k == j) v += 1.0;
+                qprev = qk;
+                ecur = en;
+            } else {
+                v = (j + 1 < nd ? -0.5 * c.e2bot[j] : 0.5) - qprev;
+            }
+            row[k] = v;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nd; j += blockDim.x) {
+        double *row = c.Lam + (size_t)j * W;
+        const double wz = (scat_g3<TS>(c, j, 0) - c.e3top[j]) * c.hD[0] - 0.5 * c.e2top[j];
+        const double r = c.tau[0] / (c.tau[1] - c.tau[0]);
+        row[0] += wz * (1.0 + r);
+        row[1] -= wz * r;
+        c.a[j] = c.eps[j] * c.B[j];
+    }
+    __syncthreads();
+}
+
 // Segment weights of row j: for every segment k (between layers k and k + 1) the weights
 // (wa, wb) of its lower and upper layer values, and of the top segment [0, tau_0] the
 // weights (wlo, whi) of S(0) and S(tau_0).  f(k, wa, wb) per segment, then top(wlo, whi).
-template <bool TABLE, class Seg, class Top>
+template <int TS, class Seg, class Top>
 __device__ __forceinline__ void scat_row_weights(const ScatCol &c, int j, Seg &&seg, Top &&top) {
     const int nd = c.nd;
     double e2p, e3p;
-    scat_E<TABLE>(c, j, 0, e2p, e3p);
+    scat_E<TS>(c, j, 0, e2p, e3p);
     {
-        double e2z, e3z, wn, wf;
-        if (TABLE) {
-            e2z = c.Etop[2 * j];
-            e3z = c.Etop[2 * j + 1];
-        } else {
-            e23(c.tau[j], e2z, e3z);
-        }
-        seg_weights(c.tau[0], 1.0 / c.tau[0], e2p, e3p, e2z, e3z, wn, wf);   // near: tau_0, far: 0
+        double wn, wf;
+        seg_weights(c.tau[0], 1.0 / c.tau[0], e2p, e3p, c.e2top[j], c.e3top[j], wn, wf);   // near: tau_0, far: 0
         top(wf, wn);
     }
     for (int k = 0; k + 1 < nd; ++k) {
         double e2k, e3k, wn, wf;
-        scat_E<TABLE>(c, j, k + 1, e2k, e3k);
+        scat_E<TS>(c, j, k + 1, e2k, e3k);
         const double D = c.tau[k + 1] - c.tau[k];
         if (k >= j) {          // below tau_j: near end k, far end k + 1
             seg_weights(D, c.invD[k], e2p, e3p, e2k, e3k, wn, wf);
@@ -525,86 +696,156 @@ __device__ __forceinline__ void scat_row_weights(const ScatCol &c, int j, Seg &&
     }
 }
 
-// rows of Lambda (J = Lambda S) and the right-hand side eps B in column nd.  Ends with a barrier.
-template <bool TABLE>
-__device__ void scat_lambda(const ScatCol &c) {
-    const int nd = c.nd, W = c.W;
-    const double D1 = c.tau[1] - c.tau[0];
-    for (int j = threadIdx.x; j < nd; j += blockDim.x) {
-        double *row = c.Lam + (size_t)j * W;
-        for (int k = 0; k < nd; ++k) row[k] = 0.0;
-        scat_row_weights<TABLE>(
-            c, j,
-            [&](int k, double wa, double wb) {
-                row[k] += wa;
-                row[k + 1] += wb;
-            },
-            [&](double wlo, double whi) {   // S(0) = S0 (1 + tau_0/D1) - S1 tau_0/D1
-                row[0] += wlo * (1.0 + c.tau[0] / D1) + whi;
-                row[1] -= wlo * (c.tau[0] / D1);
-            });
-        row[nd] = c.eps[j] * c.B[j];
+// FP32 inverse of M = I - diag(1 - eps) Lambda by Gauss-Jordan elimination in place,
+// without pivoting (M is diagonally dominant).  The CTA is a 16 x TX grid of threads;
+// thread (ty, tx) holds the elements of rows ty + 16 i (i < RT) and columns tx + TX jj
+// (jj < CT) in registers.  Step p replaces every element by a_rk - f_r g_k with
+//   f_r = (a_rp - [r = p]) / a_pp,  g_k = a_pk + [k = p],
+// which gives the scaled pivot row a_pk / a_pp, the column -a_rp / a_pp and 1 / a_pp on
+// the diagonal in the same fused multiply-add as the rest.  The pivot row and column of
+// step p + 1 are copied to double-buffered vectors by their owners, one barrier per
+// step.  Ends with the inverse in Mi and a barrier.
+template <int RT, int CT, int TX>
+__device__ void scat_inverse(const ScatCol &c) {
+    const int nd = c.nd, ld = c.ldm, W = c.W, tid = threadIdx.x;
+    const int ty = tid / TX, tx = tid - ty * TX;
+    float *colb = c.piv, *rowb = c.piv + 2 * nd;
+    float a[RT][CT];
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+        const int r = ty + 16 * i;
+        const double w = r < nd ? 1.0 - c.eps[r] : 0.0;
+#pragma unroll
+        for (int jj = 0; jj < CT; ++jj) {
+            const int k = tx + TX * jj;
+            a[i][jj] = (r < nd && k < nd) ? (float)((r == k ? 1.0 : 0.0) - w * c.Lam[(size_t)r * W + k]) : 0.0f;
+        }
+    }
+    if (ty == 0) {
+#pragma unroll
+        for (int jj = 0; jj < CT; ++jj)
+            if (tx + TX * jj < nd) rowb[tx + TX * jj] = a[0][jj];
+    }
+    if (tx == 0) {
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+            if (ty + 16 * i < nd) colb[ty + 16 * i] = a[i][0];
     }
     __syncthreads();
-}
-
-// FP32 LU factors of M = I - diag(1 - eps) Lambda (no pivoting: diagonally dominant).
-__device__ void scat_lu(const ScatCol &c) {
-    const int nd = c.nd, W = c.W, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    float *LU = c.LU;
-    for (int r = warp; r < nd; r += nwarp) {
-        const double w = 1.0 - c.eps[r];
-        for (int k = lane; k < nd; k += 32) LU[r * nd + k] = (float)((r == k ? 1.0 : 0.0) - w * c.Lam[(size_t)r * W + k]);
-    }
-    __syncthreads();
-    for (int p = 0; p + 1 < nd; ++p) {
-        // warps over the rows below the pivot, lanes over the columns p+1 .. nd-1
-        const float inv = 1.0f / LU[p * nd + p];
-        for (int r = p + 1 + warp; r < nd; r += nwarp) {
-            const float f = LU[r * nd + p] * inv;
-            for (int k = p + 1 + lane; k < nd; k += 32) LU[r * nd + k] = fmaf(-f, LU[p * nd + k], LU[r * nd + k]);
-            __syncwarp();
-            if (lane == 0) LU[r * nd + p] = f;
+    for (int p = 0; p < nd; ++p) {
+        const int par = p & 1;
+        const float *cb = colb + par * nd, *rb = rowb + par * nd;
+        float *cn = colb + (par ^ 1) * nd, *rn = rowb + (par ^ 1) * nd;
+        const float inv = __frcp_rn(rb[p]);
+        float f[RT], g[CT];
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+            const int r = ty + 16 * i;
+            f[i] = r < nd ? (cb[r] - (r == p ? 1.0f : 0.0f)) * inv : 0.0f;
+        }
+#pragma unroll
+        for (int jj = 0; jj < CT; ++jj) {
+            const int k = tx + TX * jj;
+            g[jj] = k < nd ? rb[k] + (k == p ? 1.0f : 0.0f) : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int jj = 0; jj < CT; ++jj) a[i][jj] = fmaf(-f[i], g[jj], a[i][jj]);
+        const int pn = p + 1;
+        if (pn < nd) {
+            if (ty == (pn & 15)) {
+                const int in = pn >> 4;
+#pragma unroll
+                for (int i = 0; i < RT; ++i)
+                    if (i == in) {
+#pragma unroll
+                        for (int jj = 0; jj < CT; ++jj)
+                            if (tx + TX * jj < nd) rn[tx + TX * jj] = a[i][jj];
+                    }
+            }
+            if (tx == pn % TX) {
+                const int jn = pn / TX;
+#pragma unroll
+                for (int jj = 0; jj < CT; ++jj)
+                    if (jj == jn) {
+#pragma unroll
+                        for (int i = 0; i < RT; ++i)
+                            if (ty + 16 * i < nd) cn[ty + 16 * i] = a[i][jj];
+                    }
+            }
         }
         __syncthreads();
     }
+#pragma unroll
+    for (int i = 0; i < RT; ++i)
+#pragma unroll
+        for (int jj = 0; jj < CT; ++jj) {
+            const int r = ty + 16 * i, k = tx + TX * jj;
+            if (r < nd && k < nd) c.Mi[r * ld + k] = a[i][jj];
+        }
+    __syncthreads();
+}
+
+// out_j = sum_k A[j][k] x_k (TRANS: sum_k A[k][j] x_k) in FP64, A with the row stride of
+// Lambda, split over (row, part) and summed over the parts in a fixed order.  Ends with a
+// barrier.
+template <bool TRANS>
+__device__ void scat_matvec(const ScatCol &c, const double *A, const double *x, double *out) {
+    const int nd = c.nd, W = c.W;
+    const ScatSplit sp(nd);
+    if (sp.q < sp.P) {
+        double acc = 0.0;
+        for (int k = sp.k0; k < sp.k1; ++k)
+            acc = fma(TRANS ? A[(size_t)k * W + sp.j] : A[(size_t)sp.j * W + k], x[k], acc);
+        c.p64[sp.q * nd + sp.j] = acc;
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+        double s = 0.0;
+        for (int u = 0; u < sp.P; ++u) s += c.p64[u * nd + d];
+        out[d] = s;
+    }
+    __syncthreads();
 }
 
 // Iterative refinement with FP64 residuals of M x = rhs (TRANS false) or M^T x = rhs:
-// x += (LU)^-1 (rhs - M x) until the correction is below 1e-14 of x, or until it stops
-// shrinking (at least halving per round after the second), which is where FP64
-// residuals of an ill-conditioned M (eps near 0) leave it.  A solve that stops with a
-// last correction above 1e-9 of x (stalled there, growing, or out of rounds) sets
-// kStatusScatNoConverge in the context's status word (read by pz_sync_status).
+// x += M^-1 (rhs - M x) with the FP32 inverse until the correction is below 1e-14 of x,
+// or until it stops shrinking (at least halving per round after the second), which is
+// where FP64 residuals of an ill-conditioned M (eps near 0) leave it.  A solve that
+// stops with a last correction above 1e-9 of x (stalled there, growing, or out of
+// rounds) sets kStatusScatNoConverge in the context's status word (read by
+// pz_sync_status).  Both products are split like scat_matvec.  With TRANS, wx holds
+// diag(1 - eps) x of the final x on return.
 template <bool TRANS>
 __device__ void scat_refine(const ScatCol &c, const double *rhs, double *x, int *s_done, int *status) {
-    const int nd = c.nd, W = c.W, tid = threadIdx.x;
+    const int nd = c.nd, W = c.W, ld = c.ldm, tid = threadIdx.x;
+    const ScatSplit sp(nd);
     __shared__ double s_dprev;
     for (int d = tid; d < nd; d += blockDim.x) {
         x[d] = 0.0;
-        c.res[d] = rhs[d];
+        c.r32[d] = (float)rhs[d];
     }
     if (tid == 0) s_dprev = 0.0;
     __syncthreads();
     for (int it = 0; it < kScatMaxRefine; ++it) {
+        if (sp.q < sp.P) {       // y = M^-1 r (M^-T r), FP32
+            float acc = 0.0f;
+            for (int k = sp.k0; k < sp.k1; ++k)
+                acc = fmaf(TRANS ? c.Mi[k * ld + sp.j] : c.Mi[sp.j * ld + k], c.r32[k], acc);
+            c.p32[sp.q * nd + sp.j] = acc;
+        }
+        __syncthreads();
         if (tid < 32) {
-            float y[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = tid + 32 * q;
-                y[q] = row < nd ? (float)c.res[row] : 0.0f;
-            }
-            lu_solve_warp<TRANS>(c.LU, nd, tid, y);
             double dmax = 0.0, smax = 0.0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int row = tid + 32 * q;
-                if (row < nd) {
-                    const double v = x[row] + (double)y[q];
-                    x[row] = v;
-                    dmax = fmax(dmax, fabs((double)y[q]));
-                    smax = fmax(smax, fabs(v));
-                }
+            for (int row = tid; row < nd; row += 32) {
+                float y = 0.0f;
+                for (int u = 0; u < sp.P; ++u) y += c.p32[u * nd + row];
+                const double v = x[row] + (double)y;
+                x[row] = v;
+                if (TRANS) c.wx[row] = (1.0 - c.eps[row]) * v;
+                dmax = fmax(dmax, fabs((double)y));
+                smax = fmax(smax, fabs(v));
             }
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) {
@@ -621,30 +862,35 @@ __device__ void scat_refine(const ScatCol &c, const double *rhs, double *x, int 
         }
         __syncthreads();
         if (*s_done) break;
-        for (int j = tid; j < nd; j += blockDim.x) {
-            double r = rhs[j] - x[j];
+        if (sp.q < sp.P) {       // Lambda x (Lambda^T diag(1 - eps) x), FP64
+            double acc = 0.0;
             if (!TRANS) {
-                const double *row = c.Lam + (size_t)j * W;
-                double lx = 0.0;
-                for (int k = 0; k < nd; ++k) lx = fma(row[k], x[k], lx);
-                r = fma(1.0 - c.eps[j], lx, r);
+                const double *row = c.Lam + (size_t)sp.j * W;
+                for (int k = sp.k0; k < sp.k1; ++k) acc = fma(row[k], x[k], acc);
             } else {
-                double lx = 0.0;   // (Lambda^T diag(1 - eps) x)_j
-                for (int k = 0; k < nd; ++k) lx = fma(c.Lam[(size_t)k * W + j], (1.0 - c.eps[k]) * x[k], lx);
-                r += lx;
+                for (int k = sp.k0; k < sp.k1; ++k) acc = fma(c.Lam[(size_t)k * W + sp.j], c.wx[k], acc);
             }
-            c.res[j] = r;
+            c.p64[sp.q * nd + sp.j] = acc;
+        }
+        __syncthreads();
+        for (int d = tid; d < nd; d += blockDim.x) {
+            double lx = 0.0;
+            for (int u = 0; u < sp.P; ++u) lx += c.p64[u * nd + d];
+            const double r0 = rhs[d] - x[d];
+            c.r32[d] = (float)(TRANS ? r0 + lx : fma(1.0 - c.eps[d], lx, r0));
         }
         __syncthreads();
     }
 }
 
-template <typename KT, bool TABLE>
-__global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
+// Forward: one CTA per (wavelength, star), both branches in turn; three CTAs fit an SM up
+// to 80 layers (RT = 5: rows and columns of the inverse per thread in each direction).
+template <typename KT, int RT>
+__global__ void __launch_bounds__(kScatThreadsFwd, RT <= 5 ? 3 : 1) k_flux_scatter(ScatArgs g) {
     extern __shared__ double sm[];
     __shared__ int s_done;
     const int nd = g.nd;
-    const ScatCol c = scat_carve<TABLE>(sm, nd);
+    const ScatCol c = scat_carve<1>(sm, nd);
     const int64_t i = blockIdx.x;
     const int st = blockIdx.y;
     const int tid = threadIdx.x;
@@ -654,22 +900,35 @@ __global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
     const double lam = g.lam0cm * exp((double)i * g.lnr);
     for (int d = tid; d < nd; d += blockDim.x) c.B[d] = planck_nm(lam, T[d]);
     for (int branch = 0; branch < 2; ++branch) {
-        scat_columns<KT, TABLE>(g, c, base, m, branch);
-        scat_lambda<TABLE>(c);
-        scat_lu(c);
-        for (int d = tid; d < nd; d += blockDim.x) c.a[d] = c.Lam[(size_t)d * c.W + nd];
-        __syncthreads();
+        scat_columns<KT, 1>(g, c, base, m, branch);
+        scat_lambda<1>(c);
+        scat_inverse<RT, RT, 16>(c);
         scat_refine<false>(c, c.a, c.S, &s_done, g.status);
         // emergent flux of the solved source, the closed form of the LTE kernel
-        for (int d = tid; d < nd; d += blockDim.x) expn234(c.tau[d], c.e2[d], c.e3[d], c.e4[d]);
+        for (int d = tid; d < nd; d += blockDim.x) {
+            double e2;
+            expn234(c.tau[d], e2, c.e3[d], c.e4[d]);
+        }
         __syncthreads();
-        if (tid == 0) {
-            const double D1 = c.tau[1] - c.tau[0];
-            const double s0 = (c.S[1] - c.S[0]) / D1;
-            double F = interval(0.0, c.tau[0], c.S[0] - s0 * c.tau[0], c.S[0], 0.5, 1.0 / 3.0, c.e3[0], c.e4[0]);
-            for (int d = 0; d + 1 < nd; ++d)
-                F += interval(c.tau[d], c.tau[d + 1], c.S[d], c.S[d + 1], c.e3[d], c.e4[d], c.e3[d + 1], c.e4[d + 1]);
-            (branch == 0 ? g.F : g.Fc)[(int64_t)st * g.nlam + i] = 2.0 * kPI * F;
+        // interval d (layers d, d + 1; for d = 0 also the top one [0, tau_0]) by thread d,
+        // summed by warp 0 in a fixed order
+        for (int d = tid; d < nd; d += blockDim.x) {
+            double v = 0.0;
+            if (d + 1 < nd)
+                v = interval(c.tau[d], c.tau[d + 1], c.S[d], c.S[d + 1], c.e3[d], c.e4[d], c.e3[d + 1], c.e4[d + 1]);
+            if (d == 0) {
+                const double s0 = (c.S[1] - c.S[0]) / (c.tau[1] - c.tau[0]);
+                v += interval(0.0, c.tau[0], c.S[0] - s0 * c.tau[0], c.S[0], 0.5, 1.0 / 3.0, c.e3[0], c.e4[0]);
+            }
+            c.res[d] = v;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            double F = 0.0;
+            for (int d = tid; d < nd; d += 32) F += c.res[d];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) F += __shfl_xor_sync(0xffffffffu, F, o);
+            if (tid == 0) (branch == 0 ? g.F : g.Fc)[(int64_t)st * g.nlam + i] = 2.0 * kPI * F;
         }
         __syncthreads();
     }
@@ -685,12 +944,12 @@ __global__ void __launch_bounds__(kScatThreads) k_flux_scatter(ScatArgs g) {
 // the bottom layer, the top segment's extrapolation terms, and the diagonal from
 // translation invariance (the row sums to 1/2 S(0) E_1(tau_j)).  Through the trapezoid and
 // eps = 1 - sigma/chi: G_d = dL/dchi_d + dL/deps_d sigma_d / chi_d^2, stored as G stim.
-template <typename KT, typename GT, bool TABLE>
-__global__ void __launch_bounds__(kScatThreads) k_rt_adjoint_scatter(ScatArgs g) {
+template <typename KT, typename GT, int TS, int RT, int CT>
+__global__ void __launch_bounds__(kScatThreadsAdj, 1) k_rt_adjoint_scatter(ScatArgs g) {
     extern __shared__ double sm[];
     __shared__ int s_done;
     const int nd = g.nd, W = nd + 1;
-    const ScatCol c = scat_carve<TABLE>(sm, nd);
+    const ScatCol c = scat_carve<TS>(sm, nd);
     const int64_t i = blockIdx.x;
     const int st = blockIdx.y;
     const int tid = threadIdx.x;
@@ -700,20 +959,13 @@ __global__ void __launch_bounds__(kScatThreads) k_rt_adjoint_scatter(ScatArgs g)
     const double lam = g.lam0cm * exp((double)i * g.lnr);
     const double Fb = g.dFbar[(int64_t)st * g.nlam + i];
     for (int d = tid; d < nd; d += blockDim.x) c.B[d] = planck_nm(lam, T[d]);
-    scat_columns<KT, TABLE>(g, c, base, m, 0);
-    scat_lambda<TABLE>(c);
-    scat_lu(c);
-    for (int d = tid; d < nd; d += blockDim.x) c.a[d] = c.Lam[(size_t)d * W + nd];
-    __syncthreads();
+    scat_columns<KT, TS>(g, c, base, m, 0);
+    scat_lambda<TS>(c);
+    scat_inverse<RT, CT, 32>(c);
     scat_refine<false>(c, c.a, c.S, &s_done, g.status);
     // J = Lambda S, E_n at the layers
-    for (int j = tid; j < nd; j += blockDim.x) {
-        const double *row = c.Lam + (size_t)j * W;
-        double v = 0.0;
-        for (int k = 0; k < nd; ++k) v = fma(row[k], c.S[k], v);
-        c.J[j] = v;
-        expn234(c.tau[j], c.e2[j], c.e3[j], c.e4[j]);
-    }
+    scat_matvec<false>(c, c.Lam, c.S, c.J);
+    for (int j = tid; j < nd; j += blockDim.x) expn234(c.tau[j], c.e2[j], c.e3[j], c.e4[j]);
     __syncthreads();
     // dF/dS (a, times dL/dF) and dF/dtau at fixed S (dF), both with the 2 pi of the flux
     const double D1 = c.tau[1] - c.tau[0];
@@ -757,71 +1009,131 @@ __global__ void __launch_bounds__(kScatThreads) k_rt_adjoint_scatter(ScatArgs g)
     }
     __syncthreads();
     scat_refine<true>(c, c.a, c.mu, &s_done, g.status);
-    // dJ_j/dtau_m into the Lambda area (Lambda is no longer needed), one row per thread
+    // dJ_j/dtau_m into the Lambda area (Lambda is no longer needed): the off-diagonal
+    // elements by (row, part), element k from segments k - 1 (its upper weight) and k (its
+    // lower weight), the top segment's terms at k <= 1 and the slab end at k = N - 1; then
+    // the diagonal from the row sums
     const double Szero = c.S[0] - s0 * t0;
-    for (int j = tid; j < nd; j += blockDim.x) {
-        double *row = c.Lam + (size_t)j * W;
-        for (int k = 0; k < nd; ++k) row[k] = 0.0;
-        scat_row_weights<TABLE>(
-            c, j,
-            [&](int k, double wa, double wb) {
-                const double sk = (c.S[k + 1] - c.S[k]) * c.invD[k];
-                row[k] -= sk * wa;
-                row[k + 1] -= sk * wb;
-            },
-            [&](double wlo, double whi) {
-                row[0] += -(s0 / D1) * t0 * wlo - s0 * (wlo + whi);
-                row[1] += (s0 / D1) * t0 * wlo;
-            });
-        // the slab ends with the bottom layer
-        if (j != nd - 1) row[nd - 1] += 0.5 * c.S[nd - 1] * e1(c.tau[nd - 1] - c.tau[j]);
-        double off = 0.0;
-        for (int k = 0; k < nd; ++k)
-            if (k != j) off += row[k];
-        row[j] = 0.5 * Szero * e1(c.tau[j]) - off;
+    {
+        const ScatSplit sp(nd);
+        if (sp.q < sp.P && sp.k0 < sp.k1) {
+            const int j = sp.j;
+            double *row = c.Lam + (size_t)j * W;
+            double e2p, e3p, wbs = 0.0;   // E at node k; -s_{k-1} times the upper weight of segment k - 1
+            if (sp.k0 > 0) {
+                const int k = sp.k0 - 1;
+                double e2m, e3m, wn, wf;
+                scat_E<TS>(c, j, k, e2m, e3m);
+                scat_E<TS>(c, j, k + 1, e2p, e3p);
+                const double D = c.tau[k + 1] - c.tau[k];
+                double wb;
+                if (k >= j) {
+                    seg_weights(D, c.invD[k], e2m, e3m, e2p, e3p, wn, wf);
+                    wb = wf;
+                } else {
+                    seg_weights(D, c.invD[k], e2p, e3p, e2m, e3m, wn, wf);
+                    wb = wn;
+                }
+                wbs = -((c.S[k + 1] - c.S[k]) * c.invD[k]) * wb;
+            } else {
+                scat_E<TS>(c, j, 0, e2p, e3p);
+            }
+            double off = 0.0;
+            for (int k = sp.k0; k < sp.k1; ++k) {
+                double v = wbs;
+                if (k <= 1) {   // the top segment [0, tau_0] with the extrapolated S(0)
+                    double e20, e30, whi, wlo;
+                    scat_E<TS>(c, j, 0, e20, e30);
+                    seg_weights(t0, 1.0 / t0, e20, e30, c.e2top[j], c.e3top[j], whi, wlo);   // near: tau_0, far: 0
+                    v += k == 0 ? -(s0 / D1) * t0 * wlo - s0 * (wlo + whi) : (s0 / D1) * t0 * wlo;
+                }
+                if (k + 1 < nd) {
+                    double e2n, e3n, wn, wf, wa, wb;
+                    scat_E<TS>(c, j, k + 1, e2n, e3n);
+                    const double D = c.tau[k + 1] - c.tau[k];
+                    if (k >= j) {          // below tau_j: near end k, far end k + 1
+                        seg_weights(D, c.invD[k], e2p, e3p, e2n, e3n, wn, wf);
+                        wa = wn;
+                        wb = wf;
+                    } else {               // above: near end k + 1, far end k
+                        seg_weights(D, c.invD[k], e2n, e3n, e2p, e3p, wn, wf);
+                        wa = wf;
+                        wb = wn;
+                    }
+                    const double sk = (c.S[k + 1] - c.S[k]) * c.invD[k];
+                    v -= sk * wa;
+                    wbs = -sk * wb;
+                    e2p = e2n;
+                    e3p = e3n;
+                }
+                if (k == nd - 1 && j != nd - 1) v += 0.5 * c.S[nd - 1] * e1(c.tau[nd - 1] - c.tau[j]);
+                if (k != j) {
+                    row[k] = v;
+                    off += v;
+                }
+            }
+            c.p64[sp.q * nd + j] = off;
+        }
+        __syncthreads();
+        for (int j = tid; j < nd; j += blockDim.x) {
+            double off = 0.0;
+            for (int u = 0; u < sp.P; ++u) off += c.p64[u * nd + j];
+            c.Lam[(size_t)j * W + j] = 0.5 * Szero * e1(c.tau[j]) - off;
+        }
+        __syncthreads();
     }
-    __syncthreads();
-    // dL/dtau_m and dL/deps_j
+    // dL/dtau_m = dF_m + sum_j mu_j (1 - eps_j) dJ_j/dtau_m (wx holds mu (1 - eps)), and dL/deps
+    scat_matvec<true>(c, c.Lam, c.wx, c.res);
     for (int mm = tid; mm < nd; mm += blockDim.x) {
-        double gtm = c.dF[mm];
-        for (int j = 0; j < nd; ++j) gtm = fma(c.mu[j] * (1.0 - c.eps[j]), c.Lam[(size_t)j * W + mm], gtm);
-        c.res[mm] = gtm;
+        c.res[mm] += c.dF[mm];
         c.ge[mm] = c.mu[mm] * (c.B[mm] - c.J[mm]);
     }
     __syncthreads();
-    // through the trapezoid (reverse cumulative sum) and eps = 1 - sigma/chi
-    if (tid == 0) {
-        GT *Gt = reinterpret_cast<GT *>(g.Gt) + (int64_t)st * nd * g.ld + i;
-        double Tn = 0.0;   // sum_{k > d} dL/dtau_k
-        for (int d = nd - 1; d >= 0; --d) {
-            const double Td = Tn + c.res[d];
-            double gch = 0.0;
-            if (d + 1 < nd) gch += 0.5 * (m[d + 1] - m[d]) * Tn;
-            if (d >= 1) gch += 0.5 * (m[d] - m[d - 1]) * Td;
-            else gch += m[0] * Td;
-            const double sig = g.sig[base + (int64_t)d * g.ld];
-            gch += c.ge[d] * sig / (c.chi[d] * c.chi[d]);
-            const double stim = -expm1(-kC2 / (lam * T[d]));
-            Gt[(int64_t)d * g.ld] = (GT)(gch * stim);
-            Tn = Td;
+    // through the trapezoid and eps = 1 - sigma/chi: the suffix sums T_d = sum_{k >= d}
+    // dL/dtau_k by a warp scan from the bottom layer up (exclusive ones in a, inclusive in
+    // e3), then layer d by thread d
+    if (tid < 32) {
+        double carry = 0.0;
+        for (int b = 0; b < nd; b += 32) {
+            const int d = nd - 1 - (b + tid);
+            double v = d >= 0 ? c.res[d] : 0.0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const double u = __shfl_up_sync(0xffffffffu, v, o);
+                if (tid >= o) v += u;
+            }
+            v += carry;
+            const double prev = __shfl_up_sync(0xffffffffu, v, 1);
+            if (d >= 0) {
+                c.a[d] = tid == 0 ? carry : prev;
+                c.e3[d] = v;
+            }
+            carry = __shfl_sync(0xffffffffu, v, 31);
         }
+    }
+    __syncthreads();
+    GT *Gt = reinterpret_cast<GT *>(g.Gt) + (int64_t)st * nd * g.ld + i;
+    for (int d = tid; d < nd; d += blockDim.x) {
+        const double Tn = c.a[d], Td = c.e3[d];
+        double gch = 0.0;
+        if (d + 1 < nd) gch += 0.5 * (m[d + 1] - m[d]) * Tn;
+        if (d >= 1) gch += 0.5 * (m[d] - m[d - 1]) * Td;
+        else gch += m[0] * Td;
+        const double sig = g.sig[base + (int64_t)d * g.ld];
+        gch += c.ge[d] * sig / (c.chi[d] * c.chi[d]);
+        const double stim = -expm1(-kC2 / (lam * T[d]));
+        Gt[(int64_t)d * g.ld] = (GT)(gch * stim);
     }
 }
 
-template <bool TABLE>
-static cudaError_t scatter_attr(pz_ctx *c, size_t smem) {
-    static size_t attr_set[64] = {0};   // dynamic shared memory granted so far, per device
-    if (c->device < 0 || c->device >= 64) return cudaErrorInvalidDevice;
-    if (smem <= attr_set[c->device]) return cudaSuccess;
-    const void *fns[4] = {(const void *)k_flux_scatter<float, TABLE>, (const void *)k_flux_scatter<double, TABLE>,
-                          (const void *)k_rt_adjoint_scatter<float, float, TABLE>,
-                          (const void *)k_rt_adjoint_scatter<double, double, TABLE>};
-    for (const void *f : fns) {
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    attr_set[c->device] = smem;
-    return cudaSuccess;
+// Dynamic shared memory granted to a kernel so far, per device.
+static cudaError_t scatter_attr(pz_ctx *c, const void *fn, int slot, size_t smem) {
+    static std::atomic<size_t> granted[kMaxDevices][10];
+    if (c->device < 0 || c->device >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (smem <= granted[c->device][slot].load()) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) granted[c->device][slot].store(smem);
+    return e;
 }
 
 static ScatArgs scatter_args(pz_ctx *c) {
@@ -844,34 +1156,42 @@ static ScatArgs scatter_args(pz_ctx *c) {
     return g;
 }
 
-template <bool TABLE>
-static cudaError_t launch_scatter_t(pz_ctx *c, bool adjoint, cudaStream_t s) {
-    const size_t smem = scatter_smem(c->nd, TABLE);
-    cudaError_t e = scatter_attr<TABLE>(c, smem);
+template <typename K>
+static cudaError_t launch_scat_kernel(pz_ctx *c, K *fn, int slot, int threads, size_t smem, cudaStream_t s) {
+    cudaError_t e = scatter_attr(c, (const void *)fn, slot, smem);
     if (e != cudaSuccess) return e;
-    const ScatArgs g = scatter_args(c);
-    dim3 nb((unsigned)c->nlam, c->S);
-    if (!adjoint) {
-        if (c->prec == PZ_MIXED)
-            k_flux_scatter<float, TABLE><<<nb, kScatThreads, smem, s>>>(g);
-        else
-            k_flux_scatter<double, TABLE><<<nb, kScatThreads, smem, s>>>(g);
-    } else {
-        if (c->prec == PZ_MIXED)
-            k_rt_adjoint_scatter<float, float, TABLE><<<nb, kScatThreads, smem, s>>>(g);
-        else
-            k_rt_adjoint_scatter<double, double, TABLE><<<nb, kScatThreads, smem, s>>>(g);
-    }
+    fn<<<dim3((unsigned)c->nlam, c->S), threads, smem, s>>>(scatter_args(c));
     c->launches++;
     return cudaGetLastError();
 }
 
+// Instantiations: RT = 5 (16 x 5 = 80 rows of the inverse) up to 80 layers, else 8 (128).
 cudaError_t launch_flux_scatter(pz_ctx *c, cudaStream_t s) {
-    return c->nd <= kScatTableMaxDepth ? launch_scatter_t<true>(c, false, s) : launch_scatter_t<false>(c, false, s);
+    const size_t smem = scatter_smem(c->nd, 1, kScatThreadsFwd);
+    const int T = kScatThreadsFwd;
+    if (c->nd <= 80)
+        return c->prec == PZ_MIXED ? launch_scat_kernel(c, k_flux_scatter<float, 5>, 0, T, smem, s)
+                                   : launch_scat_kernel(c, k_flux_scatter<double, 5>, 1, T, smem, s);
+    return c->prec == PZ_MIXED ? launch_scat_kernel(c, k_flux_scatter<float, 8>, 2, T, smem, s)
+                               : launch_scat_kernel(c, k_flux_scatter<double, 8>, 3, T, smem, s);
 }
 
 cudaError_t launch_rt_adjoint_scatter(pz_ctx *c, cudaStream_t s) {
-    return c->nd <= kScatTableMaxDepth ? launch_scatter_t<true>(c, true, s) : launch_scatter_t<false>(c, true, s);
+    const bool mixed = c->prec == PZ_MIXED;
+    const int T = kScatThreadsAdj;
+    if (c->nd <= 80) {
+        const size_t smem = scatter_smem(c->nd, 2, T);
+        return mixed ? launch_scat_kernel(c, k_rt_adjoint_scatter<float, float, 2, 5, 3>, 4, T, smem, s)
+                     : launch_scat_kernel(c, k_rt_adjoint_scatter<double, double, 2, 5, 3>, 5, T, smem, s);
+    }
+    if (c->nd <= kScatTableMaxDepth) {
+        const size_t smem = scatter_smem(c->nd, 2, T);
+        return mixed ? launch_scat_kernel(c, k_rt_adjoint_scatter<float, float, 2, 8, 4>, 6, T, smem, s)
+                     : launch_scat_kernel(c, k_rt_adjoint_scatter<double, double, 2, 8, 4>, 7, T, smem, s);
+    }
+    const size_t smem = scatter_smem(c->nd, 0, T);
+    return mixed ? launch_scat_kernel(c, k_rt_adjoint_scatter<float, float, 0, 8, 4>, 8, T, smem, s)
+                 : launch_scat_kernel(c, k_rt_adjoint_scatter<double, double, 0, 8, 4>, 9, T, smem, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1252,6 +1572,9 @@ __global__ void k_probe_expn(const double *x, int64_t n, double *out) {
     out[k] = e2;
     out[n + k] = e3;
     out[2 * n + k] = e4;
+    e23(x[k], e2, e3);
+    out[3 * n + k] = e2;
+    out[4 * n + k] = e3;
 }
 
 cudaError_t launch_probe_expn(const double *x, int64_t n, double *out, cudaStream_t s) {

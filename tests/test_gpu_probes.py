@@ -46,10 +46,10 @@ def test_fp64_expn(oracle):
                         edges * (1 - 1e-15), edges, edges * (1 + 1e-15),
                         np.random.default_rng(3).uniform(0.0, 50.0, 500)])
     xt = torch.tensor(x, dtype=torch.float64, device="cuda")
-    out = torch.empty(3 * x.size, dtype=torch.float64, device="cuda")
+    out = torch.empty(5 * x.size, dtype=torch.float64, device="cuda")
     pz.pz_probe_expn(xt, out)
     torch.cuda.synchronize()
-    got = out.cpu().numpy().reshape(3, -1)
+    got = out.cpu().numpy().reshape(5, -1)
     for k, n in enumerate((2, 3, 4)):
         ref = oracle.expn(n, x)
         m = ref > 1e-290
@@ -57,6 +57,15 @@ def test_fp64_expn(oracle):
         small = m & (x < 2.0)
         print("E_%d: max rel err %.3g (x < 2: %.3g)" % (n, err.max(), np.max(np.abs(got[k][small] / ref[small] - 1))))
         assert err.max() < 5e-14, n
+    # the scattering kernels' E_2, E_3 (from the E_3 table): the same bound up to x = 40,
+    # zero beyond
+    near = x <= 40.0
+    for k, n in ((3, 2), (4, 3)):
+        ref = oracle.expn(n, x)
+        err = np.abs(got[k][near] / ref[near] - 1)
+        print("scattering E_%d: max rel err %.3g" % (n, err.max()))
+        assert err.max() < 5e-14, n
+        assert np.all(got[k][~near] == 0.0)
 
 
 def test_pipe_probes_are_plausible():
