@@ -135,34 +135,50 @@ pz_status ensure_expn_table() {
     return PZ_OK;
 }
 
+// Node of x in [2^-40, 40) and the offset t = x - x0 (exact), from the bits of x alone
+// (integer operations: the FP64 pipe is kept for the series).  Below 2, eight nodes per
+// binade at the centres of its eighths (x0 keeps three mantissa bits and sets the fourth);
+// on [2, 40) nodes every 1/8 at the centres (j - kExpnGeo = floor(8 x) - 16, x0 = x rounded
+// down to a multiple of 1/8 plus 1/16).
+__device__ __forceinline__ int expn_node(double x, double &t) {
+    const long long bits = __double_as_longlong(x);
+    const int ex = (int)(bits >> 52) - 1023;           // x > 0
+    int j;
+    long long x0b;
+    if (ex < 1) {
+        j = (ex - kExpnMinExp) * 8 + (int)((bits >> 49) & 7);
+        x0b = (bits & ~((1LL << 49) - 1)) | (1LL << 48);
+    } else {
+        const int sh = 49 - ex;                        // mantissa bit of 1/8
+        j = kExpnGeo - 16 + (int)(((bits & ((1LL << 52) - 1)) | (1LL << 52)) >> sh);
+        x0b = (bits & ~((1LL << sh) - 1)) | (1LL << (sh - 1));
+    }
+    t = x - __longlong_as_double(x0b);
+    return j;
+}
+
+// Ranges of x by its bits (x >= 0 orders like its bit pattern)
+constexpr long long kBits2m40 = 0x3D70000000000000LL;   // 2^-40
+constexpr long long kBits40 = 0x4044000000000000LL;     // 40.0
+
 __device__ __forceinline__ void expn234(double x, double &E2, double &E3, double &E4) {
-    if (x <= 0.0) {
+    const long long xb = __double_as_longlong(x);
+    if (xb <= 0) {
         E2 = 1.0;
         E3 = 0.5;
         E4 = 1.0 / 3.0;
         return;
     }
-    if (x < kExpnUni1) {
-        int j;
-        double x0;
-        if (x < kExpnUni0) {
-            if (x < 0x1p-40) {
-                // E_2 = 1 + x (ln x + gamma - 1) + O(x^2), E_3 = 1/2 - x + O(x^2 ln x), E_4 = 1/3 - x/2 + O(x^2)
-                E2 = 1.0 + x * (log(x) + (kEuler - 1.0));
-                E3 = 0.5 - x;
-                E4 = 1.0 / 3.0 - 0.5 * x;
-                return;
-            }
-            const long long bits = __double_as_longlong(x);
-            const int ex = (int)((bits >> 52) & 0x7ff) - 1023, m = (int)((bits >> 49) & 7);
-            j = (ex - kExpnMinExp) * 8 + m;
-            x0 = __longlong_as_double((bits & ~((1LL << 49) - 1)) | (1LL << 48));
-        } else {
-            j = kExpnGeo + (int)((x - kExpnUni0) * 8.0);
-            x0 = kExpnUni0 + ((j - kExpnGeo) + 0.5) * 0.125;
+    if (xb < kBits40) {
+        if (xb < kBits2m40) {
+            // E_2 = 1 + x (ln x + gamma - 1) + O(x^2), E_3 = 1/2 - x + O(x^2 ln x), E_4 = 1/3 - x/2 + O(x^2)
+            E2 = 1.0 + x * (log(x) + (kEuler - 1.0));
+            E3 = 0.5 - x;
+            E4 = 1.0 / 3.0 - 0.5 * x;
+            return;
         }
-        const double t = x - x0;                       // exact
-        const double *c = g_expn_tab + j * kExpnK;
+        double t;
+        const double *c = g_expn_tab + expn_node(x, t) * kExpnK;
         double p = __ldg(c + kExpnK - 1), d1 = 0.0, d2 = 0.0;
 #pragma unroll
         for (int k = kExpnK - 2; k >= 0; --k) {
@@ -356,29 +372,13 @@ static size_t scatter_smem(int nd, int ts, int threads) {
     return sizeof(double) * n + sizeof(float) * nf;
 }
 
-// Taylor node of x in [2^-40, 40) and the offset from it (the node layout of expn234)
-__device__ __forceinline__ const double *expn3_node(double x, double &t) {
-    int j;
-    double x0;
-    if (x < kExpnUni0) {
-        const long long bits = __double_as_longlong(x);
-        const int ex = (int)((bits >> 52) & 0x7ff) - 1023, mm = (int)((bits >> 49) & 7);
-        j = (ex - kExpnMinExp) * 8 + mm;
-        x0 = __longlong_as_double((bits & ~((1LL << 49) - 1)) | (1LL << 48));
-    } else {
-        j = kExpnGeo + (int)((x - kExpnUni0) * 8.0);
-        x0 = kExpnUni0 + ((j - kExpnGeo) + 0.5) * 0.125;
-    }
-    t = x - x0;                                    // exact
-    return g_expn3_tab + j * kExpnK;
-}
-
 // E2, E3 at distance x from the E_3 Taylor table (two Horner chains); beyond x = 40 they
 // are below e^-40 / 40 and are taken as zero (a weight there is below 1e-19 of the local
 // ones)
 __device__ __forceinline__ void e23(double x, double &e2, double &e3) {
-    if (x >= kExpnUni1) {          // the table ends below x = 40
-        if (x > 40.0) {
+    const long long xb = __double_as_longlong(x);
+    if (xb >= kBits40) {           // the table ends below x = 40
+        if (xb > kBits40) {
             e2 = e3 = 0.0;
         } else {
             double e4;
@@ -386,19 +386,19 @@ __device__ __forceinline__ void e23(double x, double &e2, double &e3) {
         }
         return;
     }
-    if (x <= 0.0) {
+    if (xb <= 0) {
         e2 = 1.0;
         e3 = 0.5;
         return;
     }
-    if (x < 0x1p-40) {
+    if (xb < kBits2m40) {
         // E_2 = 1 + x (ln x + gamma - 1) + O(x^2), E_3 = 1/2 - x + O(x^2 ln x)
         e2 = 1.0 + x * (log(x) + (kEuler - 1.0));
         e3 = 0.5 - x;
         return;
     }
     double t;
-    const double *c = expn3_node(x, t);
+    const double *c = g_expn3_tab + expn_node(x, t) * kExpnK;
     double p = __ldg(c + kExpnK - 1), d1 = 0.0;
 #pragma unroll
     for (int k = kExpnK - 2; k >= 0; --k) {
@@ -411,16 +411,17 @@ __device__ __forceinline__ void e23(double x, double &e2, double &e3) {
 
 // E3 alone (one Horner chain), the same values as e23's
 __device__ __forceinline__ double e3only(double x) {
-    if (x >= kExpnUni1) {
-        if (x > 40.0) return 0.0;
+    const long long xb = __double_as_longlong(x);
+    if (xb >= kBits40) {
+        if (xb > kBits40) return 0.0;
         double e2, e3, e4;
         expn234(x, e2, e3, e4);
         return e3;
     }
-    if (x <= 0.0) return 0.5;
-    if (x < 0x1p-40) return 0.5 - x;
+    if (xb <= 0) return 0.5;
+    if (xb < kBits2m40) return 0.5 - x;
     double t;
-    const double *c = expn3_node(x, t);
+    const double *c = g_expn3_tab + expn_node(x, t) * kExpnK;
     double p = __ldg(c + kExpnK - 1);
 #pragma unroll
     for (int k = kExpnK - 2; k >= 0; --k) p = fma(p, t, __ldg(c + k));
@@ -663,6 +664,10 @@ __device__ void scat_lambda(const ScatCol &c) {
         row[0] += wz * (1.0 + r);
         row[1] -= wz * r;
         c.a[j] = c.eps[j] * c.B[j];
+        // the diagonal of M in FP64 before rounding: where the slab is optically thick and
+        // eps below the FP32 resolution, 1 - (1 - eps) Lambda_jj is far below FP32's
+        // spacing near 1 and would otherwise round to zero
+        c.p32[j] = (float)(1.0 - (1.0 - c.eps[j]) * row[j]);
     }
     __syncthreads();
 }
@@ -697,7 +702,8 @@ __device__ __forceinline__ void scat_row_weights(const ScatCol &c, int j, Seg &&
 }
 
 // FP32 inverse of M = I - diag(1 - eps) Lambda by Gauss-Jordan elimination in place,
-// without pivoting (M is diagonally dominant).  The CTA is a 16 x TX grid of threads;
+// without pivoting (M is diagonally dominant); the diagonal of M comes from scat_lambda
+// (FP64, in p32), the off-diagonal elements are formed in FP32.  The CTA is a 16 x TX grid of threads;
 // thread (ty, tx) holds the elements of rows ty + 16 i (i < RT) and columns tx + TX jj
 // (jj < CT) in registers.  Step p replaces every element by a_rk - f_r g_k with
 //   f_r = (a_rp - [r = p]) / a_pp,  g_k = a_pk + [k = p],
@@ -714,11 +720,11 @@ __device__ void scat_inverse(const ScatCol &c) {
 #pragma unroll
     for (int i = 0; i < RT; ++i) {
         const int r = ty + 16 * i;
-        const double w = r < nd ? 1.0 - c.eps[r] : 0.0;
+        const float w = r < nd ? (float)(1.0 - c.eps[r]) : 0.0f;
 #pragma unroll
         for (int jj = 0; jj < CT; ++jj) {
             const int k = tx + TX * jj;
-            a[i][jj] = (r < nd && k < nd) ? (float)((r == k ? 1.0 : 0.0) - w * c.Lam[(size_t)r * W + k]) : 0.0f;
+            a[i][jj] = (r < nd && k < nd) ? (r == k ? c.p32[r] : -w * (float)c.Lam[(size_t)r * W + k]) : 0.0f;
         }
     }
     if (ty == 0) {
@@ -736,7 +742,10 @@ __device__ void scat_inverse(const ScatCol &c) {
         const int par = p & 1;
         const float *cb = colb + par * nd, *rb = rowb + par * nd;
         float *cn = colb + (par ^ 1) * nd, *rn = rowb + (par ^ 1) * nd;
-        const float inv = __frcp_rn(rb[p]);
+        // a pivot that rounds to zero (M singular to FP32) skips its step: the result
+        // stays finite, and the refinement that cannot converge with it reports
+        const float piv = rb[p];
+        const float inv = fabsf(piv) >= 1e-30f ? __frcp_rn(piv) : 0.0f;
         float f[RT], g[CT];
 #pragma unroll
         for (int i = 0; i < RT; ++i) {
@@ -914,8 +923,11 @@ __global__ void __launch_bounds__(kScatThreadsFwd, RT <= 5 ? 3 : 1) k_flux_scatt
         // summed by warp 0 in a fixed order
         for (int d = tid; d < nd; d += blockDim.x) {
             double v = 0.0;
-            if (d + 1 < nd)
-                v = interval(c.tau[d], c.tau[d + 1], c.S[d], c.S[d + 1], c.e3[d], c.e4[d], c.e3[d + 1], c.e4[d + 1]);
+            if (d + 1 < nd) {   // interval() with the slope from the stored reciprocal 1/D = 2 hD
+                const double D = c.tau[d + 1] - c.tau[d];
+                const double sl = (c.S[d + 1] - c.S[d]) * (2.0 * c.hD[d + 1]);
+                v = c.S[d] * (c.e3[d] - c.e3[d + 1]) + sl * (c.e4[d] - c.e4[d + 1] - D * c.e3[d + 1]);
+            }
             if (d == 0) {
                 const double s0 = (c.S[1] - c.S[0]) / (c.tau[1] - c.tau[0]);
                 v += interval(0.0, c.tau[0], c.S[0] - s0 * c.tau[0], c.S[0], 0.5, 1.0 / 3.0, c.e3[0], c.e4[0]);
@@ -967,28 +979,35 @@ __global__ void __launch_bounds__(kScatThreadsAdj, 1) k_rt_adjoint_scatter(ScatA
     scat_matvec<false>(c, c.Lam, c.S, c.J);
     for (int j = tid; j < nd; j += blockDim.x) expn234(c.tau[j], c.e2[j], c.e3[j], c.e4[j]);
     __syncthreads();
-    // dF/dS (a, times dL/dF) and dF/dtau at fixed S (dF), both with the 2 pi of the flux
+    // dF/dS (a, times dL/dF) and dF/dtau at fixed S (dF), both with the 2 pi of the flux.
+    // Each interval (d, d + 1) once (the terms of interval_grad), its shares of its lower
+    // and upper layer kept in vectors that are dead here (e2bot, hD) or not yet written
+    // (mu, wx: the transposed solve's).
     const double D1 = c.tau[1] - c.tau[0];
     const double t0 = c.tau[0];
     const double s0 = (c.S[1] - c.S[0]) / D1;
+    double *a_lo = c.e2bot, *a_hi = c.hD, *f_lo = c.mu, *f_hi = c.wx;
+    for (int d = tid; d + 1 < nd; d += blockDim.x) {
+        const double iD = c.invD[d], D = c.tau[d + 1] - c.tau[d];
+        const double sl = (c.S[d + 1] - c.S[d]) * iD;
+        const double P = c.e3[d] - c.e3[d + 1];
+        const double Bq = c.e4[d] - c.e4[d + 1] - D * c.e3[d + 1];
+        const double q = Bq * iD;
+        a_lo[d] = P - q;
+        a_hi[d] = q;
+        f_lo[d] = -c.S[d] * c.e2[d] + (sl * iD) * Bq - sl * P;
+        f_hi[d] = c.S[d + 1] * c.e2[d + 1] - (sl * iD) * Bq;
+    }
+    __syncthreads();
     for (int d = tid; d < nd; d += blockDim.x) {
         double a = 0.0, df = 0.0;
         if (d + 1 < nd) {   // interval (d, d + 1), d its lower end
-            const double D = c.tau[d + 1] - c.tau[d];
-            const double q = (c.e4[d] - c.e4[d + 1] - D * c.e3[d + 1]) / D;
-            a += (c.e3[d] - c.e3[d + 1]) - q;
-            double da, db;
-            interval_grad(c.tau[d], c.tau[d + 1], c.S[d], c.S[d + 1], c.e2[d], c.e3[d], c.e4[d], c.e2[d + 1],
-                          c.e3[d + 1], c.e4[d + 1], da, db);
-            df += da;
+            a += a_lo[d];
+            df += f_lo[d];
         }
         if (d >= 1) {       // interval (d - 1, d), d its upper end
-            const double D = c.tau[d] - c.tau[d - 1];
-            a += (c.e4[d - 1] - c.e4[d] - D * c.e3[d]) / D;
-            double da, db;
-            interval_grad(c.tau[d - 1], c.tau[d], c.S[d - 1], c.S[d], c.e2[d - 1], c.e3[d - 1], c.e4[d - 1], c.e2[d],
-                          c.e3[d], c.e4[d], da, db);
-            df += db;
+            a += a_hi[d - 1];
+            df += f_hi[d - 1];
         }
         if (d <= 1) {       // top interval [0, tau_0] with S(0) = S0 - s0 tau_0
             const double qt = (1.0 / 3.0 - c.e4[0] - t0 * c.e3[0]) / t0;

@@ -119,7 +119,7 @@ def test_scattering_dominated_solve_converges_or_reports(oracle, r0):
     """eps near 0 in the upper layers (sigma_c up to r0 kappa_c): the FP64-refined solve
     either converges, and then F and f match the oracle's at the parity bars, or it
     reports PZ_ENUMERIC through pz_sync_status; an unconverged result is never returned
-    silently."""
+    silently, and the flux is finite either way."""
     prob = tiny_problem(n_lambda=160, n_depth=40, n_lines=20, W=60, seed=41, lam0=340.0)
     prob.lines.log_gf[:] -= 3.0
     sc = I.with_scattering(prob, r0=r0)
@@ -139,6 +139,7 @@ def test_scattering_dominated_solve_converges_or_reports(oracle, r0):
             converged = False
         eF = float(np.max(np.abs(got["F"] / ref["F"] - 1)))
         print("r0 %.0e prec %d: converged %s, F rel err %.3g" % (r0, prec, converged, eF))
+        assert np.all(np.isfinite(got["F"])) and np.all(np.isfinite(got["Fc"]))
         if converged:
             assert eF < ftol, eF
         s.close()
