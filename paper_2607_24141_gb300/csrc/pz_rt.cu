@@ -981,12 +981,12 @@ __global__ void __launch_bounds__(kScatThreadsAdj, 1) k_rt_adjoint_scatter(ScatA
     __syncthreads();
     // dF/dS (a, times dL/dF) and dF/dtau at fixed S (dF), both with the 2 pi of the flux.
     // Each interval (d, d + 1) once (the terms of interval_grad), its shares of its lower
-    // and upper layer kept in vectors that are dead here (e2bot, hD) or not yet written
-    // (mu, wx: the transposed solve's).
+    // and upper layer kept in vectors that are dead here (e2bot) or not yet written (ge;
+    // mu, wx: the transposed solve's).
     const double D1 = c.tau[1] - c.tau[0];
     const double t0 = c.tau[0];
     const double s0 = (c.S[1] - c.S[0]) / D1;
-    double *a_lo = c.e2bot, *a_hi = c.hD, *f_lo = c.mu, *f_hi = c.wx;
+    double *a_lo = c.e2bot, *a_hi = c.ge, *f_lo = c.mu, *f_hi = c.wx;
     for (int d = tid; d + 1 < nd; d += blockDim.x) {
         const double iD = c.invD[d], D = c.tau[d + 1] - c.tau[d];
         const double sl = (c.S[d + 1] - c.S[d]) * iD;
@@ -1028,68 +1028,68 @@ __global__ void __launch_bounds__(kScatThreadsAdj, 1) k_rt_adjoint_scatter(ScatA
     }
     __syncthreads();
     scat_refine<true>(c, c.a, c.mu, &s_done, g.status);
-    // dJ_j/dtau_m into the Lambda area (Lambda is no longer needed): the off-diagonal
-    // elements by (row, part), element k from segments k - 1 (its upper weight) and k (its
-    // lower weight), the top segment's terms at k <= 1 and the slab end at k = N - 1; then
-    // the diagonal from the row sums
+    // dJ_j/dtau_m into the Lambda area (Lambda is no longer needed), off-diagonal elements
+    // by (row, part).  Moving layer k at fixed S_k changes S(t) by -S'(t) times its hat
+    // function, so element k is -s_{k-1} wb_{k-1} - s_k wa_k (s the segment slopes, wa/wb
+    // the weights of a segment's lower and upper layer).  In the divided-difference form of
+    // the Lambda pass (wb_{k-1} = G'_k - Q_{k-1}, wa_k = Q_k - G'_k with G' continuous), for
+    // an inner layer k != j the |t - tau_j| parts cancel and
+    //   dJ_j/dtau_k = -sgn(k - j) E2(|tau_k - tau_j|)/2 (s_k - s_{k-1}) + s_{k-1} qt_{k-1} - s_k qt_k,
+    // qt as in scat_lambda; layers 0 and N - 1 take the segment weights directly, plus the top
+    // segment's terms at k <= 1 (S(0) extrapolated) and the slab end at k = N - 1.  Then the
+    // diagonal from the row sums.
     const double Szero = c.S[0] - s0 * t0;
+    for (int k = tid; k < nd; k += blockDim.x) {   // slopes and their steps (a, e2bot are free here)
+        const double sk = k + 1 < nd ? (c.S[k + 1] - c.S[k]) * c.invD[k] : 0.0;
+        c.a[k] = sk;
+        c.e2bot[k] = (k >= 1 && k + 1 < nd) ? sk - (c.S[k] - c.S[k - 1]) * c.invD[k - 1] : 0.0;
+    }
+    __syncthreads();
     {
+        const double *sl = c.a, *ds = c.e2bot;
         const ScatSplit sp(nd);
         if (sp.q < sp.P && sp.k0 < sp.k1) {
             const int j = sp.j;
             double *row = c.Lam + (size_t)j * W;
-            double e2p, e3p, wbs = 0.0;   // E at node k; -s_{k-1} times the upper weight of segment k - 1
-            if (sp.k0 > 0) {
-                const int k = sp.k0 - 1;
-                double e2m, e3m, wn, wf;
-                scat_E<TS>(c, j, k, e2m, e3m);
-                scat_E<TS>(c, j, k + 1, e2p, e3p);
-                const double D = c.tau[k + 1] - c.tau[k];
-                double wb;
-                if (k >= j) {
-                    seg_weights(D, c.invD[k], e2m, e3m, e2p, e3p, wn, wf);
-                    wb = wf;
-                } else {
-                    seg_weights(D, c.invD[k], e2p, e3p, e2m, e3m, wn, wf);
-                    wb = wn;
-                }
-                wbs = -((c.S[k + 1] - c.S[k]) * c.invD[k]) * wb;
-            } else {
-                scat_E<TS>(c, j, 0, e2p, e3p);
-            }
+            double e3c = scat_g3<TS>(c, j, sp.k0), sqp = 0.0;   // E3 at k, s_{k-1} qt_{k-1}
+            if (sp.k0 >= 1) sqp = sl[sp.k0 - 1] * ((e3c - scat_g3<TS>(c, j, sp.k0 - 1)) * c.hD[sp.k0]);
             double off = 0.0;
             for (int k = sp.k0; k < sp.k1; ++k) {
-                double v = wbs;
-                if (k <= 1) {   // the top segment [0, tau_0] with the extrapolated S(0)
-                    double e20, e30, whi, wlo;
-                    scat_E<TS>(c, j, 0, e20, e30);
-                    seg_weights(t0, 1.0 / t0, e20, e30, c.e2top[j], c.e3top[j], whi, wlo);   // near: tau_0, far: 0
-                    v += k == 0 ? -(s0 / D1) * t0 * wlo - s0 * (wlo + whi) : (s0 / D1) * t0 * wlo;
-                }
+                double e3n = 0.0, sq = 0.0;
                 if (k + 1 < nd) {
-                    double e2n, e3n, wn, wf, wa, wb;
-                    scat_E<TS>(c, j, k + 1, e2n, e3n);
-                    const double D = c.tau[k + 1] - c.tau[k];
-                    if (k >= j) {          // below tau_j: near end k, far end k + 1
-                        seg_weights(D, c.invD[k], e2p, e3p, e2n, e3n, wn, wf);
-                        wa = wn;
-                        wb = wf;
-                    } else {               // above: near end k + 1, far end k
-                        seg_weights(D, c.invD[k], e2n, e3n, e2p, e3p, wn, wf);
-                        wa = wf;
-                        wb = wn;
-                    }
-                    const double sk = (c.S[k + 1] - c.S[k]) * c.invD[k];
-                    v -= sk * wa;
-                    wbs = -sk * wb;
-                    e2p = e2n;
-                    e3p = e3n;
+                    e3n = scat_g3<TS>(c, j, k + 1);
+                    sq = sl[k] * ((e3n - e3c) * c.hD[k + 1]);
                 }
-                if (k == nd - 1 && j != nd - 1) v += 0.5 * c.S[nd - 1] * e1(c.tau[nd - 1] - c.tau[j]);
                 if (k != j) {
+                    double v;
+                    if (k == 0 || k == nd - 1) {   // the end layers: one segment's weight
+                        const int kk = k == 0 ? 0 : nd - 2;
+                        double e2a, e3a, e2b, e3b, wn, wf;
+                        scat_E<TS>(c, j, kk, e2a, e3a);
+                        scat_E<TS>(c, j, kk + 1, e2b, e3b);
+                        const double D = c.tau[kk + 1] - c.tau[kk];
+                        if (kk >= j)
+                            seg_weights(D, c.invD[kk], e2a, e3a, e2b, e3b, wn, wf);   // wa = wn, wb = wf
+                        else
+                            seg_weights(D, c.invD[kk], e2b, e3b, e2a, e3a, wf, wn);   // wa = wn, wb = wf
+                        v = -sl[kk] * (k == kk ? wn : wf);
+                        if (k == nd - 1) v += 0.5 * c.S[nd - 1] * e1(c.tau[nd - 1] - c.tau[j]);
+                    } else {
+                        double e2k, e3k;
+                        scat_E<TS>(c, j, k, e2k, e3k);
+                        v = fma(k > j ? -0.5 * e2k : 0.5 * e2k, ds[k], sqp - sq);
+                    }
+                    if (k <= 1) {   // the top segment [0, tau_0] with the extrapolated S(0)
+                        double e20, e30, whi, wlo;
+                        scat_E<TS>(c, j, 0, e20, e30);
+                        seg_weights(t0, 1.0 / t0, e20, e30, c.e2top[j], c.e3top[j], whi, wlo);   // near: tau_0, far: 0
+                        v += k == 0 ? -(s0 / D1) * t0 * wlo - s0 * (wlo + whi) : (s0 / D1) * t0 * wlo;
+                    }
                     row[k] = v;
                     off += v;
                 }
+                e3c = e3n;
+                sqp = sq;
             }
             c.p64[sp.q * nd + j] = off;
         }
