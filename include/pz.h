@@ -402,7 +402,8 @@ pz_status pz_autotune(pz_ctx *ctx, int32_t with_backward, int32_t reps, int32_t 
  *          stopped with its last correction above 1e-9 of the solution (stalled,
  *          growing, or out of rounds), in the forward or the reverse pass: the flux or
  *          the gradients of that wavelength rest on an unconverged solve.  Refinement
- *          ends at a correction below 1e-14 of the solution, or where the correction
+ *          ends once a correction below 1e-12 of the solution has been applied (what
+ *          remains is that times the contraction per round), or where the correction
  *          stops halving per round.
  * This call synchronises `stream`, stores the status word in *flags (host, may be
  * NULL), clears it, and returns PZ_ETIMEOUT if bit 0 was set, PZ_ENUMERIC if bit 1

@@ -819,7 +819,8 @@ __device__ void scat_matvec(const ScatCol &c, const double *A, const double *x, 
 }
 
 // Iterative refinement with FP64 residuals of M x = rhs (TRANS false) or M^T x = rhs:
-// x += M^-1 (rhs - M x) with the FP32 inverse until the correction is below 1e-14 of x,
+// x += M^-1 (rhs - M x) with the FP32 inverse until the correction is below 1e-12 of x
+// (it is applied, so what remains is that times the contraction per round, ~cond(M) 2^-24),
 // or until it stops shrinking (at least halving per round after the second), which is
 // where FP64 residuals of an ill-conditioned M (eps near 0) leave it.  A solve that
 // stops with a last correction above 1e-9 of x (stalled there, growing, or out of
@@ -862,7 +863,7 @@ __device__ void scat_refine(const ScatCol &c, const double *rhs, double *x, int 
                 smax = fmax(smax, __shfl_xor_sync(0xffffffffu, smax, o));
             }
             if (tid == 0) {
-                const bool conv = dmax <= 1e-14 * smax;
+                const bool conv = dmax <= 1e-12 * smax;
                 const bool stop = conv || (it >= 2 && dmax >= 0.5 * s_dprev) || it + 1 == kScatMaxRefine;
                 if (stop && !conv && dmax > 1e-9 * smax && status) atomicOr(status, kStatusScatNoConverge);
                 s_dprev = dmax;
