@@ -49,8 +49,17 @@ GOLDEN = os.path.join(ROOT, "tests", "golden")
 # the dominant kernel, from one ncu capture per (kernel, workload) written up under profiles/;
 # each entry is valid only while the library sources hash to the recorded value, and is
 # reported as null otherwise.
-TRAFFIC = {}
-NCU_PIPES = {}
+TRAFFIC = {
+    # 8-star batch launch: 161.9 MB read + 9.9 MB written, scaled to the 64-star launch by its
+    # evaluations (1.6398e12 / 1.6699e11 = 9.82; the traffic is line records per tile plus the
+    # G stim rows, both in proportion to the stars' lines and tiles)
+    ("k_line_bwd", "batch64"): (1.687e9, "fb12a3e977bc8278"),
+}
+NCU_PIPES = {
+    ("k_line_bwd", "batch64"): ({"fma_pipe_pct": 57.1, "alu_pipe_pct": 26.1, "xu_pipe_pct": 8.8,
+                                 "issue_active_pct": 62.0, "warps_active_pct": 24.9, "registers": 96,
+                                 "capture": "8-star batch, one launch, --set full"}, "fb12a3e977bc8278"),
+}
 KERNEL_SOURCES = ("pz_line.cu", "pz_voigt.cuh", "pz_internal.h", "pz_api.cu")
 FMA_PER_EN = 39      # FP64 FMAs of one E_2/E_3/E_4 Taylor step (13 rounds of value + two derivatives)
 
@@ -1235,9 +1244,14 @@ def main():
 
     # single-star APOGEE-like step; tunes the tiling every other workload reuses
     if args.only == "headline":
-        hl = run_headline(args, dev, barrier, max_over_ranks, ws, rank, None, pipe_peaks, clk_max)
+        # the single-star tiling from the tuning cache, as the full run would apply it
+        from paper_2607_24141_gb300 import inputs as I
+        from paper_2607_24141_gb300 import tuning
+        tiling = tuning.lookup(cached("config1", lambda: I.config1(seed=1)), pz.PZ_MIXED, local)
+        hl = run_headline(args, dev, barrier, max_over_ranks, ws, rank, tiling, pipe_peaks, clk_max)
         if rank == 0:
             print(json.dumps({"ms_per_step": hl["ms_per_step"], "value": hl["value"], "parity": hl["parity"],
+                              "tiling": tiling,
                               "kernel_ms_per_step": {k: v[0] / args.steps for k, v in hl["kernel_times"].items()}}),
                   flush=True)
         return 0

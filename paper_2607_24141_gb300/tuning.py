@@ -44,19 +44,35 @@ def _log2_bucket(x: float) -> int:
     return int(round(math.log2(x))) if x > 0 else -99
 
 
-def shape_class(synth) -> str:
-    """Shape key of a Synthesizer's workload (see the module docstring)."""
-    prob = synth.prob
+def shape_class_of(prob, precision: int) -> str:
+    """Shape key of a problem (single star, or a batch with .subsets) at a precision."""
     n_lambda = prob.grid.n_lambda
-    if synth.batched:
+    batched = hasattr(prob, "subsets")
+    if batched:
         lines = sum(len(x) for x in prob.subsets) / max(len(prob.subsets), 1)
         nd = prob.atmos[0].n_depth
+        n_stars = len(prob.subsets)
     else:
         lines = prob.lines.n_lines
         nd = prob.atmos.n_depth
-    return "S%d-p%d-nd%d-nl%d-W%d-lpp%d" % (synth.n_stars, synth.precision, nd, _log2_bucket(n_lambda),
+        n_stars = 1
+    return "S%d-p%d-nd%d-nl%d-W%d-lpp%d" % (n_stars, precision, nd, _log2_bucket(n_lambda),
                                             _log2_bucket(prob.lines.half_window),
                                             _log2_bucket(2.0 * lines / max(n_lambda, 1)))
+
+
+def shape_class(synth) -> str:
+    """Shape key of a Synthesizer's workload (see the module docstring)."""
+    return shape_class_of(synth.prob, synth.precision)
+
+
+def lookup(prob, precision: int, device=None, path: str = DEFAULT_CACHE):
+    """The cached tiling (5 ints) for this GPU, library build and problem shape, or None."""
+    key = "%s|%s|%s" % (gpu_key(device), library_hash(), shape_class_of(prob, precision))
+    entry = _load(path).get(key)
+    if entry and len(entry.get("tiling", ())) == 5:
+        return tuple(entry["tiling"])
+    return None
 
 
 def gpu_key(device=None) -> str:
