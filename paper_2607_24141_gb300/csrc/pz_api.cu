@@ -213,8 +213,8 @@ static void dfree(void *p) { dev_free(p); }
 //         near-core backward items are cut the same way;
 //   near: lines whose centre lies within 20 Doppler widths (the widest of the star)
 //         of the tile plus a margin; forward items for every (star, tile, group of
-//         8 layers) (they write the near-core buffer), backward items of 24 layers
-//         only where the range is not empty.
+//         kNearDepthsFwd layers) (they write the near-core buffer), backward items of
+//         kNearDepthsBwd layers only where the range is not empty.
 constexpr double kPiecesPerCta = 8.0;       // target far pieces per resident CTA
 constexpr int kMaxPieces = 32;              // pieces of one far item at most
 constexpr int kMinPieceLines = 256;         // lines of a far piece at least
@@ -227,7 +227,7 @@ static pz_status build_items(pz_ctx *c) {
     const int nt = (int)((c->nlam + T - 1) / T);
     const int DC = c->tiling.depth_per_cta();
     const int ngf = (c->nd + DC - 1) / DC;
-    const int nnf = (c->nd + 7) / 8, nnb = (c->nd + 23) / 24;
+    const int nnf = (c->nd + kNearDepthsFwd - 1) / kNearDepthsFwd, nnb = (c->nd + kNearDepthsBwd - 1) / kNearDepthsBwd;
     struct Item {
         int4 v;
         double cost;
@@ -253,10 +253,12 @@ static pz_status build_items(pz_ctx *c) {
             const int nlo = (int)(std::lower_bound(b0, b1, (int32_t)std::floor(na)) - c->h_il.begin());
             const int nhi = (int)(std::upper_bound(b0, b1, (int32_t)std::ceil(nb_)) - c->h_il.begin());
             for (int g = 0; g < nnf; ++g)
-                nf.push_back({make_int4(st, t * nnf + g, nlo, nhi), (double)(nhi - nlo) * std::min(8, c->nd - g * 8)});
+                nf.push_back({make_int4(st, t * nnf + g, nlo, nhi),
+                              (double)(nhi - nlo) * std::min(kNearDepthsFwd, c->nd - g * kNearDepthsFwd)});
             if (nhi > nlo)
                 for (int g = 0; g < nnb; ++g)
-                    nb.push_back({make_int4(st, t * nnb + g, nlo, nhi), (double)(nhi - nlo) * std::min(24, c->nd - g * 24)});
+                    nb.push_back({make_int4(st, t * nnb + g, nlo, nhi),
+                                  (double)(nhi - nlo) * std::min(kNearDepthsBwd, c->nd - g * kNearDepthsBwd)});
         }
     }
     auto order = [](std::vector<Item> &v) {

@@ -27,6 +27,8 @@ constexpr double kC2 = kH * kC / kKB;       // second radiation constant, cm K
 
 // Largest supported depth count (register/local arrays in the flux kernels).
 constexpr int kMaxDepth = 128;
+constexpr int kNearDepthsFwd = 8;    // layers per work item of the near-core forward
+constexpr int kNearDepthsBwd = 6;    // layers per work item of the near-core backward
 // Largest number of instrument taps per pixel.
 constexpr int kMaxTaps = 4096;
 // Device ordinals a context may live on (per-device launch-attribute bookkeeping).

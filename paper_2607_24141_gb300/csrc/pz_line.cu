@@ -1303,8 +1303,6 @@ struct alignas(16) NearItem {
 };
 
 constexpr int kNearBatch = 512;      // lines per shared-memory batch of the backward sums
-constexpr int kNearDepthsFwd = 8;    // depths per CTA of the near-core forward
-constexpr int kNearDepthsBwd = 24;   // depths per CTA of the near-core backward
 constexpr int kNearWarps = 8;        // warps per near-core CTA
 
 // Dense pass over the concatenated cells of one segment kind of the warp's 32 items:
