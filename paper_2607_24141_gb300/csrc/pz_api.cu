@@ -396,7 +396,7 @@ static void destroy_ctx(pz_ctx *c) {
     drop_graph(c);
     void *ptrs[] = {c->d_m, c->d_T, c->d_beta_hi, c->d_beta_lo, c->d_ne, c->d_npert, c->d_c2T, c->d_ne64,
                     c->d_npert64, c->d_rho64, c->d_R, c->d_Rbase, c->d_invdv, c->d_Ksd, c->d_pop64, c->d_mass64, c->d_xi64,
-                    c->d_thr, c->d_kc, c->d_dab, c->d_mdgf, c->d_mdg6, c->d_eos, c->L.orig, c->L.star, c->L.ilf,
+                    c->d_thr, c->d_kc, c->d_B, c->d_stim, c->d_dab, c->d_mdgf, c->d_mdg6, c->d_eos, c->L.orig, c->L.star, c->L.ilf,
                     c->L.il32, c->L.frac, c->L.sp, c->L.E, c->L.lamcm, c->L.grad, c->L.g4, c->L.g6base, c->L.g6,
                     c->L.Q, c->L.Qbase, c->L.x64, c->L.lg_gf, c->L.lg_rad, c->L.lg_4, c->L.lg_6, c->L.dgf, c->L.dg6,
                     c->d_line_off, c->d_fitems, c->d_fext, c->d_bitems, c->d_fpart, c->d_fcnt, c->d_nitems_f,
@@ -644,6 +644,10 @@ static pz_status create_impl(int S, const pz_atmos *atv, const pz_linelist *ll, 
                                     nlam * sizeof(double), nlam * sizeof(double), nd, cudaMemcpyHostToDevice),
                        "kappa_c"))
             return bail(PZ_ECUDA);
+    // ---- Planck function and stimulated-emission factor [S][nd][ld], from T and lambda ----
+    if (dalloc(&c->d_B, SD * c->ld, "Planck table") || dalloc(&c->d_stim, SD * c->ld, "Planck table"))
+        return bail(PZ_ENOMEM);
+    if (cuda_check(launch_planck_tables(c, 0), "Planck table")) return bail(PZ_ECUDA);
 
     // ---- resident buffers ----
     size_t ksz = (prec == PZ_MIXED) ? sizeof(float) : sizeof(double);

@@ -147,6 +147,8 @@ struct pz_ctx {
     float *d_thr = nullptr;         // [S][ns][nslab] fast-path distance threshold (grid units)
     int nslab = 0;                  // depth slabs of DS layers covered by the launch grid
     double *d_kc = nullptr;         // [S][nd][ld] continuum opacity FP64
+    double *d_B = nullptr;          // [S][nd][ld] Planck function B_lambda(T_d) per nm, FP64
+    double *d_stim = nullptr;       // [S][nd][ld] stimulated-emission factor 1 - exp(-hc/(lambda k T_d)), FP64
     double *d_sigma = nullptr;      // [S][nd][ld] continuum scattering FP64, or NULL (S = B)
     double *d_dab = nullptr;        // [n_elem] current abundance offsets
     float *d_mdgf = nullptr, *d_mdg6 = nullptr;   // [nl_caller] current line corrections, caller order
@@ -252,6 +254,7 @@ cudaError_t launch_probe_voigt(const float *a, const float *v, int64_t n, float 
                                cudaStream_t s);
 
 cudaError_t launch_flux(pz_ctx *c, cudaStream_t s);
+cudaError_t launch_planck_tables(pz_ctx *c, cudaStream_t s);   // fills d_B and d_stim
 cudaError_t launch_inst_build(pz_ctx *c, const double *d_pix, double v_r, double v_b, double R_lsf,
                               int32_t *d_err, cudaStream_t s);
 cudaError_t launch_inst_apply(pz_ctx *c, float *f, cudaStream_t s);

@@ -210,6 +210,28 @@ __device__ __forceinline__ double planck_nm(double lamcm, double T) {
     return 2.0 * kH * kC * kC / (l2 * l2 * lamcm) / expm1(kC2 / (lamcm * T)) * 1e-7;
 }
 
+// B_lambda(T_d) and the stimulated-emission factor 1 - exp(-hc/(lambda k T_d)) at every
+// (star, layer, grid point): they depend on the atmosphere and the grid alone, like kappa_c,
+// and the flux, its adjoint and the scattering kernels read them (one thread per point).
+__global__ void k_planck_tables(int64_t nlam, int64_t ld, int nd, double lam0cm, double lnr, const double *T,
+                                double *B, double *stim) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nlam) return;
+    const int64_t sd = blockIdx.y;     // star * nd + layer
+    const double lam = lam0cm * exp((double)i * lnr);
+    const double t = T[sd];
+    B[sd * ld + i] = planck_nm(lam, t);
+    stim[sd * ld + i] = -expm1(-kC2 / (lam * t));
+}
+
+cudaError_t launch_planck_tables(pz_ctx *c, cudaStream_t s) {
+    if (c->nlam <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((c->nlam + 255) / 256), (unsigned)((int64_t)c->S * c->nd));
+    k_planck_tables<<<grid, 256, 0, s>>>(c->nlam, c->ld, c->nd, c->lambda0_nm * 1e-7, c->lnr, c->d_T, c->d_B, c->d_stim);
+    c->launches++;
+    return cudaGetLastError();
+}
+
 __device__ __forceinline__ double interval(double ta, double tb, double Sa, double Sb, double e3a, double e4a,
                                            double e3b, double e4b) {
     double D = tb - ta;
@@ -221,7 +243,7 @@ struct FluxArgs {
     int64_t nlam, ld;
     int nd;
     double lam0cm, lnr;
-    const double *m, *T, *kc;
+    const double *m, *T, *kc, *B;
     const void *kline;
     double *F, *Fc;
 };
@@ -236,12 +258,12 @@ __global__ void k_flux(FluxArgs g) {
         g.m += (int64_t)st * g.nd;
         g.T += (int64_t)st * g.nd;
         g.kc += (int64_t)st * g.nd * g.ld;
+        g.B += (int64_t)st * g.nd * g.ld;
         g.kline = reinterpret_cast<const KT *>(g.kline) + (int64_t)st * g.nd * g.ld;
         g.F += (int64_t)st * g.nlam;
         g.Fc += (int64_t)st * g.nlam;
     }
     const KT *kl = reinterpret_cast<const KT *>(g.kline);
-    const double lam = g.lam0cm * exp((double)i * g.lnr);
     double chi_p = 0, chic_p = 0, tau_p = 0, tauc_p = 0, S_p = 0, m_p = 0;
     double e3p = 0, e4p = 0, e3cp = 0, e4cp = 0;
     double F = 0.0, Fc = 0.0;
@@ -251,7 +273,7 @@ __global__ void k_flux(FluxArgs g) {
         const double kc = g.kc[o];
         const double chi = kc + (double)kl[o];
         const double md = g.m[d];
-        const double S = planck_nm(lam, g.T[d]);
+        const double S = g.B[o];
         double tau, tauc;
         if (d == 0) {
             tau = chi * md;
@@ -297,6 +319,7 @@ cudaError_t launch_flux(pz_ctx *c, cudaStream_t s) {
     g.m = c->d_m;
     g.T = c->d_T;
     g.kc = c->d_kc;
+    g.B = c->d_B;
     g.kline = c->d_kline;
     g.F = c->d_F;
     g.Fc = c->d_Fc;
@@ -335,7 +358,7 @@ struct ScatArgs {
     int64_t nlam, ld;
     int nd;
     double lam0cm, lnr;
-    const double *m, *T, *kc, *sig;
+    const double *m, *T, *kc, *sig, *B, *stim;
     const void *kline;
     double *F, *Fc;
     const double *dFbar;   // adjoint: dL/dF [S][nlam]
@@ -905,10 +928,8 @@ __global__ void __launch_bounds__(kScatThreadsFwd, RT <= 5 ? 3 : 1) k_flux_scatt
     const int st = blockIdx.y;
     const int tid = threadIdx.x;
     const double *m = g.m + (int64_t)st * nd;
-    const double *T = g.T + (int64_t)st * nd;
     const int64_t base = (int64_t)st * nd * g.ld + i;
-    const double lam = g.lam0cm * exp((double)i * g.lnr);
-    for (int d = tid; d < nd; d += blockDim.x) c.B[d] = planck_nm(lam, T[d]);
+    for (int d = tid; d < nd; d += blockDim.x) c.B[d] = g.B[base + (int64_t)d * g.ld];
     for (int branch = 0; branch < 2; ++branch) {
         scat_columns<KT, 1>(g, c, base, m, branch);
         scat_lambda<1>(c);
@@ -967,11 +988,9 @@ __global__ void __launch_bounds__(kScatThreadsAdj, 1) k_rt_adjoint_scatter(ScatA
     const int st = blockIdx.y;
     const int tid = threadIdx.x;
     const double *m = g.m + (int64_t)st * nd;
-    const double *T = g.T + (int64_t)st * nd;
     const int64_t base = (int64_t)st * nd * g.ld + i;
-    const double lam = g.lam0cm * exp((double)i * g.lnr);
     const double Fb = g.dFbar[(int64_t)st * g.nlam + i];
-    for (int d = tid; d < nd; d += blockDim.x) c.B[d] = planck_nm(lam, T[d]);
+    for (int d = tid; d < nd; d += blockDim.x) c.B[d] = g.B[base + (int64_t)d * g.ld];
     scat_columns<KT, TS>(g, c, base, m, 0);
     scat_lambda<TS>(c);
     scat_inverse<RT, CT, 32>(c);
@@ -1141,8 +1160,7 @@ __global__ void __launch_bounds__(kScatThreadsAdj, 1) k_rt_adjoint_scatter(ScatA
         else gch += m[0] * Td;
         const double sig = g.sig[base + (int64_t)d * g.ld];
         gch += c.ge[d] * sig / (c.chi[d] * c.chi[d]);
-        const double stim = -expm1(-kC2 / (lam * T[d]));
-        Gt[(int64_t)d * g.ld] = (GT)(gch * stim);
+        Gt[(int64_t)d * g.ld] = (GT)(gch * g.stim[base + (int64_t)d * g.ld]);
     }
 }
 
@@ -1167,6 +1185,8 @@ static ScatArgs scatter_args(pz_ctx *c) {
     g.T = c->d_T;
     g.kc = c->d_kc;
     g.sig = c->d_sigma;
+    g.B = c->d_B;
+    g.stim = c->d_stim;
     g.kline = c->d_kline;
     g.F = c->d_F;
     g.Fc = c->d_Fc;
@@ -1408,7 +1428,7 @@ struct RtAdjArgs {
     int64_t nlam, ld;
     int nd;
     double lam0cm, lnr;
-    const double *m, *T, *kc;
+    const double *m, *T, *kc, *B, *stim;
     const void *kline;
     const double *dFbar;
     void *Gt;
@@ -1418,12 +1438,12 @@ struct RtAdjArgs {
 __device__ __forceinline__ void interval_grad(double ta, double tb, double Sa, double Sb, double e2a, double e3a,
                                               double e4a, double e2b, double e3b, double e4b, double &da,
                                               double &db) {
-    double D = tb - ta;
-    double s = (Sb - Sa) / D;
-    double P = e3a - e3b;
-    double Bq = e4a - e4b - D * e3b;
-    da = -Sa * e2a + (s / D) * Bq - s * P;
-    db = Sb * e2b - (s / D) * Bq;
+    const double D = tb - ta, iD = 1.0 / D;
+    const double s = (Sb - Sa) * iD;
+    const double P = e3a - e3b;
+    const double Bq = e4a - e4b - D * e3b;
+    da = -Sa * e2a + (s * iD) * Bq - s * P;
+    db = Sb * e2b - (s * iD) * Bq;
 }
 
 // one thread per (lambda, star); star = blockIdx.y
@@ -1436,13 +1456,14 @@ __global__ void k_rt_adjoint(RtAdjArgs g) {
         g.m += st * g.nd;
         g.T += st * g.nd;
         g.kc += st * g.nd * g.ld;
+        g.B += st * g.nd * g.ld;
+        g.stim += st * g.nd * g.ld;
         g.kline = reinterpret_cast<const KT *>(g.kline) + st * g.nd * g.ld;
         g.dFbar += st * g.nlam;
         g.Gt = reinterpret_cast<GT *>(g.Gt) + st * g.nd * g.ld;
     }
     const KT *kl = reinterpret_cast<const KT *>(g.kline);
     GT *Gt = reinterpret_cast<GT *>(g.Gt);
-    const double lam = g.lam0cm * exp((double)i * g.lnr);
     const double dFb = g.dFbar[i];
     double tau[kMaxDepth], S[kMaxDepth], dF[kMaxDepth];
     double chi_p = 0.0;
@@ -1450,7 +1471,7 @@ __global__ void k_rt_adjoint(RtAdjArgs g) {
         const int64_t o = (int64_t)d * g.ld + i;
         double chi = g.kc[o] + (double)kl[o];
         tau[d] = d == 0 ? chi * g.m[0] : tau[d - 1] + 0.5 * (chi_p + chi) * (g.m[d] - g.m[d - 1]);
-        S[d] = planck_nm(lam, g.T[d]);
+        S[d] = g.B[o];
         dF[d] = 0.0;
         chi_p = chi;
     }
@@ -1486,8 +1507,7 @@ __global__ void k_rt_adjoint(RtAdjArgs g) {
         if (d + 1 < g.nd) gch += 0.5 * (g.m[d + 1] - g.m[d]) * Tn;
         if (d >= 1) gch += 0.5 * (g.m[d] - g.m[d - 1]) * Td;
         else gch += g.m[0] * Td;
-        double stim = -expm1(-kC2 / (lam * g.T[d]));
-        Gt[(int64_t)d * g.ld + i] = (GT)(gch * stim);
+        Gt[(int64_t)d * g.ld + i] = (GT)(gch * g.stim[(int64_t)d * g.ld + i]);
         Tn = Td;
     }
 }
@@ -1503,6 +1523,8 @@ cudaError_t launch_rt_adjoint(pz_ctx *c, cudaStream_t s) {
     g.m = c->d_m;
     g.T = c->d_T;
     g.kc = c->d_kc;
+    g.B = c->d_B;
+    g.stim = c->d_stim;
     g.kline = c->d_kline;
     g.dFbar = c->d_dFbar;
     dim3 nb((unsigned)((c->nlam + 127) / 128), c->S);
