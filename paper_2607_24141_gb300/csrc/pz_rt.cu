@@ -1543,24 +1543,39 @@ cudaError_t launch_rt_adjoint(pz_ctx *c, cudaStream_t s) {
 // gradient finalisation: ln10 scale, sum over the stars that hold each caller line,
 // species -> element sums
 // ---------------------------------------------------------------------------
+// Per-line gradients into caller order (a line of several stars' subsets adds once per
+// subset) and the abundance gradients: use_ab 1 sums them per block in shared memory
+// (n_elem doubles), then one global add per (block, element); use_ab 2 (more elements
+// than the shared buffer takes) adds each line's term to the global sum directly.
 __global__ void k_grad_finalize(int64_t nl, int64_t nl_caller, const double *gacc, const int32_t *orig,
-                                const int32_t *sp, const int32_t *eos, int use_ab, int four, double *gline,
-                                double *gab) {
-    int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= nl) return;
-    const double ggf = kLN10 * gacc[l];
-    const double gg6 = kLN10 * gacc[nl + l];
-    const int32_t o = orig[l];
-    atomicAdd(gline + o, ggf);
-    atomicAdd(gline + nl_caller + o, gg6);
-    if (four) {
-        // the second sums of the radiative and Stark passes
-        atomicAdd(gline + 2 * nl_caller + o, kLN10 * gacc[3 * nl + l]);
-        atomicAdd(gline + 3 * nl_caller + o, kLN10 * gacc[5 * nl + l]);
+                                const int32_t *sp, const int32_t *eos, int use_ab, int n_elem, int four,
+                                double *gline, double *gab) {
+    extern __shared__ double s_ab[];
+    if (use_ab == 1) {
+        for (int k = threadIdx.x; k < n_elem; k += blockDim.x) s_ab[k] = 0.0;
+        __syncthreads();
     }
-    if (use_ab) {
-        int e = eos[sp[l]];
-        if (e >= 0) atomicAdd(gab + e, ggf);
+    const int64_t l = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (l < nl) {
+        const double ggf = kLN10 * gacc[l];
+        const double gg6 = kLN10 * gacc[nl + l];
+        const int32_t o = orig[l];
+        atomicAdd(gline + o, ggf);
+        atomicAdd(gline + nl_caller + o, gg6);
+        if (four) {
+            // the second sums of the radiative and Stark passes
+            atomicAdd(gline + 2 * nl_caller + o, kLN10 * gacc[3 * nl + l]);
+            atomicAdd(gline + 3 * nl_caller + o, kLN10 * gacc[5 * nl + l]);
+        }
+        if (use_ab) {
+            const int e = eos[sp[l]];
+            if (e >= 0) atomicAdd(use_ab == 1 ? s_ab + e : gab + e, ggf);
+        }
+    }
+    if (use_ab == 1) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < n_elem; k += blockDim.x)
+            if (s_ab[k] != 0.0) atomicAdd(gab + k, s_ab[k]);
     }
 }
 
@@ -1571,14 +1586,17 @@ __global__ void k_copy_d2f(int64_t n, const double *a, float *b) {
 
 cudaError_t launch_grad_finalize(pz_ctx *c, float *g_gf, float *g_g6, float *g_ab, cudaStream_t s, bool four,
                                  float *g_rad, float *g_g4) {
-    const int use_ab = c->n_elem > 0 ? 1 : 0;
+    constexpr int kMaxBlockElems = 4096;   // 32 KB of shared memory
+    const int use_ab = c->n_elem <= 0 ? 0 : (c->n_elem <= kMaxBlockElems ? 1 : 2);
     const int rows = four ? 4 : 2;
     cudaError_t e = cudaMemsetAsync(c->d_gline, 0, sizeof(double) * rows * std::max<int64_t>(c->nl_caller, 1), s);
     if (e != cudaSuccess) return e;
     if (use_ab && (e = cudaMemsetAsync(c->d_gab, 0, sizeof(double) * c->n_elem, s)) != cudaSuccess) return e;
     if (c->L.n > 0) {
-        k_grad_finalize<<<(unsigned)((c->L.n + 255) / 256), 256, 0, s>>>(
-            c->L.n, c->nl_caller, c->d_gacc, c->L.orig, c->L.sp, c->d_eos, use_ab, four ? 1 : 0, c->d_gline, c->d_gab);
+        const size_t smem = use_ab == 1 ? sizeof(double) * (size_t)c->n_elem : 0;
+        k_grad_finalize<<<(unsigned)((c->L.n + 255) / 256), 256, smem, s>>>(
+            c->L.n, c->nl_caller, c->d_gacc, c->L.orig, c->L.sp, c->d_eos, use_ab, (int)c->n_elem, four ? 1 : 0,
+            c->d_gline, c->d_gab);
         c->launches++;
     }
     const int64_t n = c->nl_caller;
