@@ -364,6 +364,7 @@ __device__ __forceinline__ float f2_hi(f2_t v) {
 // tile the line's window reaches.  The only per-line device array of the far kernels is
 // the 16-byte line record of each depth group (k_far_info).
 constexpr int kNQF = 2, kNQB = 3;
+constexpr int kBwdBatch = 16;   // lines per transposed partial-sum batch of the far-wing backward (2 lanes per line)
 constexpr float kUScale = 262144.0f;              // 2^18: scaled offset u 2^18
 constexpr float kKUnscale = 1.4551915228366852e-11f;   // 2^-36
 
@@ -1159,9 +1160,10 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
                 m_red3 = __ballot_sync(0xffffffffu, (f & 8) != 0);
                 m_skip = __ballot_sync(0xffffffffu, (f & 4) != 0);
             }
-            if (b < 31 && li + 1 < nl && ((m_red >> b) & 3u) == 3u && ((m_skip >> b) & 3u) == 0u) {
-                // two consecutive two-term lines: independent offset and reciprocal chains,
-                // formed together
+            if ((b & (kBwdBatch - 1)) != kBwdBatch - 1 && li + 1 < nl && ((m_red >> b) & 3u) == 3u &&
+                ((m_skip >> b) & 3u) == 0u) {
+                // two consecutive two-term lines of one batch: independent offset and
+                // reciprocal chains, formed together
                 f2_t spa[J], sqa[J], spb[J], sqb[J];
                 far_reduced_s<J>(g, s_line[li], (m_fast >> b) & 1u, lamf, lam_thr, spa, sqa);
                 far_reduced_s<J>(g, s_line[li + 1], (m_fast >> (b + 1)) & 1u, lamf, lam_thr, spb, sqb);
@@ -1169,8 +1171,9 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
                 f2_t S1a = 0ull, S2a = 0ull, S1b = 0ull, S2b = 0ull;
                 far_bwd_two_term<J, DP>(pa, spa, sqa, gv, S1a, S2a);
                 far_bwd_two_term<J, DP>(pa + DP * NQ, spb, sqb, gv, S1b, S2b);
-                s_part[b * 32 + (lane ^ b)] = make_float2(f2_lo(S1a) + f2_hi(S1a), f2_lo(S2a) + f2_hi(S2a));
-                s_part[(b + 1) * 32 + (lane ^ (b + 1))] = make_float2(f2_lo(S1b) + f2_hi(S1b), f2_lo(S2b) + f2_hi(S2b));
+                const int r = b & (kBwdBatch - 1);
+                s_part[r * 32 + (lane ^ r)] = make_float2(f2_lo(S1a) + f2_hi(S1a), f2_lo(S2a) + f2_hi(S2a));
+                s_part[(r + 1) * 32 + (lane ^ (r + 1))] = make_float2(f2_lo(S1b) + f2_hi(S1b), f2_lo(S2b) + f2_hi(S2b));
                 li += 2;
             } else {
                 const LineInfo info = s_line[li];
@@ -1215,25 +1218,30 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
                         far_bwd_line<J, DP, true>(par, u2, gv, inwin, kp, S1, S2);
                     }
                 }
-                s_part[b * 32 + (lane ^ b)] = make_float2(f2_lo(S1) + f2_hi(S1), f2_lo(S2) + f2_hi(S2));
+                const int r = b & (kBwdBatch - 1);
+                s_part[r * 32 + (lane ^ r)] = make_float2(f2_lo(S1) + f2_hi(S1), f2_lo(S2) + f2_hi(S2));
                 ++li;
             }
-            if ((li & 31) == 0 || li >= nl) {
-                // end of a batch of 32 lines: lane k adds line k's partial sums over the warp's
-                // lanes in lane order and leaves the warp's total for the CTA reduction
+            if ((li & (kBwdBatch - 1)) == 0 || li >= nl) {
+                // end of a batch of kBwdBatch lines: lanes 2r and 2r + 1 add the two halves of
+                // line r's partial sums over the warp's lanes (row r holds lane j's at column
+                // j ^ r), combine them and leave the warp's total for the CTA reduction
                 __syncwarp();
-                const int base = (li - 1) & ~31;
-                if (base + lane < nl) {
-                    const float2 *row = s_part + lane * 32;
-                    float a1 = 0.0f, a2 = 0.0f;
+                const int base = (li - 1) & ~(kBwdBatch - 1);
+                const int r = lane >> 1, h = lane & 1;
+                float a1 = 0.0f, a2 = 0.0f;
+                if (base + r < nl) {
+                    const float2 *row = s_part + r * 32;
 #pragma unroll 8
-                    for (int k = 0; k < 32; ++k) {
-                        const float2 r = row[k ^ lane];
-                        a1 += r.x;
-                        a2 += r.y;
+                    for (int t = 0; t < 16; ++t) {
+                        const float2 v = row[(16 * h + t) ^ r];
+                        a1 += v.x;
+                        a2 += v.y;
                     }
-                    s_red[(base + lane) * GW + warp] = make_float2(a1, a2);
                 }
+                a1 += __shfl_xor_sync(0xffffffffu, a1, 1);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, 1);
+                if (h == 0 && base + r < nl) s_red[(base + r) * GW + warp] = make_float2(a1, a2);
                 __syncwarp();
             }
         }
@@ -1261,7 +1269,7 @@ __global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int 
     float4 *mine = smem4 + (size_t)warp * wq;
     const WarpStage ws{mine, mine + DS, reinterpret_cast<LineInfo *>(mine + DS + (size_t)LC * (DS / 2) * kNQB)};
     float2 *s_red2 = reinterpret_cast<float2 *>(smem4 + (size_t)GW * wq);
-    float2 *s_part = s_red2 + (size_t)2 * LC * GW + (size_t)warp * 32 * 32;
+    float2 *s_part = s_red2 + (size_t)2 * LC * GW + (size_t)warp * kBwdBatch * 32;
     unsigned cc = 0;
     for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi, int) {
         return far_bwd_item<J, DS>(v, tile, group, lo, hi, GW, LC, ws, s_part, s_red2, cc);
@@ -1698,7 +1706,7 @@ static size_t far_fwd_smem(const Tiling &t) {
 }
 static size_t far_bwd_smem(const Tiling &t) {
     return (size_t)t.GW * warp_stage_quads(t.LCB, t.DS, kNQB) * sizeof(float4) +
-           (size_t)2 * t.LCB * t.GW * sizeof(float2) + (size_t)t.GW * 32 * 32 * sizeof(float2);
+           (size_t)2 * t.LCB * t.GW * sizeof(float2) + (size_t)t.GW * kBwdBatch * 32 * sizeof(float2);
 }
 constexpr size_t kFarSmemMax = 200 * 1024;   // the opt-in size the far-wing kernels are given
 
