@@ -588,10 +588,16 @@ __device__ __forceinline__ void far_kpairs(const LineArgs &g, int sp, int dfirst
     }
 }
 
-// Compensated-sum slots of depth dd of thread tid: the (hi, lo) pairs of its J points,
-// hi at [0, 4) and lo at [4, 8) (the J points of a thread are contiguous: one vector
-// access each).  They live in shared memory and are touched once per line chunk.
-__device__ __forceinline__ int comp_slot(int dd, int tid, int nthr) { return (dd * nthr + tid) << 3; }
+// Compensated-sum slots of depth dd of thread tid: the (hi, lo) quads of its J points, hi
+// at quad 2 dd nthr + tid and lo at quad (2 dd + 1) nthr + tid, so that the threads of a
+// warp touch consecutive quads (16-byte accesses without bank conflicts).  They live in
+// shared memory and are touched once per line chunk.
+__device__ __forceinline__ float4 *comp_hi(float *s_comp, int dd, int tid, int nthr) {
+    return reinterpret_cast<float4 *>(s_comp) + (size_t)(2 * dd) * nthr + tid;
+}
+__device__ __forceinline__ float4 *comp_lo(float *s_comp, int dd, int tid, int nthr) {
+    return reinterpret_cast<float4 *>(s_comp) + (size_t)(2 * dd + 1) * nthr + tid;
+}
 
 // Higher far-wing coefficients from a^2 and B1 (as depth_params forms them):
 // B3 = (3.75 - 2a^2) B1, B4 = -15 a^2 B1, B5 = 12 a^4 B1.
@@ -669,9 +675,8 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
         for (int j = 0; j < J; ++j) acc[dp][j] = 0ull;
 #pragma unroll
     for (int dd = 0; dd < DS; ++dd) {
-        float4 *cs = reinterpret_cast<float4 *>(s_comp + comp_slot(dd, tid, nthr));
-        cs[0] = make_float4(0.f, 0.f, 0.f, 0.f);
-        cs[1] = make_float4(0.f, 0.f, 0.f, 0.f);
+        *comp_hi(s_comp, dd, tid, nthr) = make_float4(0.f, 0.f, 0.f, 0.f);
+        *comp_lo(s_comp, dd, tid, nthr) = make_float4(0.f, 0.f, 0.f, 0.f);
     }
 
     warp_stage_depths<DS>(g, ws, d0 + warp * DS, lane);
@@ -848,8 +853,8 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
 #pragma unroll
             for (int h2 = 0; h2 < 2; ++h2) {
                 const int dd = 2 * dp + h2;
-                float4 *cs = reinterpret_cast<float4 *>(s_comp + comp_slot(dd, tid, nthr));
-                const float4 hsum = cs[0], lsum = cs[1];
+                float4 *ch = comp_hi(s_comp, dd, tid, nthr), *cl = comp_lo(s_comp, dd, tid, nthr);
+                const float4 hsum = *ch, lsum = *cl;
                 float hj[4] = {hsum.x, hsum.y, hsum.z, hsum.w};
                 float lj[4] = {lsum.x, lsum.y, lsum.z, lsum.w};
 #pragma unroll
@@ -861,8 +866,8 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                     hj[j] = s;
                     lj[j] += e;
                 }
-                cs[0] = make_float4(hj[0], hj[1], hj[2], hj[3]);
-                cs[1] = make_float4(lj[0], lj[1], lj[2], lj[3]);
+                *ch = make_float4(hj[0], hj[1], hj[2], hj[3]);
+                *cl = make_float4(lj[0], lj[1], lj[2], lj[3]);
             }
         }
     }
@@ -876,9 +881,8 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
         float4 *mine = g.fpart + (size_t)(ext.x + ext.w) * slot;
 #pragma unroll
         for (int dd = 0; dd < DS; ++dd) {
-            const float4 *cs = reinterpret_cast<const float4 *>(s_comp + comp_slot(dd, tid, nthr));
-            mine[((size_t)dd * nthr + tid) * 2] = cs[0];
-            mine[((size_t)dd * nthr + tid) * 2 + 1] = cs[1];
+            mine[((size_t)dd * nthr + tid) * 2] = *comp_hi(s_comp, dd, tid, nthr);
+            mine[((size_t)dd * nthr + tid) * 2 + 1] = *comp_lo(s_comp, dd, tid, nthr);
         }
         __threadfence();
         __syncthreads();
@@ -903,9 +907,8 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                     lj[j] += lq[j] + e;
                 }
             }
-            float4 *cs = reinterpret_cast<float4 *>(s_comp + comp_slot(dd, tid, nthr));
-            cs[0] = make_float4(hj[0], hj[1], hj[2], hj[3]);
-            cs[1] = make_float4(lj[0], lj[1], lj[2], lj[3]);
+            *comp_hi(s_comp, dd, tid, nthr) = make_float4(hj[0], hj[1], hj[2], hj[3]);
+            *comp_lo(s_comp, dd, tid, nthr) = make_float4(lj[0], lj[1], lj[2], lj[3]);
         }
     }
 
@@ -915,8 +918,7 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
         int d = d0 + warp * DS + dd;
         if (d >= g.nd) continue;
         float c2T = __ldg(g.c2T + d);
-        const float4 *cs = reinterpret_cast<const float4 *>(s_comp + comp_slot(dd, tid, nthr));
-        const float4 hsum = cs[0], lsum = cs[1];
+        const float4 hsum = *comp_hi(s_comp, dd, tid, nthr), lsum = *comp_lo(s_comp, dd, tid, nthr);
         const float hj[4] = {hsum.x, hsum.y, hsum.z, hsum.w};
         const float lj[4] = {lsum.x, lsum.y, lsum.z, lsum.w};
         const float *nrow = g.knear + (int64_t)d * g.ld + lam_thr;
