@@ -436,11 +436,11 @@ def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None, pipe_peaks=No
         nd = prob.atmos.n_depth
         # FP64 operations per wavelength (both branches) of the steps with a fixed count:
         # E3 at every layer pair (one Horner chain of TAYLOR_STEPS FMAs), E2 and E3 at the
-        # slab ends (two chains, 2 nd of them), E2-E4 of the flux (three chains per layer)
+        # slab ends (two chains, 2 nd of them), E3 and E4 of the flux (two chains per layer)
         # and the Lambda rows (three operations per element).  The refinement rounds,
         # whose number varies, are not counted.
         steps = FMA_PER_EN // 3
-        ops_col = 2 * (nd * (nd + 1) // 2 * steps + 2 * nd * 2 * steps + nd * 3 * steps + 3 * nd * nd)
+        ops_col = 2 * (nd * (nd + 1) // 2 * steps + 2 * nd * 2 * steps + nd * 2 * steps + 3 * nd * nd)
         t_sc = kt_sc["flux"][0] * 1e-3 / max(args.broad_steps, 1)
         scat_fma = ops_col * prob.grid.n_lambda / t_sc
         scat = {"workload": "the same spectrum with sigma_c = kappa_c (lambda/400 nm)^-4 / (1 + tau_d): source "
@@ -1090,15 +1090,17 @@ def run_config1(args, dev, pipe_peaks, clk_max):
            "roofline_frac": roof["frac"], "roofline_kernel": roof["kernel"],
            "kernel_ms_per_step": {k: v[0] / args.config1_steps for k, v in kt.items() if v[1] > 0},
            "roofline": roof}
-    # transfer stage against the measured FP64 FMA peak: E_n evaluations, two per
-    # (lambda, depth) in the flux (both branches), one in its adjoint, each a Taylor step
-    # of FMA_PER_EN FMAs (tau, Planck and the interval weights are not counted)
+    # transfer stage against the measured FP64 FMA peak: the Taylor-step FMAs of the E_n,
+    # E3 and E4 (two chains) for both branches in the flux, E2 to E4 (three chains) in its
+    # adjoint (tau and the interval weights are not counted)
     if pipe_peaks.get("fp64") and kt["flux"][1] > 0:
         cells = prob.grid.n_lambda * prob.atmos.n_depth
-        rt = {"bound": "fp64", "unit": "GFMA/s", "peak": pipe_peaks["fp64"] * 1e-9, "fma_per_En": FMA_PER_EN}
-        for name, per_cell in (("flux", 2), ("rt_adjoint", 1)):
+        steps = FMA_PER_EN // 3
+        rt = {"bound": "fp64", "unit": "GFMA/s", "peak": pipe_peaks["fp64"] * 1e-9,
+              "fma_per_cell": {"flux": 2 * 2 * steps, "rt_adjoint": 3 * steps}}
+        for name, fma_cell in (("flux", 2 * 2 * steps), ("rt_adjoint", 3 * steps)):
             t = kt[name][0] * 1e-3 / max(kt[name][1], 1)
-            ach = per_cell * cells * FMA_PER_EN / t
+            ach = cells * fma_cell / t
             rt[name] = {"ms_per_launch": t * 1e3, "achieved": ach * 1e-9, "frac": ach / pipe_peaks["fp64"]}
         out["rt_roofline"] = rt
     if not args.no_fp64:

@@ -204,6 +204,27 @@ __device__ __forceinline__ void expn234(double x, double &E2, double &E3, double
     E2 = (ex - 2.0 * E3) / x;
 }
 
+// E3 and E4 alone (the flux needs no E2): the value and first-derivative chains of the same
+// E4 Taylor table, with expn234's branches; identical E3, E4 to expn234's.
+__device__ __forceinline__ void expn34(double x, double &E3, double &E4) {
+    const long long xb = __double_as_longlong(x);
+    if (xb <= 0 || xb >= kBits40 || xb < kBits2m40) {
+        double e2;
+        expn234(x, e2, E3, E4);
+        return;
+    }
+    double t;
+    const double *c = g_expn_tab + expn_node(x, t) * kExpnK;
+    double p = __ldg(c + kExpnK - 1), d1 = 0.0;
+#pragma unroll
+    for (int k = kExpnK - 2; k >= 0; --k) {
+        d1 = fma(d1, t, p);
+        p = fma(p, t, __ldg(c + k));
+    }
+    E4 = p;
+    E3 = -d1;
+}
+
 // Planck function per nanometre
 __device__ __forceinline__ double planck_nm(double lamcm, double T) {
     double l2 = lamcm * lamcm;
@@ -282,9 +303,9 @@ __global__ void k_flux(FluxArgs g) {
             tau = tau_p + 0.5 * (chi_p + chi) * (md - m_p);
             tauc = tauc_p + 0.5 * (chic_p + kc) * (md - m_p);
         }
-        double e2, e3, e4, e2c, e3c, e4c;
-        expn234(tau, e2, e3, e4);
-        expn234(tauc, e2c, e3c, e4c);
+        double e3, e4, e3c, e4c;
+        expn34(tau, e3, e4);
+        expn34(tauc, e3c, e4c);
         if (d == 0) {
             tau0 = tau; tauc0 = tauc; S0 = S;
             e3_0 = e3; e4_0 = e4; e3c_0 = e3c; e4c_0 = e4c;
@@ -936,10 +957,7 @@ __global__ void __launch_bounds__(kScatThreadsFwd, RT <= 5 ? 3 : 1) k_flux_scatt
         scat_inverse<RT, RT, 16>(c);
         scat_refine<false>(c, c.a, c.S, &s_done, g.status);
         // emergent flux of the solved source, the closed form of the LTE kernel
-        for (int d = tid; d < nd; d += blockDim.x) {
-            double e2;
-            expn234(c.tau[d], e2, c.e3[d], c.e4[d]);
-        }
+        for (int d = tid; d < nd; d += blockDim.x) expn34(c.tau[d], c.e3[d], c.e4[d]);
         __syncthreads();
         // interval d (layers d, d + 1; for d = 0 also the top one [0, tau_0]) by thread d,
         // summed by warp 0 in a fixed order
