@@ -477,10 +477,15 @@ struct WarpStage {
     float4 *dc;          // [DS]
     float4 *par;         // [LC][DP * NQ]
     LineInfo *info;      // [LC]
+    int *idx;            // [LC] line of each staged slot (forward: gathered by warp_gather)
 };
 
 __host__ __device__ constexpr size_t warp_stage_quads(int LC, int DS, int NQ) {
-    return (size_t)DS + (size_t)LC * (DS / 2) * NQ + (size_t)LC;
+    return (size_t)DS + (size_t)LC * (DS / 2) * NQ + (size_t)LC + ((size_t)LC + 3) / 4;
+}
+__device__ __forceinline__ WarpStage make_stage(float4 *mine, int LC, int DS, int NQ) {
+    LineInfo *info = reinterpret_cast<LineInfo *>(mine + DS + (size_t)LC * (DS / 2) * NQ);
+    return WarpStage{mine, mine + DS, info, reinterpret_cast<int *>(info + LC)};
 }
 
 template <int DS>
@@ -495,13 +500,35 @@ __device__ __forceinline__ void warp_stage_depths(const LineArgs &g, const WarpS
     __syncwarp();
 }
 
+// The forward's next chunk: up to LC lines from cur on that slab w has to sweep (all lines
+// without the centre test; with it, those with a layer of the slab kept), their indices in
+// ws.idx in line order.  Returns the count and leaves cur after the last line looked at.
+__device__ __forceinline__ int warp_gather(const WarpStage &ws, const LineInfo *ginfo, int &cur, int hi, int LC,
+                                           int w, int lane) {
+    int count = 0;
+    __syncwarp();
+    while (count < LC && cur < hi) {
+        const int l = cur + lane;
+        const bool need = l < hi && !((ginfo[l].amask >> (8 + w)) & 1);
+        const unsigned m = __ballot_sync(0xffffffffu, need);
+        const int n = __popc(m);
+        const int take = min(n, LC - count);
+        const int slot = count + __popc(m & ((1u << lane) - 1u));
+        if (need && slot < LC) ws.idx[slot] = l;
+        cur += take < n ? __fns(m, 0, take) + 1 : 32;   // after the last line taken
+        count += take;
+    }
+    __syncwarp();
+    return count;
+}
+
 template <int NQ, int DS>
 __device__ __forceinline__ void warp_fill(const LineArgs &g, const WarpStage &ws, const LineInfo *ginfo,
-                                          int64_t first, int nl, int dfirst, int lane) {
+                                          int64_t first, int nl, int dfirst, int lane, bool listed = false) {
     constexpr int DP = DS / 2;
     __syncwarp();
     for (int li = lane; li < nl; li += 32) {
-        const int64_t l = first + li;
+        const int64_t l = listed ? (int64_t)ws.idx[li] : first + li;
         ws.info[li] = ginfo[l];
         const LineScalars L = load_line(g, l);
         float4 *dst = ws.par + (size_t)li * DP * NQ;
@@ -647,7 +674,7 @@ __device__ __forceinline__ void far_reduced_s(const LineArgs &g, const LineInfo 
 // evaluated here with the far polynomial; the near-core cells are summed by
 // k_line_near_fwd into knear, which this kernel adds before applying stim.
 // Returns false if a chunk never arrived (the kernel stops).
-template <int J, int DS>
+template <int J, int DS, bool GATHER>
 __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, const int group, const int lo,
                                              const int hi, const int GW, const int LC, const WarpStage &ws,
                                              float *s_comp, const int4 ext) {
@@ -680,10 +707,10 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
     }
 
     warp_stage_depths<DS>(g, ws, d0 + warp * DS, lane);
-    const int nch = (hi - lo + LC - 1) / LC;
-    for (int c = 0; c < nch; ++c) {
-        const int nl = min(LC, hi - (lo + c * LC));
-        warp_fill<NQ, DS>(g, ws, ginfo, lo + c * LC, nl, d0 + warp * DS, lane);
+    // chunks of LC lines; with GATHER (a centre test is set) of the lines this warp's slab
+    // sweeps, so that lines whose slab the test rejects entirely are neither staged nor visited
+    // one chunk of nl staged lines: the cells, then the fold into the compensated sums
+    auto chunk = [&](const int nl) {
         const ulonglong2 *s_par = reinterpret_cast<const ulonglong2 *>(ws.par);
         const LineInfo *s_line = ws.info;
         unsigned m_fast = 0u, m_red = 0u, m_red3 = 0u, m_skip = 0u;   // this warp's flags of 32 lines, one per lane
@@ -870,6 +897,21 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                 *cl = make_float4(lj[0], lj[1], lj[2], lj[3]);
             }
         }
+    };
+    if (GATHER) {
+        for (int cur = lo; cur < hi;) {
+            const int nl = warp_gather(ws, ginfo, cur, hi, LC, warp, lane);
+            if (nl == 0) break;
+            warp_fill<NQ, DS>(g, ws, ginfo, 0, nl, d0 + warp * DS, lane, true);
+            chunk(nl);
+        }
+    } else {
+        const int nch = (hi - lo + LC - 1) / LC;
+        for (int c = 0; c < nch; ++c) {
+            const int nl = min(LC, hi - (lo + c * LC));
+            warp_fill<NQ, DS>(g, ws, ginfo, lo + c * LC, nl, d0 + warp * DS, lane);
+            chunk(nl);
+        }
     }
 
     if (ext.y > 1) {
@@ -945,19 +987,19 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
 // Shared memory of the far-wing kernels: each warp's stage (warp_stage_quads), then
 // (forward) the compensated sums of every thread [DS][threads][8] or (backward) the
 // per-line sums of the warps, double-buffered by chunk [2][LC][GW], and each warp's
-// per-lane partial sums of a batch of 32 lines [32][32] (lane l of line k at column
-// l ^ k, so that both the row writes and the column reads avoid bank conflicts).
-template <int J, int DS, int MINB>
+// per-lane partial sums of a batch of kBwdBatch lines [kBwdBatch][32] (lane l of line k at
+// column l ^ k, so that both the row writes and the column reads avoid bank conflicts).
+template <int J, int DS, int MINB, bool GATHER>
 __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int LC) {
     extern __shared__ float4 smem4[];
     const int warp = threadIdx.x >> 5;
     const size_t wq = warp_stage_quads(LC, DS, kNQF);
     float4 *mine = smem4 + (size_t)warp * wq;
-    const WarpStage ws{mine, mine + DS, reinterpret_cast<LineInfo *>(mine + DS + (size_t)LC * (DS / 2) * kNQF)};
+    const WarpStage ws = make_stage(mine, LC, DS, kNQF);
     float *s_comp = reinterpret_cast<float *>(smem4 + (size_t)GW * wq);
     for_each_item(g, [&](const LineArgs &v, int tile, int group, int lo, int hi, int it) {
-        return far_fwd_item<J, DS>(v, tile, group, lo, hi, GW, LC, ws, s_comp,
-                                   g.fext ? g.fext[it] : make_int4(-1, 1, -1, 0));
+        return far_fwd_item<J, DS, GATHER>(v, tile, group, lo, hi, GW, LC, ws, s_comp,
+                                           g.fext ? g.fext[it] : make_int4(-1, 1, -1, 0));
     });
 }
 
@@ -1269,7 +1311,7 @@ __global__ void __launch_bounds__(128, MINB) k_line_bwd(LineArgs g, int GW, int 
     const int warp = threadIdx.x >> 5;
     const size_t wq = warp_stage_quads(LC, DS, kNQB);
     float4 *mine = smem4 + (size_t)warp * wq;
-    const WarpStage ws{mine, mine + DS, reinterpret_cast<LineInfo *>(mine + DS + (size_t)LC * (DS / 2) * kNQB)};
+    const WarpStage ws = make_stage(mine, LC, DS, kNQB);
     float2 *s_red2 = reinterpret_cast<float2 *>(smem4 + (size_t)GW * wq);
     float2 *s_part = s_red2 + (size_t)2 * LC * GW + (size_t)warp * kBwdBatch * 32;
     unsigned cc = 0;
@@ -1737,10 +1779,13 @@ static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
     const Tiling &t = c->tiling;
     LineArgs g = make_args(c);
     const size_t smem = far_fwd_smem(t);
-    static std::atomic<bool> attr_set[kMaxDevices];
-    if (!attr_set[c->device].load(std::memory_order_acquire)) {
-        cudaFuncSetAttribute(k_line_fwd<J, DS, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFarSmemMax);
-        attr_set[c->device].store(true, std::memory_order_release);
+    // with a centre test the kernel stages only the lines each warp's slab sweeps (GATHER)
+    const bool gather = c->d_keep != nullptr;
+    auto kern = gather ? k_line_fwd<J, DS, MINB, true> : k_line_fwd<J, DS, MINB, false>;
+    static std::atomic<bool> attr_set[kMaxDevices][2];
+    if (!attr_set[c->device][gather].load(std::memory_order_acquire)) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFarSmemMax);
+        attr_set[c->device][gather].store(true, std::memory_order_release);
     }
     cudaError_t e = cudaMemsetAsync(c->d_ctr, 0, 2 * sizeof(int), s);
     if (e != cudaSuccess) return e;
@@ -1759,8 +1804,8 @@ static cudaError_t launch_fwd_t(pz_ctx *c, cudaStream_t s) {
         e = cudaMemsetAsync(c->d_fcnt, 0, sizeof(int) * c->n_fsplit, s);
         if (e != cudaSuccess) return e;
     }
-    int grid = persistent_grid(c, k_line_fwd<J, DS, MINB>, 32 * t.GW, smem, g.n_items);
-    k_line_fwd<J, DS, MINB><<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LC);
+    int grid = persistent_grid(c, kern, 32 * t.GW, smem, g.n_items);
+    kern<<<grid, 32 * t.GW, smem, s>>>(g, t.GW, t.LC);
     c->launches++;
     return cudaGetLastError();
 }
