@@ -647,23 +647,31 @@ __device__ __forceinline__ void far_c3456(f2_t a2, f2_t C1, f2_t &C3, f2_t &C4, 
 // u_j = u_0 r^-j + (r^-j - 1) scaled by 2^18; points outside the line's window get
 // s = 0 unless the window covers the tile (full).
 template <int J>
+__device__ __forceinline__ void far_scaled_u2(const LineArgs &g, const LineInfo &info, float lamf, float (&U)[J]) {
+    // scalar chain: the offsets depend on the line and the point only, not on the depth
+    const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr) * kUScale;
+    U[0] = u0 * u0;
+#pragma unroll
+    for (int j = 1; j < J; ++j) {
+        const float u = fmaf(u0, g.rj[j], g.rm1j[j] * kUScale);
+        U[j] = u * u;
+    }
+}
+
+template <int J>
 __device__ __forceinline__ void far_reduced_s(const LineArgs &g, const LineInfo &info, bool full, float lamf,
                                               int lam_thr, f2_t (&sp)[J], f2_t (&sq)[J]) {
-    f2_t u2[J];
-    u2[0] = f2_splat(offset_u((info.ilf - lamf) + info.frac, g.lnr) * kUScale);
-#pragma unroll
-    for (int j = 1; j < J; ++j) u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j] * kUScale));
-#pragma unroll
-    for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
+    float U[J];
+    far_scaled_u2<J>(g, info, lamf, U);
     if (full) {
 #pragma unroll
-        for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(u2[j])));
+        for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(U[j]));
     } else {
         const int il = (int)info.ilf;
 #pragma unroll
         for (int j = 0; j < J; ++j) {
             const int di = lam_thr + j - il;
-            sp[j] = f2_splat(di >= -g.W && di <= g.W ? rcp_approx(f2_lo(u2[j])) : 0.0f);
+            sp[j] = f2_splat(di >= -g.W && di <= g.W ? rcp_approx(U[j]) : 0.0f);
         }
     }
 #pragma unroll
@@ -747,35 +755,23 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
             const int fl = (int)((m_fast >> b) & 1u) | (int)(((m_red >> b) & 1u) << 1) | (int)(((m_red3 >> b) & 1u) << 2);
             if ((m_skip >> b) & 1u) continue;        // every layer rejected by the centre test
             const ulonglong2 *par = s_par + (size_t)li * DP * NQ;
-            f2_t u2[J];
-            if (fl != 0) {
-                // the whole tile is in the line's far wing: offsets from the first point's,
-                // u_j = u_0 r^-j + (r^-j - 1), scaled by 2^18, and their squares U = 2^36 u^2
-                const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr) * kUScale;
-                u2[0] = f2_splat(u0);
-#pragma unroll
-                for (int j = 1; j < J; ++j)
-                    u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j] * kUScale));
-#pragma unroll
-                for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
-            } else {
-                // cells are classified near / far exactly as the near-core kernel does
-#pragma unroll
-                for (int j = 0; j < J; ++j) u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
-            }
+            // the whole tile in the line's far wing (fl != 0): offsets from the first point's,
+            // u_j = u_0 r^-j + (r^-j - 1), scaled by 2^18, and their squares U = 2^36 u^2
+            float U[J];
+            if (fl != 0) far_scaled_u2<J>(g, info, lamf, U);
             if (fl & 6) {
                 // reduced forms (B1 K) s + (B2' K^2) s^2 [+ (B3' K^3) s^3] with s = 1/U; points
                 // outside the window (lines whose window edge crosses the tile) get s = 0
                 f2_t sp[J], sq[J];
                 if (fl & 1) {
 #pragma unroll
-                    for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(u2[j])));
+                    for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(U[j]));
                 } else {
                     const int il = (int)info.ilf;
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const int di = lam_thr + j - il;
-                        sp[j] = f2_splat(di >= -g.W && di <= g.W ? rcp_approx(f2_lo(u2[j])) : 0.0f);
+                        sp[j] = f2_splat(di >= -g.W && di <= g.W ? rcp_approx(U[j]) : 0.0f);
                     }
                 }
 #pragma unroll
@@ -806,6 +802,9 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                     }
                 }
             } else if (fl & 1) {
+                f2_t u2[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) u2[j] = f2_splat(U[j]);
 #pragma unroll
                 for (int dp = 0; dp < DP; ++dp) {
                     // q0 = (K, a^2), q1 = (B1 K, B2' K^2): the polynomial in t with every
@@ -828,7 +827,11 @@ __device__ __forceinline__ bool far_fwd_item(const LineArgs &g, const int tile, 
                     }
                 }
             } else {
-                // line near the tile or partly outside its window: far cells inside the window only
+                // line near the tile or partly outside its window: far cells inside the window
+                // only, classified near / far exactly as the near-core kernel does
+                f2_t u2[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
                 const int il = (int)info.ilf;
                 bool inwin[J];
 #pragma unroll
@@ -1007,7 +1010,7 @@ __global__ void __launch_bounds__(128, MINB) k_line_fwd(LineArgs g, int GW, int 
 // after their t^2 terms (THREE: t^3).  par: the warp's depth pairs, (K, a^2) (B1 K, B2' K^2)
 // (C1 K, C2' K^2); usq: the scaled squared offsets U = 2^36 u^2 of the thread's points.
 template <int J, int DP, bool THREE>
-__device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, const f2_t (&usq)[J],
+__device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, const float (&usq)[J],
                                                      const f2_t (&gv)[DP][J], bool full, int di0, int W, f2_t &S1,
                                                      f2_t &S2) {
     // reduced forms with s = 1/U: per depth pair X1 = sum_j G s_j and X2 = sum_j G s_j^2,
@@ -1017,11 +1020,11 @@ __device__ __forceinline__ void far_bwd_line_reduced(const ulonglong2 *par, cons
     f2_t sp[J], sq[J];
     if (full) {
 #pragma unroll
-        for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(f2_lo(usq[j])));
+        for (int j = 0; j < J; ++j) sp[j] = f2_splat(rcp_approx(usq[j]));
     } else {
 #pragma unroll
         for (int j = 0; j < J; ++j)
-            sp[j] = f2_splat(di0 + j >= -W && di0 + j <= W ? rcp_approx(f2_lo(usq[j])) : 0.0f);
+            sp[j] = f2_splat(di0 + j >= -W && di0 + j <= W ? rcp_approx(usq[j]) : 0.0f);
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) sq[j] = f2_mul(sp[j], sp[j]);
@@ -1226,30 +1229,25 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
                 f2_t S1 = 0ull, S2 = 0ull;
                 // (a slab whose every layer the centre test rejects keeps zero sums)
                 if (!((m_skip >> b) & 1u)) {
-                    f2_t u2[J];
-                    if (fl != 0) {
-                        const float u0 = offset_u((info.ilf - lamf) + info.frac, g.lnr) * kUScale;
-                        u2[0] = f2_splat(u0);
-#pragma unroll
-                        for (int j = 1; j < J; ++j)
-                            u2[j] = f2_fma(u2[0], f2_splat(g.rj[j]), f2_splat(g.rm1j[j] * kUScale));
-#pragma unroll
-                        for (int j = 0; j < J; ++j) u2[j] = f2_mul(u2[j], u2[j]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < J; ++j)
-                            u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
-                    }
+                    float U[J];
+                    if (fl != 0) far_scaled_u2<J>(g, info, lamf, U);
                     if (fl & 2) {
-                        far_bwd_line_reduced<J, DP, false>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W,
+                        far_bwd_line_reduced<J, DP, false>(par, U, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W,
                                                            S1, S2);
                     } else if (fl & 4) {
-                        far_bwd_line_reduced<J, DP, true>(par, u2, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W,
+                        far_bwd_line_reduced<J, DP, true>(par, U, gv, (fl & 1) != 0, lam_thr - (int)info.ilf, g.W,
                                                           S1, S2);
                     } else if (fl & 1) {
+                        f2_t u2[J];
+#pragma unroll
+                        for (int j = 0; j < J; ++j) u2[j] = f2_splat(U[j]);
                         far_bwd_line<J, DP, false>(par, u2, gv, nullptr, nullptr, S1, S2);
                     } else {
                         // line near the tile or partly outside its window: far cells inside the window only
+                        f2_t u2[J];
+#pragma unroll
+                        for (int j = 0; j < J; ++j)
+                            u2[j] = f2_splat(offset_u((info.ilf - (lamf + (float)j)) + info.frac, g.lnr));
                         bool inwin[J];
                         const int il = (int)info.ilf;
 #pragma unroll
@@ -1290,15 +1288,15 @@ __device__ __forceinline__ bool far_bwd_item(const LineArgs &g, const int tile, 
             }
         }
         __syncthreads();
-        for (int li = tid; li < nl; li += nthr) {
-            double a1 = 0.0, a2 = 0.0;
-            for (int w = 0; w < GW; ++w) {
-                float2 r = s_red[li * GW + w];
-                a1 += r.x;
-                a2 += r.y;
-            }
-            atomicAdd(g.gacc + c0 + li, a1);
-            atomicAdd(g.gacc + g.nl + c0 + li, a2);
+        // thread k adds sum k & 1 of line k >> 1 over the warps in FP32, in warp order, and
+        // converts once for the FP64 accumulator: FP64 arithmetic runs at a small fraction
+        // of the FP32 rate, and a chain of FP64 adds here would hold the CTA at the next barrier
+        for (int k = tid; k < 2 * nl; k += nthr) {
+            const int li = k >> 1;
+            const float *r = reinterpret_cast<const float *>(s_red + li * GW) + (k & 1);
+            float a = r[0];
+            for (int w = 1; w < GW; ++w) a += r[2 * w];
+            atomicAdd(g.gacc + (int64_t)(k & 1) * g.nl + c0 + li, (double)a);
         }
     }
     cc += nch;
