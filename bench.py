@@ -444,7 +444,7 @@ def run_broad(args, dev, barrier, max_over_ranks, ws, tiling=None, pipe_peaks=No
         t_sc = kt_sc["flux"][0] * 1e-3 / max(args.broad_steps, 1)
         scat_fma = ops_col * prob.grid.n_lambda / t_sc
         scat = {"workload": "the same spectrum with sigma_c = kappa_c (lambda/400 nm)^-4 / (1 + tau_d): source "
-                            "S = eps B + (1 - eps) J solved per wavelength (72 x 72 system: FP32 LU, FP64 refinement; both branches)",
+                            "S = eps B + (1 - eps) J solved per wavelength (72 x 72 system: FP32 Gauss-Jordan inverse, FP64 refinement; both branches)",
                 "s_per_spectrum_fwd": ms_sc * 1e-3,
                 "flux_ms": kt_sc["flux"][0] / max(args.broad_steps, 1),
                 "flux_ms_lte": kt["flux"][0] / max(args.broad_steps, 1),
