@@ -34,6 +34,26 @@ def _check(prob, oracle, corr, instrument_noise=1.0 / 200):
     return out
 
 
+@pytest.mark.parametrize("tiling", [(4, 6, 4, 32, 5), (4, 8, 4, 32, 3), (4, 8, 3, 32, 2), (4, 12, 2, 64, 1),
+                                    (2, 8, 4, 16, 5), (2, 6, 4, 16, 6), (4, 6, 1, 128, 3)])
+def test_tilings_agree_on_gradients(oracle, tiling):
+    """The reverse pass of each line-kernel tiling (lambda points per thread, layers per
+    warp, warps per CTA, lines per chunk, CTAs per SM) against the oracle's adjoint, on a
+    layer count that leaves the last slab of every tiling partly or wholly past the bottom
+    layer.  A slab, line or point that a tiling drops or counts twice is an O(1) error."""
+    prob = tiny_problem(n_lambda=1037, n_depth=17, n_lines=300, W=400, seed=3)
+    n = prob.grid.n_lambda
+    f0 = oracle.forward(prob)
+    rng = np.random.default_rng(17)
+    y = (f0["f"] + rng.normal(0, 1e-3, n)).astype(np.float32).astype(np.float64)
+    w = 1e4
+    _, ggf, gg6, _, _ = oracle.gradient(prob, y, np.full(n, w), fwd=f0)
+    got = run_gradient(prob, y.astype(np.float32), np.float32(w), pz.PZ_MIXED, tiling=tiling)
+    e1 = rel_metric(got["g_gf"], ggf).max()
+    e2 = rel_metric(got["g_g6"], gg6).max()
+    assert e1 < G_TOL and e2 < G_TOL, (tiling, e1, e2)
+
+
 def test_small_calibration_gradients(oracle):
     prob = I.small_config1(n_lambda_span_nm=3.0, seed=13)
     nl = prob.lines.n_lines

@@ -39,7 +39,8 @@ def test_config0_fp64_form(cfg0):
 
 
 @pytest.mark.parametrize("tiling", [(4, 8, 4, 32, 1), (2, 8, 4, 32, 2), (4, 6, 4, 16, 4), (2, 12, 3, 8, 1), (4, 12, 2, 64, 1),
-                                    (4, 6, 1, 32, 1), (4, 6, 2, 16, 6), (2, 6, 4, 16, 6), (2, 8, 2, 32, 5)])
+                                    (4, 6, 1, 32, 1), (4, 6, 2, 16, 6), (2, 6, 4, 16, 6), (2, 8, 2, 32, 5),
+                                    (4, 6, 4, 32, 5), (4, 8, 3, 32, 3)])
 def test_tilings_agree(oracle, tiling):
     prob = tiny_problem(n_lambda=1037, n_depth=17, n_lines=300, W=400, seed=3)
     prob.lines.log_gf[:] -= 3.0
