@@ -1,6 +1,11 @@
 """Multi-update line-list calibration (Sec. 6): L-BFGS over shared line corrections of
 one or more stars.
 
+A joint fit may spread its stars over ranks (one process per GPU, each rank a Synthesizer of
+its own stars on the same line list): every rank evaluates its stars at the same corrections,
+and one all-reduce per evaluation sums the loss and the shared gradient over the ranks, so
+that every rank takes the same L-BFGS steps.  That sum is the only exchange of the path.
+
 Every function and gradient evaluation is one captured graph launch: either
 ``pz_calib_step`` with zero learning rates (per-line Delta log gf and Delta log gamma_6),
 or ``pz_group_eval`` (the four corrections of Eq. 10 -- gf and the radiative, Stark and
@@ -19,21 +24,47 @@ import time
 import numpy as np
 
 
-def _minimise(set_and_eval, n_params, dev, n_updates, history, resume=None):
+def _sum_over_ranks(process_group):
+    """The exchange of a joint fit over ranks: the loss and the gradient of this rank's
+    stars, packed in one FP64 vector, summed over the group by one all-reduce.  Every rank
+    receives the same sums, so the line searches of all ranks take the same decisions and
+    issue the same sequence of collectives."""
+    import torch
+    import torch.distributed as dist
+
+    def reduce(loss, grad):
+        buf = torch.cat([torch.as_tensor(loss, dtype=torch.float64, device=grad.device).reshape(1),
+                         grad.to(torch.float64)])
+        dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=process_group)
+        return buf[0], buf[1:]
+    return reduce
+
+
+def _minimise(set_and_eval, n_params, dev, n_updates, history, resume=None, process_group=None):
     """L-BFGS on a float64 device vector of n_params; set_and_eval(x) -> (loss, grad).
-    resume: {"x", "optimizer"} of an earlier run (see save_state) to continue from."""
+    resume: {"x", "optimizer"} of an earlier run (see save_state) to continue from.
+    process_group: sum each evaluation over the ranks of this torch.distributed group
+    (None: this process alone); the starting point is taken from the group's first rank."""
     import torch
 
     x = torch.zeros(n_params, dtype=torch.float64, device=dev, requires_grad=True)
     if resume is not None:
         with torch.no_grad():
             x.copy_(torch.as_tensor(resume["x"], dtype=torch.float64, device=dev))
+    reduce = None
+    if process_group is not None:
+        import torch.distributed as dist
+        reduce = _sum_over_ranks(process_group)
+        with torch.no_grad():
+            dist.broadcast(x.detach(), src=dist.get_global_rank(process_group, 0), group=process_group)
     evals = [0]
     t_eval = [0.0]
 
     def objective():
         t = time.perf_counter()
         loss, grad = set_and_eval(x.detach())
+        if reduce is not None:
+            loss, grad = reduce(loss, grad)
         evals[0] += 1
         x.grad = grad.to(torch.float64)
         out = float(loss)                       # a copy: the buffer is rewritten by the next evaluation
@@ -62,7 +93,8 @@ def _minimise(set_and_eval, n_params, dev, n_updates, history, resume=None):
                         "optimizer": opt.state_dict()}
 
 
-def lbfgs(synth, y, w=None, n_updates=40, history=10, fit_gamma6=True, stream=None, resume=None):
+def lbfgs(synth, y, w=None, n_updates=40, history=10, fit_gamma6=True, stream=None, resume=None,
+          process_group=None):
     """Minimise L = sum_stars sum_p w (y - f)^2 over the shared per-line corrections
     Delta log gf (and Delta log gamma_6).
 
@@ -75,6 +107,10 @@ def lbfgs(synth, y, w=None, n_updates=40, history=10, fit_gamma6=True, stream=No
     "eval_seconds": the part of it spent from each evaluation's launch to its loss
     readback, "x" and "optimizer": the final parameter vector and the L-BFGS state, which
     save_state stores and resume= takes back to continue the fit}.
+    process_group: a torch.distributed group over whose ranks the stars of a joint fit
+    are spread (each rank's synth holds its own stars and the same line list); the loss
+    and the gradients then cover the stars of every rank, "loss_start" and "loss_final"
+    included, and every rank returns the same corrections.  None: synth's stars alone.
     """
     import torch
 
@@ -94,19 +130,21 @@ def lbfgs(synth, y, w=None, n_updates=40, history=10, fit_gamma6=True, stream=No
         synth.calib_step(y, w, 0.0, 0.0, 0.0, loss, g_gf, g_g6, None, stream)
         return loss[0], (torch.cat([g_gf, g_g6]) if fit_gamma6 else g_gf)
 
-    x, res = _minimise(set_and_eval, 2 * nl if fit_gamma6 else nl, dev, n_updates, history, resume)
+    x, res = _minimise(set_and_eval, 2 * nl if fit_gamma6 else nl, dev, n_updates, history, resume, process_group)
     res["dlog_gf"] = x[:nl].float().clone()
     res["dlog_gamma6"] = x[nl:].float().clone() if fit_gamma6 else torch.zeros_like(res["dlog_gf"])
     return res
 
 
-def lbfgs_groups(synth, y, w, group_of_line, n_groups, n_updates=40, history=10, stream=None, resume=None):
+def lbfgs_groups(synth, y, w, group_of_line, n_groups, n_updates=40, history=10, stream=None, resume=None,
+                 process_group=None):
     """Minimise the chi-square over the four corrections of Eq. 10 per linked group
     (Delta log gf, Delta log gamma_rad, Delta log gamma_4, Delta log gamma_6), each
     shared by the group's members (Sec. 6).  group_of_line: host int32 [n_lines] in
     [0, n_groups) or -1.  Each evaluation is one captured pz_group_eval.
     Returns the fields of lbfgs() with "x": device FP32 [4][n_groups] instead of the
-    per-line corrections."""
+    per-line corrections.  process_group: as for lbfgs (the groups must be the same on
+    every rank)."""
     import torch
 
     from . import pz_group_eval, pz_set_line_groups
@@ -122,7 +160,7 @@ def lbfgs_groups(synth, y, w, group_of_line, n_groups, n_updates=40, history=10,
         pz_group_eval(synth.ctx, y, w, x32, loss, g, stream)
         return loss[0], g.view(-1)
 
-    x, res = _minimise(set_and_eval, 4 * G, dev, n_updates, history, resume)
+    x, res = _minimise(set_and_eval, 4 * G, dev, n_updates, history, resume, process_group)
     res["groups"] = x.view(4, G).float().clone()
     return res
 
