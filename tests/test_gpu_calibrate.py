@@ -87,3 +87,54 @@ def test_grouped_lbfgs_calibration():
     np.testing.assert_array_equal(gf, xf[0][q])
     np.testing.assert_array_equal(g6, xf[3][q])
     s.close()
+
+
+@pytest.mark.timeout(300)
+def test_joint_fit_through_one_nccl_rank_matches_the_plain_fit():
+    """The device path of the joint calibration over ranks: with one NCCL rank the all-reduce
+    of loss and gradient and the broadcast of the starting point are identities, so the fit
+    through process_group= must equal the plain fit bit for bit.  The plain FP64 form is
+    used because it is bit-reproducible from run to run (the mixed form's near-core atomics
+    are not)."""
+    import os
+    import socket
+
+    import torch
+    import torch.distributed as dist
+    if not dist.is_nccl_available():
+        pytest.skip("torch.distributed has no NCCL backend")
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+    saved = {k: os.environ.get(k) for k in ("MASTER_ADDR", "MASTER_PORT")}
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    b = I.small_batch(n_stars=2, span_nm=3.0, seed=31)
+    nl = b.lines.n_lines
+    rng = np.random.default_rng(12)
+    s = pz.Synthesizer(b, pz.PZ_FP64)
+    s.set_corrections(rng.normal(0, 0.1, nl).astype(np.float32), rng.normal(0, 0.2, nl).astype(np.float32), None)
+    f_true = s.forward()
+    y = (f_true + torch.tensor(rng.normal(0, 1e-3, tuple(f_true.shape)), dtype=torch.float32, device=dev)).contiguous()
+    w = torch.full_like(y, 1e6)
+    dist.init_process_group("nccl", rank=0, world_size=1, device_id=dev)
+    try:
+        out = []
+        for pg in (None, dist.group.WORLD):
+            s.set_corrections(np.zeros(nl, np.float32), np.zeros(nl, np.float32), None)
+            s.forward()
+            out.append(calibrate.lbfgs(s, y, w, n_updates=10, process_group=pg))
+    finally:
+        dist.destroy_process_group()
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    plain, joint = out
+    assert np.array_equal(plain["dlog_gf"].cpu().numpy(), joint["dlog_gf"].cpu().numpy())
+    assert np.array_equal(plain["dlog_gamma6"].cpu().numpy(), joint["dlog_gamma6"].cpu().numpy())
+    assert plain["loss_start"] == joint["loss_start"] and plain["loss_final"] == joint["loss_final"]
+    assert plain["evals"] == joint["evals"]
+    assert joint["loss_final"] < 0.2 * joint["loss_start"]
