@@ -733,11 +733,14 @@ def run_scaling(args, dev, tiling=None):
     1e4 .. 3e5 over 300-1000 nm (windows of fixed width in wavelength), and span
     300-400 .. 300-1000 nm at R_grid = 3e5 (the line density of the full list); per point
     the wall of one spectrum (line opacity, flux, f) with every pair and with the centre
-    test at eta = 1e-3, CUDA events over `reps` forwards after one warm-up."""
+    test at eta = 1e-3, CUDA events over `reps` forwards after one warm-up.  Each point
+    runs the forward tiling the autotuner picks for its shape (cached by shape class;
+    --no-autotune: the tiling of the headline)."""
     import torch
 
     import paper_2607_24141_gb300 as pz
     from paper_2607_24141_gb300 import inputs as I
+    from paper_2607_24141_gb300 import tuning
     stream = torch.cuda.current_stream()
     reps = max(1, args.scaling_reps)
     pts = [("R_grid", R, dict(R=R)) for R in (1e4, 3e4, 1e5, 3e5)] + \
@@ -746,7 +749,10 @@ def run_scaling(args, dev, tiling=None):
     for kind, val, kw in pts:
         prob = I.config2_sweep_point(**kw)
         s = pz.Synthesizer(prob, pz.PZ_MIXED, device=dev.index)
-        if tiling is not None:
+        used = tiling
+        if not args.no_autotune:
+            used = tuning.autotune_cached(s, with_backward=False, reps=1, stream=stream)["tiling"]
+        elif tiling is not None:
             pz.pz_set_tiling(s.ctx, *tiling)
         f = torch.empty(prob.grid.n_lambda, dtype=torch.float32, device=dev)
 
@@ -774,7 +780,8 @@ def run_scaling(args, dev, tiling=None):
         row = {"sweep": kind, "value": val, "R_grid": prob.grid.R_grid, "n_lambda": prob.grid.n_lambda,
                "n_lines": prob.lines.n_lines, "W": prob.lines.half_window, "evals": s.n_evals,
                "ms_all_pairs": ms_all, "ms_centre_test": ms_cut,
-               "kept_pair_frac": kept / max(prob.lines.n_lines * prob.atmos.n_depth, 1)}
+               "kept_pair_frac": kept / max(prob.lines.n_lines * prob.atmos.n_depth, 1),
+               "tiling": list(used) if used is not None else None}
         s.close()
         del prob
         out.append(row)
@@ -783,7 +790,8 @@ def run_scaling(args, dev, tiling=None):
     s1 = by[("span_nm", 100.0)]
     return {"workload": "config-2 recipe (solar, 80 species, centres ~ lambda^-2, 3e6 lines over 300-1000 nm): "
                         "R_grid sweep with W = 2,000 R / 3e5 and span sweep from 300 nm at R_grid = 3e5; f at full "
-                        "resolution; mean of %d forwards after one warm-up" % reps,
+                        "resolution; mean of %d forwards after one warm-up; per-point tiling from the "
+                        "autotuner" % reps,
             "points": out,
             "R_x30_wall_ratio_all_pairs": sp["ms_all_pairs"] / rs["ms_all_pairs"],
             "R_x30_wall_ratio_centre_test": sp["ms_centre_test"] / rs["ms_centre_test"],
