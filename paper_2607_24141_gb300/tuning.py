@@ -10,6 +10,8 @@ it is stored in a JSON file keyed by
 * the shape class of the context: stars, precision, layers, and the grid size, the
   window half-width and the line density (lines per grid point and star), each rounded
   on a log2 scale,
+* and whether the tiling was timed on the forward alone (suffix "|fwd"): the backward
+  kernels' best tiling can differ, so a forward-only entry never serves a fwd+bwd context,
 
 and applied with ``pz_set_tiling`` when the same key comes back.  Host-side
 bookkeeping only: nothing of the synthesis runs here.
@@ -66,9 +68,15 @@ def shape_class(synth) -> str:
     return shape_class_of(synth.prob, synth.precision)
 
 
-def lookup(prob, precision: int, device=None, path: str = DEFAULT_CACHE):
+def cache_key(gpu: str, lib_hash: str, shape: str, with_backward: bool = True) -> str:
+    """Key of a cache entry: GPU, library build, shape class, and "|fwd" for a tiling
+    timed on the forward alone."""
+    return "%s|%s|%s%s" % (gpu, lib_hash, shape, "" if with_backward else "|fwd")
+
+
+def lookup(prob, precision: int, device=None, path: str = DEFAULT_CACHE, with_backward: bool = True):
     """The cached tiling (5 ints) for this GPU, library build and problem shape, or None."""
-    key = "%s|%s|%s" % (gpu_key(device), library_hash(), shape_class_of(prob, precision))
+    key = cache_key(gpu_key(device), library_hash(), shape_class_of(prob, precision), with_backward)
     entry = _load(path).get(key)
     if entry and len(entry.get("tiling", ())) == 5:
         return tuple(entry["tiling"])
@@ -104,7 +112,7 @@ def autotune_cached(synth, path: str = DEFAULT_CACHE, with_backward: bool = True
     """Apply the cached tiling for this GPU, library build and workload shape, or tune
     (pz_autotune) and store the result.  Returns pz_autotune's dict plus "cached"
     (True when nothing was timed) and "key"."""
-    key = "%s|%s|%s" % (gpu_key(synth.device.index), library_hash(), shape_class(synth))
+    key = cache_key(gpu_key(synth.device.index), library_hash(), shape_class(synth), with_backward)
     data = _load(path)
     entry = data.get(key)
     if entry and len(entry.get("tiling", ())) == 5:

@@ -48,3 +48,23 @@ def test_second_call_applies_the_stored_tiling(tmp_path):
     f = s.forward()                                # the applied tiling runs
     assert bool((f > 0).all())
     s.close()
+
+
+def test_forward_only_entries_have_their_own_key():
+    """A tiling timed on the forward alone is stored under its own key, so that a context
+    that runs the backward too never picks it up; the fwd+bwd key keeps three fields."""
+    both = tuning.cache_key("GPU/152sm", "0123456789abcdef", "S1-p1-nd72-nl15-W11-lpp3")
+    fwd = tuning.cache_key("GPU/152sm", "0123456789abcdef", "S1-p1-nd72-nl15-W11-lpp3", with_backward=False)
+    assert both == "GPU/152sm|0123456789abcdef|S1-p1-nd72-nl15-W11-lpp3"
+    assert fwd == both + "|fwd" and fwd != both
+
+
+def test_committed_cache_entries_are_well_formed():
+    data = tuning._load(tuning.DEFAULT_CACHE)
+    assert data
+    for key, entry in data.items():
+        parts = key.split("|")
+        assert len(parts) in (3, 4) and (len(parts) == 3 or parts[3] == "fwd"), key
+        assert len(entry["tiling"]) == 5 and entry["fwd_ms"] > 0
+        if len(parts) == 4:
+            assert not entry["bwd_ms"]          # forward-only tuning times no backward
